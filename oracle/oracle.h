@@ -1,0 +1,97 @@
+/* FP64 CPU oracle for the batched FLASH time step (arxiv 2604.17513).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; both sides read the same
+ * seeded scene arrays and nothing else.
+ *
+ * What it computes, in the paper's order (Algorithm 1, "Multi-Env GPU-based
+ * Pipeline"; Sec. III "Preliminary" and Sec. IV-B):
+ *   setup   A = M + h^2 sum_i w_i G_i^T G_i  (Sec. III-B), dense Cholesky
+ *   step    collision detection, q~ = q_t + h v_t + h^2 g, then k iterations of
+ *             p_i = project(G_i q^{k-1})                      (Eq. internal)
+ *             b = M q~ + h^2 sum w_i G_i^T p_i               (Sec. III-B)
+ *             J, E, g = b + J^T gamma^{k-1}, h = -phi + J q^{k-1} (Sec. III-C)
+ *             Z = J M^-1 J^T + E  (lite metric, Sec. IV-B.1) or J A^-1 J^T + E
+ *             dgamma = Z^-1 (h - J A^-1 g)                    (Algorithm 1)
+ *             q^k = A^-1 (b + J^T gamma^k)                    (Eq. correction)
+ *           then v = (q - q_t)/h.
+ * gamma = h^2 * lambda throughout (kg m); impulses are gamma/h.
+ *
+ * Readings of the paper where it is silent are listed in the design notes
+ * and restated beside the code that takes them.
+ */
+#ifndef FLASH_ORACLE_H
+#define FLASH_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct OrMesh OrMesh;
+
+/* element types */
+#define OR_TRI 0
+#define OR_TET 1
+/* obstacle types */
+#define OR_PLANE 1
+#define OR_SPHERE 2
+#define OR_BOX 3
+
+/* dp[] (double parameters) */
+#define OR_DP_H 0
+#define OR_DP_GX 1
+#define OR_DP_GY 2
+#define OR_DP_GZ 3
+#define OR_DP_TOL 4
+#define OR_DP_MAXFORCE 5
+#define OR_DP_TAU 6
+#define OR_DP_MARGIN 7
+#define OR_DP_MU 8
+#define OR_NDP 9
+/* ip[] (integer parameters) */
+#define OR_IP_KMAX 0
+#define OR_IP_KMIN 1
+#define OR_IP_KCAP 2
+#define OR_IP_MODE 3   /* 0: exactly k_max iterations; 1: until r_ncp <= tol */
+#define OR_IP_METRIC 4 /* 0: lite  J M^-1 J^T + E;  1: full  J A^-1 J^T + E */
+#define OR_NIP 5
+
+OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elems,
+                    const double *mass, double w_stretch, double w_bend, double h);
+void or_mesh_free(OrMesh *m);
+int or_mesh_hinges(const OrMesh *m);
+void or_mesh_matrix(const OrMesh *m, double *A_out);             /* dense n x n */
+void or_solve(const OrMesh *m, const double *rhs, double *out);  /* A^-1 rhs, [n][3] */
+void or_project(const OrMesh *m, const double *q, double *p);    /* [ne][9] row-major 3x2|3x3 */
+void or_assemble_b(const OrMesh *m, const double *qt, const double *p, double *b);
+double or_pd_energy(const OrMesh *m, const double *q, const double *qt, const double *p);
+void or_closest_rotation(int cols, const double *F, double *R); /* 3x2 or 3x3, row-major */
+
+/* signed distance, unit normal and (optionally) obstacle point displacement
+ * over the step for one point; pose = (p, qw, qx, qy, qz) */
+double or_sdf(int type, const double *dims, const double *pose, const double *x, double *nrm);
+
+int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
+              const double *pose_th, const double *q, const double *v, int cap, int *cvert,
+              int *cobs);
+
+int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const int *otype,
+                  const double *odims, const double *ocomp, const double *pose_t,
+                  const double *pose_th, double *q, double *v, const double *q_init, int count,
+                  const int *cvert, const int *cobs, double *cgamma, int *iters, double *rncp,
+                  double *trace);
+
+/* NCP residual of (q, gamma) for a given contact list (max-norm, metres) */
+double or_residual(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
+                   const double *ocomp, const double *pose_t, const double *pose_th,
+                   const double *q_t, const double *q, int count, const int *cvert, const int *cobs,
+                   const double *cgamma);
+
+/* fischer-burmeister value, exported for the closed-form pins */
+double or_fb(double a, double b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,332 @@
+"""Seeded synthetic scenes for the batched deformable + contact time step.
+
+This module is INPUT DATA ONLY: rest geometry, element connectivity, lumped
+masses, material weights, per-environment parameters and kinematic obstacle
+trajectories.  It contains none of the solver's arithmetic (no deformation
+gradients, no system matrix, no projections, no contact law), so both the FP64
+oracle and the CUDA path can consume the same arrays without sharing method
+code.
+
+Every random draw comes from a counter-based Philox stream keyed by
+``(seed << 32) | env``, so scene ``e`` of a batch is identical whether the
+batch holds 1 or 4096 environments and on x86 and Arm hosts alike.
+
+Conventions (shared by oracle and library):
+  * z is up, gravity (0, 0, -9.81) m/s^2.
+  * obstacle pose = (px, py, pz, qw, qx, qy, qz): body -> world.
+  * obstacle types: PLANE (normal = body +z through the pose origin),
+    SPHERE (dims[0] = radius), BOX (dims = half extents).
+  * positions are [n][3] (vertex-major, xyz), float64 here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NONE, PLANE, SPHERE, BOX = 0, 1, 2, 3
+TRI, TET = 0, 1
+MODE_FIXED, MODE_TOL = 0, 1
+IDENTITY_POSE = (0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
+
+
+def env_rng(seed: int, env: int) -> np.random.Generator:
+    """Counter-based stream for environment ``env`` of scene seed ``seed``."""
+    return np.random.Generator(np.random.Philox(key=(int(seed) << 32) | int(env)))
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+def cloth_grid(nx: int, ny: int, side_x: float, side_y: float | None = None):
+    """Square/rectangular cloth in the z=0 plane, centred at the origin.
+
+    Cells are split along alternating diagonals, so a 16x16 grid has 450
+    triangles and a 32x32 grid 1922.  Returns (rest [n][3], tris [T][3]).
+    """
+    side_y = side_x if side_y is None else side_y
+    xs = np.linspace(-side_x / 2, side_x / 2, nx)
+    ys = np.linspace(-side_y / 2, side_y / 2, ny)
+    rest = np.zeros((nx * ny, 3))
+    for j in range(ny):
+        for i in range(nx):
+            rest[j * nx + i] = (xs[i], ys[j], 0.0)
+    tris = []
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            a, b = j * nx + i, j * nx + i + 1
+            c, d = (j + 1) * nx + i, (j + 1) * nx + i + 1
+            if (i + j) % 2 == 0:
+                tris += [(a, b, d), (a, d, c)]
+            else:
+                tris += [(a, b, c), (b, d, c)]
+    return rest, np.asarray(tris, dtype=np.int32)
+
+
+_EVEN = ((1, 2, 4, 7), (0, 1, 2, 4), (3, 2, 1, 7), (5, 4, 7, 1), (6, 7, 4, 2))
+_ODD = ((0, 3, 5, 6), (1, 0, 3, 5), (2, 3, 0, 6), (4, 5, 6, 0), (7, 6, 5, 3))
+
+
+def tet_block(cx: int, cy: int, cz: int, sx: float, sy: float, sz: float):
+    """Box of cx*cy*cz cubes, 5 tets per cube with alternating parity.
+
+    The block spans [-sx/2, sx/2] x [-sy/2, sy/2] x [0, sz].  Every tet is
+    ordered with positive orientation.  Returns (rest [n][3], tets [E][4]).
+    """
+    nx, ny, nz = cx + 1, cy + 1, cz + 1
+    rest = np.zeros((nx * ny * nz, 3))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                rest[(k * ny + j) * nx + i] = (-sx / 2 + sx * i / cx, -sy / 2 + sy * j / cy, sz * k / cz)
+    tets = []
+    for k in range(cz):
+        for j in range(cy):
+            for i in range(cx):
+                corner = [((k + (c >> 2)) * ny + (j + ((c >> 1) & 1))) * nx + i + (c & 1) for c in range(8)]
+                for t in (_EVEN if (i + j + k) % 2 == 0 else _ODD):
+                    v = [corner[c] for c in t]
+                    e1, e2, e3 = (rest[v[1]] - rest[v[0]], rest[v[2]] - rest[v[0]], rest[v[3]] - rest[v[0]])
+                    if np.dot(np.cross(e1, e2), e3) < 0:
+                        v[2], v[3] = v[3], v[2]
+                    tets.append(v)
+    return rest, np.asarray(tets, dtype=np.int32)
+
+
+def lumped_tet_mass(rest, tets, density):
+    """Per-vertex mass: a quarter of rho*volume of every incident tet."""
+    m = np.zeros(len(rest))
+    for t in tets:
+        e1, e2, e3 = rest[t[1]] - rest[t[0]], rest[t[2]] - rest[t[0]], rest[t[3]] - rest[t[0]]
+        vol = abs(np.dot(np.cross(e1, e2), e3)) / 6.0
+        m[t] += density * vol / 4.0
+    return m
+
+
+# --------------------------------------------------------------------------
+# scene container
+# --------------------------------------------------------------------------
+@dataclass
+class Scene:
+    """One mesh template shared by ``n_envs`` environments.
+
+    Arrays (float64 unless noted):
+      rest [n][3], elems int32 [E][3|4], mass [n]
+      q0, v0 [N][n][3]
+      mu [N], stiff [N] (multiplies w_stretch per environment)
+      obs_type int32 [N][K], obs_dims [N][K][3], obs_comp [N][K] (m/N)
+      poses [N][S+1][K][7]: obstacle pose at the start of step s (s = 0..S)
+    """
+    name: str
+    elem_type: int
+    rest: np.ndarray
+    elems: np.ndarray
+    mass: np.ndarray
+    w_stretch: float
+    w_bend: float
+    q0: np.ndarray
+    v0: np.ndarray
+    mu: np.ndarray
+    stiff: np.ndarray
+    obs_type: np.ndarray
+    obs_dims: np.ndarray
+    obs_comp: np.ndarray
+    poses: np.ndarray
+    h: float = 0.01
+    gravity: tuple = (0.0, 0.0, -9.81)
+    k_max: int = 10
+    k_min: int = 1
+    k_cap: int = 200
+    mode: int = MODE_FIXED
+    tol_ncp: float = 1e-5
+    maxforce: float = 1e10
+    thickness: float = 1e-3
+    margin: float = 1e-2
+    steps: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_envs(self) -> int:
+        return self.q0.shape[0]
+
+    @property
+    def n_verts(self) -> int:
+        return self.rest.shape[0]
+
+    @property
+    def n_obs(self) -> int:
+        return self.obs_type.shape[1]
+
+    def subset(self, envs) -> "Scene":
+        """The same scene restricted to the listed environments."""
+        envs = np.asarray(envs)
+        kw = {k: getattr(self, k) for k in self.__dataclass_fields__}
+        for k in ("q0", "v0", "mu", "stiff", "obs_type", "obs_dims", "obs_comp", "poses"):
+            kw[k] = getattr(self, k)[envs].copy()
+        return Scene(**kw)
+
+
+def _pose(p, q=(1.0, 0.0, 0.0, 0.0)):
+    return np.array([p[0], p[1], p[2], q[0], q[1], q[2], q[3]], dtype=np.float64)
+
+
+def _static_poses(n_envs, steps, poses_k):
+    """[N][S+1][K][7] array holding a fixed pose per obstacle."""
+    out = np.zeros((n_envs, steps + 1, len(poses_k), 7))
+    for k, p in enumerate(poses_k):
+        out[:, :, k, :] = p
+    return out
+
+
+# --------------------------------------------------------------------------
+# the five workloads
+# --------------------------------------------------------------------------
+def cloth_drop(seed: int = 0, n_side: int = 16, side: float = 0.5, steps: int = 200,
+               n_envs: int = 1, mu: float = 0.3, k_max: int = 10) -> Scene:
+    """Square cloth dropped 0.3 m onto a static sphere (r = 0.15 m) and the ground.
+
+    16x16 vertices, 0.5 m side, 0.1 kg spread evenly over the vertices, stretch
+    weight 1e4 and bending weight 10, z-perturbation N(0, 1e-3 m) per vertex,
+    h = 1/100 s, Coulomb mu = 0.3, 10 local-global iterations per step.
+    """
+    rest, tris = cloth_grid(n_side, n_side, side)
+    n = len(rest)
+    mass = np.full(n, 0.1 / n)
+    q0 = np.zeros((n_envs, n, 3))
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        q0[e] = rest
+        q0[e, :, 2] = 0.6 + g.normal(0.0, 1e-3, n)
+    obs_type = np.tile(np.array([PLANE, SPHERE], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, 2, 3))
+    obs_dims[:, 1, 0] = 0.15
+    poses = _static_poses(n_envs, steps, [_pose((0, 0, 0)), _pose((0, 0, 0.15))])
+    return Scene("cloth_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0),
+                 np.full(n_envs, mu), np.ones(n_envs), obs_type, obs_dims,
+                 np.zeros((n_envs, 2)), poses, h=0.01, k_max=k_max, steps=steps)
+
+
+def _waypoint_path(g, start, n_seg, speed, bound, steps, h, t_hold):
+    """Piecewise-linear xy path: hold for t_hold, then n_seg straight segments
+    at constant speed towards random waypoints inside [-bound, bound]^2.
+    Returns positions [steps+1][2]."""
+    pts = [np.asarray(start, float)]
+    for _ in range(n_seg):
+        pts.append(g.uniform(-bound, bound, 2))
+    out = np.zeros((steps + 1, 2))
+    seg, pos, t = 0, pts[0].copy(), 0.0
+    for s in range(steps + 1):
+        out[s] = pos
+        t += h
+        if t <= t_hold:
+            continue
+        move = speed * h
+        while move > 0 and seg < n_seg:
+            tgt = pts[seg + 1]
+            d = tgt - pos
+            L = np.linalg.norm(d)
+            if L <= move:
+                pos, move, seg = tgt.copy(), move - L, seg + 1
+            else:
+                pos, move = pos + d / L * move, 0.0
+    return out
+
+
+def cloth_gripper(seed: int = 1, n_envs: int = 1024, n_side: int = 32, side: float = 0.5,
+                  steps: int = 500, k_max: int = 10, squeeze: float = 5e-4,
+                  finger_comp: float = 5e-4) -> Scene:
+    """Cloth lying on the ground, pinched against it by a kinematic two-finger box
+    gripper and dragged along a seeded piecewise-linear path.
+
+    Fingers are 2x2x4 cm boxes 3 cm apart along x, lowered in the first 0.1 s
+    until their bottom faces sit ``squeeze`` below the cloth's upper surface
+    (thickness 1 mm), then moved in xy through 4-8 random waypoints at a speed
+    drawn from U[0.05, 0.3] m/s.  mu ~ U[0.2, 0.8] per environment (ground and
+    fingers); the finger contacts carry a normal compliance (m/N) so that the
+    pinch force is determined.  h = 1/100 s.
+    """
+    rest, tris = cloth_grid(n_side, n_side, side)
+    n = len(rest)
+    mass = np.full(n, 0.1 * side * side / 0.25 / n)
+    tau = 1e-3
+    q0 = np.repeat(rest[None], n_envs, 0).copy()
+    q0[:, :, 2] = tau
+    K = 3
+    obs_type = np.tile(np.array([PLANE, BOX, BOX], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, K, 3))
+    obs_dims[:, 1:, :] = (0.01, 0.01, 0.02)
+    obs_comp = np.zeros((n_envs, K))
+    obs_comp[:, 1:] = finger_comp
+    mu = np.zeros(n_envs)
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    h = 0.01
+    z_press = 2 * tau - squeeze + 0.02      # box centre when pressing
+    z_start = z_press + 0.01
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        mu[e] = g.uniform(0.2, 0.8)
+        speed = g.uniform(0.05, 0.3)
+        n_seg = int(g.integers(4, 9))
+        start = g.uniform(-0.12, 0.12, 2)
+        path = _waypoint_path(g, start, n_seg, speed, 0.12, steps, h, t_hold=0.15)
+        poses[e, :, 0] = _pose((0, 0, 0))
+        for s in range(steps + 1):
+            t = s * h
+            z = z_press + (z_start - z_press) * max(0.0, 1.0 - t / 0.1)
+            poses[e, s, 1] = _pose((path[s, 0] - 0.015, path[s, 1], z))
+            poses[e, s, 2] = _pose((path[s, 0] + 0.015, path[s, 1], z))
+    return Scene("cloth_gripper", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0),
+                 mu, np.ones(n_envs), obs_type, obs_dims, obs_comp, poses, h=h,
+                 k_max=k_max, thickness=tau, steps=steps)
+
+
+def tet_squeeze(seed: int = 1, n_envs: int = 4096, cubes=(8, 8, 4), size=(0.08, 0.08, 0.04),
+                steps: int = 100, k_max: int = 10, mu: float = 0.5) -> Scene:
+    """Soft tet block on the ground squeezed by a kinematic parallel gripper.
+
+    8x8x4 cubes x 5 tets = 1280 tets, 405 vertices, 8x8x4 cm, density 1000
+    kg/m^3, per-environment stiffness log-uniform in [1e3, 1e5] (weight per
+    unit rest volume), closing depth U[0.5, 2] cm reached after 0.1 s and then
+    held, h = 1/200 s.  Plates are 1 x 6 x 6 cm boxes closing along x.
+    """
+    rest, tets = tet_block(*cubes, *size)
+    n = len(rest)
+    mass = lumped_tet_mass(rest, tets, 1000.0)
+    q0 = np.repeat(rest[None], n_envs, 0).copy()
+    K = 3
+    obs_type = np.tile(np.array([PLANE, BOX, BOX], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, K, 3))
+    obs_dims[:, 1:, :] = (0.005, 0.03, 0.03)
+    stiff = np.zeros(n_envs)
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    h = 1.0 / 200
+    half = size[0] / 2 + 0.005
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        stiff[e] = 10.0 ** g.uniform(3.0, 5.0)
+        depth = g.uniform(0.005, 0.02)
+        poses[e, :, 0] = _pose((0, 0, 0))
+        for s in range(steps + 1):
+            c = 0.5 * depth * min(1.0, s * h / 0.1)
+            poses[e, s, 1] = _pose((-half + c, 0, size[2] / 2))
+            poses[e, s, 2] = _pose((half - c, 0, size[2] / 2))
+    return Scene("tet_squeeze", TET, rest, tets, mass, 1.0, 0.0, q0, np.zeros_like(q0),
+                 np.full(n_envs, mu), stiff, obs_type, obs_dims, np.zeros((n_envs, K)), poses,
+                 h=h, k_max=k_max, thickness=0.0, steps=steps)
+
+
+def incline_particle(theta: float, mu: float, steps: int = 20, h: float = 0.01, mass: float = 0.01):
+    """A single free particle resting on a plane tilted by ``theta`` about y.
+
+    Used for the Coulomb stick/slide pin: the particle sticks iff
+    tan(theta) <= mu.  The mesh is one vertex with no elements.
+    """
+    rest = np.zeros((1, 3))
+    nrm = np.array([-np.sin(theta), 0.0, np.cos(theta)])
+    tau = 1e-3
+    q0 = (rest + tau * nrm)[None].copy()
+    half = theta / 2
+    poses = _static_poses(1, steps, [_pose((0, 0, 0), (np.cos(half), 0.0, -np.sin(half), 0.0))])
+    return Scene("incline", TRI, rest, np.zeros((0, 3), np.int32), np.array([mass]), 0.0, 0.0,
+                 q0, np.zeros_like(q0), np.array([mu]), np.ones(1), np.array([[PLANE]], np.int32),
+                 np.zeros((1, 1, 3)), np.zeros((1, 1)), poses, h=h, thickness=tau, steps=steps)

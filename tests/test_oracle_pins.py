@@ -1,0 +1,310 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant of the method, a library routine that a special case
+reduces to, or brute-force enumeration.  No GPU.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_17513_gb300 import scenes
+
+
+def rot(axis, ang):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+# ------------------------------------------------------------ local step
+def test_closest_rotation_matches_svd_polar():
+    """Closest 3x3 rotation = U diag(1,1,det UV^T) V^T from numpy's SVD;
+    closest 3x2 orthonormal-column matrix = U V^T (thin SVD)."""
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        F = rng.normal(size=(3, 3))
+        U, s, Vt = np.linalg.svd(F)
+        d = np.sign(np.linalg.det(U @ Vt))
+        ref = U @ np.diag([1, 1, d]) @ Vt
+        assert np.abs(oracle.closest_rotation(F) - ref).max() < 1e-10
+        F2 = rng.normal(size=(3, 2))
+        U2, s2, Vt2 = np.linalg.svd(F2, full_matrices=False)
+        assert np.abs(oracle.closest_rotation(F2) - U2 @ Vt2).max() < 1e-10
+
+
+def test_closest_rotation_rest_and_equivariance():
+    """A rotation projects to itself; R F projects to R p (Eq. internal's
+    constitutive manifold is rotation invariant)."""
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        Q = rot(rng.normal(size=3), rng.uniform(0, np.pi))
+        assert np.abs(oracle.closest_rotation(Q) - Q).max() < 1e-12
+        F = rng.normal(size=(3, 3)) * 0.2 + np.eye(3)
+        p = oracle.closest_rotation(F)
+        assert np.abs(oracle.closest_rotation(Q @ F) - Q @ p).max() < 1e-10
+        F2 = rng.normal(size=(3, 2))
+        p2 = oracle.closest_rotation(F2)
+        assert np.abs(oracle.closest_rotation(Q @ F2) - Q @ p2).max() < 1e-10
+
+
+# ------------------------------------------------------------ system matrix
+def test_cloth_topology_counts():
+    """16x16 grid: 450 triangles and 645 interior edges (bending hinges)."""
+    sc = scenes.cloth_drop()
+    m = oracle.Mesh.from_scene(sc)
+    assert m.ne == 450 and m.hinges == 645
+    sc2 = scenes.cloth_gripper(n_envs=1, steps=1)
+    assert len(sc2.elems) == 1922 and oracle.Mesh.from_scene(sc2).hinges == 2821
+    sc3 = scenes.tet_squeeze(n_envs=1, steps=1)
+    assert sc3.n_verts == 405 and len(sc3.elems) == 1280
+
+
+@pytest.mark.parametrize("kind", ["tri", "tet"])
+def test_system_matrix_spd_and_rigid_null_space(kind):
+    """A = M + h^2 sum w G^T G is symmetric positive definite and G annihilates
+    translations, so every row of A sums to the vertex mass."""
+    sc = scenes.cloth_drop() if kind == "tri" else scenes.tet_squeeze(n_envs=1, steps=1)
+    m = oracle.Mesh.from_scene(sc)
+    A = m.matrix()
+    assert np.abs(A - A.T).max() < 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+    assert np.abs(A.sum(1) - sc.mass).max() < 1e-10 * np.abs(A).max()
+
+
+def test_solve_residual():
+    """Cholesky solve is backward stable: |A x - b| <= 1e-14 |A| |x| (FP64)."""
+    sc = scenes.cloth_drop()
+    m = oracle.Mesh.from_scene(sc)
+    A = m.matrix()
+    b = np.random.default_rng(2).normal(size=(sc.n_verts, 3))
+    x = m.solve(b)
+    assert np.linalg.norm(A @ x - b) <= 1e-14 * np.linalg.norm(A, 2) * np.linalg.norm(x)
+
+
+def test_uniform_stretch_energy_closed_form():
+    """A flat sheet stretched uniformly by (1+eps) along x: F = diag(1+eps, 1)
+    in-plane, its closest rotation is I, so the stretch energy is
+    w/2 * area * eps^2 and the flat bending energy is 0."""
+    sc = scenes.cloth_drop()
+    m = oracle.Mesh.from_scene(sc)
+    eps = 0.013
+    q = sc.rest.copy()
+    q[:, 0] *= 1 + eps
+    p = m.project(q)
+    E = m.energy(q, q, p)
+    area = 0.5 * 0.5
+    assert abs(E - 0.5 * sc.w_stretch * area * eps ** 2) < 1e-10 * E
+
+
+def test_bending_annihilates_affine_maps_and_energy_hessian():
+    """Bending energy vanishes on any affine image of the flat rest mesh; the
+    PD energy's Hessian (by central differences of the energy) equals A/h^2
+    for fixed projections (A = M + h^2 sum w G^T G + bending)."""
+    sc = scenes.cloth_drop()
+    sc.w_stretch = 0.0
+    m = oracle.Mesh.from_scene(sc)
+    rng = np.random.default_rng(3)
+    Aff = np.eye(3) + 0.3 * rng.normal(size=(3, 3))
+    q = sc.rest @ Aff.T + rng.normal(size=3)
+    p = np.zeros((m.ne, 9))
+    assert m.energy(q, q, p) < 1e-18
+    # Hessian along random directions
+    sc2 = scenes.cloth_drop()
+    m2 = oracle.Mesh.from_scene(sc2)
+    A = m2.matrix()
+    q0 = sc2.rest + 0.01 * rng.normal(size=sc2.rest.shape)
+    p0 = m2.project(q0)
+    for _ in range(3):
+        d = rng.normal(size=q0.shape)
+        t = 1e-3
+        e_p, e_0, e_m = (m2.energy(q0 + t * d, q0, p0), m2.energy(q0, q0, p0), m2.energy(q0 - t * d, q0, p0))
+        fd = (e_p - 2 * e_0 + e_m) / t ** 2
+        exact = np.sum(d * (A @ d)) / sc2.h ** 2
+        assert abs(fd - exact) < 1e-6 * abs(exact)
+
+
+# ------------------------------------------------------------ whole step
+def test_rest_shape_stays_at_rest():
+    sc = scenes.cloth_drop(steps=5)
+    sc.gravity = (0.0, 0.0, 0.0)
+    sc.q0[0] = sc.rest + [0, 0, 0.6]
+    st = oracle.rollout(sc, 0, 5)
+    # rounding only: cond(A) ~ 7e5 for this mesh, so ~1e-16 * 7e5 * |q| per solve
+    assert np.abs(st.q - sc.q0[0]).max() < 1e-9
+    assert np.abs(st.v).max() < 1e-7
+
+
+def test_free_fall_closed_form():
+    """Rigid translation under gravity with implicit Euler: z_n = z_0 - g h^2 n(n+1)/2."""
+    sc = scenes.cloth_drop(steps=12)
+    sc.q0[0] = sc.rest + [0, 0, 2.0]
+    st = oracle.rollout(sc, 0, 12)
+    n = 12
+    z = 2.0 - 9.81 * sc.h ** 2 * n * (n + 1) / 2
+    # rounding of the solves (cond(A) ~ 7e5) is ~1e-10 per step; a dropped or
+    # misplaced h^2 g term would show at 1e-3
+    assert np.abs(st.q[:, 2] - z).max() < 1e-8
+    assert np.abs(st.q[:, :2] - sc.rest[:, :2]).max() < 1e-8
+
+
+def test_local_global_energy_monotone():
+    """Without contact each local step (fixed q) and each global step (fixed p)
+    does not increase E(q, p) = |M^1/2 (q - q~)|^2 / 2h^2 + sum w/2 |Gq - p|^2."""
+    sc = scenes.cloth_drop()
+    m = oracle.Mesh.from_scene(sc)
+    rng = np.random.default_rng(4)
+    qt = sc.rest + [0, 0, 0.5] + 0.02 * rng.normal(size=sc.rest.shape)
+    q = qt.copy()
+    p = m.project(q)
+    E = m.energy(q, qt, p)
+    for _ in range(15):
+        q = m.solve(m.assemble_b(qt, p))
+        E1 = m.energy(q, qt, p)
+        p = m.project(q)
+        E2 = m.energy(q, qt, p)
+        assert E1 <= E * (1 + 1e-12) and E2 <= E1 * (1 + 1e-12)
+        E = E2
+
+
+def test_particle_resting_on_plane():
+    """Normal contact: gamma_n = m g h^2, impulse m g h, zero gap."""
+    sc = scenes.incline_particle(0.0, 0.3, steps=5)
+    st = oracle.rollout(sc, 0, 5, mode=1, tol=1e-12, k_cap=50)
+    m, g, h = sc.mass[0], 9.81, sc.h
+    assert abs(st.gamma[0, 0] - m * g * h * h) < 1e-12
+    assert abs(st.q[0, 2] - sc.thickness) < 1e-12
+    assert np.abs(st.v).max() < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.35])
+def test_coulomb_incline_stick_slide(theta):
+    """A particle on an incline sticks iff tan(theta) <= mu; sliding follows
+    x_n = a h^2 n(n+1)/2 with a = g (sin theta - mu cos theta).  mu is swept
+    in steps of 0.001 around tan(theta)."""
+    t = np.tan(theta)
+    for dmu in (-0.003, -0.002, -0.001, 0.001, 0.002, 0.003):
+        mu = t + dmu
+        sc = scenes.incline_particle(theta, mu, steps=8)
+        st = oracle.rollout(sc, 0, 8, mode=1, tol=1e-13, k_cap=100)
+        disp = np.linalg.norm(st.q[0] - sc.q0[0, 0])
+        if mu >= t:
+            assert disp < 1e-12, (mu, disp)
+        else:
+            a = 9.81 * (np.sin(theta) - mu * np.cos(theta))
+            n = 8
+            assert abs(disp - a * sc.h ** 2 * n * (n + 1) / 2) < 1e-10, (mu, disp)
+
+
+def test_complementarity_at_convergence():
+    """Converged contacts: lambda_n >= 0, gap >= -1e-6 m, |h lambda_n gap| <= 1e-8,
+    |lambda_t| <= mu lambda_n, sliding contacts oppose the slip."""
+    sc = scenes.cloth_drop(steps=40)
+    mesh = oracle.Mesh.from_scene(sc)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    for s in range(30):
+        oracle.step(mesh, sc, 0, s, st)
+    qt = st.q.copy()
+    oracle.step(mesh, sc, 0, 30, st, mode=1, metric=1, tol=1e-10, k_cap=200)
+    assert st.rncp <= 1e-10 and len(st.cvert) > 0
+    for v, o, g in zip(st.cvert, st.cobs, st.gamma):
+        sd, nrm = oracle.sdf(sc.obs_type[0, o], sc.obs_dims[0, o], sc.poses[0, 31, o], st.q[v])
+        gap = sd - sc.thickness
+        lam_n = g[0] / sc.h ** 2
+        lam_t = np.linalg.norm(g[1:]) / sc.h ** 2
+        assert lam_n >= -1e-9 and gap >= -1e-6
+        assert abs(sc.h * lam_n * gap) <= 1e-8
+        assert lam_t <= sc.mu[0] * lam_n + 1e-9
+        slip = st.q[v] - qt[v]
+        slip_t = slip - nrm * np.dot(nrm, slip)
+        if np.linalg.norm(slip_t) > 1e-7:
+            assert np.dot(g[1:], slip_t) <= 1e-12
+
+
+def test_lite_and_full_metric_share_the_fixed_point():
+    """The lite metric Z = J M^-1 J^T + E changes the Newton path, not the
+    converged NCP solution (Sec. IV-B.1).  With a quadratic energy (bending
+    only, so the local step is exact) a converged contact residual means a
+    converged step, and both metrics must land on the same state."""
+    sc = _small_bending_cloth(0.05)
+    sc.mu[:] = 0.3
+    mesh = oracle.Mesh.from_scene(sc)
+    a = oracle.EnvState(sc.q0[0], sc.v0[0])
+    b = oracle.EnvState(sc.q0[0], sc.v0[0])
+    oracle.step(mesh, sc, 0, 0, a, mode=1, metric=0, tol=1e-11, k_cap=5000)
+    oracle.step(mesh, sc, 0, 0, b, mode=1, metric=1, tol=1e-11, k_cap=500)
+    assert a.rncp <= 1e-11 and b.rncp <= 1e-11 and len(a.cvert) > 0
+    assert np.abs(a.q - b.q).max() < 1e-9
+    assert b.iters < a.iters
+
+
+def _small_bending_cloth(tilt):
+    rest, tris = scenes.cloth_grid(3, 3, 0.2)
+    n = len(rest)
+    q0 = rest.copy()
+    q0[:, 2] = 1e-3 + 2e-4 + tilt * rest[:, 0]
+    v0 = np.zeros((1, n, 3))
+    v0[0, :, 2] = -0.05
+    sc = scenes.Scene("bb", scenes.TRI, rest, tris, np.full(n, 0.01), 0.0, 0.05, q0[None], v0,
+                      np.array([0.0]), np.ones(1), np.array([[scenes.PLANE]], np.int32), np.zeros((1, 1, 3)),
+                      np.zeros((1, 1)), np.tile(np.array(scenes.IDENTITY_POSE), (1, 3, 1, 1)), thickness=1e-3,
+                      margin=0.05, steps=2)
+    return sc
+
+
+@pytest.mark.parametrize("tilt", [0.02, 0.05])
+def test_brute_force_active_sets(tilt):
+    """Frictionless plane contact with a quadratic (bending-only) energy: the
+    converged NCP solution is the unique KKT point of
+    min 1/2 q^T A q - b^T q  s.t.  z_v >= tau, found by enumerating all 2^C
+    active sets."""
+    sc = _small_bending_cloth(tilt)
+    mesh = oracle.Mesh.from_scene(sc)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    qt = sc.q0[0] + sc.h * sc.v0[0] + sc.h ** 2 * np.array(sc.gravity)
+    oracle.step(mesh, sc, 0, 0, st, mode=1, tol=1e-13, k_cap=500)
+    A = mesh.matrix()
+    n = sc.n_verts
+    b = mesh.assemble_b(qt, np.zeros((len(sc.elems), 9)))
+    # only z couples to the plane; x, y are unconstrained
+    bz = b[:, 2]
+    found = []
+    for act in itertools.product([0, 1], repeat=n):
+        idx = [i for i in range(n) if act[i]]
+        k = len(idx)
+        K = np.zeros((n + k, n + k))
+        K[:n, :n] = A
+        rhs = np.zeros(n + k)
+        rhs[:n] = bz
+        for j, i in enumerate(idx):
+            K[i, n + j] = -1.0
+            K[n + j, i] = 1.0
+            rhs[n + j] = sc.thickness
+        sol = np.linalg.solve(K, rhs)
+        z, lam = sol[:n], sol[n:]
+        if np.all(z >= sc.thickness - 1e-12) and np.all(lam >= -1e-14):
+            found.append(z)
+    assert len(found) >= 1
+    for z in found[1:]:
+        assert np.abs(z - found[0]).max() < 1e-12
+    assert np.abs(st.q[:, 2] - found[0]).max() < 1e-9
+    assert 0 < sum(np.isclose(found[0], sc.thickness, atol=1e-12)) < n
+
+
+# ------------------------------------------------------------ warm-start MLP
+def test_mlp_gradient_finite_differences():
+    """FP64 backward of the 10-128-128-6 network vs central differences."""
+    rng = np.random.default_rng(6)
+    n_par = 128 * 10 + 128 + 128 * 128 + 128 + 6 * 128 + 6
+    p = rng.normal(size=n_par) * 0.1
+    x = rng.normal(size=(7, 10))
+    t = rng.normal(size=(7, 6))
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    assert abs(loss - 0.5 * np.mean(np.sum((oracle.mlp_forward(p, x) - t) ** 2, 1))) < 1e-12
+    for i in rng.choice(n_par, 40, replace=False):
+        e = np.zeros(n_par)
+        e[i] = 1e-6
+        fd = (oracle.mlp_loss_grad(p + e, x, t)[0] - oracle.mlp_loss_grad(p - e, x, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
