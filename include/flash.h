@@ -1,0 +1,166 @@
+/* flash.h — C ABI of the GB300-native batched deformable + frictional-contact
+ * time step (FLASH, arxiv 2604.17513, Sec. III "Preliminary" and Sec. IV-B
+ * "Simulation Core", Algorithm 1 "Multi-Env GPU-based Pipeline").
+ *
+ * One process, one GPU.  All environments that share a mesh (and a stiffness
+ * scale) share one constant system matrix A = M + h^2 sum_i w_i G_i^T G_i
+ * (Sec. III-B); every step of every environment runs in this library's CUDA
+ * kernels.  Calls are stream-ordered: nothing synchronises the host except
+ * flash_scene_finalize, the *_host getters and the tolerance mode of
+ * flash_step, which reads a device flag once per iteration.
+ *
+ * Conventions
+ *   - z is up; positions in metres; obstacle pose = (px,py,pz, qw,qx,qy,qz).
+ *   - State layout seen by callers: float32 [sum_e n_e][3], environments in
+ *     the order they were added, vertices in mesh order (xyz interleaved).
+ *   - Contact multipliers gamma = h^2 * lambda (kg m), stored per contact as
+ *     (gamma_n, gamma_t world x, y, z); the contact impulse is gamma / h.
+ *   - Pointers marked "device" must be device memory of the current CUDA
+ *     device; "host" pointers are read during the call only.  The library
+ *     owns every allocation it makes and frees it in flash_scene_destroy.
+ *   - Every call returns a flash_status; on error a thread-local message is
+ *     available from flash_last_error().  Kernels never trap: device-side
+ *     problems (non-finite state, contact overflow) set a per-scene status
+ *     word that the next call reports.
+ */
+#ifndef FLASH_H
+#define FLASH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t flash_status;
+#define FLASH_OK 0
+#define FLASH_EINVAL (-1)   /* bad argument or descriptor */
+#define FLASH_ENOMEM (-2)   /* device or host allocation failed */
+#define FLASH_ECUDA (-3)    /* a CUDA runtime call failed */
+#define FLASH_ETIMEOUT (-4) /* a bounded device wait ran out */
+#define FLASH_ENOTIMPL (-5) /* feature not available in this build */
+#define FLASH_ESTATE (-6)   /* call out of order (e.g. step before finalize) */
+#define FLASH_ENUMERIC (-7) /* setup matrix not positive definite, NaN state */
+#define FLASH_WOVERFLOW 1   /* warning: contacts beyond capacity were dropped */
+
+#define FLASH_TRI 0
+#define FLASH_TET 1
+
+#define FLASH_OBS_NONE 0
+#define FLASH_OBS_PLANE 1  /* plane through the pose origin, normal = body +z */
+#define FLASH_OBS_SPHERE 2 /* dims[0] = radius */
+#define FLASH_OBS_BOX 3    /* dims = half extents */
+#define FLASH_MAX_OBS 8
+
+#define FLASH_MODE_FIXED 0 /* exactly k_max local-global iterations per step */
+#define FLASH_MODE_TOL 1   /* iterate until r_ncp <= tol_ncp (k >= k_min) or k_cap */
+
+#define FLASH_SOLVE_F32 0    /* global solve: FP32 dense apply on the CUDA cores */
+#define FLASH_SOLVE_F16X3 1  /* global solve: tcgen05 f16 hi/lo split, FP32 accumulate */
+
+#define FLASH_WARM_COLD 0    /* gamma^0 = 0, q^0 = q~ (the paper's start) */
+#define FLASH_WARM_PREV 1    /* gamma^0 = previous step's gamma of the same contact */
+#define FLASH_WARM_LEARNED 2 /* gamma^0, q^0 from the warm-start network */
+
+/* Scene-wide solver settings (Sec. III; Algorithm 1; appendix scene config).
+ * h: timestep (s).  gravity: m/s^2.  tol_ncp: NCP residual tolerance (m) of
+ * FLASH_MODE_TOL.  maxforce: clamp on the normal force (N).  thickness: the
+ * cloth half-thickness tau (m) subtracted from signed distances.  margin:
+ * detection margin delta (m).  k_max: iterations of FLASH_MODE_FIXED.
+ * k_min/k_cap: bounds of FLASH_MODE_TOL.  contact_cap: contacts per
+ * environment.  solve: FLASH_SOLVE_*.  warm: FLASH_WARM_*. */
+typedef struct {
+  double h;
+  double gravity[3];
+  double tol_ncp;
+  double maxforce;
+  double thickness;
+  double margin;
+  int32_t k_max, k_min, k_cap, mode;
+  int32_t contact_cap;
+  int32_t solve;
+  int32_t warm;
+  int32_t reserved[5];
+} flash_scene_desc;
+
+/* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
+ * bending on interior edges) or FLASH_TET (corotational strain).  rest: host
+ * float64 [n][3]; elems: host int32 [E][3|4]; mass: host float64 [n] (kg).
+ * w_stretch: weight per unit rest area (TRI) or volume (TET); w_bend: bending
+ * weight (TRI only). */
+typedef struct {
+  int32_t type;
+  int32_t n_verts, n_elems;
+  const double *rest;
+  const int32_t *elems;
+  const double *mass;
+  double w_stretch, w_bend;
+} flash_mesh_desc;
+
+/* Per-environment parameters.  mu: Coulomb coefficient.  stiffness: scale on
+ * the mesh's w_stretch (environments with equal scale share A).  Obstacles:
+ * kinematic planes, spheres and boxes (ground, fingers, props); compliance is
+ * the normal compliance in m/N (0 = rigid). */
+typedef struct {
+  float mu;
+  float stiffness;
+  int32_t n_obs;
+  int32_t obs_type[FLASH_MAX_OBS];
+  float obs_dims[FLASH_MAX_OBS][3];
+  float obs_compliance[FLASH_MAX_OBS];
+} flash_env_desc;
+
+typedef struct flash_scene flash_scene;
+
+/* Creation / setup (the paper's load_config / set_envs / initialize). */
+flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out);
+flash_status flash_mesh_add(flash_scene *s, const flash_mesh_desc *mesh, int32_t *mesh_id);
+flash_status flash_envs_add(flash_scene *s, int32_t mesh_id, int32_t n, const flash_env_desc *envs,
+                            int32_t *first_env);
+/* Builds A per (mesh, stiffness), inverts it once in FP64 on the device
+ * (Algorithm 1 setup: Cholesky / explicit inverse), allocates all state.
+ * Synchronises the stream. */
+flash_status flash_scene_finalize(flash_scene *s, void *stream);
+void flash_scene_destroy(flash_scene *s);
+
+int32_t flash_num_envs(const flash_scene *s);
+int64_t flash_num_verts(const flash_scene *s);                       /* sum_e n_e */
+flash_status flash_env_offsets(const flash_scene *s, int64_t *off); /* host [N+1] */
+
+/* State I/O: q, v device float32 [sum n_e][3] (either may be NULL). */
+flash_status flash_set_state(flash_scene *s, const float *q, const float *v, void *stream);
+flash_status flash_get_state(const flash_scene *s, float *q, float *v, void *stream);
+
+/* Kinematic obstacle targets (the paper's move_ee): device float32
+ * [N][FLASH_MAX_OBS][7].  which = 0 sets the current and next pose (reset),
+ * which = 1 sets the pose the next step moves to.  After a step the next
+ * pose becomes the current one. */
+flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_t which, void *stream);
+
+/* Advance every environment by n_steps (Algorithm 1 body). */
+flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
+
+/* Contacts of the last step: count device int32 [N]; vert, obs device int32
+ * [N][cap]; gamma device float32 [N][cap][4] (any may be NULL). */
+flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs,
+                                float *gamma, void *stream);
+int32_t flash_contact_cap(const flash_scene *s);
+
+/* Per-environment statistics of the last step: iterations used and the NCP
+ * residual max_j |phi_j| (m) of the final iterate; device int32/float32 [N]. */
+flash_status flash_get_stats(const flash_scene *s, int32_t *iters, float *rncp, void *stream);
+/* Device status word (FLASH_OK or a warning/error code); synchronises. */
+flash_status flash_status_word(flash_scene *s, void *stream);
+
+/* The global solve alone (Eq. correction's A^-1 apply) on the environments of
+ * one group [first_env, first_env + n): rhs, out device float32 [n][n_v][3].
+ * For parity tests of the dense contraction. */
+flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, const float *rhs,
+                                float *out, void *stream);
+
+const char *flash_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLASH_H */

@@ -1,0 +1,590 @@
+// Host side of the C ABI: scene description, one-time setup (element data,
+// bending stencils, the constant system matrix A = M + h^2 sum w_i G_i^T G_i
+// of Sec. III-B and its explicit inverse), state I/O and the per-step
+// launch sequence of Algorithm 1.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "flash_internal.cuh"
+
+namespace flash {
+
+static thread_local std::string g_error;
+void set_error(const std::string &msg) { g_error = msg; }
+
+namespace {
+
+flash_status fail(flash_status code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+template <typename T>
+cudaError_t dalloc(flash_scene *s, T **p, size_t count) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(ptr, 0, std::max<size_t>(count, 1) * sizeof(T));
+  s->allocs.push_back(ptr);
+  *p = (T *)ptr;
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(flash_scene *s, T **p, const std::vector<T> &h) {
+  cudaError_t e = dalloc(s, p, h.size());
+  if (e != cudaSuccess) return e;
+  if (!h.empty()) e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// element operators: F = Ds Dm^-1 written as F[c][j] = sum_a x_a[c] D[a][j]
+// ---------------------------------------------------------------------------
+struct ElemData {
+  std::vector<double> D;    // [E][12]
+  std::vector<double> size; // rest area or volume
+};
+
+ElemData element_operators(const MeshTemplate &m) {
+  ElemData out;
+  out.D.assign((size_t)m.E * 12, 0.0);
+  out.size.assign(m.E, 0.0);
+  const int vpe = m.type == FLASH_TRI ? 3 : 4;
+  for (int e = 0; e < m.E; e++) {
+    const int *v = &m.elems[(size_t)e * vpe];
+    auto X = [&](int a, int c) { return m.rest[3 * (size_t)v[a] + c]; };
+    double *D = &out.D[(size_t)e * 12];
+    if (m.type == FLASH_TRI) {
+      double e1[3], e2[3];
+      for (int c = 0; c < 3; c++) { e1[c] = X(1, c) - X(0, c); e2[c] = X(2, c) - X(0, c); }
+      double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+      double b1[3] = {e1[0] / l1, e1[1] / l1, e1[2] / l1};
+      double p = e2[0] * b1[0] + e2[1] * b1[1] + e2[2] * b1[2];
+      double o[3] = {e2[0] - p * b1[0], e2[1] - p * b1[1], e2[2] - p * b1[2]};
+      double lo = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+      // rest edges in the triangle's plane: Dm = [[l1, p], [0, lo]]
+      double i00 = 1.0 / l1, i01 = -p / (l1 * lo), i11 = 1.0 / lo;
+      double Di[2][2] = {{i00, i01}, {0.0, i11}};
+      for (int j = 0; j < 2; j++) {
+        D[0 * 3 + j] = -(Di[0][j] + Di[1][j]);
+        D[1 * 3 + j] = Di[0][j];
+        D[2 * 3 + j] = Di[1][j];
+      }
+      out.size[e] = 0.5 * l1 * lo;
+    } else {
+      double M[3][3];
+      for (int c = 0; c < 3; c++)
+        for (int j = 0; j < 3; j++) M[c][j] = X(j + 1, c) - X(0, c);
+      double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                   M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+      double I[3][3];
+      I[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / det;
+      I[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+      I[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+      I[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / det;
+      I[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+      I[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+      I[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / det;
+      I[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+      I[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+      for (int j = 0; j < 3; j++) {
+        D[0 * 3 + j] = -(I[0][j] + I[1][j] + I[2][j]);
+        for (int a = 0; a < 3; a++) D[(a + 1) * 3 + j] = I[a][j];
+      }
+      out.size[e] = std::fabs(det) / 6.0;
+    }
+  }
+  return out;
+}
+
+// Flat-rest quadratic bending on interior edges.  For the hinge (x0,x1 | x2,
+// x3) the stencil k has k2 = |e|^2 / (2 A0), k3 = |e|^2 / (2 A1) and k0, k1
+// fixed by annihilating constants and the rest positions along the edge; the
+// energy is (w_b / 2) * 3 / (A0 + A1) * |sum_a k_a x_a|^2.
+struct Hinges {
+  std::vector<int> v;      // [H][4]
+  std::vector<double> k;   // [H][4]
+  std::vector<double> s;   // [H] 3 / (A0 + A1)
+};
+
+Hinges bending_hinges(const MeshTemplate &m) {
+  Hinges out;
+  if (m.type != FLASH_TRI) return out;
+  std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> edges;  // edge -> (tri, opposite)
+  for (int t = 0; t < m.E; t++)
+    for (int k = 0; k < 3; k++) {
+      int a = m.elems[3 * t + k], b = m.elems[3 * t + (k + 1) % 3], o = m.elems[3 * t + (k + 2) % 3];
+      edges[{std::min(a, b), std::max(a, b)}].push_back({t, o});
+    }
+  for (auto &kv : edges) {
+    if (kv.second.size() != 2) continue;
+    int x[4] = {kv.first.first, kv.first.second, kv.second[0].second, kv.second[1].second};
+    auto P = [&](int i, int c) { return m.rest[3 * (size_t)x[i] + c]; };
+    double e[3], d2[3], d3[3];
+    for (int c = 0; c < 3; c++) { e[c] = P(1, c) - P(0, c); d2[c] = P(2, c) - P(0, c); d3[c] = P(3, c) - P(0, c); }
+    double le2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2], le = std::sqrt(le2);
+    auto area = [&](const double *d) {
+      double c0 = e[1] * d[2] - e[2] * d[1], c1 = e[2] * d[0] - e[0] * d[2], c2 = e[0] * d[1] - e[1] * d[0];
+      return 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    };
+    double A0 = area(d2), A1 = area(d3);
+    double k2 = le2 / (2 * A0), k3 = le2 / (2 * A1);
+    double s2 = (d2[0] * e[0] + d2[1] * e[1] + d2[2] * e[2]) / le;
+    double s3 = (d3[0] * e[0] + d3[1] * e[1] + d3[2] * e[2]) / le;
+    double k1 = -(k2 * s2 + k3 * s3) / le;
+    double k0 = -(k1 + k2 + k3);
+    for (int i = 0; i < 4; i++) out.v.push_back(x[i]);
+    out.k.insert(out.k.end(), {k0, k1, k2, k3});
+    out.s.push_back(3.0 / (A0 + A1));
+  }
+  return out;
+}
+
+// CSR incidence vertex -> slot (4 * item + local index)
+void incidence(int n, const std::vector<int> &items, int per, std::vector<int> &off, std::vector<int> &idx) {
+  off.assign(n + 1, 0);
+  size_t cnt = items.size() / per;
+  for (size_t t = 0; t < cnt; t++)
+    for (int a = 0; a < per; a++) off[items[t * per + a] + 1]++;
+  for (int i = 0; i < n; i++) off[i + 1] += off[i];
+  idx.assign(off[n], 0);
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (size_t t = 0; t < cnt; t++)
+    for (int a = 0; a < per; a++) idx[fill[items[t * per + a]]++] = (int)(4 * t + a);
+}
+
+flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
+  const MeshTemplate &m = s->meshes[g.mesh];
+  const double h = s->d.h, h2 = h * h;
+  g.type = m.type; g.n = m.n; g.E = m.E;
+  g.vpe = m.type == FLASH_TRI ? 3 : 4;
+  g.nc = m.type == FLASH_TRI ? 2 : 3;
+  g.n_pad = round_up(std::max(m.n, 1), 128);
+  g.N = (int)g.env_ids.size();
+  g.cols = 3 * g.N;
+  g.cols_pad = round_up(g.cols, 128);
+  const int n = g.n, np = g.n_pad;
+  ElemData ed = element_operators(m);
+  Hinges hg = bending_hinges(m);
+  if (m.w_bend == 0.0) hg = Hinges{};
+  g.H = (int)hg.s.size();
+  // element arrays
+  std::vector<int> el((size_t)m.E * 4, 0);
+  std::vector<float> Df((size_t)m.E * 12), wt(m.E);
+  for (int e = 0; e < m.E; e++) {
+    for (int a = 0; a < g.vpe; a++) el[(size_t)e * 4 + a] = m.elems[(size_t)e * g.vpe + a];
+    for (int t = 0; t < 12; t++) Df[(size_t)e * 12 + t] = (float)ed.D[(size_t)e * 12 + t];
+    wt[e] = (float)(h2 * m.w_stretch * g.stiff * ed.size[e]);
+  }
+  std::vector<float> hc(hg.k.size());
+  for (int t = 0; t < g.H; t++)
+    for (int a = 0; a < 4; a++) hc[4 * t + a] = (float)(hg.k[4 * t + a] * std::sqrt(h2 * m.w_bend * hg.s[t]));
+  std::vector<int> elist((size_t)m.E * g.vpe);
+  for (size_t i = 0; i < elist.size(); i++) elist[i] = m.elems[i];
+  std::vector<int> v2e_off, v2e, v2h_off, v2h;
+  incidence(n, elist, g.vpe, v2e_off, v2e);
+  incidence(n, hg.v, 4, v2h_off, v2h);
+  std::vector<float> massf(np, 0.f);
+  for (int i = 0; i < n; i++) massf[i] = (float)m.mass[i];
+  std::vector<int> genv(g.env_ids.begin(), g.env_ids.end());
+  FLASH_CUDA_TRY(upload(s, &g.genv, genv));
+  FLASH_CUDA_TRY(upload(s, &g.elems, el));
+  FLASH_CUDA_TRY(upload(s, &g.D, Df));
+  FLASH_CUDA_TRY(upload(s, &g.wt, wt));
+  std::vector<int> hv(hg.v.begin(), hg.v.end());
+  FLASH_CUDA_TRY(upload(s, &g.hv, hv));
+  FLASH_CUDA_TRY(upload(s, &g.hc, hc));
+  FLASH_CUDA_TRY(upload(s, &g.v2e_off, v2e_off));
+  FLASH_CUDA_TRY(upload(s, &g.v2e, v2e));
+  FLASH_CUDA_TRY(upload(s, &g.v2h_off, v2h_off));
+  FLASH_CUDA_TRY(upload(s, &g.v2h, v2h));
+  FLASH_CUDA_TRY(upload(s, &g.mass, massf));
+  // system matrix A (scalar n x n block of A = A_s (x) I3), padded with I
+  std::vector<double> A((size_t)np * np, 0.0);
+  for (int i = 0; i < np; i++) A[(size_t)i * np + i] = i < n ? m.mass[i] : 1.0;
+  for (int e = 0; e < m.E; e++) {
+    const double w = h2 * m.w_stretch * g.stiff * ed.size[e];
+    const double *D = &ed.D[(size_t)e * 12];
+    for (int a = 0; a < g.vpe; a++)
+      for (int b = 0; b < g.vpe; b++) {
+        double dd = 0;
+        for (int j = 0; j < g.nc; j++) dd += D[a * 3 + j] * D[b * 3 + j];
+        A[(size_t)el[(size_t)e * 4 + a] * np + el[(size_t)e * 4 + b]] += w * dd;
+      }
+  }
+  for (int t = 0; t < g.H; t++) {
+    double c = h2 * m.w_bend * hg.s[t];
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) A[(size_t)hg.v[4 * t + a] * np + hg.v[4 * t + b]] += c * hg.k[4 * t + a] * hg.k[4 * t + b];
+  }
+  for (int i = 0; i < n; i++)
+    if (!(A[(size_t)i * np + i] > 0.0)) return fail(FLASH_ENUMERIC, "system matrix has a non-positive diagonal");
+  double *dA = nullptr;
+  FLASH_CUDA_TRY(cudaMalloc(&dA, sizeof(double) * A.size()));
+  FLASH_CUDA_TRY(cudaMemcpy(dA, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice));
+  FLASH_CUDA_TRY(invert_spd_f64(dA, n, np, 1, st));
+  FLASH_CUDA_TRY(cudaMemcpyAsync(A.data(), dA, sizeof(double) * A.size(), cudaMemcpyDeviceToHost, st));
+  FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  double amax = 0;
+  for (double x : A) {
+    if (!std::isfinite(x)) { cudaFree(dA); return fail(FLASH_ENUMERIC, "system matrix inverse is not finite"); }
+    amax = std::max(amax, std::fabs(x));
+  }
+  int ex = 0;
+  std::frexp(amax, &ex);
+  g.a_exp = 14 - ex;
+  FLASH_CUDA_TRY(dalloc(s, &g.Ainv, (size_t)np * np));
+  FLASH_CUDA_TRY(dalloc(s, &g.Ahi, (size_t)np * np));
+  FLASH_CUDA_TRY(dalloc(s, &g.Alo, (size_t)np * np));
+  FLASH_CUDA_TRY(cast_inverse(dA, np, g.Ainv, g.Ahi, g.Alo, g.a_exp, st));
+  FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  cudaFree(dA);
+  // state and contact buffers
+  size_t sz = (size_t)g.cols_pad * np;
+  FLASH_CUDA_TRY(dalloc(s, &g.q, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.v, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.qt, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.qp, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.r, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.w, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.f, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.rh, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.rl, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.rscale, (size_t)g.cols_pad));
+  size_t cc = (size_t)g.N * s->cap;
+  FLASH_CUDA_TRY(dalloc(s, &g.ccount, (size_t)g.N));
+  FLASH_CUDA_TRY(dalloc(s, &g.cvert, cc));
+  FLASH_CUDA_TRY(dalloc(s, &g.cobs, cc));
+  FLASH_CUDA_TRY(dalloc(s, &g.cgam, cc * 4));
+  FLASH_CUDA_TRY(dalloc(s, &g.clin, cc * kLin));
+  FLASH_CUDA_TRY(dalloc(s, &g.pcount, (size_t)g.N));
+  FLASH_CUDA_TRY(dalloc(s, &g.pvert, cc));
+  FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));
+  FLASH_CUDA_TRY(dalloc(s, &g.pgam, cc * 4));
+  size_t per_env = (size_t)g.E * g.nc * 3 + (size_t)g.H * 3;
+  size_t full = sizeof(float) * (6 * (size_t)n + per_env);
+  if (full <= 200 * 1024) {
+    g.p_in_smem = true;
+    g.smem_local = full;
+  } else {
+    g.p_in_smem = false;
+    g.smem_local = sizeof(float) * 6 * (size_t)n;
+    if (g.smem_local > 200 * 1024) return fail(FLASH_EINVAL, "mesh too large for one CTA per environment");
+    FLASH_CUDA_TRY(dalloc(s, &g.pscratch, per_env * g.N));
+  }
+  return FLASH_OK;
+}
+
+StepArgs step_args(const flash_scene *s) {
+  StepArgs a;
+  a.h = (float)s->d.h;
+  a.gx = (float)s->d.gravity[0]; a.gy = (float)s->d.gravity[1]; a.gz = (float)s->d.gravity[2];
+  a.tol = (float)s->d.tol_ncp;
+  a.gmax = (float)(s->d.h * s->d.h * s->d.maxforce);
+  a.tau = (float)s->d.thickness;
+  a.margin = (float)s->d.margin;
+  a.k_min = s->d.k_min; a.k_cap = s->d.k_cap; a.mode = s->d.mode; a.warm = s->d.warm;
+  a.K = s->K; a.cap = s->cap;
+  return a;
+}
+
+bool use_tc(const flash_scene *s) { return s->d.solve == FLASH_SOLVE_F16X3; }
+
+cudaError_t global_solves(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
+  // w = A^-1 r ;  NCP ;  q = q + w + A^-1 J^T dgamma
+  cudaError_t e;
+  const bool tc = use_tc(s);
+  if (tc) e = gemm_tc(g, g.w, nullptr, s->done, 0, st);
+  else e = gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_ncp(s, g, a, tc ? 1 : 0, st);
+  if (e != cudaSuccess) return e;
+  if (tc) return gemm_tc(g, g.q, g.w, s->done, 1, st);
+  return gemm_simt(g, g.f, g.q, g.w, s->done, 1, st);
+}
+
+}  // namespace
+}  // namespace flash
+
+using namespace flash;
+
+extern "C" {
+
+const char *flash_last_error(void) { return g_error.c_str(); }
+
+flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out) {
+  if (!desc || !out) return fail(FLASH_EINVAL, "null argument");
+  if (!(desc->h > 0) || desc->k_max < 0 || desc->k_cap < 0 || desc->k_min < 0 || desc->contact_cap < 0)
+    return fail(FLASH_EINVAL, "invalid scene descriptor");
+  if (desc->mode != FLASH_MODE_FIXED && desc->mode != FLASH_MODE_TOL) return fail(FLASH_EINVAL, "invalid mode");
+  if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3) return fail(FLASH_EINVAL, "invalid solve");
+  if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
+  flash_scene *s = new flash_scene();
+  s->d = *desc;
+  s->cap = desc->contact_cap;
+  *out = s;
+  return FLASH_OK;
+}
+
+flash_status flash_mesh_add(flash_scene *s, const flash_mesh_desc *m, int32_t *mesh_id) {
+  if (!s || !m) return fail(FLASH_EINVAL, "null argument");
+  if (s->finalized) return fail(FLASH_ESTATE, "scene already finalized");
+  if ((m->type != FLASH_TRI && m->type != FLASH_TET) || m->n_verts <= 0 || m->n_elems < 0 || !m->rest || !m->mass ||
+      (m->n_elems > 0 && !m->elems))
+    return fail(FLASH_EINVAL, "invalid mesh descriptor");
+  MeshTemplate t;
+  t.type = m->type; t.n = m->n_verts; t.E = m->n_elems;
+  t.rest.assign(m->rest, m->rest + 3 * (size_t)m->n_verts);
+  t.mass.assign(m->mass, m->mass + m->n_verts);
+  int vpe = m->type == FLASH_TRI ? 3 : 4;
+  t.elems.assign(m->elems, m->elems + (size_t)vpe * m->n_elems);
+  for (int x : t.elems)
+    if (x < 0 || x >= t.n) return fail(FLASH_EINVAL, "element index out of range");
+  for (double x : t.mass)
+    if (!(x > 0)) return fail(FLASH_EINVAL, "vertex mass must be positive");
+  t.w_stretch = m->w_stretch; t.w_bend = m->w_bend;
+  s->meshes.push_back(std::move(t));
+  if (mesh_id) *mesh_id = (int32_t)s->meshes.size() - 1;
+  return FLASH_OK;
+}
+
+flash_status flash_envs_add(flash_scene *s, int32_t mesh_id, int32_t n, const flash_env_desc *envs,
+                            int32_t *first_env) {
+  if (!s || !envs || n <= 0) return fail(FLASH_EINVAL, "invalid arguments");
+  if (s->finalized) return fail(FLASH_ESTATE, "scene already finalized");
+  if (mesh_id < 0 || mesh_id >= (int)s->meshes.size()) return fail(FLASH_EINVAL, "unknown mesh");
+  for (int i = 0; i < n; i++) {
+    if (envs[i].n_obs < 0 || envs[i].n_obs > FLASH_MAX_OBS) return fail(FLASH_EINVAL, "too many obstacles");
+    for (int o = 0; o < envs[i].n_obs; o++)
+      if (envs[i].obs_type[o] < FLASH_OBS_NONE || envs[i].obs_type[o] > FLASH_OBS_BOX)
+        return fail(FLASH_EINVAL, "unknown obstacle type");
+  }
+  if (first_env) *first_env = (int32_t)s->envs.size();
+  for (int i = 0; i < n; i++) {
+    s->envs.push_back(envs[i]);
+    s->env_mesh.push_back(mesh_id);
+  }
+  return FLASH_OK;
+}
+
+flash_status flash_scene_finalize(flash_scene *s, void *stream) {
+  if (!s) return fail(FLASH_EINVAL, "null scene");
+  if (s->finalized) return fail(FLASH_ESTATE, "scene already finalized");
+  if (s->envs.empty()) return fail(FLASH_EINVAL, "no environments");
+  cudaStream_t st = (cudaStream_t)stream;
+  FLASH_CUDA_TRY(configure_kernels());
+  s->N = (int)s->envs.size();
+  s->K = 0;
+  for (auto &e : s->envs) s->K = std::max(s->K, (int)e.n_obs);
+  // groups by (mesh, stiffness)
+  std::map<std::pair<int, float>, int> key;
+  s->env_group.resize(s->N);
+  s->env_local.resize(s->N);
+  for (int e = 0; e < s->N; e++) {
+    auto k = std::make_pair(s->env_mesh[e], s->envs[e].stiffness);
+    auto it = key.find(k);
+    int gi;
+    if (it == key.end()) {
+      gi = (int)s->groups.size();
+      key[k] = gi;
+      Group g;
+      g.mesh = k.first;
+      g.stiff = k.second;
+      s->groups.push_back(g);
+    } else {
+      gi = it->second;
+    }
+    s->env_group[e] = gi;
+    s->env_local[e] = (int)s->groups[gi].env_ids.size();
+    s->groups[gi].env_ids.push_back(e);
+  }
+  s->voff.assign(s->N + 1, 0);
+  for (int e = 0; e < s->N; e++) s->voff[e + 1] = s->voff[e] + s->meshes[s->env_mesh[e]].n;
+  for (auto &g : s->groups) {
+    flash_status r = build_group(s, g, st);
+    if (r != FLASH_OK) return r;
+  }
+  // env-level arrays
+  std::vector<float> mu(s->N), odims((size_t)s->N * FLASH_MAX_OBS * 3, 0.f), ocomp((size_t)s->N * FLASH_MAX_OBS, 0.f);
+  std::vector<int> otype((size_t)s->N * FLASH_MAX_OBS, 0);
+  std::vector<float> pose((size_t)s->N * FLASH_MAX_OBS * 7, 0.f);
+  for (int e = 0; e < s->N; e++) {
+    const flash_env_desc &d = s->envs[e];
+    mu[e] = d.mu;
+    for (int o = 0; o < d.n_obs; o++) {
+      otype[e * FLASH_MAX_OBS + o] = d.obs_type[o];
+      ocomp[e * FLASH_MAX_OBS + o] = d.obs_compliance[o];
+      for (int c = 0; c < 3; c++) odims[(e * FLASH_MAX_OBS + o) * 3 + c] = d.obs_dims[o][c];
+    }
+    for (int o = 0; o < FLASH_MAX_OBS; o++) pose[(e * FLASH_MAX_OBS + o) * 7 + 3] = 1.f;
+  }
+  FLASH_CUDA_TRY(upload(s, &s->mu, mu));
+  FLASH_CUDA_TRY(upload(s, &s->otype, otype));
+  FLASH_CUDA_TRY(upload(s, &s->odims, odims));
+  FLASH_CUDA_TRY(upload(s, &s->ocomp, ocomp));
+  FLASH_CUDA_TRY(upload(s, &s->pose_t, pose));
+  FLASH_CUDA_TRY(upload(s, &s->pose_th, pose));
+  FLASH_CUDA_TRY(dalloc(s, &s->iters, (size_t)s->N));
+  FLASH_CUDA_TRY(dalloc(s, &s->done, (size_t)s->N));
+  FLASH_CUDA_TRY(dalloc(s, &s->rncp, (size_t)s->N));
+  FLASH_CUDA_TRY(dalloc(s, &s->status, 1));
+  FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
+  FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
+  FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
+  FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  s->finalized = true;
+  return FLASH_OK;
+}
+
+void flash_scene_destroy(flash_scene *s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  for (void *p : s->allocs) cudaFree(p);
+  if (s->h_active) cudaFreeHost(s->h_active);
+  delete s;
+}
+
+int32_t flash_num_envs(const flash_scene *s) { return s ? (int32_t)s->envs.size() : 0; }
+
+int64_t flash_num_verts(const flash_scene *s) {
+  if (!s) return 0;
+  int64_t t = 0;
+  for (size_t e = 0; e < s->envs.size(); e++) t += s->meshes[s->env_mesh[e]].n;
+  return t;
+}
+
+flash_status flash_env_offsets(const flash_scene *s, int64_t *off) {
+  if (!s || !off) return fail(FLASH_EINVAL, "null argument");
+  int64_t t = 0;
+  off[0] = 0;
+  for (size_t e = 0; e < s->envs.size(); e++) {
+    t += s->meshes[s->env_mesh[e]].n;
+    off[e + 1] = t;
+  }
+  return FLASH_OK;
+}
+
+int32_t flash_contact_cap(const flash_scene *s) { return s ? s->cap : 0; }
+
+flash_status flash_set_state(flash_scene *s, const float *q, const float *v, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  for (auto &g : s->groups) FLASH_CUDA_TRY(launch_state_io(s, g, q, v, nullptr, nullptr, 0, (cudaStream_t)stream));
+  return FLASH_OK;
+}
+
+flash_status flash_get_state(const flash_scene *s, float *q, float *v, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  for (auto &g : s->groups) FLASH_CUDA_TRY(launch_state_io(s, g, nullptr, nullptr, q, v, 1, (cudaStream_t)stream));
+  return FLASH_OK;
+}
+
+flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_t which, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (!poses || (which != 0 && which != 1)) return fail(FLASH_EINVAL, "invalid arguments");
+  size_t bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
+  cudaStream_t st = (cudaStream_t)stream;
+  FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_th, poses, bytes, cudaMemcpyDeviceToDevice, st));
+  if (which == 0) FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, poses, bytes, cudaMemcpyDeviceToDevice, st));
+  return FLASH_OK;
+}
+
+flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (n_steps < 0) return fail(FLASH_EINVAL, "negative step count");
+  if (s->d.warm == FLASH_WARM_LEARNED) return fail(FLASH_ENOTIMPL, "learned warm start needs weights");
+  cudaStream_t st = (cudaStream_t)stream;
+  const StepArgs a = step_args(s);
+  const int tc = use_tc(s) ? 1 : 0;
+  const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
+  for (int step = 0; step < n_steps; step++) {
+    for (auto &g : s->groups) FLASH_CUDA_TRY(launch_begin(s, g, a, st));
+    if (s->d.mode == FLASH_MODE_FIXED) {
+      for (int k = 1; k <= s->d.k_max; k++)
+        for (auto &g : s->groups) {
+          FLASH_CUDA_TRY(launch_local(s, g, a, k, 0, tc, st));
+          FLASH_CUDA_TRY(global_solves(s, g, a, st));
+        }
+      for (auto &g : s->groups) FLASH_CUDA_TRY(launch_local(s, g, a, s->d.k_max + 1, 1, tc, st));
+    } else {
+      for (int k = 1; k <= s->d.k_cap + 1; k++) {
+        FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
+        for (auto &g : s->groups) FLASH_CUDA_TRY(launch_local(s, g, a, k, 0, tc, st));
+        FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*s->h_active == 0) break;
+        for (auto &g : s->groups) FLASH_CUDA_TRY(global_solves(s, g, a, st));
+      }
+    }
+    for (auto &g : s->groups) FLASH_CUDA_TRY(launch_end(s, g, a, st));
+    FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  return FLASH_OK;
+}
+
+flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs, float *gamma,
+                                void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (auto &g : s->groups)
+    for (int l = 0; l < g.N; l++) {
+      int e = g.env_ids[l];
+      size_t cs = (size_t)s->cap;
+      if (count) FLASH_CUDA_TRY(cudaMemcpyAsync(count + e, g.pcount + l, sizeof(int), cudaMemcpyDeviceToDevice, st));
+      if (vert) FLASH_CUDA_TRY(cudaMemcpyAsync(vert + e * cs, g.pvert + l * cs, sizeof(int) * cs, cudaMemcpyDeviceToDevice, st));
+      if (obs) FLASH_CUDA_TRY(cudaMemcpyAsync(obs + e * cs, g.pobs + l * cs, sizeof(int) * cs, cudaMemcpyDeviceToDevice, st));
+      if (gamma)
+        FLASH_CUDA_TRY(cudaMemcpyAsync(gamma + e * cs * 4, g.pgam + l * cs * 4, sizeof(float) * cs * 4,
+                                       cudaMemcpyDeviceToDevice, st));
+    }
+  return FLASH_OK;
+}
+
+flash_status flash_get_stats(const flash_scene *s, int32_t *iters, float *rncp, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (iters) FLASH_CUDA_TRY(cudaMemcpyAsync(iters, s->iters, sizeof(int) * s->N, cudaMemcpyDeviceToDevice, st));
+  if (rncp) FLASH_CUDA_TRY(cudaMemcpyAsync(rncp, s->rncp, sizeof(float) * s->N, cudaMemcpyDeviceToDevice, st));
+  return FLASH_OK;
+}
+
+flash_status flash_status_word(flash_scene *s, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  int w = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  FLASH_CUDA_TRY(cudaMemcpyAsync(&w, s->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  if (w & (1 << 9)) return fail(FLASH_ENUMERIC, "non-finite state or residual");
+  if (w & ((1 << 8) | (1 << 10))) return FLASH_WOVERFLOW;
+  return FLASH_OK;
+}
+
+flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, const float *rhs, float *out,
+                                void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (first_env < 0 || first_env >= s->N || !rhs || !out) return fail(FLASH_EINVAL, "invalid arguments");
+  Group &g = s->groups[s->env_group[first_env]];
+  if (g.env_ids.front() != first_env || (int)g.env_ids.size() != n)
+    return fail(FLASH_EINVAL, "range must be exactly one group of environments");
+  for (int l = 0; l < n; l++)
+    if (g.env_ids[l] != first_env + l) return fail(FLASH_EINVAL, "group environments are not contiguous");
+  cudaStream_t st = (cudaStream_t)stream;
+  FLASH_CUDA_TRY(cudaMemsetAsync(s->done, 0, sizeof(int) * s->N, st));
+  FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, rhs, g.r, 0, st));
+  if (use_tc(s)) {
+    FLASH_CUDA_TRY(launch_split_rhs(g, g.r, s->done, st));
+    FLASH_CUDA_TRY(gemm_tc(g, g.w, nullptr, s->done, 0, st));
+  } else {
+    FLASH_CUDA_TRY(gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st));
+  }
+  FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, out, g.w, 1, st));
+  return FLASH_OK;
+}
+
+}  // extern "C"

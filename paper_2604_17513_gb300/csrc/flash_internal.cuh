@@ -1,0 +1,142 @@
+// Internal declarations of the FLASH CUDA library (not part of the C ABI).
+//
+// Device layout, per group of environments sharing one system matrix
+// (same mesh, same stiffness scale):
+//   state      float [N_g][3][n_pad]   one contiguous column per (env, coord),
+//                                      so the global solve is a multi-RHS
+//                                      product  A^-1 [n_pad x n_pad] * R [n_pad x 3N_g]
+//   elements   int   [E][4], float D[E][12] (F[c][j] = sum_a x_a[c] D[a][j]),
+//              float wt[E] = h^2 * w_i
+//   hinges     int   [H][4], float hc[H][4]  (bending stencil scaled by h sqrt(w_b s))
+//   incidence  CSR vertex -> element slot (4e + a) and vertex -> hinge slot
+//   contacts   per env, sorted by (vertex, obstacle): vert, obs, gamma[4], lin[24]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/flash.h"
+
+namespace flash {
+
+constexpr int kLin = 24;         // floats of per-contact linearisation
+constexpr int kMaxPerVertex = 4; // contacts solved jointly on one vertex
+constexpr float kDamp = 1e-6f;   // Newton-step damping of the per-vertex block
+
+struct MeshTemplate {
+  int type = 0, n = 0, E = 0;
+  std::vector<double> rest, mass;
+  std::vector<int> elems;
+  double w_stretch = 0, w_bend = 0;
+};
+
+struct Group {
+  int mesh = 0;
+  float stiff = 1.f;
+  int n = 0, n_pad = 0, E = 0, H = 0, vpe = 3, nc = 2, type = 0;
+  int N = 0;           // environments in the group
+  int cols = 0;        // 3 * N
+  int cols_pad = 0;    // columns allocated (multiple of 128)
+  std::vector<int> env_ids;   // group-local -> global env
+  // mesh data (device)
+  int *genv = nullptr;        // [N] global env index
+  int *elems = nullptr;       // [E][4]
+  float *D = nullptr;         // [E][12]
+  float *wt = nullptr;        // [E]
+  int *hv = nullptr;          // [H][4]
+  float *hc = nullptr;        // [H][4]
+  int *v2e_off = nullptr, *v2e = nullptr;
+  int *v2h_off = nullptr, *v2h = nullptr;
+  float *mass = nullptr;      // [n]
+  float *Ainv = nullptr;      // [n_pad][n_pad] FP32 (symmetric)
+  __half *Ahi = nullptr, *Alo = nullptr;  // [n_pad][n_pad] split copy, scaled by 2^a_exp
+  int a_exp = 0;
+  // state (device) [cols_pad][n_pad]
+  float *q = nullptr, *v = nullptr, *qt = nullptr, *qp = nullptr;
+  float *r = nullptr, *w = nullptr, *f = nullptr;
+  __half *rh = nullptr, *rl = nullptr;    // split RHS for the tensor-core path
+  float *rscale = nullptr;                // [cols_pad] power-of-two column scale
+  // contacts (device)
+  int *ccount = nullptr, *cvert = nullptr, *cobs = nullptr;
+  float *cgam = nullptr, *clin = nullptr;
+  int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
+  float *pgam = nullptr;
+  size_t smem_local = 0;
+  bool p_in_smem = true;
+  float *pscratch = nullptr;              // element projections when they do not fit in smem
+};
+
+}  // namespace flash
+
+struct flash_scene {
+  flash_scene_desc d{};
+  std::vector<flash::MeshTemplate> meshes;
+  std::vector<flash_env_desc> envs;
+  std::vector<int> env_mesh;
+  std::vector<flash::Group> groups;
+  std::vector<int> env_group, env_local;
+  std::vector<int64_t> voff;   // host [N+1]
+  int N = 0, K = 0, cap = 0;
+  bool finalized = false;
+  // env-level device arrays
+  float *mu = nullptr;
+  int *otype = nullptr;
+  float *odims = nullptr, *ocomp = nullptr;
+  float *pose_t = nullptr, *pose_th = nullptr;   // [N][FLASH_MAX_OBS][7]
+  int *iters = nullptr, *done = nullptr;
+  float *rncp = nullptr;
+  int *status = nullptr;      // device status word
+  int *active = nullptr;      // device counter of environments still iterating
+  int *h_active = nullptr;    // pinned host mirror
+  int64_t *d_voff = nullptr;
+  std::vector<void *> allocs;
+};
+
+namespace flash {
+
+// error handling ---------------------------------------------------------
+void set_error(const std::string &msg);
+#define FLASH_CUDA_TRY(expr)                                                     \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ::flash::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+      return FLASH_ECUDA;                                                        \
+    }                                                                            \
+  } while (0)
+
+// kernel launchers (step_kernels.cu) ---------------------------------------
+struct StepArgs {
+  float h, gx, gy, gz, tol, gmax, tau, margin;
+  int k_min, k_cap, mode, warm, K, cap;
+};
+cudaError_t configure_kernels();
+cudaError_t launch_begin(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a, int k, int residual_only,
+                         int tc, cudaStream_t st);
+cudaError_t launch_ncp(const flash_scene *s, const Group &g, const StepArgs &a, int tc, cudaStream_t st);
+cudaError_t launch_end(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q_user, const float *v_user,
+                            float *q_out, float *v_out, int to_user, cudaStream_t st);
+cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,
+                          int to_user, cudaStream_t st);
+cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
+
+// global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
+// mode 0: out = A^-1 * rhs
+// mode 1: q  = q + w + A^-1 * rhs   (skips environments whose done flag is set)
+cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float *w, const int *done, int mode,
+                      cudaStream_t st);
+cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st);
+bool tc_available();
+
+// setup (setup_kernels.cu) ---------------------------------------------------
+cudaError_t invert_spd_f64(double *A, int n, int n_pad, int batch, cudaStream_t st);
+cudaError_t cast_inverse(const double *A64, int n_pad, float *A32, __half *hi, __half *lo, int a_exp,
+                         cudaStream_t st);
+
+}  // namespace flash

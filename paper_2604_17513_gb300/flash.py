@@ -1,0 +1,246 @@
+"""Thin Python binding of ``libflash.so`` (argument marshalling only).
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only fills the C descriptors, passes device pointers of torch tensors and the
+current torch stream, and raises on error codes.  If the shared library is
+missing the import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import scenes as _sc
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflash.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3, -4, -5, -6, -7
+WOVERFLOW = 1
+MAX_OBS = 8
+MODE_FIXED, MODE_TOL = 0, 1
+SOLVE_F32, SOLVE_F16X3 = 0, 1
+WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
+
+
+class FlashError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"flash error {code}: {msg}")
+        self.code = code
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("tol_ncp", C.c_double), ("maxforce", C.c_double),
+                ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
+                ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
+                ("warm", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("type", C.c_int32), ("n_verts", C.c_int32), ("n_elems", C.c_int32),
+                ("rest", C.POINTER(C.c_double)), ("elems", C.POINTER(C.c_int32)), ("mass", C.POINTER(C.c_double)),
+                ("w_stretch", C.c_double), ("w_bend", C.c_double)]
+
+
+class EnvDesc(C.Structure):
+    _fields_ = [("mu", C.c_float), ("stiffness", C.c_float), ("n_obs", C.c_int32),
+                ("obs_type", C.c_int32 * MAX_OBS), ("obs_dims", (C.c_float * 3) * MAX_OBS),
+                ("obs_compliance", C.c_float * MAX_OBS)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libflash.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2604_17513_gb300.build` "
+                              "(the simulator has no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.flash_last_error.restype = C.c_char_p
+        L.flash_scene_create.argtypes = [C.POINTER(SceneDesc), C.POINTER(vp)]
+        L.flash_mesh_add.argtypes = [vp, C.POINTER(MeshDesc), C.POINTER(i32)]
+        L.flash_envs_add.argtypes = [vp, i32, i32, C.POINTER(EnvDesc), C.POINTER(i32)]
+        L.flash_scene_finalize.argtypes = [vp, vp]
+        L.flash_scene_destroy.argtypes = [vp]
+        L.flash_scene_destroy.restype = None
+        L.flash_num_envs.argtypes = [vp]
+        L.flash_num_verts.argtypes = [vp]
+        L.flash_num_verts.restype = i64
+        L.flash_env_offsets.argtypes = [vp, C.POINTER(i64)]
+        L.flash_set_state.argtypes = [vp, vp, vp, vp]
+        L.flash_get_state.argtypes = [vp, vp, vp, vp]
+        L.flash_set_obstacle_poses.argtypes = [vp, vp, i32, vp]
+        L.flash_step.argtypes = [vp, i32, vp]
+        L.flash_get_contacts.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.flash_contact_cap.argtypes = [vp]
+        L.flash_get_stats.argtypes = [vp, vp, vp, vp]
+        L.flash_status_word.argtypes = [vp, vp]
+        L.flash_global_apply.argtypes = [vp, i32, i32, vp, vp, vp]
+        for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
+                     "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
+                     "flash_step", "flash_get_contacts", "flash_get_stats", "flash_status_word",
+                     "flash_global_apply"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code < 0:
+        raise FlashError(code, lib().flash_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Sim:
+    """A batch of environments behind one C scene.
+
+    ``scenes`` is one :class:`scenes.Scene` or a list of them (one mesh
+    template each); environments are numbered in list order.
+    """
+
+    def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
+                 warm=WARM_COLD, contact_cap=None):
+        if isinstance(scenes, _sc.Scene):
+            scenes = [scenes]
+        self.scenes = scenes
+        s0 = scenes[0]
+        d = SceneDesc()
+        d.h = s0.h
+        d.gravity[:] = list(s0.gravity)
+        d.tol_ncp = s0.tol_ncp if tol is None else tol
+        d.maxforce = s0.maxforce
+        d.thickness = s0.thickness
+        d.margin = s0.margin
+        d.k_max = s0.k_max if k_max is None else k_max
+        d.k_min = s0.k_min if k_min is None else k_min
+        d.k_cap = s0.k_cap if k_cap is None else k_cap
+        d.mode = s0.mode if mode is None else mode
+        d.contact_cap = contact_cap or max(sc.n_verts * sc.n_obs for sc in scenes)
+        d.solve = solve
+        d.warm = warm
+        self.desc = d
+        self._h = C.c_void_p()
+        _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))
+        self._keep = []
+        for sc in scenes:
+            rest = np.ascontiguousarray(sc.rest, np.float64)
+            el = np.ascontiguousarray(sc.elems, np.int32)
+            if el.size == 0:
+                el = np.zeros((1, 3 if sc.elem_type == 0 else 4), np.int32)
+            mass = np.ascontiguousarray(sc.mass, np.float64)
+            self._keep += [rest, el, mass]
+            m = MeshDesc(sc.elem_type, sc.n_verts, len(sc.elems), rest.ctypes.data_as(C.POINTER(C.c_double)),
+                         el.ctypes.data_as(C.POINTER(C.c_int32)), mass.ctypes.data_as(C.POINTER(C.c_double)),
+                         sc.w_stretch, sc.w_bend)
+            mid = C.c_int32()
+            _check(lib().flash_mesh_add(self._h, C.byref(m), C.byref(mid)))
+            envs = (EnvDesc * sc.n_envs)()
+            for e in range(sc.n_envs):
+                ed = envs[e]
+                ed.mu = float(sc.mu[e])
+                ed.stiffness = float(sc.stiff[e])
+                ed.n_obs = sc.n_obs
+                for o in range(sc.n_obs):
+                    ed.obs_type[o] = int(sc.obs_type[e, o])
+                    ed.obs_compliance[o] = float(sc.obs_comp[e, o])
+                    for c in range(3):
+                        ed.obs_dims[o][c] = float(sc.obs_dims[e, o, c])
+            first = C.c_int32()
+            _check(lib().flash_envs_add(self._h, mid, sc.n_envs, envs, C.byref(first)))
+        _check(lib().flash_scene_finalize(self._h, _stream()))
+        self.n_envs = lib().flash_num_envs(self._h)
+        self.n_verts = lib().flash_num_verts(self._h)
+        off = (C.c_int64 * (self.n_envs + 1))()
+        _check(lib().flash_env_offsets(self._h, off))
+        self.offsets = np.array(off[:], np.int64)
+        self.cap = lib().flash_contact_cap(self._h)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.step_index = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().flash_scene_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------ state
+    def set_state(self, q=None, v=None):
+        """q, v: float32 tensors [n_verts, 3] on the device (either may be None)."""
+        for t in (q, v):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.shape == (self.n_verts, 3)
+        _check(lib().flash_set_state(self._h, _ptr(q), _ptr(v), _stream()))
+
+    def get_state(self):
+        q = torch.empty((self.n_verts, 3), dtype=torch.float32, device=self.dev)
+        v = torch.empty_like(q)
+        _check(lib().flash_get_state(self._h, _ptr(q), _ptr(v), _stream()))
+        return q, v
+
+    def set_poses(self, poses, which=1):
+        """poses: float32 [n_envs, 8, 7] device tensor (target pose of the next step)."""
+        assert poses.is_cuda and poses.dtype == torch.float32 and poses.shape == (self.n_envs, MAX_OBS, 7)
+        poses = poses.contiguous()
+        _check(lib().flash_set_obstacle_poses(self._h, _ptr(poses), which, _stream()))
+
+    def step(self, n=1):
+        _check(lib().flash_step(self._h, n, _stream()))
+        self.step_index += n
+
+    def contacts(self):
+        cnt = torch.empty(self.n_envs, dtype=torch.int32, device=self.dev)
+        vert = torch.empty((self.n_envs, self.cap), dtype=torch.int32, device=self.dev)
+        obs = torch.empty_like(vert)
+        gam = torch.empty((self.n_envs, self.cap, 4), dtype=torch.float32, device=self.dev)
+        _check(lib().flash_get_contacts(self._h, _ptr(cnt), _ptr(vert), _ptr(obs), _ptr(gam), _stream()))
+        return cnt, vert, obs, gam
+
+    def stats(self):
+        it = torch.empty(self.n_envs, dtype=torch.int32, device=self.dev)
+        r = torch.empty(self.n_envs, dtype=torch.float32, device=self.dev)
+        _check(lib().flash_get_stats(self._h, _ptr(it), _ptr(r), _stream()))
+        return it, r
+
+    def status(self):
+        return _check(lib().flash_status_word(self._h, _stream()))
+
+    def global_apply(self, first_env, n, rhs):
+        out = torch.empty_like(rhs)
+        _check(lib().flash_global_apply(self._h, first_env, n, _ptr(rhs), _ptr(out), _stream()))
+        return out
+
+
+def poses_tensor(scenes, step, device):
+    """[N, 8, 7] float32 device tensor of the obstacle poses at the start of ``step``."""
+    if isinstance(scenes, _sc.Scene):
+        scenes = [scenes]
+    parts = []
+    for sc in scenes:
+        p = np.zeros((sc.n_envs, MAX_OBS, 7), np.float32)
+        p[:, :, 3] = 1.0
+        p[:, : sc.n_obs] = sc.poses[:, min(step, sc.poses.shape[1] - 1)]
+        parts.append(p)
+    return torch.from_numpy(np.concatenate(parts)).to(device)
+
+
+def state_tensors(scenes, device):
+    if isinstance(scenes, _sc.Scene):
+        scenes = [scenes]
+    q = np.concatenate([sc.q0.reshape(-1, 3) for sc in scenes]).astype(np.float32)
+    v = np.concatenate([sc.v0.reshape(-1, 3) for sc in scenes]).astype(np.float32)
+    return torch.from_numpy(q).to(device), torch.from_numpy(v).to(device)
