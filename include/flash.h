@@ -158,6 +158,23 @@ flash_status flash_status_word(flash_scene *s, void *stream);
 flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, const float *rhs,
                                 float *out, void *stream);
 
+/* Kernel accounting for measurement.  Kinds: 0 begin-of-step (detection,
+ * prediction), 1 local step + residual, 2 global solve (dense apply), 3 NCP
+ * blocks, 4 end-of-step.  flash_profile_enable(s, 1) brackets every launch
+ * with CUDA events on the launching stream; flash_profile_read synchronises
+ * and returns the summed device time (ms) and launch count of one kind since
+ * the last enable.  flash_launch_count returns the number of kernels this
+ * scene has launched since creation. */
+#define FLASH_KIND_BEGIN 0
+#define FLASH_KIND_LOCAL 1
+#define FLASH_KIND_SOLVE 2
+#define FLASH_KIND_NCP 3
+#define FLASH_KIND_END 4
+#define FLASH_NUM_KINDS 5
+flash_status flash_profile_enable(flash_scene *s, int32_t enable);
+flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, int64_t *launches);
+int64_t flash_launch_count(const flash_scene *s);
+
 const char *flash_last_error(void);
 
 #ifdef __cplusplus

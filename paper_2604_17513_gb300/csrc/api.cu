@@ -297,17 +297,59 @@ StepArgs step_args(const flash_scene *s) {
 
 bool use_tc(const flash_scene *s) { return s->d.solve == FLASH_SOLVE_F16X3; }
 
-cudaError_t global_solves(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
+cudaEvent_t pool_event(flash_scene *s) {
+  if (s->ev_used == s->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    s->ev_pool.push_back(e);
+  }
+  return s->ev_pool[s->ev_used++];
+}
+
+// Launch accounting: counts kernels and, while profiling, brackets the launch
+// with a pair of events on the launching stream.
+template <typename F>
+cudaError_t timed(flash_scene *s, int kind, cudaStream_t st, F &&f) {
+  s->launches += 1;
+  if (!s->profiling) return f();
+  cudaEvent_t e0 = pool_event(s), e1 = pool_event(s);
+  if (!e0 || !e1) return cudaErrorMemoryAllocation;
+  cudaEventRecord(e0, st);
+  cudaError_t r = f();
+  cudaEventRecord(e1, st);
+  s->ev_kind.push_back(kind);
+  return r;
+}
+
+cudaError_t flush_profile(flash_scene *s) {
+  if (s->ev_kind.empty()) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(s->ev_pool[2 * s->ev_kind.size() - 1]);
+  if (e != cudaSuccess) return e;
+  for (size_t i = 0; i < s->ev_kind.size(); i++) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    s->prof_ms[s->ev_kind[i]] += ms;
+    s->prof_n[s->ev_kind[i]] += 1;
+  }
+  s->ev_kind.clear();
+  s->ev_used = 0;
+  return cudaSuccess;
+}
+
+cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
   // w = A^-1 r ;  NCP ;  q = q + w + A^-1 J^T dgamma
   cudaError_t e;
   const bool tc = use_tc(s);
-  if (tc) e = gemm_tc(g, g.w, nullptr, s->done, 0, st);
-  else e = gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st);
+  e = timed(s, FLASH_KIND_SOLVE, st, [&] {
+    return tc ? gemm_tc(g, g.w, nullptr, s->done, 0, st) : gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st);
+  });
   if (e != cudaSuccess) return e;
-  e = launch_ncp(s, g, a, tc ? 1 : 0, st);
+  e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, tc ? 1 : 0, st); });
   if (e != cudaSuccess) return e;
-  if (tc) return gemm_tc(g, g.q, g.w, s->done, 1, st);
-  return gemm_simt(g, g.f, g.q, g.w, s->done, 1, st);
+  return timed(s, FLASH_KIND_SOLVE, st, [&] {
+    return tc ? gemm_tc(g, g.q, g.w, s->done, 1, st) : gemm_simt(g, g.f, g.q, g.w, s->done, 1, st);
+  });
 }
 
 }  // namespace
@@ -405,9 +447,13 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
     s->env_local[e] = (int)s->groups[gi].env_ids.size();
     s->groups[gi].env_ids.push_back(e);
   }
+  if (s->d.solve == FLASH_SOLVE_F16X3 && !tc_available())
+    return fail(FLASH_ENOTIMPL, "tensor-core solve needs an sm_103 device and the TMA driver entry point");
+  FLASH_CUDA_TRY(dalloc(s, &s->status, 1));
   s->voff.assign(s->N + 1, 0);
   for (int e = 0; e < s->N; e++) s->voff[e + 1] = s->voff[e] + s->meshes[s->env_mesh[e]].n;
   for (auto &g : s->groups) {
+    g.status = s->status;
     flash_status r = build_group(s, g, st);
     if (r != FLASH_OK) return r;
   }
@@ -434,7 +480,6 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->iters, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->done, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->rncp, (size_t)s->N));
-  FLASH_CUDA_TRY(dalloc(s, &s->status, 1));
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
@@ -447,6 +492,7 @@ void flash_scene_destroy(flash_scene *s) {
   if (!s) return;
   cudaDeviceSynchronize();
   for (void *p : s->allocs) cudaFree(p);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->h_active) cudaFreeHost(s->h_active);
   delete s;
 }
@@ -504,29 +550,49 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
   for (int step = 0; step < n_steps; step++) {
-    for (auto &g : s->groups) FLASH_CUDA_TRY(launch_begin(s, g, a, st));
+    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, g, a, st); }));
     if (s->d.mode == FLASH_MODE_FIXED) {
       for (int k = 1; k <= s->d.k_max; k++)
         for (auto &g : s->groups) {
-          FLASH_CUDA_TRY(launch_local(s, g, a, k, 0, tc, st));
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, k, 0, tc, st); }));
           FLASH_CUDA_TRY(global_solves(s, g, a, st));
         }
-      for (auto &g : s->groups) FLASH_CUDA_TRY(launch_local(s, g, a, s->d.k_max + 1, 1, tc, st));
+      for (auto &g : s->groups)
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, s->d.k_max + 1, 1, tc, st); }));
     } else {
       for (int k = 1; k <= s->d.k_cap + 1; k++) {
         FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
-        for (auto &g : s->groups) FLASH_CUDA_TRY(launch_local(s, g, a, k, 0, tc, st));
+        for (auto &g : s->groups)
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, k, 0, tc, st); }));
         FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
         FLASH_CUDA_TRY(cudaStreamSynchronize(st));
         if (*s->h_active == 0) break;
         for (auto &g : s->groups) FLASH_CUDA_TRY(global_solves(s, g, a, st));
       }
     }
-    for (auto &g : s->groups) FLASH_CUDA_TRY(launch_end(s, g, a, st));
+    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, g, a, st); }));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
   }
   return FLASH_OK;
 }
+
+flash_status flash_profile_enable(flash_scene *s, int32_t enable) {
+  if (!s) return fail(FLASH_EINVAL, "null scene");
+  FLASH_CUDA_TRY(flush_profile(s));
+  s->profiling = enable != 0;
+  for (int k = 0; k < FLASH_NUM_KINDS; k++) { s->prof_ms[k] = 0; s->prof_n[k] = 0; }
+  return FLASH_OK;
+}
+
+flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, int64_t *launches) {
+  if (!s || kind < 0 || kind >= FLASH_NUM_KINDS) return fail(FLASH_EINVAL, "invalid arguments");
+  FLASH_CUDA_TRY(flush_profile(s));
+  if (total_ms) *total_ms = s->prof_ms[kind];
+  if (launches) *launches = s->prof_n[kind];
+  return FLASH_OK;
+}
+
+int64_t flash_launch_count(const flash_scene *s) { return s ? s->launches : 0; }
 
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs, float *gamma,
                                 void *stream) {

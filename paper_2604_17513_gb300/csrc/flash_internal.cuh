@@ -68,6 +68,7 @@ struct Group {
   size_t smem_local = 0;
   bool p_in_smem = true;
   float *pscratch = nullptr;              // element projections when they do not fit in smem
+  int *status = nullptr;                  // scene status word (device)
 };
 
 }  // namespace flash
@@ -94,6 +95,14 @@ struct flash_scene {
   int *h_active = nullptr;    // pinned host mirror
   int64_t *d_voff = nullptr;
   std::vector<void *> allocs;
+  // launch accounting
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;   // kind of each recorded pair
+  double prof_ms[FLASH_NUM_KINDS] = {0};
+  int64_t prof_n[FLASH_NUM_KINDS] = {0};
 };
 
 namespace flash {

@@ -1,14 +1,282 @@
-// Tensor-core global solve (tcgen05, f16 hi/lo split, FP32 accumulation in
-// TMEM).  Placeholder until the kernel lands: reports "not supported".
+// Tensor-core global solve for sm_103a: the dense multi-RHS apply
+//   OUT[:, j] = A^-1 * RHS[:, j]   over all columns j = (environment, coord)
+// of a group -- the "S^T S g" applies of Algorithm 1 done with the explicit
+// inverse of the constant system matrix shared by every environment.
+//
+// Precision: A^-1 and every RHS column are split into f16 hi + lo parts with
+// power-of-two scales (A^-1 by 2^a_exp once at setup, each RHS column by its
+// own scale), and three tcgen05.mma products hi*hi + hi*lo + lo*hi accumulate
+// in FP32 in tensor memory, which keeps ~21 significant bits: enough for the
+// correction form q^k = q^{k-1} + A^-1 r, whose error against the FP64
+// oracle must stay below 1e-5 m.
+//
+// Structure (one 128 x 128 output tile per CTA, 128 threads):
+//   warp 0 lane 0  TMA producer: 4 tiles (A hi/lo, B hi/lo) of 128 x 64 f16
+//                  per k-block into a 3-stage ring, 128B swizzle
+//   warp 1 lane 0  MMA issuer: 4 k-slices x 3 products of M128 N128 K16,
+//                  tcgen05.commit frees the stage / signals the epilogue
+//   warp 2         allocates / frees 128 TMEM columns
+//   all 4 warps    epilogue: tcgen05.ld 32 lanes x 32 columns at a time,
+//                  rescale, coalesced column stores (optionally q + w + .)
+// Every mbarrier wait is bounded; on timeout the CTA raises an error flag,
+// drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "flash_internal.cuh"
 
 namespace flash {
+namespace {
 
-bool tc_available() { return false; }
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_A = BM * BK * 2;   // bytes of one f16 A tile (16 KiB)
+constexpr int TILE_B = BN * BK * 2;   // bytes of one f16 B tile (16 KiB)
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s of SM clock before a wait is declared hung
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// bounded wait on the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128B swizzle
+  return d;
+}
+
+// instruction descriptor: kind::f16, A = B = f16, D = f32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+              float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
+              const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int cols,
+              float a_unscale, int mode) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const int KB = n_pad / BK;
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+  // skip tiles whose environments have all converged (mode 1 writes nothing then)
+  if (mode == 1) {
+    int live = 0;
+    for (int c = j0 + threadIdx.x; c < min(j0 + BN, cols); c += blockDim.x) live |= !done[genv[c / 3]];
+    if (!__syncthreads_or(live)) return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail_sh = 0;
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int kb = 0;
+    for (; kb < KB; kb++) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1)) { atomicExch(&fail_sh, 1); break; }
+      uint8_t *st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      const int k0 = kb * BK;
+      tma_load_2d(st, &tmAh, &full_bar[s], k0, m0);
+      tma_load_2d(st + TILE_A, &tmAl, &full_bar[s], k0, m0);
+      tma_load_2d(st + 2 * TILE_A, &tmBh, &full_bar[s], k0, j0);
+      tma_load_2d(st + 2 * TILE_A + TILE_B, &tmBl, &full_bar[s], k0, j0);
+    }
+    // drain: wait until every stage this thread armed has landed (bounded)
+    for (int t = max(0, kb - STAGES); t < kb; t++) mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_f16(BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < KB; kb++) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1)) { atomicExch(&fail_sh, 1); ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t ah = base, al = base + TILE_A, bh = base + 2 * TILE_A, bl = base + 2 * TILE_A + TILE_B;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ks++) {
+        const uint32_t off = ks * 32;   // 16 f16 along K inside the 128-byte swizzle row
+        mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, (kb | ks) ? 1u : 0u);
+        mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+        mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);
+    (void)ok;
+  }
+  __syncwarp();
+  // ---------------- epilogue (all 4 warps; warp w owns TMEM lanes 32w..32w+31)
+  bool ok = mbar_wait(&done_bar, 0);
+  if (!ok) atomicExch(&fail_sh, 1);
+  __syncthreads();
+  if (fail_sh) {
+    if (threadIdx.x == 0) atomicOr(status, 1 << 11);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        const int col = j0 + c0 + j;
+        if (col >= cols) continue;
+        const float val = __uint_as_float(v[j]) * a_unscale * rscale[col];
+        const size_t idx = (size_t)col * n_pad + row;
+        if (mode == 0) {
+          out[idx] = val;
+        } else if (!done[genv[col / 3]]) {
+          out[idx] = out[idx] + W[idx] + val;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D f16 tensor [outer][inner] (inner contiguous), box 64 x rows, 128B swizzle
+bool make_map(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && get_encode() != nullptr;
+}
 
 cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st) {
-  (void)g; (void)out; (void)w; (void)done; (void)mode; (void)st;
-  return cudaErrorNotSupported;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (g.n_pad % BM != 0 || g.n_pad % BK != 0 || g.cols_pad % BN != 0) return cudaErrorInvalidValue;
+  CUtensorMap tmAh, tmAl, tmBh, tmBl;
+  if (!make_map(&tmAh, g.Ahi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, g.Alo, g.n_pad, g.n_pad, BM) ||
+      !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN) || !make_map(&tmBl, g.rl, g.n_pad, g.cols_pad, BN))
+    return cudaErrorInvalidValue;
+  dim3 grid(g.cols_pad / BN, g.n_pad / BM);
+  k_gemm_tc<<<grid, 128, SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
+                                           g.n_pad, g.cols, ldexpf(1.f, -g.a_exp), mode);
+  return cudaGetLastError();
 }
 
 }  // namespace flash

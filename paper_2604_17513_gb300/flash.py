@@ -83,10 +83,14 @@ def lib():
         L.flash_get_stats.argtypes = [vp, vp, vp, vp]
         L.flash_status_word.argtypes = [vp, vp]
         L.flash_global_apply.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.flash_profile_enable.argtypes = [vp, i32]
+        L.flash_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
+        L.flash_launch_count.argtypes = [vp]
+        L.flash_launch_count.restype = i64
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
                      "flash_step", "flash_get_contacts", "flash_get_stats", "flash_status_word",
-                     "flash_global_apply"):
+                     "flash_global_apply", "flash_profile_enable", "flash_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -218,6 +222,24 @@ class Sim:
 
     def status(self):
         return _check(lib().flash_status_word(self._h, _stream()))
+
+    KINDS = ("begin", "local", "solve", "ncp", "end")
+
+    def profile(self, enable=True):
+        """Bracket every launch with CUDA events on the launching stream."""
+        _check(lib().flash_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (total device ms, launches)} since the last profile() call."""
+        out = {}
+        for k, name in enumerate(self.KINDS):
+            ms, n = C.c_double(), C.c_int64()
+            _check(lib().flash_profile_read(self._h, k, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def launch_count(self):
+        return lib().flash_launch_count(self._h)
 
     def global_apply(self, first_env, n, rhs):
         out = torch.empty_like(rhs)
