@@ -263,7 +263,6 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.cvert, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.cobs, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.cgam, cc * 4));
-  FLASH_CUDA_TRY(dalloc(s, &g.clin, cc * kLin));
   FLASH_CUDA_TRY(dalloc(s, &g.pcount, (size_t)g.N));
   FLASH_CUDA_TRY(dalloc(s, &g.pvert, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));

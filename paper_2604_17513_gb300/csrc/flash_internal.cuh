@@ -9,7 +9,7 @@
 //              float wt[E] = h^2 * w_i
 //   hinges     int   [H][4], float hc[H][4]  (bending stencil scaled by h sqrt(w_b s))
 //   incidence  CSR vertex -> element slot (4e + a) and vertex -> hinge slot
-//   contacts   per env, sorted by (vertex, obstacle): vert, obs, gamma[4], lin[24]
+//   contacts   per env, sorted by (vertex, obstacle): vert, obs, gamma[4]
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,7 +23,6 @@
 
 namespace flash {
 
-constexpr int kLin = 24;         // floats of per-contact linearisation
 constexpr int kMaxPerVertex = 4; // contacts solved jointly on one vertex
 constexpr float kDamp = 1e-6f;   // Newton-step damping of the per-vertex block
 
@@ -62,7 +61,7 @@ struct Group {
   float *rscale = nullptr;                // [cols_pad] power-of-two column scale
   // contacts (device)
   int *ccount = nullptr, *cvert = nullptr, *cobs = nullptr;
-  float *cgam = nullptr, *clin = nullptr;
+  float *cgam = nullptr;
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
   size_t smem_local = 0;

@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail_sh;
+  __shared__ float col_scale[BN];
+  __shared__ int col_live[BN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int KB = n_pad / BK;
@@ -182,6 +184,13 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
   // ---------------- epilogue (all 4 warps; warp w owns TMEM lanes 32w..32w+31)
+  // per-column scale (A and RHS unscaling) and liveness, staged once per tile
+  for (int c = threadIdx.x; c < BN; c += blockDim.x) {
+    const int col = j0 + c;
+    const bool in = col < cols;
+    col_scale[c] = in ? a_unscale * rscale[col] : 0.f;
+    col_live[c] = in && (mode == 0 || !done[genv[col / 3]]);
+  }
   bool ok = mbar_wait(&done_bar, 0);
   if (!ok) atomicExch(&fail_sh, 1);
   __syncthreads();
@@ -204,17 +213,19 @@ __global__ void __launch_bounds__(128, 1)
             "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float *o = out + (size_t)(j0 + c0) * n_pad + row;
+      if (mode == 0) {
 #pragma unroll
-      for (int j = 0; j < 32; j++) {
-        const int col = j0 + c0 + j;
-        if (col >= cols) continue;
-        const float val = __uint_as_float(v[j]) * a_unscale * rscale[col];
-        const size_t idx = (size_t)col * n_pad + row;
-        if (mode == 0) {
-          out[idx] = val;
-        } else if (!done[genv[col / 3]]) {
-          out[idx] = out[idx] + W[idx] + val;
-        }
+        for (int j = 0; j < 32; j++)
+          if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
+      } else {
+        const float *wv = W + (size_t)(j0 + c0) * n_pad + row;
+        float prev[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) prev[j] = col_live[c0 + j] ? o[(size_t)j * n_pad] + wv[(size_t)j * n_pad] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          if (col_live[c0 + j]) o[(size_t)j * n_pad] = prev[j] + __uint_as_float(v[j]) * col_scale[c0 + j];
       }
     }
   }

@@ -25,7 +25,7 @@ struct GroupView {
   __half *rh, *rl;
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
-  float *cgam, *clin, *pgam, *pscratch;
+  float *cgam, *pgam, *pscratch;
   int p_in_smem;
 };
 
@@ -44,7 +44,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w;
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
-  v.pobs = g.pobs; v.cgam = g.cgam; v.clin = g.clin; v.pgam = g.pgam; v.pscratch = g.pscratch;
+  v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.pscratch = g.pscratch;
   v.p_in_smem = g.p_in_smem ? 1 : 0;
   return v;
 }
@@ -95,6 +95,22 @@ __device__ float block_max(float x, float *sh) {
   float r = sh[0];
   __syncthreads();
   return r;
+}
+
+// block-wide max of three values at once (2 barriers)
+__device__ void block_max3(float &x0, float &x1, float &x2, float (*sh)[3]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = fmaxf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    x2 = fmaxf(x2, __shfl_xor_sync(0xffffffffu, x2, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) { sh[wid][0] = x0; sh[wid][1] = x1; sh[wid][2] = x2; }
+  __syncthreads();
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+  for (int w = 0; w < nw; w++) { m0 = fmaxf(m0, sh[w][0]); m1 = fmaxf(m1, sh[w][1]); m2 = fmaxf(m2, sh[w][2]); }
+  x0 = m0; x1 = m1; x2 = m2;
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -185,51 +201,74 @@ __global__ void __launch_bounds__(256) k_begin(GroupView G, EnvView V, StepArgs 
 // ---------------------------------------------------------------------------
 // local step + residual
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_lin(float *dst, const ContactLin &L) {
-  for (int i = 0; i < 9; i++) dst[i] = L.R[i];
-  dst[9] = L.phi[0]; dst[10] = L.phi[1]; dst[11] = L.phi[2];
-  dst[12] = L.cn;
-  for (int i = 0; i < 4; i++) dst[13 + i] = L.Ct[i];
-  dst[17] = L.dn; dst[18] = L.dtn[0]; dst[19] = L.dtn[1];
-  for (int i = 0; i < 4; i++) dst[20 + i] = L.Dtt[i];
-}
-
-// write one environment's three columns in f16 hi/lo with a power-of-two
-// scale per column (tensor-core RHS); vals in shared memory [3][n]
-__device__ void write_split_columns(const GroupView &G, int l, const float *vals, float *sh_red) {
+// Write one environment's three columns in f16 hi/lo with a power-of-two
+// scale per column (tensor-core RHS); vals in shared memory [3][n].  Each
+// thread passes the maxima of |vals| it already knows (or 0); the kernel
+// completes them over the rows this thread owns and reduces once.
+__device__ void write_split_columns(const GroupView &G, int l, const float *vals, float (*sh3)[3], bool scan,
+                                    float m0 = 0.f, float m1 = 0.f, float m2 = 0.f) {
   const int n = G.n, np = G.n_pad;
+  float m[3] = {m0, m1, m2};
+  if (scan)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      for (int c = 0; c < 3; c++) m[c] = fmaxf(m[c], fabsf(vals[c * n + i]));
+  block_max3(m[0], m[1], m[2], sh3);
   for (int c = 0; c < 3; c++) {
-    float m = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(vals[c * n + i]));
-    m = block_max(m, sh_red);
     int ex = 0;
-    if (m > 0.f) {
-      frexpf(m, &ex);      // m = f * 2^ex, f in [0.5, 1)
+    if (m[c] > 0.f) {
+      frexpf(m[c], &ex);   // m = f * 2^ex, f in [0.5, 1)
       ex = 14 - ex;        // scaled max in [2^13, 2^14)
     }
-    float sc = ldexpf(1.f, ex);
-    size_t col = (size_t)(l * 3 + c);
+    const float sc = ldexpf(1.f, ex);
+    const size_t col = (size_t)(l * 3 + c);
     if (threadIdx.x == 0) G.rscale[col] = ldexpf(1.f, -ex);
-    __half *hh = G.rh + col * np, *hl = G.rl + col * np;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-      float x = i < n ? vals[c * n + i] * sc : 0.f;
-      __half xh = __float2half_rn(x);
+    __half2 *hh = reinterpret_cast<__half2 *>(G.rh + col * np), *hl = reinterpret_cast<__half2 *>(G.rl + col * np);
+    for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
+      const float x0 = 2 * i < n ? vals[c * n + 2 * i] * sc : 0.f;
+      const float x1 = 2 * i + 1 < n ? vals[c * n + 2 * i + 1] * sc : 0.f;
+      const __half2 xh = __floats2half2_rn(x0, x1);
       hh[i] = xh;
-      hl[i] = __float2half_rn(x - __half2float(xh));
+      const float2 back = __half22float2(xh);
+      hl[i] = __floats2half2_rn(x0 - back.x, x1 - back.y);
     }
   }
 }
 
+struct ObsShared {
+  int type[FLASH_MAX_OBS];
+  float dims[FLASH_MAX_OBS][3], pose[FLASH_MAX_OBS][7], poset[FLASH_MAX_OBS][7], comp[FLASH_MAX_OBS];
+};
+
+__device__ __forceinline__ void load_obstacles(const EnvView &V, int e, int K, ObsShared &O) {
+  if (threadIdx.x < K) {
+    int o = threadIdx.x;
+    O.type[o] = V.otype[e * FLASH_MAX_OBS + o];
+    O.comp[o] = V.ocomp[e * FLASH_MAX_OBS + o];
+    for (int c = 0; c < 3; c++) O.dims[o][c] = V.odims[(e * FLASH_MAX_OBS + o) * 3 + c];
+    for (int c = 0; c < 7; c++) {
+      O.pose[o][c] = V.pose_th[(e * FLASH_MAX_OBS + o) * 7 + c];
+      O.poset[o][c] = V.pose_t[(e * FLASH_MAX_OBS + o) * 7 + c];
+    }
+  }
+}
+
+__device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs &a, float mu, float mv, V3 x, V3 xt,
+                                       const float *g, ContactLin &L) {
+  linearize_contact(O.type[o], O.dims[o], O.comp[o], O.poset[o], O.pose[o], a.tau, mu, a.h, mv, x, xt, g, L);
+}
+
+template <int VPE>
 __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs a, int k, int residual_only,
                                                int tc) {
+  // VPE = vertices per element: 3 (triangle, F is 3x2) or 4 (tet, F is 3x3)
+  constexpr int nc = VPE - 1, vpe = VPE;
   extern __shared__ float smem[];
   __shared__ float sh_red[32];
+  __shared__ float sh3[32][3];
   __shared__ int s_done;
-  __shared__ int s_type[FLASH_MAX_OBS];
-  __shared__ float s_dims[FLASH_MAX_OBS][3], s_pose[FLASH_MAX_OBS][7], s_poset[FLASH_MAX_OBS][7],
-      s_comp[FLASH_MAX_OBS];
+  __shared__ ObsShared O;
   const int l = blockIdx.x, e = G.genv[l];
-  const int n = G.n, np = G.n_pad, nc = G.nc, vpe = G.vpe;
+  const int n = G.n, np = G.n_pad;
   if (V.done[e]) return;
   float *qs = smem;           // [3][n]
   float *rs = qs + 3 * n;     // [3][n]
@@ -246,37 +285,111 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
     int c = i / n, j = i - c * n;
     qs[i] = q[c * np + j];
   }
-  if (threadIdx.x < a.K) {
-    int o = threadIdx.x;
-    s_type[o] = V.otype[e * FLASH_MAX_OBS + o];
-    s_comp[o] = V.ocomp[e * FLASH_MAX_OBS + o];
-    for (int c = 0; c < 3; c++) s_dims[o][c] = V.odims[(e * FLASH_MAX_OBS + o) * 3 + c];
-    for (int c = 0; c < 7; c++) {
-      s_pose[o][c] = V.pose_th[(e * FLASH_MAX_OBS + o) * 7 + c];
-      s_poset[o][c] = V.pose_t[(e * FLASH_MAX_OBS + o) * 7 + c];
+  load_obstacles(V, e, a.K, O);
+  __syncthreads();
+  if (!residual_only) {
+    // ---- local projection p_i = closest rotation to F_i = G_i q; store w~(p - F)
+    for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
+      const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
+      const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
+      const float *D = G.D + 12 * el;
+      float F[9], R[9], Dl[12];
+#pragma unroll
+      for (int t = 0; t < 3 * vpe; t++) Dl[t] = __ldg(D + t);
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int j = 0; j < nc; j++) {
+          float s = 0.f;
+#pragma unroll
+          for (int aa = 0; aa < vpe; aa++) s += qs[c * n + vv[aa]] * Dl[aa * 3 + j];
+          F[nc * c + j] = s;
+        }
+      if constexpr (nc == 2) closest_rot32(F, R);
+      else closest_rot33(F, R);
+      const float wt = __ldg(G.wt + el);
+      float *P = Ps + (size_t)el * nc * 3;
+#pragma unroll
+      for (int t = 0; t < 3 * nc; t++) P[t] = wt * (R[t] - F[t]);
+    }
+    for (int hh = threadIdx.x; hh < G.H; hh += blockDim.x) {
+      const int4 vi = *reinterpret_cast<const int4 *>(G.hv + 4 * hh);
+      const float4 cc = *reinterpret_cast<const float4 *>(G.hc + 4 * hh);
+      for (int c = 0; c < 3; c++)
+        Ss[hh * 3 + c] = cc.x * qs[c * n + vi.x] + cc.y * qs[c * n + vi.y] + cc.z * qs[c * n + vi.z] +
+                         cc.w * qs[c * n + vi.w];
+    }
+    __syncthreads();
+    // ---- residual r = M (q~ - q) + sum G^T w~ (p - G q) - bending
+    const float *qp = G.qp + (size_t)l * 3 * np;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float m = __ldg(G.mass + i);
+      float acc[3];
+      for (int c = 0; c < 3; c++) acc[c] = m * (qp[c * np + i] - qs[c * n + i]);
+      const int e0 = __ldg(G.v2e_off + i), e1 = __ldg(G.v2e_off + i + 1);
+      for (int t = e0; t < e1; t++) {
+        int slot = __ldg(G.v2e + t);
+        int el = slot >> 2, aa = slot & 3;
+        const float *D = G.D + 12 * el + 3 * aa;
+        const float *P = Ps + (size_t)el * nc * 3;
+        float d[nc];
+#pragma unroll
+        for (int j = 0; j < nc; j++) d[j] = __ldg(D + j);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          float s = 0.f;
+#pragma unroll
+          for (int j = 0; j < nc; j++) s += d[j] * P[nc * c + j];
+          acc[c] += s;
+        }
+      }
+      const int h0 = __ldg(G.v2h_off + i), h1 = __ldg(G.v2h_off + i + 1);
+      for (int t = h0; t < h1; t++) {
+        int slot = __ldg(G.v2h + t);
+        int hh = slot >> 2, aa = slot & 3;
+        float cc = __ldg(G.hc + 4 * hh + aa);
+        for (int c = 0; c < 3; c++) acc[c] -= cc * Ss[hh * 3 + c];
+      }
+      for (int c = 0; c < 3; c++) rs[c * n + i] = acc[c];
     }
   }
   __syncthreads();
-  // ---- contacts: linearise at (q^{k-1}, gamma^{k-1}); residual of that iterate
+  // ---- contacts: linearise at (q^{k-1}, gamma^{k-1}), NCP residual of that
+  //      iterate, and + J^T gamma^{k-1} (one thread per vertex run)
   const int cnt = G.ccount[l];
   const int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
   const float *gam = G.cgam + (size_t)l * G.cap * 4;
-  float *lin = G.clin + (size_t)l * G.cap * kLin;
   const float *qt = G.qt + (size_t)l * 3 * np;
   const float mu = V.mu[e];
   float rmax = 0.f;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    int vtx = cvert[j], o = cobs[j];
-    ContactLin L;
-    linearize_contact(s_type[o], s_dims[o], s_comp[o], s_poset[o], s_pose[o], a.tau, mu, a.h, G.mass[vtx],
-                      v3(qs[vtx], qs[n + vtx], qs[2 * n + vtx]), v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]),
-                      gam + 4 * j, L);
-    store_lin(lin + (size_t)j * kLin, L);
-    rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
+    const int vtx = cvert[j];
+    if (j > 0 && cvert[j - 1] == vtx) continue;
+    const V3 x = v3(qs[vtx], qs[n + vtx], qs[2 * n + vtx]);
+    const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
+    const float mv = __ldg(G.mass + vtx);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int jj = j; jj < cnt && cvert[jj] == vtx; jj++) {
+      ContactLin L;
+      const float4 g4 = *reinterpret_cast<const float4 *>(gam + 4 * jj);
+      const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+      lin_at(O, cobs[jj], a, mu, mv, x, xt, g, L);
+      rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
+      const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
+      const float y2 = L.R[6] * g[1] + L.R[7] * g[2] + L.R[8] * g[3];
+      fx += L.R[0] * g[0] + L.R[3] * y1 + L.R[6] * y2;
+      fy += L.R[1] * g[0] + L.R[4] * y1 + L.R[7] * y2;
+      fz += L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2;
+    }
+    if (!residual_only) {
+      rs[vtx] += fx;
+      rs[n + vtx] += fy;
+      rs[2 * n + vtx] += fz;
+    }
   }
   rmax = block_max(rmax, sh_red);
   if (threadIdx.x == 0) {
-    int it = k - 1;
+    const int it = k - 1;
     int stop;
     if (a.mode == FLASH_MODE_FIXED) stop = residual_only;
     else stop = (it >= a.k_min && rmax <= a.tol) || it >= a.k_cap || residual_only;
@@ -292,83 +405,8 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
   }
   __syncthreads();
   if (s_done) return;
-  // ---- local projection p_i = closest rotation to F_i = G_i q; store w~(p - F)
-  const float h2w = 1.f;  // wt already holds h^2 w_i
-  (void)h2w;
-  for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
-    const int *vi = G.elems + 4 * el;
-    const float *D = G.D + 12 * el;
-    float F[9], R[9];
-    for (int c = 0; c < 3; c++)
-      for (int j = 0; j < nc; j++) {
-        float s = 0.f;
-        for (int aa = 0; aa < vpe; aa++) s += qs[c * n + vi[aa]] * D[aa * 3 + j];
-        F[nc * c + j] = s;
-      }
-    if (nc == 2) closest_rot32(F, R);
-    else closest_rot33(F, R);
-    float wt = G.wt[el];
-    float *P = Ps + (size_t)el * nc * 3;
-    for (int t = 0; t < 3 * nc; t++) P[t] = wt * (R[t] - F[t]);
-  }
-  for (int hh = threadIdx.x; hh < G.H; hh += blockDim.x) {
-    const int *vi = G.hv + 4 * hh;
-    const float *cc = G.hc + 4 * hh;
-    for (int c = 0; c < 3; c++) {
-      float s = 0.f;
-      for (int aa = 0; aa < 4; aa++) s += cc[aa] * qs[c * n + vi[aa]];
-      Ss[hh * 3 + c] = s;
-    }
-  }
-  __syncthreads();
-  // ---- residual r = M (q~ - q) + sum G^T w~ (p - G q) - bending
-  const float *qp = G.qp + (size_t)l * 3 * np;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float m = G.mass[i];
-    float acc[3];
-    for (int c = 0; c < 3; c++) acc[c] = m * (qp[c * np + i] - qs[c * n + i]);
-    for (int t = G.v2e_off[i]; t < G.v2e_off[i + 1]; t++) {
-      int slot = G.v2e[t];
-      int el = slot >> 2, aa = slot & 3;
-      const float *D = G.D + 12 * el + 3 * aa;
-      const float *P = Ps + (size_t)el * nc * 3;
-      for (int c = 0; c < 3; c++) {
-        float s = 0.f;
-        for (int j = 0; j < nc; j++) s += D[j] * P[nc * c + j];
-        acc[c] += s;
-      }
-    }
-    for (int t = G.v2h_off[i]; t < G.v2h_off[i + 1]; t++) {
-      int slot = G.v2h[t];
-      int hh = slot >> 2, aa = slot & 3;
-      float cc = G.hc[4 * hh + aa];
-      for (int c = 0; c < 3; c++) acc[c] -= cc * Ss[hh * 3 + c];
-    }
-    for (int c = 0; c < 3; c++) rs[c * n + i] = acc[c];
-  }
-  __syncthreads();
-  // ---- + J^T gamma^{k-1} (frame of q^{k-1}); one thread per vertex run
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    if (j > 0 && cvert[j - 1] == cvert[j]) continue;
-    int vtx = cvert[j];
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int jj = j; jj < cnt && cvert[jj] == vtx; jj++) {
-      const float *L = lin + (size_t)jj * kLin;
-      const float *g = gam + 4 * jj;
-      float gn = g[0];
-      float y1 = L[3] * g[1] + L[4] * g[2] + L[5] * g[3];
-      float y2 = L[6] * g[1] + L[7] * g[2] + L[8] * g[3];
-      fx += L[0] * gn + L[3] * y1 + L[6] * y2;
-      fy += L[1] * gn + L[4] * y1 + L[7] * y2;
-      fz += L[2] * gn + L[5] * y1 + L[8] * y2;
-    }
-    rs[vtx] += fx;
-    rs[n + vtx] += fy;
-    rs[2 * n + vtx] += fz;
-  }
-  __syncthreads();
   if (tc) {
-    write_split_columns(G, l, rs, sh_red);
+    write_split_columns(G, l, rs, sh3, true);
   } else {
     float *r = G.r + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -407,96 +445,225 @@ __device__ void solve_dense(int N, float *A, float *b) {
   }
 }
 
-// rows of D_C (3x3) and D_y (3x3) of one contact from its linearisation
-__device__ __forceinline__ void lin_mats(const float *L, float DC[9], float Dy[9]) {
-  DC[0] = L[12]; DC[1] = 0.f; DC[2] = 0.f;
-  DC[3] = 0.f; DC[4] = L[13]; DC[5] = L[14];
-  DC[6] = 0.f; DC[7] = L[15]; DC[8] = L[16];
-  Dy[0] = L[17]; Dy[1] = 0.f; Dy[2] = 0.f;
-  Dy[3] = L[18]; Dy[4] = L[20]; Dy[5] = L[21];
-  Dy[6] = L[19]; Dy[7] = L[22]; Dy[8] = L[23];
+// D_C (3x3) and D_y (3x3) of one contact
+__device__ __forceinline__ void lin_mats(const ContactLin &L, float DC[9], float Dy[9]) {
+  DC[0] = L.cn; DC[1] = 0.f; DC[2] = 0.f;
+  DC[3] = 0.f; DC[4] = L.Ct[0]; DC[5] = L.Ct[1];
+  DC[6] = 0.f; DC[7] = L.Ct[2]; DC[8] = L.Ct[3];
+  Dy[0] = L.dn; Dy[1] = 0.f; Dy[2] = 0.f;
+  Dy[3] = L.dtn[0]; Dy[4] = L.Dtt[0]; Dy[5] = L.Dtt[1];
+  Dy[6] = L.dtn[1]; Dy[7] = L.Dtt[2]; Dy[8] = L.Dtt[3];
 }
 
-__global__ void __launch_bounds__(256) k_ncp(GroupView G, EnvView V, StepArgs a, int tc) {
+// gamma^k = gamma^{k-1} + m dy (normal clamped at h^2 maxforce); returns J^T dgamma
+__device__ __forceinline__ V3 apply_update(const ContactLin &L, float mv, float gmax, const float *dy, float *g) {
+  float dgn = mv * dy[0], dg1 = mv * dy[1], dg2 = mv * dy[2];
+  const float gn_old = g[0];
+  const float gn = fminf(gn_old + dgn, gmax);
+  dgn = gn - gn_old;
+  const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3] + dg1;
+  const float y2 = L.R[6] * g[1] + L.R[7] * g[2] + L.R[8] * g[3] + dg2;
+  g[0] = gn;
+  g[1] = L.R[3] * y1 + L.R[6] * y2;
+  g[2] = L.R[4] * y1 + L.R[7] * y2;
+  g[3] = L.R[5] * y1 + L.R[8] * y2;
+  return v3(L.R[0] * dgn + L.R[3] * dg1 + L.R[6] * dg2, L.R[1] * dgn + L.R[4] * dg1 + L.R[7] * dg2,
+            L.R[2] * dgn + L.R[5] * dg1 + L.R[8] * dg2);
+}
+
+// Two contacts on one vertex (e.g. a cloth point squeezed between a finger and
+// the ground): 6x6 lite block solved by block elimination in registers,
+//   S = Z22 - Z21 Z11^-1 Z12,  x2 = S^-1 (b2 - Z21 Z11^-1 b1),  x1 = Z11^-1 (b1 - Z12 x2)
+// where Z11, Z22 are the single-contact blocks (normal row, then 2x2 tangential).
+__device__ __forceinline__ void solve_single_block(const ContactLin &L, const float b[3], float x[3]) {
+  x[0] = b[0] / (L.cn + L.dn + kDamp);
+  const float b1 = b[1] - L.dtn[0] * x[0], b2 = b[2] - L.dtn[1] * x[0];
+  const float m00 = L.Ct[0] + L.Dtt[0] + kDamp, m01 = L.Ct[1] + L.Dtt[1];
+  const float m10 = L.Ct[2] + L.Dtt[2], m11 = L.Ct[3] + L.Dtt[3] + kDamp;
+  const float inv = 1.f / (m00 * m11 - m01 * m10);
+  x[1] = (m11 * b1 - m01 * b2) * inv;
+  x[2] = (m00 * b2 - m10 * b1) * inv;
+}
+
+__device__ __forceinline__ void dc_times(const ContactLin &L, const float v[3], float out[3]) {
+  out[0] = L.cn * v[0];
+  out[1] = L.Ct[0] * v[1] + L.Ct[1] * v[2];
+  out[2] = L.Ct[2] * v[1] + L.Ct[3] * v[2];
+}
+
+__device__ __noinline__ V3 solve_two(const ObsShared &O, const StepArgs &a, float mu, float mv, V3 x, V3 xt, V3 du,
+                                     const int *cobs, float *gam) {
+  ContactLin L1, L2;
+  lin_at(O, cobs[0], a, mu, mv, x, xt, gam, L1);
+  lin_at(O, cobs[1], a, mu, mv, x, xt, gam + 4, L2);
+  float RR12[9];   // R1 R2^T
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++)
+      RR12[3 * r + c] = L1.R[3 * r] * L2.R[3 * c] + L1.R[3 * r + 1] * L2.R[3 * c + 1] + L1.R[3 * r + 2] * L2.R[3 * c + 2];
+  float b1[3], b2[3], t[3];
+  {
+    const float r1[3] = {L1.R[0] * du.x + L1.R[1] * du.y + L1.R[2] * du.z, L1.R[3] * du.x + L1.R[4] * du.y + L1.R[5] * du.z,
+                         L1.R[6] * du.x + L1.R[7] * du.y + L1.R[8] * du.z};
+    const float r2[3] = {L2.R[0] * du.x + L2.R[1] * du.y + L2.R[2] * du.z, L2.R[3] * du.x + L2.R[4] * du.y + L2.R[5] * du.z,
+                         L2.R[6] * du.x + L2.R[7] * du.y + L2.R[8] * du.z};
+    dc_times(L1, r1, t);
+    for (int i = 0; i < 3; i++) b1[i] = -L1.phi[i] - t[i];
+    dc_times(L2, r2, t);
+    for (int i = 0; i < 3; i++) b2[i] = -L2.phi[i] - t[i];
+  }
+  // Z12 = D_C1 R1 R2^T, Z21 = D_C2 R2 R1^T; X = Z11^-1 Z12 (column by column)
+  float X[9], S[9];
+  for (int c = 0; c < 3; c++) {
+    const float col[3] = {RR12[c], RR12[3 + c], RR12[6 + c]};
+    float z[3], xx[3];
+    dc_times(L1, col, z);
+    solve_single_block(L1, z, xx);
+    X[c] = xx[0]; X[3 + c] = xx[1]; X[6 + c] = xx[2];
+  }
+  // S = Z22 - Z21 X, with Z22 = D_C2 + D_y2 + damp I
+  for (int c = 0; c < 3; c++) {
+    // (R2 R1^T) X[:, c]
+    float v[3];
+    for (int r = 0; r < 3; r++) v[r] = RR12[r] * X[c] + RR12[3 + r] * X[3 + c] + RR12[6 + r] * X[6 + c];
+    float z[3];
+    dc_times(L2, v, z);
+    for (int r = 0; r < 3; r++) S[3 * r + c] = -z[r];
+  }
+  S[0] += L2.cn + L2.dn + kDamp;
+  S[3] += L2.dtn[0]; S[4] += L2.Ct[0] + L2.Dtt[0] + kDamp; S[5] += L2.Ct[1] + L2.Dtt[1];
+  S[6] += L2.dtn[1]; S[7] += L2.Ct[2] + L2.Dtt[2]; S[8] += L2.Ct[3] + L2.Dtt[3] + kDamp;
+  // rhs2 = b2 - Z21 Z11^-1 b1
+  float y1[3];
+  solve_single_block(L1, b1, y1);
+  {
+    float v[3], z[3];
+    for (int r = 0; r < 3; r++) v[r] = RR12[r] * y1[0] + RR12[3 + r] * y1[1] + RR12[6 + r] * y1[2];
+    dc_times(L2, v, z);
+    for (int r = 0; r < 3; r++) b2[r] -= z[r];
+  }
+  // x2 = S^-1 rhs2 (adjugate)
+  const float c00 = S[4] * S[8] - S[5] * S[7], c01 = S[5] * S[6] - S[3] * S[8], c02 = S[3] * S[7] - S[4] * S[6];
+  const float det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+  const float id = 1.f / det;
+  float x2[3];
+  x2[0] = (c00 * b2[0] + (S[2] * S[7] - S[1] * S[8]) * b2[1] + (S[1] * S[5] - S[2] * S[4]) * b2[2]) * id;
+  x2[1] = (c01 * b2[0] + (S[0] * S[8] - S[2] * S[6]) * b2[1] + (S[2] * S[3] - S[0] * S[5]) * b2[2]) * id;
+  x2[2] = (c02 * b2[0] + (S[1] * S[6] - S[0] * S[7]) * b2[1] + (S[0] * S[4] - S[1] * S[3]) * b2[2]) * id;
+  // x1 = Z11^-1 (b1 - Z12 x2)
+  {
+    float v[3], z[3];
+    for (int r = 0; r < 3; r++) v[r] = RR12[3 * r] * x2[0] + RR12[3 * r + 1] * x2[1] + RR12[3 * r + 2] * x2[2];
+    dc_times(L1, v, z);
+    for (int r = 0; r < 3; r++) b1[r] -= z[r];
+  }
+  float x1[3];
+  solve_single_block(L1, b1, x1);
+  return apply_update(L1, mv, a.gmax, x1, gam) + apply_update(L2, mv, a.gmax, x2, gam + 4);
+}
+
+// several contacts on one vertex: dense (3c x 3c) block of the lite metric,
+// kept out of line so the common single-contact path stays in registers
+__device__ __noinline__ V3 solve_multi(const ObsShared &O, const StepArgs &a, float mu, float mv, V3 x, V3 xt, V3 du,
+                                       int c, const int *cobs, float *gam) {
+  ContactLin Ls[kMaxPerVertex];
+  for (int aa = 0; aa < c; aa++) lin_at(O, cobs[aa], a, mu, mv, x, xt, gam + 4 * aa, Ls[aa]);
+  const int N3 = 3 * c;
+  float Z[12 * 12], rhs[12];
+  for (int aa = 0; aa < c; aa++) {
+    float DC[9], Dy[9];
+    lin_mats(Ls[aa], DC, Dy);
+    const float *Ra = Ls[aa].R;
+    float Rdu[3] = {Ra[0] * du.x + Ra[1] * du.y + Ra[2] * du.z, Ra[3] * du.x + Ra[4] * du.y + Ra[5] * du.z,
+                    Ra[6] * du.x + Ra[7] * du.y + Ra[8] * du.z};
+    for (int r = 0; r < 3; r++)
+      rhs[3 * aa + r] = -Ls[aa].phi[r] - (DC[3 * r] * Rdu[0] + DC[3 * r + 1] * Rdu[1] + DC[3 * r + 2] * Rdu[2]);
+    for (int bb = 0; bb < c; bb++) {
+      const float *Rb = Ls[bb].R;
+      float RR[9];
+      for (int r = 0; r < 3; r++)
+        for (int cc = 0; cc < 3; cc++)
+          RR[3 * r + cc] = Ra[3 * r] * Rb[3 * cc] + Ra[3 * r + 1] * Rb[3 * cc + 1] + Ra[3 * r + 2] * Rb[3 * cc + 2];
+      for (int r = 0; r < 3; r++)
+        for (int cc = 0; cc < 3; cc++) {
+          float sum = DC[3 * r] * RR[cc] + DC[3 * r + 1] * RR[3 + cc] + DC[3 * r + 2] * RR[6 + cc];
+          if (aa == bb) sum += Dy[3 * r + cc] + (r == cc ? kDamp : 0.f);
+          Z[(3 * aa + r) * N3 + 3 * bb + cc] = sum;
+        }
+    }
+  }
+  solve_dense(N3, Z, rhs);
+  V3 fsum = v3(0.f, 0.f, 0.f);
+  for (int aa = 0; aa < c; aa++) fsum = fsum + apply_update(Ls[aa], mv, a.gmax, rhs + 3 * aa, gam + 4 * aa);
+  return fsum;
+}
+
+__global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs a, int tc) {
   extern __shared__ float fs[];   // [3][n] contact force (tc path)
-  __shared__ float sh_red[32];
+  __shared__ float sh3[32][3];
+  __shared__ ObsShared O;
   const int l = blockIdx.x, e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   if (V.done[e]) return;
   const int cnt = G.ccount[l];
-  const int *cvert = G.cvert + (size_t)l * G.cap;
+  const int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
   float *gam = G.cgam + (size_t)l * G.cap * 4;
-  const float *lin = G.clin + (size_t)l * G.cap * kLin;
-  const float *q = G.q + (size_t)l * 3 * np, *w = G.w + (size_t)l * 3 * np;
+  const float *q = G.q + (size_t)l * 3 * np, *w = G.w + (size_t)l * 3 * np, *qt = G.qt + (size_t)l * 3 * np;
   float *f = G.f + (size_t)l * 3 * np;
+  const float mu = V.mu[e];
+  load_obstacles(V, e, a.K, O);
   if (tc)
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) fs[i] = 0.f;
   __syncthreads();
+  float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    if (j > 0 && cvert[j - 1] == cvert[j]) continue;
     const int vtx = cvert[j];
+    if (j > 0 && cvert[j - 1] == vtx) continue;
     int c = 1;
     while (j + c < cnt && cvert[j + c] == vtx) c++;
     if (c > kMaxPerVertex) {
       atomicOr(V.status, 1 << 10);
       c = kMaxPerVertex;
     }
-    const float mv = G.mass[vtx];
-    const V3 du = {w[vtx], w[np + vtx], w[2 * np + vtx]};  // u - q^{k-1} = A^-1 r
-    const int N3 = 3 * c;
-    float Z[12 * 12], rhs[12];
-    for (int aa = 0; aa < c; aa++) {
-      const float *La = lin + (size_t)(j + aa) * kLin;
-      float DC[9], Dy[9];
-      lin_mats(La, DC, Dy);
-      float Rdu[3] = {La[0] * du.x + La[1] * du.y + La[2] * du.z, La[3] * du.x + La[4] * du.y + La[5] * du.z,
-                      La[6] * du.x + La[7] * du.y + La[8] * du.z};
-      for (int r = 0; r < 3; r++)
-        rhs[3 * aa + r] = -La[9 + r] - (DC[3 * r] * Rdu[0] + DC[3 * r + 1] * Rdu[1] + DC[3 * r + 2] * Rdu[2]);
-      for (int bb = 0; bb < c; bb++) {
-        const float *Lb = lin + (size_t)(j + bb) * kLin;
-        float RR[9];
-        for (int r = 0; r < 3; r++)
-          for (int cc = 0; cc < 3; cc++)
-            RR[3 * r + cc] = La[3 * r] * Lb[3 * cc] + La[3 * r + 1] * Lb[3 * cc + 1] + La[3 * r + 2] * Lb[3 * cc + 2];
-        for (int r = 0; r < 3; r++)
-          for (int cc = 0; cc < 3; cc++) {
-            float s = DC[3 * r] * RR[cc] + DC[3 * r + 1] * RR[3 + cc] + DC[3 * r + 2] * RR[6 + cc];
-            if (aa == bb) s += Dy[3 * r + cc] + (r == cc ? kDamp : 0.f);
-            Z[(3 * aa + r) * N3 + 3 * bb + cc] = s;
-          }
-      }
-    }
-    solve_dense(N3, Z, rhs);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int aa = 0; aa < c; aa++) {
-      const float *La = lin + (size_t)(j + aa) * kLin;
-      float *g = gam + 4 * (j + aa);
-      float dgn = mv * rhs[3 * aa], dg1 = mv * rhs[3 * aa + 1], dg2 = mv * rhs[3 * aa + 2];
-      float gn_old = g[0];
-      float gn = fminf(gn_old + dgn, a.gmax);
-      dgn = gn - gn_old;
-      float y1 = La[3] * g[1] + La[4] * g[2] + La[5] * g[3] + dg1;
-      float y2 = La[6] * g[1] + La[7] * g[2] + La[8] * g[3] + dg2;
-      g[0] = gn;
-      g[1] = La[3] * y1 + La[6] * y2;
-      g[2] = La[4] * y1 + La[7] * y2;
-      g[3] = La[5] * y1 + La[8] * y2;
-      // J^T dgamma in the frame of q^{k-1}; the tangential part of gamma^{k-1}
-      // was already projected onto that frame in the residual
-      fx += La[0] * dgn + La[3] * dg1 + La[6] * dg2;
-      fy += La[1] * dgn + La[4] * dg1 + La[7] * dg2;
-      fz += La[2] * dgn + La[5] * dg1 + La[8] * dg2;
-    }
-    if (tc) {
-      fs[vtx] = fx; fs[n + vtx] = fy; fs[2 * n + vtx] = fz;
+    const float mv = __ldg(G.mass + vtx);
+    const V3 x = v3(q[vtx], q[np + vtx], q[2 * np + vtx]);
+    const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
+    const V3 du = v3(w[vtx], w[np + vtx], w[2 * np + vtx]);   // u - q^{k-1} = A^-1 r
+    V3 fsum;
+    if (c == 1) {
+      // single contact: R R^T = I, Z = D_C + D_y + damp I is block lower
+      // triangular (normal row first, then the 2x2 tangential block)
+      ContactLin L;
+      float *g = gam + 4 * j;
+      lin_at(O, cobs[j], a, mu, mv, x, xt, g, L);
+      const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
+      const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
+      const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
+      float dy[3];
+      dy[0] = (-L.phi[0] - L.cn * Rdu0) / (L.cn + L.dn + kDamp);
+      const float b1 = -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2) - L.dtn[0] * dy[0];
+      const float b2 = -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2) - L.dtn[1] * dy[0];
+      const float m00 = L.Ct[0] + L.Dtt[0] + kDamp, m01 = L.Ct[1] + L.Dtt[1];
+      const float m10 = L.Ct[2] + L.Dtt[2], m11 = L.Ct[3] + L.Dtt[3] + kDamp;
+      const float inv = 1.f / (m00 * m11 - m01 * m10);
+      dy[1] = (m11 * b1 - m01 * b2) * inv;
+      dy[2] = (m00 * b2 - m10 * b1) * inv;
+      fsum = apply_update(L, mv, a.gmax, dy, g);
+    } else if (c == 2) {
+      fsum = solve_two(O, a, mu, mv, x, xt, du, cobs + j, gam + 4 * j);
     } else {
-      f[vtx] = fx; f[np + vtx] = fy; f[2 * np + vtx] = fz;
+      fsum = solve_multi(O, a, mu, mv, x, xt, du, c, cobs + j, gam + 4 * j);
+    }
+    fm0 = fmaxf(fm0, fabsf(fsum.x)); fm1 = fmaxf(fm1, fabsf(fsum.y)); fm2 = fmaxf(fm2, fabsf(fsum.z));
+    if (tc) {
+      fs[vtx] = fsum.x; fs[n + vtx] = fsum.y; fs[2 * n + vtx] = fsum.z;
+    } else {
+      f[vtx] = fsum.x; f[np + vtx] = fsum.y; f[2 * np + vtx] = fsum.z;
     }
   }
   if (tc) {
     __syncthreads();
-    write_split_columns(G, l, fs, sh_red);
+    // every nonzero row of fs was written by this block with its max tracked
+    write_split_columns(G, l, fs, sh3, false, fm0, fm1, fm2);
   }
 }
 
@@ -559,7 +726,7 @@ __global__ void k_rhs_io(int n, int np, const int *genv, const int64_t *voff, in
 }
 
 __global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
-  __shared__ float sh_red[32];
+  __shared__ float sh3[32][3];
   extern __shared__ float vals[];
   const int l = blockIdx.x, n = G.n, np = G.n_pad;
   for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -567,13 +734,15 @@ __global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
     vals[i] = src[(size_t)l * 3 * np + c * np + j];
   }
   __syncthreads();
-  write_split_columns(G, l, vals, sh_red);
+  write_split_columns(G, l, vals, sh3, true);
 }
 
 }  // namespace
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
@@ -587,7 +756,8 @@ cudaError_t launch_begin(const flash_scene *s, const Group &g, const StepArgs &a
 
 cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a, int k, int residual_only, int tc,
                          cudaStream_t st) {
-  k_local<<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc);
+  if (g.vpe == 3) k_local<3><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc);
+  else k_local<4><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc);
   return cudaGetLastError();
 }
 
