@@ -175,6 +175,21 @@ flash_status flash_profile_enable(flash_scene *s, int32_t enable);
 flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, int64_t *launches);
 int64_t flash_launch_count(const flash_scene *s);
 
+/* Allocation-free dense apply out = Ainv * rhs, for callers that must not
+ * call cudaMalloc: real-time control loops and plugin hosts that reserve all
+ * device memory up front, where an allocation can implicitly synchronise the
+ * device and stall the loop or exceed the host's memory budget.  The paper
+ * has no counterpart; it is the global solve's FP32 apply as a standalone
+ * call.  Ainv: device float32 [n][n] (e.g. the explicit inverse of a mesh's
+ * system matrix); rhs, out: device float32 [m][n][3], caller-owned.  Limits:
+ * n <= 512 vertices and m <= 256 environments per call; larger sizes return
+ * FLASH_EINVAL.  Scratch is a fixed 4 MiB __device__ array that every GPU
+ * loading the library holds until exit; the first call on a device looks up
+ * its address (make that first call before any stream capture).  Calls share
+ * the array: calls that overlap on the GPU race. */
+flash_status flash_dense_apply_noalloc(const float *Ainv, int32_t n, int32_t m, const float *rhs, float *out,
+                                       void *stream);
+
 const char *flash_last_error(void);
 
 #ifdef __cplusplus

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libflash.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "step_kernels.cu", "gemm_simt.cu", "gemm_tc.cu", "setup_kernels.cu", "mlp.cu"]
+SOURCES = ["api.cu", "step_kernels.cu", "gemm_simt.cu", "gemm_tc.cu", "setup_kernels.cu", "mlp.cu", "noalloc.cu"]
 
 
 def _nvcc():

@@ -141,6 +141,7 @@ cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float 
                       cudaStream_t st);
 cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st);
 bool tc_available();
+cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);
 
 // setup (setup_kernels.cu) ---------------------------------------------------
 cudaError_t invert_spd_f64(double *A, int n, int n_pad, int batch, cudaStream_t st);

@@ -95,4 +95,12 @@ cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float 
   return cudaGetLastError();
 }
 
+// Plain launch of the FP32 apply on caller-provided, already padded buffers
+// (A^-1 [n_pad][n_pad], B and C [cols rounded up to 128][n_pad]).
+cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st) {
+  dim3 grid((cols + BN - 1) / BN, n_pad / BM);
+  k_gemm_f32<<<grid, 256, 0, st>>>(Ainv, rhs, out, nullptr, nullptr, nullptr, n_pad, cols, 0);
+  return cudaGetLastError();
+}
+
 }  // namespace flash
