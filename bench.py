@@ -54,6 +54,30 @@ def dist_env():
     return rank, world, local
 
 
+def shard(n_total, rank, world):
+    """Environment range [lo, hi) owned by ``rank`` (contiguous, balanced)."""
+    lo = n_total * rank // world
+    hi = n_total * (rank + 1) // world
+    return lo, hi
+
+
+def aggregate(ms_local, envs_local, world, device):
+    """Whole-job env-steps/s from every rank's per-step time: the slowest
+    rank's time over the environments of all ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local), float(envs_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        m = t[:1].clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        n = t[1:].clone()
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms_max, envs = m.item(), n.item()
+    else:
+        ms_max, envs = t[0].item(), t[1].item()
+    return envs / ms_max * 1e3, ms_max
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
@@ -255,12 +279,8 @@ def main():
     prof = sim.profile_read()
     sim.profile(False)
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = ms_t.item()
+    value, ms_max = aggregate(ms, args.envs, world, dev)
     total_envs = args.envs * world
-    value = total_envs / ms_max * 1e3
     frac_conv = conv.item() / (args.envs * args.steps)
     mean_iters = it_sum.item() / (args.envs * args.steps)
     status = sim.status()
@@ -284,10 +304,8 @@ def main():
             q_h.copy_(q, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
-        ms_e2e = torch.tensor([e0.elapsed_time(e1) / args.steps], device=dev)
-        if world > 1:
-            dist.all_reduce(ms_e2e, op=dist.ReduceOp.MAX)
-        e2e = {"value": total_envs / ms_e2e.item() * 1e3, "unit": "env-steps/s",
+        v_e2e, _ = aggregate(e0.elapsed_time(e1) / args.steps, args.envs, world, dev)
+        e2e = {"value": v_e2e, "unit": "env-steps/s",
                "h2d_bytes_per_step": int(poses_h[0].numel() * 4), "d2h_bytes_per_step": int(q_h.numel() * 4)}
 
     # ---------------- roofline of the dominant kernel

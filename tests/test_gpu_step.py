@@ -119,3 +119,78 @@ def test_rest_stays_at_rest(cuda):
     qg, vg = gpu_step_from(sim, sc, 0, sc.q0, sc.v0, n=5)
     assert np.abs(qg - sc.q0).max() < 1e-6
     assert np.abs(vg).max() < 1e-4
+
+
+@pytest.mark.parametrize("solve", SOLVES)
+def test_tet_squeeze_one_step(cuda, solve):
+    """Soft tet blocks squeezed by the parallel gripper; per-environment
+    stiffness gives each environment its own system matrix (its own group)."""
+    sc = scenes.tet_squeeze(n_envs=3, steps=30)
+    s = 18
+    q, v, meshes = sc.q0.copy(), sc.v0.copy(), {}
+    for e in range(sc.n_envs):
+        meshes[e], st = oracle_state_at(sc, e, s)
+        q[e], v[e] = _f32(st.q), _f32(st.v)
+    sim = _sim(sc, solve=solve)
+    qg, _ = gpu_step_from(sim, sc, s, q, v)
+    for e in range(sc.n_envs):
+        ref = oracle.EnvState(q[e], v[e])
+        oracle.step(meshes[e], sc, e, s, ref)
+        err = np.abs(qg[e] - ref.q).max()
+        assert err <= POS_TOL, (e, err, len(ref.cvert))
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.35])
+def test_incline_coulomb_on_gpu(cuda, theta):
+    """Tolerance mode on the GPU: a particle on an incline sticks iff
+    tan(theta) <= mu and otherwise slides with x_n = a h^2 n(n+1)/2
+    (mu swept in steps of 0.002 around tan(theta))."""
+    from paper_2604_17513_gb300 import flash
+    t = np.tan(theta)
+    for dmu in (-0.004, -0.002, 0.002, 0.004):
+        mu = t + dmu
+        sc = scenes.incline_particle(theta, mu, steps=8)
+        sim = _sim(sc, mode=flash.MODE_TOL, k_cap=50, tol=1e-7)
+        qg, _ = gpu_step_from(sim, sc, 0, sc.q0, sc.v0, n=8)
+        disp = np.linalg.norm(qg[0, 0] - sc.q0[0, 0])
+        if mu >= t:
+            assert disp < 1e-6, (mu, disp)
+        else:
+            a = 9.81 * (np.sin(theta) - mu * np.cos(theta))
+            assert abs(disp - a * sc.h ** 2 * 36) < 2e-6, (mu, disp)
+        it, r = sim.stats()
+        assert r.max().item() <= 1e-7
+
+
+def _corner_particle():
+    """A particle pushed into the corner of three planes (x, y and z walls)."""
+    rest = np.zeros((1, 3))
+    tau = 1e-3
+    q0 = np.full((1, 1, 3), tau)
+    K = 3
+    poses = np.zeros((1, 4, K, 7))
+    # plane normals +z (identity), +x (rotate +z onto +x about y), +y (about x)
+    c = np.cos(np.pi / 4)
+    poses[0, :, 0] = (0, 0, 0, 1, 0, 0, 0)
+    poses[0, :, 1] = (0, 0, 0, c, 0, c, 0)
+    poses[0, :, 2] = (0, 0, 0, c, -c, 0, 0)
+    sc = scenes.Scene("corner", scenes.TRI, rest, np.zeros((0, 3), np.int32), np.array([0.01]), 0.0, 0.0, q0,
+                      np.zeros_like(q0), np.array([0.4]), np.ones(1),
+                      np.array([[scenes.PLANE] * 3], np.int32), np.zeros((1, K, 3)), np.zeros((1, K)), poses,
+                      thickness=tau, steps=3, gravity=(-3.0, -2.0, -9.81))
+    return sc
+
+
+def test_three_contacts_on_one_vertex(cuda):
+    """General per-vertex block (three contacts): GPU vs oracle, and the
+    particle stays in the corner."""
+    sc = _corner_particle()
+    mesh = oracle.Mesh.from_scene(sc)
+    ref = oracle.EnvState(sc.q0[0], sc.v0[0])
+    for s in range(3):
+        oracle.step(mesh, sc, 0, s, ref)
+    assert len(ref.cvert) == 3
+    sim = _sim(sc)
+    qg, _ = gpu_step_from(sim, sc, 0, sc.q0, sc.v0, n=3)
+    assert np.abs(qg[0] - ref.q).max() <= POS_TOL
+    assert np.abs(ref.q[0] - sc.q0[0, 0]).max() < 1e-4
