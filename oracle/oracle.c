@@ -539,7 +539,12 @@ static void linearize(int type, const double *dims, double comp, const double *p
   double rad = mu * (yn > 0 ? yn : 0);
   double d[2] = {yt[0] - s[0], yt[1] - s[1]};
   double dn = sqrt(d[0] * d[0] + d[1] * d[1]);
-  if (dn <= rad) { /* stick (ties included) */
+  if (rad == 0.0) {
+    /* cone of zero radius (no normal force): the proximal map is the zero
+     * map, phi_t = y_t whatever the slip */
+    L->phi[1] = yt[0]; L->phi[2] = yt[1];
+    L->Dy[4] = 1; L->Dy[8] = 1;
+  } else if (dn <= rad) { /* stick (ties included) */
     L->phi[1] = s[0]; L->phi[2] = s[1];
     L->DC[4] = 1; L->DC[8] = 1;
   } else {

@@ -242,7 +242,13 @@ __device__ __forceinline__ void linearize_contact(int type, const float *dims, f
   float rad = mu * fmaxf(yn, 0.f);
   float d0 = y0 - s0, d1 = y1 - s1;
   float dn = sqrtf(d0 * d0 + d1 * d1);
-  if (dn <= rad) {
+  if (rad == 0.f) {
+    // cone of zero radius (no normal force): proximal map is zero, phi_t = y_t
+    L.phi[1] = y0; L.phi[2] = y1;
+    L.Ct[0] = 0.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 0.f;
+    L.dtn[0] = 0.f; L.dtn[1] = 0.f;
+    L.Dtt[0] = 1.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 1.f;
+  } else if (dn <= rad) {
     L.phi[1] = s0; L.phi[2] = s1;
     L.Ct[0] = 1.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 1.f;
     L.dtn[0] = 0.f; L.dtn[1] = 0.f;
