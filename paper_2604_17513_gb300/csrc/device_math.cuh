@@ -204,6 +204,7 @@ __device__ __forceinline__ void closest_rot33(const float *F, float *R) {
 //                 Dy: dn, dtn(2), Dtt(2x2) (7)
 struct ContactLin {
   float R[9], phi[3], cn, Ct[4], dn, dtn[2], Dtt[4];
+  float gap;   // a = sd - tau at the linearisation point
 };
 
 __device__ __forceinline__ void linearize_contact(int type, const float *dims, float comp, const float *pose_t,
@@ -217,6 +218,7 @@ __device__ __forceinline__ void linearize_contact(int type, const float *dims, f
   L.R[6] = t2.x; L.R[7] = t2.y; L.R[8] = t2.z;
   float inv_m = 1.f / mv;
   float a = sd - tau;
+  L.gap = a;
   float yn = g[0] * inv_m;
   float alpha = comp * mv / (h * h);
   float ae = a + alpha * yn;

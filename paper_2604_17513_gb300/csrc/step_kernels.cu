@@ -445,6 +445,13 @@ __device__ void solve_dense(int N, float *A, float *b) {
   }
 }
 
+// A contact that is separated (gap > 0) and carries no force has D_C = 0 and
+// D_y = I, so its Newton row gives dy = 0 and it does not couple to the other
+// contacts of the vertex: it can be left out of the block exactly.
+__device__ __forceinline__ bool separated_free(const ContactLin &L, const float *g) {
+  return L.gap > 0.f && g[0] == 0.f && g[1] == 0.f && g[2] == 0.f && g[3] == 0.f;
+}
+
 // D_C (3x3) and D_y (3x3) of one contact
 __device__ __forceinline__ void lin_mats(const ContactLin &L, float DC[9], float Dy[9]) {
   DC[0] = L.cn; DC[1] = 0.f; DC[2] = 0.f;
@@ -491,11 +498,8 @@ __device__ __forceinline__ void dc_times(const ContactLin &L, const float v[3], 
   out[2] = L.Ct[2] * v[1] + L.Ct[3] * v[2];
 }
 
-__device__ __noinline__ V3 solve_two(const ObsShared &O, const StepArgs &a, float mu, float mv, V3 x, V3 xt, V3 du,
-                                     const int *cobs, float *gam) {
-  ContactLin L1, L2;
-  lin_at(O, cobs[0], a, mu, mv, x, xt, gam, L1);
-  lin_at(O, cobs[1], a, mu, mv, x, xt, gam + 4, L2);
+__device__ __noinline__ V3 solve_two(const ContactLin &L1, const ContactLin &L2, const StepArgs &a, float mv, V3 du,
+                                     float *g1, float *g2) {
   float RR12[9];   // R1 R2^T
   for (int r = 0; r < 3; r++)
     for (int c = 0; c < 3; c++)
@@ -558,15 +562,13 @@ __device__ __noinline__ V3 solve_two(const ObsShared &O, const StepArgs &a, floa
   }
   float x1[3];
   solve_single_block(L1, b1, x1);
-  return apply_update(L1, mv, a.gmax, x1, gam) + apply_update(L2, mv, a.gmax, x2, gam + 4);
+  return apply_update(L1, mv, a.gmax, x1, g1) + apply_update(L2, mv, a.gmax, x2, g2);
 }
 
 // several contacts on one vertex: dense (3c x 3c) block of the lite metric,
 // kept out of line so the common single-contact path stays in registers
-__device__ __noinline__ V3 solve_multi(const ObsShared &O, const StepArgs &a, float mu, float mv, V3 x, V3 xt, V3 du,
-                                       int c, const int *cobs, float *gam) {
-  ContactLin Ls[kMaxPerVertex];
-  for (int aa = 0; aa < c; aa++) lin_at(O, cobs[aa], a, mu, mv, x, xt, gam + 4 * aa, Ls[aa]);
+__device__ __noinline__ V3 solve_multi(const ContactLin *Ls, const StepArgs &a, float mv, V3 du, int c, float *gam,
+                                       const int *idx) {
   const int N3 = 3 * c;
   float Z[12 * 12], rhs[12];
   for (int aa = 0; aa < c; aa++) {
@@ -593,7 +595,7 @@ __device__ __noinline__ V3 solve_multi(const ObsShared &O, const StepArgs &a, fl
   }
   solve_dense(N3, Z, rhs);
   V3 fsum = v3(0.f, 0.f, 0.f);
-  for (int aa = 0; aa < c; aa++) fsum = fsum + apply_update(Ls[aa], mv, a.gmax, rhs + 3 * aa, gam + 4 * aa);
+  for (int aa = 0; aa < c; aa++) fsum = fsum + apply_update(Ls[aa], mv, a.gmax, rhs + 3 * aa, gam + 4 * idx[aa]);
   return fsum;
 }
 
@@ -628,30 +630,54 @@ __global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs
     const V3 x = v3(q[vtx], q[np + vtx], q[2 * np + vtx]);
     const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
     const V3 du = v3(w[vtx], w[np + vtx], w[2 * np + vtx]);   // u - q^{k-1} = A^-1 r
-    V3 fsum;
+    V3 fsum = v3(0.f, 0.f, 0.f);
     if (c == 1) {
       // single contact: R R^T = I, Z = D_C + D_y + damp I is block lower
       // triangular (normal row first, then the 2x2 tangential block)
       ContactLin L;
       float *g = gam + 4 * j;
       lin_at(O, cobs[j], a, mu, mv, x, xt, g, L);
-      const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
-      const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
-      const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
-      float dy[3];
-      dy[0] = (-L.phi[0] - L.cn * Rdu0) / (L.cn + L.dn + kDamp);
-      const float b1 = -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2) - L.dtn[0] * dy[0];
-      const float b2 = -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2) - L.dtn[1] * dy[0];
-      const float m00 = L.Ct[0] + L.Dtt[0] + kDamp, m01 = L.Ct[1] + L.Dtt[1];
-      const float m10 = L.Ct[2] + L.Dtt[2], m11 = L.Ct[3] + L.Dtt[3] + kDamp;
-      const float inv = 1.f / (m00 * m11 - m01 * m10);
-      dy[1] = (m11 * b1 - m01 * b2) * inv;
-      dy[2] = (m00 * b2 - m10 * b1) * inv;
-      fsum = apply_update(L, mv, a.gmax, dy, g);
-    } else if (c == 2) {
-      fsum = solve_two(O, a, mu, mv, x, xt, du, cobs + j, gam + 4 * j);
+      if (!separated_free(L, g)) {
+        const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
+        const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
+        const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
+        float dy[3];
+        dy[0] = (-L.phi[0] - L.cn * Rdu0) / (L.cn + L.dn + kDamp);
+        const float b1 = -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2) - L.dtn[0] * dy[0];
+        const float b2 = -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2) - L.dtn[1] * dy[0];
+        const float m00 = L.Ct[0] + L.Dtt[0] + kDamp, m01 = L.Ct[1] + L.Dtt[1];
+        const float m10 = L.Ct[2] + L.Dtt[2], m11 = L.Ct[3] + L.Dtt[3] + kDamp;
+        const float inv = 1.f / (m00 * m11 - m01 * m10);
+        dy[1] = (m11 * b1 - m01 * b2) * inv;
+        dy[2] = (m00 * b2 - m10 * b1) * inv;
+        fsum = apply_update(L, mv, a.gmax, dy, g);
+      }
     } else {
-      fsum = solve_multi(O, a, mu, mv, x, xt, du, c, cobs + j, gam + 4 * j);
+      // several contacts: linearise all, keep those that are not separated
+      // and force-free (those have dy = 0 exactly and do not couple)
+      ContactLin Ls[kMaxPerVertex];
+      int idx[kMaxPerVertex];
+      int na = 0;
+      for (int aa = 0; aa < c; aa++) {
+        lin_at(O, cobs[j + aa], a, mu, mv, x, xt, gam + 4 * (j + aa), Ls[na]);
+        if (!separated_free(Ls[na], gam + 4 * (j + aa))) idx[na++] = j + aa;
+      }
+      if (na == 1) {
+        const ContactLin &L = Ls[0];
+        float *g = gam + 4 * idx[0];
+        const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
+        const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
+        const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
+        float b[3] = {-L.phi[0] - L.cn * Rdu0, -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2),
+                      -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2)};
+        float dy[3];
+        solve_single_block(L, b, dy);
+        fsum = apply_update(L, mv, a.gmax, dy, g);
+      } else if (na == 2) {
+        fsum = solve_two(Ls[0], Ls[1], a, mv, du, gam + 4 * idx[0], gam + 4 * idx[1]);
+      } else if (na > 2) {
+        fsum = solve_multi(Ls, a, mv, du, na, gam, idx);
+      }
     }
     fm0 = fmaxf(fm0, fabsf(fsum.x)); fm1 = fmaxf(fm1, fabsf(fsum.y)); fm2 = fmaxf(fm2, fabsf(fsum.z));
     if (tc) {
