@@ -161,7 +161,8 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
 /* Kernel accounting for measurement.  Kinds: 0 begin-of-step (detection,
  * prediction), 1 local step + residual, 2 global solve (dense apply), 3 NCP
  * blocks, 4 end-of-step.  flash_profile_enable(s, 1) brackets every launch
- * with CUDA events on the launching stream; flash_profile_read synchronises
+ * with CUDA events on the launching stream, 5 the learned warm start;
+ * flash_profile_read synchronises
  * and returns the summed device time (ms) and launch count of one kind since
  * the last enable.  flash_launch_count returns the number of kernels this
  * scene has launched since creation. */
@@ -170,10 +171,49 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
 #define FLASH_KIND_SOLVE 2
 #define FLASH_KIND_NCP 3
 #define FLASH_KIND_END 4
-#define FLASH_NUM_KINDS 5
+#define FLASH_KIND_WARM 5 /* learned warm start: features, network, apply */
+#define FLASH_NUM_KINDS 6
 flash_status flash_profile_enable(flash_scene *s, int32_t enable);
 flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, int64_t *launches);
 int64_t flash_launch_count(const flash_scene *s);
+
+/* Learned warm start (the paper has no learned component; the network
+ * predicts the initial multipliers gamma^0 and the first iterate at each
+ * contact vertex from per-contact features).  Network: 10 -> 128 -> 128 -> 6
+ * perceptron with ReLU, flat float32 parameters W1[128][10] b1[128]
+ * W2[128][128] b2[128] W3[6][128] b3[6]; weights are rounded to bf16 when
+ * used, products accumulate in FP32.  Features per contact (frame n, t1, t2
+ * and gap at the predicted position q~): gap [mm], relative velocity in the
+ * frame [0.1 m/s], n, previous step's multipliers y = gamma/m_v in the frame
+ * [mm].  Outputs: y^0 in the frame [mm] (normal part clamped at 0) and
+ * q^0 - q~ at the vertex [mm].
+ *
+ * flash_warmstart_set: mode = FLASH_WARM_*; params (device, copied) are
+ * required for FLASH_WARM_LEARNED; flags (use_dq): bit 0 also moves contact
+ * vertices to the predicted first iterate, bit 1 keeps only the normal
+ * multiplier.  Contacts whose features exceed 100 in magnitude (outside the
+ * trained range) start cold.
+ * flash_record_contacts: while enabled every step stores features (at the
+ * start) and targets (converged multipliers and q - q~, same units) of all
+ * contacts; flash_get_recorded copies the last step's rows (environments in
+ * group order) into device X [rows][10] and T [rows][6], synchronising.
+ * Targets of environments whose final residual exceeds tol_ncp are NaN. */
+flash_status flash_warmstart_set(flash_scene *s, const float *params, int32_t mode, int32_t use_dq);
+flash_status flash_record_contacts(flash_scene *s, int32_t enable);
+flash_status flash_get_recorded(flash_scene *s, float *X, float *T, int64_t max_rows, int64_t *rows, void *stream);
+
+/* Network kernels used for inference and training (device pointers).
+ * flash_mlp_loss_grad: grad = d/dparams of (1/rows) sum_b 0.5 |f(x_b) - t_b|^2,
+ * loss = sum_b |f(x_b) - t_b|^2 (device scalar); work needs
+ * flash_mlp_work_floats(rows) floats.  flash_mlp_adam: one Adam step
+ * (beta 0.9, 0.999, eps 1e-8) of the master weights, step counted from 1. */
+int32_t flash_mlp_num_params(void);
+flash_status flash_mlp_forward(const float *params, const float *x, float *y, int64_t rows, void *stream);
+flash_status flash_mlp_loss_grad(const float *params, const float *x, const float *t, int32_t rows, float *grad,
+                                 float *loss, float *work, void *stream);
+int64_t flash_mlp_work_floats(int32_t rows);
+flash_status flash_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
+                            void *stream);
 
 /* Allocation-free dense apply out = Ainv * rhs, for callers that must not
  * call cudaMalloc: real-time control loops and plugin hosts that reserve all

@@ -281,6 +281,19 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   return FLASH_OK;
 }
 
+cudaError_t ensure_learn_buffers(flash_scene *s) {
+  for (auto &g : s->groups) {
+    if (g.row_off) continue;
+    size_t rows = (size_t)g.N * s->cap;
+    cudaError_t e = dalloc(s, &g.row_off, (size_t)g.N + 1);
+    if (e != cudaSuccess) return e;
+    if ((e = dalloc(s, &g.feat, rows * 10)) != cudaSuccess) return e;
+    if ((e = dalloc(s, &g.pred, rows * 6)) != cudaSuccess) return e;
+    if ((e = dalloc(s, &g.targ, rows * 6)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 StepArgs step_args(const flash_scene *s) {
   StepArgs a;
   a.h = (float)s->d.h;
@@ -543,13 +556,27 @@ flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_
 flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
   if (n_steps < 0) return fail(FLASH_EINVAL, "negative step count");
-  if (s->d.warm == FLASH_WARM_LEARNED) return fail(FLASH_ENOTIMPL, "learned warm start needs weights");
+  const bool learned = s->d.warm == FLASH_WARM_LEARNED;
+  if (learned && !s->mlp_params) return fail(FLASH_ESTATE, "learned warm start needs weights (flash_warmstart_set)");
   cudaStream_t st = (cudaStream_t)stream;
   const StepArgs a = step_args(s);
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
   for (int step = 0; step < n_steps; step++) {
     for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, g, a, st); }));
+    if (learned || s->record) {
+      for (auto &g : s->groups) {
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_row_offsets(g, g.row_off, st); }));
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_features(s, g, a, g.row_off, g.feat, st); }));
+        if (learned) {
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] {
+            return mlp_forward(s->mlp_params, g.feat, g.pred, g.row_off + g.N, (int64_t)g.N * s->cap, st);
+          }));
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st,
+                               [&] { return launch_apply_learned(s, g, a, g.row_off, g.feat, g.pred, s->use_dq, st); }));
+        }
+      }
+    }
     if (s->d.mode == FLASH_MODE_FIXED) {
       for (int k = 1; k <= s->d.k_max; k++)
         for (auto &g : s->groups) {
@@ -569,9 +596,55 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
         for (auto &g : s->groups) FLASH_CUDA_TRY(global_solves(s, g, a, st));
       }
     }
+    if (s->record)
+      for (auto &g : s->groups)
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, a, g.row_off, g.targ, st); }));
     for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, g, a, st); }));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
   }
+  return FLASH_OK;
+}
+
+flash_status flash_warmstart_set(flash_scene *s, const float *params, int32_t mode, int32_t use_dq) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (mode < FLASH_WARM_COLD || mode > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm-start mode");
+  if (params) {
+    if (!s->mlp_params) FLASH_CUDA_TRY(dalloc(s, &s->mlp_params, (size_t)mlp_num_params()));
+    FLASH_CUDA_TRY(cudaMemcpy(s->mlp_params, params, sizeof(float) * mlp_num_params(), cudaMemcpyDeviceToDevice));
+  }
+  if (mode == FLASH_WARM_LEARNED) {
+    if (!s->mlp_params) return fail(FLASH_EINVAL, "learned warm start needs parameters");
+    FLASH_CUDA_TRY(ensure_learn_buffers(s));
+  }
+  s->d.warm = mode;
+  s->use_dq = use_dq;
+  return FLASH_OK;
+}
+
+flash_status flash_record_contacts(flash_scene *s, int32_t enable) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (enable) FLASH_CUDA_TRY(ensure_learn_buffers(s));
+  s->record = enable != 0;
+  return FLASH_OK;
+}
+
+flash_status flash_get_recorded(flash_scene *s, float *X, float *T, int64_t max_rows, int64_t *rows, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (!s->groups.front().row_off) return fail(FLASH_ESTATE, "recording was never enabled");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t pos = 0;
+  for (auto &g : s->groups) {
+    int64_t n = 0;
+    FLASH_CUDA_TRY(cudaMemcpyAsync(&n, g.row_off + g.N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t take = std::max<int64_t>(0, std::min(n, max_rows - pos));
+    if (take > 0) {
+      if (X) FLASH_CUDA_TRY(cudaMemcpyAsync(X + pos * 10, g.feat, sizeof(float) * 10 * take, cudaMemcpyDeviceToDevice, st));
+      if (T) FLASH_CUDA_TRY(cudaMemcpyAsync(T + pos * 6, g.targ, sizeof(float) * 6 * take, cudaMemcpyDeviceToDevice, st));
+    }
+    pos += n;
+  }
+  if (rows) *rows = pos;
   return FLASH_OK;
 }
 

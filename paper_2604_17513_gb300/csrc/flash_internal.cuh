@@ -68,6 +68,9 @@ struct Group {
   bool p_in_smem = true;
   float *pscratch = nullptr;              // element projections when they do not fit in smem
   int *status = nullptr;                  // scene status word (device)
+  // learned warm start / recording (allocated on first use)
+  int64_t *row_off = nullptr;             // [N + 1] compact contact rows
+  float *feat = nullptr, *pred = nullptr, *targ = nullptr;   // [N * cap][10|6|6]
 };
 
 }  // namespace flash
@@ -100,6 +103,9 @@ struct flash_scene {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<int> ev_kind;   // kind of each recorded pair
+  float *mlp_params = nullptr;   // warm-start network (device, flat)
+  int use_dq = 0;
+  bool record = false;
   double prof_ms[FLASH_NUM_KINDS] = {0};
   int64_t prof_n[FLASH_NUM_KINDS] = {0};
 };
@@ -128,6 +134,16 @@ cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a
                          int tc, cudaStream_t st);
 cudaError_t launch_ncp(const flash_scene *s, const Group &g, const StepArgs &a, int tc, cudaStream_t st);
 cudaError_t launch_end(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_row_offsets(const Group &g, int64_t *off, cudaStream_t st);
+cudaError_t launch_features(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *X,
+                            cudaStream_t st);
+cudaError_t launch_apply_learned(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off,
+                                 const float *X, const float *Y, int flags, cudaStream_t st);
+cudaError_t launch_targets(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *T,
+                           cudaStream_t st);
+int mlp_num_params();
+cudaError_t mlp_forward(const float *params, const float *X, float *Y, const int64_t *n_rows_dev, int64_t max_rows,
+                        cudaStream_t st);
 cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q_user, const float *v_user,
                             float *q_out, float *v_out, int to_user, cudaStream_t st);
 cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,

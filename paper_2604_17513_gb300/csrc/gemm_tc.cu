@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(128, 1)
   const int KB = n_pad / BK;
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
-  // skip tiles whose environments have all converged (mode 1 writes nothing then)
-  if (mode == 1) {
+  // skip tiles whose environments have all converged (their columns are
+  // never read again in this step)
+  {
     int live = 0;
     for (int c = j0 + threadIdx.x; c < min(j0 + BN, cols); c += blockDim.x) live |= !done[genv[c / 3]];
     if (!__syncthreads_or(live)) return;

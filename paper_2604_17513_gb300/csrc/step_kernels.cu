@@ -763,6 +763,150 @@ __global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
   write_split_columns(G, l, vals, sh3, true);
 }
 
+// ---------------------------------------------------------------------------
+// learned warm start: per-contact features, prediction, training targets
+// ---------------------------------------------------------------------------
+// Feature / output scales: gaps and scaled multipliers y = gamma / m_v in
+// millimetres, velocities in units of 0.1 m/s.
+constexpr float kFeatLen = 1e3f, kFeatVel = 10.f;
+constexpr float kFeatClip = 100.f;      // trained input range (|feature| <= clip)
+constexpr int kWarmDq = 1, kWarmNormalOnly = 2;
+
+__global__ void k_row_offsets(const int *count, int N, int64_t *off) {
+  __shared__ int sh[32];
+  int64_t base = 0;
+  for (int i0 = 0; i0 < N; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const int c = i < N ? count[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(c, &total, sh);
+    if (i < N) off[i] = base + ex;
+    base += total;
+  }
+  if (threadIdx.x == 0) off[N] = base;
+}
+
+// frame (n, t1, t2) and gap of a contact at the predicted position
+__device__ __forceinline__ void contact_frame_at(const ObsShared &O, int o, float tau, V3 x, V3 &n, V3 &t1, V3 &t2,
+                                                 float &gap) {
+  gap = obstacle_sdf(O.type[o], O.dims[o], O.pose[o], x, n) - tau;
+  tangent_basis(n, t1, t2);
+}
+
+__global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepArgs a, const int64_t *off, float *X) {
+  __shared__ ObsShared O;
+  const int l = blockIdx.x, e = G.genv[l];
+  const int np = G.n_pad;
+  load_obstacles(V, e, a.K, O);
+  __syncthreads();
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
+  const float *qp = G.qp + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
+  const int pc = G.pcount[l];
+  const int *pv = G.pvert + (size_t)l * G.cap, *po = G.pobs + (size_t)l * G.cap;
+  const float *pg = G.pgam + (size_t)l * G.cap * 4;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int vtx = cvert[j], o = cobs[j];
+    const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
+    V3 n, t1, t2;
+    float gap;
+    contact_frame_at(O, o, a.tau, x, n, t1, t2, gap);
+    // obstacle velocity at the point over the step
+    const float *pt = O.poset[o], *pth = O.pose[o];
+    const V3 pb = qrot(pth + 3, x - v3(pth[0], pth[1], pth[2]), true);
+    const V3 xo = qrot(pt + 3, pb, false) + v3(pt[0], pt[1], pt[2]);
+    const V3 vr = v3(v[vtx], v[np + vtx], v[2 * np + vtx]) - (1.f / a.h) * (x - xo);
+    // previous step's multipliers of the same (vertex, obstacle)
+    float g4[4] = {0.f, 0.f, 0.f, 0.f};
+    const int key = vtx * FLASH_MAX_OBS + o;
+    int lo = 0, hi = pc - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int km = pv[mid] * FLASH_MAX_OBS + po[mid];
+      if (km == key) {
+        for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
+        break;
+      }
+      if (km < key) lo = mid + 1; else hi = mid - 1;
+    }
+    const float s = kFeatLen / __ldg(G.mass + vtx);
+    const V3 gt = v3(g4[1], g4[2], g4[3]);
+    float *xr = X + (off[l] + j) * 10;
+    xr[0] = gap * kFeatLen;
+    xr[1] = dot(n, vr) * kFeatVel; xr[2] = dot(t1, vr) * kFeatVel; xr[3] = dot(t2, vr) * kFeatVel;
+    xr[4] = n.x; xr[5] = n.y; xr[6] = n.z;
+    xr[7] = g4[0] * s; xr[8] = dot(t1, gt) * s; xr[9] = dot(t2, gt) * s;
+  }
+}
+
+// gamma^0 (and optionally q^0 at contact vertices) from the network output
+__global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, StepArgs a, const int64_t *off,
+                                                       const float *X, const float *Y, int flags) {
+  __shared__ ObsShared O;
+  const int l = blockIdx.x, e = G.genv[l];
+  const int np = G.n_pad;
+  load_obstacles(V, e, a.K, O);
+  __syncthreads();
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
+  float *qp = G.qp + (size_t)l * 3 * np, *q = G.q + (size_t)l * 3 * np;
+  float *gam = G.cgam + (size_t)l * G.cap * 4;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int vtx = cvert[j], o = cobs[j];
+    const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
+    V3 n, t1, t2;
+    float gap;
+    contact_frame_at(O, o, a.tau, x, n, t1, t2, gap);
+    const float *y = Y + (off[l] + j) * 6;
+    // contacts whose features lie outside the trained range start cold
+    const float *xr = X + (off[l] + j) * 10;
+    bool in_range = true;
+    for (int c = 0; c < 10; c++) in_range = in_range && fabsf(xr[c]) <= kFeatClip;
+    if (!in_range) continue;
+    const float mv = __ldg(G.mass + vtx) / kFeatLen;
+    const float gn = fmaxf(y[0], 0.f) * mv;
+    const V3 gt = (flags & kWarmNormalOnly) ? v3(0.f, 0.f, 0.f) : (y[1] * mv) * t1 + (y[2] * mv) * t2;
+    float *g = gam + 4 * j;
+    g[0] = fminf(gn, a.gmax); g[1] = gt.x; g[2] = gt.y; g[3] = gt.z;
+    if ((flags & kWarmDq) && (j == 0 || cvert[j - 1] != vtx)) {
+      q[vtx] = x.x + y[3] / kFeatLen;
+      q[np + vtx] = x.y + y[4] / kFeatLen;
+      q[2 * np + vtx] = x.z + y[5] / kFeatLen;
+    }
+  }
+}
+
+// training targets after the step: converged multipliers in the frame of the
+// predicted position (scaled like the features) and q* - q~ at the vertex
+__global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArgs a, const int64_t *off, float *T) {
+  __shared__ ObsShared O;
+  const int l = blockIdx.x, e = G.genv[l];
+  const int np = G.n_pad;
+  load_obstacles(V, e, a.K, O);
+  __syncthreads();
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
+  const float *qp = G.qp + (size_t)l * 3 * np, *q = G.q + (size_t)l * 3 * np;
+  const float *gam = G.cgam + (size_t)l * G.cap * 4;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int vtx = cvert[j], o = cobs[j];
+    const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
+    V3 n, t1, t2;
+    float gap;
+    contact_frame_at(O, o, a.tau, x, n, t1, t2, gap);
+    const float *g = gam + 4 * j;
+    const float s = kFeatLen / __ldg(G.mass + vtx);
+    const V3 gt = v3(g[1], g[2], g[3]);
+    float *t = T + (off[l] + j) * 6;
+    if (!(V.rncp[e] <= a.tol)) {   // not converged: no target (NaN marks the row)
+      for (int c = 0; c < 6; c++) t[c] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    t[0] = g[0] * s; t[1] = dot(t1, gt) * s; t[2] = dot(t2, gt) * s;
+    t[3] = (q[vtx] - x.x) * kFeatLen; t[4] = (q[np + vtx] - x.y) * kFeatLen; t[5] = (q[2 * np + vtx] - x.z) * kFeatLen;
+  }
+}
+
 }  // namespace
 
 cudaError_t configure_kernels() {
@@ -790,6 +934,29 @@ cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a
 cudaError_t launch_ncp(const flash_scene *s, const Group &g, const StepArgs &a, int tc, cudaStream_t st) {
   size_t sm = tc ? sizeof(float) * 3 * g.n : 0;
   k_ncp<<<g.N, 256, sm, st>>>(view(s, g), eview(s), a, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_offsets(const Group &g, int64_t *off, cudaStream_t st) {
+  k_row_offsets<<<1, 1024, 0, st>>>(g.ccount, g.N, off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *X,
+                            cudaStream_t st) {
+  k_features<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_learned(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off,
+                                 const float *X, const float *Y, int flags, cudaStream_t st) {
+  k_apply_learned<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, X, Y, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_targets(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *T,
+                           cudaStream_t st) {
+  k_targets<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, T);
   return cudaGetLastError();
 }
 

@@ -87,10 +87,22 @@ def lib():
         L.flash_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
         L.flash_launch_count.argtypes = [vp]
         L.flash_launch_count.restype = i64
+        L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
+        L.flash_record_contacts.argtypes = [vp, i32]
+        L.flash_get_recorded.argtypes = [vp, vp, vp, i64, C.POINTER(i64), vp]
+        L.flash_mlp_num_params.restype = i32
+        L.flash_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+        L.flash_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+        L.flash_mlp_work_floats.argtypes = [i32]
+        L.flash_mlp_work_floats.restype = i64
+        L.flash_mlp_adam.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp]
+        L.flash_dense_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
                      "flash_step", "flash_get_contacts", "flash_get_stats", "flash_status_word",
-                     "flash_global_apply", "flash_profile_enable", "flash_profile_read"):
+                     "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
+                     "flash_record_contacts", "flash_get_recorded", "flash_mlp_forward", "flash_mlp_loss_grad",
+                     "flash_mlp_adam", "flash_dense_apply_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -223,7 +235,7 @@ class Sim:
     def status(self):
         return _check(lib().flash_status_word(self._h, _stream()))
 
-    KINDS = ("begin", "local", "solve", "ncp", "end")
+    KINDS = ("begin", "local", "solve", "ncp", "end", "warm")
 
     def profile(self, enable=True):
         """Bracket every launch with CUDA events on the launching stream."""
@@ -240,6 +252,24 @@ class Sim:
 
     def launch_count(self):
         return lib().flash_launch_count(self._h)
+
+    def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False):
+        """Select the warm start; ``params`` (device float32, flat) is copied."""
+        flags = (1 if use_dq else 0) | (2 if normal_only else 0)
+        _check(lib().flash_warmstart_set(self._h, _ptr(params), mode, flags))
+
+    def record(self, enable=True):
+        _check(lib().flash_record_contacts(self._h, 1 if enable else 0))
+
+    def recorded(self):
+        """(features [rows][10], targets [rows][6]) of the last step."""
+        rows = C.c_int64()
+        _check(lib().flash_get_recorded(self._h, None, None, 0, C.byref(rows), _stream()))
+        X = torch.empty((rows.value, 10), dtype=torch.float32, device=self.dev)
+        T = torch.empty((rows.value, 6), dtype=torch.float32, device=self.dev)
+        if rows.value:
+            _check(lib().flash_get_recorded(self._h, _ptr(X), _ptr(T), rows.value, C.byref(rows), _stream()))
+        return X, T
 
     def global_apply(self, first_env, n, rhs):
         out = torch.empty_like(rhs)
@@ -266,3 +296,30 @@ def state_tensors(scenes, device):
     q = np.concatenate([sc.q0.reshape(-1, 3) for sc in scenes]).astype(np.float32)
     v = np.concatenate([sc.v0.reshape(-1, 3) for sc in scenes]).astype(np.float32)
     return torch.from_numpy(q).to(device), torch.from_numpy(v).to(device)
+
+
+# ------------------------------------------------------------------ network
+def mlp_num_params():
+    return lib().flash_mlp_num_params()
+
+
+def mlp_forward(params, x):
+    y = torch.empty((x.shape[0], 6), dtype=torch.float32, device=x.device)
+    _check(lib().flash_mlp_forward(_ptr(params), _ptr(x), _ptr(y), x.shape[0], _stream()))
+    return y
+
+
+def mlp_loss_grad(params, x, t, work=None):
+    """(sum of squared errors [device scalar], gradient of the mean 0.5-loss)."""
+    rows = x.shape[0]
+    if work is None or work.numel() < lib().flash_mlp_work_floats(rows):
+        work = torch.empty(lib().flash_mlp_work_floats(rows), dtype=torch.float32, device=x.device)
+    grad = torch.empty_like(params)
+    sse = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().flash_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), rows, _ptr(grad), _ptr(sse), _ptr(work),
+                                     _stream()))
+    return sse, grad
+
+
+def mlp_adam(params, grad, m, v, step, lr):
+    _check(lib().flash_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, _stream()))
