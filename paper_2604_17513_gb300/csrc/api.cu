@@ -255,6 +255,7 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.r, sz));
   FLASH_CUDA_TRY(dalloc(s, &g.w, sz));
   FLASH_CUDA_TRY(dalloc(s, &g.f, sz));
+  FLASH_CUDA_TRY(dalloc(s, &g.dq, sz));
   FLASH_CUDA_TRY(dalloc(s, &g.rh, sz));
   FLASH_CUDA_TRY(dalloc(s, &g.rl, sz));
   FLASH_CUDA_TRY(dalloc(s, &g.rscale, (size_t)g.cols_pad));
@@ -350,7 +351,7 @@ cudaError_t flush_profile(flash_scene *s) {
 }
 
 cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
-  // w = A^-1 r ;  NCP ;  q = q + w + A^-1 J^T dgamma
+  // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq)
   cudaError_t e;
   const bool tc = use_tc(s);
   e = timed(s, FLASH_KIND_SOLVE, st, [&] {
@@ -360,7 +361,8 @@ cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a, cud
   e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, tc ? 1 : 0, st); });
   if (e != cudaSuccess) return e;
   return timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.q, g.w, s->done, 1, st) : gemm_simt(g, g.f, g.q, g.w, s->done, 1, st);
+    // the position update q += w + dq is applied by the next local pass
+    return tc ? gemm_tc(g, g.dq, nullptr, s->done, 0, st) : gemm_simt(g, g.f, g.dq, nullptr, s->done, 0, st);
   });
 }
 

@@ -57,6 +57,7 @@ struct Group {
   // state (device) [cols_pad][n_pad]
   float *q = nullptr, *v = nullptr, *qt = nullptr, *qp = nullptr;
   float *r = nullptr, *w = nullptr, *f = nullptr;
+  float *dq = nullptr;                    // A^-1 J^T dgamma (second global solve)
   __half *rh = nullptr, *rl = nullptr;    // split RHS for the tensor-core path
   float *rscale = nullptr;                // [cols_pad] power-of-two column scale
   // contacts (device)
@@ -151,8 +152,8 @@ cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, co
 cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
 
 // global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
-// mode 0: out = A^-1 * rhs
-// mode 1: q  = q + w + A^-1 * rhs   (skips environments whose done flag is set)
+// mode 0: out = A^-1 * rhs              (tiles whose environments are all done are skipped)
+// mode 1: q  = q + w + A^-1 * rhs       (skips environments whose done flag is set)
 cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float *w, const int *done, int mode,
                       cudaStream_t st);
 cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st);

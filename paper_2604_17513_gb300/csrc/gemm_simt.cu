@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
   for (int j = 0; j < 8; j++) {
     int col = j0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
     if (col >= cols) continue;
-    if (mode == 1 && done[genv[col / 3]]) continue;
+    if (done && done[genv[col / 3]]) continue;
     float *c = C + (size_t)col * n_pad;
     const float *w = W + (size_t)col * n_pad;
 #pragma unroll

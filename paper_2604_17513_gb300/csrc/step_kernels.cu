@@ -21,7 +21,7 @@ struct GroupView {
   int n, n_pad, E, H, vpe, nc, type, cap;
   const int *genv, *elems, *hv, *v2e_off, *v2e, *v2h_off, *v2h;
   const float *D, *wt, *hc, *mass;
-  float *q, *v, *qt, *qp, *r, *f, *w;
+  float *q, *v, *qt, *qp, *r, *f, *w, *dq;
   __half *rh, *rl;
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
@@ -41,7 +41,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.n = g.n; v.n_pad = g.n_pad; v.E = g.E; v.H = g.H; v.vpe = g.vpe; v.nc = g.nc; v.type = g.type; v.cap = s->cap;
   v.genv = g.genv; v.elems = g.elems; v.hv = g.hv; v.v2e_off = g.v2e_off; v.v2e = g.v2e;
   v.v2h_off = g.v2h_off; v.v2h = g.v2h; v.D = g.D; v.wt = g.wt; v.hc = g.hc; v.mass = g.mass;
-  v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w;
+  v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w; v.dq = g.dq;
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.pscratch = g.pscratch;
@@ -259,7 +259,7 @@ __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs
 
 template <int VPE>
 __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs a, int k, int residual_only,
-                                               int tc) {
+                                               int tc, int pending) {
   // VPE = vertices per element: 3 (triangle, F is 3x2) or 4 (tet, F is 3x3)
   constexpr int nc = VPE - 1, vpe = VPE;
   extern __shared__ float smem[];
@@ -280,10 +280,23 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
     Ps = G.pscratch + (size_t)l * ((size_t)G.E * nc * 3 + (size_t)G.H * 3);
     Ss = Ps + (size_t)G.E * nc * 3;
   }
-  const float *q = G.q + (size_t)l * 3 * np;
-  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-    int c = i / n, j = i - c * n;
-    qs[i] = q[c * np + j];
+  // q^{k-1} = q^{k-2} + w + A^-1 J^T dgamma: the previous iteration's position
+  // update (Eq. correction in correction form) is applied here, while the
+  // state is loaded, so both global solves keep a store-only epilogue
+  float *q = G.q + (size_t)l * 3 * np;
+  if (pending) {
+    const float *w = G.w + (size_t)l * 3 * np, *dq = G.dq + (size_t)l * 3 * np;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      const int c = i / n, j = i - c * n;
+      const float x = q[c * np + j] + w[c * np + j] + dq[c * np + j];
+      qs[i] = x;
+      q[c * np + j] = x;
+    }
+  } else {
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      const int c = i / n, j = i - c * n;
+      qs[i] = q[c * np + j];
+    }
   }
   load_obstacles(V, e, a.K, O);
   __syncthreads();
@@ -926,8 +939,9 @@ cudaError_t launch_begin(const flash_scene *s, const Group &g, const StepArgs &a
 
 cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a, int k, int residual_only, int tc,
                          cudaStream_t st) {
-  if (g.vpe == 3) k_local<3><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc);
-  else k_local<4><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc);
+  const int pending = k > 1;   // a position update from the previous iteration is waiting
+  if (g.vpe == 3) k_local<3><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc, pending);
+  else k_local<4><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc, pending);
   return cudaGetLastError();
 }
 
