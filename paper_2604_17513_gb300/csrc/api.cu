@@ -206,6 +206,31 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(upload(s, &g.v2h_off, v2h_off));
   FLASH_CUDA_TRY(upload(s, &g.v2h, v2h));
   FLASH_CUDA_TRY(upload(s, &g.mass, massf));
+  {
+    // fixed-degree incidence tables (empty slots: element/hinge 0, zero coefficients)
+    g.deg_e = 0;
+    g.deg_h = 0;
+    for (int i = 0; i < n; i++) {
+      g.deg_e = std::max(g.deg_e, v2e_off[i + 1] - v2e_off[i]);
+      g.deg_h = std::max(g.deg_h, v2h_off[i + 1] - v2h_off[i]);
+    }
+    std::vector<int4> ell_e((size_t)std::max(g.deg_e, 1) * np, int4{0, 0, 0, 0});
+    std::vector<int2> ell_h((size_t)std::max(g.deg_h, 1) * np, int2{0, 0});
+    auto bits = [](float f) { int b; std::memcpy(&b, &f, 4); return b; };
+    for (int i = 0; i < n; i++) {
+      for (int t = v2e_off[i]; t < v2e_off[i + 1]; t++) {
+        const int slot = v2e[t], el = slot >> 2, a = slot & 3;
+        const float *D = &Df[(size_t)el * 12 + 3 * a];
+        ell_e[(size_t)(t - v2e_off[i]) * np + i] = int4{el, bits(D[0]), bits(D[1]), bits(D[2])};
+      }
+      for (int t = v2h_off[i]; t < v2h_off[i + 1]; t++) {
+        const int slot = v2h[t], hh = slot >> 2, a = slot & 3;
+        ell_h[(size_t)(t - v2h_off[i]) * np + i] = int2{hh, bits(hc[4 * hh + a])};
+      }
+    }
+    FLASH_CUDA_TRY(upload(s, &g.ell_e, ell_e));
+    FLASH_CUDA_TRY(upload(s, &g.ell_h, ell_h));
+  }
   // system matrix A (scalar n x n block of A = A_s (x) I3), padded with I
   std::vector<double> A((size_t)np * np, 0.0);
   for (int i = 0; i < np; i++) A[(size_t)i * np + i] = i < n ? m.mass[i] : 1.0;

@@ -71,6 +71,73 @@ __device__ __forceinline__ float obstacle_sdf(int type, const float *dims, const
   return sd;
 }
 
+// Obstacle pose as a rotation matrix (row-major, body -> world) and origin;
+// `slip` maps a world point at t+h to where the same obstacle material point
+// was at t: x_t = S x + s.
+struct PoseM {
+  float R[9], p[3];
+  float S[9], s[3];
+};
+
+__device__ __forceinline__ void quat_to_mat(const float *q, float *R) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// pose_t, pose_th (p, quat) -> PoseM of the t+h pose plus the slip map
+__device__ __forceinline__ void make_posem(const float *pose_t, const float *pose_th, PoseM &P) {
+  float Rt[9];
+  quat_to_mat(pose_th + 3, P.R);
+  quat_to_mat(pose_t + 3, Rt);
+  for (int i = 0; i < 3; i++) P.p[i] = pose_th[i];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      P.S[3 * i + j] = Rt[3 * i] * P.R[3 * j] + Rt[3 * i + 1] * P.R[3 * j + 1] + Rt[3 * i + 2] * P.R[3 * j + 2];
+  for (int i = 0; i < 3; i++)
+    P.s[i] = pose_t[i] - (P.S[3 * i] * pose_th[0] + P.S[3 * i + 1] * pose_th[1] + P.S[3 * i + 2] * pose_th[2]);
+}
+
+// signed distance and outward unit normal with a matrix pose (same rules as obstacle_sdf)
+__device__ __forceinline__ float obstacle_sdf_m(int type, const float *dims, const PoseM &P, V3 x, V3 &n) {
+  const V3 d = x - v3(P.p[0], P.p[1], P.p[2]);
+  const float *R = P.R;
+  // body coordinates: R^T d
+  const V3 p = {R[0] * d.x + R[3] * d.y + R[6] * d.z, R[1] * d.x + R[4] * d.y + R[7] * d.z,
+                R[2] * d.x + R[5] * d.y + R[8] * d.z};
+  V3 nb = {0.f, 0.f, 1.f};
+  float sd;
+  if (type == FLASH_OBS_PLANE) {
+    sd = p.z;
+  } else if (type == FLASH_OBS_SPHERE) {
+    float dd = norm(p);
+    if (dd > 1e-12f) nb = (1.f / dd) * p;
+    sd = dd - dims[0];
+  } else {
+    float dx = fabsf(p.x) - dims[0], dy = fabsf(p.y) - dims[1], dz = fabsf(p.z) - dims[2];
+    if (dx > 0.f || dy > 0.f || dz > 0.f) {
+      V3 o = {fmaxf(dx, 0.f), fmaxf(dy, 0.f), fmaxf(dz, 0.f)};
+      float on = norm(o);
+      nb = {(p.x >= 0.f ? 1.f : -1.f) * o.x / on, (p.y >= 0.f ? 1.f : -1.f) * o.y / on,
+            (p.z >= 0.f ? 1.f : -1.f) * o.z / on};
+      sd = on;
+    } else {
+      int ax = 0;
+      float dm = dx;
+      if (dy > dm) { ax = 1; dm = dy; }
+      if (dz > dm) { ax = 2; dm = dz; }
+      float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+      float sg = pc >= 0.f ? 1.f : -1.f;
+      nb = {ax == 0 ? sg : 0.f, ax == 1 ? sg : 0.f, ax == 2 ? sg : 0.f};
+      sd = dm;
+    }
+  }
+  n = {R[0] * nb.x + R[1] * nb.y + R[2] * nb.z, R[3] * nb.x + R[4] * nb.y + R[5] * nb.z,
+       R[6] * nb.x + R[7] * nb.y + R[8] * nb.z};
+  return sd;
+}
+
 // Branchless orthonormal basis (Duff et al. 2017): t1, t2 orthogonal to n.
 __device__ __forceinline__ void tangent_basis(V3 n, V3 &t1, V3 &t2) {
   float s = n.z >= 0.f ? 1.f : -1.f;
@@ -261,6 +328,69 @@ __device__ __forceinline__ void linearize_contact(int type, const float *dims, f
     L.phi[2] = y1 - rad * h1;
     float k = rad / dn;
     float P00 = 1.f - h0 * h0, P01 = -h0 * h1, P11 = 1.f - h1 * h1;
+    L.Ct[0] = k * P00; L.Ct[1] = k * P01; L.Ct[2] = k * P01; L.Ct[3] = k * P11;
+    L.Dtt[0] = 1.f - k * P00; L.Dtt[1] = -k * P01; L.Dtt[2] = -k * P01; L.Dtt[3] = 1.f - k * P11;
+    if (yn > 0.f) { L.dtn[0] = -mu * h0; L.dtn[1] = -mu * h1; }
+    else { L.dtn[0] = 0.f; L.dtn[1] = 0.f; }
+  }
+}
+
+// linearize_contact with matrix poses (identical contact law)
+__device__ __forceinline__ void linearize_contact_m(int type, const float *dims, float comp, const PoseM &P, float tau,
+                                                    float mu, float h, float mv, V3 x, V3 xt, const float *g,
+                                                    ContactLin &L) {
+  V3 n, t1, t2;
+  float sd = obstacle_sdf_m(type, dims, P, x, n);
+  tangent_basis(n, t1, t2);
+  L.R[0] = n.x; L.R[1] = n.y; L.R[2] = n.z;
+  L.R[3] = t1.x; L.R[4] = t1.y; L.R[5] = t1.z;
+  L.R[6] = t2.x; L.R[7] = t2.y; L.R[8] = t2.z;
+  const float inv_m = 1.f / mv;
+  const float a = sd - tau;
+  L.gap = a;
+  const float yn = g[0] * inv_m;
+  const float alpha = comp * mv / (h * h);
+  const float ae = a + alpha * yn;
+  const float r = sqrtf(ae * ae + yn * yn);
+  float ca, cy;
+  if (r < 1e-12f) {
+    ca = 0.29289321881345254f;
+    cy = 0.29289321881345254f;
+  } else {
+    const float ir = 1.f / r;
+    ca = 1.f - ae * ir;
+    cy = 1.f - yn * ir;
+  }
+  L.phi[0] = ae + yn - r;
+  L.cn = ca;
+  L.dn = ca * alpha + cy;
+  // slip relative to the obstacle's material point over the step
+  const V3 xo = {P.S[0] * x.x + P.S[1] * x.y + P.S[2] * x.z + P.s[0], P.S[3] * x.x + P.S[4] * x.y + P.S[5] * x.z + P.s[1],
+                 P.S[6] * x.x + P.S[7] * x.y + P.S[8] * x.z + P.s[2]};
+  const V3 rel = xo - xt;
+  const float s0 = dot(t1, rel), s1 = dot(t2, rel);
+  const V3 gt = {g[1], g[2], g[3]};
+  const float y0 = dot(t1, gt) * inv_m, y1 = dot(t2, gt) * inv_m;
+  const float rad = mu * fmaxf(yn, 0.f);
+  const float d0 = y0 - s0, d1 = y1 - s1;
+  const float dn = sqrtf(d0 * d0 + d1 * d1);
+  if (rad == 0.f) {
+    L.phi[1] = y0; L.phi[2] = y1;
+    L.Ct[0] = 0.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 0.f;
+    L.dtn[0] = 0.f; L.dtn[1] = 0.f;
+    L.Dtt[0] = 1.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 1.f;
+  } else if (dn <= rad) {
+    L.phi[1] = s0; L.phi[2] = s1;
+    L.Ct[0] = 1.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 1.f;
+    L.dtn[0] = 0.f; L.dtn[1] = 0.f;
+    L.Dtt[0] = 0.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 0.f;
+  } else {
+    const float idn = 1.f / dn;
+    const float h0 = d0 * idn, h1 = d1 * idn;
+    L.phi[1] = y0 - rad * h0;
+    L.phi[2] = y1 - rad * h1;
+    const float k = rad * idn;
+    const float P00 = 1.f - h0 * h0, P01 = -h0 * h1, P11 = 1.f - h1 * h1;
     L.Ct[0] = k * P00; L.Ct[1] = k * P01; L.Ct[2] = k * P01; L.Ct[3] = k * P11;
     L.Dtt[0] = 1.f - k * P00; L.Dtt[1] = -k * P01; L.Dtt[2] = -k * P01; L.Dtt[3] = 1.f - k * P11;
     if (yn > 0.f) { L.dtn[0] = -mu * h0; L.dtn[1] = -mu * h1; }

@@ -50,6 +50,10 @@ struct Group {
   float *hc = nullptr;        // [H][4]
   int *v2e_off = nullptr, *v2e = nullptr;
   int *v2h_off = nullptr, *v2h = nullptr;
+  // fixed-degree incidence, vertex fastest: slot k of vertex i at [k * n_pad + i]
+  int4 *ell_e = nullptr;                  // {element, D[a][0..2] as float bits}; empty slots are zero
+  int2 *ell_h = nullptr;                  // {hinge, coefficient bits}; empty slots are zero
+  int deg_e = 0, deg_h = 0;
   float *mass = nullptr;      // [n]
   float *Ainv = nullptr;      // [n_pad][n_pad] FP32 (symmetric)
   __half *Ahi = nullptr, *Alo = nullptr;  // [n_pad][n_pad] split copy, scaled by 2^a_exp

@@ -25,6 +25,9 @@ struct GroupView {
   __half *rh, *rl;
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
+  const int4 *ell_e;
+  const int2 *ell_h;
+  int deg_e, deg_h;
   float *cgam, *pgam, *pscratch;
   int p_in_smem;
 };
@@ -46,6 +49,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.pscratch = g.pscratch;
   v.p_in_smem = g.p_in_smem ? 1 : 0;
+  v.ell_e = g.ell_e; v.ell_h = g.ell_h; v.deg_e = g.deg_e; v.deg_h = g.deg_h;
   return v;
 }
 
@@ -237,6 +241,7 @@ __device__ void write_split_columns(const GroupView &G, int l, const float *vals
 struct ObsShared {
   int type[FLASH_MAX_OBS];
   float dims[FLASH_MAX_OBS][3], pose[FLASH_MAX_OBS][7], poset[FLASH_MAX_OBS][7], comp[FLASH_MAX_OBS];
+  PoseM pm[FLASH_MAX_OBS];
 };
 
 __device__ __forceinline__ void load_obstacles(const EnvView &V, int e, int K, ObsShared &O) {
@@ -249,12 +254,13 @@ __device__ __forceinline__ void load_obstacles(const EnvView &V, int e, int K, O
       O.pose[o][c] = V.pose_th[(e * FLASH_MAX_OBS + o) * 7 + c];
       O.poset[o][c] = V.pose_t[(e * FLASH_MAX_OBS + o) * 7 + c];
     }
+    make_posem(O.poset[o], O.pose[o], O.pm[o]);
   }
 }
 
 __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs &a, float mu, float mv, V3 x, V3 xt,
                                        const float *g, ContactLin &L) {
-  linearize_contact(O.type[o], O.dims[o], O.comp[o], O.poset[o], O.pose[o], a.tau, mu, a.h, mv, x, xt, g, L);
+  linearize_contact_m(O.type[o], O.dims[o], O.comp[o], O.pm[o], a.tau, mu, a.h, mv, x, xt, g, L);
 }
 
 template <int VPE>
@@ -339,15 +345,12 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
       float m = __ldg(G.mass + i);
       float acc[3];
       for (int c = 0; c < 3; c++) acc[c] = m * (qp[c * np + i] - qs[c * n + i]);
-      const int e0 = __ldg(G.v2e_off + i), e1 = __ldg(G.v2e_off + i + 1);
-      for (int t = e0; t < e1; t++) {
-        int slot = __ldg(G.v2e + t);
-        int el = slot >> 2, aa = slot & 3;
-        const float *D = G.D + 12 * el + 3 * aa;
-        const float *P = Ps + (size_t)el * nc * 3;
-        float d[nc];
-#pragma unroll
-        for (int j = 0; j < nc; j++) d[j] = __ldg(D + j);
+      // incident elements: sum_e D_e[a]^T P_e (P_e = w~ (p_e - F_e))
+#pragma unroll 4
+      for (int t = 0; t < G.deg_e; t++) {
+        const int4 sl = __ldg(G.ell_e + (size_t)t * np + i);
+        const float *P = Ps + (size_t)sl.x * nc * 3;
+        const float d[3] = {__int_as_float(sl.y), __int_as_float(sl.z), __int_as_float(sl.w)};
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           float s = 0.f;
@@ -356,12 +359,12 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
           acc[c] += s;
         }
       }
-      const int h0 = __ldg(G.v2h_off + i), h1 = __ldg(G.v2h_off + i + 1);
-      for (int t = h0; t < h1; t++) {
-        int slot = __ldg(G.v2h + t);
-        int hh = slot >> 2, aa = slot & 3;
-        float cc = __ldg(G.hc + 4 * hh + aa);
-        for (int c = 0; c < 3; c++) acc[c] -= cc * Ss[hh * 3 + c];
+      // incident hinges: - c_a S_h
+#pragma unroll 4
+      for (int t = 0; t < G.deg_h; t++) {
+        const int2 sl = __ldg(G.ell_h + (size_t)t * np + i);
+        const float cc = __int_as_float(sl.y);
+        for (int c = 0; c < 3; c++) acc[c] -= cc * Ss[sl.x * 3 + c];
       }
       for (int c = 0; c < 3; c++) rs[c * n + i] = acc[c];
     }
