@@ -370,12 +370,17 @@ def main():
         roof["kernel"] = "global solve (dense A^-1 apply)"
         roof["traffic"] = traffic_for("solve_f16x3" if solve == flash.SOLVE_F16X3 else "solve_f32")
     else:
-        # HBM-bound kernels: minimum bytes per launch
-        bytes_env = {"local": 4 * n * 3 * 3, "ncp": 4 * n * 3 * 2, "begin": 4 * n * 3 * 6, "end": 4 * n * 3 * 3}[dom]
-        b = bytes_env * N
+        # data-movement roofline with the algorithmic bytes of each kernel per
+        # environment (n vertices, C contacts): local 72n + 36C, ncp 48n + 40C,
+        # begin 72n + 8C (read q, v; write q_t, q~, q, f; contact list), end 36n + 24C
+        C = float(sim.contacts()[0].float().mean().item())
+        per_env = {"local": 72 * n + 36 * C, "ncp": 48 * n + 40 * C, "begin": 72 * n + 8 * C,
+                   "end": 36 * n + 24 * C, "warm": 64 * C}[dom]
+        b = per_env * N
         peak = peaks.get("hbm_gbs", 6787.2)
         roof = {"bound": "hbm", "achieved": b / avg_s / 1e9, "peak": peak, "unit": "GB/s", "kernel": dom,
-                "traffic": traffic_for(dom)}
+                "algorithmic_bytes_per_launch": b, "mean_contacts_per_env": C,
+                "peak_source": "measured HBM copy bandwidth", "traffic": traffic_for(dom)}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_us"] = avg_s * 1e6
     roof["launches"] = d_n
