@@ -65,7 +65,7 @@ typedef int32_t flash_status;
 /* Scene-wide solver settings (Sec. III; Algorithm 1; appendix scene config).
  * h: timestep (s).  gravity: m/s^2.  tol_ncp: NCP residual tolerance (m) of
  * FLASH_MODE_TOL.  maxforce: clamp on the normal force (N).  thickness: the
- * cloth half-thickness tau (m) subtracted from signed distances.  margin:
+ * default contact thickness tau (m) of meshes that give none.  margin:
  * detection margin delta (m).  k_max: iterations of FLASH_MODE_FIXED.
  * k_min/k_cap: bounds of FLASH_MODE_TOL.  contact_cap: contacts per
  * environment.  solve: FLASH_SOLVE_*.  warm: FLASH_WARM_*. */
@@ -87,7 +87,9 @@ typedef struct {
  * bending on interior edges) or FLASH_TET (corotational strain).  rest: host
  * float64 [n][3]; elems: host int32 [E][3|4]; mass: host float64 [n] (kg).
  * w_stretch: weight per unit rest area (TRI) or volume (TET); w_bend: bending
- * weight (TRI only). */
+ * weight (TRI only); thickness: contact thickness tau (m) subtracted from the
+ * signed distances of this mesh's vertices (a negative value takes the
+ * scene's default). */
 typedef struct {
   int32_t type;
   int32_t n_verts, n_elems;
@@ -95,6 +97,7 @@ typedef struct {
   const int32_t *elems;
   const double *mass;
   double w_stretch, w_bend;
+  double thickness;
 } flash_mesh_desc;
 
 /* Per-environment parameters.  mu: Coulomb coefficient.  stiffness: scale on

@@ -164,6 +164,7 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   const MeshTemplate &m = s->meshes[g.mesh];
   const double h = s->d.h, h2 = h * h;
   g.type = m.type; g.n = m.n; g.E = m.E;
+  g.tau = (float)(m.thickness >= 0 ? m.thickness : s->d.thickness);
   g.vpe = m.type == FLASH_TRI ? 3 : 4;
   g.nc = m.type == FLASH_TRI ? 2 : 3;
   g.n_pad = round_up(std::max(m.n, 1), 128);
@@ -335,6 +336,13 @@ StepArgs step_args(const flash_scene *s) {
 
 bool use_tc(const flash_scene *s) { return s->d.solve == FLASH_SOLVE_F16X3; }
 
+// step arguments of one group (contact thickness is a property of the mesh)
+StepArgs group_args(const StepArgs &a, const Group &g) {
+  StepArgs ga = a;
+  ga.tau = g.tau;
+  return ga;
+}
+
 cudaEvent_t pool_event(flash_scene *s) {
   if (s->ev_used == s->ev_pool.size()) {
     cudaEvent_t e;
@@ -375,7 +383,8 @@ cudaError_t flush_profile(flash_scene *s) {
   return cudaSuccess;
 }
 
-cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
+cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a0, cudaStream_t st) {
+  const StepArgs a = group_args(a0, g);
   // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq)
   cudaError_t e;
   const bool tc = use_tc(s);
@@ -431,6 +440,7 @@ flash_status flash_mesh_add(flash_scene *s, const flash_mesh_desc *m, int32_t *m
   for (double x : t.mass)
     if (!(x > 0)) return fail(FLASH_EINVAL, "vertex mass must be positive");
   t.w_stretch = m->w_stretch; t.w_bend = m->w_bend;
+  t.thickness = m->thickness;
   s->meshes.push_back(std::move(t));
   if (mesh_id) *mesh_id = (int32_t)s->meshes.size() - 1;
   return FLASH_OK;
@@ -590,33 +600,33 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
   for (int step = 0; step < n_steps; step++) {
-    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, g, a, st); }));
+    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, g, group_args(a, g), st); }));
     if (learned || s->record) {
       for (auto &g : s->groups) {
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_row_offsets(g, g.row_off, st); }));
-        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_features(s, g, a, g.row_off, g.feat, st); }));
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_features(s, g, group_args(a, g), g.row_off, g.feat, st); }));
         if (learned) {
           FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] {
             return mlp_forward(s->mlp_params, g.feat, g.pred, g.row_off + g.N, (int64_t)g.N * s->cap, st);
           }));
           FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st,
-                               [&] { return launch_apply_learned(s, g, a, g.row_off, g.feat, g.pred, s->use_dq, st); }));
+                               [&] { return launch_apply_learned(s, g, group_args(a, g), g.row_off, g.feat, g.pred, s->use_dq, st); }));
         }
       }
     }
     if (s->d.mode == FLASH_MODE_FIXED) {
       for (int k = 1; k <= s->d.k_max; k++)
         for (auto &g : s->groups) {
-          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, k, 0, tc, st); }));
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), k, 0, tc, st); }));
           FLASH_CUDA_TRY(global_solves(s, g, a, st));
         }
       for (auto &g : s->groups)
-        FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, s->d.k_max + 1, 1, tc, st); }));
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), s->d.k_max + 1, 1, tc, st); }));
     } else {
       for (int k = 1; k <= s->d.k_cap + 1; k++) {
         FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
         for (auto &g : s->groups)
-          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, a, k, 0, tc, st); }));
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), k, 0, tc, st); }));
         FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
         FLASH_CUDA_TRY(cudaStreamSynchronize(st));
         if (*s->h_active == 0) break;
@@ -625,8 +635,8 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
     }
     if (s->record)
       for (auto &g : s->groups)
-        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, a, g.row_off, g.targ, st); }));
-    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, g, a, st); }));
+        FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, group_args(a, g), g.row_off, g.targ, st); }));
+    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, g, group_args(a, g), st); }));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
   }
   return FLASH_OK;

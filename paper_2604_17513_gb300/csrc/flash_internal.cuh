@@ -31,11 +31,13 @@ struct MeshTemplate {
   std::vector<double> rest, mass;
   std::vector<int> elems;
   double w_stretch = 0, w_bend = 0;
+  double thickness = -1;
 };
 
 struct Group {
   int mesh = 0;
   float stiff = 1.f;
+  float tau = 0.f;     // contact thickness of this group's mesh
   int n = 0, n_pad = 0, E = 0, H = 0, vpe = 3, nc = 2, type = 0;
   int N = 0;           // environments in the group
   int cols = 0;        // 3 * N

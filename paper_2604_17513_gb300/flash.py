@@ -42,7 +42,7 @@ class SceneDesc(C.Structure):
 class MeshDesc(C.Structure):
     _fields_ = [("type", C.c_int32), ("n_verts", C.c_int32), ("n_elems", C.c_int32),
                 ("rest", C.POINTER(C.c_double)), ("elems", C.POINTER(C.c_int32)), ("mass", C.POINTER(C.c_double)),
-                ("w_stretch", C.c_double), ("w_bend", C.c_double)]
+                ("w_stretch", C.c_double), ("w_bend", C.c_double), ("thickness", C.c_double)]
 
 
 class EnvDesc(C.Structure):
@@ -162,7 +162,7 @@ class Sim:
             self._keep += [rest, el, mass]
             m = MeshDesc(sc.elem_type, sc.n_verts, len(sc.elems), rest.ctypes.data_as(C.POINTER(C.c_double)),
                          el.ctypes.data_as(C.POINTER(C.c_int32)), mass.ctypes.data_as(C.POINTER(C.c_double)),
-                         sc.w_stretch, sc.w_bend)
+                         sc.w_stretch, sc.w_bend, sc.thickness)
             mid = C.c_int32()
             _check(lib().flash_mesh_add(self._h, C.byref(m), C.byref(mid)))
             envs = (EnvDesc * sc.n_envs)()

@@ -330,3 +330,86 @@ def incline_particle(theta: float, mu: float, steps: int = 20, h: float = 0.01, 
     return Scene("incline", TRI, rest, np.zeros((0, 3), np.int32), np.array([mass]), 0.0, 0.0,
                  q0, np.zeros_like(q0), np.array([mu]), np.ones(1), np.array([[PLANE]], np.int32),
                  np.zeros((1, 1, 3)), np.zeros((1, 1)), poses, h=h, thickness=tau, steps=steps)
+
+
+def _tet_dims_for(n_target):
+    """Cube counts (cx, cy, cz) of a block whose vertex count (cx+1)(cy+1)(cz+1)
+    is closest to n_target, with cx = cy = 2 cz rounded (flat blocks)."""
+    best = None
+    for cz in range(1, 12):
+        for cx in range(cz, 4 * cz + 1):
+            n = (cx + 1) * (cx + 1) * (cz + 1)
+            d = abs(n - n_target)
+            if best is None or d < best[0]:
+                best = (d, (cx, cx, cz))
+    return best[1]
+
+
+def mixed_batch(seed: int = 3, n_envs: int = 2048, steps: int = 1000, side_choices=None, tet_targets=None,
+                max_obs: int = 4):
+    """Uneven batch: half cloths with side U{16..64} vertices, half tet blocks
+    with 200-3000 vertices, each dropped onto 1-4 random boxes/spheres and the
+    ground; mu ~ U[0.1, 0.9]; h = 1/100 s.
+
+    Environments of equal mesh share one template (one Scene per template,
+    returned as a list).  ``side_choices`` / ``tet_targets`` restrict the
+    drawn sizes (for small test batches)."""
+    side_choices = list(range(16, 65)) if side_choices is None else list(side_choices)
+    tet_targets = (200, 3000) if tet_targets is None else tet_targets
+    groups = {}
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        if e % 2 == 0:
+            key = ("cloth", int(side_choices[int(g.integers(0, len(side_choices)))]))
+        else:
+            if isinstance(tet_targets, tuple):
+                key = ("tet", _tet_dims_for(int(g.integers(tet_targets[0], tet_targets[1] + 1))))
+            else:
+                key = ("tet", _tet_dims_for(int(tet_targets[int(g.integers(0, len(tet_targets)))])))
+        groups.setdefault(key, []).append(e)
+    out = []
+    for key, envs in sorted(groups.items(), key=lambda kv: kv[1][0]):
+        if key[0] == "cloth":
+            ns = key[1]
+            side = 0.5 * ns / 32
+            rest, elems = cloth_grid(ns, ns, side)
+            mass = np.full(len(rest), 0.1 * side * side / 0.25 / len(rest))
+            etype, ws, wb, tau, z0 = TRI, 1e4, 10.0, 1e-3, 0.25
+        else:
+            cx, cy, cz = key[1]
+            sx, sy, sz = 0.01 * cx, 0.01 * cy, 0.01 * cz
+            rest, elems = tet_block(cx, cy, cz, sx, sy, sz)
+            mass = lumped_tet_mass(rest, elems, 1000.0)
+            etype, ws, wb, tau, z0 = TET, 3e4, 0.0, 0.0, 0.12
+        n = len(rest)
+        N = len(envs)
+        K = 1 + max_obs
+        q0 = np.zeros((N, n, 3))
+        mu = np.zeros(N)
+        obs_type = np.zeros((N, K), np.int32)
+        obs_dims = np.zeros((N, K, 3))
+        poses = np.zeros((N, steps + 1, K, 7))
+        poses[:, :, :, 3] = 1.0
+        for i, e in enumerate(envs):
+            g = env_rng(seed, e)
+            g.integers(0, 2)  # the draw that picked the size
+            mu[i] = g.uniform(0.1, 0.9)
+            q0[i] = rest + (0.0, 0.0, z0)
+            obs_type[i, 0] = PLANE
+            k_obs = int(g.integers(1, max_obs + 1))
+            for o in range(1, 1 + k_obs):
+                if g.uniform() < 0.5:
+                    obs_type[i, o] = SPHERE
+                    r = g.uniform(0.03, 0.1)
+                    obs_dims[i, o, 0] = r
+                    c = (g.uniform(-0.15, 0.15), g.uniform(-0.15, 0.15), r)
+                else:
+                    obs_type[i, o] = BOX
+                    hx = g.uniform(0.02, 0.08, 3)
+                    obs_dims[i, o] = hx
+                    c = (g.uniform(-0.15, 0.15), g.uniform(-0.15, 0.15), hx[2])
+                poses[i, :, o, :3] = c
+        out.append(Scene(f"mixed_{key[0]}_{key[1]}", etype, rest, elems, mass, ws, wb, q0, np.zeros_like(q0), mu,
+                         np.ones(N), obs_type, obs_dims, np.zeros((N, K)), poses, h=0.01, thickness=tau, steps=steps,
+                         meta={"envs": envs}))
+    return out

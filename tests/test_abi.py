@@ -61,7 +61,7 @@ def test_scene_descriptor_validation(lib):
     el = np.array([[0, 1, 5]], np.int32)
     mass = np.ones(3)
     m = flash.MeshDesc(0, 3, 1, rest.ctypes.data_as(C.POINTER(C.c_double)), el.ctypes.data_as(C.POINTER(C.c_int32)),
-                       mass.ctypes.data_as(C.POINTER(C.c_double)), 1.0, 0.0)
+                       mass.ctypes.data_as(C.POINTER(C.c_double)), 1.0, 0.0, 1e-3)
     mid = C.c_int32()
     assert lib.flash_mesh_add(h, C.byref(m), C.byref(mid)) == flash.EINVAL
     el[0, 2] = 2

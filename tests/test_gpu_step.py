@@ -194,3 +194,38 @@ def test_three_contacts_on_one_vertex(cuda):
     qg, _ = gpu_step_from(sim, sc, 0, sc.q0, sc.v0, n=3)
     assert np.abs(qg[0] - ref.q).max() <= POS_TOL
     assert np.abs(ref.q[0] - sc.q0[0, 0]).max() < 1e-4
+
+
+@pytest.mark.parametrize("solve", SOLVES)
+def test_mixed_meshes_one_step(cuda, solve):
+    """Uneven batch in one scene: cloths and tet blocks of different sizes
+    (one group per template) against random boxes and spheres; every
+    environment is checked against the oracle after one step from its
+    oracle state in contact."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    scs = scenes.mixed_batch(n_envs=8, steps=40, side_choices=(16, 20), tet_targets=(250, 500))
+    s = 22
+    qs, vs, refs = [], [], []
+    for sc in scs:
+        for e in range(sc.n_envs):
+            mesh, st = oracle_state_at(sc, e, s)
+            q0, v0 = _f32(st.q), _f32(st.v)
+            qs.append(q0)
+            vs.append(v0)
+            ref = oracle.EnvState(q0, v0)
+            oracle.step(mesh, sc, e, s, ref)
+            refs.append(ref)
+    assert sum(len(r.cvert) > 0 for r in refs) >= 4      # most environments touch something
+    sim = flash.Sim(scs, solve=solve)
+    sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
+                  torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
+    sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
+    sim.set_poses(flash.poses_tensor(scs, s + 1, cuda), which=1)
+    sim.step(1)
+    qg, _ = sim.get_state()
+    qg = qg.cpu().numpy()
+    off = sim.offsets
+    for i, ref in enumerate(refs):
+        err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
+        assert err <= POS_TOL, (i, err, len(ref.cvert))
