@@ -182,7 +182,7 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   for (int e = 0; e < m.E; e++) {
     for (int a = 0; a < g.vpe; a++) el[(size_t)e * 4 + a] = m.elems[(size_t)e * g.vpe + a];
     for (int t = 0; t < 12; t++) Df[(size_t)e * 12 + t] = (float)ed.D[(size_t)e * 12 + t];
-    wt[e] = (float)(h2 * m.w_stretch * g.stiff * ed.size[e]);
+    wt[e] = (float)(h2 * m.w_stretch * (g.eig ? 1.0 : g.stiff) * ed.size[e]);
   }
   std::vector<float> hc(hg.k.size());
   for (int t = 0; t < g.H; t++)
@@ -232,6 +232,60 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
     FLASH_CUDA_TRY(upload(s, &g.ell_e, ell_e));
     FLASH_CUDA_TRY(upload(s, &g.ell_h, ell_h));
   }
+  if (g.eig) {
+    // per-environment stiffness: A_e = M + k_e L with L = h^2 w sum vol D D^T.
+    // With B = M^-1/2 L M^-1/2 = W diag(lam) W^T and V = M^-1/2 W,
+    // A_e^-1 = V diag(1 / (1 + k_e lam)) V^T.
+    std::vector<double> B((size_t)n * n, 0.0);
+    for (int e = 0; e < m.E; e++) {
+      const double w = h2 * m.w_stretch * ed.size[e];
+      const double *D = &ed.D[(size_t)e * 12];
+      for (int a = 0; a < g.vpe; a++)
+        for (int b = 0; b < g.vpe; b++) {
+          double dd = 0;
+          for (int j = 0; j < g.nc; j++) dd += D[a * 3 + j] * D[b * 3 + j];
+          const int va = el[(size_t)e * 4 + a], vb = el[(size_t)e * 4 + b];
+          B[(size_t)va * n + vb] += w * dd / std::sqrt(m.mass[va] * m.mass[vb]);
+        }
+    }
+    std::vector<double> W, lam;
+    jacobi_eigen(n, B, W, lam);
+    std::vector<double> Vp((size_t)np * np, 0.0), Vtp((size_t)np * np, 0.0);
+    std::vector<float> lamf(np, 0.f);
+    double vmax = 0;
+    for (int i = 0; i < n; i++) {
+      const double is = 1.0 / std::sqrt(m.mass[i]);
+      for (int j = 0; j < n; j++) {
+        const double v = W[(size_t)i * n + j] * is;
+        Vp[(size_t)i * np + j] = v;
+        Vtp[(size_t)j * np + i] = v;
+        vmax = std::max(vmax, std::fabs(v));
+      }
+    }
+    for (int j = 0; j < n; j++) lamf[j] = (float)std::max(lam[j], 0.0);
+    int vex = 0;
+    std::frexp(vmax, &vex);
+    for (SolveMat *Mx : {&g.V, &g.Vt}) {
+      Mx->exp = 14 - vex;
+      FLASH_CUDA_TRY(dalloc(s, &Mx->f32, (size_t)np * np));
+      FLASH_CUDA_TRY(dalloc(s, &Mx->hi, (size_t)np * np));
+      FLASH_CUDA_TRY(dalloc(s, &Mx->lo, (size_t)np * np));
+    }
+    double *dV = nullptr;
+    FLASH_CUDA_TRY(cudaMalloc(&dV, sizeof(double) * Vp.size()));
+    FLASH_CUDA_TRY(cudaMemcpy(dV, Vp.data(), sizeof(double) * Vp.size(), cudaMemcpyHostToDevice));
+    FLASH_CUDA_TRY(cast_inverse(dV, np, g.V.f32, g.V.hi, g.V.lo, g.V.exp, st));
+    FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+    FLASH_CUDA_TRY(cudaMemcpy(dV, Vtp.data(), sizeof(double) * Vtp.size(), cudaMemcpyHostToDevice));
+    FLASH_CUDA_TRY(cast_inverse(dV, np, g.Vt.f32, g.Vt.hi, g.Vt.lo, g.Vt.exp, st));
+    FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(dV);
+    FLASH_CUDA_TRY(upload(s, &g.lam, lamf));
+    std::vector<float> ke(g.N);
+    for (int l = 0; l < g.N; l++) ke[l] = s->envs[g.env_ids[l]].stiffness;
+    FLASH_CUDA_TRY(upload(s, &g.kenv, ke));
+    FLASH_CUDA_TRY(dalloc(s, &g.y, (size_t)g.cols_pad * np));
+  } else {
   // system matrix A (scalar n x n block of A = A_s (x) I3), padded with I
   std::vector<double> A((size_t)np * np, 0.0);
   for (int i = 0; i < np; i++) A[(size_t)i * np + i] = i < n ? m.mass[i] : 1.0;
@@ -265,13 +319,14 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   }
   int ex = 0;
   std::frexp(amax, &ex);
-  g.a_exp = 14 - ex;
-  FLASH_CUDA_TRY(dalloc(s, &g.Ainv, (size_t)np * np));
-  FLASH_CUDA_TRY(dalloc(s, &g.Ahi, (size_t)np * np));
-  FLASH_CUDA_TRY(dalloc(s, &g.Alo, (size_t)np * np));
-  FLASH_CUDA_TRY(cast_inverse(dA, np, g.Ainv, g.Ahi, g.Alo, g.a_exp, st));
+  g.inv.exp = 14 - ex;
+  FLASH_CUDA_TRY(dalloc(s, &g.inv.f32, (size_t)np * np));
+  FLASH_CUDA_TRY(dalloc(s, &g.inv.hi, (size_t)np * np));
+  FLASH_CUDA_TRY(dalloc(s, &g.inv.lo, (size_t)np * np));
+  FLASH_CUDA_TRY(cast_inverse(dA, np, g.inv.f32, g.inv.hi, g.inv.lo, g.inv.exp, st));
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(dA);
+  }
   // state and contact buffers
   size_t sz = (size_t)g.cols_pad * np;
   FLASH_CUDA_TRY(dalloc(s, &g.q, sz));
@@ -383,24 +438,85 @@ cudaError_t flush_profile(flash_scene *s) {
   return cudaSuccess;
 }
 
-cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a0, cudaStream_t st) {
-  const StepArgs a = group_args(a0, g);
-  // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq)
-  cudaError_t e;
+// out = A^-1 * (the group's current right-hand side): r in FP32 (CUDA-core
+// path) or its f16 split (tensor-core path)
+cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, float *out, cudaStream_t st) {
   const bool tc = use_tc(s);
-  e = timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.w, nullptr, s->done, 0, st) : gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st);
+  if (!g.eig) {
+    return timed(s, FLASH_KIND_SOLVE, st, [&] {
+      return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st)
+                : gemm_simt(g, g.inv, rhs32, out, nullptr, s->done, 0, nullptr, nullptr, st);
+    });
+  }
+  // eigen form: y = diag(1/(1 + k_e lam)) V^T rhs, out = V y
+  // (the CUDA-core kernel reads its matrix transposed, so it is given V for V^T and V^T for V)
+  cudaError_t e = timed(s, FLASH_KIND_SOLVE, st, [&] {
+    return tc ? gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st)
+              : gemm_simt(g, g.V, rhs32, g.y, nullptr, s->done, 2, g.lam, g.kenv, st);
   });
   if (e != cudaSuccess) return e;
-  e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, tc ? 1 : 0, st); });
-  if (e != cudaSuccess) return e;
+  if (tc) {
+    e = timed(s, FLASH_KIND_SOLVE, st, [&] { return launch_split_rhs(g, g.y, s->done, st); });
+    if (e != cudaSuccess) return e;
+  }
   return timed(s, FLASH_KIND_SOLVE, st, [&] {
-    // the position update q += w + dq is applied by the next local pass
-    return tc ? gemm_tc(g, g.dq, nullptr, s->done, 0, st) : gemm_simt(g, g.f, g.dq, nullptr, s->done, 0, st);
+    return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st)
+              : gemm_simt(g, g.Vt, g.y, out, nullptr, s->done, 0, nullptr, nullptr, st);
   });
 }
 
+cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a0, cudaStream_t st) {
+  const StepArgs a = group_args(a0, g);
+  // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq, applied by the next local pass)
+  cudaError_t e = apply_inverse(s, g, g.r, g.w, st);
+  if (e != cudaSuccess) return e;
+  e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, use_tc(s) ? 1 : 0, st); });
+  if (e != cudaSuccess) return e;
+  return apply_inverse(s, g, g.f, g.dq, st);
+}
+
 }  // namespace
+
+// Cyclic Jacobi eigenvalue iteration: rotate away each off-diagonal entry in
+// turn until the off-diagonal mass is negligible; W accumulates the rotations.
+void jacobi_eigen(int n, std::vector<double> &B, std::vector<double> &W, std::vector<double> &lam) {
+  W.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) W[(size_t)i * n + i] = 1.0;
+  double total = 0;
+  for (double x : B) total += x * x;
+  for (int sweep = 0; sweep < 50; sweep++) {
+    double off = 0;
+    for (int p = 0; p < n; p++)
+      for (int q = p + 1; q < n; q++) off += B[(size_t)p * n + q] * B[(size_t)p * n + q];
+    if (off <= 1e-30 * total) break;
+    for (int p = 0; p < n - 1; p++)
+      for (int q = p + 1; q < n; q++) {
+        const double bpq = B[(size_t)p * n + q];
+        if (std::fabs(bpq) < 1e-300) continue;
+        const double theta = (B[(size_t)q * n + q] - B[(size_t)p * n + p]) / (2.0 * bpq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; k++) {   // columns p, q
+          const double bkp = B[(size_t)k * n + p], bkq = B[(size_t)k * n + q];
+          B[(size_t)k * n + p] = c * bkp - sn * bkq;
+          B[(size_t)k * n + q] = sn * bkp + c * bkq;
+        }
+        for (int k = 0; k < n; k++) {   // rows p, q
+          const double bpk = B[(size_t)p * n + k], bqk = B[(size_t)q * n + k];
+          B[(size_t)p * n + k] = c * bpk - sn * bqk;
+          B[(size_t)q * n + k] = sn * bpk + c * bqk;
+        }
+        for (int k = 0; k < n; k++) {
+          const double wkp = W[(size_t)k * n + p], wkq = W[(size_t)k * n + q];
+          W[(size_t)k * n + p] = c * wkp - sn * wkq;
+          W[(size_t)k * n + q] = sn * wkp + c * wkq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; i++) lam[i] = B[(size_t)i * n + i];
+}
+
 }  // namespace flash
 
 using namespace flash;
@@ -474,20 +590,33 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   s->N = (int)s->envs.size();
   s->K = 0;
   for (auto &e : s->envs) s->K = std::max(s->K, (int)e.n_obs);
-  // groups by (mesh, stiffness)
+  // groups: one per (mesh, stiffness); a mesh without bending whose
+  // environments use several stiffness scales gets one eigen-form group
+  std::map<int, std::vector<float>> mesh_stiff;
+  for (int e = 0; e < s->N; e++) {
+    auto &v = mesh_stiff[s->env_mesh[e]];
+    if (std::find(v.begin(), v.end(), s->envs[e].stiffness) == v.end()) v.push_back(s->envs[e].stiffness);
+  }
+  auto use_eig = [&](int mesh) {
+    const MeshTemplate &m = s->meshes[mesh];
+    return m.w_bend == 0.0 && mesh_stiff[mesh].size() > 1 && m.n <= 2048;
+  };
   std::map<std::pair<int, float>, int> key;
   s->env_group.resize(s->N);
   s->env_local.resize(s->N);
   for (int e = 0; e < s->N; e++) {
-    auto k = std::make_pair(s->env_mesh[e], s->envs[e].stiffness);
+    const int mesh = s->env_mesh[e];
+    const bool eig = use_eig(mesh);
+    auto k = std::make_pair(mesh, eig ? -1.f : s->envs[e].stiffness);
     auto it = key.find(k);
     int gi;
     if (it == key.end()) {
       gi = (int)s->groups.size();
       key[k] = gi;
       Group g;
-      g.mesh = k.first;
+      g.mesh = mesh;
       g.stiff = k.second;
+      g.eig = eig;
       s->groups.push_back(g);
     } else {
       gi = it->second;
@@ -752,12 +881,8 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemsetAsync(s->done, 0, sizeof(int) * s->N, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, rhs, g.r, 0, st));
-  if (use_tc(s)) {
-    FLASH_CUDA_TRY(launch_split_rhs(g, g.r, s->done, st));
-    FLASH_CUDA_TRY(gemm_tc(g, g.w, nullptr, s->done, 0, st));
-  } else {
-    FLASH_CUDA_TRY(gemm_simt(g, g.r, g.w, nullptr, s->done, 0, st));
-  }
+  if (use_tc(s)) FLASH_CUDA_TRY(launch_split_rhs(g, g.r, s->done, st));
+  FLASH_CUDA_TRY(apply_inverse(s, g, g.r, g.w, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, out, g.w, 1, st));
   return FLASH_OK;
 }

@@ -34,6 +34,14 @@ struct MeshTemplate {
   double thickness = -1;
 };
 
+// a matrix the global solve applies: FP32 copy for the CUDA-core path and
+// f16 hi/lo split scaled by 2^exp for the tensor-core path ([n_pad][n_pad])
+struct SolveMat {
+  float *f32 = nullptr;
+  __half *hi = nullptr, *lo = nullptr;
+  int exp = 0;
+};
+
 struct Group {
   int mesh = 0;
   float stiff = 1.f;
@@ -57,9 +65,15 @@ struct Group {
   int2 *ell_h = nullptr;                  // {hinge, coefficient bits}; empty slots are zero
   int deg_e = 0, deg_h = 0;
   float *mass = nullptr;      // [n]
-  float *Ainv = nullptr;      // [n_pad][n_pad] FP32 (symmetric)
-  __half *Ahi = nullptr, *Alo = nullptr;  // [n_pad][n_pad] split copy, scaled by 2^a_exp
-  int a_exp = 0;
+  // explicit inverse (groups with one stiffness) ...
+  SolveMat inv;
+  // ... or, for per-environment stiffness k_e on a mesh without bending, the
+  // eigenbasis of (L, M): A_e^-1 = V diag(1 / (1 + k_e lambda)) V^T
+  bool eig = false;
+  SolveMat V, Vt;
+  float *lam = nullptr;                   // [n_pad] eigenvalues (0 in the padding)
+  float *kenv = nullptr;                  // [N] stiffness scale of each environment
+  float *y = nullptr;                     // [cols_pad][n_pad] eigen-coordinates (intermediate)
   // state (device) [cols_pad][n_pad]
   float *q = nullptr, *v = nullptr, *qt = nullptr, *qp = nullptr;
   float *r = nullptr, *w = nullptr, *f = nullptr;
@@ -158,11 +172,15 @@ cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, co
 cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
 
 // global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
-// mode 0: out = A^-1 * rhs              (tiles whose environments are all done are skipped)
-// mode 1: q  = q + w + A^-1 * rhs       (skips environments whose done flag is set)
-cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float *w, const int *done, int mode,
-                      cudaStream_t st);
-cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st);
+// out = M * rhs over all columns of a group, M = A^-1, V or V^T (the CUDA-core
+// kernel computes M^T * rhs: callers pass the transposed matrix).  Epilogue
+// mode 0: out = acc (tiles whose environments are all done are skipped)
+// mode 1: q  = q + w + acc (skips environments whose done flag is set)
+// mode 2: out = acc / (1 + kenv[env] * lam[row])  (eigen-coordinate scaling)
+cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float *out, const float *w,
+                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st);
+cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
+                    const float *lam, const float *kenv, cudaStream_t st);
 bool tc_available();
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);
 
@@ -170,5 +188,8 @@ cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n
 cudaError_t invert_spd_f64(double *A, int n, int n_pad, int batch, cudaStream_t st);
 cudaError_t cast_inverse(const double *A64, int n_pad, float *A32, __half *hi, __half *lo, int a_exp,
                          cudaStream_t st);
+// symmetric eigen-decomposition by cyclic Jacobi rotations (host, FP64):
+// B (n x n, destroyed) = W diag(lam) W^T, W row-major with eigenvectors as columns
+void jacobi_eigen(int n, std::vector<double> &B, std::vector<double> &W, std::vector<double> &lam);
 
 }  // namespace flash

@@ -4,7 +4,9 @@
 // "S^T S g" applies of Algorithm 1 done with the explicit dense inverse.
 //
 // Tiles: 128 rows x 128 columns x 16 k per CTA, 256 threads, 8x8 outputs per
-// thread.  A^-1 is symmetric, so its tile is read along rows (coalesced).
+// thread.  The matrix tile is read along its rows (coalesced), so the kernel
+// computes M^T * RHS: equal to M * RHS for the symmetric A^-1; the eigen-form
+// solve passes V to get V^T * RHS and V^T to get V * RHS.
 // Epilogue mode 1 adds the previous iterate and the first solve:
 //   q^k = q^{k-1} + w + A^-1 J^T dgamma   (Eq. correction in correction form).
 #include "flash_internal.cuh"
@@ -17,7 +19,8 @@ constexpr int BM = 128, BN = 128, BK = 16;
 __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, const float *__restrict__ B,
                                                   float *__restrict__ C, const float *__restrict__ W,
                                                   const int *__restrict__ done, const int *__restrict__ genv,
-                                                  int n_pad, int cols, int mode) {
+                                                  int n_pad, int cols, int mode, const float *__restrict__ lam,
+                                                  const float *__restrict__ kenv) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
@@ -77,10 +80,12 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
     if (done && done[genv[col / 3]]) continue;
     float *c = C + (size_t)col * n_pad;
     const float *w = W + (size_t)col * n_pad;
+    const float ke = mode == 2 ? kenv[col / 3] : 0.f;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       int row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
       if (mode == 0) c[row] = acc[i][j];
+      else if (mode == 2) c[row] = acc[i][j] / (1.f + ke * lam[row]);
       else c[row] = c[row] + w[row] + acc[i][j];
     }
   }
@@ -88,10 +93,10 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
 
 }  // namespace
 
-cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float *w, const int *done, int mode,
-                      cudaStream_t st) {
+cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float *out, const float *w,
+                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st) {
   dim3 grid((g.cols + BN - 1) / BN, g.n_pad / BM);
-  k_gemm_f32<<<grid, 256, 0, st>>>(g.Ainv, rhs, out, w, done, g.genv, g.n_pad, g.cols, mode);
+  k_gemm_f32<<<grid, 256, 0, st>>>(M.f32, rhs, out, w, done, g.genv, g.n_pad, g.cols, mode, lam, kenv);
   return cudaGetLastError();
 }
 
@@ -99,7 +104,7 @@ cudaError_t gemm_simt(const Group &g, const float *rhs, float *out, const float 
 // (A^-1 [n_pad][n_pad], B and C [cols rounded up to 128][n_pad]).
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st) {
   dim3 grid((cols + BN - 1) / BN, n_pad / BM);
-  k_gemm_f32<<<grid, 256, 0, st>>>(Ainv, rhs, out, nullptr, nullptr, nullptr, n_pad, cols, 0);
+  k_gemm_f32<<<grid, 256, 0, st>>>(Ainv, rhs, out, nullptr, nullptr, nullptr, n_pad, cols, 0, nullptr, nullptr);
   return cudaGetLastError();
 }
 

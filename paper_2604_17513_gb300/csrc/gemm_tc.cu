@@ -107,12 +107,13 @@ __global__ void __launch_bounds__(128, 1)
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
               const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int cols,
-              float a_unscale, int mode) {
+              float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail_sh;
   __shared__ float col_scale[BN];
+  __shared__ float col_k[BN];
   __shared__ int col_live[BN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(128, 1)
     const int col = j0 + c;
     const bool in = col < cols;
     col_scale[c] = in ? a_unscale * rscale[col] : 0.f;
-    col_live[c] = in && (mode == 0 || !done[genv[col / 3]]);
+    col_k[c] = (in && mode == 2) ? kenv[col / 3] : 0.f;
+    col_live[c] = in && (mode != 1 || !done[genv[col / 3]]);
   }
   bool ok = mbar_wait(&done_bar, 0);
   if (!ok) atomicExch(&fail_sh, 1);
@@ -215,7 +217,13 @@ __global__ void __launch_bounds__(128, 1)
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       float *o = out + (size_t)(j0 + c0) * n_pad + row;
-      if (mode == 0) {
+      if (mode == 2) {
+        const float lr = lam[row];
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          if (col_live[c0 + j])
+            o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j] / (1.f + col_k[c0 + j] * lr);
+      } else if (mode == 0) {
 #pragma unroll
         for (int j = 0; j < 32; j++)
           if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
@@ -273,7 +281,8 @@ bool tc_available() {
   return major == 10 && minor == 3 && get_encode() != nullptr;
 }
 
-cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done, int mode, cudaStream_t st) {
+cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
+                    const float *lam, const float *kenv, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -282,12 +291,12 @@ cudaError_t gemm_tc(const Group &g, float *out, const float *w, const int *done,
   }
   if (g.n_pad % BM != 0 || g.n_pad % BK != 0 || g.cols_pad % BN != 0) return cudaErrorInvalidValue;
   CUtensorMap tmAh, tmAl, tmBh, tmBl;
-  if (!make_map(&tmAh, g.Ahi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, g.Alo, g.n_pad, g.n_pad, BM) ||
+  if (!make_map(&tmAh, M.hi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, M.lo, g.n_pad, g.n_pad, BM) ||
       !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN) || !make_map(&tmBl, g.rl, g.n_pad, g.cols_pad, BN))
     return cudaErrorInvalidValue;
   dim3 grid(g.cols_pad / BN, g.n_pad / BM);
   k_gemm_tc<<<grid, 128, SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
-                                           g.n_pad, g.cols, ldexpf(1.f, -g.a_exp), mode);
+                                           g.n_pad, g.cols, ldexpf(1.f, -M.exp), mode, lam, kenv);
   return cudaGetLastError();
 }
 

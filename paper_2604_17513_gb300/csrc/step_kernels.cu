@@ -28,6 +28,7 @@ struct GroupView {
   const int4 *ell_e;
   const int2 *ell_h;
   int deg_e, deg_h;
+  const float *kenv;   // per-environment stiffness scale (eigen-form groups), else null
   float *cgam, *pgam, *pscratch;
   int p_in_smem;
 };
@@ -50,6 +51,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.pscratch = g.pscratch;
   v.p_in_smem = g.p_in_smem ? 1 : 0;
   v.ell_e = g.ell_e; v.ell_h = g.ell_h; v.deg_e = g.deg_e; v.deg_h = g.deg_h;
+  v.kenv = g.eig ? g.kenv : nullptr;
   return v;
 }
 
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
   load_obstacles(V, e, a.K, O);
   __syncthreads();
   if (!residual_only) {
+    const float ks = G.kenv ? G.kenv[l] : 1.f;
     // ---- local projection p_i = closest rotation to F_i = G_i q; store w~(p - F)
     for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
         }
       if constexpr (nc == 2) closest_rot32(F, R);
       else closest_rot33(F, R);
-      const float wt = __ldg(G.wt + el);
+      const float wt = __ldg(G.wt + el) * ks;
       float *P = Ps + (size_t)el * nc * 3;
 #pragma unroll
       for (int t = 0; t < 3 * nc; t++) P[t] = wt * (R[t] - F[t]);
