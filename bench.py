@@ -37,7 +37,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--envs", type=int, default=1024, help="environments per GPU")
+    p.add_argument("--workload", default="cloth_gripper", choices=["cloth_gripper", "tet_squeeze", "mixed"])
+    p.add_argument("--envs", type=int, default=None, help="environments per GPU (default: the workload's)")
     p.add_argument("--side", type=int, default=32)
     p.add_argument("--k", type=int, default=10, help="local-global iterations per step (fixed mode)")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
@@ -227,7 +228,7 @@ def main():
         return
     # CPU baseline first (before any CUDA context, single thread)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cloth_gripper":
         cpu = cpu_baseline(6, 12, args.side, args.k)
 
     import numpy as np
@@ -242,8 +243,22 @@ def main():
 
     solve = {"auto": flash.SOLVE_F16X3, "f32": flash.SOLVE_F32, "f16x3": flash.SOLVE_F16X3}[args.solve]
     n_steps = args.warmup + args.steps
-    sc = scenes.cloth_gripper(seed=1 + rank, n_envs=args.envs, n_side=args.side, steps=n_steps + 3 * args.steps + 8,
-                              k_max=args.k)
+    total_steps = n_steps + 3 * args.steps + 8
+    if args.workload == "cloth_gripper":
+        args.envs = args.envs or 1024
+        sc = scenes.cloth_gripper(seed=1 + rank, n_envs=args.envs, n_side=args.side, steps=total_steps, k_max=args.k)
+        workload = (f"cloth+gripper: {args.envs} envs x {args.side}x{args.side} cloth ({len(sc.elems)} tris), "
+                    f"2 box fingers + ground, h=1/100")
+    elif args.workload == "tet_squeeze":
+        args.envs = args.envs or 4096
+        sc = scenes.tet_squeeze(seed=1 + rank, n_envs=args.envs, steps=total_steps, k_max=args.k)
+        workload = (f"tet squeeze: {args.envs} envs x 8x8x4-cube tet block (1280 tets, 405 verts), per-env "
+                    f"stiffness log-U[1e3,1e5] (eigen-form solve), parallel gripper, h=1/200")
+    else:
+        args.envs = args.envs or 2048
+        sc = scenes.mixed_batch(seed=3 + rank, n_envs=args.envs, steps=total_steps)
+        workload = (f"mixed: {args.envs} envs, cloths of side U{{16..64}} and tet blocks of 200-3000 verts "
+                    f"({len(sc)} templates), 1-4 boxes/spheres, h=1/100")
     try:
         sim = flash.Sim(sc, solve=solve, warm=flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD)
     except flash.FlashError:
@@ -253,7 +268,8 @@ def main():
         sim = flash.Sim(sc, solve=solve, warm=flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD)
     q0, v0 = flash.state_tensors(sc, dev)
     sim.set_state(q0, v0)
-    poses = torch.stack([flash.poses_tensor(sc, s, dev) for s in range(sc.poses.shape[1])])  # [S+1][N][8][7]
+    scs = sc if isinstance(sc, list) else [sc]
+    poses = torch.stack([flash.poses_tensor(sc, s, dev) for s in range(total_steps + 1)])  # [S+1][N][8][7]
     sim.set_poses(poses[0], which=0)
     for s in range(args.warmup):
         sim.set_poses(poses[s + 1])
@@ -331,7 +347,7 @@ def main():
 
     # ---------------- plain vs learned warm start (same fixed k, same residual test)
     warm_cmp = None
-    if not args.no_warm_compare:
+    if not args.no_warm_compare and args.workload == "cloth_gripper":
         from paper_2604_17513_gb300 import warmstart
         first = n_steps + args.steps
         X, T = warmstart.collect(sim, sc, first, 6, dev)
@@ -351,12 +367,19 @@ def main():
 
     # ---------------- roofline of the dominant kernel
     peaks = load_peaks()
-    n, N = sc.n_verts, args.envs
+    N = args.envs
+    # per-template (vertices, environments); one template per mesh group
+    tmpl = [(s_.n_verts, s_.n_envs) for s_ in scs]
+    n_sum = sum(nv * ne for nv, ne in tmpl)          # vertices over all environments
+    eig = args.workload == "tet_squeeze"
     dom = max(prof, key=lambda k: prof[k][0])
     d_ms, d_n = prof[dom]
     avg_s = d_ms / max(d_n, 1) / 1e3
     if dom == "solve":
-        flops = 2.0 * n * n * 3 * N     # algorithmic: dense apply A^-1 [n x n] to 3N columns
+        # per apply: dense A^-1 [n x n] on 3 columns per environment, 2n^2 flop a
+        # column; the eigen form (per-environment stiffness) executes two
+        # contractions, V^T then V, and is counted as such
+        flops = (4.0 if eig else 2.0) * sum(nv * nv * 3 * ne for nv, ne in tmpl)
         if solve == flash.SOLVE_F16X3:
             peak = peaks.get("bf16_tflops", 1900.0)
             roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -374,9 +397,8 @@ def main():
         # environment (n vertices, C contacts): local 72n + 36C, ncp 48n + 40C,
         # begin 72n + 8C (read q, v; write q_t, q~, q, f; contact list), end 36n + 24C
         C = float(sim.contacts()[0].float().mean().item())
-        per_env = {"local": 72 * n + 36 * C, "ncp": 48 * n + 40 * C, "begin": 72 * n + 8 * C,
-                   "end": 36 * n + 24 * C, "warm": 64 * C}[dom]
-        b = per_env * N
+        per = {"local": (72, 36), "ncp": (48, 40), "begin": (72, 8), "end": (36, 24), "warm": (0, 64)}[dom]
+        b = per[0] * n_sum + per[1] * C * N
         peak = peaks.get("hbm_gbs", 6787.2)
         roof = {"bound": "hbm", "achieved": b / avg_s / 1e9, "peak": peak, "unit": "GB/s", "kernel": dom,
                 "algorithmic_bytes_per_launch": b, "mean_contacts_per_env": C,
@@ -387,7 +409,7 @@ def main():
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-12)}
                for k, v in prof.items()}
     # step-level HBM fraction: minimal state traffic of a step (read q_t, v_t; write q, v)
-    step_bytes = 4 * n * 3 * 4 * N
+    step_bytes = 4 * n_sum * 3 * 4
     step_hbm_frac = step_bytes / (ms_max / 1e3) / 1e9 / peaks.get("hbm_gbs", 6787.2)
 
     if rank == 0:
@@ -395,8 +417,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "converged env-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"cloth+gripper: {N} envs x {args.side}x{args.side} cloth "
-                                   f"({len(sc.elems)} tris), 2 box fingers + ground, h=1/100",
+            "config": {"workload": workload,
                        "mode": "fixed", "k": args.k, "warm": args.warm,
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",

@@ -223,7 +223,10 @@ __device__ void write_split_columns(const GroupView &G, int l, const float *vals
     int ex = 0;
     if (m[c] > 0.f) {
       frexpf(m[c], &ex);   // m = f * 2^ex, f in [0.5, 1)
-      ex = 14 - ex;        // scaled max in [2^13, 2^14)
+      // scaled max in [2^13, 2^14); the cap keeps 2^ex finite and 2^-ex a
+      // normal float for columns below 2^-112 (a contact update that has
+      // converged to rounding level), which then scale to less than 2^14.
+      ex = min(14 - ex, 126);
     }
     const float sc = ldexpf(1.f, ex);
     const size_t col = (size_t)(l * 3 + c);

@@ -70,6 +70,31 @@ def test_global_apply_matches_cholesky(cuda, solve):
 
 
 @pytest.mark.parametrize("solve", SOLVES)
+def test_global_apply_tiny_and_zero_columns(cuda, solve):
+    """Right-hand sides near the bottom of the float range (a contact update
+    that has converged to ~1e-35, below the 2^-112 where the hi/lo split's
+    power-of-two column scale reaches its cap) and exactly zero columns: the
+    scale must stay finite and the result must still be A^-1 b.  Entries are
+    normal floats; the step kernels flush subnormals to zero."""
+    import torch
+    sc = scenes.cloth_drop(n_envs=2)
+    sim = _sim(sc, solve=solve)
+    rng = np.random.default_rng(6)
+    shape = (2, sc.n_verts, 3)
+    rhs = rng.choice([-1.0, 1.0], size=shape) * rng.uniform(0.5, 2.0, size=shape) * 1e-35
+    rhs[1, :, 2] = 0.0
+    out = sim.global_apply(0, 2, torch.from_numpy(rhs.astype(np.float32).reshape(-1, 3)).to(cuda))
+    out = out.cpu().numpy().reshape(2, sc.n_verts, 3)
+    assert np.isfinite(out).all()
+    assert (out[1, :, 2] == 0).all()
+    mesh = oracle.Mesh.from_scene(sc)
+    for e in range(2):
+        ref = mesh.solve(_f32(rhs[e]).astype(np.float64) * 1e35) * 1e-35
+        err = np.abs(out[e] - ref).max() / np.abs(ref).max()
+        assert err < (2e-5 if solve == 0 else 1e-4), (e, err)
+
+
+@pytest.mark.parametrize("solve", SOLVES)
 @pytest.mark.parametrize("s", [0, 10, 27, 40])
 def test_cloth_drop_one_step(cuda, s, solve):
     """16x16 cloth falling onto the sphere: one Mode-A step (k = 10) from the

@@ -198,6 +198,55 @@ def test_coulomb_incline_stick_slide(theta):
             assert abs(disp - a * sc.h ** 2 * n * (n + 1) / 2) < 1e-10, (mu, disp)
 
 
+def _particle_scene(obs, poses, mu, steps, x0, h=0.01, mass=0.01):
+    """One free particle (no elements) among kinematic obstacles.
+    obs: list of (type, half-extents); poses: [S+1][K][7]."""
+    K = len(obs)
+    return scenes.Scene("particle", scenes.TRI, np.zeros((1, 3)), np.zeros((0, 3), np.int32), np.array([mass]),
+                        0.0, 0.0, np.array([[x0]], float), np.zeros((1, 1, 3)), np.array([mu]), np.ones(1),
+                        np.array([[t for t, _ in obs]], np.int32), np.array([[d for _, d in obs]], float),
+                        np.zeros((1, K)), np.asarray(poses, float)[None], h=h, thickness=1e-3, steps=steps)
+
+
+@pytest.mark.parametrize("mu", [0.8, 0.2])
+def test_friction_on_translating_plane(mu):
+    """The ground translates along x at V: the slip u_t is measured against
+    the obstacle's own displacement over the step.  With mu g h >= V the
+    particle sticks from the first step on (x_n = n V h); otherwise it slides
+    with the Coulomb acceleration mu g toward the plane's velocity,
+    x_n = mu g h^2 n(n+1)/2 while n mu g h < V."""
+    V, h, n = 0.3 if mu < 0.5 else 0.05, 0.01, 8
+    poses = np.array([[[V * h * s, 0, 0, 1, 0, 0, 0]] for s in range(n + 1)])
+    sc = _particle_scene([(scenes.PLANE, (0, 0, 0))], poses, mu, n, (0, 0, 1e-3), h=h)
+    st = oracle.rollout(sc, 0, n, mode=1, tol=1e-13, k_cap=100)
+    if mu * 9.81 * h >= V:
+        assert abs(st.q[0, 0] - n * V * h) < 1e-12 and abs(st.v[0, 0] - V) < 1e-10
+    else:
+        assert n * mu * 9.81 * h < V
+        assert abs(st.q[0, 0] - mu * 9.81 * h * h * n * (n + 1) / 2) < 1e-12
+        assert abs(st.v[0, 0] - n * mu * 9.81 * h) < 1e-10
+    assert abs(st.q[0, 1]) < 1e-14 and abs(st.q[0, 2] - 1e-3) < 1e-12
+
+
+def test_box_pushes_particle_on_frictionless_ground():
+    """A 2 cm box sliding along x at V pushes a particle resting on the
+    frictionless ground: two contacts on one vertex (ground normal z, box
+    face normal x), and at convergence the particle stays exactly one
+    thickness in front of the moving face and on the ground."""
+    V, h, n, half = 0.1, 0.01, 10, 0.01
+    poses = np.array([[[0, 0, 0, 1, 0, 0, 0], [V * h * s, 0, half, 1, 0, 0, 0]] for s in range(n + 1)])
+    x0 = (half + 1e-3, 0.0, 1e-3)
+    sc = _particle_scene([(scenes.PLANE, (0, 0, 0)), (scenes.BOX, (half, half, half))], poses, 0.0, n, x0, h=h)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    for s in range(n):
+        oracle.step(mesh, sc, 0, s, st, mode=1, tol=1e-13, k_cap=100)
+        assert len(st.cvert) == 2
+        assert abs(st.q[0, 0] - (x0[0] + (s + 1) * V * h)) < 1e-12, s
+        assert abs(st.q[0, 2] - 1e-3) < 1e-12 and abs(st.q[0, 1]) < 1e-14
+    assert abs(st.v[0, 0] - V) < 1e-10
+
+
 def test_complementarity_at_convergence():
     """Converged contacts: lambda_n >= 0, gap >= -1e-6 m, |h lambda_n gap| <= 1e-8,
     |lambda_t| <= mu lambda_n, sliding contacts oppose the slip."""
