@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--envs", type=int, default=None, help="environments per GPU (default: the workload's)")
     p.add_argument("--side", type=int, default=32)
     p.add_argument("--k", type=int, default=10, help="local-global iterations per step (fixed mode)")
+    p.add_argument("--mode", default="fixed", choices=["fixed", "tol"],
+                   help="fixed: k iterations per step; tol: iterate until r_ncp <= 1e-5 (cap --k-cap)")
+    p.add_argument("--k-cap", type=int, default=200, help="iteration cap of the tolerance mode")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
     p.add_argument("--no-e2e", action="store_true")
@@ -157,8 +160,19 @@ def traffic_for(kernel):
     return d.get("bytes_per_launch_scaled", d.get("bytes_per_launch"))
 
 
+def oracle_mode_kw(args):
+    """Oracle stopping rule matching the GPU arm's --mode."""
+    if args.mode == "tol":
+        return {"mode": 1, "tol": TOL, "k_min": 1, "k_cap": args.k_cap}
+    return {}
+
+
+def mode_desc(args):
+    return f"fixed k={args.k}" if args.mode == "fixed" else f"tolerance r_ncp<=1e-5, cap {args.k_cap}"
+
+
 # --------------------------------------------------------------------------- CPU baseline
-def cpu_baseline(n_envs_sample, steps_sample, side, k):
+def cpu_baseline(n_envs_sample, steps_sample, side, k, args):
     """FP64 oracle, single thread, on a bounded sample of the same workload."""
     import oracle
     from paper_2604_17513_gb300 import scenes
@@ -170,14 +184,14 @@ def cpu_baseline(n_envs_sample, steps_sample, side, k):
         m = oracle.Mesh.from_scene(sc, e)
         st = oracle.EnvState(sc.q0[e], sc.v0[e])
         for s in range(steps_sample):
-            oracle.step(m, sc, e, s, st)
+            oracle.step(m, sc, e, s, st, **oracle_mode_kw(args))
             n_done += 1
             n_conv += st.rncp <= TOL
     dt = time.perf_counter() - t0
     return {"value": n_conv / dt, "unit": "converged env-steps/s", "all_env_steps_per_s": n_done / dt,
             "cores": 1, "kind": "oracle",
             "sample": f"{n_envs_sample} envs x {steps_sample} steps of the {side}x{side} cloth+gripper workload, "
-                      f"fixed k={k}, FP64, single thread (includes per-env system-matrix setup)",
+                      f"{mode_desc(args)}, FP64, single thread (includes per-env system-matrix setup)",
             "seconds": dt}
 
 
@@ -192,12 +206,12 @@ def run_reference(args, rank):
     states = [oracle.EnvState(sc.q0[e], sc.v0[e]) for e in range(2)]
     for s in range(args.warmup):
         for e in range(2):
-            oracle.step(meshes[e], sc, e, s, states[e])
+            oracle.step(meshes[e], sc, e, s, states[e], **oracle_mode_kw(args))
     t0 = time.perf_counter()
     conv = 0
     for s in range(args.warmup, args.warmup + args.steps):
         for e in range(2):
-            oracle.step(meshes[e], sc, e, s, states[e])
+            oracle.step(meshes[e], sc, e, s, states[e], **oracle_mode_kw(args))
             conv += states[e].rncp <= TOL
     dt = time.perf_counter() - t0
     val = 2 * args.steps / dt
@@ -208,7 +222,9 @@ def run_reference(args, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"cloth+gripper: {args.envs} envs x {args.side}x{args.side} cloth "
                                f"({2 * (args.side - 1) ** 2} tris), 2 box fingers + ground, h=1/100",
-                   "mode": "fixed", "k": args.k, "warm": "cold", "solve": "FP64 oracle (Cholesky)",
+                   "mode": args.mode, "k": args.k if args.mode == "fixed" else None,
+                   "k_cap": args.k_cap if args.mode == "tol" else None, "warm": "cold",
+                   "solve": "FP64 oracle (Cholesky)",
                    "sample": "2 of the environments per step, single thread"},
         "cpu_baseline": {"value": val_conv, "unit": "converged env-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "2 envs per step of the cloth+gripper workload, FP64, single thread",
@@ -229,7 +245,7 @@ def main():
     # CPU baseline first (before any CUDA context, single thread)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cloth_gripper":
-        cpu = cpu_baseline(6, 12, args.side, args.k)
+        cpu = cpu_baseline(6, 12, args.side, args.k, args)
 
     import numpy as np
     import torch
@@ -259,13 +275,15 @@ def main():
         sc = scenes.mixed_batch(seed=3 + rank, n_envs=args.envs, steps=total_steps)
         workload = (f"mixed: {args.envs} envs, cloths of side U{{16..64}} and tet blocks of 200-3000 verts "
                     f"({len(sc)} templates), 1-4 boxes/spheres, h=1/100")
+    mode_kw = {"mode": flash.MODE_TOL, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
+    warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
     try:
-        sim = flash.Sim(sc, solve=solve, warm=flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD)
+        sim = flash.Sim(sc, solve=solve, warm=warm, **mode_kw)
     except flash.FlashError:
         if args.solve != "auto":
             raise
         solve = flash.SOLVE_F32
-        sim = flash.Sim(sc, solve=solve, warm=flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD)
+        sim = flash.Sim(sc, solve=solve, warm=warm, **mode_kw)
     q0, v0 = flash.state_tensors(sc, dev)
     sim.set_state(q0, v0)
     scs = sc if isinstance(sc, list) else [sc]
@@ -418,7 +436,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload,
-                       "mode": "fixed", "k": args.k, "warm": args.warm,
+                       "mode": args.mode, "k": args.k if args.mode == "fixed" else None,
+                       "k_cap": args.k_cap if args.mode == "tol" else None, "warm": args.warm,
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},

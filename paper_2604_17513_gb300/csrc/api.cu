@@ -43,6 +43,9 @@ cudaError_t upload(flash_scene *s, T **p, const std::vector<T> &h) {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// streams of the per-group contraction pool (multi-group scenes)
+constexpr size_t kPoolStreams = 16;
+
 // ---------------------------------------------------------------------------
 // element operators: F = Ds Dm^-1 written as F[c][j] = sum_a x_a[c] D[a][j]
 // ---------------------------------------------------------------------------
@@ -424,10 +427,11 @@ cudaError_t timed(flash_scene *s, int kind, cudaStream_t st, F &&f) {
 
 cudaError_t flush_profile(flash_scene *s) {
   if (s->ev_kind.empty()) return cudaSuccess;
-  cudaError_t e = cudaEventSynchronize(s->ev_pool[2 * s->ev_kind.size() - 1]);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   for (size_t i = 0; i < s->ev_kind.size(); i++) {
     float ms = 0.f;
+    // pairs may sit on different streams (pool streams of multi-group scenes)
+    if ((e = cudaEventSynchronize(s->ev_pool[2 * i + 1])) != cudaSuccess) return e;
     e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
     if (e != cudaSuccess) return e;
     s->prof_ms[s->ev_kind[i]] += ms;
@@ -473,6 +477,41 @@ cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a0, cu
   e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, use_tc(s) ? 1 : 0, st); });
   if (e != cudaSuccess) return e;
   return apply_inverse(s, g, g.f, g.dq, st);
+}
+
+// Multi-group scenes: the per-group contractions of one phase run on the pool
+// streams, ordered after everything already on `st` (fork) and before
+// anything issued to `st` next (join).
+cudaStream_t pool_stream(const flash_scene *s, size_t gi, cudaStream_t st) {
+  return s->pool.empty() ? st : s->pool[gi % s->pool.size()];
+}
+
+cudaError_t fork(flash_scene *s, cudaStream_t st) {
+  if (s->pool.empty()) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(s->pool_ev[0], st);
+  for (size_t i = 0; i < s->pool.size() && e == cudaSuccess; i++) e = cudaStreamWaitEvent(s->pool[i], s->pool_ev[0], 0);
+  return e;
+}
+
+cudaError_t join(flash_scene *s, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < s->pool.size() && e == cudaSuccess; i++) {
+    e = cudaEventRecord(s->pool_ev[1 + i], s->pool[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->pool_ev[1 + i], 0);
+  }
+  return e;
+}
+
+// One phase of global applies, out_g = A_g^-1 in_g, over every group.
+template <typename In, typename Out>
+cudaError_t apply_all(flash_scene *s, cudaStream_t st, In in, Out out) {
+  cudaError_t e = fork(s, st);
+  for (size_t gi = 0; gi < s->groups.size() && e == cudaSuccess; gi++) {
+    Group &g = s->groups[gi];
+    e = apply_inverse(s, g, in(g), out(g), pool_stream(s, gi, st));
+  }
+  const cudaError_t j = join(s, st);
+  return e != cudaSuccess ? e : j;
 }
 
 }  // namespace
@@ -661,6 +700,20 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
+  if (s->groups.size() > 1) {
+    FLASH_CUDA_TRY(build_batches(s));
+    const size_t P = std::min<size_t>(s->groups.size(), kPoolStreams);
+    for (size_t i = 0; i < P; i++) {
+      cudaStream_t ps;
+      FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+      s->pool.push_back(ps);
+    }
+    for (size_t i = 0; i <= P; i++) {
+      cudaEvent_t ev;
+      FLASH_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      s->pool_ev.push_back(ev);
+    }
+  }
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   s->finalized = true;
   return FLASH_OK;
@@ -671,6 +724,8 @@ void flash_scene_destroy(flash_scene *s) {
   cudaDeviceSynchronize();
   for (void *p : s->allocs) cudaFree(p);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->pool_ev) cudaEventDestroy(e);
+  for (cudaStream_t ps : s->pool) cudaStreamDestroy(ps);
   if (s->h_active) cudaFreeHost(s->h_active);
   delete s;
 }
@@ -728,8 +783,29 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const StepArgs a = step_args(s);
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
+  // several groups: per-environment kernels as table launches over all
+  // groups, contractions per group on the stream pool
+  const bool batched = s->groups.size() > 1;
+  auto local = [&](int k, int residual_only) -> cudaError_t {
+    if (!batched)
+      return timed(s, FLASH_KIND_LOCAL, st,
+                   [&] { return launch_local(s, s->groups[0], group_args(a, s->groups[0]), k, residual_only, tc, st); });
+    int launched = 0;
+    const cudaError_t e =
+        timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local_all(s, a, k, residual_only, tc, st, &launched); });
+    s->launches += launched - 1;
+    return e;
+  };
+  auto solves = [&]() -> cudaError_t {
+    if (!batched) return global_solves(s, s->groups[0], a, st);
+    cudaError_t e = apply_all(s, st, [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+    if (e == cudaSuccess) e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp_all(s, a, tc, st); });
+    if (e == cudaSuccess) e = apply_all(s, st, [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
+    return e;
+  };
   for (int step = 0; step < n_steps; step++) {
-    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, g, group_args(a, g), st); }));
+    if (batched) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin_all(s, a, st); }));
+    else FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, s->groups[0], group_args(a, s->groups[0]), st); }));
     if (learned || s->record) {
       for (auto &g : s->groups) {
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_row_offsets(g, g.row_off, st); }));
@@ -744,28 +820,26 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
       }
     }
     if (s->d.mode == FLASH_MODE_FIXED) {
-      for (int k = 1; k <= s->d.k_max; k++)
-        for (auto &g : s->groups) {
-          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), k, 0, tc, st); }));
-          FLASH_CUDA_TRY(global_solves(s, g, a, st));
-        }
-      for (auto &g : s->groups)
-        FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), s->d.k_max + 1, 1, tc, st); }));
+      for (int k = 1; k <= s->d.k_max; k++) {
+        FLASH_CUDA_TRY(local(k, 0));
+        FLASH_CUDA_TRY(solves());
+      }
+      FLASH_CUDA_TRY(local(s->d.k_max + 1, 1));
     } else {
       for (int k = 1; k <= s->d.k_cap + 1; k++) {
         FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
-        for (auto &g : s->groups)
-          FLASH_CUDA_TRY(timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local(s, g, group_args(a, g), k, 0, tc, st); }));
+        FLASH_CUDA_TRY(local(k, 0));
         FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
         FLASH_CUDA_TRY(cudaStreamSynchronize(st));
         if (*s->h_active == 0) break;
-        for (auto &g : s->groups) FLASH_CUDA_TRY(global_solves(s, g, a, st));
+        FLASH_CUDA_TRY(solves());
       }
     }
     if (s->record)
       for (auto &g : s->groups)
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, group_args(a, g), g.row_off, g.targ, st); }));
-    for (auto &g : s->groups) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, g, group_args(a, g), st); }));
+    if (batched) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end_all(s, a, st); }));
+    else FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, s->groups[0], group_args(a, s->groups[0]), st); }));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
   }
   return FLASH_OK;

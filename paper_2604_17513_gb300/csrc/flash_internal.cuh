@@ -96,6 +96,17 @@ struct Group {
 
 }  // namespace flash
 
+namespace flash {
+// One table launch over the environments of several groups: CTA b works on
+// environment map[b].y of group map[b].x (a row of the scene's group table).
+struct Batch {
+  int vpe = 0;            // vertices per element of its groups (local pass only)
+  int blocks = 0;         // CTAs, one per environment
+  size_t smem = 0;        // dynamic shared memory per CTA: the largest need of its groups
+  int2 *map = nullptr;    // device [blocks]
+};
+}  // namespace flash
+
 struct flash_scene {
   flash_scene_desc d{};
   std::vector<flash::MeshTemplate> meshes;
@@ -129,6 +140,14 @@ struct flash_scene {
   bool record = false;
   double prof_ms[FLASH_NUM_KINDS] = {0};
   int64_t prof_n[FLASH_NUM_KINDS] = {0};
+  // scenes with several groups: per-environment kernels run as table launches
+  // over all groups, the per-group contractions on a pool of streams
+  void *gtab = nullptr;                        // device table of group views
+  std::vector<flash::Batch> b_local;           // local pass, by element type and shared-memory class
+  flash::Batch b_all;                          // begin / NCP / end over every environment
+  size_t ncp_smem_tc = 0;
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> pool_ev;            // [0] fork, [1 + i] join of pool stream i
 };
 
 namespace flash {
@@ -170,6 +189,13 @@ cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q
 cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,
                           int to_user, cudaStream_t st);
 cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
+// table launches over every group of a scene (build_batches first)
+cudaError_t build_batches(flash_scene *s);
+cudaError_t launch_begin_all(const flash_scene *s, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int residual_only, int tc,
+                             cudaStream_t st, int *launched);
+cudaError_t launch_ncp_all(const flash_scene *s, const StepArgs &a, int tc, cudaStream_t st);
+cudaError_t launch_end_all(const flash_scene *s, const StepArgs &a, cudaStream_t st);
 
 // global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
 // out = M * rhs over all columns of a group, M = A^-1, V or V^T (the CUDA-core

@@ -13,6 +13,8 @@
 #include "device_math.cuh"
 #include "flash_internal.cuh"
 
+#include <algorithm>
+
 namespace flash {
 
 namespace {
@@ -31,6 +33,7 @@ struct GroupView {
   const float *kenv;   // per-environment stiffness scale (eigen-form groups), else null
   float *cgam, *pgam, *pscratch;
   int p_in_smem;
+  float tau;           // contact thickness of the group's mesh
 };
 
 struct EnvView {
@@ -52,6 +55,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.p_in_smem = g.p_in_smem ? 1 : 0;
   v.ell_e = g.ell_e; v.ell_h = g.ell_h; v.deg_e = g.deg_e; v.deg_h = g.deg_h;
   v.kenv = g.eig ? g.kenv : nullptr;
+  v.tau = (float)g.tau;
   return v;
 }
 
@@ -122,11 +126,12 @@ __device__ void block_max3(float &x0, float &x1, float &x2, float (*sh)[3]) {
 // ---------------------------------------------------------------------------
 // begin of step: q_t, q~, detection, gamma^0
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_begin(GroupView G, EnvView V, StepArgs a) {
+__device__ __forceinline__ void begin_body(const GroupView &G, const int l, const EnvView &V, StepArgs a) {
   __shared__ int sh_scan[32];
   __shared__ int s_type[FLASH_MAX_OBS];
   __shared__ float s_dims[FLASH_MAX_OBS][3], s_pose[FLASH_MAX_OBS][7];
-  const int l = blockIdx.x, e = G.genv[l];
+  a.tau = G.tau;
+  const int e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   float *q = G.q + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
   float *qt = G.qt + (size_t)l * 3 * np, *qp = G.qp + (size_t)l * 3 * np, *f = G.f + (size_t)l * 3 * np;
@@ -269,8 +274,8 @@ __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs
 }
 
 template <int VPE>
-__global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs a, int k, int residual_only,
-                                               int tc, int pending) {
+__device__ __forceinline__ void local_body(const GroupView &G, const int l, const EnvView &V, StepArgs a, int k,
+                                           int residual_only, int tc, int pending) {
   // VPE = vertices per element: 3 (triangle, F is 3x2) or 4 (tet, F is 3x3)
   constexpr int nc = VPE - 1, vpe = VPE;
   extern __shared__ float smem[];
@@ -278,7 +283,8 @@ __global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs 
   __shared__ float sh3[32][3];
   __shared__ int s_done;
   __shared__ ObsShared O;
-  const int l = blockIdx.x, e = G.genv[l];
+  a.tau = G.tau;
+  const int e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   if (V.done[e]) return;
   float *qs = smem;           // [3][n]
@@ -621,11 +627,12 @@ __device__ __noinline__ V3 solve_multi(const ContactLin *Ls, const StepArgs &a, 
   return fsum;
 }
 
-__global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs a, int tc) {
+__device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const EnvView &V, StepArgs a, int tc) {
   extern __shared__ float fs[];   // [3][n] contact force (tc path)
   __shared__ float sh3[32][3];
   __shared__ ObsShared O;
-  const int l = blockIdx.x, e = G.genv[l];
+  a.tau = G.tau;
+  const int e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   if (V.done[e]) return;
   const int cnt = G.ccount[l];
@@ -718,10 +725,8 @@ __global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs
 // ---------------------------------------------------------------------------
 // end of step: velocity, keep the contact list for warm starts
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_end(GroupView G, EnvView V, StepArgs a) {
-  const int l = blockIdx.x, e = G.genv[l];
+__device__ __forceinline__ void end_body(const GroupView &G, const int l, const EnvView &V, const StepArgs &a) {
   const int n = G.n, np = G.n_pad;
-  (void)e;
   const float inv_h = 1.f / a.h;
   float *q = G.q + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
   const float *qt = G.qt + (size_t)l * 3 * np;
@@ -738,6 +743,41 @@ __global__ void __launch_bounds__(256) k_end(GroupView G, EnvView V, StepArgs a)
     G.pobs[(size_t)l * G.cap + j] = G.cobs[(size_t)l * G.cap + j];
     for (int c = 0; c < 4; c++) G.pgam[((size_t)l * G.cap + j) * 4 + c] = G.cgam[((size_t)l * G.cap + j) * 4 + c];
   }
+}
+
+// Entry points.  k_X runs one group, CTA = environment; k_X_tab runs a table
+// launch over several groups, CTA b = (group map[b].x, environment map[b].y).
+__global__ void __launch_bounds__(256) k_begin(GroupView G, EnvView V, StepArgs a) { begin_body(G, blockIdx.x, V, a); }
+__global__ void __launch_bounds__(256) k_begin_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                   EnvView V, StepArgs a) {
+  const int2 b = map[blockIdx.x];
+  begin_body(tab[b.x], b.y, V, a);
+}
+template <int VPE>
+__global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs a, int k, int residual_only, int tc,
+                                               int pending) {
+  local_body<VPE>(G, blockIdx.x, V, a, k, residual_only, tc, pending);
+}
+template <int VPE>
+__global__ void __launch_bounds__(512) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                   EnvView V, StepArgs a, int k, int residual_only, int tc,
+                                                   int pending) {
+  const int2 b = map[blockIdx.x];
+  local_body<VPE>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
+}
+__global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs a, int tc) {
+  ncp_body(G, blockIdx.x, V, a, tc);
+}
+__global__ void __launch_bounds__(256, 4) k_ncp_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                    EnvView V, StepArgs a, int tc) {
+  const int2 b = map[blockIdx.x];
+  ncp_body(tab[b.x], b.y, V, a, tc);
+}
+__global__ void __launch_bounds__(256) k_end(GroupView G, EnvView V, StepArgs a) { end_body(G, blockIdx.x, V, a); }
+__global__ void __launch_bounds__(256) k_end_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                 EnvView V, StepArgs a) {
+  const int2 b = map[blockIdx.x];
+  end_body(tab[b.x], b.y, V, a);
 }
 
 // user layout [sum n_e][3] <-> group columns [N_g][3][n_pad]
@@ -936,7 +976,13 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_local<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
@@ -1008,6 +1054,109 @@ cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, 
   memset(&v, 0, sizeof v);
   v.n = g.n; v.n_pad = g.n_pad; v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   k_split<<<g.N, 256, sizeof(float) * 3 * g.n, st>>>(v, src);
+  return cudaGetLastError();
+}
+
+namespace {
+
+template <typename T>
+cudaError_t upload_owned(flash_scene *s, T **p, const std::vector<T> &h) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(h.size(), 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(ptr);
+  *p = (T *)ptr;
+  if (!h.empty()) e = cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Resident local-pass CTAs per SM (512 threads, so at most 4) for a CTA with
+// `smem` bytes of dynamic shared memory next to its static shared memory.
+int local_class(size_t smem) {
+  const size_t per_sm = 228 * 1024, static_smem = sizeof(ObsShared) + 1024;
+  const int c = (int)(per_sm / (smem + static_smem + 1024));
+  return std::max(1, std::min(4, c));
+}
+
+}  // namespace
+
+// Group table and block maps for table launches.  Environments of larger
+// meshes come first so their longer CTAs start in the first wave; the local
+// pass is split by element type (template) and by how many of its CTAs fit
+// on one SM, so a small mesh is not launched with a large mesh's shared memory.
+cudaError_t build_batches(flash_scene *s) {
+  const int G = (int)s->groups.size();
+  std::vector<GroupView> tab(G);
+  for (int i = 0; i < G; i++) tab[i] = view(s, s->groups[i]);
+  GroupView *dtab = nullptr;
+  cudaError_t e = upload_owned(s, &dtab, tab);
+  if (e != cudaSuccess) return e;
+  s->gtab = dtab;
+  std::vector<int> order(G);
+  for (int i = 0; i < G; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const Group &a = s->groups[x], &b = s->groups[y];
+    return (int64_t)a.E + a.n > (int64_t)b.E + b.n;
+  });
+  std::vector<int2> all;
+  int nmax = 0;
+  for (int gi : order) {
+    for (int l = 0; l < s->groups[gi].N; l++) all.push_back(make_int2(gi, l));
+    nmax = std::max(nmax, s->groups[gi].n);
+  }
+  s->b_all = Batch();
+  s->b_all.blocks = (int)all.size();
+  if ((e = upload_owned(s, &s->b_all.map, all)) != cudaSuccess) return e;
+  s->ncp_smem_tc = sizeof(float) * 3 * (size_t)nmax;
+  s->b_local.clear();
+  for (int vpe = 3; vpe <= 4; vpe++)
+    for (int cls = 4; cls >= 1; cls--) {
+      Batch b;
+      b.vpe = vpe;
+      std::vector<int2> m;
+      for (int gi : order) {
+        const Group &g = s->groups[gi];
+        if (g.vpe != vpe || local_class(g.smem_local) != cls) continue;
+        for (int l = 0; l < g.N; l++) m.push_back(make_int2(gi, l));
+        b.smem = std::max(b.smem, g.smem_local);
+      }
+      if (m.empty()) continue;
+      b.blocks = (int)m.size();
+      if ((e = upload_owned(s, &b.map, m)) != cudaSuccess) return e;
+      s->b_local.push_back(b);
+    }
+  return cudaSuccess;
+}
+
+cudaError_t launch_begin_all(const flash_scene *s, const StepArgs &a, cudaStream_t st) {
+  k_begin_tab<<<s->b_all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int residual_only, int tc,
+                             cudaStream_t st, int *launched) {
+  const int pending = k > 1;
+  const GroupView *tab = (const GroupView *)s->gtab;
+  for (const Batch &b : s->b_local) {
+    if (b.vpe == 3)
+      k_local_tab<3><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    else
+      k_local_tab<4><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++*launched;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_ncp_all(const flash_scene *s, const StepArgs &a, int tc, cudaStream_t st) {
+  k_ncp_tab<<<s->b_all.blocks, 256, tc ? s->ncp_smem_tc : 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s),
+                                                                   a, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_end_all(const flash_scene *s, const StepArgs &a, cudaStream_t st) {
+  k_end_tab<<<s->b_all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s), a);
   return cudaGetLastError();
 }
 

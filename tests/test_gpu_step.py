@@ -257,6 +257,85 @@ def test_mixed_meshes_one_step(cuda, solve):
 
 
 @pytest.mark.parametrize("solve", SOLVES)
+def test_mixed_meshes_tolerance_mode(cuda, solve):
+    """Mode B on an uneven batch: every environment iterates until its NCP
+    residual is <= 1e-5 (cap 60).  Where the GPU and the oracle stop after the
+    same number of iterations the states agree within the position
+    tolerance; the stop decision itself may differ only where the residual
+    sits at the threshold."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    scs = scenes.mixed_batch(n_envs=8, steps=40, side_choices=(16, 20), tet_targets=(250, 500))
+    s = 22
+    qs, vs, refs = [], [], []
+    for sc in scs:
+        for e in range(sc.n_envs):
+            mesh, st = oracle_state_at(sc, e, s)
+            q0, v0 = _f32(st.q), _f32(st.v)
+            qs.append(q0)
+            vs.append(v0)
+            ref = oracle.EnvState(q0, v0)
+            oracle.step(mesh, sc, e, s, ref, mode=1, tol=1e-5, k_min=1, k_cap=60)
+            refs.append(ref)
+    sim = flash.Sim(scs, solve=solve, mode=1, tol=1e-5, k_min=1, k_cap=60)
+    sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
+                  torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
+    sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
+    sim.set_poses(flash.poses_tensor(scs, s + 1, cuda), which=1)
+    sim.step(1)
+    it, r = sim.stats()
+    it, r = it.cpu().numpy(), r.cpu().numpy()
+    qg = sim.get_state()[0].cpu().numpy()
+    off = sim.offsets
+    same = 0
+    for i, ref in enumerate(refs):
+        if it[i] < 60:
+            assert r[i] <= 1e-5, (i, it[i], r[i])
+        if it[i] == ref.iters:
+            same += 1
+            err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
+            assert err <= POS_TOL, (i, err, it[i])
+        else:
+            assert abs(int(it[i]) - ref.iters) <= 2, (i, it[i], ref.iters)
+    assert same >= 6, (it, [r.iters for r in refs])
+
+
+@pytest.mark.parametrize("solve", SOLVES)
+def test_batched_groups_equal_separate_scenes(cuda, solve):
+    """A scene of several mesh templates runs its per-environment kernels as
+    table launches over all groups and its contractions on a stream pool;
+    stepping it must give bit-identical states to stepping each template in a
+    scene of its own."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    scs = scenes.mixed_batch(n_envs=12, steps=12, side_choices=(16, 24), tet_targets=(250, 600))
+    assert len(scs) >= 3
+    big = flash.Sim(scs, solve=solve)
+    q0, v0 = flash.state_tensors(scs, cuda)
+    big.set_state(q0, v0)
+    big.set_poses(flash.poses_tensor(scs, 0, cuda), which=0)
+    for s in range(3):
+        big.set_poses(flash.poses_tensor(scs, s + 1, cuda))
+        big.step(1)
+    qb = big.get_state()[0].cpu().numpy()
+    off = big.offsets
+    env0 = 0
+    for sc in scs:
+        one = flash.Sim(sc, solve=solve, contact_cap=big.desc.contact_cap)
+        q1, v1 = flash.state_tensors(sc, cuda)
+        one.set_state(q1, v1)
+        one.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        for s in range(3):
+            one.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            one.step(1)
+        q = one.get_state()[0].cpu().numpy()
+        part = qb[off[env0]:off[env0 + sc.n_envs]]
+        assert np.array_equal(part, q), (sc.name, np.abs(part - q).max())
+        env0 += sc.n_envs
+    assert big.status() == 0
+
+
+@pytest.mark.parametrize("solve", SOLVES)
 def test_global_apply_eigen_form(cuda, solve):
     """Per-environment stiffness on one tet mesh: the library applies
     A_e^-1 = V diag(1/(1 + k_e lam)) V^T with one shared eigenbasis; each
