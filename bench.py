@@ -372,7 +372,7 @@ def main():
         params, hist, held = warmstart.train(X, T, epochs=2, batch=4096, lr=1e-3)
         first += 6
         ms_c, conv_c, _ = timed_steps(first)
-        sim.warmstart(params, flash.WARM_LEARNED)
+        sim.warmstart(params, flash.WARM_LEARNED, bounds=warmstart.input_range(X, T))
         ms_l, conv_l, _ = timed_steps(first + args.steps)
         sim.warmstart(None, flash.WARM_COLD)
         v_c, _ = aggregate(ms_c, conv_c / args.steps, world, dev)

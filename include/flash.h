@@ -194,14 +194,16 @@ int64_t flash_launch_count(const flash_scene *s);
  * flash_warmstart_set: mode = FLASH_WARM_*; params (device, copied) are
  * required for FLASH_WARM_LEARNED; flags (use_dq): bit 0 also moves contact
  * vertices to the predicted first iterate, bit 1 keeps only the normal
- * multiplier.  Contacts whose features exceed 100 in magnitude (outside the
- * trained range) start cold.
+ * multiplier.  A contact whose features leave the trained input range
+ * starts cold: flash_warmstart_bounds sets that range per feature (host
+ * arrays lo[10], hi[10], lo <= hi, copied; default -100..100).
  * flash_record_contacts: while enabled every step stores features (at the
  * start) and targets (converged multipliers and q - q~, same units) of all
  * contacts; flash_get_recorded copies the last step's rows (environments in
  * group order) into device X [rows][10] and T [rows][6], synchronising.
  * Targets of environments whose final residual exceeds tol_ncp are NaN. */
 flash_status flash_warmstart_set(flash_scene *s, const float *params, int32_t mode, int32_t use_dq);
+flash_status flash_warmstart_bounds(flash_scene *s, const float *lo, const float *hi);
 flash_status flash_record_contacts(flash_scene *s, int32_t enable);
 flash_status flash_get_recorded(flash_scene *s, float *X, float *T, int64_t max_rows, int64_t *rows, void *stream);
 

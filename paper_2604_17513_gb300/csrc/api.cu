@@ -150,19 +150,6 @@ Hinges bending_hinges(const MeshTemplate &m) {
   return out;
 }
 
-// CSR incidence vertex -> slot (4 * item + local index)
-void incidence(int n, const std::vector<int> &items, int per, std::vector<int> &off, std::vector<int> &idx) {
-  off.assign(n + 1, 0);
-  size_t cnt = items.size() / per;
-  for (size_t t = 0; t < cnt; t++)
-    for (int a = 0; a < per; a++) off[items[t * per + a] + 1]++;
-  for (int i = 0; i < n; i++) off[i + 1] += off[i];
-  idx.assign(off[n], 0);
-  std::vector<int> fill(off.begin(), off.end() - 1);
-  for (size_t t = 0; t < cnt; t++)
-    for (int a = 0; a < per; a++) idx[fill[items[t * per + a]]++] = (int)(4 * t + a);
-}
-
 flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   const MeshTemplate &m = s->meshes[g.mesh];
   const double h = s->d.h, h2 = h * h;
@@ -187,14 +174,6 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
     for (int t = 0; t < 12; t++) Df[(size_t)e * 12 + t] = (float)ed.D[(size_t)e * 12 + t];
     wt[e] = (float)(h2 * m.w_stretch * (g.eig ? 1.0 : g.stiff) * ed.size[e]);
   }
-  std::vector<float> hc(hg.k.size());
-  for (int t = 0; t < g.H; t++)
-    for (int a = 0; a < 4; a++) hc[4 * t + a] = (float)(hg.k[4 * t + a] * std::sqrt(h2 * m.w_bend * hg.s[t]));
-  std::vector<int> elist((size_t)m.E * g.vpe);
-  for (size_t i = 0; i < elist.size(); i++) elist[i] = m.elems[i];
-  std::vector<int> v2e_off, v2e, v2h_off, v2h;
-  incidence(n, elist, g.vpe, v2e_off, v2e);
-  incidence(n, hg.v, 4, v2h_off, v2h);
   std::vector<float> massf(np, 0.f);
   for (int i = 0; i < n; i++) massf[i] = (float)m.mass[i];
   std::vector<int> genv(g.env_ids.begin(), g.env_ids.end());
@@ -202,38 +181,43 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(upload(s, &g.elems, el));
   FLASH_CUDA_TRY(upload(s, &g.D, Df));
   FLASH_CUDA_TRY(upload(s, &g.wt, wt));
-  std::vector<int> hv(hg.v.begin(), hg.v.end());
-  FLASH_CUDA_TRY(upload(s, &g.hv, hv));
-  FLASH_CUDA_TRY(upload(s, &g.hc, hc));
-  FLASH_CUDA_TRY(upload(s, &g.v2e_off, v2e_off));
-  FLASH_CUDA_TRY(upload(s, &g.v2e, v2e));
-  FLASH_CUDA_TRY(upload(s, &g.v2h_off, v2h_off));
-  FLASH_CUDA_TRY(upload(s, &g.v2h, v2h));
   FLASH_CUDA_TRY(upload(s, &g.mass, massf));
   {
-    // fixed-degree incidence tables (empty slots: element/hinge 0, zero coefficients)
-    g.deg_e = 0;
-    g.deg_h = 0;
-    for (int i = 0; i < n; i++) {
-      g.deg_e = std::max(g.deg_e, v2e_off[i + 1] - v2e_off[i]);
-      g.deg_h = std::max(g.deg_h, v2h_off[i + 1] - v2h_off[i]);
+    // CSR vertex -> element slots (e * vpe + a), incidence order
+    g.ev = m.E * g.vpe;
+    if (g.ev > 65534) return fail(FLASH_EINVAL, "mesh has more than 65534 element-vertex slots");
+    std::vector<uint16_t> coff((size_t)n + 2, 0), cidx((size_t)g.ev + 1, 0);
+    for (int e = 0; e < m.E; e++)
+      for (int a = 0; a < g.vpe; a++) coff[el[(size_t)e * 4 + a] + 1]++;
+    for (int i = 0; i < n; i++) coff[i + 1] += coff[i];
+    std::vector<int> fill(coff.begin(), coff.begin() + n);
+    for (int e = 0; e < m.E; e++)
+      for (int a = 0; a < g.vpe; a++) cidx[fill[el[(size_t)e * 4 + a]]++] = (uint16_t)(e * g.vpe + a);
+    coff.resize(((size_t)n + 2) & ~(size_t)1);      // even length: copied as 4-byte words
+    cidx.resize(((size_t)g.ev + 1) & ~(size_t)1);
+    FLASH_CUDA_TRY(upload(s, &g.coff, coff));
+    FLASH_CUDA_TRY(upload(s, &g.cidx, cidx));
+    // bending operator K_b = sum_h c_h k_h k_h^T (c_h = h^2 w_b 3 / (A0 + A1));
+    // its rows sum to zero, so the residual uses sum_{j != i} K_ij (q_j - q_i)
+    std::vector<std::map<int, double>> rows(n);
+    for (int t = 0; t < g.H; t++) {
+      const double c = h2 * m.w_bend * hg.s[t];
+      for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++)
+          if (hg.v[4 * t + a] != hg.v[4 * t + b])
+            rows[hg.v[4 * t + a]][hg.v[4 * t + b]] += c * hg.k[4 * t + a] * hg.k[4 * t + b];
     }
-    std::vector<int4> ell_e((size_t)std::max(g.deg_e, 1) * np, int4{0, 0, 0, 0});
-    std::vector<int2> ell_h((size_t)std::max(g.deg_h, 1) * np, int2{0, 0});
+    g.deg_b = 0;
+    for (int i = 0; i < n; i++) g.deg_b = std::max(g.deg_b, (int)rows[i].size());
+    std::vector<int2> kb((size_t)std::max(g.deg_b, 1) * np);
     auto bits = [](float f) { int b; std::memcpy(&b, &f, 4); return b; };
+    for (int i = 0; i < np; i++)
+      for (int t = 0; t < std::max(g.deg_b, 1); t++) kb[(size_t)t * np + i] = int2{i < n ? i : 0, 0};
     for (int i = 0; i < n; i++) {
-      for (int t = v2e_off[i]; t < v2e_off[i + 1]; t++) {
-        const int slot = v2e[t], el = slot >> 2, a = slot & 3;
-        const float *D = &Df[(size_t)el * 12 + 3 * a];
-        ell_e[(size_t)(t - v2e_off[i]) * np + i] = int4{el, bits(D[0]), bits(D[1]), bits(D[2])};
-      }
-      for (int t = v2h_off[i]; t < v2h_off[i + 1]; t++) {
-        const int slot = v2h[t], hh = slot >> 2, a = slot & 3;
-        ell_h[(size_t)(t - v2h_off[i]) * np + i] = int2{hh, bits(hc[4 * hh + a])};
-      }
+      int t = 0;
+      for (auto &kv : rows[i]) kb[(size_t)(t++) * np + i] = int2{kv.first, bits((float)kv.second)};
     }
-    FLASH_CUDA_TRY(upload(s, &g.ell_e, ell_e));
-    FLASH_CUDA_TRY(upload(s, &g.ell_h, ell_h));
+    FLASH_CUDA_TRY(upload(s, &g.kb, kb));
   }
   if (g.eig) {
     // per-environment stiffness: A_e = M + k_e L with L = h^2 w sum vol D D^T.
@@ -352,21 +336,34 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.pvert, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pgam, cc * 4));
-  size_t per_env = (size_t)g.E * g.nc * 3 + (size_t)g.H * 3;
-  size_t full = sizeof(float) * (6 * (size_t)n + per_env);
-  if (full <= 200 * 1024) {
-    g.p_in_smem = true;
-    g.smem_local = full;
+  // local pass shared memory: q and r ([3][ns] each, ns = n rounded up to 4),
+  // then the element forces [ev + 1][3] (last row zero) and the CSR tables
+  const size_t ns = ((size_t)n + 3) & ~(size_t)3;
+  const size_t base = sizeof(float) * 6 * ns;
+  const size_t forces = sizeof(float) * 3 * ((size_t)g.ev + 1);
+  const size_t tables = sizeof(uint16_t) * ((((size_t)n + 2) & ~(size_t)1) + (((size_t)g.ev + 1) & ~(size_t)1));
+  if (base + forces + tables <= 200 * 1024) {
+    g.c_in_smem = true;
+    g.smem_local = base + forces + tables;
   } else {
-    g.p_in_smem = false;
-    g.smem_local = sizeof(float) * 6 * (size_t)n;
+    g.c_in_smem = false;
+    g.smem_local = base;
     if (g.smem_local > 200 * 1024) return fail(FLASH_EINVAL, "mesh too large for one CTA per environment");
-    FLASH_CUDA_TRY(dalloc(s, &g.pscratch, per_env * g.N));
+    FLASH_CUDA_TRY(dalloc(s, &g.cscratch, 3 * ((size_t)g.ev + 1) * g.N));
   }
   return FLASH_OK;
 }
 
+// default input range of the warm-start network: |feature| <= 100
+constexpr float kDefaultFeatureBound = 100.f;
+
 cudaError_t ensure_learn_buffers(flash_scene *s) {
+  if (!s->ws_bounds) {
+    std::vector<float> b(20);
+    for (int c = 0; c < 10; c++) { b[c] = -kDefaultFeatureBound; b[10 + c] = kDefaultFeatureBound; }
+    cudaError_t e = upload(s, &s->ws_bounds, b);
+    if (e != cudaSuccess) return e;
+  }
   for (auto &g : s->groups) {
     if (g.row_off) continue;
     size_t rows = (size_t)g.N * s->cap;
@@ -467,16 +464,6 @@ cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, fl
     return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st)
               : gemm_simt(g, g.Vt, g.y, out, nullptr, s->done, 0, nullptr, nullptr, st);
   });
-}
-
-cudaError_t global_solves(flash_scene *s, const Group &g, const StepArgs &a0, cudaStream_t st) {
-  const StepArgs a = group_args(a0, g);
-  // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq, applied by the next local pass)
-  cudaError_t e = apply_inverse(s, g, g.r, g.w, st);
-  if (e != cudaSuccess) return e;
-  e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp(s, g, a, use_tc(s) ? 1 : 0, st); });
-  if (e != cudaSuccess) return e;
-  return apply_inverse(s, g, g.f, g.dq, st);
 }
 
 // Multi-group scenes: the per-group contractions of one phase run on the pool
@@ -700,8 +687,8 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
+  FLASH_CUDA_TRY(build_batches(s));
   if (s->groups.size() > 1) {
-    FLASH_CUDA_TRY(build_batches(s));
     const size_t P = std::min<size_t>(s->groups.size(), kPoolStreams);
     for (size_t i = 0; i < P; i++) {
       cudaStream_t ps;
@@ -783,13 +770,9 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const StepArgs a = step_args(s);
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
-  // several groups: per-environment kernels as table launches over all
-  // groups, contractions per group on the stream pool
-  const bool batched = s->groups.size() > 1;
+  // per-environment kernels: table launches over every group; contractions
+  // per group (on the stream pool when there are several groups)
   auto local = [&](int k, int residual_only) -> cudaError_t {
-    if (!batched)
-      return timed(s, FLASH_KIND_LOCAL, st,
-                   [&] { return launch_local(s, s->groups[0], group_args(a, s->groups[0]), k, residual_only, tc, st); });
     int launched = 0;
     const cudaError_t e =
         timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local_all(s, a, k, residual_only, tc, st, &launched); });
@@ -797,15 +780,14 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
     return e;
   };
   auto solves = [&]() -> cudaError_t {
-    if (!batched) return global_solves(s, s->groups[0], a, st);
+    // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq, applied by the next local pass)
     cudaError_t e = apply_all(s, st, [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
     if (e == cudaSuccess) e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp_all(s, a, tc, st); });
     if (e == cudaSuccess) e = apply_all(s, st, [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
     return e;
   };
   for (int step = 0; step < n_steps; step++) {
-    if (batched) FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin_all(s, a, st); }));
-    else FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin(s, s->groups[0], group_args(a, s->groups[0]), st); }));
+    FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin_all(s, a, st); }));
     if (learned || s->record) {
       for (auto &g : s->groups) {
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_row_offsets(g, g.row_off, st); }));
@@ -815,7 +797,7 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
             return mlp_forward(s->mlp_params, g.feat, g.pred, g.row_off + g.N, (int64_t)g.N * s->cap, st);
           }));
           FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st,
-                               [&] { return launch_apply_learned(s, g, group_args(a, g), g.row_off, g.feat, g.pred, s->use_dq, st); }));
+                               [&] { return launch_apply_learned(s, g, group_args(a, g), g.row_off, g.feat, g.pred, s->ws_bounds, s->use_dq, st); }));
         }
       }
     }
@@ -838,8 +820,7 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
     if (s->record)
       for (auto &g : s->groups)
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, group_args(a, g), g.row_off, g.targ, st); }));
-    if (batched) FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end_all(s, a, st); }));
-    else FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end(s, s->groups[0], group_args(a, s->groups[0]), st); }));
+    FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end_all(s, a, st); }));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
   }
   return FLASH_OK;
@@ -858,6 +839,20 @@ flash_status flash_warmstart_set(flash_scene *s, const float *params, int32_t mo
   }
   s->d.warm = mode;
   s->use_dq = use_dq;
+  return FLASH_OK;
+}
+
+flash_status flash_warmstart_bounds(flash_scene *s, const float *lo, const float *hi) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (!lo || !hi) return fail(FLASH_EINVAL, "null bounds");
+  std::vector<float> b(20);
+  for (int c = 0; c < 10; c++) {
+    if (!(lo[c] <= hi[c])) return fail(FLASH_EINVAL, "warm-start bounds need lo <= hi");
+    b[c] = lo[c];
+    b[10 + c] = hi[c];
+  }
+  FLASH_CUDA_TRY(ensure_learn_buffers(s));
+  FLASH_CUDA_TRY(cudaMemcpy(s->ws_bounds, b.data(), sizeof(float) * 20, cudaMemcpyHostToDevice));
   return FLASH_OK;
 }
 

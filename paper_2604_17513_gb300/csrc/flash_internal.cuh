@@ -56,14 +56,16 @@ struct Group {
   int *elems = nullptr;       // [E][4]
   float *D = nullptr;         // [E][12]
   float *wt = nullptr;        // [E]
-  int *hv = nullptr;          // [H][4]
-  float *hc = nullptr;        // [H][4]
-  int *v2e_off = nullptr, *v2e = nullptr;
-  int *v2h_off = nullptr, *v2h = nullptr;
-  // fixed-degree incidence, vertex fastest: slot k of vertex i at [k * n_pad + i]
-  int4 *ell_e = nullptr;                  // {element, D[a][0..2] as float bits}; empty slots are zero
-  int2 *ell_h = nullptr;                  // {hinge, coefficient bits}; empty slots are zero
-  int deg_e = 0, deg_h = 0;
+  // element -> vertex forces are summed per vertex through CSR tables over
+  // the slots e * vpe + a (element e, local vertex a), in incidence order
+  uint16_t *coff = nullptr;   // [n + 1, padded to even] slot offsets
+  uint16_t *cidx = nullptr;   // [E * vpe, padded to even] slots
+  int ev = 0;                 // E * vpe
+  // bending as a constant operator K_b (rows sum to zero), off-diagonal
+  // entries slot-major: entry t of vertex i at [t * n_pad + i] = {j, K_ij bits};
+  // empty entries are {i, 0}
+  int2 *kb = nullptr;
+  int deg_b = 0;
   float *mass = nullptr;      // [n]
   // explicit inverse (groups with one stiffness) ...
   SolveMat inv;
@@ -86,8 +88,8 @@ struct Group {
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
   size_t smem_local = 0;
-  bool p_in_smem = true;
-  float *pscratch = nullptr;              // element projections when they do not fit in smem
+  bool c_in_smem = true;                  // element forces and CSR tables in shared memory
+  float *cscratch = nullptr;              // element forces [N][ev + 1][3] when they do not fit
   int *status = nullptr;                  // scene status word (device)
   // learned warm start / recording (allocated on first use)
   int64_t *row_off = nullptr;             // [N + 1] compact contact rows
@@ -136,6 +138,7 @@ struct flash_scene {
   size_t ev_used = 0;
   std::vector<int> ev_kind;   // kind of each recorded pair
   float *mlp_params = nullptr;   // warm-start network (device, flat)
+  float *ws_bounds = nullptr;    // warm-start input range [lo 10][hi 10] (device)
   int use_dq = 0;
   bool record = false;
   double prof_ms[FLASH_NUM_KINDS] = {0};
@@ -169,16 +172,11 @@ struct StepArgs {
   int k_min, k_cap, mode, warm, K, cap;
 };
 cudaError_t configure_kernels();
-cudaError_t launch_begin(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st);
-cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a, int k, int residual_only,
-                         int tc, cudaStream_t st);
-cudaError_t launch_ncp(const flash_scene *s, const Group &g, const StepArgs &a, int tc, cudaStream_t st);
-cudaError_t launch_end(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_row_offsets(const Group &g, int64_t *off, cudaStream_t st);
 cudaError_t launch_features(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *X,
                             cudaStream_t st);
 cudaError_t launch_apply_learned(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off,
-                                 const float *X, const float *Y, int flags, cudaStream_t st);
+                                 const float *X, const float *Y, const float *bounds, int flags, cudaStream_t st);
 cudaError_t launch_targets(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *T,
                            cudaStream_t st);
 int mlp_num_params();
@@ -189,7 +187,7 @@ cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q
 cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,
                           int to_user, cudaStream_t st);
 cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
-// table launches over every group of a scene (build_batches first)
+// table launches over every group of a scene (build_batches at finalize)
 cudaError_t build_batches(flash_scene *s);
 cudaError_t launch_begin_all(const flash_scene *s, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int residual_only, int tc,

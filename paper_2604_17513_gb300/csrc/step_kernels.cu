@@ -21,18 +21,18 @@ namespace {
 
 struct GroupView {
   int n, n_pad, E, H, vpe, nc, type, cap;
-  const int *genv, *elems, *hv, *v2e_off, *v2e, *v2h_off, *v2h;
-  const float *D, *wt, *hc, *mass;
+  const int *genv, *elems;
+  const float *D, *wt, *mass;
   float *q, *v, *qt, *qp, *r, *f, *w, *dq;
   __half *rh, *rl;
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
-  const int4 *ell_e;
-  const int2 *ell_h;
-  int deg_e, deg_h;
+  const uint16_t *coff, *cidx;   // CSR vertex -> element slots e * vpe + a
+  const int2 *kb;                // bending operator, off-diagonal entries, slot-major
+  int ev, deg_b;
   const float *kenv;   // per-environment stiffness scale (eigen-form groups), else null
-  float *cgam, *pgam, *pscratch;
-  int p_in_smem;
+  float *cgam, *pgam, *cscratch;
+  int c_in_smem;
   float tau;           // contact thickness of the group's mesh
 };
 
@@ -46,14 +46,13 @@ struct EnvView {
 GroupView view(const flash_scene *s, const Group &g) {
   GroupView v;
   v.n = g.n; v.n_pad = g.n_pad; v.E = g.E; v.H = g.H; v.vpe = g.vpe; v.nc = g.nc; v.type = g.type; v.cap = s->cap;
-  v.genv = g.genv; v.elems = g.elems; v.hv = g.hv; v.v2e_off = g.v2e_off; v.v2e = g.v2e;
-  v.v2h_off = g.v2h_off; v.v2h = g.v2h; v.D = g.D; v.wt = g.wt; v.hc = g.hc; v.mass = g.mass;
+  v.genv = g.genv; v.elems = g.elems; v.D = g.D; v.wt = g.wt; v.mass = g.mass;
   v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w; v.dq = g.dq;
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
-  v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.pscratch = g.pscratch;
-  v.p_in_smem = g.p_in_smem ? 1 : 0;
-  v.ell_e = g.ell_e; v.ell_h = g.ell_h; v.deg_e = g.deg_e; v.deg_h = g.deg_h;
+  v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch;
+  v.c_in_smem = g.c_in_smem ? 1 : 0;
+  v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
   v.kenv = g.eig ? g.kenv : nullptr;
   v.tau = (float)g.tau;
   return v;
@@ -213,16 +212,16 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
 // local step + residual
 // ---------------------------------------------------------------------------
 // Write one environment's three columns in f16 hi/lo with a power-of-two
-// scale per column (tensor-core RHS); vals in shared memory [3][n].  Each
+// scale per column (tensor-core RHS); vals in shared memory [3][ld].  Each
 // thread passes the maxima of |vals| it already knows (or 0); the kernel
 // completes them over the rows this thread owns and reduces once.
-__device__ void write_split_columns(const GroupView &G, int l, const float *vals, float (*sh3)[3], bool scan,
+__device__ void write_split_columns(const GroupView &G, int l, const float *vals, int ld, float (*sh3)[3], bool scan,
                                     float m0 = 0.f, float m1 = 0.f, float m2 = 0.f) {
   const int n = G.n, np = G.n_pad;
   float m[3] = {m0, m1, m2};
   if (scan)
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-      for (int c = 0; c < 3; c++) m[c] = fmaxf(m[c], fabsf(vals[c * n + i]));
+      for (int c = 0; c < 3; c++) m[c] = fmaxf(m[c], fabsf(vals[c * ld + i]));
   block_max3(m[0], m[1], m[2], sh3);
   for (int c = 0; c < 3; c++) {
     int ex = 0;
@@ -238,8 +237,8 @@ __device__ void write_split_columns(const GroupView &G, int l, const float *vals
     if (threadIdx.x == 0) G.rscale[col] = ldexpf(1.f, -ex);
     __half2 *hh = reinterpret_cast<__half2 *>(G.rh + col * np), *hl = reinterpret_cast<__half2 *>(G.rl + col * np);
     for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
-      const float x0 = 2 * i < n ? vals[c * n + 2 * i] * sc : 0.f;
-      const float x1 = 2 * i + 1 < n ? vals[c * n + 2 * i + 1] * sc : 0.f;
+      const float x0 = 2 * i < n ? vals[c * ld + 2 * i] * sc : 0.f;
+      const float x1 = 2 * i + 1 < n ? vals[c * ld + 2 * i + 1] * sc : 0.f;
       const __half2 xh = __floats2half2_rn(x0, x1);
       hh[i] = xh;
       const float2 back = __half22float2(xh);
@@ -285,100 +284,138 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
   __shared__ ObsShared O;
   a.tau = G.tau;
   const int e = G.genv[l];
-  const int n = G.n, np = G.n_pad;
+  const int n = G.n, np = G.n_pad, ns = (n + 3) & ~3;
   if (V.done[e]) return;
-  float *qs = smem;           // [3][n]
-  float *rs = qs + 3 * n;     // [3][n]
-  float *Ps, *Ss;
-  if (G.p_in_smem) {
-    Ps = rs + 3 * n;          // [E][nc*3]
-    Ss = Ps + (size_t)G.E * nc * 3;  // [H][3]
+  float *qs = smem;             // [3][ns]
+  float *rs = qs + 3 * ns;      // [3][ns]
+  float *Fs;                    // element forces on their vertices [ev][3]
+  const uint16_t *coff, *cidx;  // CSR vertex -> slots of Fs
+  if (G.c_in_smem) {
+    Fs = rs + 3 * ns;
+    uint32_t *t = reinterpret_cast<uint32_t *>(Fs + 3 * (G.ev + 1));
+    const int w_off = (n + 2) >> 1, w_idx = (G.ev + 1) >> 1;   // table sizes in 4-byte words
+    const uint32_t *src_off = reinterpret_cast<const uint32_t *>(G.coff);
+    const uint32_t *src_idx = reinterpret_cast<const uint32_t *>(G.cidx);
+    for (int i = threadIdx.x; i < w_off; i += blockDim.x) t[i] = __ldg(src_off + i);
+    for (int i = threadIdx.x; i < w_idx; i += blockDim.x) t[w_off + i] = __ldg(src_idx + i);
+    coff = reinterpret_cast<const uint16_t *>(t);
+    cidx = coff + 2 * w_off;
   } else {
-    Ps = G.pscratch + (size_t)l * ((size_t)G.E * nc * 3 + (size_t)G.H * 3);
-    Ss = Ps + (size_t)G.E * nc * 3;
+    Fs = G.cscratch + (size_t)l * 3 * (G.ev + 1);
+    coff = G.coff;
+    cidx = G.cidx;
   }
   // q^{k-1} = q^{k-2} + w + A^-1 J^T dgamma: the previous iteration's position
-  // update (Eq. correction in correction form) is applied here, while the
-  // state is loaded, so both global solves keep a store-only epilogue
+  // update (correction form) is applied here, while the state is loaded, so
+  // both global solves keep a store-only epilogue.  Columns are 16-byte
+  // aligned (n_pad is a multiple of 128); the padding reads as zero.
   float *q = G.q + (size_t)l * 3 * np;
+  const int n4 = ns >> 2;
   if (pending) {
     const float *w = G.w + (size_t)l * 3 * np, *dq = G.dq + (size_t)l * 3 * np;
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-      const int c = i / n, j = i - c * n;
-      const float x = q[c * np + j] + w[c * np + j] + dq[c * np + j];
-      qs[i] = x;
-      q[c * np + j] = x;
+    for (int i = threadIdx.x; i < 3 * n4; i += blockDim.x) {
+      const int c = i / n4, j = (i - c * n4) * 4;
+      float4 x = *reinterpret_cast<const float4 *>(q + c * np + j);
+      const float4 u = *reinterpret_cast<const float4 *>(w + c * np + j);
+      const float4 d = *reinterpret_cast<const float4 *>(dq + c * np + j);
+      x.x = x.x + u.x + d.x; x.y = x.y + u.y + d.y; x.z = x.z + u.z + d.z; x.w = x.w + u.w + d.w;
+      *reinterpret_cast<float4 *>(q + c * np + j) = x;
+      *reinterpret_cast<float4 *>(qs + c * ns + j) = x;
     }
   } else {
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-      const int c = i / n, j = i - c * n;
-      qs[i] = q[c * np + j];
+    for (int i = threadIdx.x; i < 3 * n4; i += blockDim.x) {
+      const int c = i / n4, j = (i - c * n4) * 4;
+      *reinterpret_cast<float4 *>(qs + c * ns + j) = *reinterpret_cast<const float4 *>(q + c * np + j);
     }
   }
   load_obstacles(V, e, a.K, O);
   __syncthreads();
   if (!residual_only) {
     const float ks = G.kenv ? G.kenv[l] : 1.f;
-    // ---- local projection p_i = closest rotation to F_i = G_i q; store w~(p - F)
+    // ---- local projection p_i = closest rotation to F_i = G_i q, and the
+    //      element's forces w~ D_a^T (p - F) on each of its vertices a.
+    //      F is formed from edge differences (the operator annihilates
+    //      translations), which keeps |q| out of its rounding.
     for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
       const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
       const float *D = G.D + 12 * el;
-      float F[9], R[9], Dl[12];
+      float F[9], R[9], P[9], Dl[12];
 #pragma unroll
       for (int t = 0; t < 3 * vpe; t++) Dl[t] = __ldg(D + t);
 #pragma unroll
-      for (int c = 0; c < 3; c++)
+      for (int c = 0; c < 3; c++) {
+        const float x0 = qs[c * ns + vv[0]];
+        float dx[vpe - 1];
+#pragma unroll
+        for (int aa = 1; aa < vpe; aa++) dx[aa - 1] = qs[c * ns + vv[aa]] - x0;
 #pragma unroll
         for (int j = 0; j < nc; j++) {
           float s = 0.f;
 #pragma unroll
-          for (int aa = 0; aa < vpe; aa++) s += qs[c * n + vv[aa]] * Dl[aa * 3 + j];
+          for (int aa = 1; aa < vpe; aa++) s += dx[aa - 1] * Dl[aa * 3 + j];
           F[nc * c + j] = s;
         }
+      }
       if constexpr (nc == 2) closest_rot32(F, R);
       else closest_rot33(F, R);
       const float wt = __ldg(G.wt + el) * ks;
-      float *P = Ps + (size_t)el * nc * 3;
 #pragma unroll
       for (int t = 0; t < 3 * nc; t++) P[t] = wt * (R[t] - F[t]);
-    }
-    for (int hh = threadIdx.x; hh < G.H; hh += blockDim.x) {
-      const int4 vi = *reinterpret_cast<const int4 *>(G.hv + 4 * hh);
-      const float4 cc = *reinterpret_cast<const float4 *>(G.hc + 4 * hh);
-      for (int c = 0; c < 3; c++)
-        Ss[hh * 3 + c] = cc.x * qs[c * n + vi.x] + cc.y * qs[c * n + vi.y] + cc.z * qs[c * n + vi.z] +
-                         cc.w * qs[c * n + vi.w];
-    }
-    __syncthreads();
-    // ---- residual r = M (q~ - q) + sum G^T w~ (p - G q) - bending
-    const float *qp = G.qp + (size_t)l * 3 * np;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float m = __ldg(G.mass + i);
-      float acc[3];
-      for (int c = 0; c < 3; c++) acc[c] = m * (qp[c * np + i] - qs[c * n + i]);
-      // incident elements: sum_e D_e[a]^T P_e (P_e = w~ (p_e - F_e))
-#pragma unroll 4
-      for (int t = 0; t < G.deg_e; t++) {
-        const int4 sl = __ldg(G.ell_e + (size_t)t * np + i);
-        const float *P = Ps + (size_t)sl.x * nc * 3;
-        const float d[3] = {__int_as_float(sl.y), __int_as_float(sl.z), __int_as_float(sl.w)};
+      float *Fe = Fs + (size_t)el * vpe * 3;
+#pragma unroll
+      for (int aa = 0; aa < vpe; aa++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           float s = 0.f;
 #pragma unroll
-          for (int j = 0; j < nc; j++) s += d[j] * P[nc * c + j];
-          acc[c] += s;
+          for (int j = 0; j < nc; j++) s += Dl[aa * 3 + j] * P[nc * c + j];
+          Fe[aa * 3 + c] = s;
+        }
+    }
+    // ---- per vertex: inertia M (q~ - q) and bending - sum_j K_ij (q_j - q_i).
+    //      The operator's rows sum to zero; the terms are large and cancel.
+    //      Summed naively, each vertex's rounding errors would add up to a net
+    //      force over the mesh that the rigid modes of A^-1 amplify, so the
+    //      products and sums use error-free transforms (the row is rounded
+    //      once); the operations are explicitly rounded, out of FMA contraction.
+    const float *qp = G.qp + (size_t)l * 3 * np;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float m = __ldg(G.mass + i);
+      const float x[3] = {qs[i], qs[ns + i], qs[2 * ns + i]};
+      float sum[3] = {0.f, 0.f, 0.f}, err[3] = {0.f, 0.f, 0.f};
+#pragma unroll 2
+      for (int t = 0; t < G.deg_b; t++) {
+        const int2 kj = __ldg(G.kb + (size_t)t * np + i);
+        const float kk = __int_as_float(kj.y);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const float d = __fsub_rn(qs[c * ns + kj.x], x[c]);
+          const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
+          const float s1 = __fadd_rn(sum[c], pr), bp = __fsub_rn(s1, sum[c]);
+          const float se = __fadd_rn(__fsub_rn(sum[c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
+          sum[c] = s1;
+          err[c] = __fadd_rn(err[c], __fadd_rn(se, pe));
         }
       }
-      // incident hinges: - c_a S_h
-#pragma unroll 4
-      for (int t = 0; t < G.deg_h; t++) {
-        const int2 sl = __ldg(G.ell_h + (size_t)t * np + i);
-        const float cc = __int_as_float(sl.y);
-        for (int c = 0; c < 3; c++) acc[c] -= cc * Ss[sl.x * 3 + c];
+      rs[i] = m * (qp[i] - x[0]) - (sum[0] + err[0]);
+      rs[ns + i] = m * (qp[np + i] - x[1]) - (sum[1] + err[1]);
+      rs[2 * ns + i] = m * (qp[2 * np + i] - x[2]) - (sum[2] + err[2]);
+    }
+    __syncthreads();
+    // ---- residual r = M (q~ - q) + sum_e D_a^T w~ (p_e - F_e) - bending
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float acc0 = rs[i], acc1 = rs[ns + i], acc2 = rs[2 * ns + i];
+      const int t1 = coff[i + 1];
+      for (int t = coff[i]; t < t1; t++) {
+        const float *f = Fs + 3 * (int)cidx[t];
+        acc0 += f[0];
+        acc1 += f[1];
+        acc2 += f[2];
       }
-      for (int c = 0; c < 3; c++) rs[c * n + i] = acc[c];
+      rs[i] = acc0;
+      rs[ns + i] = acc1;
+      rs[2 * ns + i] = acc2;
     }
   }
   __syncthreads();
@@ -393,7 +430,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j];
     if (j > 0 && cvert[j - 1] == vtx) continue;
-    const V3 x = v3(qs[vtx], qs[n + vtx], qs[2 * n + vtx]);
+    const V3 x = v3(qs[vtx], qs[ns + vtx], qs[2 * ns + vtx]);
     const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
     const float mv = __ldg(G.mass + vtx);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -411,8 +448,8 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     }
     if (!residual_only) {
       rs[vtx] += fx;
-      rs[n + vtx] += fy;
-      rs[2 * n + vtx] += fz;
+      rs[ns + vtx] += fy;
+      rs[2 * ns + vtx] += fz;
     }
   }
   rmax = block_max(rmax, sh_red);
@@ -434,12 +471,12 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
   __syncthreads();
   if (s_done) return;
   if (tc) {
-    write_split_columns(G, l, rs, sh3, true);
+    write_split_columns(G, l, rs, ns, sh3, true);
   } else {
     float *r = G.r + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
       int c = i / n, j = i - c * n;
-      r[c * np + j] = rs[i];
+      r[c * np + j] = rs[c * ns + j];
     }
   }
 }
@@ -718,7 +755,7 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
   if (tc) {
     __syncthreads();
     // every nonzero row of fs was written by this block with its max tracked
-    write_split_columns(G, l, fs, sh3, false, fm0, fm1, fm2);
+    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
   }
 }
 
@@ -745,35 +782,26 @@ __device__ __forceinline__ void end_body(const GroupView &G, const int l, const 
   }
 }
 
-// Entry points.  k_X runs one group, CTA = environment; k_X_tab runs a table
-// launch over several groups, CTA b = (group map[b].x, environment map[b].y).
-__global__ void __launch_bounds__(256) k_begin(GroupView G, EnvView V, StepArgs a) { begin_body(G, blockIdx.x, V, a); }
+// Entry points: table launches over the environments of one or more groups,
+// CTA b = (group map[b].x, environment map[b].y).  Every scene, one group or
+// many, runs these same kernels.
 __global__ void __launch_bounds__(256) k_begin_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                    EnvView V, StepArgs a) {
   const int2 b = map[blockIdx.x];
   begin_body(tab[b.x], b.y, V, a);
 }
 template <int VPE>
-__global__ void __launch_bounds__(512) k_local(GroupView G, EnvView V, StepArgs a, int k, int residual_only, int tc,
-                                               int pending) {
-  local_body<VPE>(G, blockIdx.x, V, a, k, residual_only, tc, pending);
-}
-template <int VPE>
-__global__ void __launch_bounds__(512) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
-                                                   EnvView V, StepArgs a, int k, int residual_only, int tc,
-                                                   int pending) {
+__global__ void __launch_bounds__(512, 2) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                      EnvView V, StepArgs a, int k, int residual_only, int tc,
+                                                      int pending) {
   const int2 b = map[blockIdx.x];
   local_body<VPE>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
-}
-__global__ void __launch_bounds__(256, 4) k_ncp(GroupView G, EnvView V, StepArgs a, int tc) {
-  ncp_body(G, blockIdx.x, V, a, tc);
 }
 __global__ void __launch_bounds__(256, 4) k_ncp_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                     EnvView V, StepArgs a, int tc) {
   const int2 b = map[blockIdx.x];
   ncp_body(tab[b.x], b.y, V, a, tc);
 }
-__global__ void __launch_bounds__(256) k_end(GroupView G, EnvView V, StepArgs a) { end_body(G, blockIdx.x, V, a); }
 __global__ void __launch_bounds__(256) k_end_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                  EnvView V, StepArgs a) {
   const int2 b = map[blockIdx.x];
@@ -822,7 +850,7 @@ __global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
     vals[i] = src[(size_t)l * 3 * np + c * np + j];
   }
   __syncthreads();
-  write_split_columns(G, l, vals, sh3, true);
+  write_split_columns(G, l, vals, n, sh3, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -831,7 +859,6 @@ __global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
 // Feature / output scales: gaps and scaled multipliers y = gamma / m_v in
 // millimetres, velocities in units of 0.1 m/s.
 constexpr float kFeatLen = 1e3f, kFeatVel = 10.f;
-constexpr float kFeatClip = 100.f;      // trained input range (|feature| <= clip)
 constexpr int kWarmDq = 1, kWarmNormalOnly = 2;
 
 __global__ void k_row_offsets(const int *count, int N, int64_t *off) {
@@ -903,7 +930,8 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
 
 // gamma^0 (and optionally q^0 at contact vertices) from the network output
 __global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, StepArgs a, const int64_t *off,
-                                                       const float *X, const float *Y, int flags) {
+                                                       const float *X, const float *Y, const float *bounds,
+                                                       int flags) {
   __shared__ ObsShared O;
   const int l = blockIdx.x, e = G.genv[l];
   const int np = G.n_pad;
@@ -923,7 +951,7 @@ __global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, S
     // contacts whose features lie outside the trained range start cold
     const float *xr = X + (off[l] + j) * 10;
     bool in_range = true;
-    for (int c = 0; c < 10; c++) in_range = in_range && fabsf(xr[c]) <= kFeatClip;
+    for (int c = 0; c < 10; c++) in_range = in_range && xr[c] >= bounds[c] && xr[c] <= bounds[10 + c];
     if (!in_range) continue;
     const float mv = __ldg(G.mass + vtx) / kFeatLen;
     const float gn = fmaxf(y[0], 0.f) * mv;
@@ -972,38 +1000,13 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
 }  // namespace
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_local_tab<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_local_tab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_ncp, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-}
-
-cudaError_t launch_begin(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
-  k_begin<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_local(const flash_scene *s, const Group &g, const StepArgs &a, int k, int residual_only, int tc,
-                         cudaStream_t st) {
-  const int pending = k > 1;   // a position update from the previous iteration is waiting
-  if (g.vpe == 3) k_local<3><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc, pending);
-  else k_local<4><<<g.N, 512, g.smem_local, st>>>(view(s, g), eview(s), a, k, residual_only, tc, pending);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ncp(const flash_scene *s, const Group &g, const StepArgs &a, int tc, cudaStream_t st) {
-  size_t sm = tc ? sizeof(float) * 3 * g.n : 0;
-  k_ncp<<<g.N, 256, sm, st>>>(view(s, g), eview(s), a, tc);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_row_offsets(const Group &g, int64_t *off, cudaStream_t st) {
@@ -1018,19 +1021,14 @@ cudaError_t launch_features(const flash_scene *s, const Group &g, const StepArgs
 }
 
 cudaError_t launch_apply_learned(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off,
-                                 const float *X, const float *Y, int flags, cudaStream_t st) {
-  k_apply_learned<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, X, Y, flags);
+                                 const float *X, const float *Y, const float *bounds, int flags, cudaStream_t st) {
+  k_apply_learned<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, X, Y, bounds, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_targets(const flash_scene *s, const Group &g, const StepArgs &a, const int64_t *off, float *T,
                            cudaStream_t st) {
   k_targets<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a, off, T);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_end(const flash_scene *s, const Group &g, const StepArgs &a, cudaStream_t st) {
-  k_end<<<g.N, 256, 0, st>>>(view(s, g), eview(s), a);
   return cudaGetLastError();
 }
 

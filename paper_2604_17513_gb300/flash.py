@@ -88,6 +88,7 @@ def lib():
         L.flash_launch_count.argtypes = [vp]
         L.flash_launch_count.restype = i64
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
+        L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]
         L.flash_get_recorded.argtypes = [vp, vp, vp, i64, C.POINTER(i64), vp]
         L.flash_mlp_num_params.restype = i32
@@ -101,6 +102,7 @@ def lib():
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
                      "flash_step", "flash_get_contacts", "flash_get_stats", "flash_status_word",
                      "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
+                     "flash_warmstart_bounds",
                      "flash_record_contacts", "flash_get_recorded", "flash_mlp_forward", "flash_mlp_loss_grad",
                      "flash_mlp_adam", "flash_dense_apply_noalloc"):
             getattr(L, name).restype = i32
@@ -253,10 +255,17 @@ class Sim:
     def launch_count(self):
         return lib().flash_launch_count(self._h)
 
-    def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False):
-        """Select the warm start; ``params`` (device float32, flat) is copied."""
+    def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False, bounds=None):
+        """Select the warm start; ``params`` (device float32, flat) is copied.
+        ``bounds`` = (lo[10], hi[10]): the trained input range; contacts
+        outside it start cold."""
         flags = (1 if use_dq else 0) | (2 if normal_only else 0)
         _check(lib().flash_warmstart_set(self._h, _ptr(params), mode, flags))
+        if bounds is not None:
+            lo = np.ascontiguousarray(np.asarray(bounds[0], np.float32).reshape(10))
+            hi = np.ascontiguousarray(np.asarray(bounds[1], np.float32).reshape(10))
+            fp = C.POINTER(C.c_float)
+            _check(lib().flash_warmstart_bounds(self._h, lo.ctypes.data_as(fp), hi.ctypes.data_as(fp)))
 
     def record(self, enable=True):
         _check(lib().flash_record_contacts(self._h, 1 if enable else 0))

@@ -49,6 +49,20 @@ def usable(X, T, clip=100.0):
     return X[ok].contiguous(), T[ok].contiguous()
 
 
+def input_range(X, T, clip=100.0):
+    """Per-feature (lo, hi) of the usable training rows: the range the network
+    was fitted on (host float32 arrays for ``Sim.warmstart(bounds=...)``)."""
+    Xu, _ = usable(X, T, clip)
+    return Xu.min(0).values.cpu().numpy(), Xu.max(0).values.cpu().numpy()
+
+
+def in_range(X, lo, hi):
+    """Rows of X inside [lo, hi] feature by feature (the library's gate)."""
+    lo = torch.as_tensor(lo, device=X.device)
+    hi = torch.as_tensor(hi, device=X.device)
+    return ((X >= lo) & (X <= hi)).all(1)
+
+
 def train(X, T, epochs=5, batch=4096, lr=1e-3, seed=0, params=None, holdout=0.1):
     """Adam on the mean squared error; returns (params, train losses per
     epoch, held-out loss).  Rows are shuffled once on the host (seeded)."""

@@ -73,7 +73,8 @@ def test_adam_decreases_loss(cuda):
 
 def test_learned_warm_start_gain(cuda):
     """Train on the simulator's own converged steps (tolerance mode), then on
-    held-out rows compare the initial multipliers with the converged ones:
+    held-out rows inside the trained input range (the rows the library's gate
+    lets through) compare the initial multipliers with the converged ones:
     the network's prediction must beat the cold start (zero) and the previous
     step's multipliers.  With the learned start the plain iteration still runs
     to the same residual."""
@@ -89,9 +90,13 @@ def test_learned_warm_start_gain(cuda):
         sim.step(1)
     X, T = warmstart.collect(sim, sc, 5, 45, cuda)
     p, hist, _ = warmstart.train(X, T, epochs=6, batch=2048, lr=1e-3)
+    lo, hi = warmstart.input_range(X, T)
     assert hist[-1] < hist[0]
     Xh, Th = warmstart.collect(sim, sc, 50, 10, cuda)       # later steps: held out
     Xh, Th = warmstart.usable(Xh, Th)
+    keep = warmstart.in_range(Xh, lo, hi)
+    assert keep.float().mean().item() > 0.9
+    Xh, Th = Xh[keep].contiguous(), Th[keep].contiguous()
     pred = flash.mlp_forward(p, Xh)
     err = lambda y: ((y[:, :3] - Th[:, :3]) ** 2).sum(1).mean().item()
     e_learned = err(pred)
@@ -99,7 +104,7 @@ def test_learned_warm_start_gain(cuda):
     e_prev = err(torch.cat([Xh[:, 7:10], Xh[:, 7:10]], 1))
     assert e_learned < e_cold and e_learned < e_prev, (e_learned, e_cold, e_prev)
     # same residual target with the learned start (the plain iteration decides)
-    sim.warmstart(p, flash.WARM_LEARNED)
+    sim.warmstart(p, flash.WARM_LEARNED, bounds=(lo, hi))
     conv = []
     for s in range(60, 70):
         sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
