@@ -687,6 +687,8 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
+  if (use_tc(s))
+    for (auto &g : s->groups) FLASH_CUDA_TRY(tune_gemm_tc(g, s->done, st));
   FLASH_CUDA_TRY(build_batches(s));
   if (s->groups.size() > 1) {
     const size_t P = std::min<size_t>(s->groups.size(), kPoolStreams);

@@ -87,6 +87,7 @@ struct Group {
   float *cgam = nullptr;
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
+  int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner
   size_t smem_local = 0;
   bool c_in_smem = true;                  // element forces and CSR tables in shared memory
   float *cscratch = nullptr;              // element forces [N][ev + 1][3] when they do not fit
@@ -206,6 +207,7 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                     const float *lam, const float *kenv, cudaStream_t st);
 bool tc_available();
+cudaError_t tune_gemm_tc(Group &g, const int *done, cudaStream_t st);
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);
 
 // setup (setup_kernels.cu) ---------------------------------------------------

@@ -10,14 +10,17 @@
 // correction form q^k = q^{k-1} + A^-1 r, whose error against the FP64
 // oracle must stay below 1e-5 m.
 //
-// Structure (one 128 x 128 output tile per CTA, 128 threads):
-//   warp 0 lane 0  TMA producer: 4 tiles (A hi/lo, B hi/lo) of 128 x 64 f16
-//                  per k-block into a 3-stage ring, 128B swizzle
-//   warp 1 lane 0  MMA issuer: 4 k-slices x 3 products of M128 N128 K16,
+// Structure (one 128 x BN output tile per CTA, 128 threads; BN = 64, 128,
+// 176 or 256 columns, chosen per group by timing the candidates on the
+// group's own matrix when the scene is finalised):
+//   warp 0 lane 0  TMA producer: 4 tiles (A hi/lo 128 x 64, B hi/lo BN x 64
+//                  f16) per k-block into a 2..4-stage ring, 128B swizzle; the
+//                  last column tile may run past the matrix (zero fill)
+//   warp 1 lane 0  MMA issuer: 4 k-slices x 3 products of M128 N(BN) K16,
 //                  tcgen05.commit frees the stage / signals the epilogue
-//   warp 2         allocates / frees 128 TMEM columns
-//   all 4 warps    epilogue: tcgen05.ld 32 lanes x 32 columns at a time,
-//                  rescale, coalesced column stores (optionally q + w + .)
+//   warp 2         allocates / frees the TMEM columns
+//   all 4 warps    epilogue: tcgen05.ld 32 lanes x 32 (or 16) columns at a
+//                  time, rescale, coalesced column stores of live columns
 // Every mbarrier wait is bounded; on timeout the CTA raises an error flag,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -28,11 +31,8 @@
 namespace flash {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int BM = 128, BK = 64;
 constexpr int TILE_A = BM * BK * 2;   // bytes of one f16 A tile (16 KiB)
-constexpr int TILE_B = BN * BK * 2;   // bytes of one f16 B tile (16 KiB)
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s of SM clock before a wait is declared hung
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -102,12 +102,74 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// tile configuration: B tile bytes, ring depth that fits 227 KB, TMEM columns
+template <int BN> struct TileCfg {
+  static constexpr int TILE_B = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES > 4 ? 4 : (227 * 1024 - 2048) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+  static constexpr int TMEM_COLS = BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static_assert(BN % 16 == 0 && BN >= 64 && BN <= 256, "tcgen05 M128 needs N in [16, 256], multiple of 16");
+  static_assert(TILE_B % 1024 == 0, "128B-swizzled tiles start on 1 KiB boundaries");
+  static_assert(STAGES >= 2, "ring needs two stages");
+};
+
+// 32 lanes x 32 (X = 32) or 16 (X = 16) consecutive TMEM columns into registers
+template <int X> __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t *v);
+template <> __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t *v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+        "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t *v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// epilogue of X columns starting at tile column c0: rescale and store the live ones
+template <int X>
+__device__ __forceinline__ void store_cols(uint32_t taddr, float *o, const float *wv, int n_pad, int mode, float lr,
+                                           const float *col_scale, const float *col_k, const int *col_live, int c0) {
+  uint32_t v[X];
+  tmem_ld<X>(taddr, v);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  if (mode == 2) {
+#pragma unroll
+    for (int j = 0; j < X; j++)
+      if (col_live[c0 + j])
+        o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j] / (1.f + col_k[c0 + j] * lr);
+  } else if (mode == 0) {
+#pragma unroll
+    for (int j = 0; j < X; j++)
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
+  } else {
+    float prev[X];
+#pragma unroll
+    for (int j = 0; j < X; j++) prev[j] = col_live[c0 + j] ? o[(size_t)j * n_pad] + wv[(size_t)j * n_pad] : 0.f;
+#pragma unroll
+    for (int j = 0; j < X; j++)
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] = prev[j] + __uint_as_float(v[j]) * col_scale[c0 + j];
+  }
+}
+
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
               const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int cols,
               float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
+  using Cfg = TileCfg<BN>;
+  constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, TILE_B = Cfg::TILE_B;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ uint32_t tmem_base_sh;
@@ -138,7 +200,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(BN));
+                 "r"(Cfg::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -202,46 +264,22 @@ __global__ void __launch_bounds__(128, 1)
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int row = m0 + warp * 32 + lane;
+    const float lr = mode == 2 ? lam[row] : 0.f;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-            "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float *o = out + (size_t)(j0 + c0) * n_pad + row;
-      if (mode == 2) {
-        const float lr = lam[row];
-#pragma unroll
-        for (int j = 0; j < 32; j++)
-          if (col_live[c0 + j])
-            o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j] / (1.f + col_k[c0 + j] * lr);
-      } else if (mode == 0) {
-#pragma unroll
-        for (int j = 0; j < 32; j++)
-          if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
-      } else {
-        const float *wv = W + (size_t)(j0 + c0) * n_pad + row;
-        float prev[32];
-#pragma unroll
-        for (int j = 0; j < 32; j++) prev[j] = col_live[c0 + j] ? o[(size_t)j * n_pad] + wv[(size_t)j * n_pad] : 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; j++)
-          if (col_live[c0 + j]) o[(size_t)j * n_pad] = prev[j] + __uint_as_float(v[j]) * col_scale[c0 + j];
-      }
+    for (int c0 = 0; c0 + 32 <= BN; c0 += 32)
+      store_cols<32>(tbase + (uint32_t)c0, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
+                     n_pad, mode, lr, col_scale, col_k, col_live, c0);
+    if constexpr (BN % 32 == 16) {
+      constexpr int c0 = BN - 16;
+      store_cols<16>(tbase + (uint32_t)c0, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
+                     n_pad, mode, lr, col_scale, col_k, col_live, c0);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
   }
 }
 
@@ -281,23 +319,76 @@ bool tc_available() {
   return major == 10 && minor == 3 && get_encode() != nullptr;
 }
 
-cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st) {
+namespace {
+
+template <int BN>
+cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
+                        const float *lam, const float *kenv, cudaStream_t st) {
+  using Cfg = TileCfg<BN>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (g.n_pad % BM != 0 || g.n_pad % BK != 0 || g.cols_pad % BN != 0) return cudaErrorInvalidValue;
+  if (g.n_pad % BM != 0 || g.n_pad % BK != 0) return cudaErrorInvalidValue;
   CUtensorMap tmAh, tmAl, tmBh, tmBl;
   if (!make_map(&tmAh, M.hi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, M.lo, g.n_pad, g.n_pad, BM) ||
       !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN) || !make_map(&tmBl, g.rl, g.n_pad, g.cols_pad, BN))
     return cudaErrorInvalidValue;
-  dim3 grid(g.cols_pad / BN, g.n_pad / BM);
-  k_gemm_tc<<<grid, 128, SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
-                                           g.n_pad, g.cols, ldexpf(1.f, -M.exp), mode, lam, kenv);
+  // column tiles cover the live columns; the last may run past the
+  // matrix (TMA fills zeros, the epilogue stores only columns < cols)
+  dim3 grid((g.cols + BN - 1) / BN, g.n_pad / BM);
+  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
+                                                     g.n_pad, g.cols, ldexpf(1.f, -M.exp), mode, lam, kenv);
   return cudaGetLastError();
+}
+
+cudaError_t launch_bn(int bn, const Group &g, const SolveMat &M, float *out, const float *w, const int *done,
+                      int mode, const float *lam, const float *kenv, cudaStream_t st) {
+  switch (bn) {
+    case 64: return launch_tile<64>(g, M, out, w, done, mode, lam, kenv, st);
+    case 176: return launch_tile<176>(g, M, out, w, done, mode, lam, kenv, st);
+    case 256: return launch_tile<256>(g, M, out, w, done, mode, lam, kenv, st);
+    default: return launch_tile<128>(g, M, out, w, done, mode, lam, kenv, st);
+  }
+}
+
+}  // namespace
+
+cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
+                    const float *lam, const float *kenv, cudaStream_t st) {
+  return launch_bn(g.tc_bn, g, M, out, w, done, mode, lam, kenv, st);
+}
+
+// Tile autotuner: time each candidate tile width on the group's own matrix
+// and column count (the right-hand side is whatever the group holds, zeros
+// at setup) and keep the fastest.  Which width wins depends on how the
+// 128 x BN tiles of the group fill the SMs.
+cudaError_t tune_gemm_tc(Group &g, const int *done, cudaStream_t st) {
+  const SolveMat &M = g.eig ? g.Vt : g.inv;
+  const int cand[] = {64, 128, 176, 256};
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  float best = 1e30f;
+  int best_bn = 128;
+  for (int bn : cand) {
+    if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st)) != cudaSuccess) break;   // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; r++)
+      if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st)) != cudaSuccess) break;
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_bn = bn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.tc_bn = best_bn;
+  return e;
 }
 
 }  // namespace flash
