@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--mode", default="fixed", choices=["fixed", "tol"],
                    help="fixed: k iterations per step; tol: iterate until r_ncp <= 1e-5 (cap --k-cap)")
     p.add_argument("--k-cap", type=int, default=200, help="iteration cap of the tolerance mode")
+    p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
     p.add_argument("--no-e2e", action="store_true")
@@ -157,7 +158,17 @@ def traffic_for(kernel):
         return None
     if h != d.get("source_sha256_16"):
         return None
-    return d.get("bytes_per_launch_scaled", d.get("bytes_per_launch"))
+    b = d.get("bytes_per_launch_scaled", d.get("bytes_per_launch"))
+    return None if b is None else (b, d.get("envs_per_launch"))
+
+
+def scaled_traffic(t, envs_per_launch):
+    """Captured DRAM bytes per launch scaled to a launch over ``envs_per_launch``
+    environments (traffic grows with the environments a launch processes)."""
+    if t is None:
+        return None
+    b, e = t
+    return b if not e else b * envs_per_launch / e
 
 
 def oracle_mode_kw(args):
@@ -259,7 +270,7 @@ def main():
 
     solve = {"auto": flash.SOLVE_F16X3, "f32": flash.SOLVE_F32, "f16x3": flash.SOLVE_F16X3}[args.solve]
     n_steps = args.warmup + args.steps
-    total_steps = n_steps + 3 * args.steps + 8
+    total_steps = n_steps + 3 * args.steps + 8 + 10   # + the profiled pass (at most 10 steps)
     if args.workload == "cloth_gripper":
         args.envs = args.envs or 1024
         sc = scenes.cloth_gripper(seed=1 + rank, n_envs=args.envs, n_side=args.side, steps=total_steps, k_max=args.k)
@@ -278,12 +289,12 @@ def main():
     mode_kw = {"mode": flash.MODE_TOL, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
     warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
     try:
-        sim = flash.Sim(sc, solve=solve, warm=warm, **mode_kw)
+        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, **mode_kw)
     except flash.FlashError:
         if args.solve != "auto":
             raise
         solve = flash.SOLVE_F32
-        sim = flash.Sim(sc, solve=solve, warm=warm, **mode_kw)
+        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, **mode_kw)
     q0, v0 = flash.state_tensors(sc, dev)
     sim.set_state(q0, v0)
     scs = sc if isinstance(sc, list) else [sc]
@@ -318,7 +329,6 @@ def main():
         return ms, conv.item(), it_sum.item()
 
     launches0 = sim.launch_count()
-    sim.profile(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -327,8 +337,18 @@ def main():
     if world > 1:
         dist.barrier()
     launches = sim.launch_count() - launches0
+    # kernel breakdown: a separate pass with CUDA events around every launch
+    # (kept out of the timed steps above), continuing the same rollout
+    prof_steps = min(args.steps, 10)
+    sim.profile(True)
+    for i, s in enumerate(range(args.warmup + args.steps, args.warmup + args.steps + prof_steps)):
+        flush_buf.fill_(float(i))
+        sim.set_poses(poses[s + 1])
+        sim.step(1)
+    torch.cuda.synchronize()
     prof = sim.profile_read()
     sim.profile(False)
+    n_steps += prof_steps            # the rollout continues from here
     frac_conv = n_conv / (args.envs * args.steps)
     mean_iters = n_it / (args.envs * args.steps)
     # headline: env-steps that reach r_ncp <= 1e-5, per second (all ranks)
@@ -393,34 +413,46 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     d_ms, d_n = prof[dom]
     avg_s = d_ms / max(d_n, 1) / 1e3
+    # passes of each kernel class over every environment per step (Mode A:
+    # k local-global iterations + one residual pass; Mode B: the mean count)
+    it_pp = float(args.k) if args.mode == "fixed" else max(mean_iters, 1e-9)
+    passes = {"local": it_pp + 1, "ncp": it_pp, "solve": 2 * it_pp, "begin": 1, "end": 1, "warm": 1}[dom]
+    # achieved = the kind's algorithmic work over the profiled steps / its
+    # summed launch time (= per-launch work / mean launch time for any launch
+    # split, e.g. lanes or mesh groups)
     if dom == "solve":
         # per apply: dense A^-1 [n x n] on 3 columns per environment, 2n^2 flop a
         # column; the eigen form (per-environment stiffness) executes two
         # contractions, V^T then V, and is counted as such
-        flops = (4.0 if eig else 2.0) * sum(nv * nv * 3 * ne for nv, ne in tmpl)
+        flops = (4.0 if eig else 2.0) * sum(nv * nv * 3 * ne for nv, ne in tmpl) * passes * prof_steps
         if solve == flash.SOLVE_F16X3:
             peak = peaks.get("bf16_tflops", 1900.0)
-            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            roof = {"bound": "tensor", "achieved": flops / (d_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "peak_source": "measured bf16 burst (f16 runs at the bf16 rate)",
                     "note": "3 f16 passes per apply are executed; achieved counts the algorithmic 2n^2 per column"}
         else:
             sm = (clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
             peak = 152 * 128 * 2 * sm * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            roof = {"bound": "alu", "achieved": flops / (d_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
         roof["kernel"] = "global solve (dense A^-1 apply)"
-        roof["traffic"] = traffic_for("solve_f16x3" if solve == flash.SOLVE_F16X3 else "solve_f32")
+        roof["algorithmic_flops_per_launch"] = flops / max(d_n, 1)
+        roof["traffic"] = scaled_traffic(traffic_for("solve_f16x3" if solve == flash.SOLVE_F16X3 else "solve_f32"),
+                                         N * passes * prof_steps / max(d_n, 1))
     else:
         # data-movement roofline with the algorithmic bytes of each kernel per
         # environment (n vertices, C contacts): local 72n + 36C, ncp 48n + 40C,
         # begin 72n + 8C (read q, v; write q_t, q~, q, f; contact list), end 36n + 24C
         C = float(sim.contacts()[0].float().mean().item())
         per = {"local": (72, 36), "ncp": (48, 40), "begin": (72, 8), "end": (36, 24), "warm": (0, 64)}[dom]
-        b = per[0] * n_sum + per[1] * C * N
+        b = (per[0] * n_sum + per[1] * C * N) * passes * prof_steps
         peak = peaks.get("hbm_gbs", 6787.2)
-        roof = {"bound": "hbm", "achieved": b / avg_s / 1e9, "peak": peak, "unit": "GB/s", "kernel": dom,
-                "algorithmic_bytes_per_launch": b, "mean_contacts_per_env": C,
-                "peak_source": "measured HBM copy bandwidth", "traffic": traffic_for(dom)}
+        roof = {"bound": "hbm", "achieved": b / (d_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "kernel": dom,
+                "algorithmic_bytes_per_launch": b / max(d_n, 1), "mean_contacts_per_env": C,
+                "peak_source": "measured HBM copy bandwidth",
+                "traffic": scaled_traffic(traffic_for(dom), N * passes * prof_steps / max(d_n, 1))}
+    roof["lanes"] = sim.lane_count()
+    roof["note_lanes"] = "launch times measured while the other lanes' kernels run" if sim.lane_count() > 1 else None
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_us"] = avg_s * 1e6
     roof["launches"] = d_n
@@ -440,7 +472,7 @@ def main():
                        "k_cap": args.k_cap if args.mode == "tol" else None, "warm": args.warm,
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "lanes": sim.lane_count()},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
             "status": status, "warm_start": warm_cmp,
             "step_hbm_frac_of_measured": step_hbm_frac,

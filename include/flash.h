@@ -68,7 +68,12 @@ typedef int32_t flash_status;
  * default contact thickness tau (m) of meshes that give none.  margin:
  * detection margin delta (m).  k_max: iterations of FLASH_MODE_FIXED.
  * k_min/k_cap: bounds of FLASH_MODE_TOL.  contact_cap: contacts per
- * environment.  solve: FLASH_SOLVE_*.  warm: FLASH_WARM_*. */
+ * environment.  solve: FLASH_SOLVE_*.  warm: FLASH_WARM_*.  lanes: number of
+ * independent environment partitions stepped concurrently on their own
+ * streams (0 = chosen from the batch size; results do not depend on it).
+ * eager: 0 = a FLASH_MODE_FIXED step is captured once in a CUDA graph and
+ * replayed (not while profiling or with the learned warm start or contact
+ * recording on); 1 = every step launches its kernels one by one. */
 typedef struct {
   double h;
   double gravity[3];
@@ -80,7 +85,9 @@ typedef struct {
   int32_t contact_cap;
   int32_t solve;
   int32_t warm;
-  int32_t reserved[5];
+  int32_t lanes;
+  int32_t eager;
+  int32_t reserved[3];
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -179,6 +186,9 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
 flash_status flash_profile_enable(flash_scene *s, int32_t enable);
 flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, int64_t *launches);
 int64_t flash_launch_count(const flash_scene *s);
+/* Number of lanes the scene steps concurrently (flash_scene_desc.lanes, or
+ * the count chosen from the batch size); 0 before finalize. */
+int32_t flash_lane_count(const flash_scene *s);
 
 /* Learned warm start (the paper has no learned component; the network
  * predicts the initial multipliers gamma^0 and the first iterate at each

@@ -43,8 +43,8 @@ cudaError_t upload(flash_scene *s, T **p, const std::vector<T> &h) {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// streams of the per-group contraction pool (multi-group scenes)
-constexpr size_t kPoolStreams = 16;
+// most lanes chosen automatically
+constexpr int kMaxAutoLanes = 4;
 
 // ---------------------------------------------------------------------------
 // element operators: F = Ds Dm^-1 written as F[c][j] = sum_a x_a[c] D[a][j]
@@ -427,7 +427,7 @@ cudaError_t flush_profile(flash_scene *s) {
   cudaError_t e;
   for (size_t i = 0; i < s->ev_kind.size(); i++) {
     float ms = 0.f;
-    // pairs may sit on different streams (pool streams of multi-group scenes)
+    // pairs may sit on different streams (the lanes of a scene)
     if ((e = cudaEventSynchronize(s->ev_pool[2 * i + 1])) != cudaSuccess) return e;
     e = cudaEventElapsedTime(&ms, s->ev_pool[2 * i], s->ev_pool[2 * i + 1]);
     if (e != cudaSuccess) return e;
@@ -439,66 +439,69 @@ cudaError_t flush_profile(flash_scene *s) {
   return cudaSuccess;
 }
 
-// out = A^-1 * (the group's current right-hand side): r in FP32 (CUDA-core
-// path) or its f16 split (tensor-core path)
-cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, float *out, cudaStream_t st) {
+// out = A^-1 * (the group's current right-hand side) for environments
+// [l0, l1) (l1 < 0: all): r in FP32 (CUDA-core path) or its f16 split
+// (tensor-core path); bn is the tile width for that column range
+cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, float *out, cudaStream_t st, int l0 = 0,
+                          int l1 = -1, int bn = 0) {
   const bool tc = use_tc(s);
+  if (l1 < 0) l1 = g.N;
+  const int c0 = 3 * l0, c1 = 3 * l1;
   if (!g.eig) {
     return timed(s, FLASH_KIND_SOLVE, st, [&] {
-      return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st)
-                : gemm_simt(g, g.inv, rhs32, out, nullptr, s->done, 0, nullptr, nullptr, st);
+      return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn)
+                : gemm_simt(g, g.inv, rhs32, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1);
     });
   }
   // eigen form: y = diag(1/(1 + k_e lam)) V^T rhs, out = V y
   // (the CUDA-core kernel reads its matrix transposed, so it is given V for V^T and V^T for V)
   cudaError_t e = timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st)
-              : gemm_simt(g, g.V, rhs32, g.y, nullptr, s->done, 2, g.lam, g.kenv, st);
+    return tc ? gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn)
+              : gemm_simt(g, g.V, rhs32, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1);
   });
   if (e != cudaSuccess) return e;
   if (tc) {
-    e = timed(s, FLASH_KIND_SOLVE, st, [&] { return launch_split_rhs(g, g.y, s->done, st); });
+    e = timed(s, FLASH_KIND_SOLVE, st, [&] { return launch_split_rhs(g, g.y, st, l0, l1); });
     if (e != cudaSuccess) return e;
   }
   return timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st)
-              : gemm_simt(g, g.Vt, g.y, out, nullptr, s->done, 0, nullptr, nullptr, st);
+    return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn)
+              : gemm_simt(g, g.Vt, g.y, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1);
   });
 }
 
-// Multi-group scenes: the per-group contractions of one phase run on the pool
-// streams, ordered after everything already on `st` (fork) and before
-// anything issued to `st` next (join).
-cudaStream_t pool_stream(const flash_scene *s, size_t gi, cudaStream_t st) {
-  return s->pool.empty() ? st : s->pool[gi % s->pool.size()];
-}
+// Lanes: every lane's work of a phase is ordered after everything already on
+// the caller's stream (fork) and before anything issued to it next (join).
+// A single-lane scene runs on the caller's stream directly.
+cudaStream_t lane_stream(const Lane &L, cudaStream_t st) { return L.st ? L.st : st; }
 
 cudaError_t fork(flash_scene *s, cudaStream_t st) {
-  if (s->pool.empty()) return cudaSuccess;
-  cudaError_t e = cudaEventRecord(s->pool_ev[0], st);
-  for (size_t i = 0; i < s->pool.size() && e == cudaSuccess; i++) e = cudaStreamWaitEvent(s->pool[i], s->pool_ev[0], 0);
+  if (s->lanes.size() < 2) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(s->fork_ev, st);
+  for (size_t i = 0; i < s->lanes.size() && e == cudaSuccess; i++) e = cudaStreamWaitEvent(s->lanes[i].st, s->fork_ev, 0);
   return e;
 }
 
 cudaError_t join(flash_scene *s, cudaStream_t st) {
+  if (s->lanes.size() < 2) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  for (size_t i = 0; i < s->pool.size() && e == cudaSuccess; i++) {
-    e = cudaEventRecord(s->pool_ev[1 + i], s->pool[i]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->pool_ev[1 + i], 0);
+  for (size_t i = 0; i < s->lanes.size() && e == cudaSuccess; i++) {
+    e = cudaEventRecord(s->lanes[i].done, s->lanes[i].st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->lanes[i].done, 0);
   }
   return e;
 }
 
-// One phase of global applies, out_g = A_g^-1 in_g, over every group.
+// One lane's global applies of a phase, out_g = A_g^-1 in_g over its ranges.
 template <typename In, typename Out>
-cudaError_t apply_all(flash_scene *s, cudaStream_t st, In in, Out out) {
-  cudaError_t e = fork(s, st);
-  for (size_t gi = 0; gi < s->groups.size() && e == cudaSuccess; gi++) {
-    Group &g = s->groups[gi];
-    e = apply_inverse(s, g, in(g), out(g), pool_stream(s, gi, st));
+cudaError_t apply_lane(flash_scene *s, const Lane &L, cudaStream_t st, In in, Out out) {
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < L.ranges.size() && e == cudaSuccess; i++) {
+    const LaneRange &r = L.ranges[i];
+    Group &g = s->groups[r.group];
+    e = apply_inverse(s, g, in(g), out(g), st, r.l0, r.l1, r.tc_bn);
   }
-  const cudaError_t j = join(s, st);
-  return e != cudaSuccess ? e : j;
+  return e;
 }
 
 }  // namespace
@@ -687,21 +690,41 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
-  if (use_tc(s))
-    for (auto &g : s->groups) FLASH_CUDA_TRY(tune_gemm_tc(g, s->done, st));
-  FLASH_CUDA_TRY(build_batches(s));
-  if (s->groups.size() > 1) {
-    const size_t P = std::min<size_t>(s->groups.size(), kPoolStreams);
-    for (size_t i = 0; i < P; i++) {
-      cudaStream_t ps;
-      FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
-      s->pool.push_back(ps);
+  // lanes: explicit count, or about one per 256 environments (at most 4);
+  // a lane needs enough CTAs to fill a good part of the GPU by itself
+  int n_lanes = s->d.lanes > 0 ? s->d.lanes : std::max(1, std::min(kMaxAutoLanes, s->N / 256));
+  FLASH_CUDA_TRY(build_lanes(s, n_lanes));
+  if (s->lanes.size() > 1) {
+    FLASH_CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    for (Lane &L : s->lanes) {
+      FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+      FLASH_CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
     }
-    for (size_t i = 0; i <= P; i++) {
-      cudaEvent_t ev;
-      FLASH_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      s->pool_ev.push_back(ev);
+  }
+  if (use_tc(s)) {
+    // tile autotuner: each group's full column range (global applies) and
+    // each lane's range (the step), timed once per distinct column count
+    std::map<std::pair<int, int>, int> tuned;
+    auto tune = [&](int gi, int l0, int l1) -> int {
+      const auto key = std::make_pair(gi, l1 - l0);
+      auto it = tuned.find(key);
+      if (it != tuned.end()) return it->second;
+      int bn = 128;
+      if (tune_gemm_tc(s->groups[gi], s->done, st, 3 * l0, 3 * l1, &bn) != cudaSuccess) bn = -1;
+      tuned[key] = bn;
+      return bn;
+    };
+    for (size_t gi = 0; gi < s->groups.size(); gi++) {
+      const int bn = tune((int)gi, 0, s->groups[gi].N);
+      if (bn < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
+      s->groups[gi].tc_bn = bn;
     }
+    for (Lane &L : s->lanes)
+      for (LaneRange &r : L.ranges) {
+        const int bn = tune(r.group, r.l0, r.l1);
+        if (bn < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
+        r.tc_bn = bn;
+      }
   }
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   s->finalized = true;
@@ -712,9 +735,14 @@ void flash_scene_destroy(flash_scene *s) {
   if (!s) return;
   cudaDeviceSynchronize();
   for (void *p : s->allocs) cudaFree(p);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->cap_st) cudaStreamDestroy(s->cap_st);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-  for (cudaEvent_t e : s->pool_ev) cudaEventDestroy(e);
-  for (cudaStream_t ps : s->pool) cudaStreamDestroy(ps);
+  for (flash::Lane &L : s->lanes) {
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.st) cudaStreamDestroy(L.st);
+  }
+  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   if (s->h_active) cudaFreeHost(s->h_active);
   delete s;
 }
@@ -763,34 +791,59 @@ flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_
   return FLASH_OK;
 }
 
-flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
-  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
-  if (n_steps < 0) return fail(FLASH_EINVAL, "negative step count");
+namespace {
+
+// One time step (Algorithm 1 body) issued on st and the lanes' streams.
+flash_status step_once(flash_scene *s, cudaStream_t st) {
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
-  if (learned && !s->mlp_params) return fail(FLASH_ESTATE, "learned warm start needs weights (flash_warmstart_set)");
-  cudaStream_t st = (cudaStream_t)stream;
   const StepArgs a = step_args(s);
   const int tc = use_tc(s) ? 1 : 0;
   const size_t pose_bytes = sizeof(float) * s->N * FLASH_MAX_OBS * 7;
-  // per-environment kernels: table launches over every group; contractions
-  // per group (on the stream pool when there are several groups)
+  // Every phase is issued lane by lane; each lane's kernels run in order on
+  // its own stream, so lanes only meet at the forks and joins below.
+  auto begin = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess)
+        e = timed(s, FLASH_KIND_BEGIN, lane_stream(L, st), [&] { return launch_begin_lane(s, L, a, lane_stream(L, st)); });
+    return e;
+  };
   auto local = [&](int k, int residual_only) -> cudaError_t {
-    int launched = 0;
-    const cudaError_t e =
-        timed(s, FLASH_KIND_LOCAL, st, [&] { return launch_local_all(s, a, k, residual_only, tc, st, &launched); });
-    s->launches += launched - 1;
+    cudaError_t e = cudaSuccess;
+    for (const Lane &L : s->lanes) {
+      if (e != cudaSuccess) break;
+      const cudaStream_t ls = lane_stream(L, st);
+      int launched = 0;
+      e = timed(s, FLASH_KIND_LOCAL, ls, [&] { return launch_local_lane(s, L, a, k, residual_only, tc, ls, &launched); });
+      s->launches += launched - 1;
+    }
     return e;
   };
   auto solves = [&]() -> cudaError_t {
     // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq, applied by the next local pass)
-    cudaError_t e = apply_all(s, st, [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
-    if (e == cudaSuccess) e = timed(s, FLASH_KIND_NCP, st, [&] { return launch_ncp_all(s, a, tc, st); });
-    if (e == cudaSuccess) e = apply_all(s, st, [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
+    cudaError_t e = cudaSuccess;
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess)
+        e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_ncp_lane(s, L, a, tc, lane_stream(L, st)); });
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
     return e;
   };
-  for (int step = 0; step < n_steps; step++) {
-    FLASH_CUDA_TRY(timed(s, FLASH_KIND_BEGIN, st, [&] { return launch_begin_all(s, a, st); }));
+  auto end = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess)
+        e = timed(s, FLASH_KIND_END, lane_stream(L, st), [&] { return launch_end_lane(s, L, a, lane_stream(L, st)); });
+    return e;
+  };
+  {
+    FLASH_CUDA_TRY(fork(s, st));
+    FLASH_CUDA_TRY(begin());
     if (learned || s->record) {
+      // per-group warm-start work on the caller's stream, between the lanes' phases
+      FLASH_CUDA_TRY(join(s, st));
       for (auto &g : s->groups) {
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_row_offsets(g, g.row_off, st); }));
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_features(s, g, group_args(a, g), g.row_off, g.feat, st); }));
@@ -798,10 +851,12 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
           FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] {
             return mlp_forward(s->mlp_params, g.feat, g.pred, g.row_off + g.N, (int64_t)g.N * s->cap, st);
           }));
-          FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st,
-                               [&] { return launch_apply_learned(s, g, group_args(a, g), g.row_off, g.feat, g.pred, s->ws_bounds, s->use_dq, st); }));
+          FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] {
+            return launch_apply_learned(s, g, group_args(a, g), g.row_off, g.feat, g.pred, s->ws_bounds, s->use_dq, st);
+          }));
         }
       }
+      FLASH_CUDA_TRY(fork(s, st));
     }
     if (s->d.mode == FLASH_MODE_FIXED) {
       for (int k = 1; k <= s->d.k_max; k++) {
@@ -809,21 +864,83 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
         FLASH_CUDA_TRY(solves());
       }
       FLASH_CUDA_TRY(local(s->d.k_max + 1, 1));
+      FLASH_CUDA_TRY(join(s, st));
     } else {
+      FLASH_CUDA_TRY(join(s, st));
       for (int k = 1; k <= s->d.k_cap + 1; k++) {
         FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
+        FLASH_CUDA_TRY(fork(s, st));
         FLASH_CUDA_TRY(local(k, 0));
+        FLASH_CUDA_TRY(join(s, st));
         FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
         FLASH_CUDA_TRY(cudaStreamSynchronize(st));
         if (*s->h_active == 0) break;
+        FLASH_CUDA_TRY(fork(s, st));
         FLASH_CUDA_TRY(solves());
+        FLASH_CUDA_TRY(join(s, st));
       }
     }
     if (s->record)
       for (auto &g : s->groups)
         FLASH_CUDA_TRY(timed(s, FLASH_KIND_WARM, st, [&] { return launch_targets(s, g, group_args(a, g), g.row_off, g.targ, st); }));
-    FLASH_CUDA_TRY(timed(s, FLASH_KIND_END, st, [&] { return launch_end_all(s, a, st); }));
+    FLASH_CUDA_TRY(fork(s, st));
+    FLASH_CUDA_TRY(end());
+    FLASH_CUDA_TRY(join(s, st));
     FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, s->pose_th, pose_bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  return FLASH_OK;
+}
+
+// Capture one FLASH_MODE_FIXED step into a graph on an internal stream (the
+// caller's stream may be the legacy default stream, which cannot capture).
+flash_status capture_step(flash_scene *s) {
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (!s->cap_st) FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+  FLASH_CUDA_TRY(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = s->launches;
+  const flash_status r = step_once(s, s->cap_st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
+  s->graph_launches = s->launches - l0;
+  s->launches = l0;
+  if (r != FLASH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  FLASH_CUDA_TRY(e);
+  const cudaError_t ei = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  FLASH_CUDA_TRY(ei);
+  s->graph_stale = false;
+  return FLASH_OK;
+}
+
+}  // namespace
+
+flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (n_steps < 0) return fail(FLASH_EINVAL, "negative step count");
+  const bool learned = s->d.warm == FLASH_WARM_LEARNED;
+  if (learned && !s->mlp_params) return fail(FLASH_ESTATE, "learned warm start needs weights (flash_warmstart_set)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool graphed = !s->d.eager && s->d.mode == FLASH_MODE_FIXED && !s->profiling && !learned && !s->record;
+  if (graphed) {
+    if (!s->graph || s->graph_stale) {
+      const flash_status r = capture_step(s);
+      if (r != FLASH_OK) return r;
+    }
+    for (int step = 0; step < n_steps; step++) {
+      FLASH_CUDA_TRY(cudaGraphLaunch(s->graph, st));
+      s->launches += s->graph_launches;
+    }
+    return FLASH_OK;
+  }
+  for (int step = 0; step < n_steps; step++) {
+    const flash_status r = step_once(s, st);
+    if (r != FLASH_OK) return r;
   }
   return FLASH_OK;
 }
@@ -841,6 +958,7 @@ flash_status flash_warmstart_set(flash_scene *s, const float *params, int32_t mo
   }
   s->d.warm = mode;
   s->use_dq = use_dq;
+  s->graph_stale = true;
   return FLASH_OK;
 }
 
@@ -862,6 +980,7 @@ flash_status flash_record_contacts(flash_scene *s, int32_t enable) {
   if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
   if (enable) FLASH_CUDA_TRY(ensure_learn_buffers(s));
   s->record = enable != 0;
+  s->graph_stale = true;
   return FLASH_OK;
 }
 
@@ -902,6 +1021,8 @@ flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, 
 }
 
 int64_t flash_launch_count(const flash_scene *s) { return s ? s->launches : 0; }
+
+int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int32_t)s->lanes.size() : 0; }
 
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs, float *gamma,
                                 void *stream) {
@@ -952,7 +1073,7 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemsetAsync(s->done, 0, sizeof(int) * s->N, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, rhs, g.r, 0, st));
-  if (use_tc(s)) FLASH_CUDA_TRY(launch_split_rhs(g, g.r, s->done, st));
+  if (use_tc(s)) FLASH_CUDA_TRY(launch_split_rhs(g, g.r, st));
   FLASH_CUDA_TRY(apply_inverse(s, g, g.r, g.w, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, out, g.w, 1, st));
   return FLASH_OK;

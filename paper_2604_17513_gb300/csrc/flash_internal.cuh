@@ -108,6 +108,22 @@ struct Batch {
   size_t smem = 0;        // dynamic shared memory per CTA: the largest need of its groups
   int2 *map = nullptr;    // device [blocks]
 };
+// Environments [l0, l1) of one group: columns 3 l0 .. 3 l1 of its solves.
+struct LaneRange {
+  int group = 0, l0 = 0, l1 = 0;
+  int tc_bn = 128;        // tensor-core tile width for this column range (autotuned)
+};
+// A lane: a partition of the environments stepped on its own stream, so
+// that the wave tails of one lane's kernels overlap other lanes' work.
+// Results do not depend on the partition.
+struct Lane {
+  cudaStream_t st = nullptr;    // null: the caller's stream (single-lane scenes)
+  cudaEvent_t done = nullptr;   // join event
+  std::vector<LaneRange> ranges;
+  Batch all;                    // begin / NCP / end over the lane's environments
+  std::vector<Batch> local;     // local pass, by element type and shared-memory class
+  size_t ncp_smem_tc = 0;
+};
 }  // namespace flash
 
 struct flash_scene {
@@ -144,14 +160,16 @@ struct flash_scene {
   bool record = false;
   double prof_ms[FLASH_NUM_KINDS] = {0};
   int64_t prof_n[FLASH_NUM_KINDS] = {0};
-  // scenes with several groups: per-environment kernels run as table launches
-  // over all groups, the per-group contractions on a pool of streams
+  // per-environment kernels run as table launches (CTA -> group, environment)
+  // over the environments of a lane; lanes step concurrently on their streams
   void *gtab = nullptr;                        // device table of group views
-  std::vector<flash::Batch> b_local;           // local pass, by element type and shared-memory class
-  flash::Batch b_all;                          // begin / NCP / end over every environment
-  size_t ncp_smem_tc = 0;
-  std::vector<cudaStream_t> pool;
-  std::vector<cudaEvent_t> pool_ev;            // [0] fork, [1 + i] join of pool stream i
+  std::vector<flash::Lane> lanes;
+  cudaEvent_t fork_ev = nullptr;
+  // captured FLASH_MODE_FIXED step, replayed by flash_step
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_launches = 0;   // kernels in one replay
+  bool graph_stale = true;      // a setting that changes the step's launches has changed
 };
 
 namespace flash {
@@ -187,27 +205,31 @@ cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q
                             float *q_out, float *v_out, int to_user, cudaStream_t st);
 cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,
                           int to_user, cudaStream_t st);
-cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st);
-// table launches over every group of a scene (build_batches at finalize)
-cudaError_t build_batches(flash_scene *s);
-cudaError_t launch_begin_all(const flash_scene *s, const StepArgs &a, cudaStream_t st);
-cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int residual_only, int tc,
-                             cudaStream_t st, int *launched);
-cudaError_t launch_ncp_all(const flash_scene *s, const StepArgs &a, int tc, cudaStream_t st);
-cudaError_t launch_end_all(const flash_scene *s, const StepArgs &a, cudaStream_t st);
+// f16 hi/lo split of the columns of environments [l0, l1) of src (l1 < 0: all)
+cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0 = 0, int l1 = -1);
+// lanes and their table launches (build_lanes at finalize)
+cudaError_t build_lanes(flash_scene *s, int n_lanes);
+cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
+                              cudaStream_t st, int *launched);
+cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);
+cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
 
 // global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
-// out = M * rhs over all columns of a group, M = A^-1, V or V^T (the CUDA-core
+// out = M * rhs over columns [c0, c1) of a group (c1 < 0: all), M = A^-1, V or V^T (the CUDA-core
 // kernel computes M^T * rhs: callers pass the transposed matrix).  Epilogue
 // mode 0: out = acc (tiles whose environments are all done are skipped)
 // mode 1: q  = q + w + acc (skips environments whose done flag is set)
 // mode 2: out = acc / (1 + kenv[env] * lam[row])  (eigen-coordinate scaling)
 cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float *out, const float *w,
-                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st);
+                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st, int c0 = 0,
+                      int c1 = -1);
+// bn: tile width (0: the group's autotuned width)
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st);
+                    const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0);
 bool tc_available();
-cudaError_t tune_gemm_tc(Group &g, const int *done, cudaStream_t st);
+// time the tile widths on columns [c0, c1) of the group; fastest in *bn
+cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn);
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);
 
 // setup (setup_kernels.cu) ---------------------------------------------------

@@ -19,12 +19,13 @@ constexpr int BM = 128, BN = 128, BK = 16;
 __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, const float *__restrict__ B,
                                                   float *__restrict__ C, const float *__restrict__ W,
                                                   const int *__restrict__ done, const int *__restrict__ genv,
-                                                  int n_pad, int cols, int mode, const float *__restrict__ lam,
-                                                  const float *__restrict__ kenv) {
+                                                  int n_pad, int c0, int cols, int mode,
+                                                  const float *__restrict__ lam, const float *__restrict__ kenv) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
-  const int m0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  // columns [c0, cols) of the buffers; tiles past `cols` read zeros
+  const int m0 = blockIdx.y * BM, j0 = c0 + blockIdx.x * BN;
   const int tx = tid & 15, ty = tid >> 4;
   float acc[8][8];
 #pragma unroll
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
       float4 va = *reinterpret_cast<const float4 *>(A + (size_t)(k0 + kr) * n_pad + m0 + mc);
       *reinterpret_cast<float4 *>(&As[buf][kr][mc]) = va;
       int jc = idx >> 2, kq = (idx & 3) * 4;
-      float4 vb = *reinterpret_cast<const float4 *>(B + (size_t)(j0 + jc) * n_pad + k0 + kq);
+      const float4 vb = j0 + jc < cols ? *reinterpret_cast<const float4 *>(B + (size_t)(j0 + jc) * n_pad + k0 + kq)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
       Bs[buf][kq + 0][jc] = vb.x;
       Bs[buf][kq + 1][jc] = vb.y;
       Bs[buf][kq + 2][jc] = vb.z;
@@ -94,9 +96,11 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
 }  // namespace
 
 cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float *out, const float *w,
-                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st) {
-  dim3 grid((g.cols + BN - 1) / BN, g.n_pad / BM);
-  k_gemm_f32<<<grid, 256, 0, st>>>(M.f32, rhs, out, w, done, g.genv, g.n_pad, g.cols, mode, lam, kenv);
+                      const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
+  if (c1 < 0) c1 = g.cols;
+  if (c0 < 0 || c1 > g.cols || c0 >= c1) return c0 == c1 ? cudaSuccess : cudaErrorInvalidValue;
+  dim3 grid((c1 - c0 + BN - 1) / BN, g.n_pad / BM);
+  k_gemm_f32<<<grid, 256, 0, st>>>(M.f32, rhs, out, w, done, g.genv, g.n_pad, c0, c1, mode, lam, kenv);
   return cudaGetLastError();
 }
 
@@ -104,7 +108,7 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
 // (A^-1 [n_pad][n_pad], B and C [cols rounded up to 128][n_pad]).
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st) {
   dim3 grid((cols + BN - 1) / BN, n_pad / BM);
-  k_gemm_f32<<<grid, 256, 0, st>>>(Ainv, rhs, out, nullptr, nullptr, nullptr, n_pad, cols, 0, nullptr, nullptr);
+  k_gemm_f32<<<grid, 256, 0, st>>>(Ainv, rhs, out, nullptr, nullptr, nullptr, n_pad, 0, cols, 0, nullptr, nullptr);
   return cudaGetLastError();
 }
 

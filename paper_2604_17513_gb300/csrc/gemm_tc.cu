@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
-              const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int cols,
-              float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
+              const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int c_begin,
+              int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
   using Cfg = TileCfg<BN>;
   constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, TILE_B = Cfg::TILE_B;
   extern __shared__ uint8_t smem_raw[];
@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ float col_k[BN];
   __shared__ int col_live[BN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  // columns [c_begin, cols): tile x starts at c_begin + x BN
+  const int m0 = blockIdx.y * BM, j0 = c_begin + blockIdx.x * BN;
   const int KB = n_pad / BK;
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
@@ -323,7 +324,7 @@ namespace {
 
 template <int BN>
 cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                        const float *lam, const float *kenv, cudaStream_t st) {
+                        const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
   using Cfg = TileCfg<BN>;
   static bool configured = false;
   if (!configured) {
@@ -338,34 +339,36 @@ cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const flo
     return cudaErrorInvalidValue;
   // column tiles cover the live columns; the last may run past the
   // matrix (TMA fills zeros, the epilogue stores only columns < cols)
-  dim3 grid((g.cols + BN - 1) / BN, g.n_pad / BM);
+  dim3 grid((c1 - c0 + BN - 1) / BN, g.n_pad / BM);
   k_gemm_tc<BN><<<grid, 128, Cfg::SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
-                                                     g.n_pad, g.cols, ldexpf(1.f, -M.exp), mode, lam, kenv);
+                                                     g.n_pad, c0, c1, ldexpf(1.f, -M.exp), mode, lam, kenv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bn(int bn, const Group &g, const SolveMat &M, float *out, const float *w, const int *done,
-                      int mode, const float *lam, const float *kenv, cudaStream_t st) {
+                      int mode, const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
+  if (c1 < 0) c1 = g.cols;
+  if (c0 < 0 || c1 > g.cols || c0 >= c1) return c0 == c1 ? cudaSuccess : cudaErrorInvalidValue;
   switch (bn) {
-    case 64: return launch_tile<64>(g, M, out, w, done, mode, lam, kenv, st);
-    case 176: return launch_tile<176>(g, M, out, w, done, mode, lam, kenv, st);
-    case 256: return launch_tile<256>(g, M, out, w, done, mode, lam, kenv, st);
-    default: return launch_tile<128>(g, M, out, w, done, mode, lam, kenv, st);
+    case 64: return launch_tile<64>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 176: return launch_tile<176>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 256: return launch_tile<256>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    default: return launch_tile<128>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
   }
 }
 
 }  // namespace
 
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st) {
-  return launch_bn(g.tc_bn, g, M, out, w, done, mode, lam, kenv, st);
+                    const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn) {
+  return launch_bn(bn > 0 ? bn : g.tc_bn, g, M, out, w, done, mode, lam, kenv, st, c0, c1);
 }
 
 // Tile autotuner: time each candidate tile width on the group's own matrix
 // and column count (the right-hand side is whatever the group holds, zeros
 // at setup) and keep the fastest.  Which width wins depends on how the
 // 128 x BN tiles of the group fill the SMs.
-cudaError_t tune_gemm_tc(Group &g, const int *done, cudaStream_t st) {
+cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn_out) {
   const SolveMat &M = g.eig ? g.Vt : g.inv;
   const int cand[] = {64, 128, 176, 256};
   cudaEvent_t e0, e1;
@@ -375,19 +378,24 @@ cudaError_t tune_gemm_tc(Group &g, const int *done, cudaStream_t st) {
   float best = 1e30f;
   int best_bn = 128;
   for (int bn : cand) {
-    if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st)) != cudaSuccess) break;   // warm-up
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; r++)
-      if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st)) != cudaSuccess) break;
-    cudaEventRecord(e1, st);
-    if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_bn = bn; }
+    if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1)) != cudaSuccess) break;
+    float t_min = 1e30f;
+    for (int r = 0; r < 5 && e == cudaSuccess; r++) {
+      // one launch per measurement; the minimum is the least disturbed
+      cudaEventRecord(e0, st);
+      e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1);
+      cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      t_min = fminf(t_min, ms);
+    }
+    if (e != cudaSuccess) break;
+    if (t_min < best) { best = t_min; best_bn = bn; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  g.tc_bn = best_bn;
+  *bn_out = best_bn;
   return e;
 }
 

@@ -841,10 +841,10 @@ __global__ void k_rhs_io(int n, int np, const int *genv, const int64_t *voff, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_split(GroupView G, const float *src) {
+__global__ void __launch_bounds__(256) k_split(GroupView G, const float *src, int l0) {
   __shared__ float sh3[32][3];
   extern __shared__ float vals[];
-  const int l = blockIdx.x, n = G.n, np = G.n_pad;
+  const int l = l0 + blockIdx.x, n = G.n, np = G.n_pad;
   for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
     int c = i / n, j = i - c * n;
     vals[i] = src[(size_t)l * 3 * np + c * np + j];
@@ -1046,12 +1046,13 @@ cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_rhs(const Group &g, const float *src, const int *done, cudaStream_t st) {
-  (void)done;
+cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0, int l1) {
+  if (l1 < 0) l1 = g.N;
+  if (l0 < 0 || l1 > g.N || l0 >= l1) return l0 == l1 ? cudaSuccess : cudaErrorInvalidValue;
   GroupView v;
   memset(&v, 0, sizeof v);
   v.n = g.n; v.n_pad = g.n_pad; v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
-  k_split<<<g.N, 256, sizeof(float) * 3 * g.n, st>>>(v, src);
+  k_split<<<l1 - l0, 256, sizeof(float) * 3 * g.n, st>>>(v, src, l0);
   return cudaGetLastError();
 }
 
@@ -1078,11 +1079,17 @@ int local_class(size_t smem) {
 
 }  // namespace
 
-// Group table and block maps for table launches.  Environments of larger
-// meshes come first so their longer CTAs start in the first wave; the local
-// pass is split by element type (template) and by how many of its CTAs fit
-// on one SM, so a small mesh is not launched with a large mesh's shared memory.
-cudaError_t build_batches(flash_scene *s) {
+// Lanes: the environments are partitioned into lanes that step concurrently
+// on their own streams.  A group with at least kMinLaneEnvs environments per
+// lane is split into contiguous environment ranges, one per lane (each range
+// still fills whole contraction tiles); smaller groups go whole to the
+// least-loaded lane (work ~ environments x (vertices + elements)).  Each
+// lane gets block maps for its table launches: larger
+// meshes first, so their longer CTAs start in the first wave; the local
+// pass split by element type and by how many of its CTAs fit on one SM.
+constexpr int kMinLaneEnvs = 64;
+
+cudaError_t build_lanes(flash_scene *s, int n_lanes) {
   const int G = (int)s->groups.size();
   std::vector<GroupView> tab(G);
   for (int i = 0; i < G; i++) tab[i] = view(s, s->groups[i]);
@@ -1090,52 +1097,80 @@ cudaError_t build_batches(flash_scene *s) {
   cudaError_t e = upload_owned(s, &dtab, tab);
   if (e != cudaSuccess) return e;
   s->gtab = dtab;
+  n_lanes = std::max(1, n_lanes);
+  s->lanes.assign(n_lanes, Lane());
+  std::vector<double> load(n_lanes, 0.0);
   std::vector<int> order(G);
   for (int i = 0; i < G; i++) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const Group &a = s->groups[x], &b = s->groups[y];
-    return (int64_t)a.E + a.n > (int64_t)b.E + b.n;
-  });
-  std::vector<int2> all;
-  int nmax = 0;
+  auto work = [&](int gi) { const Group &g = s->groups[gi]; return (double)g.N * (g.n + g.E); };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
   for (int gi : order) {
-    for (int l = 0; l < s->groups[gi].N; l++) all.push_back(make_int2(gi, l));
-    nmax = std::max(nmax, s->groups[gi].n);
-  }
-  s->b_all = Batch();
-  s->b_all.blocks = (int)all.size();
-  if ((e = upload_owned(s, &s->b_all.map, all)) != cudaSuccess) return e;
-  s->ncp_smem_tc = sizeof(float) * 3 * (size_t)nmax;
-  s->b_local.clear();
-  for (int vpe = 3; vpe <= 4; vpe++)
-    for (int cls = 4; cls >= 1; cls--) {
-      Batch b;
-      b.vpe = vpe;
-      std::vector<int2> m;
-      for (int gi : order) {
-        const Group &g = s->groups[gi];
-        if (g.vpe != vpe || local_class(g.smem_local) != cls) continue;
-        for (int l = 0; l < g.N; l++) m.push_back(make_int2(gi, l));
-        b.smem = std::max(b.smem, g.smem_local);
+    const Group &g = s->groups[gi];
+    if (g.N >= kMinLaneEnvs * n_lanes) {
+      for (int k = 0; k < n_lanes; k++) {
+        LaneRange r;
+        r.group = gi;
+        r.l0 = (int)((int64_t)g.N * k / n_lanes);
+        r.l1 = (int)((int64_t)g.N * (k + 1) / n_lanes);
+        s->lanes[k].ranges.push_back(r);
+        load[k] += work(gi) / n_lanes;
       }
-      if (m.empty()) continue;
-      b.blocks = (int)m.size();
-      if ((e = upload_owned(s, &b.map, m)) != cudaSuccess) return e;
-      s->b_local.push_back(b);
+    } else {
+      const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      LaneRange r;
+      r.group = gi;
+      r.l0 = 0;
+      r.l1 = g.N;
+      s->lanes[k].ranges.push_back(r);
+      load[k] += work(gi);
     }
+  }
+  for (Lane &L : s->lanes) {
+    // ranges of larger meshes first
+    std::stable_sort(L.ranges.begin(), L.ranges.end(), [&](const LaneRange &x, const LaneRange &y) {
+      const Group &a = s->groups[x.group], &b = s->groups[y.group];
+      return (int64_t)a.E + a.n > (int64_t)b.E + b.n;
+    });
+    std::vector<int2> all;
+    int nmax = 0;
+    for (const LaneRange &r : L.ranges) {
+      for (int l = r.l0; l < r.l1; l++) all.push_back(make_int2(r.group, l));
+      nmax = std::max(nmax, s->groups[r.group].n);
+    }
+    L.all.blocks = (int)all.size();
+    if ((e = upload_owned(s, &L.all.map, all)) != cudaSuccess) return e;
+    L.ncp_smem_tc = sizeof(float) * 3 * (size_t)nmax;
+    for (int vpe = 3; vpe <= 4; vpe++)
+      for (int cls = 4; cls >= 1; cls--) {
+        Batch b;
+        b.vpe = vpe;
+        std::vector<int2> m;
+        for (const LaneRange &r : L.ranges) {
+          const Group &g = s->groups[r.group];
+          if (g.vpe != vpe || local_class(g.smem_local) != cls) continue;
+          for (int l = r.l0; l < r.l1; l++) m.push_back(make_int2(r.group, l));
+          b.smem = std::max(b.smem, g.smem_local);
+        }
+        if (m.empty()) continue;
+        b.blocks = (int)m.size();
+        if ((e = upload_owned(s, &b.map, m)) != cudaSuccess) return e;
+        L.local.push_back(b);
+      }
+  }
   return cudaSuccess;
 }
 
-cudaError_t launch_begin_all(const flash_scene *s, const StepArgs &a, cudaStream_t st) {
-  k_begin_tab<<<s->b_all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s), a);
+cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
+  if (!L.all.blocks) return cudaSuccess;
+  k_begin_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int residual_only, int tc,
-                             cudaStream_t st, int *launched) {
+cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
+                              cudaStream_t st, int *launched) {
   const int pending = k > 1;
   const GroupView *tab = (const GroupView *)s->gtab;
-  for (const Batch &b : s->b_local) {
+  for (const Batch &b : L.local) {
     if (b.vpe == 3)
       k_local_tab<3><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
     else
@@ -1147,14 +1182,16 @@ cudaError_t launch_local_all(const flash_scene *s, const StepArgs &a, int k, int
   return cudaSuccess;
 }
 
-cudaError_t launch_ncp_all(const flash_scene *s, const StepArgs &a, int tc, cudaStream_t st) {
-  k_ncp_tab<<<s->b_all.blocks, 256, tc ? s->ncp_smem_tc : 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s),
-                                                                   a, tc);
+cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st) {
+  if (!L.all.blocks) return cudaSuccess;
+  k_ncp_tab<<<L.all.blocks, 256, tc ? L.ncp_smem_tc : 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a,
+                                                              tc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_end_all(const flash_scene *s, const StepArgs &a, cudaStream_t st) {
-  k_end_tab<<<s->b_all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, s->b_all.map, eview(s), a);
+cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
+  if (!L.all.blocks) return cudaSuccess;
+  k_end_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ class SceneDesc(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("tol_ncp", C.c_double), ("maxforce", C.c_double),
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
-                ("warm", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class MeshDesc(C.Structure):
@@ -87,6 +87,8 @@ def lib():
         L.flash_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]
         L.flash_launch_count.argtypes = [vp]
         L.flash_launch_count.restype = i64
+        L.flash_lane_count.argtypes = [vp]
+        L.flash_lane_count.restype = i32
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
         L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]
@@ -132,7 +134,7 @@ class Sim:
     """
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
-                 warm=WARM_COLD, contact_cap=None):
+                 warm=WARM_COLD, contact_cap=None, lanes=0, eager=False):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -151,6 +153,8 @@ class Sim:
         d.contact_cap = contact_cap or max(sc.n_verts * sc.n_obs for sc in scenes)
         d.solve = solve
         d.warm = warm
+        d.lanes = lanes
+        d.eager = 1 if eager else 0
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))
@@ -254,6 +258,9 @@ class Sim:
 
     def launch_count(self):
         return lib().flash_launch_count(self._h)
+
+    def lane_count(self):
+        return lib().flash_lane_count(self._h)
 
     def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False, bounds=None):
         """Select the warm start; ``params`` (device float32, flat) is copied.

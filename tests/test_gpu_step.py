@@ -336,6 +336,33 @@ def test_batched_groups_equal_separate_scenes(cuda, solve):
 
 
 @pytest.mark.parametrize("solve", SOLVES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lanes_do_not_change_results(cuda, solve, mode):
+    """Environments partitioned into lanes that step concurrently on their own
+    streams (each lane's contractions over its own column range), and fixed
+    steps replayed from a captured CUDA graph, give bit-identical states to
+    one lane launched kernel by kernel, in both stopping modes."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_gripper(n_envs=260, n_side=16, side=0.25, steps=30)
+    kw = dict(mode=1, tol=1e-5, k_cap=40) if mode else {}
+    out = []
+    # 3 and 4 lanes split the 260 environments unevenly
+    for lanes, eager in ((1, True), (1, False), (3, False), (4, True)):
+        sim = flash.Sim(sc, solve=solve, lanes=lanes, eager=eager, **kw)
+        q0, v0 = flash.state_tensors(sc, cuda)
+        sim.set_state(q0, v0)
+        sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        for s in range(20):
+            sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            sim.step(1)
+        it, r = sim.stats()
+        out.append((sim.get_state()[0].cpu().numpy(), it.cpu().numpy(), sim.status()))
+    for q, it, st in out[1:]:
+        assert np.array_equal(q, out[0][0]) and np.array_equal(it, out[0][1]) and st == out[0][2]
+
+
+@pytest.mark.parametrize("solve", SOLVES)
 def test_global_apply_eigen_form(cuda, solve):
     """Per-environment stiffness on one tet mesh: the library applies
     A_e^-1 = V diag(1/(1 + k_e lam)) V^T with one shared eigenbasis; each
