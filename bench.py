@@ -472,7 +472,8 @@ def main():
                        "k_cap": args.k_cap if args.mode == "tol" else None, "warm": args.warm,
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                       "parallelism": f"replicas x{world}", "lanes": sim.lane_count()},
+                       "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
+                       "graph": args.mode == "fixed", "tile_widths": sorted(set(sim.tile_widths()))},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
             "status": status, "warm_start": warm_cmp,
             "step_hbm_frac_of_measured": step_hbm_frac,

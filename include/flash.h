@@ -189,6 +189,11 @@ int64_t flash_launch_count(const flash_scene *s);
 /* Number of lanes the scene steps concurrently (flash_scene_desc.lanes, or
  * the count chosen from the batch size); 0 before finalize. */
 int32_t flash_lane_count(const flash_scene *s);
+/* Tensor-core tile width (output columns per CTA) the autotuner chose for
+ * each lane's column range of each group, lane by lane: up to max_out values
+ * into the host array out; returns how many ranges there are (0 on the
+ * CUDA-core path or before finalize). */
+int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out);
 
 /* Learned warm start (the paper has no learned component; the network
  * predicts the initial multipliers gamma^0 and the first iterate at each

@@ -44,7 +44,7 @@ cudaError_t upload(flash_scene *s, T **p, const std::vector<T> &h) {
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // most lanes chosen automatically
-constexpr int kMaxAutoLanes = 4;
+constexpr int kMaxAutoLanes = 4, kMaxAutoLanesGroups = 8;
 
 // ---------------------------------------------------------------------------
 // element operators: F = Ds Dm^-1 written as F[c][j] = sum_a x_a[c] D[a][j]
@@ -690,9 +690,13 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
-  // lanes: explicit count, or about one per 256 environments (at most 4);
-  // a lane needs enough CTAs to fill a good part of the GPU by itself
-  int n_lanes = s->d.lanes > 0 ? s->d.lanes : std::max(1, std::min(kMaxAutoLanes, s->N / 256));
+  // lanes: explicit count, or about one per 256 environments (at most 4):
+  // a lane needs enough CTAs to fill a good part of the GPU by itself;
+  // several mesh groups: one lane per group up to kMaxAutoLanesGroups (the
+  // lanes are what runs the groups' small contractions concurrently)
+  int n_lanes = s->d.lanes > 0 ? s->d.lanes
+                : s->groups.size() > 1 ? std::min<int>(kMaxAutoLanesGroups, (int)s->groups.size())
+                                       : std::max(1, std::min(kMaxAutoLanes, s->N / 256));
   FLASH_CUDA_TRY(build_lanes(s, n_lanes));
   if (s->lanes.size() > 1) {
     FLASH_CUDA_TRY(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
@@ -725,6 +729,56 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
         if (bn < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
         r.tc_bn = bn;
       }
+    if (s->lanes.size() > 1) {
+      // lanes run their contractions at the same time, which the per-range
+      // timings above do not see: time one phase of every lane's applies
+      // running concurrently for those choices and for each uniform width,
+      // and keep the fastest configuration
+      const int64_t launches0 = s->launches;
+      cudaEvent_t e0, e1;
+      FLASH_CUDA_TRY(cudaEventCreate(&e0));
+      FLASH_CUDA_TRY(cudaEventCreate(&e1));
+      auto phase_ms = [&](float *best_ms) -> cudaError_t {
+        float t = 1e30f;
+        for (int rep = 0; rep < 4; rep++) {
+          cudaError_t e = cudaEventRecord(e0, st);
+          if (e == cudaSuccess) e = fork(s, st);
+          for (const Lane &L : s->lanes)
+            if (e == cudaSuccess)
+              e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+          if (e == cudaSuccess) e = join(s, st);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) return e;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) t = std::min(t, ms);     // the first run warms up
+        }
+        *best_ms = t;
+        return cudaSuccess;
+      };
+      std::vector<int> chosen;
+      for (const Lane &L : s->lanes)
+        for (const LaneRange &r : L.ranges) chosen.push_back(r.tc_bn);
+      float best = 0.f;
+      FLASH_CUDA_TRY(phase_ms(&best));
+      for (int bn : {64, 128, 176, 256}) {
+        for (Lane &L : s->lanes)
+          for (LaneRange &r : L.ranges) r.tc_bn = bn;
+        float t = 0.f;
+        FLASH_CUDA_TRY(phase_ms(&t));
+        if (t < best) {
+          best = t;
+          chosen.assign(chosen.size(), bn);
+        }
+      }
+      size_t k = 0;
+      for (Lane &L : s->lanes)
+        for (LaneRange &r : L.ranges) r.tc_bn = chosen[k++];
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      s->launches = launches0;
+    }
   }
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   s->finalized = true;
@@ -1023,6 +1077,17 @@ flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, 
 int64_t flash_launch_count(const flash_scene *s) { return s ? s->launches : 0; }
 
 int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int32_t)s->lanes.size() : 0; }
+
+int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out) {
+  if (!s || !s->finalized || !use_tc(s)) return 0;
+  int32_t k = 0;
+  for (const Lane &L : s->lanes)
+    for (const LaneRange &r : L.ranges) {
+      if (out && k < max_out) out[k] = r.tc_bn;
+      k++;
+    }
+  return k;
+}
 
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs, float *gamma,
                                 void *stream) {

@@ -89,6 +89,8 @@ def lib():
         L.flash_launch_count.restype = i64
         L.flash_lane_count.argtypes = [vp]
         L.flash_lane_count.restype = i32
+        L.flash_tile_widths.argtypes = [vp, C.POINTER(i32), i32]
+        L.flash_tile_widths.restype = i32
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
         L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]
@@ -261,6 +263,13 @@ class Sim:
 
     def lane_count(self):
         return lib().flash_lane_count(self._h)
+
+    def tile_widths(self):
+        """Autotuned tensor-core tile width of each lane's column range."""
+        n = lib().flash_tile_widths(self._h, None, 0)
+        out = (C.c_int32 * max(n, 1))()
+        lib().flash_tile_widths(self._h, out, n)
+        return list(out[:n])
 
     def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False, bounds=None):
         """Select the warm start; ``params`` (device float32, flat) is copied.
