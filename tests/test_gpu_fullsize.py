@@ -1,0 +1,95 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times: automatic lanes, graph replay of fixed-iteration steps and autotuned
+tensor-core tiles.  Every environment steps on the GPU; a sample, including
+the first and last environment of lanes, starts from the oracle's state at
+step s and is checked against one oracle step, one by one (max vertex
+position error <= 1e-5 m).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_17513_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+
+
+def _f32(x):
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+def _oracle_state(sc, e, s):
+    mesh = oracle.Mesh.from_scene(sc, e)
+    st = oracle.EnvState(sc.q0[e], sc.v0[e])
+    for k in range(s):
+        oracle.step(mesh, sc, e, k, st)
+    return mesh, _f32(st.q), _f32(st.v)
+
+
+def _step_all(cuda, scs, qs, vs, s):
+    """One GPU step of every environment of the scenes from (qs, vs) at step s,
+    in the bench's configuration (f16x3, automatic lanes, graph replay)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sim = flash.Sim(scs, solve=flash.SOLVE_F16X3)
+    sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
+                  torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
+    sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
+    sim.set_poses(flash.poses_tensor(scs, s + 1, cuda), which=1)
+    sim.step(1)
+    q = sim.get_state()[0].cpu().numpy()
+    assert sim.status() == 0
+    return sim, q
+
+
+def _check(scs, picks, s, cuda, lanes):
+    """picks: (scene index, local environment) pairs checked against the oracle."""
+    qs = [sc.q0.reshape(-1, 3).copy() for sc in scs]
+    vs = [sc.v0.reshape(-1, 3).copy() for sc in scs]
+    refs = []
+    for si, e in picks:
+        sc = scs[si]
+        mesh, q0, v0 = _oracle_state(sc, e, s)
+        n = sc.n_verts
+        qs[si][e * n:(e + 1) * n] = q0
+        vs[si][e * n:(e + 1) * n] = v0
+        ref = oracle.EnvState(q0, v0)
+        oracle.step(mesh, sc, e, s, ref)
+        refs.append(ref)
+    sim, q = _step_all(cuda, scs, qs, vs, s)
+    assert sim.lane_count() == lanes
+    base = np.cumsum([0] + [sc.n_envs for sc in scs])
+    off = sim.offsets
+    for (si, e), ref in zip(picks, refs):
+        g = base[si] + e
+        err = np.abs(q[off[g]:off[g + 1]] - ref.q).max()
+        assert err <= POS_TOL, (si, e, err, len(ref.cvert))
+
+
+def test_cloth_gripper_full_size(cuda):
+    """1024 environments of the 32x32 cloth under the gripper (4 lanes of
+    256); samples at both ends of lanes."""
+    sc = scenes.cloth_gripper(seed=1, n_envs=1024, steps=20)
+    _check([sc], [(0, 0), (0, 255), (0, 256), (0, 1023)], 10, cuda, lanes=4)
+
+
+def test_tet_squeeze_full_size(cuda):
+    """4096 tet blocks with per-environment stiffness (eigen-form solve,
+    4 lanes of 1024); samples at both ends of lanes."""
+    sc = scenes.tet_squeeze(seed=1, n_envs=4096, steps=12)
+    _check([sc], [(0, 0), (0, 1023), (0, 1024), (0, 4095)], 6, cuda, lanes=4)
+
+
+def test_mixed_batch_full_size(cuda):
+    """The 2048-environment mixed batch (cloths of side 16..64, tet blocks of
+    200..3000 vertices, one group per template, 8 lanes); samples from the
+    smallest cloth and tet templates and a mid-size cloth (the oracle's dense
+    Cholesky keeps the largest templates out of a test)."""
+    scs = scenes.mixed_batch(seed=3, n_envs=2048, steps=16)
+    cloths = sorted((sc.n_verts, i) for i, sc in enumerate(scs) if sc.elem_type == scenes.TRI)
+    tets = sorted((sc.n_verts, i) for i, sc in enumerate(scs) if sc.elem_type == scenes.TET)
+    mid = [i for n, i in cloths if 900 <= n <= 1300][0]
+    picks = [(cloths[0][1], 0), (tets[0][1], scs[tets[0][1]].n_envs - 1), (mid, 0)]
+    _check(scs, picks, 8, cuda, lanes=8)
