@@ -58,6 +58,9 @@ typedef int32_t flash_status;
 #define FLASH_SOLVE_F32 0    /* global solve: FP32 dense apply on the CUDA cores */
 #define FLASH_SOLVE_F16X3 1  /* global solve: tcgen05 f16 hi/lo split, FP32 accumulate */
 
+#define FLASH_METRIC_LITE 0  /* contact metric Z = J M^-1 J^T + E (Sec. IV-B.1), per-vertex blocks */
+#define FLASH_METRIC_FULL 1  /* Z = J A^-1 J^T + E (Sec. III-C), lin_iters steps of GMRES per Newton step */
+
 #define FLASH_WARM_COLD 0    /* gamma^0 = 0, q^0 = q~ (the paper's start) */
 #define FLASH_WARM_PREV 1    /* gamma^0 = previous step's gamma of the same contact */
 #define FLASH_WARM_LEARNED 2 /* gamma^0, q^0 from the warm-start network */
@@ -73,7 +76,12 @@ typedef int32_t flash_status;
  * streams (0 = chosen from the batch size; results do not depend on it).
  * eager: 0 = a FLASH_MODE_FIXED step is captured once in a CUDA graph and
  * replayed (not while profiling or with the learned warm start or contact
- * recording on); 1 = every step launches its kernels one by one. */
+ * recording on); 1 = every step launches its kernels one by one.
+ * metric: FLASH_METRIC_*.  lin_iters: linear-solver iterations of the full
+ * metric, 1..32 (0 = 10, the paper's parameter table): each Newton step runs
+ * that many GMRES steps on Z dy = rhs over all contacts of an environment,
+ * preconditioned by Z's 3x3 diagonal blocks; every GMRES step costs one
+ * application of A^-1 to all environments. */
 typedef struct {
   double h;
   double gravity[3];
@@ -87,7 +95,9 @@ typedef struct {
   int32_t warm;
   int32_t lanes;
   int32_t eager;
-  int32_t reserved[3];
+  int32_t metric;
+  int32_t lin_iters;
+  int32_t reserved[1];
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest

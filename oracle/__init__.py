@@ -20,7 +20,7 @@ _SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
 _lib = None
 
 DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU = range(9)
-IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC = range(5)
+IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC, IP_LINIT = range(6)
 
 
 def build(force: bool = False) -> str:
@@ -156,7 +156,8 @@ def fb(a, b):
     return lib().or_fb(float(a), float(b))
 
 
-def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None, k_cap=None, tol=None):
+def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None, k_cap=None, tol=None,
+           lin_iters: int = 10):
     dp = np.zeros(9)
     dp[DP_H] = sc.h
     dp[DP_GX:DP_GZ + 1] = sc.gravity
@@ -165,12 +166,13 @@ def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None,
     dp[DP_TAU] = sc.thickness
     dp[DP_MARGIN] = sc.margin
     dp[DP_MU] = sc.mu[env]
-    ip = np.zeros(5, np.int32)
+    ip = np.zeros(6, np.int32)
     ip[IP_KMAX] = sc.k_max if k_max is None else k_max
     ip[IP_KMIN] = sc.k_min if k_min is None else k_min
     ip[IP_KCAP] = sc.k_cap if k_cap is None else k_cap
     ip[IP_MODE] = sc.mode if mode is None else mode
     ip[IP_METRIC] = metric
+    ip[IP_LINIT] = lin_iters
     return dp, ip
 
 
@@ -212,9 +214,11 @@ def warm_from_previous(cvert, cobs, prev: EnvState):
 
 
 def step(mesh: Mesh, sc, env, s, st: EnvState, mode=None, metric=0, warm="cold", gamma0=None,
-         q_init=None, k_max=None, k_min=None, k_cap=None, tol=None, trace=False):
-    """Advance one environment by one step (Algorithm 1 body).  Mutates ``st``."""
-    dp, ip = params(sc, env, mode, metric, k_max, k_min, k_cap, tol)
+         q_init=None, k_max=None, k_min=None, k_cap=None, tol=None, trace=False, lin_iters=10):
+    """Advance one environment by one step (Algorithm 1 body).  Mutates ``st``.
+    metric 0: lite Z = J M^-1 J^T + E; 1: full Z = J A^-1 J^T + E solved
+    exactly; 2: full Z solved by ``lin_iters`` steps of preconditioned GMRES."""
+    dp, ip = params(sc, env, mode, metric, k_max, k_min, k_cap, tol, lin_iters)
     cvert, cobs = detect(mesh, sc, env, s, st.q, st.v, dp)
     if gamma0 is not None:
         gam = _f64(gamma0).reshape(len(cvert), 4).copy()
@@ -249,7 +253,7 @@ def residual(mesh: Mesh, sc, env, s, q_t, q, cvert, cobs, gamma):
 
 
 def rollout(sc, env=0, steps=None, mode=None, warm="cold", metric=0, k_max=None, k_min=None, k_cap=None, tol=None,
-            mesh=None, record=False):
+            mesh=None, record=False, lin_iters=10):
     """Run ``steps`` steps of one environment; returns the final EnvState (and the
     per-step positions when ``record``)."""
     mesh = Mesh.from_scene(sc, env) if mesh is None else mesh
@@ -257,7 +261,8 @@ def rollout(sc, env=0, steps=None, mode=None, warm="cold", metric=0, k_max=None,
     steps = sc.steps if steps is None else steps
     traj = []
     for s in range(steps):
-        step(mesh, sc, env, s, st, mode=mode, metric=metric, warm=warm, k_max=k_max, k_min=k_min, k_cap=k_cap, tol=tol)
+        step(mesh, sc, env, s, st, mode=mode, metric=metric, warm=warm, k_max=k_max, k_min=k_min, k_cap=k_cap, tol=tol,
+             lin_iters=lin_iters)
         if record:
             traj.append((st.q.copy(), st.iters, st.rncp))
     return (st, traj) if record else st

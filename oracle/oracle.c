@@ -74,6 +74,7 @@ struct OrMesh {
   double *hs;    /* [nh] hinge scale 3 / (A0 + A1) */
   double *A;     /* [n][n] dense system matrix (scalar block, A = A_s (x) I3) */
   double *L;     /* [n][n] Cholesky factor, lower */
+  double *Adiag; /* [n] diagonal of A^-1 (computed on first use) */
 };
 
 static int ncols(const OrMesh *m) { return m->type == OR_TRI ? 2 : 3; }
@@ -251,7 +252,7 @@ OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elem
 void or_mesh_free(OrMesh *m) {
   if (!m) return;
   free(m->mass); free(m->elems); free(m->D); free(m->w);
-  free(m->hv); free(m->hk); free(m->hs); free(m->A); free(m->L);
+  free(m->hv); free(m->hk); free(m->hs); free(m->A); free(m->L); free(m->Adiag);
   free(m);
 }
 int or_mesh_hinges(const OrMesh *m) { return m->nh; }
@@ -688,6 +689,160 @@ static void newton_block(const OrMesh *m, int metric, const double *Ainv, int k,
   free(rhs);
 }
 
+/* diag(A^-1), one solve per vertex on first use */
+static const double *ainv_diag(OrMesh *m) {
+  if (m->Adiag) return m->Adiag;
+  int n = m->n;
+  m->Adiag = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *e = (double *)calloc(3 * (size_t)n, sizeof(double)), *col = (double *)malloc(sizeof(double) * 3 * n);
+  for (int j = 0; j < n; j++) {
+    e[3 * j] = 1.0;
+    or_solve(m, e, col);
+    m->Adiag[j] = col[3 * j];
+    e[3 * j] = 0.0;
+  }
+  free(e); free(col);
+  return m->Adiag;
+}
+
+/* z = Z x for the full metric, matrix-free: forces m_b R_b^T x_b on the
+ * contact vertices, one solve with A, then at each contact a
+ * D_C(a) R_a (A^-1 f)_{v_a} + (D_y(a) + damping) x_a. */
+static void full_z_apply(const OrMesh *m, int k, const int *cvert, const Lin *lin, const double *x, double *f,
+                         double *u, double *z) {
+  memset(f, 0, sizeof(double) * 3 * m->n);
+  for (int b = 0; b < k; b++) {
+    int v = cvert[b];
+    double mv = m->mass[v];
+    for (int c = 0; c < 3; c++)
+      f[3 * v + c] += mv * (lin[b].R[c] * x[3 * b] + lin[b].R[3 + c] * x[3 * b + 1] + lin[b].R[6 + c] * x[3 * b + 2]);
+  }
+  or_solve(m, f, u);
+  for (int a = 0; a < k; a++) {
+    const Lin *L = lin + a;
+    const double *ua = u + 3 * cvert[a];
+    double Ru[3] = {dot3(L->R, ua), dot3(L->R + 3, ua), dot3(L->R + 6, ua)};
+    for (int r = 0; r < 3; r++) {
+      double s = OR_DAMP * x[3 * a + r];
+      for (int c = 0; c < 3; c++) s += L->DC[3 * r + c] * Ru[c] + L->Dy[3 * r + c] * x[3 * a + c];
+      z[3 * a + r] = s;
+    }
+  }
+}
+
+/* Full-metric Newton step with an iterative Z solve (the "linear-solver
+ * iterations" of the paper's parameter table): mlin steps of GMRES (Saad and
+ * Schultz 1986) on Z dy = rhs from dy = 0, right-preconditioned by the
+ * inverses of Z's 3x3 diagonal blocks, Arnoldi with modified Gram-Schmidt,
+ * Givens rotations for the small least-squares problem; stops early when
+ * the new Arnoldi vector's norm falls below 1e-6 |rhs| (the Krylov space is
+ * exhausted to rounding).  Contacts: the whole list of the environment.
+ * The multiplier update is the one of newton_block. */
+static void newton_gmres(OrMesh *m, int k, const int *cvert, const Lin *lin, const double *u, const double *q,
+                         double *cg, double gmax, int mlin) {
+  int N = 3 * k;
+  if (k == 0 || mlin < 1) return;
+  const double *ad = ainv_diag(m);
+  double *rhs = (double *)malloc(sizeof(double) * N);
+  double *Pinv = (double *)malloc(sizeof(double) * 9 * k);
+  for (int a = 0; a < k; a++) {
+    const Lin *L = lin + a;
+    int v = cvert[a];
+    double du[3] = {u[3 * v] - q[3 * v], u[3 * v + 1] - q[3 * v + 1], u[3 * v + 2] - q[3 * v + 2]};
+    double Rdu[3] = {dot3(L->R, du), dot3(L->R + 3, du), dot3(L->R + 6, du)};
+    for (int r = 0; r < 3; r++) {
+      double s = 0;
+      for (int c = 0; c < 3; c++) s += L->DC[3 * r + c] * Rdu[c];
+      rhs[3 * a + r] = -L->phi[r] - s;
+    }
+    /* diagonal block D_C a_vv m_v + D_y + damping (R R^T = I) and its inverse */
+    double B[9], I[9];
+    for (int t = 0; t < 9; t++) B[t] = L->DC[t] * ad[v] * m->mass[v] + L->Dy[t];
+    for (int r = 0; r < 3; r++) B[4 * r] += OR_DAMP;
+    for (int c = 0; c < 3; c++) {
+      double e3[3] = {0, 0, 0}, A3[9];
+      e3[c] = 1.0;
+      memcpy(A3, B, sizeof A3);
+      gauss_solve(3, A3, e3);
+      for (int r = 0; r < 3; r++) I[3 * r + c] = e3[r];
+    }
+    memcpy(Pinv + 9 * a, I, sizeof I);
+  }
+  double beta = 0;
+  for (int i = 0; i < N; i++) beta += rhs[i] * rhs[i];
+  beta = sqrt(beta);
+  double *dy = (double *)calloc(N, sizeof(double));
+  if (beta > 0) {
+    double *V = (double *)calloc((size_t)(mlin + 1) * N, sizeof(double));
+    double *H = (double *)calloc((size_t)(mlin + 1) * mlin, sizeof(double));  /* H[i][j] at i * mlin + j */
+    double *cs = (double *)calloc(mlin, sizeof(double)), *sn = (double *)calloc(mlin, sizeof(double));
+    double *gv = (double *)calloc(mlin + 1, sizeof(double));
+    double *t = (double *)malloc(sizeof(double) * N), *w = (double *)malloc(sizeof(double) * N);
+    double *f = (double *)malloc(sizeof(double) * 3 * m->n), *uu = (double *)malloc(sizeof(double) * 3 * m->n);
+    for (int i = 0; i < N; i++) V[i] = rhs[i] / beta;
+    gv[0] = beta;
+    int jm = 0;
+    for (int j = 0; j < mlin; j++) {
+      const double *vj = V + (size_t)j * N;
+      for (int a = 0; a < k; a++)
+        for (int r = 0; r < 3; r++) t[3 * a + r] = dot3(Pinv + 9 * a + 3 * r, vj + 3 * a);
+      full_z_apply(m, k, cvert, lin, t, f, uu, w);
+      for (int i = 0; i <= j; i++) {
+        const double *vi = V + (size_t)i * N;
+        double h = 0;
+        for (int e = 0; e < N; e++) h += w[e] * vi[e];
+        H[i * mlin + j] = h;
+        for (int e = 0; e < N; e++) w[e] -= h * vi[e];
+      }
+      double hn = 0;
+      for (int e = 0; e < N; e++) hn += w[e] * w[e];
+      hn = sqrt(hn);
+      H[(j + 1) * mlin + j] = hn;
+      for (int i = 0; i < j; i++) {  /* previous rotations on column j */
+        double a0 = H[i * mlin + j], a1 = H[(i + 1) * mlin + j];
+        H[i * mlin + j] = cs[i] * a0 + sn[i] * a1;
+        H[(i + 1) * mlin + j] = -sn[i] * a0 + cs[i] * a1;
+      }
+      double a0 = H[j * mlin + j], a1 = H[(j + 1) * mlin + j], rr = sqrt(a0 * a0 + a1 * a1);
+      cs[j] = rr > 0 ? a0 / rr : 1.0;
+      sn[j] = rr > 0 ? a1 / rr : 0.0;
+      H[j * mlin + j] = rr;
+      H[(j + 1) * mlin + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      jm = j + 1;
+      if (hn <= 1e-6 * beta) break;
+      for (int e = 0; e < N; e++) V[(size_t)(j + 1) * N + e] = w[e] / hn;
+    }
+    /* H[0..jm)[0..jm) y = g, back substitution; z = V y; dy = P^-1 z */
+    double *y = (double *)calloc(jm > 0 ? jm : 1, sizeof(double));
+    for (int i = jm - 1; i >= 0; i--) {
+      double s = gv[i];
+      for (int c = i + 1; c < jm; c++) s -= H[i * mlin + c] * y[c];
+      y[i] = H[i * mlin + i] != 0 ? s / H[i * mlin + i] : 0.0;
+    }
+    for (int e = 0; e < N; e++) {
+      double s = 0;
+      for (int i = 0; i < jm; i++) s += V[(size_t)i * N + e] * y[i];
+      w[e] = s;
+    }
+    for (int a = 0; a < k; a++)
+      for (int r = 0; r < 3; r++) dy[3 * a + r] = dot3(Pinv + 9 * a + 3 * r, w + 3 * a);
+    free(y); free(V); free(H); free(cs); free(sn); free(gv); free(t); free(w); free(f); free(uu);
+  }
+  for (int a = 0; a < k; a++) {
+    double mv = m->mass[cvert[a]];
+    const double *R = lin[a].R;
+    double *g = cg + 4 * a;
+    g[0] += mv * dy[3 * a];
+    if (g[0] > gmax) g[0] = gmax;
+    double yt1 = dot3(R + 3, g + 1) + mv * dy[3 * a + 1];
+    double yt2 = dot3(R + 6, g + 1) + mv * dy[3 * a + 2];
+    for (int c = 0; c < 3; c++) g[1 + c] = R[3 + c] * yt1 + R[6 + c] * yt2;
+  }
+  free(dy); free(rhs); free(Pinv);
+}
+
 int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const int *otype,
                   const double *odims, const double *ocomp, const double *pose_t,
                   const double *pose_th, double *q, double *v, const double *q_init, int count,
@@ -747,8 +902,10 @@ int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const
     if (metric == 0) {
       for (int t = 0; t < ngrp; t++)
         newton_block(m, 0, NULL, grp[t + 1] - grp[t], all + grp[t], cvert, lin, u, qc, cgamma, gmax);
-    } else if (count > 0) {
+    } else if (metric == 1 && count > 0) {
       newton_block(m, 1, Ainv, count, all, cvert, lin, u, qc, cgamma, gmax);
+    } else if (metric == 2) {
+      newton_gmres((OrMesh *)m, count, cvert, lin, u, qc, cgamma, gmax, ip[OR_IP_LINIT]);
     }
     /* q^k = A^-1 (b + J^T gamma^k) */
     memcpy(g, b, vb);

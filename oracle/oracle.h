@@ -54,7 +54,9 @@ typedef struct OrMesh OrMesh;
 #define OR_IP_KMIN 1
 #define OR_IP_KCAP 2
 #define OR_IP_MODE 3   /* 0: exactly k_max iterations; 1: until r_ncp <= tol */
-#define OR_IP_METRIC 4 /* 0: lite  J M^-1 J^T + E;  1: full  J A^-1 J^T + E */
+#define OR_IP_METRIC 4 /* 0: lite  J M^-1 J^T + E;  1: full  J A^-1 J^T + E (exact solve);
+                          2: full, Z solved by OR_IP_LINIT steps of preconditioned GMRES */
+#define OR_IP_LINIT 5  /* linear-solver iterations of metric 2 */
 #define OR_NIP 5
 
 OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elems,

@@ -45,6 +45,9 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // most lanes chosen automatically
 constexpr int kMaxAutoLanes = 4, kMaxAutoLanesGroups = 8;
+// most linear-solver iterations of the full contact metric (the kernels' bound)
+constexpr int kMaxLinIters = 32;
+constexpr int kFmLinFloats = 22;   // per-contact linearisation record of the full metric
 
 // ---------------------------------------------------------------------------
 // element operators: F = Ds Dm^-1 written as F[c][j] = sum_a x_a[c] D[a][j]
@@ -561,8 +564,11 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
   if (desc->mode != FLASH_MODE_FIXED && desc->mode != FLASH_MODE_TOL) return fail(FLASH_EINVAL, "invalid mode");
   if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3) return fail(FLASH_EINVAL, "invalid solve");
   if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
+  if (desc->metric != FLASH_METRIC_LITE && desc->metric != FLASH_METRIC_FULL) return fail(FLASH_EINVAL, "invalid metric");
+  if (desc->lin_iters < 0 || desc->lin_iters > kMaxLinIters) return fail(FLASH_EINVAL, "lin_iters must be 0..32");
   flash_scene *s = new flash_scene();
   s->d = *desc;
+  if (s->d.lin_iters == 0) s->d.lin_iters = 10;
   s->cap = desc->contact_cap;
   *out = s;
   return FLASH_OK;
@@ -663,6 +669,25 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
     g.status = s->status;
     flash_status r = build_group(s, g, st);
     if (r != FLASH_OK) return r;
+    if (s->d.metric == FLASH_METRIC_FULL) {
+      // full metric: per-contact linearisation, Krylov basis, Hessenberg
+      // matrix, rotations, diag(A^-1), and the output of the Krylov applies
+      const int m = s->d.lin_iters;
+      const size_t cc = (size_t)g.N * s->cap;
+      g.fm_m = m;
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_lin, cc * kFmLinFloats));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_V, (size_t)(m + 1) * 3 * cc));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_H, (size_t)g.N * (m + 1) * m));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_cs, (size_t)g.N * m));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_sn, (size_t)g.N * m));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_g, (size_t)g.N * (m + 1)));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_beta, (size_t)g.N));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_jm, (size_t)g.N));
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_u, (size_t)g.cols_pad * g.n_pad));
+      g.fm_adiag_stride = g.eig ? g.n_pad : 0;
+      FLASH_CUDA_TRY(dalloc(s, &g.fm_adiag, g.eig ? (size_t)g.N * g.n_pad : (size_t)g.n_pad));
+      FLASH_CUDA_TRY(launch_fm_adiag(g, st));
+    }
   }
   // env-level arrays
   std::vector<float> mu(s->N), odims((size_t)s->N * FLASH_MAX_OBS * 3, 0.f), ocomp((size_t)s->N * FLASH_MAX_OBS, 0.f);
@@ -878,9 +903,31 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (const Lane &L : s->lanes)
       if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+    if (s->d.metric == FLASH_METRIC_FULL) {
+      // Newton step on the full metric: GMRES, one A^-1 application per step
+      for (const Lane &L : s->lanes)
+        if (e == cudaSuccess)
+          e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_fm_setup_lane(s, L, a, lane_stream(L, st)); });
+      for (int j = 0; j < s->d.lin_iters && e == cudaSuccess; j++) {
+        for (const Lane &L : s->lanes)
+          if (e == cudaSuccess)
+            e = timed(s, FLASH_KIND_NCP, lane_stream(L, st),
+                      [&] { return launch_fm_scatter_lane(s, L, a, j, tc, lane_stream(L, st)); });
+        for (const Lane &L : s->lanes)
+          if (e == cudaSuccess)
+            e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.fm_u; });
+        for (const Lane &L : s->lanes)
+          if (e == cudaSuccess)
+            e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_fm_gather_lane(s, L, a, j, lane_stream(L, st)); });
+      }
+      for (const Lane &L : s->lanes)
+        if (e == cudaSuccess)
+          e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_fm_finish_lane(s, L, a, tc, lane_stream(L, st)); });
+    } else {
     for (const Lane &L : s->lanes)
       if (e == cudaSuccess)
         e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_ncp_lane(s, L, a, tc, lane_stream(L, st)); });
+    }
     for (const Lane &L : s->lanes)
       if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
     return e;

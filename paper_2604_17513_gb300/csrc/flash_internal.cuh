@@ -88,6 +88,11 @@ struct Group {
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
   int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner
+  // full contact metric (flash_scene_desc.metric = FLASH_METRIC_FULL)
+  float *fm_lin = nullptr, *fm_V = nullptr, *fm_H = nullptr, *fm_cs = nullptr, *fm_sn = nullptr, *fm_g = nullptr;
+  float *fm_beta = nullptr, *fm_adiag = nullptr, *fm_u = nullptr;
+  int *fm_jm = nullptr;
+  int fm_m = 0, fm_adiag_stride = 0;
   size_t smem_local = 0;
   bool c_in_smem = true;                  // element forces and CSR tables in shared memory
   float *cscratch = nullptr;              // element forces [N][ev + 1][3] when they do not fit
@@ -214,6 +219,14 @@ cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArg
                               cudaStream_t st, int *launched);
 cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);
 cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
+// full contact metric: Newton step with preconditioned GMRES on Z = J A^-1 J^T + E
+cudaError_t launch_fm_setup_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_fm_scatter_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int j, int tc,
+                                   cudaStream_t st);
+cudaError_t launch_fm_gather_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int j, cudaStream_t st);
+cudaError_t launch_fm_finish_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);
+// diag(A_e^-1) of every environment of an eigen-form group, and of a dense inverse
+cudaError_t launch_fm_adiag(const Group &g, cudaStream_t st);
 
 // global solve (gemm_simt.cu / gemm_tc.cu) -----------------------------------
 // out = M * rhs over columns [c0, c1) of a group (c1 < 0: all), M = A^-1, V or V^T (the CUDA-core

@@ -34,6 +34,16 @@ struct GroupView {
   float *cgam, *pgam, *cscratch;
   int c_in_smem;
   float tau;           // contact thickness of the group's mesh
+  // full contact metric (iterative Z solve); null unless the scene uses it
+  float *fm_lin;       // [N][cap][kFmLin] per contact: R, cn, Ct, dn, dtn, Dtt, preconditioner scale s
+  float *fm_V;         // [N][m + 1][3 cap] Krylov basis
+  float *fm_H;         // [N][(m + 1) m] Hessenberg matrix after the rotations, H[i][j] at i m + j
+  float *fm_cs, *fm_sn, *fm_g;   // [N][m], [N][m], [N][m + 1] Givens rotations and rotated right side
+  float *fm_beta;      // [N] norm of the right side
+  int *fm_jm;          // [N] Arnoldi columns built; negative once the basis stopped early
+  const float *fm_adiag;   // [N or 1][n_pad] diagonal of A^-1 (fm_adiag_stride 0: shared)
+  float *fm_u;         // [cols_pad][n_pad] A^-1 applied to the Krylov forces
+  int fm_m, fm_adiag_stride;
 };
 
 struct EnvView {
@@ -53,6 +63,9 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch;
   v.c_in_smem = g.c_in_smem ? 1 : 0;
   v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
+  v.fm_lin = g.fm_lin; v.fm_V = g.fm_V; v.fm_H = g.fm_H; v.fm_cs = g.fm_cs; v.fm_sn = g.fm_sn; v.fm_g = g.fm_g;
+  v.fm_beta = g.fm_beta; v.fm_jm = g.fm_jm; v.fm_adiag = g.fm_adiag; v.fm_u = g.fm_u; v.fm_m = g.fm_m;
+  v.fm_adiag_stride = g.fm_adiag_stride;
   v.kenv = g.eig ? g.kenv : nullptr;
   v.tau = (float)g.tau;
   return v;
@@ -760,6 +773,349 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
 }
 
 // ---------------------------------------------------------------------------
+// Full contact metric (Sec. III-C, Eq. schur): Z = J A^-1 J^T + E instead of
+// the lite J M^-1 J^T + E.  Per environment and local-global iteration the
+// Newton system Z dy = rhs over all its contacts is solved by m steps of
+// GMRES (the paper's "linear-solver iterations") from dy = 0,
+// right-preconditioned by the inverses of Z's 3x3 diagonal blocks
+// D_C a_vv m_v + D_y (+ damping), Arnoldi with classical Gram-Schmidt and
+// one reorthogonalisation, Givens rotations for the least-squares problem;
+// the basis stops early once a new Arnoldi vector's norm is below 1e-6 |rhs|.
+// Z is applied matrix-free: forces m_v R^T x on the contact vertices
+// (fm_scatter), one A^-1 contraction over all environments (the group's
+// global solve), then D_C R u + (D_y + damping) x at each contact
+// (fm_gather).  fm_finish forms dy, updates the multipliers and writes
+// J^T dgamma like the lite NCP kernel.
+// ---------------------------------------------------------------------------
+constexpr int kFmLin = 22;   // floats per contact: R[9], cn, Ct[4], dn, dtn[2], Dtt[4], s
+constexpr int kFmMax = 32;   // most linear-solver iterations
+
+__device__ __forceinline__ void fm_store(float *d, const ContactLin &L, float sc) {
+#pragma unroll
+  for (int t = 0; t < 9; t++) d[t] = L.R[t];
+  d[9] = L.cn;
+#pragma unroll
+  for (int t = 0; t < 4; t++) d[10 + t] = L.Ct[t];
+  d[14] = L.dn; d[15] = L.dtn[0]; d[16] = L.dtn[1];
+#pragma unroll
+  for (int t = 0; t < 4; t++) d[17 + t] = L.Dtt[t];
+  d[21] = sc;
+}
+
+__device__ __forceinline__ float fm_load(const float *d, ContactLin &L) {
+#pragma unroll
+  for (int t = 0; t < 9; t++) L.R[t] = d[t];
+  L.cn = d[9];
+#pragma unroll
+  for (int t = 0; t < 4; t++) L.Ct[t] = d[10 + t];
+  L.dn = d[14]; L.dtn[0] = d[15]; L.dtn[1] = d[16];
+#pragma unroll
+  for (int t = 0; t < 4; t++) L.Dtt[t] = d[17 + t];
+  return d[21];
+}
+
+// x = P^-1 v with P = D_C s + D_y + damping (s = a_vv m_v): the lite block
+// with the D_C rows scaled by s
+__device__ __forceinline__ void fm_pinv(const ContactLin &L, float sc, const float v[3], float x[3]) {
+  ContactLin Ls = L;
+  Ls.cn *= sc;
+#pragma unroll
+  for (int t = 0; t < 4; t++) Ls.Ct[t] *= sc;
+  solve_single_block(Ls, v, x);
+}
+
+__device__ float block_sum(float v, float *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < nw; w++) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
+// block-wide sums of cnt (<= kFmMax + 1) values per thread, in place
+__device__ void block_sum_n(float *v, int cnt, float (*sh)[kFmMax + 1]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < cnt; i++) {
+    float x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][i] = x;
+  }
+  __syncthreads();
+  for (int i = 0; i < cnt; i++) {
+    float t = 0.f;
+    for (int w = 0; w < nw; w++) t += sh[w][i];
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
+// right side, stored linearisation and first Arnoldi vector
+__device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, const EnvView &V, StepArgs a) {
+  __shared__ ObsShared O;
+  __shared__ float sh[32];
+  a.tau = G.tau;
+  const int e = G.genv[l];
+  if (V.done[e]) return;
+  const int np = G.n_pad, cap = G.cap, m = G.fm_m;
+  const size_t N3 = 3 * (size_t)cap;
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * cap, *cobs = G.cobs + (size_t)l * cap;
+  const float *gam = G.cgam + (size_t)l * cap * 4;
+  const float *q = G.q + (size_t)l * 3 * np, *w = G.w + (size_t)l * 3 * np, *qt = G.qt + (size_t)l * 3 * np;
+  const float *ad = G.fm_adiag + (size_t)l * G.fm_adiag_stride;
+  float *lin = G.fm_lin + (size_t)l * cap * kFmLin;
+  float *V0 = G.fm_V + (size_t)l * (m + 1) * N3;
+  const float mu = V.mu[e];
+  load_obstacles(V, e, a.K, O);
+  __syncthreads();
+  float ss = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    const int vtx = cvert[c];
+    const float mv = __ldg(G.mass + vtx);
+    const V3 x = v3(q[vtx], q[np + vtx], q[2 * np + vtx]);
+    const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
+    const V3 du = v3(w[vtx], w[np + vtx], w[2 * np + vtx]);   // u - q^{k-1} = A^-1 r
+    ContactLin L;
+    lin_at(O, cobs[c], a, mu, mv, x, xt, gam + 4 * c, L);
+    const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
+    const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
+    const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
+    const float b0 = -L.phi[0] - L.cn * Rdu0;
+    const float b1 = -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2);
+    const float b2 = -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2);
+    fm_store(lin + (size_t)c * kFmLin, L, ad[vtx] * mv);
+    V0[3 * c] = b0; V0[3 * c + 1] = b1; V0[3 * c + 2] = b2;
+    ss += b0 * b0 + b1 * b1 + b2 * b2;
+  }
+  const float beta = sqrtf(block_sum(ss, sh));
+  if (threadIdx.x == 0) {
+    G.fm_beta[l] = beta;
+    G.fm_g[(size_t)l * (m + 1)] = beta;
+    G.fm_jm[l] = beta > 0.f ? 0 : -1;    // -1: stopped with no column
+  }
+  if (beta > 0.f)
+    for (int c = threadIdx.x; c < cnt; c += blockDim.x)
+      for (int r = 0; r < 3; r++) V0[3 * c + r] = V0[3 * c + r] / beta;
+}
+
+// forces m_v R^T P^-1 v_j on the contact vertices, written as the group's
+// right-hand columns (f16 split on the tensor-core path)
+__device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l, const EnvView &V, int j, int tc) {
+  extern __shared__ float fs[];   // [3][n]
+  __shared__ float sh3[32][3];
+  const int e = G.genv[l];
+  if (V.done[e] || G.fm_jm[l] < 0) return;
+  const int n = G.n, np = G.n_pad, cap = G.cap, m = G.fm_m;
+  const size_t N3 = 3 * (size_t)cap;
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * cap;
+  const float *lin = G.fm_lin + (size_t)l * cap * kFmLin;
+  const float *Vj = G.fm_V + ((size_t)l * (m + 1) + j) * N3;
+  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) fs[i] = 0.f;
+  __syncthreads();
+  float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    const int vtx = cvert[c];
+    if (c > 0 && cvert[c - 1] == vtx) continue;
+    const float mv = __ldg(G.mass + vtx);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int cc = c; cc < cnt && cvert[cc] == vtx; cc++) {
+      ContactLin L;
+      const float sc = fm_load(lin + (size_t)cc * kFmLin, L);
+      const float v[3] = {Vj[3 * cc], Vj[3 * cc + 1], Vj[3 * cc + 2]};
+      float t[3];
+      fm_pinv(L, sc, v, t);
+      fx += mv * (L.R[0] * t[0] + L.R[3] * t[1] + L.R[6] * t[2]);
+      fy += mv * (L.R[1] * t[0] + L.R[4] * t[1] + L.R[7] * t[2]);
+      fz += mv * (L.R[2] * t[0] + L.R[5] * t[1] + L.R[8] * t[2]);
+    }
+    fs[vtx] = fx; fs[n + vtx] = fy; fs[2 * n + vtx] = fz;
+    fm0 = fmaxf(fm0, fabsf(fx)); fm1 = fmaxf(fm1, fabsf(fy)); fm2 = fmaxf(fm2, fabsf(fz));
+  }
+  __syncthreads();
+  if (tc) {
+    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
+  } else {
+    float *f = G.f + (size_t)l * 3 * np;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      const int c = i / n, jj = i - c * n;
+      f[c * np + jj] = fs[i];
+    }
+  }
+}
+
+// w = Z P^-1 v_j from u = A^-1 f, orthogonalised against v_0..v_j (two
+// classical Gram-Schmidt passes), rotated column j of H, next basis vector
+__device__ __forceinline__ void fm_gather_body(const GroupView &G, const int l, const EnvView &V, int j) {
+  __shared__ float shn[32][kFmMax + 1];
+  __shared__ float sh[32];
+  __shared__ float s_hn;
+  __shared__ int s_stop;
+  const int e = G.genv[l];
+  if (V.done[e] || G.fm_jm[l] < 0) return;
+  const int np = G.n_pad, cap = G.cap, m = G.fm_m;
+  const size_t N3 = 3 * (size_t)cap;
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * cap;
+  const float *lin = G.fm_lin + (size_t)l * cap * kFmLin;
+  const float *u = G.fm_u + (size_t)l * 3 * np;
+  float *Vb = G.fm_V + (size_t)l * (m + 1) * N3;
+  const float *Vj = Vb + (size_t)j * N3;
+  float *Vn = Vb + (size_t)(j + 1) * N3;   // w, then v_{j+1}
+  float d[kFmMax + 1];
+  for (int i = 0; i <= j; i++) d[i] = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    ContactLin L;
+    const float sc = fm_load(lin + (size_t)c * kFmLin, L);
+    const float v[3] = {Vj[3 * c], Vj[3 * c + 1], Vj[3 * c + 2]};
+    float t[3];
+    fm_pinv(L, sc, v, t);
+    const int vtx = cvert[c];
+    const float ux = u[vtx], uy = u[np + vtx], uz = u[2 * np + vtx];
+    const float Ru0 = L.R[0] * ux + L.R[1] * uy + L.R[2] * uz;
+    const float Ru1 = L.R[3] * ux + L.R[4] * uy + L.R[5] * uz;
+    const float Ru2 = L.R[6] * ux + L.R[7] * uy + L.R[8] * uz;
+    const float z0 = L.cn * Ru0 + (L.dn + kDamp) * t[0];
+    const float z1 = L.Ct[0] * Ru1 + L.Ct[1] * Ru2 + L.dtn[0] * t[0] + (L.Dtt[0] + kDamp) * t[1] + L.Dtt[1] * t[2];
+    const float z2 = L.Ct[2] * Ru1 + L.Ct[3] * Ru2 + L.dtn[1] * t[0] + L.Dtt[2] * t[1] + (L.Dtt[3] + kDamp) * t[2];
+    Vn[3 * c] = z0; Vn[3 * c + 1] = z1; Vn[3 * c + 2] = z2;
+    for (int i = 0; i <= j; i++) {
+      const float *vi = Vb + (size_t)i * N3 + 3 * c;
+      d[i] += z0 * vi[0] + z1 * vi[1] + z2 * vi[2];
+    }
+  }
+  block_sum_n(d, j + 1, shn);
+  float d2[kFmMax + 1];
+  for (int i = 0; i <= j; i++) d2[i] = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x)
+    for (int r = 0; r < 3; r++) {
+      float z = Vn[3 * c + r];
+      for (int i = 0; i <= j; i++) z -= d[i] * Vb[(size_t)i * N3 + 3 * c + r];
+      Vn[3 * c + r] = z;
+      for (int i = 0; i <= j; i++) d2[i] += z * Vb[(size_t)i * N3 + 3 * c + r];
+    }
+  block_sum_n(d2, j + 1, shn);
+  float hs = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x)
+    for (int r = 0; r < 3; r++) {
+      float z = Vn[3 * c + r];
+      for (int i = 0; i <= j; i++) z -= d2[i] * Vb[(size_t)i * N3 + 3 * c + r];
+      Vn[3 * c + r] = z;
+      hs += z * z;
+    }
+  const float hn = sqrtf(block_sum(hs, sh));
+  if (threadIdx.x == 0) {
+    float *H = G.fm_H + (size_t)l * (m + 1) * m;
+    float *cs = G.fm_cs + (size_t)l * m, *sn = G.fm_sn + (size_t)l * m, *g = G.fm_g + (size_t)l * (m + 1);
+    float h[kFmMax + 1];
+    for (int i = 0; i <= j; i++) h[i] = d[i] + d2[i];
+    h[j + 1] = hn;
+    for (int i = 0; i < j; i++) {   // earlier rotations on column j
+      const float a0 = h[i], a1 = h[i + 1];
+      h[i] = cs[i] * a0 + sn[i] * a1;
+      h[i + 1] = -sn[i] * a0 + cs[i] * a1;
+    }
+    const float a0 = h[j], a1 = h[j + 1], rr = sqrtf(a0 * a0 + a1 * a1);
+    cs[j] = rr > 0.f ? a0 / rr : 1.f;
+    sn[j] = rr > 0.f ? a1 / rr : 0.f;
+    h[j] = rr;
+    for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = h[i];
+    H[(size_t)(j + 1) * m + j] = 0.f;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const int stop = hn <= 1e-6f * G.fm_beta[l];
+    G.fm_jm[l] = stop ? -(j + 1) - 1 : j + 1;
+    s_hn = hn;
+    s_stop = stop;
+  }
+  __syncthreads();
+  if (!s_stop)
+    for (int c = threadIdx.x; c < cnt; c += blockDim.x)
+      for (int r = 0; r < 3; r++) Vn[3 * c + r] = Vn[3 * c + r] / s_hn;
+}
+
+// dy = P^-1 V y from the triangular system, multiplier update and J^T dgamma
+__device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, const EnvView &V, const StepArgs &a,
+                                               int tc) {
+  extern __shared__ float fs[];   // [3][n]
+  __shared__ float sh3[32][3];
+  __shared__ float ys[kFmMax];
+  const int e = G.genv[l];
+  if (V.done[e]) return;
+  const int n = G.n, np = G.n_pad, cap = G.cap, m = G.fm_m;
+  const size_t N3 = 3 * (size_t)cap;
+  const int jv = G.fm_jm[l], jm = jv < 0 ? -jv - 1 : jv;
+  if (threadIdx.x == 0) {
+    const float *H = G.fm_H + (size_t)l * (m + 1) * m, *g = G.fm_g + (size_t)l * (m + 1);
+    for (int i = jm - 1; i >= 0; i--) {
+      float sacc = g[i];
+      for (int c = i + 1; c < jm; c++) sacc -= H[(size_t)i * m + c] * ys[c];
+      const float hii = H[(size_t)i * m + i];
+      ys[i] = hii != 0.f ? sacc / hii : 0.f;
+    }
+  }
+  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) fs[i] = 0.f;
+  __syncthreads();
+  const int cnt = G.ccount[l];
+  const int *cvert = G.cvert + (size_t)l * cap;
+  const float *lin = G.fm_lin + (size_t)l * cap * kFmLin;
+  const float *Vb = G.fm_V + (size_t)l * (m + 1) * N3;
+  float *gam = G.cgam + (size_t)l * cap * 4;
+  float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    const int vtx = cvert[c];
+    if (c > 0 && cvert[c - 1] == vtx) continue;
+    const float mv = __ldg(G.mass + vtx);
+    V3 fsum = v3(0.f, 0.f, 0.f);
+    for (int cc = c; cc < cnt && cvert[cc] == vtx; cc++) {
+      ContactLin L;
+      const float sc = fm_load(lin + (size_t)cc * kFmLin, L);
+      float z[3] = {0.f, 0.f, 0.f};
+      for (int i = 0; i < jm; i++)
+        for (int r = 0; r < 3; r++) z[r] += ys[i] * Vb[(size_t)i * N3 + 3 * cc + r];
+      float dy[3];
+      fm_pinv(L, sc, z, dy);
+      fsum = fsum + apply_update(L, mv, a.gmax, dy, gam + 4 * cc);
+    }
+    fs[vtx] = fsum.x; fs[n + vtx] = fsum.y; fs[2 * n + vtx] = fsum.z;
+    fm0 = fmaxf(fm0, fabsf(fsum.x)); fm1 = fmaxf(fm1, fabsf(fsum.y)); fm2 = fmaxf(fm2, fabsf(fsum.z));
+  }
+  __syncthreads();
+  if (tc) {
+    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
+  } else {
+    float *f = G.f + (size_t)l * 3 * np;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+      const int c = i / n, jj = i - c * n;
+      f[c * np + jj] = fs[i];
+    }
+  }
+}
+
+// diag(A^-1): dense inverse (shared by the group's environments) or, for the
+// eigen form, sum_k V[v][k]^2 / (1 + k_e lam_k) per environment
+__global__ void k_fm_adiag(const float *Ainv, const float *Vm, const float *lam, const float *kenv, int n, int np,
+                           float *out) {
+  const int l = blockIdx.y;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (Ainv) {
+      out[v] = Ainv[(size_t)v * np + v];
+    } else {
+      const float ke = kenv[l];
+      float s = 0.f;
+      for (int k = 0; k < n; k++) {
+        const float x = Vm[(size_t)v * np + k];
+        s += x * x / (1.f + ke * lam[k]);
+      }
+      out[(size_t)l * np + v] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // end of step: velocity, keep the contact list for warm starts
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void end_body(const GroupView &G, const int l, const EnvView &V, const StepArgs &a) {
@@ -806,6 +1162,27 @@ __global__ void __launch_bounds__(256) k_end_tab(const GroupView *__restrict__ t
                                                  EnvView V, StepArgs a) {
   const int2 b = map[blockIdx.x];
   end_body(tab[b.x], b.y, V, a);
+}
+
+__global__ void __launch_bounds__(256) k_fm_setup_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                      EnvView V, StepArgs a) {
+  const int2 b = map[blockIdx.x];
+  fm_setup_body(tab[b.x], b.y, V, a);
+}
+__global__ void __launch_bounds__(256) k_fm_scatter_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                        EnvView V, int j, int tc) {
+  const int2 b = map[blockIdx.x];
+  fm_scatter_body(tab[b.x], b.y, V, j, tc);
+}
+__global__ void __launch_bounds__(256) k_fm_gather_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                       EnvView V, int j) {
+  const int2 b = map[blockIdx.x];
+  fm_gather_body(tab[b.x], b.y, V, j);
+}
+__global__ void __launch_bounds__(256) k_fm_finish_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+                                                       EnvView V, StepArgs a, int tc) {
+  const int2 b = map[blockIdx.x];
+  fm_finish_body(tab[b.x], b.y, V, a, tc);
 }
 
 // user layout [sum n_e][3] <-> group columns [N_g][3][n_pad]
@@ -1006,6 +1383,10 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fm_scatter_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fm_finish_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
 
@@ -1192,6 +1573,39 @@ cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs 
 cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
   if (!L.all.blocks) return cudaSuccess;
   k_end_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fm_setup_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
+  if (!L.all.blocks) return cudaSuccess;
+  k_fm_setup_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fm_scatter_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int j, int tc,
+                                   cudaStream_t st) {
+  (void)a;
+  if (!L.all.blocks) return cudaSuccess;
+  k_fm_scatter_tab<<<L.all.blocks, 256, L.ncp_smem_tc, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), j, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fm_gather_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int j, cudaStream_t st) {
+  (void)a;
+  if (!L.all.blocks) return cudaSuccess;
+  k_fm_gather_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fm_finish_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st) {
+  if (!L.all.blocks) return cudaSuccess;
+  k_fm_finish_tab<<<L.all.blocks, 256, L.ncp_smem_tc, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fm_adiag(const Group &g, cudaStream_t st) {
+  dim3 grid((g.n + 255) / 256, g.eig ? g.N : 1);
+  k_fm_adiag<<<grid, 256, 0, st>>>(g.eig ? nullptr : g.inv.f32, g.V.f32, g.lam, g.kenv, g.n, g.n_pad, g.fm_adiag);
   return cudaGetLastError();
 }
 

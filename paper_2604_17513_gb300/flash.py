@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3,
 WOVERFLOW = 1
 MAX_OBS = 8
 MODE_FIXED, MODE_TOL = 0, 1
+METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -36,7 +37,8 @@ class SceneDesc(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("tol_ncp", C.c_double), ("maxforce", C.c_double),
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
-                ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
+                ("lin_iters", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class MeshDesc(C.Structure):
@@ -136,7 +138,7 @@ class Sim:
     """
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
-                 warm=WARM_COLD, contact_cap=None, lanes=0, eager=False):
+                 warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -157,6 +159,8 @@ class Sim:
         d.warm = warm
         d.lanes = lanes
         d.eager = 1 if eager else 0
+        d.metric = metric
+        d.lin_iters = lin_iters
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))

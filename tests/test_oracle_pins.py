@@ -289,6 +289,37 @@ def test_lite_and_full_metric_share_the_fixed_point():
     assert b.iters < a.iters
 
 
+def test_gmres_full_metric_exhausted_space_equals_exact_solve():
+    """Full metric with the iterative Z solve (metric 2): when the linear
+    iterations reach the dimension 3C of the contact system, GMRES has
+    searched the whole space and every Newton step equals the exact dense
+    solve of metric 1, in every local-global iterate."""
+    sc = _small_bending_cloth(0.05)
+    sc.mu[:] = 0.3
+    mesh = oracle.Mesh.from_scene(sc)
+    a = oracle.EnvState(sc.q0[0], sc.v0[0])
+    b = oracle.EnvState(sc.q0[0], sc.v0[0])
+    oracle.step(mesh, sc, 0, 0, a, k_max=6, metric=1)
+    oracle.step(mesh, sc, 0, 0, b, k_max=6, metric=2, lin_iters=3 * 9)
+    assert len(a.cvert) == 9
+    assert np.abs(a.q - b.q).max() < 1e-10 and np.abs(a.gamma - b.gamma).max() < 1e-10 * np.abs(a.gamma).max()
+
+
+def test_gmres_full_metric_shares_the_fixed_point():
+    """With 10 linear iterations (fewer than the 3C = 27 unknowns) each Newton
+    step is inexact, but run to convergence the full metric lands on the
+    same state as the lite metric and the exact full metric."""
+    sc = _small_bending_cloth(0.05)
+    sc.mu[:] = 0.3
+    mesh = oracle.Mesh.from_scene(sc)
+    a = oracle.EnvState(sc.q0[0], sc.v0[0])
+    c = oracle.EnvState(sc.q0[0], sc.v0[0])
+    oracle.step(mesh, sc, 0, 0, a, mode=1, metric=0, tol=1e-11, k_cap=5000)
+    oracle.step(mesh, sc, 0, 0, c, mode=1, metric=2, lin_iters=10, tol=1e-11, k_cap=500)
+    assert c.rncp <= 1e-11
+    assert np.abs(a.q - c.q).max() < 1e-9
+
+
 def _small_bending_cloth(tilt):
     rest, tris = scenes.cloth_grid(3, 3, 0.2)
     n = len(rest)
