@@ -45,6 +45,9 @@ def parse():
                    help="fixed: k iterations per step; tol: iterate until r_ncp <= 1e-5 (cap --k-cap)")
     p.add_argument("--k-cap", type=int, default=200, help="iteration cap of the tolerance mode")
     p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
+    p.add_argument("--metric", default="lite", choices=["lite", "full"],
+                   help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve")
+    p.add_argument("--lin-iters", type=int, default=10, help="linear-solver (GMRES) iterations of the full metric")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
     p.add_argument("--no-e2e", action="store_true")
@@ -172,10 +175,11 @@ def scaled_traffic(t, envs_per_launch):
 
 
 def oracle_mode_kw(args):
-    """Oracle stopping rule matching the GPU arm's --mode."""
-    if args.mode == "tol":
-        return {"mode": 1, "tol": TOL, "k_min": 1, "k_cap": args.k_cap}
-    return {}
+    """Oracle stopping rule and contact metric matching the GPU arm's options."""
+    kw = {"mode": 1, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
+    if args.metric == "full":
+        kw.update(metric=2, lin_iters=args.lin_iters)
+    return kw
 
 
 def mode_desc(args):
@@ -287,6 +291,8 @@ def main():
         workload = (f"mixed: {args.envs} envs, cloths of side U{{16..64}} and tet blocks of 200-3000 verts "
                     f"({len(sc)} templates), 1-4 boxes/spheres, h=1/100")
     mode_kw = {"mode": flash.MODE_TOL, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
+    if args.metric == "full":
+        mode_kw.update(metric=flash.METRIC_FULL, lin_iters=args.lin_iters)
     warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
     try:
         sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, **mode_kw)
@@ -410,13 +416,17 @@ def main():
     tmpl = [(s_.n_verts, s_.n_envs) for s_ in scs]
     n_sum = sum(nv * ne for nv, ne in tmpl)          # vertices over all environments
     eig = args.workload == "tet_squeeze"
-    dom = max(prof, key=lambda k: prof[k][0])
+    # dominant kernel class with an algorithmic model (with the full metric the
+    # "ncp" class times the GMRES kernels, which the byte model does not cover)
+    modelled = [k for k in prof if prof[k][1] and not (args.metric == "full" and k == "ncp")]
+    dom = max(modelled, key=lambda k: prof[k][0])
     d_ms, d_n = prof[dom]
     avg_s = d_ms / max(d_n, 1) / 1e3
     # passes of each kernel class over every environment per step (Mode A:
     # k local-global iterations + one residual pass; Mode B: the mean count)
     it_pp = float(args.k) if args.mode == "fixed" else max(mean_iters, 1e-9)
-    passes = {"local": it_pp + 1, "ncp": it_pp, "solve": 2 * it_pp, "begin": 1, "end": 1, "warm": 1}[dom]
+    applies = 2 + (args.lin_iters if args.metric == "full" else 0)   # A^-1 applications per iteration
+    passes = {"local": it_pp + 1, "ncp": it_pp, "solve": applies * it_pp, "begin": 1, "end": 1, "warm": 1}[dom]
     # achieved = the kind's algorithmic work over the profiled steps / its
     # summed launch time (= per-launch work / mean launch time for any launch
     # split, e.g. lanes or mesh groups)
@@ -470,6 +480,7 @@ def main():
             "config": {"workload": workload,
                        "mode": args.mode, "k": args.k if args.mode == "fixed" else None,
                        "k_cap": args.k_cap if args.mode == "tol" else None, "warm": args.warm,
+                       "metric": args.metric if args.metric == "lite" else f"full, {args.lin_iters} GMRES iterations",
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),

@@ -20,20 +20,20 @@ def _f32(x):
     return np.asarray(x, np.float32).astype(np.float64)
 
 
-def _oracle_state(sc, e, s):
+def _oracle_state(sc, e, s, metric=0):
     mesh = oracle.Mesh.from_scene(sc, e)
     st = oracle.EnvState(sc.q0[e], sc.v0[e])
     for k in range(s):
-        oracle.step(mesh, sc, e, k, st)
+        oracle.step(mesh, sc, e, k, st, metric=metric)
     return mesh, _f32(st.q), _f32(st.v)
 
 
-def _step_all(cuda, scs, qs, vs, s):
+def _step_all(cuda, scs, qs, vs, s, metric=0):
     """One GPU step of every environment of the scenes from (qs, vs) at step s,
     in the bench's configuration (f16x3, automatic lanes, graph replay)."""
     import torch
     from paper_2604_17513_gb300 import flash
-    sim = flash.Sim(scs, solve=flash.SOLVE_F16X3)
+    sim = flash.Sim(scs, solve=flash.SOLVE_F16X3, metric=metric)
     sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
                   torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
     sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
@@ -44,21 +44,23 @@ def _step_all(cuda, scs, qs, vs, s):
     return sim, q
 
 
-def _check(scs, picks, s, cuda, lanes):
-    """picks: (scene index, local environment) pairs checked against the oracle."""
+def _check(scs, picks, s, cuda, lanes, metric=0):
+    """picks: (scene index, local environment) pairs checked against the oracle
+    (GPU metric 1, the full metric, is the oracle's metric 2: the same GMRES)."""
+    om = 2 if metric else 0
     qs = [sc.q0.reshape(-1, 3).copy() for sc in scs]
     vs = [sc.v0.reshape(-1, 3).copy() for sc in scs]
     refs = []
     for si, e in picks:
         sc = scs[si]
-        mesh, q0, v0 = _oracle_state(sc, e, s)
+        mesh, q0, v0 = _oracle_state(sc, e, s, om)
         n = sc.n_verts
         qs[si][e * n:(e + 1) * n] = q0
         vs[si][e * n:(e + 1) * n] = v0
         ref = oracle.EnvState(q0, v0)
-        oracle.step(mesh, sc, e, s, ref)
+        oracle.step(mesh, sc, e, s, ref, metric=om)
         refs.append(ref)
-    sim, q = _step_all(cuda, scs, qs, vs, s)
+    sim, q = _step_all(cuda, scs, qs, vs, s, metric)
     assert sim.lane_count() == lanes
     base = np.cumsum([0] + [sc.n_envs for sc in scs])
     off = sim.offsets
@@ -93,3 +95,12 @@ def test_mixed_batch_full_size(cuda):
     mid = [i for n, i in cloths if 900 <= n <= 1300][0]
     picks = [(cloths[0][1], 0), (tets[0][1], scs[tets[0][1]].n_envs - 1), (mid, 0)]
     _check(scs, picks, 8, cuda, lanes=8)
+
+
+def test_tet_squeeze_full_metric_full_size(cuda):
+    """4096 tet blocks with the full contact metric (10 GMRES iterations per
+    Newton step, each an A^-1 application to all 12288 columns), 4 lanes,
+    graph replay; samples at both ends of lanes, from the oracle's
+    full-metric state at step 10 (the plates squeeze)."""
+    sc = scenes.tet_squeeze(seed=1, n_envs=4096, steps=14)
+    _check([sc], [(0, 0), (0, 1023), (0, 1024), (0, 4095)], 10, cuda, lanes=4, metric=1)
