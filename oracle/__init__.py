@@ -19,7 +19,9 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
 _lib = None
 
-DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU = range(9)
+DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU, DP_GRASP_OBS = range(10)
+DP_ANCHOR, DP_SIZE = 10, 13
+GRASP_SLOT = 8   # contact-list slot of grasp constraints (after every obstacle)
 IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC, IP_LINIT = range(6)
 
 
@@ -57,7 +59,7 @@ def lib():
         _lib.or_fb.restype = d
         _lib.or_fb.argtypes = [d, d]
         _lib.or_detect.restype = i
-        _lib.or_detect.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, i, pi, pi]
+        _lib.or_detect.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, C.POINTER(C.c_ubyte), i, pi, pi]
         _lib.or_solve_step.restype = i
         _lib.or_solve_step.argtypes = [C.c_void_p, pd, pi, i, pi, pd, pd, pd, pd, pd, pd, pd, i,
                                        pi, pi, pd, pi, pd, pd]
@@ -158,7 +160,7 @@ def fb(a, b):
 
 def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None, k_cap=None, tol=None,
            lin_iters: int = 10):
-    dp = np.zeros(9)
+    dp = np.zeros(DP_SIZE)
     dp[DP_H] = sc.h
     dp[DP_GX:DP_GZ + 1] = sc.gravity
     dp[DP_TOL] = sc.tol_ncp if tol is None else tol
@@ -166,6 +168,10 @@ def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None,
     dp[DP_TAU] = sc.thickness
     dp[DP_MARGIN] = sc.margin
     dp[DP_MU] = sc.mu[env]
+    g = sc.meta.get("grasp") if sc.meta else None
+    dp[DP_GRASP_OBS] = g["obstacle"] if g else -1
+    if g:
+        dp[DP_ANCHOR:DP_ANCHOR + 3] = g["anchor"]
     ip = np.zeros(6, np.int32)
     ip[IP_KMAX] = sc.k_max if k_max is None else k_max
     ip[IP_KMIN] = sc.k_min if k_min is None else k_min
@@ -186,16 +192,45 @@ class EnvState:
         self.gamma = np.zeros((0, 4))
         self.iters, self.rncp = 0, 0.0
         self.trace = None
+        self.attached = np.zeros(len(self.q), np.uint8)   # grasped vertices
 
 
-def detect(mesh: Mesh, sc, env, step, q, v, dp=None):
+def _to_world(pose, p):
+    """pose = (x, y, z, qw, qx, qy, qz) applied to a body-frame point."""
+    w, x, y, z = pose[3:7]
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    return R @ np.asarray(p, float) + pose[:3]
+
+
+def apply_grasp(sc, env, s, st):
+    """Grasp schedule of the scene (appendix, Bilateral Constraint for Cloth
+    Control) at the start of step s: a request 1 attaches every vertex within
+    the radius of the anchor (gripper pose at the start of the step); 0
+    releases all.  Scenes keep vertices away from the radius boundary, so the
+    FP32 test of the CUDA path takes the same decision."""
+    g = sc.meta.get("grasp") if sc.meta else None
+    if not g:
+        return
+    req = g["schedule"].get(s)
+    if req == 1:
+        p = _to_world(sc.poses[env, s, g["obstacle"]], g["anchor"])
+        st.attached = (np.linalg.norm(st.q - p, axis=1) <= g["radius"]).astype(np.uint8)
+    elif req == 0:
+        st.attached = np.zeros(len(st.q), np.uint8)
+
+
+def detect(mesh: Mesh, sc, env, step, q, v, dp=None, attached=None):
     dp = params(sc, env)[0] if dp is None else dp
     K = sc.n_obs
     ot, od = _i32(sc.obs_type[env]), _f64(sc.obs_dims[env])
     pth = _f64(sc.poses[env, step + 1])
-    cap = mesh.n * K
+    cap = mesh.n * (K + 1)
     cv, co = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    att = None if attached is None else np.ascontiguousarray(attached, np.uint8)
     cnt = lib().or_detect(mesh._p, _pd(dp), K, _pi(ot), _pd(od), _pd(pth), _pd(_f64(q)), _pd(_f64(v)),
+                          None if att is None else att.ctypes.data_as(C.POINTER(C.c_ubyte)),
                           cap, _pi(cv), _pi(co))
     return cv[:cnt].copy(), co[:cnt].copy()
 
@@ -219,7 +254,8 @@ def step(mesh: Mesh, sc, env, s, st: EnvState, mode=None, metric=0, warm="cold",
     metric 0: lite Z = J M^-1 J^T + E; 1: full Z = J A^-1 J^T + E solved
     exactly; 2: full Z solved by ``lin_iters`` steps of preconditioned GMRES."""
     dp, ip = params(sc, env, mode, metric, k_max, k_min, k_cap, tol, lin_iters)
-    cvert, cobs = detect(mesh, sc, env, s, st.q, st.v, dp)
+    apply_grasp(sc, env, s, st)
+    cvert, cobs = detect(mesh, sc, env, s, st.q, st.v, dp, st.attached)
     if gamma0 is not None:
         gam = _f64(gamma0).reshape(len(cvert), 4).copy()
     elif warm == "prev":

@@ -474,8 +474,8 @@ static void tangent_frame(const double *n, double *t1, double *t2) {
 double or_fb(double a, double b) { return a + b - sqrt(a * a + b * b); }
 
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
-              const double *pose_th, const double *q, const double *v, int cap, int *cvert,
-              int *cobs) {
+              const double *pose_th, const double *q, const double *v, const unsigned char *attached,
+              int cap, int *cvert, int *cobs) {
   double h = dp[OR_DP_H], tau = dp[OR_DP_TAU], marg = dp[OR_DP_MARGIN];
   int cnt = 0;
   for (int i = 0; i < m->n; i++) {
@@ -489,6 +489,10 @@ int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const 
         if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = o; }
         cnt++;
       }
+    }
+    if (attached && attached[i]) {
+      if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_GRASP_SLOT; }
+      cnt++;
     }
   }
   return cnt;
@@ -588,12 +592,29 @@ static void gauss_solve(int k, double *A, double *b) {
   }
 }
 
+/* Bilateral grasp row: world axes as the frame, phi = x - p_grip (t+h),
+ * D_C = I (phi moves with the vertex one to one), D_y = 0 (rigid link). */
+static void linearize_grasp(const double *dp, const double *pose_th, const double *x, Lin *L) {
+  double p[3];
+  to_world(pose_th + 7 * (int)dp[OR_DP_GRASP_OBS], dp + OR_DP_ANCHOR, p);
+  memset(L, 0, sizeof *L);
+  for (int r = 0; r < 3; r++) {
+    L->R[4 * r] = 1.0;
+    L->DC[4 * r] = 1.0;
+    L->phi[r] = x[r] - p[r];
+  }
+}
+
 static void contact_lin_all(const OrMesh *m, const double *dp, const int *otype, const double *odims,
                             const double *ocomp, const double *pose_t, const double *pose_th,
                             const double *qt, const double *q, int count, const int *cvert,
                             const int *cobs, const double *cg, Lin *lin) {
   for (int i = 0; i < count; i++) {
     int v = cvert[i], o = cobs[i];
+    if (o == OR_GRASP_SLOT) {
+      linearize_grasp(dp, pose_th, q + 3 * v, lin + i);
+      continue;
+    }
     linearize(otype[o], odims + 3 * o, ocomp[o], pose_t + 7 * o, pose_th + 7 * o, dp[OR_DP_TAU],
               dp[OR_DP_MU], dp[OR_DP_H], m->mass[v], q + 3 * v, qt + 3 * v, cg + 4 * i, lin + i);
   }

@@ -48,6 +48,15 @@ typedef struct OrMesh OrMesh;
 #define OR_DP_TAU 6
 #define OR_DP_MARGIN 7
 #define OR_DP_MU 8
+#define OR_DP_GRASP_OBS 9 /* obstacle carrying the grasp anchor (as a double), -1: no grasp */
+#define OR_DP_ANCHOR 10   /* 10..12: anchor point in that obstacle's frame */
+#define OR_DP_SIZE 13
+
+/* Bilateral grasp (appendix, Bilateral Constraint for Cloth Control): a
+ * grasped vertex i carries the equality C = x_i - p_grip = 0 with p_grip the
+ * anchor at the gripper's pose at t+h.  It sits in the contact list with the
+ * obstacle slot OR_GRASP_SLOT (after every obstacle, so lists stay sorted). */
+#define OR_GRASP_SLOT 8
 #define OR_NDP 9
 /* ip[] (integer parameters) */
 #define OR_IP_KMAX 0
@@ -74,9 +83,11 @@ void or_closest_rotation(int cols, const double *F, double *R); /* 3x2 or 3x3, r
  * over the step for one point; pose = (p, qw, qx, qy, qz) */
 double or_sdf(int type, const double *dims, const double *pose, const double *x, double *nrm);
 
+/* attached: [n] grasp flags (or NULL); a flagged vertex gets an OR_GRASP_SLOT
+ * entry after its obstacle contacts */
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
-              const double *pose_th, const double *q, const double *v, int cap, int *cvert,
-              int *cobs);
+              const double *pose_th, const double *q, const double *v, const unsigned char *attached,
+              int cap, int *cvert, int *cobs);
 
 int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const int *otype,
                   const double *odims, const double *ocomp, const double *pose_t,

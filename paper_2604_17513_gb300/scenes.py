@@ -280,6 +280,55 @@ def cloth_gripper(seed: int = 1, n_envs: int = 1024, n_side: int = 32, side: flo
                  k_max=k_max, thickness=tau, steps=steps)
 
 
+def cloth_grasp(seed: int = 2, n_envs: int = 64, n_side: int = 16, side: float = 0.25, steps: int = 120,
+                k_max: int = 10, grasp_step: int = 2, release_step: int = 90, lift=(0.08, 0.15),
+                inward=(0.03, 0.08), rise_time: float = 0.5) -> Scene:
+    """Cloth lying on the ground, grasped at one corner by a point gripper
+    (appendix, Bilateral Constraint for Cloth Control), lifted, carried and
+    released.
+
+    The gripper is a kinematic pose carrier (obstacle type NONE: no contact of
+    its own) starting on a random corner vertex; at step ``grasp_step`` every
+    vertex within 0.3 grid spacings of its anchor is attached (the corner
+    vertex), the corner is lifted by U[lift] m over ``rise_time`` s while
+    moving U[inward] m towards the centre, held, and released at
+    ``release_step``.
+    mu ~ U[0.2, 0.8]; h = 1/100 s.  The grasp schedule is in meta["grasp"].
+    """
+    rest, tris = cloth_grid(n_side, n_side, side)
+    n = len(rest)
+    mass = np.full(n, 0.1 * side * side / 0.25 / n)
+    tau = 1e-3
+    q0 = np.repeat(rest[None], n_envs, 0).copy()
+    q0[:, :, 2] = tau
+    K = 2
+    obs_type = np.tile(np.array([PLANE, NONE], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, K, 3))
+    mu = np.zeros(n_envs)
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    h = 0.01
+    corners = [0, n_side - 1, n - n_side, n - 1]
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        mu[e] = g.uniform(0.2, 0.8)
+        c = corners[int(g.integers(0, 4))]
+        up = g.uniform(*lift)
+        shift = g.uniform(*inward)
+        p0 = np.array([rest[c, 0], rest[c, 1], tau])
+        d = -np.sign(p0[:2])
+        poses[e, :, 0] = _pose((0, 0, 0))
+        for s_ in range(steps + 1):
+            u = min(1.0, max(0.0, (s_ - grasp_step) * h / rise_time))
+            p = p0 + np.array([d[0] * shift * u / np.sqrt(2), d[1] * shift * u / np.sqrt(2), up * u])
+            poses[e, s_, 1] = _pose(p)
+    spacing = side / (n_side - 1)
+    meta = {"grasp": {"obstacle": 1, "anchor": (0.0, 0.0, 0.0), "radius": 0.3 * spacing,
+                      "schedule": {grasp_step: 1, release_step: 0}}}
+    return Scene("cloth_grasp", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0),
+                 mu, np.ones(n_envs), obs_type, obs_dims, np.zeros((n_envs, K)), poses, h=h,
+                 k_max=k_max, thickness=tau, steps=steps, meta=meta)
+
+
 def tet_squeeze(seed: int = 1, n_envs: int = 4096, cubes=(8, 8, 4), size=(0.08, 0.08, 0.04),
                 steps: int = 100, k_max: int = 10, mu: float = 0.5) -> Scene:
     """Soft tet block on the ground squeezed by a kinematic parallel gripper.

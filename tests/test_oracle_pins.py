@@ -388,3 +388,86 @@ def test_mlp_gradient_finite_differences():
         e[i] = 1e-6
         fd = (oracle.mlp_loss_grad(p + e, x, t)[0] - oracle.mlp_loss_grad(p - e, x, t)[0]) / 2e-6
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+# ---------------------------------------------------------------------------
+# bilateral grasp (appendix, Bilateral Constraint for Cloth Control)
+# ---------------------------------------------------------------------------
+def _grasp_scene(release_step=45):
+    """6x6 cloth of side 10 cm, a corner grasped at step 2 and lifted 40 cm in
+    0.3 s (13 mm per step), released at ``release_step``."""
+    return scenes.cloth_grasp(n_envs=1, n_side=6, side=0.1, steps=50, lift=(0.4, 0.4), inward=(0.0, 0.0),
+                              rise_time=0.3, release_step=release_step)
+
+
+def _world_force(st):
+    """Sum over the contact list of the world-frame multiplier R^T gamma:
+    normal along +z for the ground plane, along world x for a grasp row
+    (frame = world axes); gamma[1:] is already the world tangential part."""
+    F = np.zeros(3)
+    for o, g in zip(st.cobs, st.gamma):
+        n = np.array([1.0, 0.0, 0.0]) if o == oracle.GRASP_SLOT else np.array([0.0, 0.0, 1.0])
+        F += n * g[0] + g[1:]
+    return F
+
+
+def test_grasp_activation_and_constraint():
+    """Activation attaches exactly the vertices within the radius of the anchor
+    (the corner: its neighbours are 20 mm away, the radius 6 mm), and, with
+    the full metric, every step ends with the grasped vertex on the gripper
+    at t+h (C = x - p_grip(t+h) ~ 0) while the gripper rises 13 mm per step;
+    the constraint is one row of the contact list, after every obstacle row."""
+    sc = _grasp_scene()
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    corner = None
+    for s in range(20):
+        oracle.step(mesh, sc, 0, s, st, metric=2)
+        att = np.nonzero(st.attached)[0]
+        if s < 2:
+            assert len(att) == 0 and (st.cobs != oracle.GRASP_SLOT).all()
+            continue
+        p_t = oracle._to_world(sc.poses[0, 2, 1], (0, 0, 0))
+        d = np.linalg.norm(sc.q0[0] - p_t, axis=1)
+        if corner is None:
+            corner = int(np.argmin(d))
+            assert list(att) == [corner] and np.sort(d)[1] > 3 * sc.meta["grasp"]["radius"]
+        assert list(att) == [corner]
+        rows = np.nonzero(st.cobs == oracle.GRASP_SLOT)[0]
+        assert len(rows) == 1 and st.cvert[rows[0]] == corner
+        assert rows[0] == len(st.cvert) - 1 or st.cvert[rows[0] + 1] > corner
+        p_th = oracle._to_world(sc.poses[0, s + 1, 1], (0, 0, 0))
+        assert np.abs(st.q[corner] - p_th).max() <= 1e-8, (s, st.q[corner] - p_th)
+    # the cloth left the ground with the corner
+    assert st.q[:, 2].min() > 0.1
+
+
+def test_grasp_momentum_balance_and_release():
+    """Every global solve keeps sum_i m_i (q_i - q~_i) = sum of the contact
+    multipliers in world axes (A has zero row sums apart from M), for ground
+    and grasp rows alike and at any iteration count: while the cloth hangs
+    from the corner rising at constant speed that sum is the grasp force
+    (about the weight impulse M g h^2 upwards); after the release the contact list is empty and the
+    centre of mass falls freely (sum = 0)."""
+    sc = _grasp_scene(release_step=40)
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    m = sc.mass[:, None]
+    weight = sc.mass.sum() * 9.81 * sc.h ** 2
+    for s in range(46):
+        qt, vt = st.q.copy(), st.v.copy()
+        for metric in ([0, 2] if s in (2, 12) else [2]):
+            trial = oracle.EnvState(qt, vt)
+            trial.attached = st.attached.copy()
+            oracle.step(mesh, sc, 0, s, trial, metric=metric)
+            qtil = qt + sc.h * vt + sc.h ** 2 * np.asarray(sc.gravity)
+            lhs = (m * (trial.q - qtil)).sum(0)
+            assert np.abs(lhs - _world_force(trial)).max() <= 1e-12, (s, metric, lhs, _world_force(trial))
+        st = trial
+        if 10 <= s < 40:
+            assert list(st.cobs) == [oracle.GRASP_SLOT]
+        if 10 <= s < 30:   # gripper rising at constant speed: the force carries the weight
+            assert 0.8 * weight < lhs[2] < 1.2 * weight, (s, lhs[2], weight)
+        if s >= 40:
+            assert len(st.cvert) == 0 and not st.attached.any()
+            assert np.abs(lhs).max() <= 1e-12
