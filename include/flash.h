@@ -51,6 +51,7 @@ typedef int32_t flash_status;
 #define FLASH_OBS_SPHERE 2 /* dims[0] = radius */
 #define FLASH_OBS_BOX 3    /* dims = half extents */
 #define FLASH_MAX_OBS 8
+#define FLASH_GRASP_SLOT FLASH_MAX_OBS /* contact-list obstacle slot of grasp rows */
 
 #define FLASH_MODE_FIXED 0 /* exactly k_max local-global iterations per step */
 #define FLASH_MODE_TOL 1   /* iterate until r_ncp <= tol_ncp (k >= k_min) or k_cap */
@@ -157,11 +158,39 @@ flash_status flash_get_state(const flash_scene *s, float *q, float *v, void *str
  * pose becomes the current one. */
 flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_t which, void *stream);
 
+/* Bilateral grasp (the paper's grasp_ee; appendix "Bilateral Constraint for
+ * Cloth Control"): every vertex i of the grasped set S_grip of an environment
+ * carries the equality constraint C = x_i - p_grip(t+h) = 0, with p_grip the
+ * point `anchor` (body frame of obstacle `obstacle`) at that obstacle's pose
+ * at the end of the step.  The constraint is one more row of the
+ * environment's contact list (obstacle slot FLASH_GRASP_SLOT, after the
+ * vertex's obstacle rows; frame = world axes, gamma = its multiplier) solved
+ * by the same Newton/NCP iterations; use the full metric to hold it tightly.
+ *
+ * For environments [first_env, first_env + count): request host int32
+ * [count], per environment
+ *    1  activate: at the start of the next step, S_grip becomes the vertices
+ *       whose position lies within `radius` (metres, Euclidean, FP32) of the
+ *       anchor at the obstacle's current pose;
+ *    0  release: S_grip becomes empty at the start of the next step;
+ *   -1  leave the environment's grasp unchanged.
+ * obstacle in [0, FLASH_MAX_OBS) (typically a FLASH_OBS_NONE pose carrier,
+ * moved by flash_set_obstacle_poses like any obstacle); anchor host float [3]
+ * (NULL: the obstacle's origin); radius >= 0.  One gripper per environment:
+ * a new activation replaces S_grip.  Stream-ordered with flash_step; the
+ * grasp set is kept across steps and is not changed by flash_set_state.
+ * FLASH_EINVAL for a bad range, obstacle, radius or request value. */
+flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const int32_t *request,
+                         int32_t obstacle, const float *anchor, float radius, void *stream);
+
 /* Advance every environment by n_steps (Algorithm 1 body). */
 flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
 
 /* Contacts of the last step: count device int32 [N]; vert, obs device int32
- * [N][cap]; gamma device float32 [N][cap][4] (any may be NULL). */
+ * [N][cap] (obs = FLASH_GRASP_SLOT for a grasp row); gamma device float32
+ * [N][cap][4] (any may be NULL).  A vertex holds at most one row per
+ * obstacle plus one grasp row, so cap = n_verts * (n_obs + 1) never
+ * overflows. */
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs,
                                 float *gamma, void *stream);
 int32_t flash_contact_cap(const flash_scene *s);

@@ -339,6 +339,7 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.pvert, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pgam, cc * 4));
+  FLASH_CUDA_TRY(dalloc(s, &g.gflag, (size_t)g.N * np));
   // local pass shared memory: q and r ([3][ns] each, ns = n rounded up to 4),
   // then the element forces [ev + 1][3] (last row zero) and the CSR tables
   const size_t ns = ((size_t)n + 3) & ~(size_t)3;
@@ -713,6 +714,10 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->done, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->rncp, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
+  FLASH_CUDA_TRY(dalloc(s, &s->gstate, (size_t)s->N));
+  FLASH_CUDA_TRY(upload(s, &s->gobs, std::vector<int>(s->N, -1)));
+  FLASH_CUDA_TRY(dalloc(s, &s->greq, (size_t)s->N));
+  FLASH_CUDA_TRY(dalloc(s, &s->ganchor, (size_t)s->N * 4));
   FLASH_CUDA_TRY(upload(s, &s->d_voff, s->voff));
   FLASH_CUDA_TRY(cudaMallocHost(&s->h_active, sizeof(int)));
   // lanes: explicit count, or about one per 256 environments (at most 4):
@@ -867,6 +872,29 @@ flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_th, poses, bytes, cudaMemcpyDeviceToDevice, st));
   if (which == 0) FLASH_CUDA_TRY(cudaMemcpyAsync(s->pose_t, poses, bytes, cudaMemcpyDeviceToDevice, st));
+  return FLASH_OK;
+}
+
+flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const int32_t *request,
+                         int32_t obstacle, const float *anchor, float radius, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (count == 0) return FLASH_OK;
+  if (!request || first_env < 0 || count < 0 || first_env > s->N - count)
+    return fail(FLASH_EINVAL, "invalid environment range");
+  if (obstacle < 0 || obstacle >= FLASH_MAX_OBS) return fail(FLASH_EINVAL, "grasp obstacle out of range");
+  if (!(radius >= 0.f) || !std::isfinite(radius)) return fail(FLASH_EINVAL, "grasp radius must be finite and >= 0");
+  float an[3] = {0.f, 0.f, 0.f};
+  if (anchor)
+    for (int c = 0; c < 3; c++) {
+      if (!std::isfinite(anchor[c])) return fail(FLASH_EINVAL, "grasp anchor is not finite");
+      an[c] = anchor[c];
+    }
+  for (int i = 0; i < count; i++)
+    if (request[i] < -1 || request[i] > 1) return fail(FLASH_EINVAL, "grasp request must be -1, 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  FLASH_CUDA_TRY(cudaMemcpyAsync(s->greq + first_env, request, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+  FLASH_CUDA_TRY(launch_grasp_set(s, first_env, count, obstacle, an[0], an[1], an[2], radius, st));
+  s->launches++;
   return FLASH_OK;
 }
 

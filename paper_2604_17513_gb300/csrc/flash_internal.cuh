@@ -87,6 +87,7 @@ struct Group {
   float *cgam = nullptr;
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
+  uint8_t *gflag = nullptr;               // [N][n_pad] grasped vertices (S_grip)
   int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner
   // full contact metric (flash_scene_desc.metric = FLASH_METRIC_FULL)
   float *fm_lin = nullptr, *fm_V = nullptr, *fm_H = nullptr, *fm_cs = nullptr, *fm_sn = nullptr, *fm_g = nullptr;
@@ -148,6 +149,11 @@ struct flash_scene {
   float *pose_t = nullptr, *pose_th = nullptr;   // [N][FLASH_MAX_OBS][7]
   int *iters = nullptr, *done = nullptr;
   float *rncp = nullptr;
+  // bilateral grasp per environment: state 0 none, 1 activate at the next
+  // step's start, 2 held, 3 release at the next step's start; the obstacle
+  // carrying the anchor (-1 none); anchor xyz and activation radius
+  int *gstate = nullptr, *gobs = nullptr, *greq = nullptr;
+  float *ganchor = nullptr;   // [N][4]
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
@@ -215,6 +221,9 @@ cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, 
 // lanes and their table launches (build_lanes at finalize)
 cudaError_t build_lanes(flash_scene *s, int n_lanes);
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
+// grasp requests s->greq[first_env, first_env + count) -> per-environment grasp state
+cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int obstacle, float ax, float ay,
+                             float az, float radius, cudaStream_t st);
 cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
                               cudaStream_t st, int *launched);
 cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);

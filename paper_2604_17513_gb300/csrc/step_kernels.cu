@@ -27,6 +27,7 @@ struct GroupView {
   __half *rh, *rl;
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
+  uint8_t *gflag;                // [N][n_pad] grasped vertices
   const uint16_t *coff, *cidx;   // CSR vertex -> element slots e * vpe + a
   const int2 *kb;                // bending operator, off-diagonal entries, slot-major
   int ev, deg_b;
@@ -51,6 +52,9 @@ struct EnvView {
   const int *otype;
   int *iters, *done, *status, *active;
   float *rncp;
+  int *gstate;
+  const int *gobs;
+  const float *ganchor;
 };
 
 GroupView view(const flash_scene *s, const Group &g) {
@@ -60,7 +64,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w; v.dq = g.dq;
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
-  v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch;
+  v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch; v.gflag = g.gflag;
   v.c_in_smem = g.c_in_smem ? 1 : 0;
   v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
   v.fm_lin = g.fm_lin; v.fm_V = g.fm_V; v.fm_H = g.fm_H; v.fm_cs = g.fm_cs; v.fm_sn = g.fm_sn; v.fm_g = g.fm_g;
@@ -76,6 +80,7 @@ EnvView eview(const flash_scene *s) {
   e.mu = s->mu; e.odims = s->odims; e.ocomp = s->ocomp; e.pose_t = s->pose_t; e.pose_th = s->pose_th;
   e.otype = s->otype; e.iters = s->iters; e.done = s->done; e.status = s->status; e.active = s->active;
   e.rncp = s->rncp;
+  e.gstate = s->gstate; e.gobs = s->gobs; e.ganchor = s->ganchor;
   return e;
 }
 
@@ -154,6 +159,19 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     for (int c = 0; c < 7; c++) s_pose[o][c] = V.pose_th[(e * FLASH_MAX_OBS + o) * 7 + c];
   }
   if (threadIdx.x == 0) V.done[e] = 0;
+  // bilateral grasp: a pending activation takes the vertices within the
+  // radius of the anchor at the carrying obstacle's current pose; a pending
+  // release empties the set (appendix, Bilateral Constraint for Cloth Control)
+  const int gst = V.gstate[e];
+  V3 gp = v3(0.f, 0.f, 0.f);
+  float grad2 = -1.f;
+  if (gst == 1) {
+    const float *ps = V.pose_t + (e * FLASH_MAX_OBS + V.gobs[e]) * 7;
+    const float *an = V.ganchor + 4 * e;
+    gp = qrot(ps + 3, v3(an[0], an[1], an[2]), false) + v3(ps[0], ps[1], ps[2]);
+    grad2 = an[3] * an[3];
+  }
+  uint8_t *gflag = G.gflag + (size_t)l * np;
   __syncthreads();
   const float h = a.h, h2 = a.h * a.h;
   const float gv[3] = {a.gx, a.gy, a.gz};
@@ -163,6 +181,13 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     int i = i0 + threadIdx.x;
     unsigned mask = 0;
     if (i < n) {
+      if (gst == 1) {
+        const V3 d = v3(q[i], q[np + i], q[2 * np + i]) - gp;
+        gflag[i] = dot(d, d) <= grad2 ? 1 : 0;
+      } else if (gst == 3) {
+        gflag[i] = 0;
+      }
+      if (gflag[i]) mask |= 1u << FLASH_GRASP_SLOT;
       float x0[3], x1[3];
       for (int c = 0; c < 3; c++) {
         float qq = q[c * np + i], vv = v[c * np + i];
@@ -190,11 +215,17 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         if (pos < G.cap) { cvert[pos] = i; cobs[pos] = o; }
         pos++;
       }
+    if (mask & (1u << FLASH_GRASP_SLOT)) {   // the grasp row follows the obstacle rows
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_GRASP_SLOT; }
+      pos++;
+    }
     base += total;
   }
   if (threadIdx.x == 0) {
     G.ccount[l] = min(base, G.cap);
     if (base > G.cap) atomicOr(V.status, 1 << 8);
+    if (gst == 1) V.gstate[e] = 2;
+    if (gst == 3) V.gstate[e] = 0;
   }
   __syncthreads();
   int cnt = min(base, G.cap);
@@ -205,11 +236,11 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
     if (a.warm == FLASH_WARM_PREV && pc > 0) {
-      int key = cvert[j] * FLASH_MAX_OBS + cobs[j];
+      int key = cvert[j] * (FLASH_GRASP_SLOT + 1) + cobs[j];
       int lo = 0, hi = pc - 1;
       while (lo <= hi) {  // previous list is sorted by (vertex, obstacle)
         int mid = (lo + hi) >> 1;
-        int km = pv[mid] * FLASH_MAX_OBS + po[mid];
+        int km = pv[mid] * (FLASH_GRASP_SLOT + 1) + po[mid];
         if (km == key) {
           for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
           break;
@@ -264,6 +295,7 @@ struct ObsShared {
   int type[FLASH_MAX_OBS];
   float dims[FLASH_MAX_OBS][3], pose[FLASH_MAX_OBS][7], poset[FLASH_MAX_OBS][7], comp[FLASH_MAX_OBS];
   PoseM pm[FLASH_MAX_OBS];
+  float gp[3];   // grasp target p_grip(t+h)
 };
 
 __device__ __forceinline__ void load_obstacles(const EnvView &V, int e, int K, ObsShared &O) {
@@ -278,10 +310,39 @@ __device__ __forceinline__ void load_obstacles(const EnvView &V, int e, int K, O
     }
     make_posem(O.poset[o], O.pose[o], O.pm[o]);
   }
+  if (threadIdx.x == 0) {
+    const int go = V.gobs[e];
+    if (go >= 0) {
+      const float *ps = V.pose_th + (e * FLASH_MAX_OBS + go) * 7;
+      const float *an = V.ganchor + 4 * e;
+      const V3 p = qrot(ps + 3, v3(an[0], an[1], an[2]), false) + v3(ps[0], ps[1], ps[2]);
+      O.gp[0] = p.x; O.gp[1] = p.y; O.gp[2] = p.z;
+    } else {
+      O.gp[0] = 0.f; O.gp[1] = 0.f; O.gp[2] = 0.f;
+    }
+  }
+}
+
+// Grasp row: the frame is the world axes, phi = x - p_grip(t+h) (the
+// constraint itself), D_C = I (phi moves one to one with x) and D_y = 0 (a
+// rigid, zero-length link); never "separated".
+__device__ __forceinline__ void linearize_grasp(const float *gp, V3 x, ContactLin &L) {
+#pragma unroll
+  for (int t = 0; t < 9; t++) L.R[t] = (t % 4 == 0) ? 1.f : 0.f;
+  L.phi[0] = x.x - gp[0]; L.phi[1] = x.y - gp[1]; L.phi[2] = x.z - gp[2];
+  L.cn = 1.f;
+  L.Ct[0] = 1.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 1.f;
+  L.dn = 0.f; L.dtn[0] = 0.f; L.dtn[1] = 0.f;
+  L.Dtt[0] = 0.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 0.f;
+  L.gap = -1.f;
 }
 
 __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs &a, float mu, float mv, V3 x, V3 xt,
                                        const float *g, ContactLin &L) {
+  if (o == FLASH_GRASP_SLOT) {
+    linearize_grasp(O.gp, x, L);
+    return;
+  }
   linearize_contact_m(O.type[o], O.dims[o], O.comp[o], O.pm[o], a.tau, mu, a.h, mv, x, xt, g, L);
 }
 
@@ -1138,6 +1199,23 @@ __device__ __forceinline__ void end_body(const GroupView &G, const int l, const 
   }
 }
 
+// grasp requests (1 activate, 0 release, -1 keep) -> per-environment grasp
+// state; the activation itself runs in the next step's begin kernel
+__global__ void k_grasp_set(int *gstate, int *gobs, float *ganchor, const int *req, int first, int count, int obstacle,
+                            float4 anchor_radius) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int e = first + i, r = req[e];
+  if (r == 1) {
+    gstate[e] = 1;
+    gobs[e] = obstacle;
+    ganchor[4 * e] = anchor_radius.x; ganchor[4 * e + 1] = anchor_radius.y;
+    ganchor[4 * e + 2] = anchor_radius.z; ganchor[4 * e + 3] = anchor_radius.w;
+  } else if (r == 0) {
+    gstate[e] = gstate[e] == 0 ? 0 : 3;
+  }
+}
+
 // Entry points: table launches over the environments of one or more groups,
 // CTA b = (group map[b].x, environment map[b].y).  Every scene, one group or
 // many, runs these same kernels.
@@ -1273,6 +1351,10 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
   const float *pg = G.pgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
+    if (o == FLASH_GRASP_SLOT) {   // grasp rows are not predicted: NaN features keep them cold
+      for (int c = 0; c < 10; c++) X[(off[l] + j) * 10 + c] = __int_as_float(0x7fc00000);
+      continue;
+    }
     const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
     V3 n, t1, t2;
     float gap;
@@ -1284,11 +1366,11 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
     const V3 vr = v3(v[vtx], v[np + vtx], v[2 * np + vtx]) - (1.f / a.h) * (x - xo);
     // previous step's multipliers of the same (vertex, obstacle)
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
-    const int key = vtx * FLASH_MAX_OBS + o;
+    const int key = vtx * (FLASH_GRASP_SLOT + 1) + o;
     int lo = 0, hi = pc - 1;
     while (lo <= hi) {
       const int mid = (lo + hi) >> 1;
-      const int km = pv[mid] * FLASH_MAX_OBS + po[mid];
+      const int km = pv[mid] * (FLASH_GRASP_SLOT + 1) + po[mid];
       if (km == key) {
         for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
         break;
@@ -1320,6 +1402,7 @@ __global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, S
   float *gam = G.cgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
+    if (o == FLASH_GRASP_SLOT) continue;
     const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
     V3 n, t1, t2;
     float gap;
@@ -1357,6 +1440,11 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
   const float *gam = G.cgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
+    float *t = T + (off[l] + j) * 6;
+    if (o == FLASH_GRASP_SLOT || !(V.rncp[e] <= a.tol)) {   // grasp row or not converged: no target (NaN row)
+      for (int c = 0; c < 6; c++) t[c] = __int_as_float(0x7fc00000);
+      continue;
+    }
     const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
     V3 n, t1, t2;
     float gap;
@@ -1364,11 +1452,6 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
     const float *g = gam + 4 * j;
     const float s = kFeatLen / __ldg(G.mass + vtx);
     const V3 gt = v3(g[1], g[2], g[3]);
-    float *t = T + (off[l] + j) * 6;
-    if (!(V.rncp[e] <= a.tol)) {   // not converged: no target (NaN marks the row)
-      for (int c = 0; c < 6; c++) t[c] = __int_as_float(0x7fc00000);
-      continue;
-    }
     t[0] = g[0] * s; t[1] = dot(t1, gt) * s; t[2] = dot(t2, gt) * s;
     t[3] = (q[vtx] - x.x) * kFeatLen; t[4] = (q[np + vtx] - x.y) * kFeatLen; t[5] = (q[2 * np + vtx] - x.z) * kFeatLen;
   }
@@ -1539,6 +1622,13 @@ cudaError_t build_lanes(flash_scene *s, int n_lanes) {
       }
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int obstacle, float ax, float ay,
+                             float az, float radius, cudaStream_t st) {
+  k_grasp_set<<<(count + 255) / 256, 256, 0, st>>>(s->gstate, s->gobs, s->ganchor, s->greq, first_env, count,
+                                                   obstacle, make_float4(ax, ay, az, radius));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {

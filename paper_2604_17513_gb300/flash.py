@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libflash.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3, -4, -5, -6, -7
 WOVERFLOW = 1
 MAX_OBS = 8
+GRASP_SLOT = MAX_OBS   # contact-list obstacle slot of grasp rows
 MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
@@ -80,6 +81,7 @@ def lib():
         L.flash_get_state.argtypes = [vp, vp, vp, vp]
         L.flash_set_obstacle_poses.argtypes = [vp, vp, i32, vp]
         L.flash_step.argtypes = [vp, i32, vp]
+        L.flash_grasp.argtypes = [vp, i32, i32, C.POINTER(i32), i32, C.POINTER(C.c_float), C.c_float, vp]
         L.flash_get_contacts.argtypes = [vp, vp, vp, vp, vp, vp]
         L.flash_contact_cap.argtypes = [vp]
         L.flash_get_stats.argtypes = [vp, vp, vp, vp]
@@ -106,7 +108,7 @@ def lib():
         L.flash_dense_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
-                     "flash_step", "flash_get_contacts", "flash_get_stats", "flash_status_word",
+                     "flash_step", "flash_grasp", "flash_get_contacts", "flash_get_stats", "flash_status_word",
                      "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
                      "flash_warmstart_bounds",
                      "flash_record_contacts", "flash_get_recorded", "flash_mlp_forward", "flash_mlp_loss_grad",
@@ -154,7 +156,9 @@ class Sim:
         d.k_min = s0.k_min if k_min is None else k_min
         d.k_cap = s0.k_cap if k_cap is None else k_cap
         d.mode = s0.mode if mode is None else mode
-        d.contact_cap = contact_cap or max(sc.n_verts * sc.n_obs for sc in scenes)
+        # one row per (vertex, obstacle), plus one grasp row per vertex where grasps are scheduled
+        d.contact_cap = contact_cap or max(sc.n_verts * (sc.n_obs + (1 if sc.meta.get("grasp") else 0))
+                                           for sc in scenes)
         d.solve = solve
         d.warm = warm
         d.lanes = lanes
@@ -229,6 +233,26 @@ class Sim:
     def step(self, n=1):
         _check(lib().flash_step(self._h, n, _stream()))
         self.step_index += n
+
+    def grasp(self, request, obstacle, anchor=(0.0, 0.0, 0.0), radius=0.0, first_env=0):
+        """Grasp requests for environments [first_env, first_env + len(request)):
+        1 activates (vertices within ``radius`` of ``anchor`` on obstacle
+        ``obstacle`` at the start of the next step), 0 releases, -1 keeps."""
+        req = np.ascontiguousarray(np.atleast_1d(request), np.int32)
+        an = np.ascontiguousarray(anchor, np.float32)
+        _check(lib().flash_grasp(self._h, first_env, len(req), req.ctypes.data_as(C.POINTER(C.c_int32)), obstacle,
+                                 an.ctypes.data_as(C.POINTER(C.c_float)), float(radius), _stream()))
+
+    def apply_grasp_schedule(self, step):
+        """Issue the grasp requests that the scenes' schedules (meta["grasp"])
+        hold for the start of step ``step``."""
+        first = 0
+        for sc in self.scenes:
+            g = sc.meta.get("grasp")
+            if g and step in g["schedule"]:
+                self.grasp(np.full(sc.n_envs, g["schedule"][step], np.int32), g["obstacle"], g["anchor"],
+                           g["radius"], first)
+            first += sc.n_envs
 
     def contacts(self):
         cnt = torch.empty(self.n_envs, dtype=torch.int32, device=self.dev)
