@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec on 1 GB300 at NCP residual <=1e-5 (batched vs plain); % HBM roofline"
 TOL = 1e-5
+DEFAULT_ENVS = {"cloth_gripper": 1024, "cloth_grasp": 1024, "tet_squeeze": 4096, "mixed": 2048}
+CPU_SAMPLE = {"cloth_gripper": (6, 12), "cloth_grasp": (2, 6), "tet_squeeze": (24, 40)}   # (envs, steps), 10-30 s
 
 
 def parse():
@@ -37,7 +39,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="cloth_gripper", choices=["cloth_gripper", "tet_squeeze", "mixed"])
+    p.add_argument("--workload", default="cloth_gripper",
+                   choices=["cloth_gripper", "cloth_grasp", "tet_squeeze", "mixed"])
     p.add_argument("--envs", type=int, default=None, help="environments per GPU (default: the workload's)")
     p.add_argument("--side", type=int, default=32)
     p.add_argument("--k", type=int, default=10, help="local-global iterations per step (fixed mode)")
@@ -45,15 +48,20 @@ def parse():
                    help="fixed: k iterations per step; tol: iterate until r_ncp <= 1e-5 (cap --k-cap)")
     p.add_argument("--k-cap", type=int, default=200, help="iteration cap of the tolerance mode")
     p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
-    p.add_argument("--metric", default="lite", choices=["lite", "full"],
-                   help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve")
+    p.add_argument("--metric", default=None, choices=["lite", "full"],
+                   help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve "
+                        "(default: full for cloth_grasp, whose bilateral grasp the lite metric cannot hold, "
+                        "else lite)")
     p.add_argument("--lin-iters", type=int, default=10, help="linear-solver (GMRES) iterations of the full metric")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-warm-compare", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.metric is None:
+        args.metric = "full" if args.workload == "cloth_grasp" else "lite"
+    return args
 
 
 def dist_env():
@@ -186,27 +194,58 @@ def mode_desc(args):
     return f"fixed k={args.k}" if args.mode == "fixed" else f"tolerance r_ncp<=1e-5, cap {args.k_cap}"
 
 
+# --------------------------------------------------------------------------- workloads
+def workload_scene(args, n_envs, steps, rank=0):
+    """The workload's seeded scene(s) with n_envs environments per GPU and its
+    description."""
+    from paper_2604_17513_gb300 import scenes
+    if args.workload == "cloth_gripper":
+        sc = scenes.cloth_gripper(seed=1 + rank, n_envs=n_envs, n_side=args.side, steps=steps, k_max=args.k)
+        desc = (f"cloth+gripper: {n_envs} envs x {args.side}x{args.side} cloth ({len(sc.elems)} tris), "
+                f"2 box fingers + ground, h=1/100")
+    elif args.workload == "cloth_grasp":
+        # grasped at step 2, held for the rest of the run (no release)
+        sc = scenes.cloth_grasp(seed=1 + rank, n_envs=n_envs, n_side=args.side, side=0.5, steps=steps,
+                                k_max=args.k, grasp_step=2, release_step=1 << 30)
+        desc = (f"cloth grasp: {n_envs} envs x {args.side}x{args.side} cloth ({len(sc.elems)} tris) on the ground, "
+                f"a corner held by a bilateral grasp from step 2, lifted 8-15 cm over 0.5 s, h=1/100")
+    elif args.workload == "tet_squeeze":
+        sc = scenes.tet_squeeze(seed=1 + rank, n_envs=n_envs, steps=steps, k_max=args.k)
+        desc = (f"tet squeeze: {n_envs} envs x 8x8x4-cube tet block (1280 tets, 405 verts), per-env "
+                f"stiffness log-U[1e3,1e5] (eigen-form solve), parallel gripper, h=1/200")
+    else:
+        sc = scenes.mixed_batch(seed=3 + rank, n_envs=n_envs, steps=steps)
+        desc = (f"mixed: {n_envs} envs, cloths of side U{{16..64}} and tet blocks of 200-3000 verts "
+                f"({len(sc)} templates), 1-4 boxes/spheres, h=1/100")
+    return sc, desc
+
+
+def _env_list(sc):
+    scs = sc if isinstance(sc, list) else [sc]
+    return [(x, e) for x in scs for e in range(x.n_envs)]
+
+
 # --------------------------------------------------------------------------- CPU baseline
-def cpu_baseline(n_envs_sample, steps_sample, side, k, args):
+def cpu_baseline(n_envs_sample, steps_sample, args):
     """FP64 oracle, single thread, on a bounded sample of the same workload."""
     import oracle
-    from paper_2604_17513_gb300 import scenes
     oracle.build()
-    sc = scenes.cloth_gripper(n_envs=n_envs_sample, n_side=side, steps=steps_sample + 1, k_max=k)
+    sc, _ = workload_scene(args, n_envs_sample, steps_sample + 1)
     t0 = time.perf_counter()
     n_done = n_conv = 0
-    for e in range(n_envs_sample):
-        m = oracle.Mesh.from_scene(sc, e)
-        st = oracle.EnvState(sc.q0[e], sc.v0[e])
+    for x, e in _env_list(sc):
+        m = oracle.Mesh.from_scene(x, e)
+        st = oracle.EnvState(x.q0[e], x.v0[e])
         for s in range(steps_sample):
-            oracle.step(m, sc, e, s, st, **oracle_mode_kw(args))
+            oracle.step(m, x, e, s, st, **oracle_mode_kw(args))
             n_done += 1
             n_conv += st.rncp <= TOL
     dt = time.perf_counter() - t0
     return {"value": n_conv / dt, "unit": "converged env-steps/s", "all_env_steps_per_s": n_done / dt,
             "cores": 1, "kind": "oracle",
-            "sample": f"{n_envs_sample} envs x {steps_sample} steps of the {side}x{side} cloth+gripper workload, "
-                      f"{mode_desc(args)}, FP64, single thread (includes per-env system-matrix setup)",
+            "sample": f"{n_envs_sample} envs x {steps_sample} steps of the {args.workload} workload, "
+                      f"{mode_desc(args)}, {args.metric} metric, FP64, single thread "
+                      f"(includes per-env system-matrix setup)",
             "seconds": dt}
 
 
@@ -214,39 +253,41 @@ def run_reference(args, rank):
     if rank != 0:
         return
     import oracle
-    from paper_2604_17513_gb300 import scenes
     oracle.build()
-    sc = scenes.cloth_gripper(n_envs=2, n_side=args.side, steps=args.warmup + args.steps + 1, k_max=args.k)
-    meshes = [oracle.Mesh.from_scene(sc, e) for e in range(2)]
-    states = [oracle.EnvState(sc.q0[e], sc.v0[e]) for e in range(2)]
+    n_sample = 2
+    sc, _ = workload_scene(args, n_sample, args.warmup + args.steps + 1)
+    _, desc = workload_scene(args, args.envs or DEFAULT_ENVS[args.workload], 1) if args.workload != "mixed" else \
+        (None, f"mixed: {args.envs or DEFAULT_ENVS['mixed']} envs")
+    envs = _env_list(sc)
+    meshes = [oracle.Mesh.from_scene(x, e) for x, e in envs]
+    states = [oracle.EnvState(x.q0[e], x.v0[e]) for x, e in envs]
     for s in range(args.warmup):
-        for e in range(2):
-            oracle.step(meshes[e], sc, e, s, states[e], **oracle_mode_kw(args))
+        for (x, e), m, st in zip(envs, meshes, states):
+            oracle.step(m, x, e, s, st, **oracle_mode_kw(args))
     t0 = time.perf_counter()
     conv = 0
     for s in range(args.warmup, args.warmup + args.steps):
-        for e in range(2):
-            oracle.step(meshes[e], sc, e, s, states[e], **oracle_mode_kw(args))
-            conv += states[e].rncp <= TOL
+        for (x, e), m, st in zip(envs, meshes, states):
+            oracle.step(m, x, e, s, st, **oracle_mode_kw(args))
+            conv += st.rncp <= TOL
     dt = time.perf_counter() - t0
-    val = 2 * args.steps / dt
+    val = len(envs) * args.steps / dt
     val_conv = conv / dt
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val_conv, "unit": "converged env-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"cloth+gripper: {args.envs} envs x {args.side}x{args.side} cloth "
-                               f"({2 * (args.side - 1) ** 2} tris), 2 box fingers + ground, h=1/100",
+        "config": {"workload": desc,
                    "mode": args.mode, "k": args.k if args.mode == "fixed" else None,
                    "k_cap": args.k_cap if args.mode == "tol" else None, "warm": "cold",
-                   "solve": "FP64 oracle (Cholesky)",
-                   "sample": "2 of the environments per step, single thread"},
+                   "metric": args.metric, "solve": "FP64 oracle (Cholesky)",
+                   "sample": f"{len(envs)} of the environments per step, single thread"},
         "cpu_baseline": {"value": val_conv, "unit": "converged env-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "2 envs per step of the cloth+gripper workload, FP64, single thread",
+                         "sample": f"{len(envs)} envs per step of the {args.workload} workload, FP64, single thread",
                          "all_env_steps_per_s": val},
         "e2e": {"value": val_conv, "unit": "converged env-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
-        "frac_rncp_le_tol": conv / (2 * args.steps),
+        "frac_rncp_le_tol": conv / (len(envs) * args.steps),
     }), flush=True)
 
 
@@ -259,8 +300,8 @@ def main():
         return
     # CPU baseline first (before any CUDA context, single thread)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cloth_gripper":
-        cpu = cpu_baseline(6, 12, args.side, args.k, args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "mixed":
+        cpu = cpu_baseline(*CPU_SAMPLE[args.workload], args)
 
     import numpy as np
     import torch
@@ -275,21 +316,8 @@ def main():
     solve = {"auto": flash.SOLVE_F16X3, "f32": flash.SOLVE_F32, "f16x3": flash.SOLVE_F16X3}[args.solve]
     n_steps = args.warmup + args.steps
     total_steps = n_steps + 3 * args.steps + 8 + 10   # + the profiled pass (at most 10 steps)
-    if args.workload == "cloth_gripper":
-        args.envs = args.envs or 1024
-        sc = scenes.cloth_gripper(seed=1 + rank, n_envs=args.envs, n_side=args.side, steps=total_steps, k_max=args.k)
-        workload = (f"cloth+gripper: {args.envs} envs x {args.side}x{args.side} cloth ({len(sc.elems)} tris), "
-                    f"2 box fingers + ground, h=1/100")
-    elif args.workload == "tet_squeeze":
-        args.envs = args.envs or 4096
-        sc = scenes.tet_squeeze(seed=1 + rank, n_envs=args.envs, steps=total_steps, k_max=args.k)
-        workload = (f"tet squeeze: {args.envs} envs x 8x8x4-cube tet block (1280 tets, 405 verts), per-env "
-                    f"stiffness log-U[1e3,1e5] (eigen-form solve), parallel gripper, h=1/200")
-    else:
-        args.envs = args.envs or 2048
-        sc = scenes.mixed_batch(seed=3 + rank, n_envs=args.envs, steps=total_steps)
-        workload = (f"mixed: {args.envs} envs, cloths of side U{{16..64}} and tet blocks of 200-3000 verts "
-                    f"({len(sc)} templates), 1-4 boxes/spheres, h=1/100")
+    args.envs = args.envs or DEFAULT_ENVS[args.workload]
+    sc, workload = workload_scene(args, args.envs, total_steps, rank)
     mode_kw = {"mode": flash.MODE_TOL, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
     if args.metric == "full":
         mode_kw.update(metric=flash.METRIC_FULL, lin_iters=args.lin_iters)
@@ -308,6 +336,7 @@ def main():
     sim.set_poses(poses[0], which=0)
     for s in range(args.warmup):
         sim.set_poses(poses[s + 1])
+        sim.apply_grasp_schedule(s)
         sim.step(1)
     torch.cuda.synchronize()
 
@@ -325,6 +354,7 @@ def main():
             flush_buf.fill_(float(i))
             ev[i][0].record()
             sim.set_poses(poses[s + 1])
+            sim.apply_grasp_schedule(s)
             sim.step(1)
             ev[i][1].record()
             it, r = sim.stats()
@@ -350,6 +380,7 @@ def main():
     for i, s in enumerate(range(args.warmup + args.steps, args.warmup + args.steps + prof_steps)):
         flush_buf.fill_(float(i))
         sim.set_poses(poses[s + 1])
+        sim.apply_grasp_schedule(s)
         sim.step(1)
     torch.cuda.synchronize()
     prof = sim.profile_read()
@@ -379,6 +410,7 @@ def main():
         for s in range(n_steps, n_steps + args.steps):
             dpose.copy_(poses_h[s + 1], non_blocking=True)
             sim.set_poses(dpose)
+            sim.apply_grasp_schedule(s)
             sim.step(1)
             q, _ = sim.get_state()
             q_h.copy_(q, non_blocking=True)
