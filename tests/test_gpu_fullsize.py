@@ -25,7 +25,7 @@ def _oracle_state(sc, e, s, metric=0):
     st = oracle.EnvState(sc.q0[e], sc.v0[e])
     for k in range(s):
         oracle.step(mesh, sc, e, k, st, metric=metric)
-    return mesh, _f32(st.q), _f32(st.v)
+    return mesh, _f32(st.q), _f32(st.v), st.attached.copy()
 
 
 def _step_all(cuda, scs, qs, vs, s, metric=0):
@@ -38,6 +38,13 @@ def _step_all(cuda, scs, qs, vs, s, metric=0):
                   torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
     sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
     sim.set_poses(flash.poses_tensor(scs, s + 1, cuda), which=1)
+    first = 0
+    for sc in scs:   # grasps held at s: re-activated (the held vertex sits on the gripper)
+        g = sc.meta.get("grasp")
+        if g and min(k for k, r in g["schedule"].items() if r == 1) < s:
+            sim.grasp(np.ones(sc.n_envs, np.int32), g["obstacle"], g["anchor"], g["radius"], first)
+        first += sc.n_envs
+    sim.apply_grasp_schedule(s)
     sim.step(1)
     q = sim.get_state()[0].cpu().numpy()
     assert sim.status() == 0
@@ -53,11 +60,12 @@ def _check(scs, picks, s, cuda, lanes, metric=0):
     refs = []
     for si, e in picks:
         sc = scs[si]
-        mesh, q0, v0 = _oracle_state(sc, e, s, om)
+        mesh, q0, v0, att = _oracle_state(sc, e, s, om)
         n = sc.n_verts
         qs[si][e * n:(e + 1) * n] = q0
         vs[si][e * n:(e + 1) * n] = v0
         ref = oracle.EnvState(q0, v0)
+        ref.attached = att
         oracle.step(mesh, sc, e, s, ref, metric=om)
         refs.append(ref)
     sim, q = _step_all(cuda, scs, qs, vs, s, metric)
@@ -104,3 +112,13 @@ def test_tet_squeeze_full_metric_full_size(cuda):
     full-metric state at step 10 (the plates squeeze)."""
     sc = scenes.tet_squeeze(seed=1, n_envs=4096, steps=14)
     _check([sc], [(0, 0), (0, 1023), (0, 1024), (0, 4095)], 10, cuda, lanes=4, metric=1)
+
+
+def test_cloth_grasp_full_metric_full_size(cuda):
+    """1024 environments of the 32x32 cloth held at a corner by the bilateral
+    grasp, full metric (the bench's cloth-grasp workload: 4 lanes, graph
+    replay), one step while the corner rises; samples at both ends of lanes
+    start from the oracle's full-metric state at step 6."""
+    sc = scenes.cloth_grasp(seed=1, n_envs=1024, n_side=32, side=0.5, steps=10, grasp_step=2,
+                            release_step=1 << 30)
+    _check([sc], [(0, 0), (0, 255), (0, 256), (0, 1023)], 6, cuda, lanes=4, metric=1)
