@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
-_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
+_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c", "raycast.c")]
 _lib = None
 
 DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU, DP_GRASP_OBS = range(10)
@@ -65,6 +65,8 @@ def lib():
                                        pi, pi, pd, pi, pd, pd]
         _lib.or_residual.restype = d
         _lib.or_residual.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, pd, pd, i, pi, pi, pd]
+        _lib.or_raycast.argtypes = [i, pd, i, pi, i, pi, pd, pd, pd, pd, i, i, d, pd, pi, pd]
+        _lib.or_raycast.restype = None
         _lib.or_mlp_forward.argtypes = [i, pd, pd, pd]
         _lib.or_mlp_loss_grad.restype = d
         _lib.or_mlp_loss_grad.argtypes = [i, pd, pd, pd, pd]
@@ -320,3 +322,26 @@ def mlp_loss_grad(params_flat, x, t):
     g = np.zeros_like(p)
     loss = lib().or_mlp_loss_grad(len(x), _pd(p), _pd(x), _pd(t), _pd(g))
     return loss, g
+
+
+def raycast(x, tris, otype, odims, opose, cam_pose, intr, W, H, dil=0.0):
+    """Depth ray casting of one environment (appendix, depth rendering), by
+    brute force in FP64.  x [n][3], tris [T][3]; obstacles otype [K], odims
+    [K][3], opose [K][7]; cam_pose [7] camera-to-world; intr = (fx, fy, cx,
+    cy, z_near, z_far).  Returns depth [H][W] (0: no hit), seg [H][W] (0 none,
+    1 mesh, 2 + k obstacle k), points [H][W][3] (NaN: no hit).  ``dil`` grows
+    (> 0) or shrinks (< 0) every primitive (see oracle.h)."""
+    x = _f64(x).reshape(-1, 3)
+    tris = _i32(tris).reshape(-1, 3)
+    otype = _i32(otype).reshape(-1)
+    K = len(otype)
+    odims = _f64(odims).reshape(max(K, 1), 3) if K else np.zeros((1, 3))
+    opose = _f64(opose).reshape(max(K, 1), 7) if K else np.zeros((1, 7))
+    depth = np.zeros((H, W))
+    seg = np.zeros((H, W), np.int32)
+    pts = np.zeros((H, W, 3))
+    lib().or_raycast(len(x), _pd(x if len(x) else np.zeros((1, 3))), len(tris),
+                     _pi(tris if len(tris) else np.zeros((1, 3), np.int32)), K,
+                     _pi(otype if K else np.zeros(1, np.int32)), _pd(odims), _pd(opose), _pd(_f64(cam_pose)),
+                     _pd(_f64(intr)), W, H, float(dil), _pd(depth), _pi(seg), _pd(pts))
+    return depth, seg, pts

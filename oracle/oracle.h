@@ -104,6 +104,22 @@ double or_residual(const OrMesh *m, const double *dp, int K, const int *otype, c
 /* fischer-burmeister value, exported for the closed-form pins */
 double or_fb(double a, double b);
 
+/* Depth ray casting of one environment (raycast.c; appendix, depth
+ * rendering).  x [n][3] world vertex positions, tris [T][3] (instance 1);
+ * obstacles k < K of type otype[k], dims odims[k][3], pose opose[k][7]
+ * (instance 2 + k; type 0 invisible).  cam[7] camera-to-world pose; intr =
+ * (fx, fy, cx, cy, z_near, z_far).  Pixel (u, v): ray through image point
+ * (u + 1/2, v + 1/2), d_cam = ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1), so
+ * t = depth.  Hit = smallest t in [z_near, z_far] (ties: smaller instance,
+ * then smaller triangle index).  dil grows (> 0) or shrinks (< 0) every
+ * primitive: triangles by |dil| in barycentric coordinates, spheres by
+ * |dil| r, boxes by |dil| times the largest half extent; planes unchanged.
+ * Outputs depth [H][W] (0: no hit), seg [H][W] (0: no hit), pts [H][W][3]
+ * world hit points (NaN: no hit). */
+void or_raycast(int n, const double *x, int T, const int *tris, int K, const int *otype, const double *odims,
+                const double *opose, const double *cam, const double *intr, int W, int H, double dil,
+                double *depth, int *seg, double *pts);
+
 #ifdef __cplusplus
 }
 #endif
