@@ -183,6 +183,59 @@ flash_status flash_set_obstacle_poses(flash_scene *s, const float *poses, int32_
 flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const int32_t *request,
                          int32_t obstacle, const float *anchor, float radius, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Depth ray casting (appendix, depth rendering: depth maps, instance
+ * segmentation masks and point clouds cast directly from the simulation
+ * state).
+ *
+ * Camera model: pinhole with the intrinsics below and a pose per
+ * environment, camera-to-world (px,py,pz, qw,qx,qy,qz); camera axes x right,
+ * y down, z along the view.  Pixel (u, v) (u the column; images row-major
+ * [H][W]) casts the ray from the camera centre through image point
+ * (u + 1/2, v + 1/2), direction d = ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1)
+ * in camera axes, so a hit's ray parameter is its depth.  A pixel sees the
+ * nearest hit with depth in [z_near, z_far] over the environment's surface
+ * triangles (instance 1; tetrahedral meshes show their boundary faces) and
+ * its obstacles (instance 2 + k for obstacle k; FLASH_OBS_NONE is
+ * invisible); every surface is two-sided; equal depths go to the smaller
+ * instance.  Mesh edge tests are watertight: a ray never passes between two
+ * triangles that share an edge.
+ *
+ * Outputs (device; seg and points may be NULL): depth float32 [N][H][W]
+ * (0: no hit), seg uint8 [N][H][W] (0: no hit), points float32
+ * [N][H][W][3] world hit points (NaN: no hit).  Two kernel launches per
+ * call, stream-ordered; the caller keeps the output buffers.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t width, height; /* pixels; 1 <= width*height <= 2^26 */
+  float fx, fy, cx, cy;  /* intrinsics in pixels; fx, fy > 0 */
+  float z_near, z_far;   /* depth range (m); 0 < z_near < z_far */
+} flash_camera;
+
+/* Renders every environment of a finalized scene from its current state:
+ * positions as left by the last step or flash_set_state, obstacle poses of
+ * the current time (after a step: the pose it moved to).  cam_poses: device
+ * float32 [N][7].  The scene keeps a per-pixel work buffer of N*W*H*8 bytes,
+ * allocated on the first call (and again when the image grows). */
+flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *cam_poses, float *depth,
+                          uint8_t *seg, float *points, void *stream);
+
+/* Standalone batched ray caster for N environments that share one triangle
+ * mesh (n_verts vertices, tris host int32 [n_tris][3], indices checked),
+ * independent of a scene.  Owns the triangle list and the N*W*H*8-byte work
+ * buffer; synchronous allocation in create. */
+typedef struct flash_raycaster flash_raycaster;
+flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int32_t n_verts, int32_t n_tris,
+                                    const int32_t *tris, flash_raycaster **out);
+/* verts device float32 [N][n_verts][3]; obstacles per environment: n_obs
+ * (0..FLASH_MAX_OBS), obs_type device int32 [N][n_obs], obs_dims device
+ * float32 [N][n_obs][3], obs_poses device float32 [N][n_obs][7] (pose as
+ * in flash_set_obstacle_poses); cam_poses device float32 [N][7]. */
+flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_obs, const int32_t *obs_type,
+                           const float *obs_dims, const float *obs_poses, const float *cam_poses, float *depth,
+                           uint8_t *seg, float *points, void *stream);
+void flash_raycaster_destroy(flash_raycaster *rc);
+
 /* Advance every environment by n_steps (Algorithm 1 body). */
 flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
 

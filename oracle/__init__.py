@@ -67,6 +67,8 @@ def lib():
         _lib.or_residual.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, pd, pd, i, pi, pi, pd]
         _lib.or_raycast.argtypes = [i, pd, i, pi, i, pi, pd, pd, pd, pd, i, i, d, pd, pi, pd]
         _lib.or_raycast.restype = None
+        _lib.or_raycast_pixels.argtypes = [i, pd, i, pi, i, pi, pd, pd, pd, pd, i, pi, d, pd, pi, pd]
+        _lib.or_raycast_pixels.restype = None
         _lib.or_mlp_forward.argtypes = [i, pd, pd, pd]
         _lib.or_mlp_loss_grad.restype = d
         _lib.or_mlp_loss_grad.argtypes = [i, pd, pd, pd, pd]
@@ -324,6 +326,18 @@ def mlp_loss_grad(params_flat, x, t):
     return loss, g
 
 
+def _rc_args(x, tris, otype, odims, opose):
+    x = _f64(x).reshape(-1, 3)
+    tris = _i32(tris).reshape(-1, 3)
+    otype = _i32(otype).reshape(-1)
+    K = len(otype)
+    odims = _f64(odims).reshape(K, 3) if K else np.zeros((1, 3))
+    opose = _f64(opose).reshape(K, 7) if K else np.zeros((1, 7))
+    return (len(x), _pd(x if len(x) else np.zeros((1, 3))), len(tris),
+            _pi(tris if len(tris) else np.zeros((1, 3), np.int32)), K,
+            _pi(otype if K else np.zeros(1, np.int32)), _pd(odims), _pd(opose)), (x, tris, otype, odims, opose)
+
+
 def raycast(x, tris, otype, odims, opose, cam_pose, intr, W, H, dil=0.0):
     """Depth ray casting of one environment (appendix, depth rendering), by
     brute force in FP64.  x [n][3], tris [T][3]; obstacles otype [K], odims
@@ -331,17 +345,23 @@ def raycast(x, tris, otype, odims, opose, cam_pose, intr, W, H, dil=0.0):
     cy, z_near, z_far).  Returns depth [H][W] (0: no hit), seg [H][W] (0 none,
     1 mesh, 2 + k obstacle k), points [H][W][3] (NaN: no hit).  ``dil`` grows
     (> 0) or shrinks (< 0) every primitive (see oracle.h)."""
-    x = _f64(x).reshape(-1, 3)
-    tris = _i32(tris).reshape(-1, 3)
-    otype = _i32(otype).reshape(-1)
-    K = len(otype)
-    odims = _f64(odims).reshape(max(K, 1), 3) if K else np.zeros((1, 3))
-    opose = _f64(opose).reshape(max(K, 1), 7) if K else np.zeros((1, 7))
+    args, keep = _rc_args(x, tris, otype, odims, opose)
     depth = np.zeros((H, W))
     seg = np.zeros((H, W), np.int32)
     pts = np.zeros((H, W, 3))
-    lib().or_raycast(len(x), _pd(x if len(x) else np.zeros((1, 3))), len(tris),
-                     _pi(tris if len(tris) else np.zeros((1, 3), np.int32)), K,
-                     _pi(otype if K else np.zeros(1, np.int32)), _pd(odims), _pd(opose), _pd(_f64(cam_pose)),
-                     _pd(_f64(intr)), W, H, float(dil), _pd(depth), _pi(seg), _pd(pts))
+    cam, it = _f64(cam_pose), _f64(intr)
+    lib().or_raycast(*args, _pd(cam), _pd(it), W, H, float(dil), _pd(depth), _pi(seg), _pd(pts))
+    return depth, seg, pts
+
+
+def raycast_pixels(x, tris, otype, odims, opose, cam_pose, intr, uv, dil=0.0):
+    """``raycast`` for the pixels uv [m][2] = (u, v) only; outputs [m]."""
+    args, keep = _rc_args(x, tris, otype, odims, opose)
+    uv = _i32(uv).reshape(-1, 2)
+    m = len(uv)
+    depth = np.zeros(m)
+    seg = np.zeros(m, np.int32)
+    pts = np.zeros((m, 3))
+    cam, it = _f64(cam_pose), _f64(intr)
+    lib().or_raycast_pixels(*args, _pd(cam), _pd(it), m, _pi(uv), float(dil), _pd(depth), _pi(seg), _pd(pts))
     return depth, seg, pts

@@ -119,6 +119,10 @@ double or_fb(double a, double b);
 void or_raycast(int n, const double *x, int T, const int *tris, int K, const int *otype, const double *odims,
                 const double *opose, const double *cam, const double *intr, int W, int H, double dil,
                 double *depth, int *seg, double *pts);
+/* the same for a list of pixels uv [npix][2] = (u, v); outputs [npix] */
+void or_raycast_pixels(int n, const double *x, int T, const int *tris, int K, const int *otype,
+                       const double *odims, const double *opose, const double *cam, const double *intr, int npix,
+                       const int *uv, double dil, double *depth, int *seg, double *pts);
 
 #ifdef __cplusplus
 }

@@ -110,47 +110,65 @@ static int ray_obstacle(int type, const double *dims, const double *pose, const 
   return 0;
 }
 
+/* the nearest hit of pixel (u, v) */
+static void cast_pixel(const double *x, int T, const int *tris, int K, const int *otype, const double *odims,
+                       const double *opose, const double *cam, const double *Rc, const double *intr, int u, int v,
+                       double dil, double *depth, int *seg, double *pt) {
+  const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], zn = intr[4], zf = intr[5];
+  const double dc[3] = {(u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1.0};
+  double d[3];
+  rc_mul(Rc, dc, d);
+  double best = INFINITY;
+  int inst = 0;
+  /* triangles: instance 1, in index order (strict < keeps the smaller index) */
+  for (int f = 0; f < T; f++) {
+    double t;
+    if (ray_triangle(cam, d, x + 3 * tris[3 * f], x + 3 * tris[3 * f + 1], x + 3 * tris[3 * f + 2], dil, &t) &&
+        t >= zn && t <= zf && t < best) {
+      best = t;
+      inst = 1;
+    }
+  }
+  /* obstacles: instance 2 + k; on a tie the smaller instance keeps the pixel */
+  for (int k = 0; k < K; k++) {
+    double t;
+    if (otype[k] == 0) continue;
+    if (ray_obstacle(otype[k], odims + 3 * k, opose + 7 * k, cam, d, dil, zn, &t) && t <= zf && t < best) {
+      best = t;
+      inst = 2 + k;
+    }
+  }
+  if (inst) {
+    *depth = best;
+    *seg = inst;
+    for (int c = 0; c < 3; c++) pt[c] = cam[c] + best * d[c];
+  } else {
+    *depth = 0.0;
+    *seg = 0;
+    for (int c = 0; c < 3; c++) pt[c] = NAN;
+  }
+}
+
 void or_raycast(int n, const double *x, int T, const int *tris, int K, const int *otype, const double *odims,
                 const double *opose, const double *cam, const double *intr, int W, int H, double dil,
                 double *depth, int *seg, double *pts) {
   (void)n;
-  const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], zn = intr[4], zf = intr[5];
   double Rc[9];
   rc_quat_mat(cam + 3, Rc);
   for (int v = 0; v < H; v++)
     for (int u = 0; u < W; u++) {
-      const double dc[3] = {(u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1.0};
-      double d[3];
-      rc_mul(Rc, dc, d);
-      double best = INFINITY;
-      int inst = 0;
-      /* triangles: instance 1, in index order (strict < keeps the smaller index) */
-      for (int f = 0; f < T; f++) {
-        double t;
-        if (ray_triangle(cam, d, x + 3 * tris[3 * f], x + 3 * tris[3 * f + 1], x + 3 * tris[3 * f + 2], dil, &t) &&
-            t >= zn && t <= zf && t < best) {
-          best = t;
-          inst = 1;
-        }
-      }
-      /* obstacles: instance 2 + k; on a tie the smaller instance keeps the pixel */
-      for (int k = 0; k < K; k++) {
-        double t;
-        if (otype[k] == 0) continue;
-        if (ray_obstacle(otype[k], odims + 3 * k, opose + 7 * k, cam, d, dil, zn, &t) && t <= zf && t < best) {
-          best = t;
-          inst = 2 + k;
-        }
-      }
       const size_t p = (size_t)v * W + u;
-      if (inst) {
-        depth[p] = best;
-        seg[p] = inst;
-        for (int c = 0; c < 3; c++) pts[3 * p + c] = cam[c] + best * d[c];
-      } else {
-        depth[p] = 0.0;
-        seg[p] = 0;
-        for (int c = 0; c < 3; c++) pts[3 * p + c] = NAN;
-      }
+      cast_pixel(x, T, tris, K, otype, odims, opose, cam, Rc, intr, u, v, dil, depth + p, seg + p, pts + 3 * p);
     }
+}
+
+void or_raycast_pixels(int n, const double *x, int T, const int *tris, int K, const int *otype,
+                       const double *odims, const double *opose, const double *cam, const double *intr, int npix,
+                       const int *uv, double dil, double *depth, int *seg, double *pts) {
+  (void)n;
+  double Rc[9];
+  rc_quat_mat(cam + 3, Rc);
+  for (int i = 0; i < npix; i++)
+    cast_pixel(x, T, tris, K, otype, odims, opose, cam, Rc, intr, uv[2 * i], uv[2 * i + 1], dil, depth + i,
+               seg + i, pts + 3 * i);
 }

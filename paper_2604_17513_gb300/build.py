@@ -21,7 +21,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 # per-file extra flags: the step kernels use the hardware division / square root
 # (a few ulp; the parity tests bound the effect on positions at 1e-5 m)
 EXTRA = {"step_kernels.cu": ["--use_fast_math"]}
-SOURCES = ["api.cu", "step_kernels.cu", "gemm_simt.cu", "gemm_tc.cu", "setup_kernels.cu", "mlp.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "step_kernels.cu", "gemm_simt.cu", "gemm_tc.cu", "setup_kernels.cu", "mlp.cu", "noalloc.cu",
+           "raycast.cu"]
 
 
 def _nvcc():

@@ -3,6 +3,7 @@
 // of Sec. III-B and its explicit inverse), state I/O and the per-step
 // launch sequence of Algorithm 1.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -185,6 +186,36 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(upload(s, &g.D, Df));
   FLASH_CUDA_TRY(upload(s, &g.wt, wt));
   FLASH_CUDA_TRY(upload(s, &g.mass, massf));
+  {
+    // surface triangles for ray casting: the triangles themselves, or the
+    // faces that belong to one tetrahedron only (in tetrahedron order)
+    std::vector<int> rt;
+    if (m.type == FLASH_TRI) {
+      rt.assign(m.elems.begin(), m.elems.begin() + (size_t)3 * m.E);
+    } else {
+      std::map<std::array<int, 3>, int> count;
+      auto face = [&](int e, int k) {
+        std::array<int, 3> f;
+        for (int a = 0, j = 0; a < 4; a++)
+          if (a != k) f[j++] = m.elems[(size_t)e * 4 + a];
+        return f;
+      };
+      auto key = [](std::array<int, 3> f) { std::sort(f.begin(), f.end()); return f; };
+      for (int e = 0; e < m.E; e++)
+        for (int k = 0; k < 4; k++) count[key(face(e, k))]++;
+      for (int e = 0; e < m.E; e++)
+        for (int k = 0; k < 4; k++) {
+          const std::array<int, 3> f = face(e, k);
+          if (count[key(f)] == 1) rt.insert(rt.end(), f.begin(), f.end());
+        }
+    }
+    g.rT = (int)(rt.size() / 3);
+    if (g.rT > 0) {
+      int *d = nullptr;
+      FLASH_CUDA_TRY(upload(s, &d, rt));
+      g.rtris = reinterpret_cast<int3 *>(d);
+    }
+  }
   {
     // CSR vertex -> element slots (e * vpe + a), incidence order
     g.ev = m.E * g.vpe;
@@ -828,6 +859,7 @@ void flash_scene_destroy(flash_scene *s) {
   }
   if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   if (s->h_active) cudaFreeHost(s->h_active);
+  if (s->rc_keys) cudaFree(s->rc_keys);
   delete s;
 }
 
@@ -894,6 +926,38 @@ flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemcpyAsync(s->greq + first_env, request, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
   FLASH_CUDA_TRY(launch_grasp_set(s, first_env, count, obstacle, an[0], an[1], an[2], radius, st));
+  s->launches++;
+  return FLASH_OK;
+}
+
+flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *cam_poses, float *depth,
+                          uint8_t *seg, float *points, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (!cam_poses || !depth) return fail(FLASH_EINVAL, "cam_poses and depth are required");
+  if (s->N > 65535) return fail(FLASH_EINVAL, "ray casting takes at most 65535 environments");
+  RcCam C;
+  const flash_status r = rc_check_camera(cam, s->N, &C);
+  if (r != FLASH_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = (size_t)s->N * C.W * C.H;
+  if (need > s->rc_keys_n) {
+    if (s->rc_keys) {
+      FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+      FLASH_CUDA_TRY(cudaFree(s->rc_keys));
+      s->rc_keys = nullptr;
+      s->rc_keys_n = 0;
+    }
+    FLASH_CUDA_TRY(cudaMalloc(&s->rc_keys, need * sizeof(unsigned long long)));
+    s->rc_keys_n = need;
+    FLASH_CUDA_TRY(cudaMemsetAsync(s->rc_keys, 0xff, need * sizeof(unsigned long long), st));
+  }
+  for (const Group &g : s->groups) {
+    const RcMesh M{g.q, 3LL * g.n_pad, g.n_pad, 1, g.genv, 0, g.rtris, g.rT};
+    FLASH_CUDA_TRY(rc_launch_tri(M, g.N, cam_poses, C, s->rc_keys, st));
+    if (g.rT > 0) s->launches++;
+  }
+  const RcObs O{s->otype, s->odims, s->pose_t, s->K, FLASH_MAX_OBS};
+  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, depth, seg, points, st));
   s->launches++;
   return FLASH_OK;
 }

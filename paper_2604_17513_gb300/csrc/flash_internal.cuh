@@ -88,6 +88,8 @@ struct Group {
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
   uint8_t *gflag = nullptr;               // [N][n_pad] grasped vertices (S_grip)
+  int3 *rtris = nullptr;                  // [rT] surface triangles for ray casting
+  int rT = 0;
   int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner
   // full contact metric (flash_scene_desc.metric = FLASH_METRIC_FULL)
   float *fm_lin = nullptr, *fm_V = nullptr, *fm_H = nullptr, *fm_cs = nullptr, *fm_sn = nullptr, *fm_g = nullptr;
@@ -154,6 +156,8 @@ struct flash_scene {
   // carrying the anchor (-1 none); anchor xyz and activation radius
   int *gstate = nullptr, *gobs = nullptr, *greq = nullptr;
   float *ganchor = nullptr;   // [N][4]
+  unsigned long long *rc_keys = nullptr;   // ray casting work buffer (all bits set between calls)
+  size_t rc_keys_n = 0;
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
@@ -221,6 +225,34 @@ cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, 
 // lanes and their table launches (build_lanes at finalize)
 cudaError_t build_lanes(flash_scene *s, int n_lanes);
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
+// ray casting (raycast.cu) -------------------------------------------------
+struct RcCam {
+  int W, H;
+  float fx, fy, cx, cy, zn, zf;
+};
+// vertex positions of the environments of one mesh: vertex i, coordinate c
+// of source environment l at x[l * env_stride + c * coord_stride + i * vert_stride]
+struct RcMesh {
+  const float *x;
+  long long env_stride;
+  int coord_stride, vert_stride;
+  const int *genv;   // source environment -> output environment (nullptr: first_env + l)
+  int first_env;
+  const int3 *tris;
+  int T;
+};
+// obstacles of output environment e: k < K at [e * stride + k]
+struct RcObs {
+  const int *type;
+  const float *dims, *pose;
+  int K, stride;
+};
+cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
+                          unsigned long long *keys, cudaStream_t st);
+cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
+                              unsigned long long *keys, float *depth, uint8_t *seg, float *pts, cudaStream_t st);
+flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out);
+
 // grasp requests s->greq[first_env, first_env + count) -> per-environment grasp state
 cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int obstacle, float ax, float ay,
                              float az, float radius, cudaStream_t st);

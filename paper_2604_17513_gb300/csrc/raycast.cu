@@ -1,0 +1,347 @@
+// Batched depth ray casting of the simulation state (appendix, depth
+// rendering: depth maps, instance segmentation masks and point clouds cast
+// directly from the simulated meshes and obstacles).
+//
+// Every pixel sees the nearest hit along its ray.  The mesh part runs in
+// object order, which suits the many small triangles of a cloth (a triangle
+// covers a few pixels): one thread per (environment, triangle) transforms its
+// three vertices into the camera frame, walks the pixels of its projected
+// bounding box, tests each pixel's ray exactly and keeps the nearest hit per
+// pixel with a 64-bit atomicMin of (depth bits, triangle index): the result
+// is the nearest triangle hit of every pixel, the same answer as a ray-first
+// traversal, without building or refitting an acceleration structure for
+// the per-step geometry.  A second pass per pixel intersects the analytic
+// obstacles, picks the nearest surface and writes depth, instance and the
+// world point, and leaves the per-pixel keys empty for the next frame.
+//
+// Watertight edge tests: a ray from the camera centre with direction d lies
+// inside triangle (a, b, c) iff the three triple products d.(a x b),
+// d.(b x c), d.(c x a) share a sign.  Each edge's cross product is formed
+// from its two vertices in ascending index order with pinned rounding, so
+// the two triangles that share an edge evaluate exactly opposite values and
+// no ray slips between them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "flash_internal.cuh"
+
+namespace flash {
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ void rc_quat_mat(const float *q, float *R) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// a x b with every product and sum rounded explicitly (no contraction
+// choices left to the compiler), so equal operands give equal bits anywhere
+__device__ __forceinline__ float3 cross_rn(float3 a, float3 b) {
+  return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                     __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+// d.c with d = (dx, dy, 1)
+__device__ __forceinline__ float edge_rn(float3 c, float dx, float dy) {
+  return __fmaf_rn(dx, c.x, __fmaf_rn(dy, c.y, c.z));
+}
+// ray direction of pixel (u, v) in camera axes (z component 1)
+__device__ __forceinline__ float ray_dx(int u, const RcCam &C) { return __fdiv_rn(__fadd_rn(u + 0.5f, -C.cx), C.fx); }
+__device__ __forceinline__ float ray_dy(int v, const RcCam &C) { return __fdiv_rn(__fadd_rn(v + 0.5f, -C.cy), C.fy); }
+
+__global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restrict__ cam_poses, RcCam C,
+                                                unsigned long long *__restrict__ keys) {
+  __shared__ float sR[9], sp[3];
+  const int l = blockIdx.y;
+  const int e = M.genv ? M.genv[l] : M.first_env + l;
+  if (threadIdx.x == 0) {
+    const float *cp = cam_poses + 7 * (size_t)e;
+    rc_quat_mat(cp + 3, sR);
+    sp[0] = cp[0]; sp[1] = cp[1]; sp[2] = cp[2];
+  }
+  __syncthreads();
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= M.T) return;
+  const int3 t = M.tris[f];
+  const int vi[3] = {t.x, t.y, t.z};
+  const float *xe = M.x + (size_t)l * M.env_stride;
+  float3 y[3];
+  float zmin = INFINITY, zmax = -INFINITY;
+  bool finite = true;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float *xv = xe + (size_t)vi[k] * M.vert_stride;
+    const float w0 = __fsub_rn(xv[0], sp[0]), w1 = __fsub_rn(xv[M.coord_stride], sp[1]),
+                w2 = __fsub_rn(xv[2 * M.coord_stride], sp[2]);
+    // camera coordinates y = R^T (x - p)
+    y[k] = make_float3(__fmaf_rn(sR[6], w2, __fmaf_rn(sR[3], w1, __fmul_rn(sR[0], w0))),
+                       __fmaf_rn(sR[7], w2, __fmaf_rn(sR[4], w1, __fmul_rn(sR[1], w0))),
+                       __fmaf_rn(sR[8], w2, __fmaf_rn(sR[5], w1, __fmul_rn(sR[2], w0))));
+    finite = finite && isfinite(y[k].x) && isfinite(y[k].y) && isfinite(y[k].z);
+    zmin = fminf(zmin, y[k].z);
+    zmax = fmaxf(zmax, y[k].z);
+  }
+  // no point of the triangle can lie in the depth range
+  if (!finite || zmax < C.zn || zmin > C.zf) return;
+  // canonical edge normals: edge k joins the two vertices other than k
+  float3 ce[3];
+  float sg[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    if (vi[a] < vi[b]) { ce[k] = cross_rn(y[a], y[b]); sg[k] = 1.f; }
+    else { ce[k] = cross_rn(y[b], y[a]); sg[k] = -1.f; }
+  }
+  // supporting plane n.x = n.y0 (edge vectors are short and accurate)
+  const float3 e1 = make_float3(y[1].x - y[0].x, y[1].y - y[0].y, y[1].z - y[0].z);
+  const float3 e2 = make_float3(y[2].x - y[0].x, y[2].y - y[0].y, y[2].z - y[0].z);
+  const float3 n = make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+  const float num = n.x * y[0].x + n.y * y[0].y + n.z * y[0].z;
+  // pixels whose centres the projection may cover, one pixel of slack each
+  // way; a triangle reaching behind the camera takes the whole image
+  int u0 = 0, u1 = C.W - 1, v0 = 0, v1 = C.H - 1;
+  if (zmin > 0.5f * C.zn) {
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const float iz = 1.f / y[k].z;
+      const float uu = C.fx * y[k].x * iz + C.cx, vv = C.fy * y[k].y * iz + C.cy;
+      umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+      vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+    }
+    if (umax < -1.f || vmax < -1.f || umin > C.W + 1.f || vmin > C.H + 1.f) return;
+    u0 = max(0, (int)floorf(fmaxf(umin - 0.5f, -1.f)));
+    u1 = min(C.W - 1, (int)ceilf(fminf(umax - 0.5f, (float)C.W)));
+    v0 = max(0, (int)floorf(fmaxf(vmin - 0.5f, -1.f)));
+    v1 = min(C.H - 1, (int)ceilf(fminf(vmax - 0.5f, (float)C.H)));
+  }
+  unsigned long long *ke = keys + (size_t)e * C.W * C.H;
+  for (int v = v0; v <= v1; v++) {
+    const float dy = ray_dy(v, C);
+    for (int u = u0; u <= u1; u++) {
+      const float dx = ray_dx(u, C);
+      const float s0 = sg[0] * edge_rn(ce[0], dx, dy);
+      const float s1 = sg[1] * edge_rn(ce[1], dx, dy);
+      const float s2 = sg[2] * edge_rn(ce[2], dx, dy);
+      const bool in = (s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f);
+      if (!in) continue;
+      const float nd = n.x * dx + n.y * dy + n.z;
+      if (nd == 0.f) continue;
+      const float depth = num / nd;
+      if (!(depth >= C.zn && depth <= C.zf)) continue;
+      atomicMin(ke + (size_t)v * C.W + u, ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f);
+    }
+  }
+}
+
+// nearest hit t >= zn of ray o + t d with an analytic obstacle (INFINITY: none)
+__device__ float ray_obstacle(int type, const float *dims, const float *R, const float *p, float3 o, float3 d,
+                              float zn) {
+  if (type == FLASH_OBS_PLANE) {
+    const float3 nn = make_float3(R[2], R[5], R[8]);   // body +z in world axes
+    const float dn = nn.x * d.x + nn.y * d.y + nn.z * d.z;
+    if (dn == 0.f) return INFINITY;
+    const float t = (nn.x * (p[0] - o.x) + nn.y * (p[1] - o.y) + nn.z * (p[2] - o.z)) / dn;
+    return t >= zn ? t : INFINITY;
+  }
+  if (type == FLASH_OBS_SPHERE) {
+    // closest approach along the unit direction, then the chord: no
+    // cancellation between |c - o|^2 and r^2 near the silhouette
+    const float r = dims[0];
+    const float dl = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    const float3 u = make_float3(d.x / dl, d.y / dl, d.z / dl);
+    const float3 co = make_float3(p[0] - o.x, p[1] - o.y, p[2] - o.z);
+    const float tc = u.x * co.x + u.y * co.y + u.z * co.z;
+    const float3 q = make_float3(co.x - tc * u.x, co.y - tc * u.y, co.z - tc * u.z);
+    const float h2 = q.x * q.x + q.y * q.y + q.z * q.z;
+    if (h2 > r * r) return INFINITY;
+    const float s = sqrtf(r * r - h2);
+    const float t1 = (tc - s) / dl, t2 = (tc + s) / dl;
+    return t1 >= zn ? t1 : (t2 >= zn ? t2 : INFINITY);
+  }
+  if (type == FLASH_OBS_BOX) {
+    const float w[3] = {o.x - p[0], o.y - p[1], o.z - p[2]};
+    const float dw[3] = {d.x, d.y, d.z};
+    float tmin = -INFINITY, tmax = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float ob = R[i] * w[0] + R[3 + i] * w[1] + R[6 + i] * w[2];
+      const float db = R[i] * dw[0] + R[3 + i] * dw[1] + R[6 + i] * dw[2];
+      if (db == 0.f) {
+        if (fabsf(ob) > dims[i]) return INFINITY;
+        continue;
+      }
+      float ta = (-dims[i] - ob) / db, tb = (dims[i] - ob) / db;
+      if (ta > tb) { const float x = ta; ta = tb; tb = x; }
+      tmin = fmaxf(tmin, ta);
+      tmax = fminf(tmax, tb);
+    }
+    if (tmin > tmax) return INFINITY;
+    return tmin >= zn ? tmin : (tmax >= zn ? tmax : INFINITY);
+  }
+  return INFINITY;
+}
+
+__global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__restrict__ cam_poses, RcCam C,
+                                                    int first_env, unsigned long long *__restrict__ keys,
+                                                    float *__restrict__ depth, uint8_t *__restrict__ seg,
+                                                    float *__restrict__ pts) {
+  __shared__ float sRc[9], spc[3];
+  __shared__ int otype[FLASH_MAX_OBS];
+  __shared__ float odims[FLASH_MAX_OBS][3], oR[FLASH_MAX_OBS][9], op[FLASH_MAX_OBS][3];
+  const int e = first_env + blockIdx.y;
+  if (threadIdx.x == 0) {
+    const float *cp = cam_poses + 7 * (size_t)e;
+    rc_quat_mat(cp + 3, sRc);
+    spc[0] = cp[0]; spc[1] = cp[1]; spc[2] = cp[2];
+  }
+  if (threadIdx.x < O.K) {
+    const int k = threadIdx.x;
+    const size_t b = (size_t)e * O.stride + k;
+    otype[k] = O.type[b];
+    for (int c = 0; c < 3; c++) odims[k][c] = O.dims[3 * b + c];
+    rc_quat_mat(O.pose + 7 * b + 3, oR[k]);
+    for (int c = 0; c < 3; c++) op[k][c] = O.pose[7 * b + c];
+  }
+  __syncthreads();
+  const int WH = C.W * C.H;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= WH) return;
+  const int v = pix / C.W, u = pix - v * C.W;
+  const float dx = ray_dx(u, C), dy = ray_dy(v, C);
+  const float3 d = make_float3(sRc[0] * dx + sRc[1] * dy + sRc[2], sRc[3] * dx + sRc[4] * dy + sRc[5],
+                               sRc[6] * dx + sRc[7] * dy + sRc[8]);
+  const float3 o = make_float3(spc[0], spc[1], spc[2]);
+  const size_t pe = (size_t)e * WH + pix;
+  const unsigned long long key = keys[pe];
+  keys[pe] = kEmpty;   // ready for the next frame
+  float best = INFINITY;
+  int inst = 0;
+  if (key != kEmpty) {
+    best = __uint_as_float((unsigned)(key >> 32));
+    inst = 1;
+  }
+  for (int k = 0; k < O.K; k++) {   // ties keep the smaller instance
+    if (otype[k] == FLASH_OBS_NONE) continue;
+    const float t = ray_obstacle(otype[k], odims[k], oR[k], op[k], o, d, C.zn);
+    if (t <= C.zf && t < best) {
+      best = t;
+      inst = 2 + k;
+    }
+  }
+  depth[pe] = inst ? best : 0.f;
+  if (seg) seg[pe] = (uint8_t)inst;
+  if (pts) {
+    const float nan = __int_as_float(0x7fc00000);
+    pts[3 * pe] = inst ? o.x + best * d.x : nan;
+    pts[3 * pe + 1] = inst ? o.y + best * d.y : nan;
+    pts[3 * pe + 2] = inst ? o.z + best * d.z : nan;
+  }
+}
+
+}  // namespace
+
+cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
+                          unsigned long long *keys, cudaStream_t st) {
+  if (M.T <= 0 || n_envs <= 0) return cudaSuccess;
+  k_rc_tri<<<dim3((M.T + 255) / 256, n_envs), 256, 0, st>>>(M, cam_poses, C, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
+                              unsigned long long *keys, float *depth, uint8_t *seg, float *pts, cudaStream_t st) {
+  if (n_envs <= 0) return cudaSuccess;
+  const int WH = C.W * C.H;
+  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, depth, seg, pts);
+  return cudaGetLastError();
+}
+
+flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out) {
+  if (!cam) { set_error("camera is NULL"); return FLASH_EINVAL; }
+  const int64_t W = cam->width, H = cam->height;
+  if (W < 1 || H < 1 || W * H > (1 << 26) || n_envs * W * H > ((int64_t)1 << 34)) {
+    set_error("camera size out of range (1 <= W*H <= 2^26 pixels, N*W*H <= 2^34)");
+    return FLASH_EINVAL;
+  }
+  const float v[6] = {cam->fx, cam->fy, cam->cx, cam->cy, cam->z_near, cam->z_far};
+  for (float x : v)
+    if (!std::isfinite(x)) { set_error("camera parameters must be finite"); return FLASH_EINVAL; }
+  if (!(cam->fx > 0.f && cam->fy > 0.f) || !(cam->z_near > 0.f && cam->z_near < cam->z_far)) {
+    set_error("camera needs fx, fy > 0 and 0 < z_near < z_far");
+    return FLASH_EINVAL;
+  }
+  *out = RcCam{(int)W, (int)H, cam->fx, cam->fy, cam->cx, cam->cy, cam->z_near, cam->z_far};
+  return FLASH_OK;
+}
+
+}  // namespace flash
+
+struct flash_raycaster {
+  flash::RcCam cam{};
+  int N = 0, n = 0, T = 0;
+  int3 *tris = nullptr;
+  unsigned long long *keys = nullptr;
+};
+
+using flash::set_error;
+
+flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int32_t n_verts, int32_t n_tris,
+                                    const int32_t *tris, flash_raycaster **out) {
+  if (!out) { set_error("out is NULL"); return FLASH_EINVAL; }
+  *out = nullptr;
+  if (n_envs < 1 || n_envs > 65535 || n_verts < 0 || n_tris < 0 || (n_tris > 0 && !tris)) {
+    set_error("invalid ray caster sizes (1 <= n_envs <= 65535, n_verts, n_tris >= 0)");
+    return FLASH_EINVAL;
+  }
+  flash::RcCam C;
+  flash_status r = flash::rc_check_camera(cam, n_envs, &C);
+  if (r != FLASH_OK) return r;
+  for (int64_t i = 0; i < 3 * (int64_t)n_tris; i++)
+    if (tris[i] < 0 || tris[i] >= n_verts) { set_error("triangle vertex index out of range"); return FLASH_EINVAL; }
+  flash_raycaster *rc = new flash_raycaster;
+  rc->cam = C;
+  rc->N = n_envs; rc->n = n_verts; rc->T = n_tris;
+  const size_t keys = (size_t)n_envs * C.W * C.H;
+  cudaError_t e = cudaMalloc(&rc->keys, keys * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(rc->keys, 0xff, keys * sizeof(unsigned long long));
+  if (e == cudaSuccess && n_tris > 0) {
+    e = cudaMalloc(&rc->tris, sizeof(int3) * n_tris);
+    if (e == cudaSuccess) e = cudaMemcpy(rc->tris, tris, sizeof(int3) * n_tris, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("ray caster allocation: ") + cudaGetErrorString(e));
+    flash_raycaster_destroy(rc);
+    return e == cudaErrorMemoryAllocation ? FLASH_ENOMEM : FLASH_ECUDA;
+  }
+  *out = rc;
+  return FLASH_OK;
+}
+
+void flash_raycaster_destroy(flash_raycaster *rc) {
+  if (!rc) return;
+  if (rc->tris) cudaFree(rc->tris);
+  if (rc->keys) cudaFree(rc->keys);
+  delete rc;
+}
+
+flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_obs, const int32_t *obs_type,
+                           const float *obs_dims, const float *obs_poses, const float *cam_poses, float *depth,
+                           uint8_t *seg, float *points, void *stream) {
+  if (!rc || !depth || !cam_poses || (rc->T > 0 && !verts)) { set_error("invalid arguments"); return FLASH_EINVAL; }
+  if (n_obs < 0 || n_obs > FLASH_MAX_OBS || (n_obs > 0 && (!obs_type || !obs_dims || !obs_poses))) {
+    set_error("obstacles: 0 <= n_obs <= FLASH_MAX_OBS with type, dims and poses");
+    return FLASH_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  flash::RcMesh M{verts, 3LL * rc->n, 1, 3, nullptr, 0, rc->tris, rc->T};
+  FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, st));
+  flash::RcObs O{obs_type, obs_dims, obs_poses, n_obs, n_obs};
+  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, depth, seg, points, st));
+  return FLASH_OK;
+}

@@ -34,6 +34,13 @@ class FlashError(RuntimeError):
         self.code = code
 
 
+class Camera(C.Structure):
+    """Pinhole camera of the ray caster (flash_camera): image size in pixels,
+    intrinsics fx, fy, cx, cy in pixels, depth range [z_near, z_far] in m."""
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("z_near", C.c_float), ("z_far", C.c_float)]
+
+
 class SceneDesc(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("tol_ncp", C.c_double), ("maxforce", C.c_double),
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
@@ -82,6 +89,11 @@ def lib():
         L.flash_set_obstacle_poses.argtypes = [vp, vp, i32, vp]
         L.flash_step.argtypes = [vp, i32, vp]
         L.flash_grasp.argtypes = [vp, i32, i32, C.POINTER(i32), i32, C.POINTER(C.c_float), C.c_float, vp]
+        L.flash_render.argtypes = [vp, C.POINTER(Camera), vp, vp, vp, vp, vp]
+        L.flash_raycaster_create.argtypes = [C.POINTER(Camera), i32, i32, i32, C.POINTER(i32), C.POINTER(vp)]
+        L.flash_raycast.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.flash_raycaster_destroy.argtypes = [vp]
+        L.flash_raycaster_destroy.restype = None
         L.flash_get_contacts.argtypes = [vp, vp, vp, vp, vp, vp]
         L.flash_contact_cap.argtypes = [vp]
         L.flash_get_stats.argtypes = [vp, vp, vp, vp]
@@ -108,7 +120,7 @@ def lib():
         L.flash_dense_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
-                     "flash_step", "flash_grasp", "flash_get_contacts", "flash_get_stats", "flash_status_word",
+                     "flash_step", "flash_grasp", "flash_render", "flash_raycaster_create", "flash_raycast", "flash_get_contacts", "flash_get_stats", "flash_status_word",
                      "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
                      "flash_warmstart_bounds",
                      "flash_record_contacts", "flash_get_recorded", "flash_mlp_forward", "flash_mlp_loss_grad",
@@ -254,6 +266,22 @@ class Sim:
                            g["radius"], first)
             first += sc.n_envs
 
+    def render(self, cam, cam_poses, seg=True, points=True):
+        """Ray cast every environment from its current state (flash_render):
+        cam a Camera, cam_poses CUDA float32 [N][7] camera-to-world.  Returns
+        depth [N][H][W] (0: no hit), seg uint8 [N][H][W] (0 none, 1 mesh, 2 + k
+        obstacle k) and world points [N][H][W][3] (NaN: no hit), or None for
+        the outputs not asked for."""
+        assert cam_poses.is_cuda and cam_poses.dtype == torch.float32 and cam_poses.shape == (self.n_envs, 7)
+        cam_poses = cam_poses.contiguous()
+        H, W = cam.height, cam.width
+        depth = torch.empty((self.n_envs, H, W), dtype=torch.float32, device=self.dev)
+        sg = torch.empty((self.n_envs, H, W), dtype=torch.uint8, device=self.dev) if seg else None
+        pt = torch.empty((self.n_envs, H, W, 3), dtype=torch.float32, device=self.dev) if points else None
+        _check(lib().flash_render(self._h, C.byref(cam), _ptr(cam_poses), _ptr(depth), _ptr(sg), _ptr(pt),
+                                  _stream()))
+        return depth, sg, pt
+
     def contacts(self):
         cnt = torch.empty(self.n_envs, dtype=torch.int32, device=self.dev)
         vert = torch.empty((self.n_envs, self.cap), dtype=torch.int32, device=self.dev)
@@ -376,3 +404,39 @@ def mlp_loss_grad(params, x, t, work=None):
 
 def mlp_adam(params, grad, m, v, step, lr):
     _check(lib().flash_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, _stream()))
+
+
+class Raycaster:
+    """Standalone batched ray caster (flash_raycaster_*): N environments that
+    share one triangle mesh ``tris`` [T][3] over ``n_verts`` vertices."""
+
+    def __init__(self, cam, n_envs, n_verts, tris):
+        tris = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
+        self.cam, self.n_envs, self.n_verts = cam, n_envs, n_verts
+        self._h = C.c_void_p()
+        _check(lib().flash_raycaster_create(C.byref(cam), n_envs, n_verts, len(tris),
+                                            tris.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(self._h)))
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().flash_raycaster_destroy(self._h)
+            self._h = None
+
+    def cast(self, verts, obs_type, obs_dims, obs_poses, cam_poses, seg=True, points=True, out=None):
+        """verts CUDA float32 [N][n][3]; obs_type int32 [N][K], obs_dims [N][K][3],
+        obs_poses [N][K][7] (K may be 0); cam_poses [N][7].  Returns (depth,
+        seg, points) like Sim.render; ``out`` reuses a previous result's
+        tensors."""
+        N, H, W = self.n_envs, self.cam.height, self.cam.width
+        K = 0 if obs_type is None else obs_type.shape[1]
+        if out is None:
+            depth = torch.empty((N, H, W), dtype=torch.float32, device=self.dev)
+            sg = torch.empty((N, H, W), dtype=torch.uint8, device=self.dev) if seg else None
+            pt = torch.empty((N, H, W, 3), dtype=torch.float32, device=self.dev) if points else None
+        else:
+            depth, sg, pt = out
+        _check(lib().flash_raycast(self._h, _ptr(verts), K, _ptr(obs_type) if K else None,
+                                   _ptr(obs_dims) if K else None, _ptr(obs_poses) if K else None, _ptr(cam_poses),
+                                   _ptr(depth), _ptr(sg), _ptr(pt), _stream()))
+        return depth, sg, pt

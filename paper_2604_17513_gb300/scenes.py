@@ -462,3 +462,106 @@ def mixed_batch(seed: int = 3, n_envs: int = 2048, steps: int = 1000, side_choic
                          np.ones(N), obs_type, obs_dims, np.zeros((N, K)), poses, h=0.01, thickness=tau, steps=steps,
                          meta={"envs": envs}))
     return out
+
+
+# --------------------------------------------------------------------------
+# ray-casting inputs
+# --------------------------------------------------------------------------
+def _quat_axis_angle(axis, ang):
+    a = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    return np.array([np.cos(ang / 2), *(np.sin(ang / 2) * a)])
+
+
+def _quat_mul(a, b):
+    """Hamilton product of quaternions (w, x, y, z)."""
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+@dataclass
+class RayScene:
+    """Batched ray-casting input: N environments sharing one triangle mesh.
+
+    verts [N][n][3], tris int32 [T][3]; obstacles obs_type int32 [N][K],
+    obs_dims [N][K][3], obs_poses [N][K][7]; cam_poses [N][7]
+    (camera-to-world, camera x right, y down, z along the view); cam =
+    (width, height, fx, fy, cx, cy, z_near, z_far).
+    """
+    name: str
+    verts: np.ndarray
+    tris: np.ndarray
+    obs_type: np.ndarray
+    obs_dims: np.ndarray
+    obs_poses: np.ndarray
+    cam_poses: np.ndarray
+    cam: tuple
+
+    @property
+    def n_envs(self) -> int:
+        return self.verts.shape[0]
+
+
+def towel_views(seed: int = 4, n_envs: int = 128, n_side: int = 181, side: float = 0.6, width: int = 640,
+                height: int = 480, hfov_deg: float = 56.0, cam_height=(0.8, 1.0), tilt_deg: float = 15.0) -> RayScene:
+    """Towel-folding views for depth rendering (appendix, depth rendering
+    overhead: a towel on a table seen by an overhead depth camera).
+
+    The towel is an n_side x n_side grid (181: 32,761 vertices, 64,800
+    triangles) of side ``side`` lying on the ground 1 mm up, with wrinkles
+    (four plane waves, wavelength U[3, 15] cm, amplitude U[0, 4] mm) and one
+    fold: the part beyond a random line near the centre wraps around a
+    cylinder of radius U[5, 15] mm by U[144, 180] degrees and continues
+    straight, so the folded layer lies over the towel.  Obstacles: the ground plane, two
+    gripper finger boxes (2 x 2 x 4 cm) 5-15 cm above the towel, and one
+    invisible pose carrier.  The camera looks down at the towel (its centre
+    within 2 cm) from U[cam_height] m with
+    up to ``tilt_deg`` of tilt and a random yaw; pinhole with horizontal field
+    of view ``hfov_deg``, depth range [0.05, 5] m.
+    """
+    rest, tris = cloth_grid(n_side, n_side, side)
+    n = len(rest)
+    verts = np.zeros((n_envs, n, 3))
+    K = 4
+    obs_type = np.tile(np.array([PLANE, BOX, BOX, NONE], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, K, 3))
+    obs_dims[:, 1:3] = (0.01, 0.01, 0.02)
+    obs_poses = np.zeros((n_envs, K, 7))
+    cam_poses = np.zeros((n_envs, 7))
+    fx = width / 2 / np.tan(np.radians(hfov_deg) / 2)
+    cam = (width, height, fx, fx, width / 2, height / 2, 0.05, 5.0)
+    tau = 1e-3
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        xy = rest[:, :2].copy()
+        z = np.full(n, tau)
+        for _ in range(4):
+            ang, lam = g.uniform(0, 2 * np.pi), g.uniform(0.03, 0.15)
+            amp, ph = g.uniform(0, 0.004), g.uniform(0, 2 * np.pi)
+            k = 2 * np.pi / lam * np.array([np.cos(ang), np.sin(ang)])
+            z += amp * 0.5 * (1 + np.sin(xy @ k + ph))
+        c = g.uniform(-0.25 * side, 0.25 * side, 2)
+        beta = g.uniform(0, 2 * np.pi)
+        m = np.array([np.cos(beta), np.sin(beta)])
+        alpha, rf = g.uniform(0.8 * np.pi, np.pi), g.uniform(0.005, 0.015)
+        s = (xy - c) @ m
+        th = np.minimum(s / rf, alpha)
+        sp = np.where(s < rf * alpha, rf * np.sin(th), rf * np.sin(alpha) + (s - rf * alpha) * np.cos(alpha))
+        zp = np.where(s < rf * alpha, rf * (1 - np.cos(th)), rf * (1 - np.cos(alpha)) + (s - rf * alpha) * np.sin(alpha))
+        fold = s > 0
+        xy[fold] += ((sp - s)[fold])[:, None] * m
+        z[fold] += zp[fold]
+        verts[e] = np.c_[xy, z]
+        obs_poses[e, 0] = _pose((0, 0, 0))
+        for k in (1, 2):
+            p = g.uniform(-0.3 * side, 0.3 * side, 2)
+            obs_poses[e, k] = _pose((p[0], p[1], g.uniform(0.05, 0.15)),
+                                    _quat_axis_angle((0, 0, 1), g.uniform(0, 2 * np.pi)))
+        obs_poses[e, 3] = _pose((0, 0, 0.3))
+        q = _quat_mul(_quat_axis_angle((0, 0, 1), g.uniform(0, 2 * np.pi)),
+                      _quat_axis_angle((1, 0, 0), np.pi + np.radians(g.uniform(-tilt_deg, tilt_deg))))
+        ctr = verts[e, :, :2].mean(0)
+        pc = (ctr[0] + g.uniform(-0.02, 0.02), ctr[1] + g.uniform(-0.02, 0.02), g.uniform(*cam_height))
+        cam_poses[e] = _pose(pc, q)
+    return RayScene("towel_views", verts, tris, obs_type, obs_dims, obs_poses, cam_poses, cam)
