@@ -310,6 +310,7 @@ flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int
   const size_t keys = (size_t)n_envs * C.W * C.H;
   cudaError_t e = cudaMalloc(&rc->keys, keys * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(rc->keys, 0xff, keys * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the buffer is ready for any stream
   if (e == cudaSuccess && n_tris > 0) {
     e = cudaMalloc(&rc->tris, sizeof(int3) * n_tris);
     if (e == cudaSuccess) e = cudaMemcpy(rc->tris, tris, sizeof(int3) * n_tris, cudaMemcpyHostToDevice);
