@@ -235,6 +235,14 @@ flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_ob
                            const float *obs_dims, const float *obs_poses, const float *cam_poses, float *depth,
                            uint8_t *seg, float *points, void *stream);
 void flash_raycaster_destroy(flash_raycaster *rc);
+/* Per-kernel device time of later flash_raycast calls: enable != 0 brackets
+ * the two launches with CUDA events on the call's stream and waits for them
+ * at the end of each call (for measurement only); the totals restart at
+ * every flash_raycaster_profile call.  profile_read: ms host double [2] and
+ * launches host int64 [2], index 0 the triangle pass, 1 the per-pixel
+ * resolve. */
+flash_status flash_raycaster_profile(flash_raycaster *rc, int32_t enable);
+flash_status flash_raycaster_profile_read(const flash_raycaster *rc, double *ms, int64_t *launches);
 
 /* Advance every environment by n_steps (Algorithm 1 body). */
 flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);

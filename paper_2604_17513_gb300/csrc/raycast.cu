@@ -287,6 +287,11 @@ struct flash_raycaster {
   int N = 0, n = 0, T = 0;
   int3 *tris = nullptr;
   unsigned long long *keys = nullptr;
+  // per-kernel device time while profiling (0: triangles, 1: resolve)
+  bool profiling = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double prof_ms[2] = {0, 0};
+  int64_t prof_n[2] = {0, 0};
 };
 
 using flash::set_error;
@@ -326,6 +331,8 @@ flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int
 
 void flash_raycaster_destroy(flash_raycaster *rc) {
   if (!rc) return;
+  for (cudaEvent_t e : rc->ev)
+    if (e) cudaEventDestroy(e);
   if (rc->tris) cudaFree(rc->tris);
   if (rc->keys) cudaFree(rc->keys);
   delete rc;
@@ -340,9 +347,38 @@ flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_ob
     return FLASH_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const bool prof = rc->profiling;
+  if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[0], st));
   flash::RcMesh M{verts, 3LL * rc->n, 1, 3, nullptr, 0, rc->tris, rc->T};
   FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, st));
+  if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[1], st));
   flash::RcObs O{obs_type, obs_dims, obs_poses, n_obs, n_obs};
   FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, depth, seg, points, st));
+  if (prof) {
+    FLASH_CUDA_TRY(cudaEventRecord(rc->ev[2], st));
+    FLASH_CUDA_TRY(cudaEventSynchronize(rc->ev[2]));
+    float a = 0.f, b = 0.f;
+    FLASH_CUDA_TRY(cudaEventElapsedTime(&a, rc->ev[0], rc->ev[1]));
+    FLASH_CUDA_TRY(cudaEventElapsedTime(&b, rc->ev[1], rc->ev[2]));
+    if (rc->T > 0) { rc->prof_ms[0] += a; rc->prof_n[0]++; }
+    rc->prof_ms[1] += b;
+    rc->prof_n[1]++;
+  }
+  return FLASH_OK;
+}
+
+flash_status flash_raycaster_profile(flash_raycaster *rc, int32_t enable) {
+  if (!rc) { set_error("ray caster is NULL"); return FLASH_EINVAL; }
+  if (enable && !rc->ev[0])
+    for (cudaEvent_t &e : rc->ev) FLASH_CUDA_TRY(cudaEventCreate(&e));
+  rc->profiling = enable != 0;
+  rc->prof_ms[0] = rc->prof_ms[1] = 0.0;
+  rc->prof_n[0] = rc->prof_n[1] = 0;
+  return FLASH_OK;
+}
+
+flash_status flash_raycaster_profile_read(const flash_raycaster *rc, double *ms, int64_t *launches) {
+  if (!rc || !ms || !launches) { set_error("invalid arguments"); return FLASH_EINVAL; }
+  for (int k = 0; k < 2; k++) { ms[k] = rc->prof_ms[k]; launches[k] = rc->prof_n[k]; }
   return FLASH_OK;
 }

@@ -94,6 +94,8 @@ def lib():
         L.flash_raycast.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.flash_raycaster_destroy.argtypes = [vp]
         L.flash_raycaster_destroy.restype = None
+        L.flash_raycaster_profile.argtypes = [vp, i32]
+        L.flash_raycaster_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
         L.flash_get_contacts.argtypes = [vp, vp, vp, vp, vp, vp]
         L.flash_contact_cap.argtypes = [vp]
         L.flash_get_stats.argtypes = [vp, vp, vp, vp]
@@ -120,7 +122,8 @@ def lib():
         L.flash_dense_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
-                     "flash_step", "flash_grasp", "flash_render", "flash_raycaster_create", "flash_raycast", "flash_get_contacts", "flash_get_stats", "flash_status_word",
+                     "flash_step", "flash_grasp", "flash_render", "flash_raycaster_create", "flash_raycast",
+                     "flash_raycaster_profile", "flash_raycaster_profile_read", "flash_get_contacts", "flash_get_stats", "flash_status_word",
                      "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
                      "flash_warmstart_bounds",
                      "flash_record_contacts", "flash_get_recorded", "flash_mlp_forward", "flash_mlp_loss_grad",
@@ -440,3 +443,13 @@ class Raycaster:
                                    _ptr(obs_dims) if K else None, _ptr(obs_poses) if K else None, _ptr(cam_poses),
                                    _ptr(depth), _ptr(sg), _ptr(pt), _stream()))
         return depth, sg, pt
+
+    def profile(self, enable=True):
+        """Bracket the two kernels of every later cast with CUDA events."""
+        _check(lib().flash_raycaster_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{"tri": (ms, launches), "resolve": (ms, launches)} since profile()."""
+        ms, n = (C.c_double * 2)(), (C.c_int64 * 2)()
+        _check(lib().flash_raycaster_profile_read(self._h, ms, n))
+        return {"tri": (ms[0], n[0]), "resolve": (ms[1], n[1])}
