@@ -14,12 +14,13 @@
 // obstacles, picks the nearest surface and writes depth, instance and the
 // world point, and leaves the per-pixel keys empty for the next frame.
 //
-// Watertight edge tests: a ray from the camera centre with direction d lies
-// inside triangle (a, b, c) iff the three triple products d.(a x b),
-// d.(b x c), d.(c x a) share a sign.  Each edge's cross product is formed
-// from its two vertices in ascending index order with pinned rounding, so
-// the two triangles that share an edge evaluate exactly opposite values and
-// no ray slips between them.
+// Watertight coverage: for a triangle in front of the camera, a pixel's ray
+// meets it iff the pixel centre lies in its projection; projections are
+// snapped to 1/4096 pixel per vertex and the 2D edge functions evaluated
+// exactly in integers, so no ray slips between triangles that share an edge
+// or a vertex (the snap moves a decision by at most 1/4096 pixel).
+// Triangles reaching behind the camera use the 3D cone test (the three
+// triple products d.(a x b) share a sign).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,6 +34,11 @@ namespace flash {
 namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
+// fixed-point image coordinates: 1/4096 pixel; projections beyond 2^17
+// pixels take the 3D path, so every edge-function product fits in 62 bits
+constexpr int kSubBits = 12;
+constexpr long long kSub = 1LL << kSubBits;
+constexpr float kMaxProj = 131072.f;
 
 __device__ __forceinline__ void rc_quat_mat(const float *q, float *R) {
   const float w = q[0], x = q[1], y = q[2], z = q[3];
@@ -89,7 +95,61 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
   }
   // no point of the triangle can lie in the depth range
   if (!finite || zmax < C.zn || zmin > C.zf) return;
-  // canonical edge normals: edge k joins the two vertices other than k
+  // supporting plane n.x = n.y0 (edge vectors are short and accurate)
+  const float3 e1 = make_float3(y[1].x - y[0].x, y[1].y - y[0].y, y[1].z - y[0].z);
+  const float3 e2 = make_float3(y[2].x - y[0].x, y[2].y - y[0].y, y[2].z - y[0].z);
+  const float3 n = make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+  const float num = n.x * y[0].x + n.y * y[0].y + n.z * y[0].z;
+  unsigned long long *ke = keys + (size_t)e * C.W * C.H;
+  // Coverage.  With every vertex in front of the camera the ray of a pixel
+  // meets the triangle iff the pixel centre lies in the projected triangle:
+  // vertices are projected and snapped to 1/4096 pixel (per vertex, the same
+  // bits in every triangle that uses it) and the 2D edge functions are
+  // evaluated exactly in 64-bit integers, so shared edges and vertices leave
+  // no gap.  Pixel centres sit on integer coordinates.
+  long long X[3], Y[3];
+  bool fixed_point = zmin > 0.5f * C.zn;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    if (!fixed_point) break;
+    const float iz = __fdiv_rn(1.f, y[k].z);
+    const float uc = __fmaf_rn(C.fx, __fmul_rn(y[k].x, iz), C.cx - 0.5f);
+    const float vc = __fmaf_rn(C.fy, __fmul_rn(y[k].y, iz), C.cy - 0.5f);
+    if (!(fabsf(uc) < kMaxProj && fabsf(vc) < kMaxProj)) fixed_point = false;
+    X[k] = __float2ll_rn(__fmul_rn(uc, (float)kSub));
+    Y[k] = __float2ll_rn(__fmul_rn(vc, (float)kSub));
+  }
+  if (fixed_point) {
+    const long long xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
+    const long long ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
+    // pixels with centres inside the bounding box (ceil / floor of the scaled range)
+    const long long u0 = max(0LL, -((-xmin) >> kSubBits)), u1 = min((long long)C.W - 1, xmax >> kSubBits);
+    const long long v0 = max(0LL, -((-ymin) >> kSubBits)), v1 = min((long long)C.H - 1, ymax >> kSubBits);
+    const long long area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    if (area == 0 || u0 > u1 || v0 > v1) return;   // seen edge-on, or between pixel centres
+    for (long long v = v0; v <= v1; v++) {
+      const long long py = v << kSubBits;
+      const float dy = ray_dy((int)v, C);
+      for (long long u = u0; u <= u1; u++) {
+        const long long px = u << kSubBits;
+        const long long E0 = (X[2] - X[1]) * (py - Y[1]) - (Y[2] - Y[1]) * (px - X[1]);
+        const long long E1 = (X[0] - X[2]) * (py - Y[2]) - (Y[0] - Y[2]) * (px - X[2]);
+        const long long E2 = (X[1] - X[0]) * (py - Y[0]) - (Y[1] - Y[0]) * (px - X[0]);
+        const bool in = (E0 >= 0 && E1 >= 0 && E2 >= 0) || (E0 <= 0 && E1 <= 0 && E2 <= 0);
+        if (!in) continue;
+        const float dx = ray_dx((int)u, C);
+        const float nd = n.x * dx + n.y * dy + n.z;
+        if (nd == 0.f) continue;
+        const float depth = num / nd;
+        if (!(depth >= C.zn && depth <= C.zf)) continue;
+        atomicMin(ke + (size_t)v * C.W + u, ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f);
+      }
+    }
+    return;
+  }
+  // A triangle reaching behind the camera (or projecting absurdly far): the
+  // 3D test over the whole image, d inside the cone of the three vertices
+  // (edge normals formed in ascending vertex order, so shared edges agree).
   float3 ce[3];
   float sg[3];
 #pragma unroll
@@ -98,33 +158,9 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
     if (vi[a] < vi[b]) { ce[k] = cross_rn(y[a], y[b]); sg[k] = 1.f; }
     else { ce[k] = cross_rn(y[b], y[a]); sg[k] = -1.f; }
   }
-  // supporting plane n.x = n.y0 (edge vectors are short and accurate)
-  const float3 e1 = make_float3(y[1].x - y[0].x, y[1].y - y[0].y, y[1].z - y[0].z);
-  const float3 e2 = make_float3(y[2].x - y[0].x, y[2].y - y[0].y, y[2].z - y[0].z);
-  const float3 n = make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
-  const float num = n.x * y[0].x + n.y * y[0].y + n.z * y[0].z;
-  // pixels whose centres the projection may cover, one pixel of slack each
-  // way; a triangle reaching behind the camera takes the whole image
-  int u0 = 0, u1 = C.W - 1, v0 = 0, v1 = C.H - 1;
-  if (zmin > 0.5f * C.zn) {
-    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      const float iz = 1.f / y[k].z;
-      const float uu = C.fx * y[k].x * iz + C.cx, vv = C.fy * y[k].y * iz + C.cy;
-      umin = fminf(umin, uu); umax = fmaxf(umax, uu);
-      vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
-    }
-    if (umax < -1.f || vmax < -1.f || umin > C.W + 1.f || vmin > C.H + 1.f) return;
-    u0 = max(0, (int)floorf(fmaxf(umin - 0.5f, -1.f)));
-    u1 = min(C.W - 1, (int)ceilf(fminf(umax - 0.5f, (float)C.W)));
-    v0 = max(0, (int)floorf(fmaxf(vmin - 0.5f, -1.f)));
-    v1 = min(C.H - 1, (int)ceilf(fminf(vmax - 0.5f, (float)C.H)));
-  }
-  unsigned long long *ke = keys + (size_t)e * C.W * C.H;
-  for (int v = v0; v <= v1; v++) {
+  for (int v = 0; v < C.H; v++) {
     const float dy = ray_dy(v, C);
-    for (int u = u0; u <= u1; u++) {
+    for (int u = 0; u < C.W; u++) {
       const float dx = ray_dx(u, C);
       const float s0 = sg[0] * edge_rn(ce[0], dx, dy);
       const float s1 = sg[1] * edge_rn(ce[1], dx, dy);
