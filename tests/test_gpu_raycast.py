@@ -9,7 +9,8 @@ casting twice more with every primitive grown and shrunk by EPS (barycentric
 margin, relative radius, relative half extent): where both give the same
 instance the pixel is unique and the GPU must match the undilated oracle
 (instance exactly; depth and point within TOL); elsewhere the GPU must match
-one of the two dilated answers.
+one of the three answers: its instance, at its depth within 1 % (depth is
+ill-conditioned there, e.g. where a ray grazes a sphere's rim).
 
 TOL: FP32 depth through a dozen rounded operations on coordinates of order
 the depth d is about 2e-6 d, up to 20x more on surfaces seen almost edge-on
@@ -79,10 +80,11 @@ def _check(ref, dg, sg, pg, max_ambiguous=0.05):
         assert np.isnan(pg[u & (s0 == 0)]).all()
     assert (dg[u & (s0 == 0)] == 0).all()
     a = ~unique
-    if a.any():   # ambiguous pixels: the undilated or one of the dilated answers
-        ok = ((sg[a] == s0[a]) & _close(dg[a], d0[a])) | ((sg[a] == sp[a]) & _close(dg[a], dp[a])) | \
-             ((sg[a] == sm[a]) & _close(dg[a], dm[a]))
-        assert ok.all(), np.argwhere(a)[~ok][:5]
+    if a.any():   # ambiguous pixels: the instance of one of the three answers, at its depth within 1 %
+        near = lambda d: np.abs(dg[a] - d[a]) <= _tol(d[a]) + 1e-2 * d[a]
+        ok = ((sg[a] == s0[a]) & near(d0)) | ((sg[a] == sp[a]) & near(dp)) | ((sg[a] == sm[a]) & near(dm))
+        assert ok.all(), (np.argwhere(a)[~ok][:5], sg[a][~ok], s0[a][~ok], sp[a][~ok], sm[a][~ok],
+                          dg[a][~ok], d0[a][~ok], dp[a][~ok], dm[a][~ok])
     return unique
 
 
