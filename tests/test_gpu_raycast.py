@@ -210,7 +210,8 @@ def test_render_simulation_state(cuda, kind):
     for e in range(sc.n_envs):
         qd = scenes._quat_mul(scenes._quat_axis_angle((0, 0, 1), g.uniform(0, 6.3)),
                               scenes._quat_axis_angle((1, 0, 0), np.pi + g.uniform(-0.3, 0.3)))
-        cams[e] = [*(q[e].mean(0)[:2] + g.uniform(-0.02, 0.02, 2)), 0.35 + g.uniform(0, 0.1), *qd]
+        above = (0.3 if kind == "cloth_grasp" else 0.12) + g.uniform(0, 0.05)   # the mesh fills much of the view
+        cams[e] = [*(q[e].mean(0)[:2] + g.uniform(-0.01, 0.01, 2)), q[e][:, 2].max() + above, *qd]
     W, H = 61, 45
     cam = flash.Camera(W, H, 50.0, 50.0, W / 2, H / 2, 0.05, 5.0)
     dg, sg, pg = (t.cpu().numpy() for t in sim.render(cam, torch.from_numpy(cams.astype(np.float32)).to(cuda)))
@@ -221,7 +222,7 @@ def test_render_simulation_state(cuda, kind):
                              (W, H, 50.0, 50.0, W / 2, H / 2, 0.05, 5.0))
         ref = _oracle(rs, 0)
         _check(ref, dg[e], sg[e], pg[e])
-        assert (ref[0][1] == 1).mean() > 0.05
+        assert (ref[0][1] == 1).mean() > 0.1
 
 
 def test_full_size_towel_sampled(cuda):
