@@ -441,11 +441,11 @@ def run_render(args, rank, world, local):
     peak = peaks.get("hbm_gbs", 6787.2)
     dom = max(prof, key=lambda k: prof[k][0])
     d_ms, d_n = prof[dom]
-    # algorithmic bytes per launch: resolve reads and re-arms the 8-byte key
-    # and writes depth (4), segmentation (1) and the point (12) of every pixel;
-    # the triangle pass reads every vertex once (12) and writes the key of the
+    # algorithmic bytes per launch: resolve reads the 8-byte key and writes
+    # depth (4), segmentation (1) and the point (12) of every pixel; the
+    # triangle pass reads every vertex once (12) and writes the key of the
     # pixels the mesh wins (8)
-    per = {"resolve": 33.0 * W * H * n_envs, "tri": 12.0 * n * n_envs + 8.0 * mesh_px}[dom]
+    per = {"resolve": 25.0 * W * H * n_envs, "tri": 12.0 * n * n_envs + 8.0 * mesh_px}[dom]
     achieved = per * d_n / (d_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "kernel": {"resolve": "k_rc_resolve", "tri": "k_rc_tri"}[dom], "algorithmic_bytes_per_launch": per,

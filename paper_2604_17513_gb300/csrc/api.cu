@@ -949,16 +949,19 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
     }
     FLASH_CUDA_TRY(cudaMalloc(&s->rc_keys, need * sizeof(unsigned long long)));
     s->rc_keys_n = need;
+    s->rc_frame = 0;
     FLASH_CUDA_TRY(cudaMemsetAsync(s->rc_keys, 0xff, need * sizeof(unsigned long long), st));
   }
+  const int odd = s->rc_frame & 1;
   for (const Group &g : s->groups) {
     const RcMesh M{g.q, 3LL * g.n_pad, g.n_pad, 1, g.genv, 0, g.rtris, g.rT};
-    FLASH_CUDA_TRY(rc_launch_tri(M, g.N, cam_poses, C, s->rc_keys, st));
+    FLASH_CUDA_TRY(rc_launch_tri(M, g.N, cam_poses, C, s->rc_keys, odd, st));
     if (g.rT > 0) s->launches++;
   }
   const RcObs O{s->otype, s->odims, s->pose_t, s->K, FLASH_MAX_OBS};
-  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, depth, seg, points, st));
+  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, odd, depth, seg, points, st));
   s->launches++;
+  s->rc_frame ^= 1;
   return FLASH_OK;
 }
 

@@ -156,8 +156,9 @@ struct flash_scene {
   // carrying the anchor (-1 none); anchor xyz and activation radius
   int *gstate = nullptr, *gobs = nullptr, *greq = nullptr;
   float *ganchor = nullptr;   // [N][4]
-  unsigned long long *rc_keys = nullptr;   // ray casting work buffer (all bits set between calls)
+  unsigned long long *rc_keys = nullptr;   // ray casting work buffer
   size_t rc_keys_n = 0;
+  int rc_frame = 0;                        // parity of the next render (key encoding)
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
@@ -247,10 +248,12 @@ struct RcObs {
   const float *dims, *pose;
   int K, stride;
 };
+// keys: per-pixel work buffer; odd: parity of the frame (key encoding)
 cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
-                          unsigned long long *keys, cudaStream_t st);
+                          unsigned long long *keys, int odd, cudaStream_t st);
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              unsigned long long *keys, float *depth, uint8_t *seg, float *pts, cudaStream_t st);
+                              const unsigned long long *keys, int odd, float *depth, uint8_t *seg, float *pts,
+                              cudaStream_t st);
 flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out);
 
 // grasp requests s->greq[first_env, first_env + count) -> per-environment grasp state

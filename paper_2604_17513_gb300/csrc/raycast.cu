@@ -7,12 +7,12 @@
 // covers a few pixels): one thread per (environment, triangle) transforms its
 // three vertices into the camera frame, walks the pixels of its projected
 // bounding box, tests each pixel's ray exactly and keeps the nearest hit per
-// pixel with a 64-bit atomicMin of (depth bits, triangle index): the result
+// pixel with a 64-bit atomic min of (depth bits, triangle index): the result
 // is the nearest triangle hit of every pixel, the same answer as a ray-first
 // traversal, without building or refitting an acceleration structure for
 // the per-step geometry.  A second pass per pixel intersects the analytic
 // obstacles, picks the nearest surface and writes depth, instance and the
-// world point, and leaves the per-pixel keys empty for the next frame.
+// world point.
 //
 // Watertight coverage: for a triangle in front of the camera, a pixel's ray
 // meets it iff the pixel centre lies in its projection; projections are
@@ -33,7 +33,18 @@ namespace flash {
 
 namespace {
 
-constexpr unsigned long long kEmpty = ~0ull;
+// Per-pixel keys need no clearing between frames: even frames keep the
+// minimum of (depth bits << 32 | triangle) with atomicMin, odd frames the
+// maximum of its complement with atomicMax.  A key's top bit is 0 for an
+// even-frame hit (depth > 0 has a clear sign bit) and 1 for an odd-frame
+// hit, so whatever the previous frame left behind loses to any hit of the
+// current frame and reads as "no hit" when nothing replaced it.  A new
+// buffer is all ones (empty for frame 0).
+__device__ __forceinline__ void store_key(unsigned long long *k, float depth, int f, int odd) {
+  const unsigned long long key = ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f;
+  if (odd) atomicMax(k, ~key);
+  else atomicMin(k, key);
+}
 // fixed-point image coordinates: 1/4096 pixel; projections beyond 2^17
 // pixels take the 3D path, so every edge-function product fits in 62 bits
 constexpr int kSubBits = 12;
@@ -62,7 +73,7 @@ __device__ __forceinline__ float ray_dx(int u, const RcCam &C) { return __fdiv_r
 __device__ __forceinline__ float ray_dy(int v, const RcCam &C) { return __fdiv_rn(__fadd_rn(v + 0.5f, -C.cy), C.fy); }
 
 __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restrict__ cam_poses, RcCam C,
-                                                unsigned long long *__restrict__ keys) {
+                                                unsigned long long *__restrict__ keys, int odd) {
   __shared__ float sR[9], sp[3];
   const int l = blockIdx.y;
   const int e = M.genv ? M.genv[l] : M.first_env + l;
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
         if (nd == 0.f) continue;
         const float depth = num / nd;
         if (!(depth >= C.zn && depth <= C.zf)) continue;
-        atomicMin(ke + (size_t)v * C.W + u, ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f);
+        store_key(ke + (size_t)v * C.W + u, depth, f, odd);
       }
     }
     return;
@@ -171,49 +182,51 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
       if (nd == 0.f) continue;
       const float depth = num / nd;
       if (!(depth >= C.zn && depth <= C.zf)) continue;
-      atomicMin(ke + (size_t)v * C.W + u, ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f);
+      store_key(ke + (size_t)v * C.W + u, depth, f, odd);
     }
   }
 }
 
-// nearest hit t >= zn of ray o + t d with an analytic obstacle (INFINITY: none)
-__device__ float ray_obstacle(int type, const float *dims, const float *R, const float *p, float3 o, float3 d,
-                              float zn) {
-  if (type == FLASH_OBS_PLANE) {
-    const float3 nn = make_float3(R[2], R[5], R[8]);   // body +z in world axes
-    const float dn = nn.x * d.x + nn.y * d.y + nn.z * d.z;
-    if (dn == 0.f) return INFINITY;
-    const float t = (nn.x * (p[0] - o.x) + nn.y * (p[1] - o.y) + nn.z * (p[2] - o.z)) / dn;
-    return t >= zn ? t : INFINITY;
+// Obstacles in the frame of one camera: what every pixel's test shares.
+struct ObsRay {
+  int type;
+  float a[3];   // plane: world normal; sphere: centre - camera; box: camera in box axes
+  float b;      // plane: n.(p - o); sphere: r^2
+  float R[9];   // box: rotation body -> world (rows), so R^T d is the ray in box axes
+  float h[3];   // box: half extents
+};
+
+// nearest hit t >= zn of the ray o + t d with an obstacle (INFINITY: none)
+__device__ __forceinline__ float ray_obstacle(const ObsRay &Q, float3 d, float zn) {
+  if (Q.type == FLASH_OBS_PLANE) {
+    const float dn = Q.a[0] * d.x + Q.a[1] * d.y + Q.a[2] * d.z;
+    const float t = __fdividef(Q.b, dn);
+    return (dn != 0.f && t >= zn) ? t : INFINITY;
   }
-  if (type == FLASH_OBS_SPHERE) {
+  if (Q.type == FLASH_OBS_SPHERE) {
     // closest approach along the unit direction, then the chord: no
     // cancellation between |c - o|^2 and r^2 near the silhouette
-    const float r = dims[0];
-    const float dl = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    const float3 u = make_float3(d.x / dl, d.y / dl, d.z / dl);
-    const float3 co = make_float3(p[0] - o.x, p[1] - o.y, p[2] - o.z);
-    const float tc = u.x * co.x + u.y * co.y + u.z * co.z;
-    const float3 q = make_float3(co.x - tc * u.x, co.y - tc * u.y, co.z - tc * u.z);
+    const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    const float3 u = make_float3(d.x * il, d.y * il, d.z * il);
+    const float tc = u.x * Q.a[0] + u.y * Q.a[1] + u.z * Q.a[2];
+    const float3 q = make_float3(Q.a[0] - tc * u.x, Q.a[1] - tc * u.y, Q.a[2] - tc * u.z);
     const float h2 = q.x * q.x + q.y * q.y + q.z * q.z;
-    if (h2 > r * r) return INFINITY;
-    const float s = sqrtf(r * r - h2);
-    const float t1 = (tc - s) / dl, t2 = (tc + s) / dl;
+    if (h2 > Q.b) return INFINITY;
+    const float sq = sqrtf(Q.b - h2);
+    const float t1 = (tc - sq) * il, t2 = (tc + sq) * il;
     return t1 >= zn ? t1 : (t2 >= zn ? t2 : INFINITY);
   }
-  if (type == FLASH_OBS_BOX) {
-    const float w[3] = {o.x - p[0], o.y - p[1], o.z - p[2]};
-    const float dw[3] = {d.x, d.y, d.z};
+  if (Q.type == FLASH_OBS_BOX) {
     float tmin = -INFINITY, tmax = INFINITY;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-      const float ob = R[i] * w[0] + R[3 + i] * w[1] + R[6 + i] * w[2];
-      const float db = R[i] * dw[0] + R[3 + i] * dw[1] + R[6 + i] * dw[2];
+      const float db = Q.R[i] * d.x + Q.R[3 + i] * d.y + Q.R[6 + i] * d.z;
       if (db == 0.f) {
-        if (fabsf(ob) > dims[i]) return INFINITY;
+        if (fabsf(Q.a[i]) > Q.h[i]) return INFINITY;
         continue;
       }
-      float ta = (-dims[i] - ob) / db, tb = (dims[i] - ob) / db;
+      const float inv = __frcp_rn(db);
+      float ta = (-Q.h[i] - Q.a[i]) * inv, tb = (Q.h[i] - Q.a[i]) * inv;
       if (ta > tb) { const float x = ta; ta = tb; tb = x; }
       tmin = fmaxf(tmin, ta);
       tmax = fminf(tmax, tb);
@@ -225,47 +238,59 @@ __device__ float ray_obstacle(int type, const float *dims, const float *R, const
 }
 
 __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__restrict__ cam_poses, RcCam C,
-                                                    int first_env, unsigned long long *__restrict__ keys,
-                                                    float *__restrict__ depth, uint8_t *__restrict__ seg,
+                                                    int first_env, const unsigned long long *__restrict__ keys,
+                                                    int odd, float *__restrict__ depth, uint8_t *__restrict__ seg,
                                                     float *__restrict__ pts) {
-  __shared__ float sRc[9], spc[3];
-  __shared__ int otype[FLASH_MAX_OBS];
-  __shared__ float odims[FLASH_MAX_OBS][3], oR[FLASH_MAX_OBS][9], op[FLASH_MAX_OBS][3];
+  __shared__ float sRc[9], spc[3], sif[2];
+  __shared__ ObsRay sq[FLASH_MAX_OBS];
   const int e = first_env + blockIdx.y;
   if (threadIdx.x == 0) {
     const float *cp = cam_poses + 7 * (size_t)e;
     rc_quat_mat(cp + 3, sRc);
     spc[0] = cp[0]; spc[1] = cp[1]; spc[2] = cp[2];
+    sif[0] = 1.f / C.fx;
+    sif[1] = 1.f / C.fy;
   }
   if (threadIdx.x < O.K) {
     const int k = threadIdx.x;
     const size_t b = (size_t)e * O.stride + k;
-    otype[k] = O.type[b];
-    for (int c = 0; c < 3; c++) odims[k][c] = O.dims[3 * b + c];
-    rc_quat_mat(O.pose + 7 * b + 3, oR[k]);
-    for (int c = 0; c < 3; c++) op[k][c] = O.pose[7 * b + c];
+    const float *cp = cam_poses + 7 * (size_t)e, *pose = O.pose + 7 * b, *dims = O.dims + 3 * b;
+    ObsRay &Q = sq[k];
+    Q.type = O.type[b];
+    float R[9];
+    rc_quat_mat(pose + 3, R);
+    const float w[3] = {pose[0] - cp[0], pose[1] - cp[1], pose[2] - cp[2]};   // obstacle origin - camera
+    if (Q.type == FLASH_OBS_PLANE) {
+      Q.a[0] = R[2]; Q.a[1] = R[5]; Q.a[2] = R[8];
+      Q.b = R[2] * w[0] + R[5] * w[1] + R[8] * w[2];
+    } else if (Q.type == FLASH_OBS_SPHERE) {
+      Q.a[0] = w[0]; Q.a[1] = w[1]; Q.a[2] = w[2];
+      Q.b = dims[0] * dims[0];
+    } else {
+      for (int i = 0; i < 3; i++) Q.a[i] = -(R[i] * w[0] + R[3 + i] * w[1] + R[6 + i] * w[2]);
+      for (int i = 0; i < 9; i++) Q.R[i] = R[i];
+      for (int i = 0; i < 3; i++) Q.h[i] = dims[i];
+    }
   }
   __syncthreads();
   const int WH = C.W * C.H;
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= WH) return;
   const int v = pix / C.W, u = pix - v * C.W;
-  const float dx = ray_dx(u, C), dy = ray_dy(v, C);
+  const float dx = (u + 0.5f - C.cx) * sif[0], dy = (v + 0.5f - C.cy) * sif[1];
   const float3 d = make_float3(sRc[0] * dx + sRc[1] * dy + sRc[2], sRc[3] * dx + sRc[4] * dy + sRc[5],
                                sRc[6] * dx + sRc[7] * dy + sRc[8]);
-  const float3 o = make_float3(spc[0], spc[1], spc[2]);
   const size_t pe = (size_t)e * WH + pix;
-  const unsigned long long key = keys[pe];
-  keys[pe] = kEmpty;   // ready for the next frame
+  unsigned long long key = keys[pe];
   float best = INFINITY;
   int inst = 0;
-  if (key != kEmpty) {
+  if ((key >> 63) == (unsigned long long)odd) {   // a hit of this frame
+    if (odd) key = ~key;
     best = __uint_as_float((unsigned)(key >> 32));
     inst = 1;
   }
   for (int k = 0; k < O.K; k++) {   // ties keep the smaller instance
-    if (otype[k] == FLASH_OBS_NONE) continue;
-    const float t = ray_obstacle(otype[k], odims[k], oR[k], op[k], o, d, C.zn);
+    const float t = ray_obstacle(sq[k], d, C.zn);
     if (t <= C.zf && t < best) {
       best = t;
       inst = 2 + k;
@@ -275,26 +300,28 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
   if (seg) seg[pe] = (uint8_t)inst;
   if (pts) {
     const float nan = __int_as_float(0x7fc00000);
-    pts[3 * pe] = inst ? o.x + best * d.x : nan;
-    pts[3 * pe + 1] = inst ? o.y + best * d.y : nan;
-    pts[3 * pe + 2] = inst ? o.z + best * d.z : nan;
+    pts[3 * pe] = inst ? spc[0] + best * d.x : nan;
+    pts[3 * pe + 1] = inst ? spc[1] + best * d.y : nan;
+    pts[3 * pe + 2] = inst ? spc[2] + best * d.z : nan;
   }
 }
 
 }  // namespace
 
 cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
-                          unsigned long long *keys, cudaStream_t st) {
+                          unsigned long long *keys, int odd, cudaStream_t st) {
   if (M.T <= 0 || n_envs <= 0) return cudaSuccess;
-  k_rc_tri<<<dim3((M.T + 255) / 256, n_envs), 256, 0, st>>>(M, cam_poses, C, keys);
+  k_rc_tri<<<dim3((M.T + 255) / 256, n_envs), 256, 0, st>>>(M, cam_poses, C, keys, odd);
   return cudaGetLastError();
 }
 
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              unsigned long long *keys, float *depth, uint8_t *seg, float *pts, cudaStream_t st) {
+                              const unsigned long long *keys, int odd, float *depth, uint8_t *seg, float *pts,
+                              cudaStream_t st) {
   if (n_envs <= 0) return cudaSuccess;
   const int WH = C.W * C.H;
-  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, depth, seg, pts);
+  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, odd, depth, seg,
+                                                               pts);
   return cudaGetLastError();
 }
 
@@ -323,6 +350,7 @@ struct flash_raycaster {
   int N = 0, n = 0, T = 0;
   int3 *tris = nullptr;
   unsigned long long *keys = nullptr;
+  int frame = 0;   // parity of the next cast (key encoding)
   // per-kernel device time while profiling (0: triangles, 1: resolve)
   bool profiling = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -386,10 +414,12 @@ flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_ob
   const bool prof = rc->profiling;
   if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[0], st));
   flash::RcMesh M{verts, 3LL * rc->n, 1, 3, nullptr, 0, rc->tris, rc->T};
-  FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, st));
+  const int odd = rc->frame & 1;
+  FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, odd, st));
   if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[1], st));
   flash::RcObs O{obs_type, obs_dims, obs_poses, n_obs, n_obs};
-  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, depth, seg, points, st));
+  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, odd, depth, seg, points, st));
+  rc->frame ^= 1;
   if (prof) {
     FLASH_CUDA_TRY(cudaEventRecord(rc->ev[2], st));
     FLASH_CUDA_TRY(cudaEventSynchronize(rc->ev[2]));

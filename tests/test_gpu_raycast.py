@@ -173,6 +173,31 @@ def test_edge_cases(cuda):
         _check(_oracle(one, e), dg4[e], sg4[e], pg4[e], max_ambiguous=1.0)
 
 
+def test_consecutive_casts_are_independent(cuda):
+    """One ray caster used for several frames (the per-pixel keys are reused
+    without clearing, their encoding alternating between frames): every frame
+    equals a fresh cast of its own geometry, whether pixels gain or lose the
+    mesh between frames."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    rs = scenes.towel_views(n_envs=2, n_side=24, side=0.3, width=64, height=48, cam_height=(0.32, 0.4))
+    lifted = rs.verts.copy()
+    lifted[:, :, 2] += 0.05
+    moved = rs.verts.copy()
+    moved[:, :, 0] += 0.2        # the towel leaves part of the view
+    W, H, fx, fy, cx, cy, zn, zf = rs.cam
+    cam = flash.Camera(W, H, fx, fy, cx, cy, zn, zf)
+    t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt, device=cuda)
+    obs = (t(rs.obs_type, torch.int32), t(rs.obs_dims), t(rs.obs_poses))
+    rc = flash.Raycaster(cam, rs.n_envs, rs.verts.shape[1], rs.tris)
+    for frame, v in enumerate([rs.verts, moved, lifted, rs.verts, moved]):
+        got = [o.cpu().numpy() for o in rc.cast(t(v), *obs, t(rs.cam_poses))]
+        fresh = flash.Raycaster(cam, rs.n_envs, rs.verts.shape[1], rs.tris)
+        ref = [o.cpu().numpy() for o in fresh.cast(t(v), *obs, t(rs.cam_poses))]
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), frame
+        assert np.array_equal(np.nan_to_num(got[2], nan=-1), np.nan_to_num(ref[2], nan=-1)), frame
+
+
 def _boundary_faces(tets):
     """Faces of a tetrahedral mesh that belong to one tetrahedron only."""
     faces = np.concatenate([tets[:, [1, 2, 3]], tets[:, [0, 2, 3]], tets[:, [0, 1, 3]], tets[:, [0, 1, 2]]])
