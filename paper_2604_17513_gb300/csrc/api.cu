@@ -210,6 +210,7 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
         }
     }
     g.rT = (int)(rt.size() / 3);
+    if (g.rT > kMaxRcTris) return fail(FLASH_EINVAL, "mesh has too many surface triangles for ray casting");
     if (g.rT > 0) {
       int *d = nullptr;
       FLASH_CUDA_TRY(upload(s, &d, rt));
@@ -949,19 +950,19 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
     }
     FLASH_CUDA_TRY(cudaMalloc(&s->rc_keys, need * sizeof(unsigned long long)));
     s->rc_keys_n = need;
-    s->rc_frame = 0;
-    FLASH_CUDA_TRY(cudaMemsetAsync(s->rc_keys, 0xff, need * sizeof(unsigned long long), st));
+    s->rc_tag = -1;   // the first render fills the buffer
   }
-  const int odd = s->rc_frame & 1;
+  FLASH_CUDA_TRY(rc_next_tag(s->rc_keys, s->rc_keys_n, &s->rc_tag, st));
+  const unsigned tag = (unsigned)s->rc_tag;
   for (const Group &g : s->groups) {
     const RcMesh M{g.q, 3LL * g.n_pad, g.n_pad, 1, g.genv, 0, g.rtris, g.rT};
-    FLASH_CUDA_TRY(rc_launch_tri(M, g.N, cam_poses, C, s->rc_keys, odd, st));
+    FLASH_CUDA_TRY(rc_launch_tri(M, g.N, cam_poses, C, s->rc_keys, tag, st));
     if (g.rT > 0) s->launches++;
   }
   const RcObs O{s->otype, s->odims, s->pose_t, s->K, FLASH_MAX_OBS};
-  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, odd, depth, seg, points, st));
+  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, tag, depth, seg, points, st));
   s->launches++;
-  s->rc_frame ^= 1;
+  s->rc_tag--;
   return FLASH_OK;
 }
 

@@ -158,7 +158,7 @@ struct flash_scene {
   float *ganchor = nullptr;   // [N][4]
   unsigned long long *rc_keys = nullptr;   // ray casting work buffer
   size_t rc_keys_n = 0;
-  int rc_frame = 0;                        // parity of the next render (key encoding)
+  int rc_tag = 0;                          // frame tag of the next render
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
@@ -248,11 +248,15 @@ struct RcObs {
   const float *dims, *pose;
   int K, stride;
 };
-// keys: per-pixel work buffer; odd: parity of the frame (key encoding)
+// keys: per-pixel work buffer; tag: the frame's tag (kFirstTag down to 0,
+// then rc_next_tag refills the buffer); triangles per mesh < kMaxRcTris
+constexpr int kFirstTag = 254;
+constexpr int kMaxRcTris = (1 << 25) - 1;
+cudaError_t rc_next_tag(unsigned long long *keys, size_t n_keys, int *tag, cudaStream_t st);
 cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
-                          unsigned long long *keys, int odd, cudaStream_t st);
+                          unsigned long long *keys, unsigned tag, cudaStream_t st);
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              const unsigned long long *keys, int odd, float *depth, uint8_t *seg, float *pts,
+                              const unsigned long long *keys, unsigned tag, float *depth, uint8_t *seg, float *pts,
                               cudaStream_t st);
 flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out);
 

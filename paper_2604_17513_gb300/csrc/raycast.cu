@@ -33,17 +33,17 @@ namespace flash {
 
 namespace {
 
-// Per-pixel keys need no clearing between frames: even frames keep the
-// minimum of (depth bits << 32 | triangle) with atomicMin, odd frames the
-// maximum of its complement with atomicMax.  A key's top bit is 0 for an
-// even-frame hit (depth > 0 has a clear sign bit) and 1 for an odd-frame
-// hit, so whatever the previous frame left behind loses to any hit of the
-// current frame and reads as "no hit" when nothing replaced it.  A new
-// buffer is all ones (empty for frame 0).
-__device__ __forceinline__ void store_key(unsigned long long *k, float depth, int f, int odd) {
-  const unsigned long long key = ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned)f;
-  if (odd) atomicMax(k, ~key);
-  else atomicMin(k, key);
+// Per-pixel keys are not cleared between frames.  A key packs an 8-bit frame
+// tag, the depth's bits without the sign (depth > 0) and the triangle index:
+// tag << 56 | depth_bits << 25 | triangle.  Frames count their tag down
+// (254, 253, ..., 0), so with atomicMin any hit of the current frame beats
+// whatever an older frame left, and the resolve pass reads a key as a hit
+// only when its tag is the current one.  After tag 0 the buffer is refilled
+// with all ones (tag 255: never current) and the count restarts at 254.
+__device__ __forceinline__ void store_key(unsigned long long *k, float depth, int f, unsigned tag) {
+  const unsigned long long key = ((unsigned long long)tag << 56) |
+                                 ((unsigned long long)(__float_as_uint(depth) & 0x7fffffffu) << 25) | (unsigned)f;
+  atomicMin(k, key);
 }
 // fixed-point image coordinates: 1/4096 pixel; projections beyond 2^17
 // pixels take the 3D path, so every edge-function product fits in 62 bits
@@ -73,7 +73,7 @@ __device__ __forceinline__ float ray_dx(int u, const RcCam &C) { return __fdiv_r
 __device__ __forceinline__ float ray_dy(int v, const RcCam &C) { return __fdiv_rn(__fadd_rn(v + 0.5f, -C.cy), C.fy); }
 
 __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restrict__ cam_poses, RcCam C,
-                                                unsigned long long *__restrict__ keys, int odd) {
+                                                unsigned long long *__restrict__ keys, unsigned tag) {
   __shared__ float sR[9], sp[3];
   const int l = blockIdx.y;
   const int e = M.genv ? M.genv[l] : M.first_env + l;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
         if (nd == 0.f) continue;
         const float depth = num / nd;
         if (!(depth >= C.zn && depth <= C.zf)) continue;
-        store_key(ke + (size_t)v * C.W + u, depth, f, odd);
+        store_key(ke + (size_t)v * C.W + u, depth, f, tag);
       }
     }
     return;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
       if (nd == 0.f) continue;
       const float depth = num / nd;
       if (!(depth >= C.zn && depth <= C.zf)) continue;
-      store_key(ke + (size_t)v * C.W + u, depth, f, odd);
+      store_key(ke + (size_t)v * C.W + u, depth, f, tag);
     }
   }
 }
@@ -239,7 +239,7 @@ __device__ __forceinline__ float ray_obstacle(const ObsRay &Q, float3 d, float z
 
 __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__restrict__ cam_poses, RcCam C,
                                                     int first_env, const unsigned long long *__restrict__ keys,
-                                                    int odd, float *__restrict__ depth, uint8_t *__restrict__ seg,
+                                                    unsigned tag, float *__restrict__ depth, uint8_t *__restrict__ seg,
                                                     float *__restrict__ pts) {
   __shared__ float sRc[9], spc[3], sif[2];
   __shared__ ObsRay sq[FLASH_MAX_OBS];
@@ -281,12 +281,11 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
   const float3 d = make_float3(sRc[0] * dx + sRc[1] * dy + sRc[2], sRc[3] * dx + sRc[4] * dy + sRc[5],
                                sRc[6] * dx + sRc[7] * dy + sRc[8]);
   const size_t pe = (size_t)e * WH + pix;
-  unsigned long long key = keys[pe];
+  const unsigned long long key = keys[pe];
   float best = INFINITY;
   int inst = 0;
-  if ((key >> 63) == (unsigned long long)odd) {   // a hit of this frame
-    if (odd) key = ~key;
-    best = __uint_as_float((unsigned)(key >> 32));
+  if ((unsigned)(key >> 56) == tag) {   // a hit of this frame
+    best = __uint_as_float((unsigned)(key >> 25) & 0x7fffffffu);
     inst = 1;
   }
   for (int k = 0; k < O.K; k++) {   // ties keep the smaller instance
@@ -309,20 +308,29 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
 }  // namespace
 
 cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
-                          unsigned long long *keys, int odd, cudaStream_t st) {
+                          unsigned long long *keys, unsigned tag, cudaStream_t st) {
   if (M.T <= 0 || n_envs <= 0) return cudaSuccess;
-  k_rc_tri<<<dim3((M.T + 255) / 256, n_envs), 256, 0, st>>>(M, cam_poses, C, keys, odd);
+  k_rc_tri<<<dim3((M.T + 255) / 256, n_envs), 256, 0, st>>>(M, cam_poses, C, keys, tag);
   return cudaGetLastError();
 }
 
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              const unsigned long long *keys, int odd, float *depth, uint8_t *seg, float *pts,
+                              const unsigned long long *keys, unsigned tag, float *depth, uint8_t *seg, float *pts,
                               cudaStream_t st) {
   if (n_envs <= 0) return cudaSuccess;
   const int WH = C.W * C.H;
-  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, odd, depth, seg,
+  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, tag, depth, seg,
                                                                pts);
   return cudaGetLastError();
+}
+
+cudaError_t rc_next_tag(unsigned long long *keys, size_t n_keys, int *tag, cudaStream_t st) {
+  if (*tag < 0) {   // tags used up: refill with all ones (tag 255) and restart
+    const cudaError_t e = cudaMemsetAsync(keys, 0xff, n_keys * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    *tag = kFirstTag;
+  }
+  return cudaSuccess;
 }
 
 flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out) {
@@ -350,7 +358,7 @@ struct flash_raycaster {
   int N = 0, n = 0, T = 0;
   int3 *tris = nullptr;
   unsigned long long *keys = nullptr;
-  int frame = 0;   // parity of the next cast (key encoding)
+  int tag = flash::kFirstTag;   // frame tag of the next cast
   // per-kernel device time while profiling (0: triangles, 1: resolve)
   bool profiling = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -364,8 +372,9 @@ flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int
                                     const int32_t *tris, flash_raycaster **out) {
   if (!out) { set_error("out is NULL"); return FLASH_EINVAL; }
   *out = nullptr;
-  if (n_envs < 1 || n_envs > 65535 || n_verts < 0 || n_tris < 0 || (n_tris > 0 && !tris)) {
-    set_error("invalid ray caster sizes (1 <= n_envs <= 65535, n_verts, n_tris >= 0)");
+  if (n_envs < 1 || n_envs > 65535 || n_verts < 0 || n_tris < 0 || n_tris > flash::kMaxRcTris ||
+      (n_tris > 0 && !tris)) {
+    set_error("invalid ray caster sizes (1 <= n_envs <= 65535, n_verts >= 0, 0 <= n_tris < 2^25)");
     return FLASH_EINVAL;
   }
   flash::RcCam C;
@@ -414,12 +423,13 @@ flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_ob
   const bool prof = rc->profiling;
   if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[0], st));
   flash::RcMesh M{verts, 3LL * rc->n, 1, 3, nullptr, 0, rc->tris, rc->T};
-  const int odd = rc->frame & 1;
-  FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, odd, st));
+  FLASH_CUDA_TRY(flash::rc_next_tag(rc->keys, (size_t)rc->N * rc->cam.W * rc->cam.H, &rc->tag, st));
+  const unsigned tag = (unsigned)rc->tag;
+  FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, tag, st));
   if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[1], st));
   flash::RcObs O{obs_type, obs_dims, obs_poses, n_obs, n_obs};
-  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, odd, depth, seg, points, st));
-  rc->frame ^= 1;
+  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, tag, depth, seg, points, st));
+  rc->tag--;
   if (prof) {
     FLASH_CUDA_TRY(cudaEventRecord(rc->ev[2], st));
     FLASH_CUDA_TRY(cudaEventSynchronize(rc->ev[2]));

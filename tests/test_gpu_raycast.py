@@ -174,10 +174,10 @@ def test_edge_cases(cuda):
 
 
 def test_consecutive_casts_are_independent(cuda):
-    """One ray caster used for several frames (the per-pixel keys are reused
-    without clearing, their encoding alternating between frames): every frame
-    equals a fresh cast of its own geometry, whether pixels gain or lose the
-    mesh between frames."""
+    """One ray caster used for 260 frames (the per-pixel keys are reused
+    without clearing, tagged by frame, the buffer refilled after 255 frames):
+    every checked frame equals a fresh cast of its own geometry, whether
+    pixels gain or lose the mesh between frames."""
     import torch
     from paper_2604_17513_gb300 import flash
     rs = scenes.towel_views(n_envs=2, n_side=24, side=0.3, width=64, height=48, cam_height=(0.32, 0.4))
@@ -190,12 +190,21 @@ def test_consecutive_casts_are_independent(cuda):
     t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt, device=cuda)
     obs = (t(rs.obs_type, torch.int32), t(rs.obs_dims), t(rs.obs_poses))
     rc = flash.Raycaster(cam, rs.n_envs, rs.verts.shape[1], rs.tris)
-    for frame, v in enumerate([rs.verts, moved, lifted, rs.verts, moved]):
-        got = [o.cpu().numpy() for o in rc.cast(t(v), *obs, t(rs.cam_poses))]
+    geoms = [t(rs.verts), t(moved), t(lifted)]
+    refs = []
+    for v in geoms:
         fresh = flash.Raycaster(cam, rs.n_envs, rs.verts.shape[1], rs.tris)
-        ref = [o.cpu().numpy() for o in fresh.cast(t(v), *obs, t(rs.cam_poses))]
-        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), frame
-        assert np.array_equal(np.nan_to_num(got[2], nan=-1), np.nan_to_num(ref[2], nan=-1)), frame
+        refs.append([o.cpu().numpy() for o in fresh.cast(v, *obs, t(rs.cam_poses))])
+    checked = {0, 1, 2, 3, 4, 253, 254, 255, 256, 257, 259}
+    for frame in range(260):
+        g = (frame * 7 + frame // 3) % 3
+        out = rc.cast(geoms[g], *obs, t(rs.cam_poses))
+        if frame in checked:
+            got = [o.cpu().numpy() for o in out]
+            ref = refs[g]
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), frame
+            assert np.array_equal(np.nan_to_num(got[2], nan=-1), np.nan_to_num(ref[2], nan=-1)), frame
+    assert len({(f * 7 + f // 3) % 3 for f in checked}) == 3
 
 
 def _boundary_faces(tets):
