@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     if (!fixed_point) break;
-    const float iz = __fdiv_rn(1.f, y[k].z);
+    const float iz = __fdividef(1.f, y[k].z);
     const float uc = __fmaf_rn(C.fx, __fmul_rn(y[k].x, iz), C.cx - 0.5f);
     const float vc = __fmaf_rn(C.fy, __fmul_rn(y[k].y, iz), C.cy - 0.5f);
     if (!(fabsf(uc) < kMaxProj && fabsf(vc) < kMaxProj)) fixed_point = false;
@@ -138,20 +138,22 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
     const long long v0 = max(0LL, -((-ymin) >> kSubBits)), v1 = min((long long)C.H - 1, ymax >> kSubBits);
     const long long area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
     if (area == 0 || u0 > u1 || v0 > v1) return;   // seen edge-on, or between pixel centres
+    // edge functions at the row's first pixel, then stepped exactly by
+    // their (integer) change per pixel
+    const long long s0 = (Y[1] - Y[2]) * kSub, s1 = (Y[2] - Y[0]) * kSub, s2 = (Y[0] - Y[1]) * kSub;
+    const float ifx = 1.f / C.fx, ify = 1.f / C.fy;
     for (long long v = v0; v <= v1; v++) {
-      const long long py = v << kSubBits;
-      const float dy = ray_dy((int)v, C);
-      for (long long u = u0; u <= u1; u++) {
-        const long long px = u << kSubBits;
-        const long long E0 = (X[2] - X[1]) * (py - Y[1]) - (Y[2] - Y[1]) * (px - X[1]);
-        const long long E1 = (X[0] - X[2]) * (py - Y[2]) - (Y[0] - Y[2]) * (px - X[2]);
-        const long long E2 = (X[1] - X[0]) * (py - Y[0]) - (Y[1] - Y[0]) * (px - X[0]);
+      const long long py = v * kSub, px = u0 * kSub;
+      long long E0 = (X[2] - X[1]) * (py - Y[1]) - (Y[2] - Y[1]) * (px - X[1]);
+      long long E1 = (X[0] - X[2]) * (py - Y[2]) - (Y[0] - Y[2]) * (px - X[2]);
+      long long E2 = (X[1] - X[0]) * (py - Y[0]) - (Y[1] - Y[0]) * (px - X[0]);
+      const float rowc = n.y * ((v + 0.5f - C.cy) * ify) + n.z;
+      for (long long u = u0; u <= u1; u++, E0 += s0, E1 += s1, E2 += s2) {
         const bool in = (E0 >= 0 && E1 >= 0 && E2 >= 0) || (E0 <= 0 && E1 <= 0 && E2 <= 0);
         if (!in) continue;
-        const float dx = ray_dx((int)u, C);
-        const float nd = n.x * dx + n.y * dy + n.z;
+        const float nd = n.x * ((u + 0.5f - C.cx) * ifx) + rowc;
         if (nd == 0.f) continue;
-        const float depth = num / nd;
+        const float depth = __fdividef(num, nd);
         if (!(depth >= C.zn && depth <= C.zf)) continue;
         store_key(ke + (size_t)v * C.W + u, depth, f, tag);
       }
@@ -243,7 +245,9 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
                                                     float *__restrict__ pts) {
   __shared__ float sRc[9], spc[3], sif[2];
   __shared__ ObsRay sq[FLASH_MAX_OBS];
+  __shared__ int sact[FLASH_MAX_OBS];
   const int e = first_env + blockIdx.y;
+  const int WH = C.W * C.H;
   if (threadIdx.x == 0) {
     const float *cp = cam_poses + 7 * (size_t)e;
     rc_quat_mat(cp + 3, sRc);
@@ -271,9 +275,41 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
       for (int i = 0; i < 9; i++) Q.R[i] = R[i];
       for (int i = 0; i < 3; i++) Q.h[i] = dims[i];
     }
+    // Sphere or box whose projection (bounded by the projected corners of
+    // the box, or of the sphere's bounding cube) misses this block's pixel
+    // centres by more than a pixel is skipped for the whole block; a shape
+    // reaching behind the camera is always tested.
+    int act = Q.type != FLASH_OBS_NONE;
+    if (Q.type == FLASH_OBS_SPHERE || Q.type == FLASH_OBS_BOX) {
+      float Rc[9];
+      rc_quat_mat(cp + 3, Rc);
+      const bool sph = Q.type == FLASH_OBS_SPHERE;
+      const float hx = sph ? dims[0] : dims[0], hy = sph ? dims[0] : dims[1], hz = sph ? dims[0] : dims[2];
+      bool front = true;
+      float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+      for (int c = 0; c < 8; c++) {
+        const float bx = (c & 1) ? hx : -hx, by = (c & 2) ? hy : -hy, bz = (c & 4) ? hz : -hz;
+        float x[3];
+        for (int i = 0; i < 3; i++)
+          x[i] = w[i] + (sph ? (i == 0 ? bx : i == 1 ? by : bz) : R[3 * i] * bx + R[3 * i + 1] * by + R[3 * i + 2] * bz);
+        const float yx = Rc[0] * x[0] + Rc[3] * x[1] + Rc[6] * x[2];
+        const float yy = Rc[1] * x[0] + Rc[4] * x[1] + Rc[7] * x[2];
+        const float yz = Rc[2] * x[0] + Rc[5] * x[1] + Rc[8] * x[2];
+        if (!(yz > 0.5f * C.zn)) { front = false; break; }
+        const float uc = C.fx * yx / yz + C.cx - 0.5f, vc = C.fy * yy / yz + C.cy - 0.5f;
+        umin = fminf(umin, uc); umax = fmaxf(umax, uc);
+        vmin = fminf(vmin, vc); vmax = fmaxf(vmax, vc);
+      }
+      if (front) {
+        const int p0 = blockIdx.x * blockDim.x, p1 = min(p0 + (int)blockDim.x, WH) - 1;
+        const int r0 = p0 / C.W, r1 = p1 / C.W;
+        const int c0 = r0 == r1 ? p0 - r0 * C.W : 0, c1 = r0 == r1 ? p1 - r0 * C.W : C.W - 1;
+        act = umax >= c0 - 1.f && umin <= c1 + 1.f && vmax >= r0 - 1.f && vmin <= r1 + 1.f;
+      }
+    }
+    sact[k] = act;
   }
   __syncthreads();
-  const int WH = C.W * C.H;
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= WH) return;
   const int v = pix / C.W, u = pix - v * C.W;
@@ -289,6 +325,7 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
     inst = 1;
   }
   for (int k = 0; k < O.K; k++) {   // ties keep the smaller instance
+    if (!sact[k]) continue;
     const float t = ray_obstacle(sq[k], d, C.zn);
     if (t <= C.zf && t < best) {
       best = t;
