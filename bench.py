@@ -465,7 +465,7 @@ def run_render(args, rank, world, local):
                        "l2": "flushed between timed casts (256 MiB write, outside the events)",
                        "parallelism": f"replicas x{world}"},
             "ms_per_batch_by_envs": sweep, "mesh_pixel_fraction": mesh_px / (W * H * n_envs),
-            "roofline": roof, "kernels": kernels, "gpu_launches": 2 * args.steps,
+            "roofline": roof, "kernels": kernels, "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
         }), flush=True)
     if world > 1:

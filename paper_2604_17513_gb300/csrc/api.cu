@@ -861,6 +861,7 @@ void flash_scene_destroy(flash_scene *s) {
   if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   if (s->h_active) cudaFreeHost(s->h_active);
   if (s->rc_keys) cudaFree(s->rc_keys);
+  if (s->rc_prep) cudaFree(s->rc_prep);
   delete s;
 }
 
@@ -950,6 +951,7 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
     }
     FLASH_CUDA_TRY(cudaMalloc(&s->rc_keys, need * sizeof(unsigned long long)));
     s->rc_keys_n = need;
+    if (!s->rc_prep) FLASH_CUDA_TRY(cudaMalloc(&s->rc_prep, rc_prep_bytes(s->N)));
     s->rc_tag = -1;   // the first render fills the buffer
   }
   FLASH_CUDA_TRY(rc_next_tag(s->rc_keys, s->rc_keys_n, &s->rc_tag, st));
@@ -960,8 +962,8 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
     if (g.rT > 0) s->launches++;
   }
   const RcObs O{s->otype, s->odims, s->pose_t, s->K, FLASH_MAX_OBS};
-  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, tag, depth, seg, points, st));
-  s->launches++;
+  FLASH_CUDA_TRY(rc_launch_resolve(O, cam_poses, C, 0, s->N, s->rc_keys, tag, s->rc_prep, depth, seg, points, st));
+  s->launches += 2;
   s->rc_tag--;
   return FLASH_OK;
 }

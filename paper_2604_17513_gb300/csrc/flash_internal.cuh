@@ -159,6 +159,7 @@ struct flash_scene {
   unsigned long long *rc_keys = nullptr;   // ray casting work buffer
   size_t rc_keys_n = 0;
   int rc_tag = 0;                          // frame tag of the next render
+  void *rc_prep = nullptr;                 // per-environment view constants
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
@@ -255,9 +256,11 @@ constexpr int kMaxRcTris = (1 << 25) - 1;
 cudaError_t rc_next_tag(unsigned long long *keys, size_t n_keys, int *tag, cudaStream_t st);
 cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, const RcCam &C,
                           unsigned long long *keys, unsigned tag, cudaStream_t st);
+// prep: device workspace of rc_prep_bytes(n_envs) (per-environment view constants)
+size_t rc_prep_bytes(int n_envs);
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              const unsigned long long *keys, unsigned tag, float *depth, uint8_t *seg, float *pts,
-                              cudaStream_t st);
+                              const unsigned long long *keys, unsigned tag, void *prep, float *depth, uint8_t *seg,
+                              float *pts, cudaStream_t st);
 flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out);
 
 // grasp requests s->greq[first_env, first_env + count) -> per-environment grasp state

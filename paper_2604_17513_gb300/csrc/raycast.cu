@@ -23,6 +23,7 @@
 // triple products d.(a x b) share a sign).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -239,73 +240,101 @@ __device__ __forceinline__ float ray_obstacle(const ObsRay &Q, float3 d, float z
   return INFINITY;
 }
 
-__global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__restrict__ cam_poses, RcCam C,
-                                                    int first_env, const unsigned long long *__restrict__ keys,
-                                                    unsigned tag, float *__restrict__ depth, uint8_t *__restrict__ seg,
+// What every pixel of one environment's view shares: the camera and, per
+// obstacle, its ray-test constants and the bounds of its projection.
+struct EnvPrep {
+  float Rc[9], p[3], ifx, ify;
+  ObsRay Q[FLASH_MAX_OBS];
+  float bounds[FLASH_MAX_OBS][4];   // projected corners, pixel-centre units: umin, umax, vmin, vmax
+  int act[FLASH_MAX_OBS];           // 0: invisible; 1: test where the bounds reach; 2: test everywhere
+};
+
+__global__ void __launch_bounds__(32) k_rc_prep(RcObs O, const float *__restrict__ cam_poses, RcCam C,
+                                                int first_env, EnvPrep *__restrict__ prep) {
+  const int e = first_env + blockIdx.x;
+  EnvPrep &P = prep[blockIdx.x];
+  const float *cp = cam_poses + 7 * (size_t)e;
+  if (threadIdx.x == 31) {
+    rc_quat_mat(cp + 3, P.Rc);
+    P.p[0] = cp[0]; P.p[1] = cp[1]; P.p[2] = cp[2];
+    P.ifx = 1.f / C.fx;
+    P.ify = 1.f / C.fy;
+  }
+  if (threadIdx.x >= O.K) return;
+  const int k = threadIdx.x;
+  const size_t b = (size_t)e * O.stride + k;
+  const float *pose = O.pose + 7 * b, *dims = O.dims + 3 * b;
+  ObsRay &Q = P.Q[k];
+  Q.type = O.type[b];
+  float R[9];
+  rc_quat_mat(pose + 3, R);
+  const float w[3] = {pose[0] - cp[0], pose[1] - cp[1], pose[2] - cp[2]};   // obstacle origin - camera
+  if (Q.type == FLASH_OBS_PLANE) {
+    Q.a[0] = R[2]; Q.a[1] = R[5]; Q.a[2] = R[8];
+    Q.b = R[2] * w[0] + R[5] * w[1] + R[8] * w[2];
+  } else if (Q.type == FLASH_OBS_SPHERE) {
+    Q.a[0] = w[0]; Q.a[1] = w[1]; Q.a[2] = w[2];
+    Q.b = dims[0] * dims[0];
+  } else {
+    for (int i = 0; i < 3; i++) Q.a[i] = -(R[i] * w[0] + R[3 + i] * w[1] + R[6 + i] * w[2]);
+    for (int i = 0; i < 9; i++) Q.R[i] = R[i];
+    for (int i = 0; i < 3; i++) Q.h[i] = dims[i];
+  }
+  // A sphere or box is tested only near its projection, bounded by the
+  // projected corners of the box (of the sphere's bounding cube); a shape
+  // reaching behind the camera is tested everywhere.
+  int act = Q.type == FLASH_OBS_NONE ? 0 : 2;
+  if (Q.type == FLASH_OBS_SPHERE || Q.type == FLASH_OBS_BOX) {
+    float Rc[9];
+    rc_quat_mat(cp + 3, Rc);
+    const bool sph = Q.type == FLASH_OBS_SPHERE;
+    const float hx = dims[0], hy = sph ? dims[0] : dims[1], hz = sph ? dims[0] : dims[2];
+    bool front = true;
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int c = 0; c < 8 && front; c++) {
+      const float bx = (c & 1) ? hx : -hx, by = (c & 2) ? hy : -hy, bz = (c & 4) ? hz : -hz;
+      float x[3];
+      for (int i = 0; i < 3; i++)
+        x[i] = w[i] + (sph ? (i == 0 ? bx : i == 1 ? by : bz) : R[3 * i] * bx + R[3 * i + 1] * by + R[3 * i + 2] * bz);
+      const float yx = Rc[0] * x[0] + Rc[3] * x[1] + Rc[6] * x[2];
+      const float yy = Rc[1] * x[0] + Rc[4] * x[1] + Rc[7] * x[2];
+      const float yz = Rc[2] * x[0] + Rc[5] * x[1] + Rc[8] * x[2];
+      if (!(yz > 0.5f * C.zn)) { front = false; break; }
+      const float uc = C.fx * yx / yz + C.cx - 0.5f, vc = C.fy * yy / yz + C.cy - 0.5f;
+      umin = fminf(umin, uc); umax = fmaxf(umax, uc);
+      vmin = fminf(vmin, vc); vmax = fmaxf(vmax, vc);
+    }
+    if (front) {
+      act = 1;
+      P.bounds[k][0] = umin - 1.f; P.bounds[k][1] = umax + 1.f;   // a pixel of slack each way
+      P.bounds[k][2] = vmin - 1.f; P.bounds[k][3] = vmax + 1.f;
+    }
+  }
+  P.act[k] = act;
+}
+
+__global__ void __launch_bounds__(256) k_rc_resolve(int K, const EnvPrep *__restrict__ prep, RcCam C, int first_env,
+                                                    const unsigned long long *__restrict__ keys, unsigned tag,
+                                                    float *__restrict__ depth, uint8_t *__restrict__ seg,
                                                     float *__restrict__ pts) {
-  __shared__ float sRc[9], spc[3], sif[2];
-  __shared__ ObsRay sq[FLASH_MAX_OBS];
+  __shared__ EnvPrep P;
   __shared__ int sact[FLASH_MAX_OBS];
   const int e = first_env + blockIdx.y;
   const int WH = C.W * C.H;
-  if (threadIdx.x == 0) {
-    const float *cp = cam_poses + 7 * (size_t)e;
-    rc_quat_mat(cp + 3, sRc);
-    spc[0] = cp[0]; spc[1] = cp[1]; spc[2] = cp[2];
-    sif[0] = 1.f / C.fx;
-    sif[1] = 1.f / C.fy;
+  {
+    const int *src = reinterpret_cast<const int *>(prep + blockIdx.y);
+    int *dst = reinterpret_cast<int *>(&P);
+    for (int i = threadIdx.x; i < (int)(sizeof(EnvPrep) / 4); i += blockDim.x) dst[i] = src[i];
   }
-  if (threadIdx.x < O.K) {
+  __syncthreads();
+  if (threadIdx.x < K) {   // obstacles whose projection reaches this block's pixels
     const int k = threadIdx.x;
-    const size_t b = (size_t)e * O.stride + k;
-    const float *cp = cam_poses + 7 * (size_t)e, *pose = O.pose + 7 * b, *dims = O.dims + 3 * b;
-    ObsRay &Q = sq[k];
-    Q.type = O.type[b];
-    float R[9];
-    rc_quat_mat(pose + 3, R);
-    const float w[3] = {pose[0] - cp[0], pose[1] - cp[1], pose[2] - cp[2]};   // obstacle origin - camera
-    if (Q.type == FLASH_OBS_PLANE) {
-      Q.a[0] = R[2]; Q.a[1] = R[5]; Q.a[2] = R[8];
-      Q.b = R[2] * w[0] + R[5] * w[1] + R[8] * w[2];
-    } else if (Q.type == FLASH_OBS_SPHERE) {
-      Q.a[0] = w[0]; Q.a[1] = w[1]; Q.a[2] = w[2];
-      Q.b = dims[0] * dims[0];
-    } else {
-      for (int i = 0; i < 3; i++) Q.a[i] = -(R[i] * w[0] + R[3 + i] * w[1] + R[6 + i] * w[2]);
-      for (int i = 0; i < 9; i++) Q.R[i] = R[i];
-      for (int i = 0; i < 3; i++) Q.h[i] = dims[i];
-    }
-    // Sphere or box whose projection (bounded by the projected corners of
-    // the box, or of the sphere's bounding cube) misses this block's pixel
-    // centres by more than a pixel is skipped for the whole block; a shape
-    // reaching behind the camera is always tested.
-    int act = Q.type != FLASH_OBS_NONE;
-    if (Q.type == FLASH_OBS_SPHERE || Q.type == FLASH_OBS_BOX) {
-      float Rc[9];
-      rc_quat_mat(cp + 3, Rc);
-      const bool sph = Q.type == FLASH_OBS_SPHERE;
-      const float hx = sph ? dims[0] : dims[0], hy = sph ? dims[0] : dims[1], hz = sph ? dims[0] : dims[2];
-      bool front = true;
-      float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-      for (int c = 0; c < 8; c++) {
-        const float bx = (c & 1) ? hx : -hx, by = (c & 2) ? hy : -hy, bz = (c & 4) ? hz : -hz;
-        float x[3];
-        for (int i = 0; i < 3; i++)
-          x[i] = w[i] + (sph ? (i == 0 ? bx : i == 1 ? by : bz) : R[3 * i] * bx + R[3 * i + 1] * by + R[3 * i + 2] * bz);
-        const float yx = Rc[0] * x[0] + Rc[3] * x[1] + Rc[6] * x[2];
-        const float yy = Rc[1] * x[0] + Rc[4] * x[1] + Rc[7] * x[2];
-        const float yz = Rc[2] * x[0] + Rc[5] * x[1] + Rc[8] * x[2];
-        if (!(yz > 0.5f * C.zn)) { front = false; break; }
-        const float uc = C.fx * yx / yz + C.cx - 0.5f, vc = C.fy * yy / yz + C.cy - 0.5f;
-        umin = fminf(umin, uc); umax = fmaxf(umax, uc);
-        vmin = fminf(vmin, vc); vmax = fmaxf(vmax, vc);
-      }
-      if (front) {
-        const int p0 = blockIdx.x * blockDim.x, p1 = min(p0 + (int)blockDim.x, WH) - 1;
-        const int r0 = p0 / C.W, r1 = p1 / C.W;
-        const int c0 = r0 == r1 ? p0 - r0 * C.W : 0, c1 = r0 == r1 ? p1 - r0 * C.W : C.W - 1;
-        act = umax >= c0 - 1.f && umin <= c1 + 1.f && vmax >= r0 - 1.f && vmin <= r1 + 1.f;
-      }
+    int act = P.act[k];
+    if (act == 1) {
+      const int p0 = blockIdx.x * blockDim.x, p1 = min(p0 + (int)blockDim.x, WH) - 1;
+      const int r0 = p0 / C.W, r1 = p1 / C.W;
+      const int c0 = r0 == r1 ? p0 - r0 * C.W : 0, c1 = r0 == r1 ? p1 - r0 * C.W : C.W - 1;
+      act = P.bounds[k][1] >= c0 && P.bounds[k][0] <= c1 && P.bounds[k][3] >= r0 && P.bounds[k][2] <= r1;
     }
     sact[k] = act;
   }
@@ -313,9 +342,9 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= WH) return;
   const int v = pix / C.W, u = pix - v * C.W;
-  const float dx = (u + 0.5f - C.cx) * sif[0], dy = (v + 0.5f - C.cy) * sif[1];
-  const float3 d = make_float3(sRc[0] * dx + sRc[1] * dy + sRc[2], sRc[3] * dx + sRc[4] * dy + sRc[5],
-                               sRc[6] * dx + sRc[7] * dy + sRc[8]);
+  const float dx = (u + 0.5f - C.cx) * P.ifx, dy = (v + 0.5f - C.cy) * P.ify;
+  const float3 d = make_float3(P.Rc[0] * dx + P.Rc[1] * dy + P.Rc[2], P.Rc[3] * dx + P.Rc[4] * dy + P.Rc[5],
+                               P.Rc[6] * dx + P.Rc[7] * dy + P.Rc[8]);
   const size_t pe = (size_t)e * WH + pix;
   const unsigned long long key = keys[pe];
   float best = INFINITY;
@@ -324,9 +353,9 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
     best = __uint_as_float((unsigned)(key >> 25) & 0x7fffffffu);
     inst = 1;
   }
-  for (int k = 0; k < O.K; k++) {   // ties keep the smaller instance
+  for (int k = 0; k < K; k++) {   // ties keep the smaller instance
     if (!sact[k]) continue;
-    const float t = ray_obstacle(sq[k], d, C.zn);
+    const float t = ray_obstacle(P.Q[k], d, C.zn);
     if (t <= C.zf && t < best) {
       best = t;
       inst = 2 + k;
@@ -336,9 +365,9 @@ __global__ void __launch_bounds__(256) k_rc_resolve(RcObs O, const float *__rest
   if (seg) seg[pe] = (uint8_t)inst;
   if (pts) {
     const float nan = __int_as_float(0x7fc00000);
-    pts[3 * pe] = inst ? spc[0] + best * d.x : nan;
-    pts[3 * pe + 1] = inst ? spc[1] + best * d.y : nan;
-    pts[3 * pe + 2] = inst ? spc[2] + best * d.z : nan;
+    pts[3 * pe] = inst ? P.p[0] + best * d.x : nan;
+    pts[3 * pe + 1] = inst ? P.p[1] + best * d.y : nan;
+    pts[3 * pe + 2] = inst ? P.p[2] + best * d.z : nan;
   }
 }
 
@@ -351,13 +380,18 @@ cudaError_t rc_launch_tri(const RcMesh &M, int n_envs, const float *cam_poses, c
   return cudaGetLastError();
 }
 
+size_t rc_prep_bytes(int n_envs) { return sizeof(EnvPrep) * (size_t)std::max(n_envs, 1); }
+
 cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCam &C, int first_env, int n_envs,
-                              const unsigned long long *keys, unsigned tag, float *depth, uint8_t *seg, float *pts,
-                              cudaStream_t st) {
+                              const unsigned long long *keys, unsigned tag, void *prep, float *depth, uint8_t *seg,
+                              float *pts, cudaStream_t st) {
   if (n_envs <= 0) return cudaSuccess;
+  EnvPrep *P = reinterpret_cast<EnvPrep *>(prep);
+  k_rc_prep<<<n_envs, 32, 0, st>>>(O, cam_poses, C, first_env, P);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int WH = C.W * C.H;
-  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O, cam_poses, C, first_env, keys, tag, depth, seg,
-                                                               pts);
+  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O.K, P, C, first_env, keys, tag, depth, seg, pts);
   return cudaGetLastError();
 }
 
@@ -395,6 +429,7 @@ struct flash_raycaster {
   int N = 0, n = 0, T = 0;
   int3 *tris = nullptr;
   unsigned long long *keys = nullptr;
+  void *prep = nullptr;   // per-environment view constants
   int tag = flash::kFirstTag;   // frame tag of the next cast
   // per-kernel device time while profiling (0: triangles, 1: resolve)
   bool profiling = false;
@@ -426,6 +461,7 @@ flash_status flash_raycaster_create(const flash_camera *cam, int32_t n_envs, int
   cudaError_t e = cudaMalloc(&rc->keys, keys * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(rc->keys, 0xff, keys * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the buffer is ready for any stream
+  if (e == cudaSuccess) e = cudaMalloc(&rc->prep, flash::rc_prep_bytes(n_envs));
   if (e == cudaSuccess && n_tris > 0) {
     e = cudaMalloc(&rc->tris, sizeof(int3) * n_tris);
     if (e == cudaSuccess) e = cudaMemcpy(rc->tris, tris, sizeof(int3) * n_tris, cudaMemcpyHostToDevice);
@@ -445,6 +481,7 @@ void flash_raycaster_destroy(flash_raycaster *rc) {
     if (e) cudaEventDestroy(e);
   if (rc->tris) cudaFree(rc->tris);
   if (rc->keys) cudaFree(rc->keys);
+  if (rc->prep) cudaFree(rc->prep);
   delete rc;
 }
 
@@ -465,7 +502,8 @@ flash_status flash_raycast(flash_raycaster *rc, const float *verts, int32_t n_ob
   FLASH_CUDA_TRY(flash::rc_launch_tri(M, rc->N, cam_poses, rc->cam, rc->keys, tag, st));
   if (prof) FLASH_CUDA_TRY(cudaEventRecord(rc->ev[1], st));
   flash::RcObs O{obs_type, obs_dims, obs_poses, n_obs, n_obs};
-  FLASH_CUDA_TRY(flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, tag, depth, seg, points, st));
+  FLASH_CUDA_TRY(
+      flash::rc_launch_resolve(O, cam_poses, rc->cam, 0, rc->N, rc->keys, tag, rc->prep, depth, seg, points, st));
   rc->tag--;
   if (prof) {
     FLASH_CUDA_TRY(cudaEventRecord(rc->ev[2], st));
