@@ -207,7 +207,7 @@ flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const
  * call, stream-ordered; the caller keeps the output buffers.
  * ------------------------------------------------------------------------- */
 typedef struct {
-  int32_t width, height; /* pixels; 1 <= width*height <= 2^26 */
+  int32_t width, height; /* pixels; 1 <= width*height <= 2^26, height <= 524280 */
   float fx, fy, cx, cy;  /* intrinsics in pixels; fx, fy > 0 */
   float z_near, z_far;   /* depth range (m); 0 < z_near < z_far */
 } flash_camera;

@@ -139,10 +139,39 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
     const long long v0 = max(0LL, -((-ymin) >> kSubBits)), v1 = min((long long)C.H - 1, ymax >> kSubBits);
     const long long area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
     if (area == 0 || u0 > u1 || v0 > v1) return;   // seen edge-on, or between pixel centres
+    const float ifx = 1.f / C.fx, ify = 1.f / C.fy;
+    if (u1 - u0 < 4 && v1 - v0 < 4) {
+      // Small triangle (at most 4 x 4 pixel centres): coordinates relative to
+      // the first pixel centre are below 5 pixels = 20480 units, so every
+      // edge-function product stays below 2^29 and 32-bit integers are exact.
+      const long long bx = u0 * kSub, by = v0 * kSub;
+      int x[3], yy[3];
+#pragma unroll
+      for (int k = 0; k < 3; k++) { x[k] = (int)(X[k] - bx); yy[k] = (int)(Y[k] - by); }
+      const int t0 = yy[1] - yy[2], t1 = yy[2] - yy[0], t2 = yy[0] - yy[1];   // change per pixel / kSub
+      const int nu = (int)(u1 - u0), nv = (int)(v1 - v0);
+      for (int j = 0; j <= nv; j++) {
+        const int py = j * (int)kSub;
+        int E0 = (x[2] - x[1]) * (py - yy[1]) + t0 * (0 - x[1]);
+        int E1 = (x[0] - x[2]) * (py - yy[2]) + t1 * (0 - x[2]);
+        int E2 = (x[1] - x[0]) * (py - yy[0]) + t2 * (0 - x[0]);
+        const float rowc = n.y * (((int)v0 + j + 0.5f - C.cy) * ify) + n.z;
+        for (int i = 0; i <= nu; i++, E0 += t0 * (int)kSub, E1 += t1 * (int)kSub, E2 += t2 * (int)kSub) {
+          const bool in = (E0 >= 0 && E1 >= 0 && E2 >= 0) || (E0 <= 0 && E1 <= 0 && E2 <= 0);
+          if (!in) continue;
+          const int u = (int)u0 + i;
+          const float nd = n.x * ((u + 0.5f - C.cx) * ifx) + rowc;
+          if (nd == 0.f) continue;
+          const float depth = __fdividef(num, nd);
+          if (!(depth >= C.zn && depth <= C.zf)) continue;
+          store_key(ke + (size_t)(v0 + j) * C.W + u, depth, f, tag);
+        }
+      }
+      return;
+    }
     // edge functions at the row's first pixel, then stepped exactly by
     // their (integer) change per pixel
     const long long s0 = (Y[1] - Y[2]) * kSub, s1 = (Y[2] - Y[0]) * kSub, s2 = (Y[0] - Y[1]) * kSub;
-    const float ifx = 1.f / C.fx, ify = 1.f / C.fy;
     for (long long v = v0; v <= v1; v++) {
       const long long py = v * kSub, px = u0 * kSub;
       long long E0 = (X[2] - X[1]) * (py - Y[1]) - (Y[2] - Y[1]) * (px - X[1]);
@@ -317,31 +346,29 @@ __global__ void __launch_bounds__(256) k_rc_resolve(int K, const EnvPrep *__rest
                                                     const unsigned long long *__restrict__ keys, unsigned tag,
                                                     float *__restrict__ depth, uint8_t *__restrict__ seg,
                                                     float *__restrict__ pts) {
+  // block = a 32 x 8 pixel tile of environment blockIdx.z
   __shared__ EnvPrep P;
   __shared__ int sact[FLASH_MAX_OBS];
-  const int e = first_env + blockIdx.y;
+  const int e = first_env + blockIdx.z;
   const int WH = C.W * C.H;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   {
-    const int *src = reinterpret_cast<const int *>(prep + blockIdx.y);
+    const int *src = reinterpret_cast<const int *>(prep + blockIdx.z);
     int *dst = reinterpret_cast<int *>(&P);
-    for (int i = threadIdx.x; i < (int)(sizeof(EnvPrep) / 4); i += blockDim.x) dst[i] = src[i];
+    for (int i = tid; i < (int)(sizeof(EnvPrep) / 4); i += 256) dst[i] = src[i];
   }
   __syncthreads();
-  if (threadIdx.x < K) {   // obstacles whose projection reaches this block's pixels
-    const int k = threadIdx.x;
-    int act = P.act[k];
-    if (act == 1) {
-      const int p0 = blockIdx.x * blockDim.x, p1 = min(p0 + (int)blockDim.x, WH) - 1;
-      const int r0 = p0 / C.W, r1 = p1 / C.W;
-      const int c0 = r0 == r1 ? p0 - r0 * C.W : 0, c1 = r0 == r1 ? p1 - r0 * C.W : C.W - 1;
-      act = P.bounds[k][1] >= c0 && P.bounds[k][0] <= c1 && P.bounds[k][3] >= r0 && P.bounds[k][2] <= r1;
-    }
-    sact[k] = act;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 8;
+  if (tid < K) {   // obstacles whose projection reaches this tile
+    int act = P.act[tid];
+    if (act == 1)
+      act = P.bounds[tid][1] >= c0 && P.bounds[tid][0] <= c0 + 31 && P.bounds[tid][3] >= r0 && P.bounds[tid][2] <= r0 + 7;
+    sact[tid] = act;
   }
   __syncthreads();
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= WH) return;
-  const int v = pix / C.W, u = pix - v * C.W;
+  const int u = c0 + threadIdx.x, v = r0 + threadIdx.y;
+  if (u >= C.W || v >= C.H) return;
+  const int pix = v * C.W + u;
   const float dx = (u + 0.5f - C.cx) * P.ifx, dy = (v + 0.5f - C.cy) * P.ify;
   const float3 d = make_float3(P.Rc[0] * dx + P.Rc[1] * dy + P.Rc[2], P.Rc[3] * dx + P.Rc[4] * dy + P.Rc[5],
                                P.Rc[6] * dx + P.Rc[7] * dy + P.Rc[8]);
@@ -390,8 +417,8 @@ cudaError_t rc_launch_resolve(const RcObs &O, const float *cam_poses, const RcCa
   k_rc_prep<<<n_envs, 32, 0, st>>>(O, cam_poses, C, first_env, P);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int WH = C.W * C.H;
-  k_rc_resolve<<<dim3((WH + 255) / 256, n_envs), 256, 0, st>>>(O.K, P, C, first_env, keys, tag, depth, seg, pts);
+  k_rc_resolve<<<dim3((C.W + 31) / 32, (C.H + 7) / 8, n_envs), dim3(32, 8), 0, st>>>(O.K, P, C, first_env, keys, tag,
+                                                                                      depth, seg, pts);
   return cudaGetLastError();
 }
 
@@ -407,8 +434,8 @@ cudaError_t rc_next_tag(unsigned long long *keys, size_t n_keys, int *tag, cudaS
 flash_status rc_check_camera(const flash_camera *cam, int64_t n_envs, RcCam *out) {
   if (!cam) { set_error("camera is NULL"); return FLASH_EINVAL; }
   const int64_t W = cam->width, H = cam->height;
-  if (W < 1 || H < 1 || W * H > (1 << 26) || n_envs * W * H > ((int64_t)1 << 34)) {
-    set_error("camera size out of range (1 <= W*H <= 2^26 pixels, N*W*H <= 2^34)");
+  if (W < 1 || H < 1 || W * H > (1 << 26) || H > 8 * 65535 || n_envs * W * H > ((int64_t)1 << 34)) {
+    set_error("camera size out of range (1 <= W*H <= 2^26 pixels, H <= 524280, N*W*H <= 2^34)");
     return FLASH_EINVAL;
   }
   const float v[6] = {cam->fx, cam->fy, cam->cx, cam->cy, cam->z_near, cam->z_far};
