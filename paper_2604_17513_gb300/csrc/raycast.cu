@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
   // bits in every triangle that uses it) and the 2D edge functions are
   // evaluated exactly in 64-bit integers, so shared edges and vertices leave
   // no gap.  Pixel centres sit on integer coordinates.
-  long long X[3], Y[3];
+  int X[3], Y[3];   // |X|, |Y| < 2^29
   bool fixed_point = zmin > 0.5f * C.zn;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
@@ -128,38 +128,39 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
     const float uc = __fmaf_rn(C.fx, __fmul_rn(y[k].x, iz), C.cx - 0.5f);
     const float vc = __fmaf_rn(C.fy, __fmul_rn(y[k].y, iz), C.cy - 0.5f);
     if (!(fabsf(uc) < kMaxProj && fabsf(vc) < kMaxProj)) fixed_point = false;
-    X[k] = __float2ll_rn(__fmul_rn(uc, (float)kSub));
-    Y[k] = __float2ll_rn(__fmul_rn(vc, (float)kSub));
+    X[k] = __float2int_rn(__fmul_rn(uc, (float)kSub));
+    Y[k] = __float2int_rn(__fmul_rn(vc, (float)kSub));
   }
   if (fixed_point) {
-    const long long xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
-    const long long ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
-    // pixels with centres inside the bounding box (ceil / floor of the scaled range)
-    const long long u0 = max(0LL, -((-xmin) >> kSubBits)), u1 = min((long long)C.W - 1, xmax >> kSubBits);
-    const long long v0 = max(0LL, -((-ymin) >> kSubBits)), v1 = min((long long)C.H - 1, ymax >> kSubBits);
-    const long long area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    const int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
+    const int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
+    // pixels with centres inside the bounding box (ceil / floor of the scaled
+    // range; >> of a negative value rounds towards minus infinity)
+    const int u0 = max(0, -((-xmin) >> kSubBits)), u1 = min(C.W - 1, xmax >> kSubBits);
+    const int v0 = max(0, -((-ymin) >> kSubBits)), v1 = min(C.H - 1, ymax >> kSubBits);
+    const long long area = (long long)(X[1] - X[0]) * (Y[2] - Y[0]) - (long long)(Y[1] - Y[0]) * (X[2] - X[0]);
     if (area == 0 || u0 > u1 || v0 > v1) return;   // seen edge-on, or between pixel centres
     const float ifx = 1.f / C.fx, ify = 1.f / C.fy;
     if (u1 - u0 < 4 && v1 - v0 < 4) {
       // Small triangle (at most 4 x 4 pixel centres): coordinates relative to
       // the first pixel centre are below 5 pixels = 20480 units, so every
       // edge-function product stays below 2^29 and 32-bit integers are exact.
-      const long long bx = u0 * kSub, by = v0 * kSub;
+      const int bx = u0 * (int)kSub, by = v0 * (int)kSub;
       int x[3], yy[3];
 #pragma unroll
-      for (int k = 0; k < 3; k++) { x[k] = (int)(X[k] - bx); yy[k] = (int)(Y[k] - by); }
+      for (int k = 0; k < 3; k++) { x[k] = X[k] - bx; yy[k] = Y[k] - by; }
       const int t0 = yy[1] - yy[2], t1 = yy[2] - yy[0], t2 = yy[0] - yy[1];   // change per pixel / kSub
-      const int nu = (int)(u1 - u0), nv = (int)(v1 - v0);
+      const int nu = u1 - u0, nv = v1 - v0;
       for (int j = 0; j <= nv; j++) {
         const int py = j * (int)kSub;
         int E0 = (x[2] - x[1]) * (py - yy[1]) + t0 * (0 - x[1]);
         int E1 = (x[0] - x[2]) * (py - yy[2]) + t1 * (0 - x[2]);
         int E2 = (x[1] - x[0]) * (py - yy[0]) + t2 * (0 - x[0]);
-        const float rowc = n.y * (((int)v0 + j + 0.5f - C.cy) * ify) + n.z;
+        const float rowc = n.y * ((v0 + j + 0.5f - C.cy) * ify) + n.z;
         for (int i = 0; i <= nu; i++, E0 += t0 * (int)kSub, E1 += t1 * (int)kSub, E2 += t2 * (int)kSub) {
           const bool in = (E0 >= 0 && E1 >= 0 && E2 >= 0) || (E0 <= 0 && E1 <= 0 && E2 <= 0);
           if (!in) continue;
-          const int u = (int)u0 + i;
+          const int u = u0 + i;
           const float nd = n.x * ((u + 0.5f - C.cx) * ifx) + rowc;
           if (nd == 0.f) continue;
           const float depth = __fdividef(num, nd);
@@ -171,14 +172,15 @@ __global__ void __launch_bounds__(256) k_rc_tri(RcMesh M, const float *__restric
     }
     // edge functions at the row's first pixel, then stepped exactly by
     // their (integer) change per pixel
-    const long long s0 = (Y[1] - Y[2]) * kSub, s1 = (Y[2] - Y[0]) * kSub, s2 = (Y[0] - Y[1]) * kSub;
-    for (long long v = v0; v <= v1; v++) {
-      const long long py = v * kSub, px = u0 * kSub;
-      long long E0 = (X[2] - X[1]) * (py - Y[1]) - (Y[2] - Y[1]) * (px - X[1]);
-      long long E1 = (X[0] - X[2]) * (py - Y[2]) - (Y[0] - Y[2]) * (px - X[2]);
-      long long E2 = (X[1] - X[0]) * (py - Y[0]) - (Y[1] - Y[0]) * (px - X[0]);
+    const long long s0 = (long long)(Y[1] - Y[2]) * kSub, s1 = (long long)(Y[2] - Y[0]) * kSub,
+                    s2 = (long long)(Y[0] - Y[1]) * kSub;
+    for (int v = v0; v <= v1; v++) {
+      const long long py = (long long)v * kSub, px = (long long)u0 * kSub;
+      long long E0 = (long long)(X[2] - X[1]) * (py - Y[1]) - (long long)(Y[2] - Y[1]) * (px - X[1]);
+      long long E1 = (long long)(X[0] - X[2]) * (py - Y[2]) - (long long)(Y[0] - Y[2]) * (px - X[2]);
+      long long E2 = (long long)(X[1] - X[0]) * (py - Y[0]) - (long long)(Y[1] - Y[0]) * (px - X[0]);
       const float rowc = n.y * ((v + 0.5f - C.cy) * ify) + n.z;
-      for (long long u = u0; u <= u1; u++, E0 += s0, E1 += s1, E2 += s2) {
+      for (int u = u0; u <= u1; u++, E0 += s0, E1 += s1, E2 += s2) {
         const bool in = (E0 >= 0 && E1 >= 0 && E2 >= 0) || (E0 <= 0 && E1 <= 0 && E2 <= 0);
         if (!in) continue;
         const float nd = n.x * ((u + 0.5f - C.cx) * ifx) + rowc;
