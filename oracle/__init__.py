@@ -20,8 +20,10 @@ _SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c", "raycast.c")]
 _lib = None
 
 DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU, DP_GRASP_OBS = range(10)
-DP_ANCHOR, DP_SIZE = 10, 13
+DP_ANCHOR, DP_SELF, DP_SIZE = 10, 13, 14
 GRASP_SLOT = 8   # contact-list slot of grasp constraints (after every obstacle)
+SELF_SLOT = 9    # contact-list slot of cloth self contacts (after the grasp row)
+SELF_MAX = 4     # self contacts per vertex at most
 IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC, IP_LINIT = range(6)
 
 
@@ -59,12 +61,12 @@ def lib():
         _lib.or_fb.restype = d
         _lib.or_fb.argtypes = [d, d]
         _lib.or_detect.restype = i
-        _lib.or_detect.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, C.POINTER(C.c_ubyte), i, pi, pi]
+        _lib.or_detect.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, C.POINTER(C.c_ubyte), i, pi, pi, pi]
         _lib.or_solve_step.restype = i
         _lib.or_solve_step.argtypes = [C.c_void_p, pd, pi, i, pi, pd, pd, pd, pd, pd, pd, pd, i,
-                                       pi, pi, pd, pi, pd, pd]
+                                       pi, pi, pi, pd, pi, pd, pd]
         _lib.or_residual.restype = d
-        _lib.or_residual.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, pd, pd, i, pi, pi, pd]
+        _lib.or_residual.argtypes = [C.c_void_p, pd, i, pi, pd, pd, pd, pd, pd, pd, i, pi, pi, pi, pd]
         _lib.or_raycast.argtypes = [i, pd, i, pi, i, pi, pd, pd, pd, pd, i, i, d, pd, pi, pd]
         _lib.or_raycast.restype = None
         _lib.or_raycast_pixels.argtypes = [i, pd, i, pi, i, pi, pd, pd, pd, pd, i, pi, d, pd, pi, pd]
@@ -176,6 +178,7 @@ def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None,
     dp[DP_GRASP_OBS] = g["obstacle"] if g else -1
     if g:
         dp[DP_ANCHOR:DP_ANCHOR + 3] = g["anchor"]
+    dp[DP_SELF] = 1.0 if (sc.meta and sc.meta.get("self_collision")) else 0.0
     ip = np.zeros(6, np.int32)
     ip[IP_KMAX] = sc.k_max if k_max is None else k_max
     ip[IP_KMIN] = sc.k_min if k_min is None else k_min
@@ -193,6 +196,7 @@ class EnvState:
         self.q, self.v = _f64(q).copy(), _f64(v).copy()
         self.cvert = np.zeros(0, np.int32)
         self.cobs = np.zeros(0, np.int32)
+        self.ctri = np.zeros(0, np.int32)     # triangle of each self contact, -1 otherwise
         self.gamma = np.zeros((0, 4))
         self.iters, self.rncp = 0, 0.0
         self.trace = None
@@ -230,23 +234,22 @@ def detect(mesh: Mesh, sc, env, step, q, v, dp=None, attached=None):
     K = sc.n_obs
     ot, od = _i32(sc.obs_type[env]), _f64(sc.obs_dims[env])
     pth = _f64(sc.poses[env, step + 1])
-    cap = mesh.n * (K + 1)
-    cv, co = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    cap = mesh.n * (K + 1 + SELF_MAX)
+    cv, co, ct = np.zeros(cap, np.int32), np.zeros(cap, np.int32), np.zeros(cap, np.int32)
     att = None if attached is None else np.ascontiguousarray(attached, np.uint8)
     cnt = lib().or_detect(mesh._p, _pd(dp), K, _pi(ot), _pd(od), _pd(pth), _pd(_f64(q)), _pd(_f64(v)),
                           None if att is None else att.ctypes.data_as(C.POINTER(C.c_ubyte)),
-                          cap, _pi(cv), _pi(co))
-    return cv[:cnt].copy(), co[:cnt].copy()
+                          cap, _pi(cv), _pi(co), _pi(ct))
+    return cv[:cnt].copy(), co[:cnt].copy(), ct[:cnt].copy()
 
 
-def warm_from_previous(cvert, cobs, prev: EnvState):
-    """gamma^0 of the new list: the previous step's gamma of the same (vertex, obstacle)."""
+def warm_from_previous(cvert, cobs, ctri, prev: EnvState):
+    """gamma^0 of the new list: the previous step's gamma of the same (vertex, slot, triangle)."""
     g = np.zeros((len(cvert), 4))
     if len(prev.cvert):
-        key_prev = prev.cvert.astype(np.int64) * 64 + prev.cobs
-        pos = {int(k): i for i, k in enumerate(key_prev)}
-        for i, (v, o) in enumerate(zip(cvert, cobs)):
-            j = pos.get(int(v) * 64 + int(o))
+        pos = {(int(v), int(o), int(t)): i for i, (v, o, t) in enumerate(zip(prev.cvert, prev.cobs, prev.ctri))}
+        for i, key in enumerate(zip(cvert, cobs, ctri)):
+            j = pos.get(tuple(int(x) for x in key))
             if j is not None:
                 g[i] = prev.gamma[j]
     return g
@@ -259,11 +262,11 @@ def step(mesh: Mesh, sc, env, s, st: EnvState, mode=None, metric=0, warm="cold",
     exactly; 2: full Z solved by ``lin_iters`` steps of preconditioned GMRES."""
     dp, ip = params(sc, env, mode, metric, k_max, k_min, k_cap, tol, lin_iters)
     apply_grasp(sc, env, s, st)
-    cvert, cobs = detect(mesh, sc, env, s, st.q, st.v, dp, st.attached)
+    cvert, cobs, ctri = detect(mesh, sc, env, s, st.q, st.v, dp, st.attached)
     if gamma0 is not None:
         gam = _f64(gamma0).reshape(len(cvert), 4).copy()
     elif warm == "prev":
-        gam = warm_from_previous(cvert, cobs, st)
+        gam = warm_from_previous(cvert, cobs, ctri, st)
     else:
         gam = np.zeros((len(cvert), 4))
     K = sc.n_obs
@@ -274,22 +277,25 @@ def step(mesh: Mesh, sc, env, s, st: EnvState, mode=None, metric=0, warm="cold",
                         _pd(_f64(sc.obs_comp[env])), _pd(_f64(sc.poses[env, s])), _pd(_f64(sc.poses[env, s + 1])),
                         _pd(st.q), _pd(st.v), None if q_init is None else _pd(_f64(q_init)), len(cvert),
                         _pi(cvert if len(cvert) else np.zeros(1, np.int32)),
-                        _pi(cobs if len(cobs) else np.zeros(1, np.int32)), _pd(gbuf), C.byref(it), C.byref(rn),
+                        _pi(cobs if len(cobs) else np.zeros(1, np.int32)),
+                        _pi(ctri if len(ctri) else np.zeros(1, np.int32)), _pd(gbuf), C.byref(it), C.byref(rn),
                         _pd(tr))
-    st.cvert, st.cobs, st.gamma = cvert, cobs, gbuf[: len(cvert)].copy()
+    st.cvert, st.cobs, st.ctri, st.gamma = cvert, cobs, ctri, gbuf[: len(cvert)].copy()
     st.iters, st.rncp = it.value, rn.value
     st.trace = tr[: it.value + 1].copy() if trace else None
     return st
 
 
-def residual(mesh: Mesh, sc, env, s, q_t, q, cvert, cobs, gamma):
+def residual(mesh: Mesh, sc, env, s, q_t, q, cvert, cobs, gamma, ctri=None):
     dp = params(sc, env)[0]
+    ctri = np.full(len(cvert), -1, np.int32) if ctri is None else _i32(ctri)
     g = _f64(gamma).reshape(-1, 4) if len(cvert) else np.zeros((1, 4))
     return lib().or_residual(mesh._p, _pd(dp), sc.n_obs, _pi(_i32(sc.obs_type[env])), _pd(_f64(sc.obs_dims[env])),
                              _pd(_f64(sc.obs_comp[env])), _pd(_f64(sc.poses[env, s])), _pd(_f64(sc.poses[env, s + 1])),
                              _pd(_f64(q_t)), _pd(_f64(q)), len(cvert),
                              _pi(_i32(cvert) if len(cvert) else np.zeros(1, np.int32)),
-                             _pi(_i32(cobs) if len(cobs) else np.zeros(1, np.int32)), _pd(g))
+                             _pi(_i32(cobs) if len(cobs) else np.zeros(1, np.int32)),
+                             _pi(ctri if len(ctri) else np.zeros(1, np.int32)), _pd(g))
 
 
 def rollout(sc, env=0, steps=None, mode=None, warm="cold", metric=0, k_max=None, k_min=None, k_cap=None, tol=None,

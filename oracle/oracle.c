@@ -473,28 +473,71 @@ static void tangent_frame(const double *n, double *t1, double *t2) {
 
 double or_fb(double a, double b) { return a + b - sqrt(a * a + b * b); }
 
+static int tri_plane(const double *a, const double *b, const double *c, const double *p, double *nh, double *d,
+                     double *w);
+
+/* triangles f and g share a vertex */
+static int tri_touch(const int *f, const int *g) {
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      if (f[a] == g[b]) return 1;
+  return 0;
+}
+
+/* Self-contact candidate (a reading): vertex p and triangle f of the same
+ * cloth, f not touching any triangle incident to p (topological neighbours
+ * are excluded), with p within tau + margin of f's plane and its projection
+ * inside f up to OR_SELF_BARY in barycentric terms, at q_t or at q~. */
+static int self_candidate(const OrMesh *m, double reach, int p, int f, const double *x0, const double *x1) {
+  const int *t = m->elems + 3 * f;
+  if (t[0] == p || t[1] == p || t[2] == p) return 0;
+  int hit = 0;
+  for (int k = 0; k < 2 && !hit; k++) {
+    const double *x = k == 0 ? x0 : x1;
+    double nh[3], d, w[3];
+    if (!tri_plane(x + 3 * t[0], x + 3 * t[1], x + 3 * t[2], x + 3 * p, nh, &d, w)) continue;
+    hit = fabs(d) < reach && w[0] >= -OR_SELF_BARY && w[1] >= -OR_SELF_BARY && w[2] >= -OR_SELF_BARY;
+  }
+  if (!hit) return 0;
+  for (int g = 0; g < m->ne; g++) {
+    const int *tg = m->elems + 3 * g;
+    if ((tg[0] == p || tg[1] == p || tg[2] == p) && tri_touch(tg, t)) return 0;
+  }
+  return 1;
+}
+
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
-              int cap, int *cvert, int *cobs) {
+              int cap, int *cvert, int *cobs, int *ctri) {
   double h = dp[OR_DP_H], tau = dp[OR_DP_TAU], marg = dp[OR_DP_MARGIN];
+  const int self = dp[OR_DP_SELF] != 0.0 && m->type == OR_TRI;
+  double *xp = (double *)malloc(sizeof(double) * 3 * (m->n > 0 ? m->n : 1));
+  for (int i = 0; i < m->n; i++)
+    for (int c = 0; c < 3; c++) xp[3 * i + c] = q[3 * i + c] + h * v[3 * i + c] + h * h * dp[OR_DP_GX + c];
   int cnt = 0;
   for (int i = 0; i < m->n; i++) {
-    double xp[3];
-    for (int c = 0; c < 3; c++) xp[c] = q[3 * i + c] + h * v[3 * i + c] + h * h * dp[OR_DP_GX + c];
     for (int o = 0; o < K; o++) {
       if (otype[o] == 0) continue;
       double s0 = or_sdf(otype[o], odims + 3 * o, pose_th + 7 * o, q + 3 * i, NULL);
-      double s1 = or_sdf(otype[o], odims + 3 * o, pose_th + 7 * o, xp, NULL);
+      double s1 = or_sdf(otype[o], odims + 3 * o, pose_th + 7 * o, xp + 3 * i, NULL);
       if (fmin(s0, s1) < tau + marg) {
-        if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = o; }
+        if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = o; if (ctri) ctri[cnt] = -1; }
         cnt++;
       }
     }
     if (attached && attached[i]) {
-      if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_GRASP_SLOT; }
+      if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_GRASP_SLOT; if (ctri) ctri[cnt] = -1; }
       cnt++;
     }
+    /* self contacts: the first OR_SELF_MAX candidate triangles in index order */
+    for (int f = 0, ns = 0; self && f < m->ne && ns < OR_SELF_MAX; f++)
+      if (self_candidate(m, tau + marg, i, f, q, xp)) {
+        if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_SELF_SLOT; if (ctri) ctri[cnt] = f; }
+        cnt++;
+        ns++;
+      }
   }
+  free(xp);
   return cnt;
 }
 
@@ -510,19 +553,24 @@ typedef struct {
   double phi[3];
   double DC[9];     /* 3x3 */
   double Dy[9];     /* 3x3 */
+  /* the contact point moves as sum_i w[i] x[vi[i]] (vertex contacts: the
+   * vertex alone; self contacts: +1 on the vertex, minus the barycentric
+   * weights of its closest point on the triangle); meff = 1 / sum w^2 / m */
+  int nv, vi[4];
+  double w[4], meff;
 } Lin;
 
-static void linearize(int type, const double *dims, double comp, const double *pose_t,
-                      const double *pose_th, double tau, double mu, double h, double mv,
-                      const double *x, const double *xt, const double *g, Lin *L) {
-  double n[3], t1[3], t2[3];
-  double sd = or_sdf(type, dims, pose_th, x, n);
+/* The contact law at a linearisation point: unit normal n, gap a (metres),
+ * tangential slip rel over the step (world vector), normal compliance comp,
+ * mass mv that scales the multipliers (y = gamma / mv). */
+static void contact_law(const double *n, double a, const double *rel, double comp, double mu, double h, double mv,
+                        const double *g, Lin *L) {
+  double t1[3], t2[3];
   tangent_frame(n, t1, t2);
   for (int i = 0; i < 3; i++) { L->R[i] = n[i]; L->R[3 + i] = t1[i]; L->R[6 + i] = t2[i]; }
   memset(L->DC, 0, sizeof L->DC);
   memset(L->Dy, 0, sizeof L->Dy);
   /* normal: FB with compliance */
-  double a = sd - tau;
   double yn = g[0] / mv;
   double alpha = comp * mv / (h * h);
   double ae = a + alpha * yn;
@@ -533,12 +581,6 @@ static void linearize(int type, const double *dims, double comp, const double *p
   L->phi[0] = ae + yn - r;
   L->DC[0] = ca;
   L->Dy[0] = ca * alpha + cy;
-  /* tangential slip: displacement relative to the obstacle's material point */
-  double pb[3], xo[3];
-  to_body(pose_th, x, pb);
-  to_world(pose_t, pb, xo);               /* where that material point was at t */
-  double dc[3] = {x[0] - xo[0], x[1] - xo[1], x[2] - xo[2]};
-  double rel[3] = {x[0] - xt[0] - dc[0], x[1] - xt[1] - dc[1], x[2] - xt[2] - dc[2]};
   double s[2] = {dot3(t1, rel), dot3(t2, rel)};
   double yt[2] = {dot3(t1, g + 1) / mv, dot3(t2, g + 1) / mv};
   double rad = mu * (yn > 0 ? yn : 0);
@@ -564,6 +606,79 @@ static void linearize(int type, const double *dims, double comp, const double *p
       }
     if (yn > 0) { L->Dy[3] = -mu * dh[0]; L->Dy[6] = -mu * dh[1]; }
   }
+}
+
+/* vertex against a kinematic obstacle */
+static void linearize(int type, const double *dims, double comp, const double *pose_t,
+                      const double *pose_th, double tau, double mu, double h, double mv,
+                      const double *x, const double *xt, const double *g, Lin *L) {
+  double n[3];
+  double sd = or_sdf(type, dims, pose_th, x, n);
+  /* tangential slip: displacement relative to the obstacle's material point */
+  double pb[3], xo[3];
+  to_body(pose_th, x, pb);
+  to_world(pose_t, pb, xo);               /* where that material point was at t */
+  double dc[3] = {x[0] - xo[0], x[1] - xo[1], x[2] - xo[2]};
+  double rel[3] = {x[0] - xt[0] - dc[0], x[1] - xt[1] - dc[1], x[2] - xt[2] - dc[2]};
+  contact_law(n, sd - tau, rel, comp, mu, h, mv, g, L);
+}
+
+/* Plane of triangle (a, b, c) at x: unit normal nh, signed distance d of the
+ * point p and the barycentric weights w of its projection; 0 if degenerate. */
+static int tri_plane(const double *a, const double *b, const double *c, const double *p, double *nh, double *d,
+                     double *w) {
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double nf[3];
+  cross3(e1, e2, nf);
+  double ar = norm3(nf);
+  if (ar <= 1e-300) return 0;
+  for (int i = 0; i < 3; i++) nh[i] = nf[i] / ar;
+  double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  *d = dot3(nh, ap);
+  double y[3] = {p[0] - *d * nh[0], p[1] - *d * nh[1], p[2] - *d * nh[2]};
+  double ya[3] = {a[0] - y[0], a[1] - y[1], a[2] - y[2]}, yb[3] = {b[0] - y[0], b[1] - y[1], b[2] - y[2]},
+         yc[3] = {c[0] - y[0], c[1] - y[1], c[2] - y[2]}, t[3];
+  cross3(yb, yc, t);
+  w[0] = dot3(nh, t) / ar;
+  cross3(yc, ya, t);
+  w[1] = dot3(nh, t) / ar;
+  w[2] = 1.0 - w[0] - w[1];
+  return 1;
+}
+
+/* Self contact of vertex p with triangle f (a reading: the paper disables
+ * self-collision and describes none).  Frame normal n = the triangle's unit
+ * normal at x, oriented towards the side p was on at t; gap = n.(x_p - c) -
+ * tau with c the projection of p on the triangle's plane, barycentric
+ * weights w; slip = displacement of p relative to the triangle point c over
+ * the step; the multipliers scale with the contact's effective mass
+ * meff = 1 / (1/m_p + sum w_i^2 / m_i). */
+static void linearize_self(const OrMesh *m, double tau, double mu, double h, int p, int f, const double *q,
+                           const double *qt, const double *g, Lin *L) {
+  const int *t = m->elems + 3 * f;
+  double nh[3], d, w[3], nt[3], dt, wt[3];
+  L->nv = 4;
+  L->vi[0] = p;
+  for (int i = 0; i < 3; i++) L->vi[1 + i] = t[i];
+  if (!tri_plane(q + 3 * t[0], q + 3 * t[1], q + 3 * t[2], q + 3 * p, nh, &d, w)) {
+    nh[0] = 0; nh[1] = 0; nh[2] = 1; d = 0; w[0] = w[1] = w[2] = 1.0 / 3.0;
+  }
+  double side = 1.0;
+  if (tri_plane(qt + 3 * t[0], qt + 3 * t[1], qt + 3 * t[2], qt + 3 * p, nt, &dt, wt) && dt < 0) side = -1.0;
+  double n[3] = {side * nh[0], side * nh[1], side * nh[2]};
+  double inv = 1.0 / m->mass[p];
+  L->w[0] = 1.0;
+  for (int i = 0; i < 3; i++) {
+    L->w[1 + i] = -w[i];
+    inv += w[i] * w[i] / m->mass[t[i]];
+  }
+  L->meff = 1.0 / inv;
+  double rel[3];
+  for (int c = 0; c < 3; c++) {
+    rel[c] = q[3 * p + c] - qt[3 * p + c];
+    for (int i = 0; i < 3; i++) rel[c] -= w[i] * (q[3 * t[i] + c] - qt[3 * t[i] + c]);
+  }
+  contact_law(n, side * d - tau, rel, 0.0, mu, h, L->meff, g, L);
 }
 
 /* Gaussian elimination with partial pivoting, in place; x = A^-1 b (size k) */
@@ -608,15 +723,22 @@ static void linearize_grasp(const double *dp, const double *pose_th, const doubl
 static void contact_lin_all(const OrMesh *m, const double *dp, const int *otype, const double *odims,
                             const double *ocomp, const double *pose_t, const double *pose_th,
                             const double *qt, const double *q, int count, const int *cvert,
-                            const int *cobs, const double *cg, Lin *lin) {
+                            const int *cobs, const int *ctri, const double *cg, Lin *lin) {
   for (int i = 0; i < count; i++) {
     int v = cvert[i], o = cobs[i];
-    if (o == OR_GRASP_SLOT) {
-      linearize_grasp(dp, pose_th, q + 3 * v, lin + i);
+    Lin *L = lin + i;
+    if (o == OR_SELF_SLOT) {
+      linearize_self(m, dp[OR_DP_TAU], dp[OR_DP_MU], dp[OR_DP_H], v, ctri[i], q, qt, cg + 4 * i, L);
       continue;
     }
-    linearize(otype[o], odims + 3 * o, ocomp[o], pose_t + 7 * o, pose_th + 7 * o, dp[OR_DP_TAU],
-              dp[OR_DP_MU], dp[OR_DP_H], m->mass[v], q + 3 * v, qt + 3 * v, cg + 4 * i, lin + i);
+    if (o == OR_GRASP_SLOT) linearize_grasp(dp, pose_th, q + 3 * v, L);
+    else
+      linearize(otype[o], odims + 3 * o, ocomp[o], pose_t + 7 * o, pose_th + 7 * o, dp[OR_DP_TAU],
+                dp[OR_DP_MU], dp[OR_DP_H], m->mass[v], q + 3 * v, qt + 3 * v, cg + 4 * i, L);
+    L->nv = 1;
+    L->vi[0] = v;
+    L->w[0] = 1.0;
+    L->meff = m->mass[v];
   }
 }
 
@@ -630,10 +752,10 @@ static double max_abs_phi(int count, const Lin *lin) {
 double or_residual(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
                    const double *ocomp, const double *pose_t, const double *pose_th,
                    const double *q_t, const double *q, int count, const int *cvert, const int *cobs,
-                   const double *cgamma) {
+                   const int *ctri, const double *cgamma) {
   (void)K;
   Lin *lin = (Lin *)malloc(sizeof(Lin) * (count > 0 ? count : 1));
-  contact_lin_all(m, dp, otype, odims, ocomp, pose_t, pose_th, q_t, q, count, cvert, cobs, cgamma, lin);
+  contact_lin_all(m, dp, otype, odims, ocomp, pose_t, pose_th, q_t, q, count, cvert, cobs, ctri, cgamma, lin);
   double r = max_abs_phi(count, lin);
   free(lin);
   return r;
@@ -641,11 +763,23 @@ double or_residual(const OrMesh *m, const double *dp, int K, const int *otype, c
 
 /* J^T gamma for every contact added into f [n][3]: n g_n + P_t g_t (the
  * tangential multiplier is kept as a world vector in the tangent plane) */
-static void add_contact_force(int count, const int *cvert, const Lin *lin, const double *cg, double *f) {
+static void add_contact_force(int count, const Lin *lin, const double *cg, double *f) {
   for (int i = 0; i < count; i++) {
-    const double *R = lin[i].R, *g = cg + 4 * i;
+    const Lin *L = lin + i;
+    const double *R = L->R, *g = cg + 4 * i;
     double yt1 = dot3(R + 3, g + 1), yt2 = dot3(R + 6, g + 1);
-    for (int c = 0; c < 3; c++) f[3 * cvert[i] + c] += R[c] * g[0] + R[3 + c] * yt1 + R[6 + c] * yt2;
+    for (int c = 0; c < 3; c++) {
+      double F = R[c] * g[0] + R[3 + c] * yt1 + R[6 + c] * yt2;
+      for (int a = 0; a < L->nv; a++) f[3 * L->vi[a] + c] += L->w[a] * F;
+    }
+  }
+}
+
+/* J du at contact L: the contact point's share of du [n][3] */
+static void contact_gather(const Lin *L, const double *du, double *out) {
+  for (int c = 0; c < 3; c++) {
+    out[c] = 0;
+    for (int a = 0; a < L->nv; a++) out[c] += L->w[a] * du[3 * L->vi[a] + c];
   }
 }
 
@@ -654,15 +788,17 @@ static void add_contact_force(int count, const int *cvert, const Lin *lin, const
  * with X = M^-1 (lite metric, Sec. IV-B.1) or A^-1 (full metric, Eq. schur),
  * then gamma += m dy (Algorithm 1: lambda^k = lambda^{k-1} + dlambda). */
 static void newton_block(const OrMesh *m, int metric, const double *Ainv, int k, const int *idx,
-                         const int *cvert, const Lin *lin, const double *u, const double *q,
-                         double *cg, double gmax) {
+                         const Lin *lin, const double *u, const double *q, double *cg, double gmax) {
   int N = 3 * k;
   double *Z = (double *)calloc((size_t)N * N, sizeof(double));
   double *rhs = (double *)malloc(sizeof(double) * N);
+  double *dd = (double *)malloc(sizeof(double) * 3 * m->n);
+  for (int i = 0; i < 3 * m->n; i++) dd[i] = u[i] - q[i];
   for (int a = 0; a < k; a++) {
-    int i = idx[a], vi = cvert[i];
+    int i = idx[a];
     const Lin *Li = lin + i;
-    double du[3] = {u[3 * vi] - q[3 * vi], u[3 * vi + 1] - q[3 * vi + 1], u[3 * vi + 2] - q[3 * vi + 2]};
+    double du[3];
+    contact_gather(Li, dd, du);
     double Rdu[3] = {dot3(Li->R, du), dot3(Li->R + 3, du), dot3(Li->R + 6, du)};
     for (int r = 0; r < 3; r++) {
       double s = 0;
@@ -670,14 +806,20 @@ static void newton_block(const OrMesh *m, int metric, const double *Ainv, int k,
       rhs[3 * a + r] = -Li->phi[r] - s;
     }
     for (int b = 0; b < k; b++) {
-      int j = idx[b], vj = cvert[j];
-      double X;
-      if (metric == 0) X = (vi == vj) ? 1.0 / m->mass[vi] : 0.0;
-      else X = Ainv[(size_t)vi * m->n + vj];
+      int j = idx[b];
+      const Lin *Lj = lin + j;
+      /* X = J_a X J_b^T with X = M^-1 (lite) or A^-1 (full), both scalar per vertex pair */
+      double X = 0;
+      for (int s1 = 0; s1 < Li->nv; s1++)
+        for (int s2 = 0; s2 < Lj->nv; s2++) {
+          int va = Li->vi[s1], vb = Lj->vi[s2];
+          double x = metric == 0 ? (va == vb ? 1.0 / m->mass[va] : 0.0) : Ainv[(size_t)va * m->n + vb];
+          X += Li->w[s1] * Lj->w[s2] * x;
+        }
       if (X == 0.0 && a != b) continue;
       double RR[9];
       for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 3; c++) RR[3 * r + c] = dot3(Li->R + 3 * r, lin[j].R + 3 * c) * X * m->mass[vj];
+        for (int c = 0; c < 3; c++) RR[3 * r + c] = dot3(Li->R + 3 * r, Lj->R + 3 * c) * X * Lj->meff;
       for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
           double s = 0;
@@ -697,7 +839,7 @@ static void newton_block(const OrMesh *m, int metric, const double *Ainv, int k,
   gauss_solve(N, Z, rhs);
   for (int a = 0; a < k; a++) {
     int i = idx[a];
-    double mv = m->mass[cvert[i]];
+    double mv = lin[i].meff;
     const double *R = lin[i].R;
     double *g = cg + 4 * i;
     g[0] += mv * rhs[3 * a];
@@ -708,6 +850,7 @@ static void newton_block(const OrMesh *m, int metric, const double *Ainv, int k,
   }
   free(Z);
   free(rhs);
+  free(dd);
 }
 
 /* diag(A^-1), one solve per vertex on first use */
@@ -729,19 +872,21 @@ static const double *ainv_diag(OrMesh *m) {
 /* z = Z x for the full metric, matrix-free: forces m_b R_b^T x_b on the
  * contact vertices, one solve with A, then at each contact a
  * D_C(a) R_a (A^-1 f)_{v_a} + (D_y(a) + damping) x_a. */
-static void full_z_apply(const OrMesh *m, int k, const int *cvert, const Lin *lin, const double *x, double *f,
-                         double *u, double *z) {
+static void full_z_apply(const OrMesh *m, int k, const Lin *lin, const double *x, double *f, double *u,
+                         double *z) {
   memset(f, 0, sizeof(double) * 3 * m->n);
   for (int b = 0; b < k; b++) {
-    int v = cvert[b];
-    double mv = m->mass[v];
-    for (int c = 0; c < 3; c++)
-      f[3 * v + c] += mv * (lin[b].R[c] * x[3 * b] + lin[b].R[3 + c] * x[3 * b + 1] + lin[b].R[6 + c] * x[3 * b + 2]);
+    const Lin *L = lin + b;
+    for (int c = 0; c < 3; c++) {
+      double F = L->meff * (L->R[c] * x[3 * b] + L->R[3 + c] * x[3 * b + 1] + L->R[6 + c] * x[3 * b + 2]);
+      for (int s2 = 0; s2 < L->nv; s2++) f[3 * L->vi[s2] + c] += L->w[s2] * F;
+    }
   }
   or_solve(m, f, u);
   for (int a = 0; a < k; a++) {
     const Lin *L = lin + a;
-    const double *ua = u + 3 * cvert[a];
+    double ua[3];
+    contact_gather(L, u, ua);
     double Ru[3] = {dot3(L->R, ua), dot3(L->R + 3, ua), dot3(L->R + 6, ua)};
     for (int r = 0; r < 3; r++) {
       double s = OR_DAMP * x[3 * a + r];
@@ -759,26 +904,32 @@ static void full_z_apply(const OrMesh *m, int k, const int *cvert, const Lin *li
  * the new Arnoldi vector's norm falls below 1e-6 |rhs| (the Krylov space is
  * exhausted to rounding).  Contacts: the whole list of the environment.
  * The multiplier update is the one of newton_block. */
-static void newton_gmres(OrMesh *m, int k, const int *cvert, const Lin *lin, const double *u, const double *q,
-                         double *cg, double gmax, int mlin) {
+static void newton_gmres(OrMesh *m, int k, const Lin *lin, const double *u, const double *q, double *cg,
+                         double gmax, int mlin) {
   int N = 3 * k;
   if (k == 0 || mlin < 1) return;
   const double *ad = ainv_diag(m);
   double *rhs = (double *)malloc(sizeof(double) * N);
   double *Pinv = (double *)malloc(sizeof(double) * 9 * k);
+  double *dd = (double *)malloc(sizeof(double) * 3 * m->n);
+  for (int i = 0; i < 3 * m->n; i++) dd[i] = u[i] - q[i];
   for (int a = 0; a < k; a++) {
     const Lin *L = lin + a;
-    int v = cvert[a];
-    double du[3] = {u[3 * v] - q[3 * v], u[3 * v + 1] - q[3 * v + 1], u[3 * v + 2] - q[3 * v + 2]};
+    double du[3];
+    contact_gather(L, dd, du);
     double Rdu[3] = {dot3(L->R, du), dot3(L->R + 3, du), dot3(L->R + 6, du)};
     for (int r = 0; r < 3; r++) {
       double s = 0;
       for (int c = 0; c < 3; c++) s += L->DC[3 * r + c] * Rdu[c];
       rhs[3 * a + r] = -L->phi[r] - s;
     }
-    /* diagonal block D_C a_vv m_v + D_y + damping (R R^T = I) and its inverse */
+    /* diagonal block D_C (sum_i w_i^2 a_{v_i v_i}) meff + D_y + damping (R R^T
+     * = I; a reading for contacts over several vertices: the diagonal of
+     * A^-1 only) and its inverse */
+    double av = 0;
+    for (int s2 = 0; s2 < L->nv; s2++) av += L->w[s2] * L->w[s2] * ad[L->vi[s2]];
     double B[9], I[9];
-    for (int t = 0; t < 9; t++) B[t] = L->DC[t] * ad[v] * m->mass[v] + L->Dy[t];
+    for (int t = 0; t < 9; t++) B[t] = L->DC[t] * av * L->meff + L->Dy[t];
     for (int r = 0; r < 3; r++) B[4 * r] += OR_DAMP;
     for (int c = 0; c < 3; c++) {
       double e3[3] = {0, 0, 0}, A3[9];
@@ -807,7 +958,7 @@ static void newton_gmres(OrMesh *m, int k, const int *cvert, const Lin *lin, con
       const double *vj = V + (size_t)j * N;
       for (int a = 0; a < k; a++)
         for (int r = 0; r < 3; r++) t[3 * a + r] = dot3(Pinv + 9 * a + 3 * r, vj + 3 * a);
-      full_z_apply(m, k, cvert, lin, t, f, uu, w);
+      full_z_apply(m, k, lin, t, f, uu, w);
       for (int i = 0; i <= j; i++) {
         const double *vi = V + (size_t)i * N;
         double h = 0;
@@ -852,7 +1003,7 @@ static void newton_gmres(OrMesh *m, int k, const int *cvert, const Lin *lin, con
     free(y); free(V); free(H); free(cs); free(sn); free(gv); free(t); free(w); free(f); free(uu);
   }
   for (int a = 0; a < k; a++) {
-    double mv = m->mass[cvert[a]];
+    double mv = lin[a].meff;
     const double *R = lin[a].R;
     double *g = cg + 4 * a;
     g[0] += mv * dy[3 * a];
@@ -861,13 +1012,13 @@ static void newton_gmres(OrMesh *m, int k, const int *cvert, const Lin *lin, con
     double yt2 = dot3(R + 6, g + 1) + mv * dy[3 * a + 2];
     for (int c = 0; c < 3; c++) g[1 + c] = R[3 + c] * yt1 + R[6 + c] * yt2;
   }
-  free(dy); free(rhs); free(Pinv);
+  free(dy); free(rhs); free(Pinv); free(dd);
 }
 
 int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const int *otype,
                   const double *odims, const double *ocomp, const double *pose_t,
                   const double *pose_th, double *q, double *v, const double *q_init, int count,
-                  const int *cvert, const int *cobs, double *cgamma, int *iters, double *rncp,
+                  const int *cvert, const int *cobs, const int *ctri, double *cgamma, int *iters, double *rncp,
                   double *trace) {
   (void)K;
   int n = m->n;
@@ -907,7 +1058,7 @@ int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const
   int k = 0;
   double r = 0;
   for (;;) {
-    contact_lin_all(m, dp, otype, odims, ocomp, pose_t, pose_th, qt, qc, count, cvert, cobs, cgamma, lin);
+    contact_lin_all(m, dp, otype, odims, ocomp, pose_t, pose_th, qt, qc, count, cvert, cobs, ctri, cgamma, lin);
     r = max_abs_phi(count, lin);
     if (trace) trace[k] = r;
     if (mode == 0) { if (k >= kmax) break; }
@@ -917,20 +1068,20 @@ int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const
     or_assemble_b(m, qp, p, b);
     /* g = b + J^T gamma^{k-1};  u = A^-1 g */
     memcpy(g, b, vb);
-    add_contact_force(count, cvert, lin, cgamma, g);
+    add_contact_force(count, lin, cgamma, g);
     or_solve(m, g, u);
     /* dgamma = Z^-1 (h - J u),  gamma^k = gamma^{k-1} + dgamma */
     if (metric == 0) {
       for (int t = 0; t < ngrp; t++)
-        newton_block(m, 0, NULL, grp[t + 1] - grp[t], all + grp[t], cvert, lin, u, qc, cgamma, gmax);
+        newton_block(m, 0, NULL, grp[t + 1] - grp[t], all + grp[t], lin, u, qc, cgamma, gmax);
     } else if (metric == 1 && count > 0) {
-      newton_block(m, 1, Ainv, count, all, cvert, lin, u, qc, cgamma, gmax);
+      newton_block(m, 1, Ainv, count, all, lin, u, qc, cgamma, gmax);
     } else if (metric == 2) {
-      newton_gmres((OrMesh *)m, count, cvert, lin, u, qc, cgamma, gmax, ip[OR_IP_LINIT]);
+      newton_gmres((OrMesh *)m, count, lin, u, qc, cgamma, gmax, ip[OR_IP_LINIT]);
     }
     /* q^k = A^-1 (b + J^T gamma^k) */
     memcpy(g, b, vb);
-    add_contact_force(count, cvert, lin, cgamma, g);
+    add_contact_force(count, lin, cgamma, g);
     or_solve(m, g, qc);
     k++;
   }

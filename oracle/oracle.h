@@ -50,13 +50,20 @@ typedef struct OrMesh OrMesh;
 #define OR_DP_MU 8
 #define OR_DP_GRASP_OBS 9 /* obstacle carrying the grasp anchor (as a double), -1: no grasp */
 #define OR_DP_ANCHOR 10   /* 10..12: anchor point in that obstacle's frame */
-#define OR_DP_SIZE 13
+#define OR_DP_SELF 13 /* nonzero: cloth self-collision (vertex against triangle) */
+#define OR_DP_SIZE 14
 
 /* Bilateral grasp (appendix, Bilateral Constraint for Cloth Control): a
  * grasped vertex i carries the equality C = x_i - p_grip = 0 with p_grip the
  * anchor at the gripper's pose at t+h.  It sits in the contact list with the
  * obstacle slot OR_GRASP_SLOT (after every obstacle, so lists stay sorted). */
 #define OR_GRASP_SLOT 8
+/* Self contact of a cloth vertex with a triangle of the same cloth (contact
+ * list slot OR_SELF_SLOT, triangle in ctri): at most OR_SELF_MAX per vertex,
+ * projections inside the triangle up to OR_SELF_BARY (barycentric). */
+#define OR_SELF_SLOT 9
+#define OR_SELF_MAX 4
+#define OR_SELF_BARY 0.1
 #define OR_NDP 9
 /* ip[] (integer parameters) */
 #define OR_IP_KMAX 0
@@ -84,22 +91,24 @@ void or_closest_rotation(int cols, const double *F, double *R); /* 3x2 or 3x3, r
 double or_sdf(int type, const double *dims, const double *pose, const double *x, double *nrm);
 
 /* attached: [n] grasp flags (or NULL); a flagged vertex gets an OR_GRASP_SLOT
- * entry after its obstacle contacts */
+ * entry after its obstacle contacts, then its self contacts (OR_SELF_SLOT,
+ * triangle in ctri; -1 for the other rows; ctri may be NULL) when
+ * dp[OR_DP_SELF] is set */
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
-              int cap, int *cvert, int *cobs);
+              int cap, int *cvert, int *cobs, int *ctri);
 
 int or_solve_step(const OrMesh *m, const double *dp, const int *ip, int K, const int *otype,
                   const double *odims, const double *ocomp, const double *pose_t,
                   const double *pose_th, double *q, double *v, const double *q_init, int count,
-                  const int *cvert, const int *cobs, double *cgamma, int *iters, double *rncp,
-                  double *trace);
+                  const int *cvert, const int *cobs, const int *ctri, double *cgamma, int *iters,
+                  double *rncp, double *trace);
 
 /* NCP residual of (q, gamma) for a given contact list (max-norm, metres) */
 double or_residual(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
                    const double *ocomp, const double *pose_t, const double *pose_th,
                    const double *q_t, const double *q, int count, const int *cvert, const int *cobs,
-                   const double *cgamma);
+                   const int *ctri, const double *cgamma);
 
 /* fischer-burmeister value, exported for the closed-form pins */
 double or_fb(double a, double b);

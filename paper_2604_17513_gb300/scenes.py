@@ -565,3 +565,47 @@ def towel_views(seed: int = 4, n_envs: int = 128, n_side: int = 181, side: float
         pc = (ctr[0] + g.uniform(-0.02, 0.02), ctr[1] + g.uniform(-0.02, 0.02), g.uniform(*cam_height))
         cam_poses[e] = _pose(pc, q)
     return RayScene("towel_views", verts, tris, obs_type, obs_dims, obs_poses, cam_poses, cam)
+
+
+def cloth_stack_drop(seed: int = 5, n_envs: int = 8, n_side: int = 16, side: float = 0.25, steps: int = 60,
+                     k_max: int = 10, drop=(0.004, 0.012)) -> Scene:
+    """A small cloth dropped onto a larger one lying on the ground: both are
+    components of one mesh, so they meet through cloth self-collision.
+
+    Base: n_side x n_side grid of side ``side`` on the ground 1 mm up.  Top:
+    a (n_side/2) x (n_side/2) grid of side side/2, turned by U[0, 90] degrees
+    about z, its centre U[-side/8, side/8] off the base's, released flat at
+    U[drop] m above the base (at rest).  Self-collision on
+    (meta["self_collision"]), ground plane only, mu ~ U[0.2, 0.6],
+    h = 1/100; the same areal mass and stiffness as the other cloths.
+    """
+    rb, tb = cloth_grid(n_side, n_side, side)
+    m_side = max(n_side // 2, 2)
+    rt, tt = cloth_grid(m_side, m_side, side / 2)
+    nb = len(rb)
+    rest = np.concatenate([rb, rt + [0.0, 0.0, 0.05]])   # rest shapes are flat; the offset only separates them
+    tris = np.concatenate([tb, tt + nb]).astype(np.int32)
+    n = len(rest)
+    mass = np.concatenate([np.full(nb, 0.1 * side * side / 0.25 / nb),
+                           np.full(len(rt), 0.1 * (side / 2) ** 2 / 0.25 / len(rt))])
+    tau = 1e-3
+    q0 = np.zeros((n_envs, n, 3))
+    K = 1
+    obs_type = np.full((n_envs, K), PLANE, np.int32)
+    obs_dims = np.zeros((n_envs, K, 3))
+    mu = np.zeros(n_envs)
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    poses[:, :, 0] = _pose((0, 0, 0))
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        mu[e] = g.uniform(0.2, 0.6)
+        ang = g.uniform(0, 0.5 * np.pi)
+        ca, sa = np.cos(ang), np.sin(ang)
+        off = g.uniform(-side / 8, side / 8, 2)
+        top = rt[:, :2] @ np.array([[ca, sa], [-sa, ca]]) + off
+        z_top = 2 * tau + g.uniform(*drop)
+        q0[e, :nb] = np.c_[rb[:, :2], np.full(nb, tau)]
+        q0[e, nb:] = np.c_[top, np.full(len(rt), z_top)]
+    return Scene("cloth_stack_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0), mu, np.ones(n_envs),
+                 obs_type, obs_dims, np.zeros((n_envs, K)), poses, h=0.01, k_max=k_max, thickness=tau, steps=steps,
+                 meta={"self_collision": True})

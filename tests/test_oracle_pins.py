@@ -471,3 +471,129 @@ def test_grasp_momentum_balance_and_release():
         if s >= 40:
             assert len(st.cvert) == 0 and not st.attached.any()
             assert np.abs(lhs).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# cloth self-collision (vertex against triangle; the paper disables it and
+# describes no method, so these pin the reading's geometry and mechanics)
+# ---------------------------------------------------------------------------
+def _stack(self_collision=True, n_envs=1, n_side=16):
+    sc = scenes.cloth_stack_drop(n_envs=n_envs, n_side=n_side, steps=30)
+    if not self_collision:
+        sc.meta = {}
+    return sc
+
+
+def _self_candidates_numpy(sc, q0, q1, reach):
+    """Independent detection: each triangle's plane by SVD of its centred
+    corners, barycentric coordinates of the projection by pseudo-inverse,
+    topological neighbours as sets, both configurations, the first SELF_MAX
+    triangles per vertex."""
+    tris = sc.elems
+    ring = [set() for _ in range(sc.n_verts)]
+    for t in tris:
+        for a in t:
+            ring[a].update(int(x) for x in t)
+    hit = np.zeros((sc.n_verts, len(tris)), bool)
+    for x in (q0, q1):
+        P = x[tris]                                        # [T][3][3]
+        nrm = np.linalg.svd(P - P.mean(1, keepdims=True))[2][:, 2]   # [T][3]
+        E = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]], -1)      # [T][3][2]
+        pinv = np.linalg.pinv(E)                           # [T][2][3]
+        rel = x[:, None, :] - P[None, :, 0]                # [n][T][3]
+        d = (rel * nrm[None]).sum(-1)
+        y = rel - d[..., None] * nrm[None]
+        w12 = np.einsum("tij,ntj->nti", pinv, y)
+        w = np.concatenate([1 - w12.sum(-1, keepdims=True), w12], -1)
+        hit |= (np.abs(d) < reach) & (w.min(-1) >= -0.1)
+    out = set()
+    for p in range(sc.n_verts):
+        found = [f for f in np.nonzero(hit[p])[0] if not any(int(v) in ring[p] for v in tris[f])]
+        out.update((p, int(f)) for f in found[:oracle.SELF_MAX])
+    return out
+
+
+def test_self_detection_matches_brute_force():
+    """Self-contact candidates at the step start equal an independent
+    computation of the rule (plane distance < tau + margin, projection inside
+    the triangle up to 0.1, no triangle touching the vertex's own triangles,
+    at q_t or q~, at most SELF_MAX per vertex in triangle order)."""
+    sc = _stack()
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    for s in range(3):
+        oracle.step(mesh, sc, 0, s, st, metric=2)
+    dp = oracle.params(sc, 0)[0]
+    cv, co, ct = oracle.detect(mesh, sc, 0, 3, st.q, st.v, dp)
+    got = {(int(v), int(t)) for v, o, t in zip(cv, co, ct) if o == oracle.SELF_SLOT}
+    qp = st.q + sc.h * st.v + sc.h ** 2 * np.asarray(sc.gravity)
+    ref = _self_candidates_numpy(sc, st.q, qp, sc.thickness + sc.margin)
+    assert len(got) > 100 and got == ref
+    assert all(t == -1 for o, t in zip(co, ct) if o != oracle.SELF_SLOT)
+
+
+@pytest.mark.parametrize("metric", [0, 2])
+def test_self_contact_forces_are_internal(metric):
+    """Self contacts push the vertex and the triangle's points equally and
+    oppositely (weights 1 and -w, sum zero): sum_i m_i (q_i - q~_i) equals
+    the world-frame sum of the ground multipliers alone (to 1e-12), at any
+    iteration count, while self contacts carry force."""
+    sc = _stack()
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    m = sc.mass[:, None]
+    carried = 0
+    for s in range(8):
+        qt, vt = st.q.copy(), st.v.copy()
+        oracle.step(mesh, sc, 0, s, st, metric=metric)
+        qtil = qt + sc.h * vt + sc.h ** 2 * np.asarray(sc.gravity)
+        lhs = (m * (st.q - qtil)).sum(0)
+        ground = st.cobs == 0
+        F = st.gamma[ground, 0].sum() * np.array([0, 0, 1.0]) + st.gamma[ground, 1:].sum(0)
+        assert np.abs(lhs - F).max() <= 1e-12, (s, lhs, F)
+        carried += (st.gamma[st.cobs == oracle.SELF_SLOT, 0] > 0).sum()
+    assert carried > 100
+
+
+def test_stacked_cloth_rests_on_the_base():
+    """With self-collision (full metric, 10 GMRES iterations) the dropped
+    piece comes to rest one thickness tau above the base; without it the
+    piece falls through to the ground."""
+    nb = 256
+    for on in (True, False):
+        sc = _stack(self_collision=on)
+        mesh = oracle.Mesh.from_scene(sc, 0)
+        st = oracle.EnvState(sc.q0[0], sc.v0[0])
+        for s in range(15):
+            oracle.step(mesh, sc, 0, s, st, metric=2)
+        zb, zt = st.q[:nb, 2], st.q[nb:, 2]
+        if on:
+            assert np.abs(zb - sc.thickness).max() < 2e-4
+            assert np.abs(zt - 2 * sc.thickness).max() < 2e-4, (zt.min(), zt.max())
+        else:
+            assert np.abs(zt - sc.thickness).max() < 2e-4
+
+
+def test_self_contact_complementarity_at_convergence():
+    """Full-metric Newton steps (GMRES to 32 iterations) to r_ncp <= 1e-9 on a
+    10x10 base with a 5x5 piece: every self contact
+    has gap >= -1e-8, lambda_n >= 0 and |lambda_n gap| tiny, and the friction
+    multiplier lies in the cone."""
+    sc = _stack(n_side=10)
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    for s in range(6):
+        oracle.step(mesh, sc, 0, s, st, metric=2, lin_iters=32, mode=1, tol=1e-9, k_cap=300)
+    assert st.rncp <= 1e-9
+    sel = np.nonzero(st.cobs == oracle.SELF_SLOT)[0]
+    assert len(sel) > 20
+    tri = sc.elems
+    for i in sel:
+        p, f = st.cvert[i], st.ctri[i]
+        a, b, c = st.q[tri[f]]
+        nrm = np.cross(b - a, c - a)
+        nrm /= np.linalg.norm(nrm)
+        gap = abs(nrm @ (st.q[p] - a)) - sc.thickness
+        g = st.gamma[i]
+        assert gap >= -1e-8 and g[0] >= -1e-15 and abs(g[0] * gap) <= 1e-14
+        assert np.linalg.norm(g[1:]) <= sc.mu[0] * max(g[0], 0) + 1e-13   # 1e-9 m x effective mass
