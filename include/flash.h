@@ -52,6 +52,8 @@ typedef int32_t flash_status;
 #define FLASH_OBS_BOX 3    /* dims = half extents */
 #define FLASH_MAX_OBS 8
 #define FLASH_GRASP_SLOT FLASH_MAX_OBS /* contact-list obstacle slot of grasp rows */
+#define FLASH_SELF_SLOT (FLASH_MAX_OBS + 1) /* contact-list slot of cloth self contacts */
+#define FLASH_SELF_MAX 4 /* self contacts per vertex at most */
 
 #define FLASH_MODE_FIXED 0 /* exactly k_max local-global iterations per step */
 #define FLASH_MODE_TOL 1   /* iterate until r_ncp <= tol_ncp (k >= k_min) or k_cap */
@@ -82,7 +84,17 @@ typedef int32_t flash_status;
  * metric, 1..32 (0 = 10, the paper's parameter table): each Newton step runs
  * that many GMRES steps on Z dy = rhs over all contacts of an environment,
  * preconditioned by Z's 3x3 diagonal blocks; every GMRES step costs one
- * application of A^-1 to all environments. */
+ * application of A^-1 to all environments.
+ * self_collide: 1 turns on cloth self-collision for triangle meshes (needs
+ * FLASH_METRIC_FULL): a vertex p and a triangle f of the same mesh that
+ * touches none of p's own triangles are in contact when p lies within
+ * thickness + margin of f's plane with its projection inside f up to 0.1 in
+ * barycentric terms (at q_t or q~); the first FLASH_SELF_MAX such triangles
+ * (in index order) per vertex get a row (slot FLASH_SELF_SLOT) whose normal
+ * is f's, oriented towards the side p was on at the step start, gap =
+ * distance to the plane - thickness, the contact point moving as p minus
+ * the barycentric combination of f's corners.  The paper disables
+ * self-collision and describes no method; this is the library's reading. */
 typedef struct {
   double h;
   double gravity[3];
@@ -98,7 +110,7 @@ typedef struct {
   int32_t eager;
   int32_t metric;
   int32_t lin_iters;
-  int32_t reserved[1];
+  int32_t self_collide;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -255,6 +267,9 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs,
                                 float *gamma, void *stream);
 int32_t flash_contact_cap(const flash_scene *s);
+/* Triangle of each row of the last step's contact lists: device int32
+ * [N][cap] (-1 for rows that are not self contacts). */
+flash_status flash_get_contact_tris(const flash_scene *s, int32_t *tri, void *stream);
 
 /* Per-environment statistics of the last step: iterations used and the NCP
  * residual max_j |phi_j| (m) of the final iterate; device int32/float32 [N]. */

@@ -372,6 +372,11 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pgam, cc * 4));
   FLASH_CUDA_TRY(dalloc(s, &g.gflag, (size_t)g.N * np));
+  g.self = s->d.self_collide && m.type == FLASH_TRI ? 1 : 0;
+  if (g.self) {
+    FLASH_CUDA_TRY(dalloc(s, &g.ctri, cc));
+    FLASH_CUDA_TRY(dalloc(s, &g.pctri, cc));
+  }
   // local pass shared memory: q and r ([3][ns] each, ns = n rounded up to 4),
   // then the element forces [ev + 1][3] (last row zero) and the CSR tables
   const size_t ns = ((size_t)n + 3) & ~(size_t)3;
@@ -599,6 +604,9 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
   if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
   if (desc->metric != FLASH_METRIC_LITE && desc->metric != FLASH_METRIC_FULL) return fail(FLASH_EINVAL, "invalid metric");
   if (desc->lin_iters < 0 || desc->lin_iters > kMaxLinIters) return fail(FLASH_EINVAL, "lin_iters must be 0..32");
+  if (desc->self_collide != 0 && desc->self_collide != 1) return fail(FLASH_EINVAL, "self_collide must be 0 or 1");
+  if (desc->self_collide && desc->metric != FLASH_METRIC_FULL)
+    return fail(FLASH_EINVAL, "cloth self-collision needs the full metric (FLASH_METRIC_FULL)");
   flash_scene *s = new flash_scene();
   s->d = *desc;
   if (s->d.lin_iters == 0) s->d.lin_iters = 10;
@@ -709,6 +717,7 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
       const size_t cc = (size_t)g.N * s->cap;
       g.fm_m = m;
       FLASH_CUDA_TRY(dalloc(s, &g.fm_lin, cc * kFmLinFloats));
+      if (g.self) FLASH_CUDA_TRY(dalloc(s, &g.fm_w, cc * 4));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_V, (size_t)(m + 1) * 3 * cc));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_H, (size_t)g.N * (m + 1) * m));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_cs, (size_t)g.N * m));
@@ -1248,6 +1257,22 @@ flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *v
       if (gamma)
         FLASH_CUDA_TRY(cudaMemcpyAsync(gamma + e * cs * 4, g.pgam + l * cs * 4, sizeof(float) * cs * 4,
                                        cudaMemcpyDeviceToDevice, st));
+    }
+  return FLASH_OK;
+}
+
+flash_status flash_get_contact_tris(const flash_scene *s, int32_t *tri, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (!tri) return fail(FLASH_EINVAL, "tri is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cs = (size_t)s->cap;
+  for (auto &g : s->groups)
+    for (int l = 0; l < g.N; l++) {
+      const int e = g.env_ids[l];
+      if (g.self)
+        FLASH_CUDA_TRY(cudaMemcpyAsync(tri + e * cs, g.pctri + l * cs, sizeof(int) * cs, cudaMemcpyDeviceToDevice, st));
+      else
+        FLASH_CUDA_TRY(cudaMemsetAsync(tri + e * cs, 0xff, sizeof(int) * cs, st));
     }
   return FLASH_OK;
 }

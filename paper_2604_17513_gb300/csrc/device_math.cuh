@@ -336,17 +336,15 @@ __device__ __forceinline__ void linearize_contact(int type, const float *dims, f
 }
 
 // linearize_contact with matrix poses (identical contact law)
-__device__ __forceinline__ void linearize_contact_m(int type, const float *dims, float comp, const PoseM &P, float tau,
-                                                    float mu, float h, float mv, V3 x, V3 xt, const float *g,
-                                                    ContactLin &L) {
-  V3 n, t1, t2;
-  float sd = obstacle_sdf_m(type, dims, P, x, n);
-  tangent_basis(n, t1, t2);
+// The contact law at a linearisation point (unit normal n with its tangent
+// basis t1, t2; gap a; slip rel over the step; normal compliance comp; mass mv
+// that scales the multipliers, y = gamma / mv).
+__device__ __forceinline__ void contact_law(V3 n, V3 t1, V3 t2, float a, V3 rel, float comp, float mu, float h,
+                                            float mv, const float *g, ContactLin &L) {
   L.R[0] = n.x; L.R[1] = n.y; L.R[2] = n.z;
   L.R[3] = t1.x; L.R[4] = t1.y; L.R[5] = t1.z;
   L.R[6] = t2.x; L.R[7] = t2.y; L.R[8] = t2.z;
   const float inv_m = 1.f / mv;
-  const float a = sd - tau;
   L.gap = a;
   const float yn = g[0] * inv_m;
   const float alpha = comp * mv / (h * h);
@@ -364,10 +362,6 @@ __device__ __forceinline__ void linearize_contact_m(int type, const float *dims,
   L.phi[0] = ae + yn - r;
   L.cn = ca;
   L.dn = ca * alpha + cy;
-  // slip relative to the obstacle's material point over the step
-  const V3 xo = {P.S[0] * x.x + P.S[1] * x.y + P.S[2] * x.z + P.s[0], P.S[3] * x.x + P.S[4] * x.y + P.S[5] * x.z + P.s[1],
-                 P.S[6] * x.x + P.S[7] * x.y + P.S[8] * x.z + P.s[2]};
-  const V3 rel = xo - xt;
   const float s0 = dot(t1, rel), s1 = dot(t2, rel);
   const V3 gt = {g[1], g[2], g[3]};
   const float y0 = dot(t1, gt) * inv_m, y1 = dot(t2, gt) * inv_m;
@@ -396,6 +390,18 @@ __device__ __forceinline__ void linearize_contact_m(int type, const float *dims,
     if (yn > 0.f) { L.dtn[0] = -mu * h0; L.dtn[1] = -mu * h1; }
     else { L.dtn[0] = 0.f; L.dtn[1] = 0.f; }
   }
+}
+
+__device__ __forceinline__ void linearize_contact_m(int type, const float *dims, float comp, const PoseM &P, float tau,
+                                                    float mu, float h, float mv, V3 x, V3 xt, const float *g,
+                                                    ContactLin &L) {
+  V3 n, t1, t2;
+  const float sd = obstacle_sdf_m(type, dims, P, x, n);
+  tangent_basis(n, t1, t2);
+  // slip relative to the obstacle's material point over the step
+  const V3 xo = {P.S[0] * x.x + P.S[1] * x.y + P.S[2] * x.z + P.s[0], P.S[3] * x.x + P.S[4] * x.y + P.S[5] * x.z + P.s[1],
+                 P.S[6] * x.x + P.S[7] * x.y + P.S[8] * x.z + P.s[2]};
+  contact_law(n, t1, t2, sd - tau, xo - xt, comp, mu, h, mv, g, L);
 }
 
 }  // namespace flash

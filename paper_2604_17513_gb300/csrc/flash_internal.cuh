@@ -88,6 +88,10 @@ struct Group {
   int *pcount = nullptr, *pvert = nullptr, *pobs = nullptr;
   float *pgam = nullptr;
   uint8_t *gflag = nullptr;               // [N][n_pad] grasped vertices (S_grip)
+  // cloth self-collision (triangle meshes of a scene with self_collide)
+  int self = 0;
+  int *ctri = nullptr, *pctri = nullptr;  // [N][cap] triangle of each self-contact row, -1 otherwise
+  float *fm_w = nullptr;                  // [N][cap][4] full metric: barycentric weights and effective mass
   int3 *rtris = nullptr;                  // [rT] surface triangles for ray casting
   int rT = 0;
   int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner

@@ -28,6 +28,9 @@ struct GroupView {
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
   uint8_t *gflag;                // [N][n_pad] grasped vertices
+  int self;                      // cloth self-collision on
+  int *ctri, *pctri;             // [N][cap] triangle of self-contact rows
+  float *fm_w;                   // [N][cap][4] full metric: weights and effective mass of self rows
   const uint16_t *coff, *cidx;   // CSR vertex -> element slots e * vpe + a
   const int2 *kb;                // bending operator, off-diagonal entries, slot-major
   int ev, deg_b;
@@ -65,6 +68,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch; v.gflag = g.gflag;
+  v.self = g.self; v.ctri = g.ctri; v.pctri = g.pctri; v.fm_w = g.fm_w;
   v.c_in_smem = g.c_in_smem ? 1 : 0;
   v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
   v.fm_lin = g.fm_lin; v.fm_V = g.fm_V; v.fm_H = g.fm_H; v.fm_cs = g.fm_cs; v.fm_sn = g.fm_sn; v.fm_g = g.fm_g;
@@ -143,6 +147,44 @@ __device__ void block_max3(float &x0, float &x1, float &x2, float (*sh)[3]) {
 // ---------------------------------------------------------------------------
 // begin of step: q_t, q~, detection, gamma^0
 // ---------------------------------------------------------------------------
+// Self-contact candidate (cloth self-collision, the library's reading; the
+// paper disables it): vertex p and triangle f (not touching a triangle of
+// p), p within `reach` of f's plane with its projection inside f up to
+// kSelfBary (barycentric), at q_t or at q~.
+constexpr float kSelfBary = 0.1f;
+
+__device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f, float reach, const float *x0,
+                                               const float *x1) {
+  const int np = G.n_pad;
+  const int t0 = G.elems[4 * f], t1 = G.elems[4 * f + 1], t2 = G.elems[4 * f + 2];
+  if (t0 == p || t1 == p || t2 == p) return false;
+  bool hit = false;
+  for (int k = 0; k < 2 && !hit; k++) {
+    const float *x = k == 0 ? x0 : x1;
+    const V3 A = v3(x[t0], x[np + t0], x[2 * np + t0]), B = v3(x[t1], x[np + t1], x[2 * np + t1]);
+    const V3 Cc = v3(x[t2], x[np + t2], x[2 * np + t2]), P = v3(x[p], x[np + p], x[2 * np + p]);
+    const V3 nf = cross(B - A, Cc - A);
+    const float ar = norm(nf);
+    if (!(ar > 0.f)) continue;
+    const V3 nh = (1.f / ar) * nf;
+    const float d = dot(nh, P - A);
+    const V3 y = P - d * nh;
+    const float wa = dot(nh, cross(B - y, Cc - y)) / ar, wb = dot(nh, cross(Cc - y, A - y)) / ar;
+    const float wc = 1.f - wa - wb;
+    hit = fabsf(d) < reach && wa >= -kSelfBary && wb >= -kSelfBary && wc >= -kSelfBary;
+  }
+  if (!hit) return false;
+  // f must not touch a triangle of p (topological neighbours never collide)
+  for (int sl = G.coff[p]; sl < G.coff[p + 1]; sl++) {
+    const int g = G.cidx[sl] / 3;
+    for (int c = 0; c < 3; c++) {
+      const int u = G.elems[4 * g + c];
+      if (u == t0 || u == t1 || u == t2) return false;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ void begin_body(const GroupView &G, const int l, const EnvView &V, StepArgs a) {
   __shared__ int sh_scan[32];
   __shared__ int s_type[FLASH_MAX_OBS];
@@ -172,33 +214,53 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     grad2 = an[3] * an[3];
   }
   uint8_t *gflag = G.gflag + (size_t)l * np;
-  __syncthreads();
   const float h = a.h, h2 = a.h * a.h;
   const float gv[3] = {a.gx, a.gy, a.gz};
+  if (G.self) {
+    // self contacts test triangles against q_t and q~ of every vertex: both
+    // are written first
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      for (int c = 0; c < 3; c++) {
+        const float qq = q[c * np + i], pp = qq + h * v[c * np + i] + h2 * gv[c];
+        qt[c * np + i] = qq;
+        qp[c * np + i] = pp;
+        q[c * np + i] = pp;   // q^0 = q~
+        f[c * np + i] = 0.f;
+      }
+  }
+  __syncthreads();
   int base = 0;
   int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
+  int *ctri = G.self ? G.ctri + (size_t)l * G.cap : nullptr;
+  const float reach = a.tau + a.margin;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     int i = i0 + threadIdx.x;
     unsigned mask = 0;
+    int sf[FLASH_SELF_MAX];
+    int ns = 0;
     if (i < n) {
+      float x0[3], x1[3];
+      if (G.self) {
+        for (int c = 0; c < 3; c++) { x0[c] = qt[c * np + i]; x1[c] = qp[c * np + i]; }
+      } else {
+        for (int c = 0; c < 3; c++) {
+          float qq = q[c * np + i], vv = v[c * np + i];
+          float pp = qq + h * vv + h2 * gv[c];
+          qt[c * np + i] = qq;
+          qp[c * np + i] = pp;
+          q[c * np + i] = pp;   // q^0 = q~
+          f[c * np + i] = 0.f;
+          x0[c] = qq;
+          x1[c] = pp;
+        }
+      }
       if (gst == 1) {
-        const V3 d = v3(q[i], q[np + i], q[2 * np + i]) - gp;
+        const V3 d = v3(x0[0], x0[1], x0[2]) - gp;
         gflag[i] = dot(d, d) <= grad2 ? 1 : 0;
       } else if (gst == 3) {
         gflag[i] = 0;
       }
       if (gflag[i]) mask |= 1u << FLASH_GRASP_SLOT;
-      float x0[3], x1[3];
-      for (int c = 0; c < 3; c++) {
-        float qq = q[c * np + i], vv = v[c * np + i];
-        float pp = qq + h * vv + h2 * gv[c];
-        qt[c * np + i] = qq;
-        qp[c * np + i] = pp;
-        q[c * np + i] = pp;   // q^0 = q~
-        f[c * np + i] = 0.f;
-        x0[c] = qq;
-        x1[c] = pp;
-      }
       for (int o = 0; o < a.K; o++) {
         if (s_type[o] == FLASH_OBS_NONE) continue;
         V3 nn;
@@ -206,17 +268,24 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         float s1 = obstacle_sdf(s_type[o], s_dims[o], s_pose[o], v3(x1[0], x1[1], x1[2]), nn);
         if (fminf(s0, s1) < a.tau + a.margin) mask |= 1u << o;
       }
+      if (G.self)   // the first FLASH_SELF_MAX candidate triangles in index order
+        for (int t = 0; t < G.E && ns < FLASH_SELF_MAX; t++)
+          if (self_candidate(G, i, t, reach, qt, qp)) sf[ns++] = t;
     }
-    int cnt = __popc(mask), total;
+    int cnt = __popc(mask) + ns, total;
     int off = block_exclusive_scan(cnt, &total, sh_scan);
     int pos = base + off;
     for (int o = 0; o < a.K; o++)
       if (mask & (1u << o)) {
-        if (pos < G.cap) { cvert[pos] = i; cobs[pos] = o; }
+        if (pos < G.cap) { cvert[pos] = i; cobs[pos] = o; if (ctri) ctri[pos] = -1; }
         pos++;
       }
     if (mask & (1u << FLASH_GRASP_SLOT)) {   // the grasp row follows the obstacle rows
-      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_GRASP_SLOT; }
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_GRASP_SLOT; if (ctri) ctri[pos] = -1; }
+      pos++;
+    }
+    for (int k = 0; k < ns; k++) {           // then the self contacts
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_SELF_SLOT; ctri[pos] = sf[k]; }
       pos++;
     }
     base += total;
@@ -232,15 +301,19 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   float *gam = G.cgam + (size_t)l * G.cap * 4;
   const int pc = G.pcount[l];
   const int *pv = G.pvert + (size_t)l * G.cap, *po = G.pobs + (size_t)l * G.cap;
+  const int *pt = G.self ? G.pctri + (size_t)l * G.cap : nullptr;
   const float *pg = G.pgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
     if (a.warm == FLASH_WARM_PREV && pc > 0) {
-      int key = cvert[j] * (FLASH_GRASP_SLOT + 1) + cobs[j];
+      // previous list sorted by (vertex, slot, triangle)
+      const long long key = (long long)(cvert[j] * (FLASH_SELF_SLOT + 1) + cobs[j]) * 0x100000000LL +
+                            (ctri ? ctri[j] + 1 : 0);
       int lo = 0, hi = pc - 1;
-      while (lo <= hi) {  // previous list is sorted by (vertex, obstacle)
+      while (lo <= hi) {
         int mid = (lo + hi) >> 1;
-        int km = pv[mid] * (FLASH_GRASP_SLOT + 1) + po[mid];
+        const long long km = (long long)(pv[mid] * (FLASH_SELF_SLOT + 1) + po[mid]) * 0x100000000LL +
+                             (pt ? pt[mid] + 1 : 0);
         if (km == key) {
           for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
           break;
@@ -344,6 +417,72 @@ __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs
     return;
   }
   linearize_contact_m(O.type[o], O.dims[o], O.comp[o], O.pm[o], a.tau, mu, a.h, mv, x, xt, g, L);
+}
+
+// Self contact of vertex p with triangle f (cloth self-collision, the
+// library's reading): positions x of the iterate ([3][ld]) and xt of the step
+// start ([3][n_pad]).  Frame normal = f's unit normal, oriented towards the
+// side p was on at q_t; gap = distance to the plane - tau; the contact point
+// moves as p minus the barycentric combination w of f's corners (p's
+// projection), effective mass meff = 1 / (1/m_p + sum w^2 / m_i); slip =
+// displacement of p relative to that point over the step.
+__device__ __noinline__ void lin_self(const GroupView &G, int p, int f, const float *x, int ld, const float *xt,
+                                         float mu, float h, float tau, const float *g, ContactLin &L, float w[3],
+                                         float &meff) {
+  const int np = G.n_pad;
+  const int t[3] = {G.elems[4 * f], G.elems[4 * f + 1], G.elems[4 * f + 2]};
+  V3 X[3], Xt[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    X[k] = v3(x[t[k]], x[ld + t[k]], x[2 * ld + t[k]]);
+    Xt[k] = v3(xt[t[k]], xt[np + t[k]], xt[2 * np + t[k]]);
+  }
+  const V3 P = v3(x[p], x[ld + p], x[2 * ld + p]), Pt = v3(xt[p], xt[np + p], xt[2 * np + p]);
+  const V3 nf = cross(X[1] - X[0], X[2] - X[0]);
+  const float ar = norm(nf);
+  V3 nh = v3(0.f, 0.f, 1.f);
+  float d = 0.f;
+  w[0] = w[1] = w[2] = 1.f / 3.f;
+  if (ar > 0.f) {
+    nh = (1.f / ar) * nf;
+    d = dot(nh, P - X[0]);
+    const V3 y = P - d * nh;
+    w[0] = dot(nh, cross(X[1] - y, X[2] - y)) / ar;
+    w[1] = dot(nh, cross(X[2] - y, X[0] - y)) / ar;
+    w[2] = 1.f - w[0] - w[1];
+  }
+  const float side = dot(cross(Xt[1] - Xt[0], Xt[2] - Xt[0]), Pt - Xt[0]) < 0.f ? -1.f : 1.f;
+  const V3 n = side * nh;
+  float inv = 1.f / __ldg(G.mass + p);
+  V3 rel = P - Pt;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    inv += w[k] * w[k] / __ldg(G.mass + t[k]);
+    rel = rel - w[k] * (X[k] - Xt[k]);
+  }
+  meff = 1.f / inv;
+  V3 t1, t2;
+  tangent_basis(n, t1, t2);
+  contact_law(n, t1, t2, side * d - tau, rel, 0.f, mu, h, meff, g, L);
+}
+
+// world force R^T gamma of a contact (gamma = (g_n, g_t world))
+__device__ __forceinline__ V3 contact_force(const ContactLin &L, const float *g) {
+  const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
+  const float y2 = L.R[6] * g[1] + L.R[7] * g[2] + L.R[8] * g[3];
+  return v3(L.R[0] * g[0] + L.R[3] * y1 + L.R[6] * y2, L.R[1] * g[0] + L.R[4] * y1 + L.R[7] * y2,
+            L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2);
+}
+
+// -w_k F added to the corners of self-contact triangle f ([3][ld] columns)
+__device__ __forceinline__ void scatter_tri(const GroupView &G, int f, const float w[3], V3 F, float *col, int ld) {
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int t = G.elems[4 * f + k];
+    atomicAdd(col + t, -w[k] * F.x);
+    atomicAdd(col + ld + t, -w[k] * F.y);
+    atomicAdd(col + 2 * ld + t, -w[k] * F.z);
+  }
 }
 
 template <int VPE>
@@ -512,6 +651,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       ContactLin L;
       const float4 g4 = *reinterpret_cast<const float4 *>(gam + 4 * jj);
       const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+      if (G.self && cobs[jj] == FLASH_SELF_SLOT) continue;   // second pass below
       lin_at(O, cobs[jj], a, mu, mv, x, xt, g, L);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
@@ -521,9 +661,34 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       fz += L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2;
     }
     if (!residual_only) {
-      rs[vtx] += fx;
-      rs[ns + vtx] += fy;
-      rs[2 * ns + vtx] += fz;
+      if (G.self) {   // triangle corners of other threads' self contacts may be this vertex
+        atomicAdd(rs + vtx, fx);
+        atomicAdd(rs + ns + vtx, fy);
+        atomicAdd(rs + 2 * ns + vtx, fz);
+      } else {
+        rs[vtx] += fx;
+        rs[ns + vtx] += fy;
+        rs[2 * ns + vtx] += fz;
+      }
+    }
+  }
+  if (G.self) {
+    // self contacts: +F on the vertex, -w_k F on the triangle's corners
+    const int *ctri = G.ctri + (size_t)l * G.cap;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      if (cobs[j] != FLASH_SELF_SLOT) continue;
+      ContactLin L;
+      float wt[3], me;
+      const int vtx = cvert[j], tri = ctri[j];
+      lin_self(G, vtx, tri, qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, wt, me);
+      rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
+      if (!residual_only) {
+        const V3 F = contact_force(L, gam + 4 * j);
+        atomicAdd(rs + vtx, F.x);
+        atomicAdd(rs + ns + vtx, F.y);
+        atomicAdd(rs + 2 * ns + vtx, F.z);
+        scatter_tri(G, tri, wt, F, rs, ns);
+      }
     }
   }
   rmax = block_max(rmax, sh_red);
@@ -940,14 +1105,34 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
     const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
     const V3 du = v3(w[vtx], w[np + vtx], w[2 * np + vtx]);   // u - q^{k-1} = A^-1 r
     ContactLin L;
-    lin_at(O, cobs[c], a, mu, mv, x, xt, gam + 4 * c, L);
-    const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
-    const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
-    const float Rdu2 = L.R[6] * du.x + L.R[7] * du.y + L.R[8] * du.z;
+    V3 du_c = du;
+    float sc;
+    if (G.self && cobs[c] == FLASH_SELF_SLOT) {
+      // J du = du_p - sum w_k du_k; preconditioner scale (a_pp + sum w_k^2 a_kk) meff
+      float wt[3], me;
+      const int tri = G.ctri[(size_t)l * cap + c];
+      lin_self(G, vtx, tri, q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, wt, me);
+      float av = ad[vtx];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const int t = G.elems[4 * tri + k];
+        du_c = du_c - wt[k] * v3(w[t], w[np + t], w[2 * np + t]);
+        av += wt[k] * wt[k] * ad[t];
+      }
+      sc = av * me;
+      float *fw = G.fm_w + ((size_t)l * cap + c) * 4;
+      fw[0] = wt[0]; fw[1] = wt[1]; fw[2] = wt[2]; fw[3] = me;
+    } else {
+      lin_at(O, cobs[c], a, mu, mv, x, xt, gam + 4 * c, L);
+      sc = ad[vtx] * mv;
+    }
+    const float Rdu0 = L.R[0] * du_c.x + L.R[1] * du_c.y + L.R[2] * du_c.z;
+    const float Rdu1 = L.R[3] * du_c.x + L.R[4] * du_c.y + L.R[5] * du_c.z;
+    const float Rdu2 = L.R[6] * du_c.x + L.R[7] * du_c.y + L.R[8] * du_c.z;
     const float b0 = -L.phi[0] - L.cn * Rdu0;
     const float b1 = -L.phi[1] - (L.Ct[0] * Rdu1 + L.Ct[1] * Rdu2);
     const float b2 = -L.phi[2] - (L.Ct[2] * Rdu1 + L.Ct[3] * Rdu2);
-    fm_store(lin + (size_t)c * kFmLin, L, ad[vtx] * mv);
+    fm_store(lin + (size_t)c * kFmLin, L, sc);
     V0[3 * c] = b0; V0[3 * c + 1] = b1; V0[3 * c + 2] = b2;
     ss += b0 * b0 + b1 * b1 + b2 * b2;
   }
@@ -989,16 +1174,26 @@ __device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l,
       const float v[3] = {Vj[3 * cc], Vj[3 * cc + 1], Vj[3 * cc + 2]};
       float t[3];
       fm_pinv(L, sc, v, t);
-      fx += mv * (L.R[0] * t[0] + L.R[3] * t[1] + L.R[6] * t[2]);
-      fy += mv * (L.R[1] * t[0] + L.R[4] * t[1] + L.R[7] * t[2]);
-      fz += mv * (L.R[2] * t[0] + L.R[5] * t[1] + L.R[8] * t[2]);
+      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] == FLASH_SELF_SLOT;
+      const float *fw = selfrow ? G.fm_w + ((size_t)l * cap + cc) * 4 : nullptr;
+      const float me = selfrow ? fw[3] : mv;
+      const V3 F = v3(me * (L.R[0] * t[0] + L.R[3] * t[1] + L.R[6] * t[2]),
+                      me * (L.R[1] * t[0] + L.R[4] * t[1] + L.R[7] * t[2]),
+                      me * (L.R[2] * t[0] + L.R[5] * t[1] + L.R[8] * t[2]));
+      fx += F.x; fy += F.y; fz += F.z;
+      if (selfrow) scatter_tri(G, G.ctri[(size_t)l * cap + cc], fw, F, fs, n);
     }
-    fs[vtx] = fx; fs[n + vtx] = fy; fs[2 * n + vtx] = fz;
+    if (G.self) {
+      atomicAdd(fs + vtx, fx); atomicAdd(fs + n + vtx, fy); atomicAdd(fs + 2 * n + vtx, fz);
+    } else {
+      fs[vtx] = fx; fs[n + vtx] = fy; fs[2 * n + vtx] = fz;
+    }
     fm0 = fmaxf(fm0, fabsf(fx)); fm1 = fmaxf(fm1, fabsf(fy)); fm2 = fmaxf(fm2, fabsf(fz));
   }
   __syncthreads();
   if (tc) {
-    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
+    // with self contacts the column maxima are known only after the sums
+    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2);
   } else {
     float *f = G.f + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -1035,7 +1230,16 @@ __device__ __forceinline__ void fm_gather_body(const GroupView &G, const int l, 
     float t[3];
     fm_pinv(L, sc, v, t);
     const int vtx = cvert[c];
-    const float ux = u[vtx], uy = u[np + vtx], uz = u[2 * np + vtx];
+    float ux = u[vtx], uy = u[np + vtx], uz = u[2 * np + vtx];
+    if (G.self && G.cobs[(size_t)l * cap + c] == FLASH_SELF_SLOT) {   // J u = u_p - sum w_k u_k
+      const float *fw = G.fm_w + ((size_t)l * cap + c) * 4;
+      const int tri = G.ctri[(size_t)l * cap + c];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const int t = G.elems[4 * tri + k];
+        ux -= fw[k] * u[t]; uy -= fw[k] * u[np + t]; uz -= fw[k] * u[2 * np + t];
+      }
+    }
     const float Ru0 = L.R[0] * ux + L.R[1] * uy + L.R[2] * uz;
     const float Ru1 = L.R[3] * ux + L.R[4] * uy + L.R[5] * uz;
     const float Ru2 = L.R[6] * ux + L.R[7] * uy + L.R[8] * uz;
@@ -1139,14 +1343,22 @@ __device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, 
         for (int r = 0; r < 3; r++) z[r] += ys[i] * Vb[(size_t)i * N3 + 3 * cc + r];
       float dy[3];
       fm_pinv(L, sc, z, dy);
-      fsum = fsum + apply_update(L, mv, a.gmax, dy, gam + 4 * cc);
+      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] == FLASH_SELF_SLOT;
+      const float *fw = selfrow ? G.fm_w + ((size_t)l * cap + cc) * 4 : nullptr;
+      const V3 F = apply_update(L, selfrow ? fw[3] : mv, a.gmax, dy, gam + 4 * cc);
+      fsum = fsum + F;
+      if (selfrow) scatter_tri(G, G.ctri[(size_t)l * cap + cc], fw, F, fs, n);
     }
-    fs[vtx] = fsum.x; fs[n + vtx] = fsum.y; fs[2 * n + vtx] = fsum.z;
+    if (G.self) {
+      atomicAdd(fs + vtx, fsum.x); atomicAdd(fs + n + vtx, fsum.y); atomicAdd(fs + 2 * n + vtx, fsum.z);
+    } else {
+      fs[vtx] = fsum.x; fs[n + vtx] = fsum.y; fs[2 * n + vtx] = fsum.z;
+    }
     fm0 = fmaxf(fm0, fabsf(fsum.x)); fm1 = fmaxf(fm1, fabsf(fsum.y)); fm2 = fmaxf(fm2, fabsf(fsum.z));
   }
   __syncthreads();
   if (tc) {
-    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
+    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2);
   } else {
     float *f = G.f + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -1195,6 +1407,7 @@ __device__ __forceinline__ void end_body(const GroupView &G, const int l, const 
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     G.pvert[(size_t)l * G.cap + j] = G.cvert[(size_t)l * G.cap + j];
     G.pobs[(size_t)l * G.cap + j] = G.cobs[(size_t)l * G.cap + j];
+    if (G.self) G.pctri[(size_t)l * G.cap + j] = G.ctri[(size_t)l * G.cap + j];
     for (int c = 0; c < 4; c++) G.pgam[((size_t)l * G.cap + j) * 4 + c] = G.cgam[((size_t)l * G.cap + j) * 4 + c];
   }
 }
@@ -1351,7 +1564,7 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
   const float *pg = G.pgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
-    if (o == FLASH_GRASP_SLOT) {   // grasp rows are not predicted: NaN features keep them cold
+    if (o >= FLASH_GRASP_SLOT) {   // grasp and self rows are not predicted: NaN features keep them cold
       for (int c = 0; c < 10; c++) X[(off[l] + j) * 10 + c] = __int_as_float(0x7fc00000);
       continue;
     }
@@ -1366,11 +1579,11 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
     const V3 vr = v3(v[vtx], v[np + vtx], v[2 * np + vtx]) - (1.f / a.h) * (x - xo);
     // previous step's multipliers of the same (vertex, obstacle)
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
-    const int key = vtx * (FLASH_GRASP_SLOT + 1) + o;
+    const int key = vtx * (FLASH_SELF_SLOT + 1) + o;
     int lo = 0, hi = pc - 1;
     while (lo <= hi) {
       const int mid = (lo + hi) >> 1;
-      const int km = pv[mid] * (FLASH_GRASP_SLOT + 1) + po[mid];
+      const int km = pv[mid] * (FLASH_SELF_SLOT + 1) + po[mid];
       if (km == key) {
         for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
         break;
@@ -1402,7 +1615,7 @@ __global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, S
   float *gam = G.cgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
-    if (o == FLASH_GRASP_SLOT) continue;
+    if (o >= FLASH_GRASP_SLOT) continue;
     const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
     V3 n, t1, t2;
     float gap;
@@ -1441,7 +1654,7 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     const int vtx = cvert[j], o = cobs[j];
     float *t = T + (off[l] + j) * 6;
-    if (o == FLASH_GRASP_SLOT || !(V.rncp[e] <= a.tol)) {   // grasp row or not converged: no target (NaN row)
+    if (o >= FLASH_GRASP_SLOT || !(V.rncp[e] <= a.tol)) {   // grasp / self row or not converged: no target
       for (int c = 0; c < 6; c++) t[c] = __int_as_float(0x7fc00000);
       continue;
     }

@@ -22,6 +22,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3,
 WOVERFLOW = 1
 MAX_OBS = 8
 GRASP_SLOT = MAX_OBS   # contact-list obstacle slot of grasp rows
+SELF_SLOT = MAX_OBS + 1   # contact-list slot of cloth self contacts
+SELF_MAX = 4           # self contacts per vertex at most
 MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
@@ -46,7 +48,7 @@ class SceneDesc(C.Structure):
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
-                ("lin_iters", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("lin_iters", C.c_int32), ("self_collide", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -90,6 +92,7 @@ def lib():
         L.flash_step.argtypes = [vp, i32, vp]
         L.flash_grasp.argtypes = [vp, i32, i32, C.POINTER(i32), i32, C.POINTER(C.c_float), C.c_float, vp]
         L.flash_render.argtypes = [vp, C.POINTER(Camera), vp, vp, vp, vp, vp]
+        L.flash_get_contact_tris.argtypes = [vp, vp, vp]
         L.flash_raycaster_create.argtypes = [C.POINTER(Camera), i32, i32, i32, C.POINTER(i32), C.POINTER(vp)]
         L.flash_raycast.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.flash_raycaster_destroy.argtypes = [vp]
@@ -122,7 +125,7 @@ def lib():
         L.flash_dense_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         for name in ("flash_scene_create", "flash_mesh_add", "flash_envs_add", "flash_scene_finalize",
                      "flash_env_offsets", "flash_set_state", "flash_get_state", "flash_set_obstacle_poses",
-                     "flash_step", "flash_grasp", "flash_render", "flash_raycaster_create", "flash_raycast",
+                     "flash_step", "flash_grasp", "flash_render", "flash_raycaster_create", "flash_raycast", "flash_get_contact_tris",
                      "flash_raycaster_profile", "flash_raycaster_profile_read", "flash_get_contacts", "flash_get_stats", "flash_status_word",
                      "flash_global_apply", "flash_profile_enable", "flash_profile_read", "flash_warmstart_set",
                      "flash_warmstart_bounds",
@@ -155,7 +158,8 @@ class Sim:
     """
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
-                 warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10):
+                 warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
+                 self_collision=None):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -171,9 +175,13 @@ class Sim:
         d.k_min = s0.k_min if k_min is None else k_min
         d.k_cap = s0.k_cap if k_cap is None else k_cap
         d.mode = s0.mode if mode is None else mode
-        # one row per (vertex, obstacle), plus one grasp row per vertex where grasps are scheduled
-        d.contact_cap = contact_cap or max(sc.n_verts * (sc.n_obs + (1 if sc.meta.get("grasp") else 0))
-                                           for sc in scenes)
+        if self_collision is None:   # on when a scene asks for it
+            self_collision = any(sc.meta.get("self_collision") for sc in scenes)
+        # one row per (vertex, obstacle), plus one grasp row per vertex where grasps are
+        # scheduled, plus up to SELF_MAX self rows per vertex with self-collision
+        d.contact_cap = contact_cap or max(sc.n_verts * (sc.n_obs + (1 if sc.meta.get("grasp") else 0) +
+                                                         (SELF_MAX if self_collision else 0)) for sc in scenes)
+        d.self_collide = 1 if self_collision else 0
         d.solve = solve
         d.warm = warm
         d.lanes = lanes
@@ -292,6 +300,13 @@ class Sim:
         gam = torch.empty((self.n_envs, self.cap, 4), dtype=torch.float32, device=self.dev)
         _check(lib().flash_get_contacts(self._h, _ptr(cnt), _ptr(vert), _ptr(obs), _ptr(gam), _stream()))
         return cnt, vert, obs, gam
+
+    def contact_tris(self):
+        """Triangle of each row of the last step's contact lists, [N][cap]
+        (-1 for rows that are not self contacts)."""
+        tri = torch.empty((self.n_envs, self.cap), dtype=torch.int32, device=self.dev)
+        _check(lib().flash_get_contact_tris(self._h, _ptr(tri), _stream()))
+        return tri
 
     def stats(self):
         it = torch.empty(self.n_envs, dtype=torch.int32, device=self.dev)
