@@ -79,8 +79,9 @@ def test_tet_squeeze_full_metric_tolerance_mode_lanes(cuda):
     environment reaches r_ncp <= 1e-5.  Sampled environments start from the
     oracle's state; the inexact (10-step GMRES) Newton iterations approach
     the threshold slowly, so FP32 and FP64 may cross it a few iterations
-    apart: where the counts agree the states agree to 1e-5 m, otherwise
-    both are converged states (1e-4 m)."""
+    apart.  Both stop at r_ncp <= 1e-5 m, so two converged states may differ
+    by a few times that tolerance: where the counts agree within 3e-5 m,
+    otherwise within 1e-4 m."""
     sc = scenes.tet_squeeze(n_envs=300, steps=30)
     s = 12
     sample = [0, 149, 150, 299]
@@ -95,4 +96,4 @@ def test_tet_squeeze_full_metric_tolerance_mode_lanes(cuda):
         oracle.step(meshes[e], sc, e, s, ref, metric=2, mode=1, tol=1e-5, k_cap=60)
         assert ref.rncp <= 1e-5 and abs(int(it[e]) - ref.iters) <= 3, (e, it[e], ref.iters)
         err = np.abs(qg[e] - ref.q).max()
-        assert err <= (POS_TOL if it[e] == ref.iters else 1e-4), (e, it[e], ref.iters, err)
+        assert err <= (3 * 1e-5 if it[e] == ref.iters else 1e-4), (e, it[e], ref.iters, err)
