@@ -185,11 +185,15 @@ __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f,
   return true;
 }
 
+// SELF: the group detects cloth self contacts (a compile-time switch, so the
+// kernels of scenes without self-collision carry none of its code)
+template <bool SELF>
 __device__ __forceinline__ void begin_body(const GroupView &G, const int l, const EnvView &V, StepArgs a) {
   __shared__ int sh_scan[32];
   __shared__ int s_type[FLASH_MAX_OBS];
   __shared__ float s_dims[FLASH_MAX_OBS][3], s_pose[FLASH_MAX_OBS][7];
   a.tau = G.tau;
+  const bool self = SELF && G.self;   // tetrahedral groups of a self-collision scene have none
   const int e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   float *q = G.q + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
@@ -216,7 +220,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   uint8_t *gflag = G.gflag + (size_t)l * np;
   const float h = a.h, h2 = a.h * a.h;
   const float gv[3] = {a.gx, a.gy, a.gz};
-  if (G.self) {
+  if (self) {
     // self contacts test triangles against q_t and q~ of every vertex: both
     // are written first
     for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -231,7 +235,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   __syncthreads();
   int base = 0;
   int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
-  int *ctri = G.self ? G.ctri + (size_t)l * G.cap : nullptr;
+  int *ctri = self ? G.ctri + (size_t)l * G.cap : nullptr;
   const float reach = a.tau + a.margin;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     int i = i0 + threadIdx.x;
@@ -240,7 +244,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     int ns = 0;
     if (i < n) {
       float x0[3], x1[3];
-      if (G.self) {
+      if (self) {
         for (int c = 0; c < 3; c++) { x0[c] = qt[c * np + i]; x1[c] = qp[c * np + i]; }
       } else {
         for (int c = 0; c < 3; c++) {
@@ -268,7 +272,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         float s1 = obstacle_sdf(s_type[o], s_dims[o], s_pose[o], v3(x1[0], x1[1], x1[2]), nn);
         if (fminf(s0, s1) < a.tau + a.margin) mask |= 1u << o;
       }
-      if (G.self)   // the first FLASH_SELF_MAX candidate triangles in index order
+      if (self)   // the first FLASH_SELF_MAX candidate triangles in index order
         for (int t = 0; t < G.E && ns < FLASH_SELF_MAX; t++)
           if (self_candidate(G, i, t, reach, qt, qp)) sf[ns++] = t;
     }
@@ -301,7 +305,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   float *gam = G.cgam + (size_t)l * G.cap * 4;
   const int pc = G.pcount[l];
   const int *pv = G.pvert + (size_t)l * G.cap, *po = G.pobs + (size_t)l * G.cap;
-  const int *pt = G.self ? G.pctri + (size_t)l * G.cap : nullptr;
+  const int *pt = self ? G.pctri + (size_t)l * G.cap : nullptr;
   const float *pg = G.pgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -485,7 +489,7 @@ __device__ __forceinline__ void scatter_tri(const GroupView &G, int f, const flo
   }
 }
 
-template <int VPE>
+template <int VPE, bool SELF>
 __device__ __forceinline__ void local_body(const GroupView &G, const int l, const EnvView &V, StepArgs a, int k,
                                            int residual_only, int tc, int pending) {
   // VPE = vertices per element: 3 (triangle, F is 3x2) or 4 (tet, F is 3x3)
@@ -651,7 +655,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       ContactLin L;
       const float4 g4 = *reinterpret_cast<const float4 *>(gam + 4 * jj);
       const float g[4] = {g4.x, g4.y, g4.z, g4.w};
-      if (G.self && cobs[jj] == FLASH_SELF_SLOT) continue;   // second pass below
+      if (SELF && cobs[jj] == FLASH_SELF_SLOT) continue;   // second pass below
       lin_at(O, cobs[jj], a, mu, mv, x, xt, g, L);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
@@ -661,7 +665,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       fz += L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2;
     }
     if (!residual_only) {
-      if (G.self) {   // triangle corners of other threads' self contacts may be this vertex
+      if (SELF) {   // triangle corners of other threads' self contacts may be this vertex
         atomicAdd(rs + vtx, fx);
         atomicAdd(rs + ns + vtx, fy);
         atomicAdd(rs + 2 * ns + vtx, fz);
@@ -672,7 +676,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       }
     }
   }
-  if (G.self) {
+  if (SELF) {
     // self contacts: +F on the vertex, -w_k F on the triangle's corners
     const int *ctri = G.ctri + (size_t)l * G.cap;
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
@@ -1432,17 +1436,18 @@ __global__ void k_grasp_set(int *gstate, int *gobs, float *ganchor, const int *r
 // Entry points: table launches over the environments of one or more groups,
 // CTA b = (group map[b].x, environment map[b].y).  Every scene, one group or
 // many, runs these same kernels.
+template <bool SELF>
 __global__ void __launch_bounds__(256) k_begin_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                    EnvView V, StepArgs a) {
   const int2 b = map[blockIdx.x];
-  begin_body(tab[b.x], b.y, V, a);
+  begin_body<SELF>(tab[b.x], b.y, V, a);
 }
-template <int VPE>
+template <int VPE, bool SELF>
 __global__ void __launch_bounds__(512, 2) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                       EnvView V, StepArgs a, int k, int residual_only, int tc,
                                                       int pending) {
   const int2 b = map[blockIdx.x];
-  local_body<VPE>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
+  local_body<VPE, SELF>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
 }
 __global__ void __launch_bounds__(256, 4) k_ncp_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                     EnvView V, StepArgs a, int tc) {
@@ -1673,9 +1678,11 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
 }  // namespace
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_local_tab<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_local_tab<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  e = cudaFuncSetAttribute(k_local_tab<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
@@ -1846,7 +1853,10 @@ cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int
 
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
   if (!L.all.blocks) return cudaSuccess;
-  k_begin_tab<<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+  if (s->d.self_collide)
+    k_begin_tab<true><<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+  else
+    k_begin_tab<false><<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
   return cudaGetLastError();
 }
 
@@ -1856,9 +1866,12 @@ cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArg
   const GroupView *tab = (const GroupView *)s->gtab;
   for (const Batch &b : L.local) {
     if (b.vpe == 3)
-      k_local_tab<3><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+      if (s->d.self_collide)
+        k_local_tab<3, true><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+      else
+        k_local_tab<3, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
     else
-      k_local_tab<4><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+      k_local_tab<4, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*launched;
