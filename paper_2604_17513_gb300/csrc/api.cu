@@ -185,6 +185,19 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(upload(s, &g.elems, el));
   FLASH_CUDA_TRY(upload(s, &g.D, Df));
   FLASH_CUDA_TRY(upload(s, &g.wt, wt));
+  if (m.type == FLASH_TRI) {
+    std::vector<float> rec((size_t)m.E * 8);
+    for (int e = 0; e < m.E; e++) {
+      float *r = rec.data() + (size_t)e * 8;
+      for (int a = 0; a < 3; a++) std::memcpy(r + a, &el[(size_t)e * 4 + a], sizeof(int));
+      r[3] = wt[e];
+      r[4] = Df[(size_t)e * 12 + 3]; r[5] = Df[(size_t)e * 12 + 4];
+      r[6] = Df[(size_t)e * 12 + 6]; r[7] = Df[(size_t)e * 12 + 7];
+    }
+    float *d = nullptr;
+    FLASH_CUDA_TRY(upload(s, &d, rec));
+    g.erec = reinterpret_cast<float4 *>(d);
+  }
   FLASH_CUDA_TRY(upload(s, &g.mass, massf));
   {
     // surface triangles for ray casting: the triangles themselves, or the

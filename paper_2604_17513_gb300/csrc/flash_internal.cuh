@@ -56,6 +56,10 @@ struct Group {
   int *elems = nullptr;       // [E][4]
   float *D = nullptr;         // [E][12]
   float *wt = nullptr;        // [E]
+  // triangle meshes: one 32-byte record per element for the local pass,
+  // {v0, v1, v2 (int bits), weight}, {D[1][0], D[1][1], D[2][0], D[2][1]}
+  // (row 0 of the operator is -(row 1 + row 2): it annihilates translations)
+  float4 *erec = nullptr;     // [E][2]
   // element -> vertex forces are summed per vertex through CSR tables over
   // the slots e * vpe + a (element e, local vertex a), in incidence order
   uint16_t *coff = nullptr;   // [n + 1, padded to even] slot offsets

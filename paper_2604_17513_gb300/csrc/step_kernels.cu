@@ -23,6 +23,7 @@ struct GroupView {
   int n, n_pad, E, H, vpe, nc, type, cap;
   const int *genv, *elems;
   const float *D, *wt, *mass;
+  const float4 *erec;            // triangle meshes: packed element records [E][2]
   float *q, *v, *qt, *qp, *r, *f, *w, *dq;
   __half *rh, *rl;
   float *rscale;
@@ -63,7 +64,7 @@ struct EnvView {
 GroupView view(const flash_scene *s, const Group &g) {
   GroupView v;
   v.n = g.n; v.n_pad = g.n_pad; v.E = g.E; v.H = g.H; v.vpe = g.vpe; v.nc = g.nc; v.type = g.type; v.cap = s->cap;
-  v.genv = g.genv; v.elems = g.elems; v.D = g.D; v.wt = g.wt; v.mass = g.mass;
+  v.genv = g.genv; v.elems = g.elems; v.D = g.D; v.wt = g.wt; v.mass = g.mass; v.erec = g.erec;
   v.q = g.q; v.v = g.v; v.qt = g.qt; v.qp = g.qp; v.r = g.r; v.f = g.f; v.w = g.w; v.dq = g.dq;
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
@@ -553,6 +554,36 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     //      element's forces w~ D_a^T (p - F) on each of its vertices a.
     //      F is formed from edge differences (the operator annihilates
     //      translations), which keeps |q| out of its rounding.
+    if constexpr (VPE == 3) {
+      // triangles: one packed record per element (two 16-byte loads); the
+      // force on the first vertex is minus the other two, so every element's
+      // forces sum to zero as the operator's rows do
+      for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
+        const float4 r0 = __ldg(G.erec + 2 * el), r1 = __ldg(G.erec + 2 * el + 1);
+        const int v0 = __float_as_int(r0.x), v1 = __float_as_int(r0.y), v2 = __float_as_int(r0.z);
+        float F[6], R[6], P[6];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const float x0 = qs[c * ns + v0];
+          const float d1 = qs[c * ns + v1] - x0, d2 = qs[c * ns + v2] - x0;
+          F[2 * c] = d1 * r1.x + d2 * r1.z;
+          F[2 * c + 1] = d1 * r1.y + d2 * r1.w;
+        }
+        closest_rot32(F, R);
+        const float wt = r0.w * ks;
+#pragma unroll
+        for (int t = 0; t < 6; t++) P[t] = wt * (R[t] - F[t]);
+        float *Fe = Fs + (size_t)el * 9;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const float f1 = r1.x * P[2 * c] + r1.y * P[2 * c + 1];
+          const float f2 = r1.z * P[2 * c] + r1.w * P[2 * c + 1];
+          Fe[3 + c] = f1;
+          Fe[6 + c] = f2;
+          Fe[c] = -(f1 + f2);
+        }
+      }
+    } else
     for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
       const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
@@ -601,7 +632,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       const float m = __ldg(G.mass + i);
       const float x[3] = {qs[i], qs[ns + i], qs[2 * ns + i]};
       float sum[3] = {0.f, 0.f, 0.f}, err[3] = {0.f, 0.f, 0.f};
-#pragma unroll 2
+#pragma unroll 4
       for (int t = 0; t < G.deg_b; t++) {
         const int2 kj = __ldg(G.kb + (size_t)t * np + i);
         const float kk = __int_as_float(kj.y);
