@@ -744,6 +744,14 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
       FLASH_CUDA_TRY(launch_fm_adiag(g, st));
     }
   }
+  // self-collision: the begin kernel keeps every triangle's box in shared
+  // memory when the largest triangle mesh fits (else it tests every pair)
+  if (s->d.self_collide) {
+    size_t need = 0;
+    for (const Group &g : s->groups)
+      if (g.self) need = std::max(need, sizeof(float) * 6 * (size_t)g.E);
+    s->begin_smem = need <= (size_t)kMaxBeginSmem ? need : 0;
+  }
   // env-level arrays
   std::vector<float> mu(s->N), odims((size_t)s->N * FLASH_MAX_OBS * 3, 0.f), ocomp((size_t)s->N * FLASH_MAX_OBS, 0.f);
   std::vector<int> otype((size_t)s->N * FLASH_MAX_OBS, 0);

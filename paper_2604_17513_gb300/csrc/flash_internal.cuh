@@ -24,6 +24,7 @@
 namespace flash {
 
 constexpr int kMaxPerVertex = 4; // contacts solved jointly on one vertex
+constexpr int kMaxBeginSmem = 160 * 1024;   // self-contact triangle boxes in the begin kernel
 constexpr float kDamp = 1e-6f;   // Newton-step damping of the per-vertex block
 
 struct MeshTemplate {
@@ -167,6 +168,7 @@ struct flash_scene {
   unsigned long long *rc_keys = nullptr;   // ray casting work buffer
   size_t rc_keys_n = 0;
   int rc_tag = 0;                          // frame tag of the next render
+  size_t begin_smem = 0;                   // begin kernel's triangle boxes (self-collision scenes)
   void *rc_prep = nullptr;                 // per-environment view constants
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating

@@ -189,7 +189,7 @@ __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f,
 // SELF: the group detects cloth self contacts (a compile-time switch, so the
 // kernels of scenes without self-collision carry none of its code)
 template <bool SELF>
-__device__ __forceinline__ void begin_body(const GroupView &G, const int l, const EnvView &V, StepArgs a) {
+__device__ __forceinline__ void begin_body(const GroupView &G, const int l, const EnvView &V, StepArgs a, int boxes) {
   __shared__ int sh_scan[32];
   __shared__ int s_type[FLASH_MAX_OBS];
   __shared__ float s_dims[FLASH_MAX_OBS][3], s_pose[FLASH_MAX_OBS][7];
@@ -234,10 +234,31 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
       }
   }
   __syncthreads();
+  // per-triangle boxes over q_t and q~, grown by the reach plus a fifth of the
+  // longest edge (a projection may lie a tenth outside in barycentric terms):
+  // a vertex whose own box misses a triangle's cannot be its candidate
+  extern __shared__ float sbox[];   // [E][6] when boxes
+  const float reach = a.tau + a.margin;
+  if (self && boxes) {
+    for (int t = threadIdx.x; t < G.E; t += blockDim.x) {
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, el = 0.f;
+      int tv[3];
+      for (int k = 0; k < 3; k++) tv[k] = G.elems[4 * t + k];
+      for (int k = 0; k < 3; k++)
+        for (int c = 0; c < 3; c++) {
+          const float x0 = qt[c * np + tv[k]], x1 = qp[c * np + tv[k]];
+          lo[c] = fminf(lo[c], fminf(x0, x1));
+          hi[c] = fmaxf(hi[c], fmaxf(x0, x1));
+        }
+      for (int c = 0; c < 3; c++) el = fmaxf(el, hi[c] - lo[c]);
+      const float g = reach + 0.2f * 1.7320508f * el;   // longest edge <= sqrt(3) x the box's largest side
+      for (int c = 0; c < 3; c++) { sbox[6 * t + c] = lo[c] - g; sbox[6 * t + 3 + c] = hi[c] + g; }
+    }
+    __syncthreads();
+  }
   int base = 0;
   int *cvert = G.cvert + (size_t)l * G.cap, *cobs = G.cobs + (size_t)l * G.cap;
   int *ctri = self ? G.ctri + (size_t)l * G.cap : nullptr;
-  const float reach = a.tau + a.margin;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     int i = i0 + threadIdx.x;
     unsigned mask = 0;
@@ -273,9 +294,18 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         float s1 = obstacle_sdf(s_type[o], s_dims[o], s_pose[o], v3(x1[0], x1[1], x1[2]), nn);
         if (fminf(s0, s1) < a.tau + a.margin) mask |= 1u << o;
       }
-      if (self)   // the first FLASH_SELF_MAX candidate triangles in index order
-        for (int t = 0; t < G.E && ns < FLASH_SELF_MAX; t++)
+      if (self) {   // the first FLASH_SELF_MAX candidate triangles in index order
+        const float vlo[3] = {fminf(x0[0], x1[0]), fminf(x0[1], x1[1]), fminf(x0[2], x1[2])};
+        const float vhi[3] = {fmaxf(x0[0], x1[0]), fmaxf(x0[1], x1[1]), fmaxf(x0[2], x1[2])};
+        for (int t = 0; t < G.E && ns < FLASH_SELF_MAX; t++) {
+          if (boxes) {
+            const float *b = sbox + 6 * t;
+            if (vhi[0] < b[0] || vlo[0] > b[3] || vhi[1] < b[1] || vlo[1] > b[4] || vhi[2] < b[2] || vlo[2] > b[5])
+              continue;
+          }
           if (self_candidate(G, i, t, reach, qt, qp)) sf[ns++] = t;
+        }
+      }
     }
     int cnt = __popc(mask) + ns, total;
     int off = block_exclusive_scan(cnt, &total, sh_scan);
@@ -1469,9 +1499,9 @@ __global__ void k_grasp_set(int *gstate, int *gobs, float *ganchor, const int *r
 // many, runs these same kernels.
 template <bool SELF>
 __global__ void __launch_bounds__(256) k_begin_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
-                                                   EnvView V, StepArgs a) {
+                                                   EnvView V, StepArgs a, int boxes) {
   const int2 b = map[blockIdx.x];
-  begin_body<SELF>(tab[b.x], b.y, V, a);
+  begin_body<SELF>(tab[b.x], b.y, V, a, boxes);
 }
 template <int VPE, bool SELF>
 __global__ void __launch_bounds__(512, 2) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
@@ -1717,6 +1747,8 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_begin_tab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBeginSmem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fm_scatter_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_fm_finish_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1885,9 +1917,10 @@ cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
   if (!L.all.blocks) return cudaSuccess;
   if (s->d.self_collide)
-    k_begin_tab<true><<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+    k_begin_tab<true><<<L.all.blocks, 256, s->begin_smem, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a,
+                                                               s->begin_smem > 0 ? 1 : 0);
   else
-    k_begin_tab<false><<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a);
+    k_begin_tab<false><<<L.all.blocks, 256, 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a, 0);
   return cudaGetLastError();
 }
 
