@@ -46,6 +46,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // most lanes chosen automatically
 constexpr int kMaxAutoLanes = 4, kMaxAutoLanesGroups = 8;
+// tolerance mode: iterations between the host's reads of the active count
+constexpr int kTolCheck = 4;
 // most linear-solver iterations of the full contact metric (the kernels' bound)
 constexpr int kMaxLinIters = 32;
 constexpr int kFmLinFloats = 22;   // per-contact linearisation record of the full metric
@@ -1095,16 +1097,26 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
       FLASH_CUDA_TRY(local(s->d.k_max + 1, 1));
       FLASH_CUDA_TRY(join(s, st));
     } else {
+      // Every environment stops on the device (its local pass sets its done
+      // flag; later passes skip it), so the host only needs to learn when all
+      // have stopped: it reads the count of environments still iterating
+      // every kTolCheck iterations, and the launches in between queue ahead
+      // of the GPU.  Iterations after the last environment stopped change
+      // nothing.
       FLASH_CUDA_TRY(join(s, st));
-      for (int k = 1; k <= s->d.k_cap + 1; k++) {
-        FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
+      const int last = s->d.k_cap + 1;
+      for (int k = 1; k <= last; k++) {
+        const bool check = k % kTolCheck == 0 || k == last;
+        if (check) FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
         FLASH_CUDA_TRY(fork(s, st));
         FLASH_CUDA_TRY(local(k, 0));
-        FLASH_CUDA_TRY(join(s, st));
-        FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        FLASH_CUDA_TRY(cudaStreamSynchronize(st));
-        if (*s->h_active == 0) break;
-        FLASH_CUDA_TRY(fork(s, st));
+        if (check) {
+          FLASH_CUDA_TRY(join(s, st));
+          FLASH_CUDA_TRY(cudaMemcpyAsync(s->h_active, s->active, sizeof(int), cudaMemcpyDeviceToHost, st));
+          FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+          if (*s->h_active == 0) break;
+          FLASH_CUDA_TRY(fork(s, st));
+        }
         FLASH_CUDA_TRY(solves());
         FLASH_CUDA_TRY(join(s, st));
       }
