@@ -22,8 +22,10 @@ _lib = None
 DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU, DP_GRASP_OBS = range(10)
 DP_ANCHOR, DP_SELF, DP_SIZE = 10, 13, 14
 GRASP_SLOT = 8   # contact-list slot of grasp constraints (after every obstacle)
-SELF_SLOT = 9    # contact-list slot of cloth self contacts (after the grasp row)
-SELF_MAX = 4     # self contacts per vertex at most
+SELF_SLOT = 9    # contact-list slot of cloth vertex-triangle self contacts (after the grasp row)
+SELF_MAX = 4     # vertex-triangle self contacts per vertex at most
+EE_SLOT = 10     # contact-list slot of cloth edge-edge self contacts
+EE_MAX = 4       # edge-edge self contacts per vertex (owning the first edge) at most
 IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC, IP_LINIT = range(6)
 
 
@@ -49,6 +51,8 @@ def lib():
         _lib.or_mesh_new.argtypes = [i, i, pd, i, pi, pd, d, d, d]
         _lib.or_mesh_free.argtypes = [C.c_void_p]
         _lib.or_mesh_hinges.argtypes = [C.c_void_p]
+        _lib.or_mesh_edges.argtypes = [C.c_void_p, pi]
+        _lib.or_mesh_edges.restype = i
         _lib.or_mesh_matrix.argtypes = [C.c_void_p, pd]
         _lib.or_solve.argtypes = [C.c_void_p, pd, pd]
         _lib.or_project.argtypes = [C.c_void_p, pd, pd]
@@ -117,6 +121,14 @@ class Mesh:
     @property
     def hinges(self) -> int:
         return lib().or_mesh_hinges(self._p)
+
+    @property
+    def edges(self):
+        """Unique edges (a < b) of a triangle mesh, sorted: [n_edges][2]."""
+        ne = lib().or_mesh_edges(self._p, None)
+        out = np.zeros((max(ne, 1), 2), np.int32)
+        lib().or_mesh_edges(self._p, _pi(out))
+        return out[:ne]
 
     def matrix(self):
         A = np.zeros((self.n, self.n))
@@ -234,7 +246,7 @@ def detect(mesh: Mesh, sc, env, step, q, v, dp=None, attached=None):
     K = sc.n_obs
     ot, od = _i32(sc.obs_type[env]), _f64(sc.obs_dims[env])
     pth = _f64(sc.poses[env, step + 1])
-    cap = mesh.n * (K + 1 + SELF_MAX)
+    cap = mesh.n * (K + 1 + SELF_MAX + EE_MAX)
     cv, co, ct = np.zeros(cap, np.int32), np.zeros(cap, np.int32), np.zeros(cap, np.int32)
     att = None if attached is None else np.ascontiguousarray(attached, np.uint8)
     cnt = lib().or_detect(mesh._p, _pd(dp), K, _pi(ot), _pd(od), _pd(pth), _pd(_f64(q)), _pd(_f64(v)),

@@ -75,6 +75,8 @@ struct OrMesh {
   double *A;     /* [n][n] dense system matrix (scalar block, A = A_s (x) I3) */
   double *L;     /* [n][n] Cholesky factor, lower */
   double *Adiag; /* [n] diagonal of A^-1 (computed on first use) */
+  int ned;       /* triangle meshes: unique edges (a < b), sorted by (a, b) */
+  int *ed;       /* [ned][2] */
 };
 
 static int ncols(const OrMesh *m) { return m->type == OR_TRI ? 2 : 3; }
@@ -210,6 +212,34 @@ static int cholesky(int n, const double *A, double *L) {
   return 0;
 }
 
+static int edge_cmp(const void *x, const void *y) {
+  const int *a = (const int *)x, *b = (const int *)y;
+  return a[0] != b[0] ? (a[0] > b[0]) - (a[0] < b[0]) : (a[1] > b[1]) - (a[1] < b[1]);
+}
+
+/* unique edges of a triangle mesh, (a < b), sorted */
+static void build_edges(OrMesh *m) {
+  m->ned = 0;
+  m->ed = NULL;
+  if (m->type != OR_TRI || m->ne == 0) return;
+  int *all = (int *)malloc(sizeof(int) * 6 * m->ne);
+  for (int e = 0; e < m->ne; e++)
+    for (int k = 0; k < 3; k++) {
+      int a = m->elems[3 * e + k], b = m->elems[3 * e + (k + 1) % 3];
+      all[6 * e + 2 * k] = a < b ? a : b;
+      all[6 * e + 2 * k + 1] = a < b ? b : a;
+    }
+  qsort(all, 3 * m->ne, 2 * sizeof(int), edge_cmp);
+  m->ed = (int *)malloc(sizeof(int) * 6 * m->ne);
+  for (int k = 0; k < 3 * m->ne; k++)
+    if (k == 0 || all[2 * k] != all[2 * k - 2] || all[2 * k + 1] != all[2 * k - 1]) {
+      m->ed[2 * m->ned] = all[2 * k];
+      m->ed[2 * m->ned + 1] = all[2 * k + 1];
+      m->ned++;
+    }
+  free(all);
+}
+
 OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elems,
                     const double *mass, double w_stretch, double w_bend, double h) {
   OrMesh *m = (OrMesh *)calloc(1, sizeof(OrMesh));
@@ -224,6 +254,7 @@ OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elem
   for (int e = 0; e < ne; e++) { m->w[e] = w_stretch; build_element(m, e, rest); }
   build_hinges(m, rest);
   if (w_bend == 0.0) m->nh = 0;
+  build_edges(m);
   /* assemble A (scalar n x n) */
   m->A = (double *)calloc((size_t)n * n, sizeof(double));
   m->L = (double *)malloc(sizeof(double) * (size_t)n * n);
@@ -251,11 +282,16 @@ OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elem
 
 void or_mesh_free(OrMesh *m) {
   if (!m) return;
+  free(m->ed);
   free(m->mass); free(m->elems); free(m->D); free(m->w);
   free(m->hv); free(m->hk); free(m->hs); free(m->A); free(m->L); free(m->Adiag);
   free(m);
 }
 int or_mesh_hinges(const OrMesh *m) { return m->nh; }
+int or_mesh_edges(const OrMesh *m, int *out) {
+  if (out && m->ned) memcpy(out, m->ed, sizeof(int) * 2 * m->ned);
+  return m->ned;
+}
 void or_mesh_matrix(const OrMesh *m, double *A_out) { memcpy(A_out, m->A, sizeof(double) * (size_t)m->n * m->n); }
 
 /* A^-1 rhs via the Cholesky factor, per coordinate (A = A_s (x) I3) */
@@ -506,6 +542,50 @@ static int self_candidate(const OrMesh *m, double reach, int p, int f, const dou
   return 1;
 }
 
+/* Closest points of the lines through segments (a, b) and (c, d): a + s (b -
+ * a) and c + t (d - c); 0 if the lines are parallel to rounding. */
+static int line_params(const double *a, const double *b, const double *c, const double *d, double *s, double *t) {
+  double d1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, d2[3] = {d[0] - c[0], d[1] - c[1], d[2] - c[2]};
+  double r[3] = {a[0] - c[0], a[1] - c[1], a[2] - c[2]};
+  double A = dot3(d1, d1), B = dot3(d1, d2), C = dot3(d2, d2), D = dot3(d1, r), E = dot3(d2, r);
+  double den = A * C - B * B;
+  if (!(den > 1e-12 * A * C)) return 0;
+  *s = (B * E - C * D) / den;
+  *t = (A * E - B * D) / den;
+  return 1;
+}
+
+/* Edge-edge candidate (a reading, like the vertex-triangle one): edges e1
+ * = (a, b) and e2 = (c, d) of the same cloth, e2 touching no triangle of a
+ * or b, whose lines' closest points lie inside both segments and within
+ * reach of each other, at q_t or at q~. */
+static int ee_candidate(const OrMesh *m, double reach, int e1, int e2, const double *x0, const double *x1) {
+  const int a = m->ed[2 * e1], b = m->ed[2 * e1 + 1], c = m->ed[2 * e2], d = m->ed[2 * e2 + 1];
+  if (a == c || a == d || b == c || b == d) return 0;
+  int hit = 0;
+  for (int k = 0; k < 2 && !hit; k++) {
+    const double *x = k == 0 ? x0 : x1;
+    double s, t;
+    if (!line_params(x + 3 * a, x + 3 * b, x + 3 * c, x + 3 * d, &s, &t)) continue;
+    if (!(s > 0 && s < 1 && t > 0 && t < 1)) continue;
+    double dd[3];
+    for (int i = 0; i < 3; i++)
+      dd[i] = (1 - s) * x[3 * a + i] + s * x[3 * b + i] - (1 - t) * x[3 * c + i] - t * x[3 * d + i];
+    hit = norm3(dd) < reach;
+  }
+  if (!hit) return 0;
+  for (int g = 0; g < m->ne; g++) {
+    const int *tg = m->elems + 3 * g;
+    int has_ab = 0, has_cd = 0;
+    for (int k = 0; k < 3; k++) {
+      has_ab |= tg[k] == a || tg[k] == b;
+      has_cd |= tg[k] == c || tg[k] == d;
+    }
+    if (has_ab && has_cd) return 0;
+  }
+  return 1;
+}
+
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
               int cap, int *cvert, int *cobs, int *ctri) {
@@ -536,6 +616,18 @@ int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const 
         cnt++;
         ns++;
       }
+    /* edge-edge contacts of the edges (i, b), b > i (in edge order): the
+     * first OR_EE_MAX candidate pairs, feature index e1 * ned + e2 */
+    int ne_i = 0;
+    for (int e1 = 0; self && e1 < m->ned && ne_i < OR_EE_MAX; e1++) {
+      if (m->ed[2 * e1] != i) continue;
+      for (int e2 = 0; e2 < m->ned && ne_i < OR_EE_MAX; e2++)
+        if (ee_candidate(m, tau + marg, e1, e2, q, xp)) {
+          if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_EE_SLOT; if (ctri) ctri[cnt] = e1 * m->ned + e2; }
+          cnt++;
+          ne_i++;
+        }
+    }
   }
   free(xp);
   return cnt;
@@ -681,6 +773,57 @@ static void linearize_self(const OrMesh *m, double tau, double mu, double h, int
   contact_law(n, side * d - tau, rel, 0.0, mu, h, L->meff, g, L);
 }
 
+/* Edge-edge self contact of e1 = (a, b) and e2 = (c, d): the contact point
+ * moves as (1 - s) x_a + s x_b - (1 - t) x_c - t x_d with (s, t) the closest
+ * points of the two lines at x; frame normal = the unit normal of both
+ * edges, oriented by the side the first edge was on at t; gap = distance
+ * between the lines along it - tau. */
+static void linearize_ee(const OrMesh *m, double tau, double mu, double h, int e1, int e2, const double *q,
+                         const double *qt, const double *g, Lin *L) {
+  const int v[4] = {m->ed[2 * e1], m->ed[2 * e1 + 1], m->ed[2 * e2], m->ed[2 * e2 + 1]};
+  double s = 0.5, t = 0.5, st = 0.5, tt = 0.5;
+  line_params(q + 3 * v[0], q + 3 * v[1], q + 3 * v[2], q + 3 * v[3], &s, &t);
+  double d1[3], d2[3], nr[3], dd[3];
+  for (int i = 0; i < 3; i++) {
+    d1[i] = q[3 * v[1] + i] - q[3 * v[0] + i];
+    d2[i] = q[3 * v[3] + i] - q[3 * v[2] + i];
+  }
+  cross3(d1, d2, nr);
+  double nn = norm3(nr);
+  if (nn > 0) for (int i = 0; i < 3; i++) nr[i] /= nn;
+  else { nr[0] = 0; nr[1] = 0; nr[2] = 1; }
+  /* side at the step start */
+  line_params(qt + 3 * v[0], qt + 3 * v[1], qt + 3 * v[2], qt + 3 * v[3], &st, &tt);
+  double e1t[3], e2t[3], nt[3], dt[3];
+  for (int i = 0; i < 3; i++) {
+    e1t[i] = qt[3 * v[1] + i] - qt[3 * v[0] + i];
+    e2t[i] = qt[3 * v[3] + i] - qt[3 * v[2] + i];
+    dt[i] = (1 - st) * qt[3 * v[0] + i] + st * qt[3 * v[1] + i] - (1 - tt) * qt[3 * v[2] + i] - tt * qt[3 * v[3] + i];
+  }
+  cross3(e1t, e2t, nt);
+  const double side = dot3(nt, dt) < 0 ? -1.0 : 1.0;
+  const double w[4] = {1 - s, s, -(1 - t), -t};
+  double inv = 0;
+  L->nv = 4;
+  for (int k = 0; k < 4; k++) {
+    L->vi[k] = v[k];
+    L->w[k] = w[k];
+    inv += w[k] * w[k] / m->mass[v[k]];
+  }
+  L->meff = 1.0 / inv;
+  double rel[3];
+  for (int i = 0; i < 3; i++) {
+    dd[i] = 0;
+    rel[i] = 0;
+    for (int k = 0; k < 4; k++) {
+      dd[i] += w[k] * q[3 * v[k] + i];
+      rel[i] += w[k] * (q[3 * v[k] + i] - qt[3 * v[k] + i]);
+    }
+  }
+  double n[3] = {side * nr[0], side * nr[1], side * nr[2]};
+  contact_law(n, dot3(n, dd) - tau, rel, 0.0, mu, h, L->meff, g, L);
+}
+
 /* Gaussian elimination with partial pivoting, in place; x = A^-1 b (size k) */
 static void gauss_solve(int k, double *A, double *b) {
   for (int c = 0; c < k; c++) {
@@ -729,6 +872,11 @@ static void contact_lin_all(const OrMesh *m, const double *dp, const int *otype,
     Lin *L = lin + i;
     if (o == OR_SELF_SLOT) {
       linearize_self(m, dp[OR_DP_TAU], dp[OR_DP_MU], dp[OR_DP_H], v, ctri[i], q, qt, cg + 4 * i, L);
+      continue;
+    }
+    if (o == OR_EE_SLOT) {
+      linearize_ee(m, dp[OR_DP_TAU], dp[OR_DP_MU], dp[OR_DP_H], ctri[i] / m->ned, ctri[i] % m->ned, q, qt,
+                   cg + 4 * i, L);
       continue;
     }
     if (o == OR_GRASP_SLOT) linearize_grasp(dp, pose_th, q + 3 * v, L);

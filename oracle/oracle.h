@@ -64,6 +64,11 @@ typedef struct OrMesh OrMesh;
 #define OR_SELF_SLOT 9
 #define OR_SELF_MAX 4
 #define OR_SELF_BARY 0.1
+/* Edge-edge self contact of an edge (i, b), b > i, with another edge (slot
+ * OR_EE_SLOT, feature e1 * n_edges + e2 in ctri, edges (a < b) sorted): at
+ * most OR_EE_MAX per vertex i. */
+#define OR_EE_SLOT 10
+#define OR_EE_MAX 4
 #define OR_NDP 9
 /* ip[] (integer parameters) */
 #define OR_IP_KMAX 0
@@ -79,6 +84,9 @@ OrMesh *or_mesh_new(int type, int n, const double *rest, int ne, const int *elem
                     const double *mass, double w_stretch, double w_bend, double h);
 void or_mesh_free(OrMesh *m);
 int or_mesh_hinges(const OrMesh *m);
+/* unique edges (a < b) of a triangle mesh in (a, b) order: count, and the
+ * pairs into out [count][2] when out is not NULL */
+int or_mesh_edges(const OrMesh *m, int *out);
 void or_mesh_matrix(const OrMesh *m, double *A_out);             /* dense n x n */
 void or_solve(const OrMesh *m, const double *rhs, double *out);  /* A^-1 rhs, [n][3] */
 void or_project(const OrMesh *m, const double *q, double *p);    /* [ne][9] row-major 3x2|3x3 */
@@ -92,8 +100,8 @@ double or_sdf(int type, const double *dims, const double *pose, const double *x,
 
 /* attached: [n] grasp flags (or NULL); a flagged vertex gets an OR_GRASP_SLOT
  * entry after its obstacle contacts, then its self contacts (OR_SELF_SLOT,
- * triangle in ctri; -1 for the other rows; ctri may be NULL) when
- * dp[OR_DP_SELF] is set */
+ * triangle in ctri; OR_EE_SLOT, edge pair in ctri; -1 for the other rows;
+ * ctri may be NULL) when dp[OR_DP_SELF] is set */
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
               int cap, int *cvert, int *cobs, int *ctri);

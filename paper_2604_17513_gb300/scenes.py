@@ -609,3 +609,39 @@ def cloth_stack_drop(seed: int = 5, n_envs: int = 8, n_side: int = 16, side: flo
     return Scene("cloth_stack_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0), mu, np.ones(n_envs),
                  obs_type, obs_dims, np.zeros((n_envs, K)), poses, h=0.01, k_max=k_max, thickness=tau, steps=steps,
                  meta={"self_collision": True})
+
+
+def strips_cross_drop(seed: int = 6, n_envs: int = 4, steps: int = 40, k_max: int = 10) -> Scene:
+    """Two narrow cloth strips crossing at right angles: the top one is
+    released U[2, 6] mm above the bottom one (on the ground).  Each strip is
+    2 x 4 vertices, 1 cm wide and 20 cm long (cells 6.7 cm long), placed so
+    that no vertex of one strip lies over the other: they can meet only edge
+    against edge (cloth self-collision, meta["self_collision"]).  Ground
+    plane, mu ~ U[0.2, 0.6], h = 1/100."""
+    m, L, wdt = 4, 0.2, 0.01
+    xs = np.linspace(-L / 2, L / 2, m)
+    bottom = np.array([(x, y, 0.0) for y in (-wdt / 2, wdt / 2) for x in xs])
+    top = np.array([(x, y, 0.0) for x in (-wdt / 2, wdt / 2) for y in xs])
+    tris = []
+    for k in range(m - 1):
+        a, b, c, d = k, k + 1, m + k, m + k + 1
+        tris += [(a, b, d), (a, d, c)]
+    tris = np.array(tris + [tuple(v + 2 * m for v in t) for t in tris], np.int32)
+    rest = np.concatenate([bottom, top + [0.0, 0.0, 0.05]])
+    n = len(rest)
+    mass = np.full(n, 1e-3)
+    tau = 1e-3
+    q0 = np.zeros((n_envs, n, 3))
+    K = 1
+    obs_type = np.full((n_envs, K), PLANE, np.int32)
+    mu = np.zeros(n_envs)
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    poses[:, :, 0] = _pose((0, 0, 0))
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        mu[e] = g.uniform(0.2, 0.6)
+        q0[e, :2 * m] = bottom + [0.0, 0.0, tau]
+        q0[e, 2 * m:] = top + [0.0, 0.0, 2 * tau + g.uniform(0.002, 0.006)]
+    return Scene("strips_cross_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0), mu, np.ones(n_envs),
+                 obs_type, np.zeros((n_envs, K, 3)), np.zeros((n_envs, K)), poses, h=0.01, k_max=k_max,
+                 thickness=tau, steps=steps, meta={"self_collision": True})
