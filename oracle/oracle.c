@@ -616,12 +616,14 @@ int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const 
         cnt++;
         ns++;
       }
-    /* edge-edge contacts of the edges (i, b), b > i (in edge order): the
-     * first OR_EE_MAX candidate pairs, feature index e1 * ned + e2 */
+    /* edge-edge contacts of the edges (i, b), b > i (in edge order), each
+     * unordered pair once (e2 > e1: the pair (e2, e1) would be the same
+     * constraint again): the first OR_EE_MAX candidate pairs, feature index
+     * e1 * ned + e2 */
     int ne_i = 0;
     for (int e1 = 0; self && e1 < m->ned && ne_i < OR_EE_MAX; e1++) {
       if (m->ed[2 * e1] != i) continue;
-      for (int e2 = 0; e2 < m->ned && ne_i < OR_EE_MAX; e2++)
+      for (int e2 = e1 + 1; e2 < m->ned && ne_i < OR_EE_MAX; e2++)
         if (ee_candidate(m, tau + marg, e1, e2, q, xp)) {
           if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_EE_SLOT; if (ctri) ctri[cnt] = e1 * m->ned + e2; }
           cnt++;

@@ -64,9 +64,9 @@ typedef struct OrMesh OrMesh;
 #define OR_SELF_SLOT 9
 #define OR_SELF_MAX 4
 #define OR_SELF_BARY 0.1
-/* Edge-edge self contact of an edge (i, b), b > i, with another edge (slot
- * OR_EE_SLOT, feature e1 * n_edges + e2 in ctri, edges (a < b) sorted): at
- * most OR_EE_MAX per vertex i. */
+/* Edge-edge self contact of an edge e1 = (i, b), b > i, with an edge e2 > e1
+ * (slot OR_EE_SLOT, feature e1 * n_edges + e2 in ctri, edges (a < b)
+ * sorted; each unordered pair once): at most OR_EE_MAX per vertex i. */
 #define OR_EE_SLOT 10
 #define OR_EE_MAX 4
 #define OR_NDP 9

@@ -614,7 +614,7 @@ def _ee_candidates_numpy(sc, q0, q1, reach):
         for e1 in np.nonzero(E[:, 0] == i)[0]:
             a, b = E[e1]
             for e2, (c, d) in enumerate(E):
-                if len({a, b, c, d}) < 4:
+                if e2 <= e1 or len({a, b, c, d}) < 4:
                     continue
                 if any(({a, b} & ts) and ({int(c), int(d)} & ts) for ts in tri_sets):
                     continue
