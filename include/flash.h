@@ -53,7 +53,9 @@ typedef int32_t flash_status;
 #define FLASH_MAX_OBS 8
 #define FLASH_GRASP_SLOT FLASH_MAX_OBS /* contact-list obstacle slot of grasp rows */
 #define FLASH_SELF_SLOT (FLASH_MAX_OBS + 1) /* contact-list slot of cloth self contacts */
-#define FLASH_SELF_MAX 4 /* self contacts per vertex at most */
+#define FLASH_SELF_MAX 4 /* vertex-triangle self contacts per vertex at most */
+#define FLASH_EE_SLOT (FLASH_MAX_OBS + 2) /* contact-list slot of cloth edge-edge contacts */
+#define FLASH_EE_MAX 4 /* edge-edge contacts per vertex at most */
 
 #define FLASH_MODE_FIXED 0 /* exactly k_max local-global iterations per step */
 #define FLASH_MODE_TOL 1   /* iterate until r_ncp <= tol_ncp (k >= k_min) or k_cap */
@@ -93,8 +95,19 @@ typedef int32_t flash_status;
  * (in index order) per vertex get a row (slot FLASH_SELF_SLOT) whose normal
  * is f's, oriented towards the side p was on at the step start, gap =
  * distance to the plane - thickness, the contact point moving as p minus
- * the barycentric combination of f's corners.  The paper disables
- * self-collision and describes no method; this is the library's reading. */
+ * the barycentric combination of f's corners.  Edge-edge contacts: the
+ * mesh's unique edges (a, b), a < b, numbered in (a, b) order; edges e1 =
+ * (a, b) and e2 = (c, d), e1 < e2 (each pair once), with no common vertex
+ * and no triangle holding a or b together with c or d are in contact when the closest points of their
+ * lines lie inside both edges, nearer than thickness + margin (at q_t or
+ * q~); vertex a gets a row (slot FLASH_EE_SLOT, feature e1 * n_edges + e2)
+ * for each of the first FLASH_EE_MAX such pairs of its edges (e1, then e2
+ * ascending).  Its normal is that of both edges, oriented by the side
+ * (a, b) was on at the step start, gap = distance between the lines -
+ * thickness, the contact point moving as (1 - s) x_a + s x_b - (1 - t) x_c
+ * - t x_d.  Rows of a vertex: obstacles, grasp, vertex-triangle, edge-edge.
+ * The paper disables self-collision and describes no method; this is the
+ * library's reading. */
 typedef struct {
   double h;
   double gravity[3];
@@ -262,13 +275,15 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
 /* Contacts of the last step: count device int32 [N]; vert, obs device int32
  * [N][cap] (obs = FLASH_GRASP_SLOT for a grasp row); gamma device float32
  * [N][cap][4] (any may be NULL).  A vertex holds at most one row per
- * obstacle plus one grasp row, so cap = n_verts * (n_obs + 1) never
- * overflows. */
+ * obstacle plus one grasp row, FLASH_SELF_MAX vertex-triangle and
+ * FLASH_EE_MAX edge-edge rows, so cap = n_verts * (n_obs + 1 +
+ * FLASH_SELF_MAX + FLASH_EE_MAX) never overflows. */
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs,
                                 float *gamma, void *stream);
 int32_t flash_contact_cap(const flash_scene *s);
-/* Triangle of each row of the last step's contact lists: device int32
- * [N][cap] (-1 for rows that are not self contacts). */
+/* Feature of each row of the last step's contact lists: device int32
+ * [N][cap]; the triangle of a vertex-triangle self contact, e1 * n_edges +
+ * e2 for an edge-edge contact, -1 for the other rows. */
 flash_status flash_get_contact_tris(const flash_scene *s, int32_t *tri, void *stream);
 
 /* Per-environment statistics of the last step: iterations used and the NCP

@@ -391,6 +391,30 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   if (g.self) {
     FLASH_CUDA_TRY(dalloc(s, &g.ctri, cc));
     FLASH_CUDA_TRY(dalloc(s, &g.pctri, cc));
+    // unique edges (a < b) in (a, b) order and the range owned by each a
+    std::vector<std::pair<int, int>> all;
+    all.reserve((size_t)3 * m.E);
+    for (int e = 0; e < m.E; e++)
+      for (int k = 0; k < 3; k++) {
+        const int a = m.elems[(size_t)3 * e + k], b = m.elems[(size_t)3 * e + (k + 1) % 3];
+        all.emplace_back(std::min(a, b), std::max(a, b));
+      }
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    g.ned = (int)all.size();
+    if ((long long)g.ned * g.ned > 0x7fffffffLL)
+      return fail(FLASH_EINVAL, "too many edges for edge-edge self contacts (n_edges^2 must fit in int32)");
+    std::vector<int> ed((size_t)2 * std::max(g.ned, 1), 0), eoff((size_t)n + 1, 0);
+    for (int k = 0; k < g.ned; k++) {
+      ed[2 * k] = all[k].first;
+      ed[2 * k + 1] = all[k].second;
+      eoff[all[k].first + 1]++;
+    }
+    for (int i = 0; i < n; i++) eoff[i + 1] += eoff[i];
+    int *d = nullptr;
+    FLASH_CUDA_TRY(upload(s, &d, ed));
+    g.edges = reinterpret_cast<int2 *>(d);
+    FLASH_CUDA_TRY(upload(s, &g.eoff, eoff));
   }
   // local pass shared memory: q and r ([3][ns] each, ns = n rounded up to 4),
   // then the element forces [ev + 1][3] (last row zero) and the CSR tables
@@ -732,7 +756,7 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
       const size_t cc = (size_t)g.N * s->cap;
       g.fm_m = m;
       FLASH_CUDA_TRY(dalloc(s, &g.fm_lin, cc * kFmLinFloats));
-      if (g.self) FLASH_CUDA_TRY(dalloc(s, &g.fm_w, cc * 4));
+      if (g.self) FLASH_CUDA_TRY(dalloc(s, &g.fm_w, cc * kFmW));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_V, (size_t)(m + 1) * 3 * cc));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_H, (size_t)g.N * (m + 1) * m));
       FLASH_CUDA_TRY(dalloc(s, &g.fm_cs, (size_t)g.N * m));
@@ -746,12 +770,13 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
       FLASH_CUDA_TRY(launch_fm_adiag(g, st));
     }
   }
-  // self-collision: the begin kernel keeps every triangle's box in shared
-  // memory when the largest triangle mesh fits (else it tests every pair)
+  // self-collision: the begin kernel keeps every triangle's and edge's box
+  // in shared memory when the largest triangle mesh fits (else it tests
+  // every pair)
   if (s->d.self_collide) {
     size_t need = 0;
     for (const Group &g : s->groups)
-      if (g.self) need = std::max(need, sizeof(float) * 6 * (size_t)g.E);
+      if (g.self) need = std::max(need, sizeof(float) * 6 * ((size_t)g.E + g.ned));
     s->begin_smem = need <= (size_t)kMaxBeginSmem ? need : 0;
   }
   // env-level arrays

@@ -274,68 +274,6 @@ struct ContactLin {
   float gap;   // a = sd - tau at the linearisation point
 };
 
-__device__ __forceinline__ void linearize_contact(int type, const float *dims, float comp, const float *pose_t,
-                                                  const float *pose_th, float tau, float mu, float h, float mv,
-                                                  V3 x, V3 xt, const float *g, ContactLin &L) {
-  V3 n, t1, t2;
-  float sd = obstacle_sdf(type, dims, pose_th, x, n);
-  tangent_basis(n, t1, t2);
-  L.R[0] = n.x; L.R[1] = n.y; L.R[2] = n.z;
-  L.R[3] = t1.x; L.R[4] = t1.y; L.R[5] = t1.z;
-  L.R[6] = t2.x; L.R[7] = t2.y; L.R[8] = t2.z;
-  float inv_m = 1.f / mv;
-  float a = sd - tau;
-  L.gap = a;
-  float yn = g[0] * inv_m;
-  float alpha = comp * mv / (h * h);
-  float ae = a + alpha * yn;
-  float r = sqrtf(ae * ae + yn * yn);
-  float ca, cy;
-  if (r < 1e-12f) {
-    ca = 0.29289321881345254f;
-    cy = 0.29289321881345254f;
-  } else {
-    ca = 1.f - ae / r;
-    cy = 1.f - yn / r;
-  }
-  L.phi[0] = ae + yn - r;
-  L.cn = ca;
-  L.dn = ca * alpha + cy;
-  // slip relative to the obstacle's material point over the step
-  V3 pb = qrot(pose_th + 3, x - v3(pose_th[0], pose_th[1], pose_th[2]), true);
-  V3 xo = qrot(pose_t + 3, pb, false) + v3(pose_t[0], pose_t[1], pose_t[2]);
-  V3 rel = x - xt - (x - xo);
-  float s0 = dot(t1, rel), s1 = dot(t2, rel);
-  V3 gt = {g[1], g[2], g[3]};
-  float y0 = dot(t1, gt) * inv_m, y1 = dot(t2, gt) * inv_m;
-  float rad = mu * fmaxf(yn, 0.f);
-  float d0 = y0 - s0, d1 = y1 - s1;
-  float dn = sqrtf(d0 * d0 + d1 * d1);
-  if (rad == 0.f) {
-    // cone of zero radius (no normal force): proximal map is zero, phi_t = y_t
-    L.phi[1] = y0; L.phi[2] = y1;
-    L.Ct[0] = 0.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 0.f;
-    L.dtn[0] = 0.f; L.dtn[1] = 0.f;
-    L.Dtt[0] = 1.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 1.f;
-  } else if (dn <= rad) {
-    L.phi[1] = s0; L.phi[2] = s1;
-    L.Ct[0] = 1.f; L.Ct[1] = 0.f; L.Ct[2] = 0.f; L.Ct[3] = 1.f;
-    L.dtn[0] = 0.f; L.dtn[1] = 0.f;
-    L.Dtt[0] = 0.f; L.Dtt[1] = 0.f; L.Dtt[2] = 0.f; L.Dtt[3] = 0.f;
-  } else {
-    float h0 = d0 / dn, h1 = d1 / dn;
-    L.phi[1] = y0 - rad * h0;
-    L.phi[2] = y1 - rad * h1;
-    float k = rad / dn;
-    float P00 = 1.f - h0 * h0, P01 = -h0 * h1, P11 = 1.f - h1 * h1;
-    L.Ct[0] = k * P00; L.Ct[1] = k * P01; L.Ct[2] = k * P01; L.Ct[3] = k * P11;
-    L.Dtt[0] = 1.f - k * P00; L.Dtt[1] = -k * P01; L.Dtt[2] = -k * P01; L.Dtt[3] = 1.f - k * P11;
-    if (yn > 0.f) { L.dtn[0] = -mu * h0; L.dtn[1] = -mu * h1; }
-    else { L.dtn[0] = 0.f; L.dtn[1] = 0.f; }
-  }
-}
-
-// linearize_contact with matrix poses (identical contact law)
 // The contact law at a linearisation point (unit normal n with its tangent
 // basis t1, t2; gap a; slip rel over the step; normal compliance comp; mass mv
 // that scales the multipliers, y = gamma / mv).
@@ -354,12 +292,22 @@ __device__ __forceinline__ void contact_law(V3 n, V3 t1, V3 t2, float a, V3 rel,
   if (r < 1e-12f) {
     ca = 0.29289321881345254f;
     cy = 0.29289321881345254f;
+    L.phi[0] = ae + yn - r;
+  } else if (yn == 0.f) {
+    // no multiplier yet: r = |ae| exactly.  Taken apart so that a separated
+    // row keeps phi = 0 and D_C = 0 exactly (its multiplier stays zero); the
+    // approximate square root would leave 1 - ae / r at a rounding error,
+    // enough for a multiplier of ~1e-15 whose cone of that radius then turns
+    // the next iteration's friction towards the direction of rounding noise
+    ca = ae > 0.f ? 0.f : 2.f;
+    cy = 1.f;
+    L.phi[0] = ae > 0.f ? 0.f : 2.f * ae;
   } else {
     const float ir = 1.f / r;
     ca = 1.f - ae * ir;
     cy = 1.f - yn * ir;
+    L.phi[0] = ae + yn - r;
   }
-  L.phi[0] = ae + yn - r;
   L.cn = ca;
   L.dn = ca * alpha + cy;
   const float s0 = dot(t1, rel), s1 = dot(t2, rel);

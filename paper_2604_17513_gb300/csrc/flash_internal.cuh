@@ -24,7 +24,8 @@
 namespace flash {
 
 constexpr int kMaxPerVertex = 4; // contacts solved jointly on one vertex
-constexpr int kMaxBeginSmem = 160 * 1024;   // self-contact triangle boxes in the begin kernel
+constexpr int kMaxBeginSmem = 160 * 1024;   // self-contact triangle and edge boxes in the begin kernel
+constexpr int kFmW = 8;          // floats per self-contact row of the full metric's fm_w
 constexpr float kDamp = 1e-6f;   // Newton-step damping of the per-vertex block
 
 struct MeshTemplate {
@@ -95,8 +96,11 @@ struct Group {
   uint8_t *gflag = nullptr;               // [N][n_pad] grasped vertices (S_grip)
   // cloth self-collision (triangle meshes of a scene with self_collide)
   int self = 0;
-  int *ctri = nullptr, *pctri = nullptr;  // [N][cap] triangle of each self-contact row, -1 otherwise
-  float *fm_w = nullptr;                  // [N][cap][4] full metric: barycentric weights and effective mass
+  int *ctri = nullptr, *pctri = nullptr;  // [N][cap] feature of each self-contact row, -1 otherwise
+  float *fm_w = nullptr;                  // [N][cap][8] full metric: weights, effective mass, vertices 1..3
+  int ned = 0;                            // unique edges (a < b) in (a, b) order
+  int2 *edges = nullptr;                  // [ned]
+  int *eoff = nullptr;                    // [n + 1] edges owned by vertex a: eoff[a] .. eoff[a + 1]
   int3 *rtris = nullptr;                  // [rT] surface triangles for ray casting
   int rT = 0;
   int tc_bn = 128;                        // tensor-core tile width (columns), set by the tile autotuner

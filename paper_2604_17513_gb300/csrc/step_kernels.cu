@@ -30,8 +30,11 @@ struct GroupView {
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
   uint8_t *gflag;                // [N][n_pad] grasped vertices
   int self;                      // cloth self-collision on
-  int *ctri, *pctri;             // [N][cap] triangle of self-contact rows
-  float *fm_w;                   // [N][cap][4] full metric: weights and effective mass of self rows
+  int *ctri, *pctri;             // [N][cap] feature of self-contact rows (triangle, or e1 * ned + e2)
+  float *fm_w;                   // [N][cap][kFmW] full metric: weights, effective mass, vertices 1..3
+  int ned;                       // unique edges (a < b), (a, b) order
+  const int2 *edges;             // [ned]
+  const int *eoff;               // [n + 1] edges owned by vertex a
   const uint16_t *coff, *cidx;   // CSR vertex -> element slots e * vpe + a
   const int2 *kb;                // bending operator, off-diagonal entries, slot-major
   int ev, deg_b;
@@ -70,6 +73,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch; v.gflag = g.gflag;
   v.self = g.self; v.ctri = g.ctri; v.pctri = g.pctri; v.fm_w = g.fm_w;
+  v.ned = g.ned; v.edges = g.edges; v.eoff = g.eoff;
   v.c_in_smem = g.c_in_smem ? 1 : 0;
   v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
   v.fm_lin = g.fm_lin; v.fm_V = g.fm_V; v.fm_H = g.fm_H; v.fm_cs = g.fm_cs; v.fm_sn = g.fm_sn; v.fm_g = g.fm_g;
@@ -153,6 +157,7 @@ __device__ void block_max3(float &x0, float &x1, float &x2, float (*sh)[3]) {
 // p), p within `reach` of f's plane with its projection inside f up to
 // kSelfBary (barycentric), at q_t or at q~.
 constexpr float kSelfBary = 0.1f;
+constexpr int kSlots = FLASH_EE_SLOT + 1;   // contact-list slots: obstacles, grasp, self, edge-edge
 
 __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f, float reach, const float *x0,
                                                const float *x1) {
@@ -181,6 +186,57 @@ __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f,
     for (int c = 0; c < 3; c++) {
       const int u = G.elems[4 * g + c];
       if (u == t0 || u == t1 || u == t2) return false;
+    }
+  }
+  return true;
+}
+
+// Closest points of the lines through (A, B) and (C, D): A + s (B - A) and
+// C + t (D - C).  With nn = (B - A) x (D - C): s = ((C - A) x (D - C)).nn /
+// |nn|^2 and t = ((C - A) x (B - A)).nn / |nn|^2, which keeps the
+// cancellation of |d1|^2 |d2|^2 - (d1.d2)^2 out of near-parallel pairs;
+// false when the lines are parallel to rounding.
+__device__ __forceinline__ bool line_params(V3 A, V3 B, V3 C, V3 D, float &s, float &t) {
+  const V3 d1 = B - A, d2 = D - C, r = C - A;
+  const V3 nn = cross(d1, d2);
+  const float n2 = dot(nn, nn);
+  if (!(n2 > 1e-12f * dot(d1, d1) * dot(d2, d2))) return false;
+  s = dot(cross(r, d2), nn) / n2;
+  t = dot(cross(r, d1), nn) / n2;
+  return true;
+}
+
+__device__ __forceinline__ V3 col3(const float *x, int ld, int i) { return v3(x[i], x[ld + i], x[2 * ld + i]); }
+
+// Edge-edge candidate (the library's reading, like the vertex-triangle one):
+// edges e1 = (a, b) and e2 = (c, d) with no common vertex and no triangle
+// holding a or b together with c or d, whose lines' closest points lie
+// inside both edges and nearer than `reach`, at q_t or at q~.
+__device__ __forceinline__ bool ee_candidate(const GroupView &G, int e1, int e2, float reach, const float *x0,
+                                             const float *x1) {
+  const int np = G.n_pad;
+  const int2 E1 = G.edges[e1], E2 = G.edges[e2];
+  const int a = E1.x, b = E1.y, c = E2.x, d = E2.y;
+  if (a == c || a == d || b == c || b == d) return false;
+  bool hit = false;
+  for (int k = 0; k < 2 && !hit; k++) {
+    const float *x = k == 0 ? x0 : x1;
+    const V3 A = col3(x, np, a), B = col3(x, np, b), C = col3(x, np, c), D = col3(x, np, d);
+    float s, t;
+    if (!line_params(A, B, C, D, s, t)) continue;
+    if (!(s > 0.f && s < 1.f && t > 0.f && t < 1.f)) continue;
+    const V3 dd = (A - C) + s * (B - A) - t * (D - C);
+    hit = norm(dd) < reach;
+  }
+  if (!hit) return false;
+  for (int k = 0; k < 2; k++) {
+    const int p = k == 0 ? a : b;
+    for (int sl = G.coff[p]; sl < G.coff[p + 1]; sl++) {
+      const int g = G.cidx[sl] / 3;
+      for (int j = 0; j < 3; j++) {
+        const int u = G.elems[4 * g + j];
+        if (u == c || u == d) return false;
+      }
     }
   }
   return true;
@@ -236,8 +292,10 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   __syncthreads();
   // per-triangle boxes over q_t and q~, grown by the reach plus a fifth of the
   // longest edge (a projection may lie a tenth outside in barycentric terms):
-  // a vertex whose own box misses a triangle's cannot be its candidate
-  extern __shared__ float sbox[];   // [E][6] when boxes
+  // a vertex whose own box misses a triangle's cannot be its candidate.
+  // Per-edge boxes over q_t and q~ grown by the reach: two edges whose
+  // boxes miss each other cannot come within reach.
+  extern __shared__ float sbox[];   // [E][6] then [ned][6] when boxes
   const float reach = a.tau + a.margin;
   if (self && boxes) {
     for (int t = threadIdx.x; t < G.E; t += blockDim.x) {
@@ -254,6 +312,15 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
       const float g = reach + 0.2f * 1.7320508f * el;   // longest edge <= sqrt(3) x the box's largest side
       for (int c = 0; c < 3; c++) { sbox[6 * t + c] = lo[c] - g; sbox[6 * t + 3 + c] = hi[c] + g; }
     }
+    float *ebox = sbox + 6 * G.E;
+    for (int k = threadIdx.x; k < G.ned; k += blockDim.x) {
+      const int2 ev = G.edges[k];
+      for (int c = 0; c < 3; c++) {
+        const float a0 = qt[c * np + ev.x], a1 = qp[c * np + ev.x], b0 = qt[c * np + ev.y], b1 = qp[c * np + ev.y];
+        ebox[6 * k + c] = fminf(fminf(a0, a1), fminf(b0, b1)) - reach;
+        ebox[6 * k + 3 + c] = fmaxf(fmaxf(a0, a1), fmaxf(b0, b1)) + reach;
+      }
+    }
     __syncthreads();
   }
   int base = 0;
@@ -262,8 +329,8 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     int i = i0 + threadIdx.x;
     unsigned mask = 0;
-    int sf[FLASH_SELF_MAX];
-    int ns = 0;
+    int sf[FLASH_SELF_MAX], se[FLASH_EE_MAX];
+    int ns = 0, ne = 0;
     if (i < n) {
       float x0[3], x1[3];
       if (self) {
@@ -305,9 +372,26 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
           }
           if (self_candidate(G, i, t, reach, qt, qp)) sf[ns++] = t;
         }
+        // edge-edge: the first FLASH_EE_MAX pairs (e1, e2 > e1) of the edges
+        // i owns (e1, then e2 ascending); the pair (e2, e1) would repeat the
+        // same constraint
+        const float *ebox = sbox + 6 * G.E;
+        for (int e1 = G.eoff[i]; e1 < G.eoff[i + 1] && ne < FLASH_EE_MAX; e1++) {
+          float b1[6];
+          if (boxes)
+            for (int c = 0; c < 6; c++) b1[c] = ebox[6 * e1 + c];
+          for (int e2 = e1 + 1; e2 < G.ned && ne < FLASH_EE_MAX; e2++) {
+            if (boxes) {
+              const float *b = ebox + 6 * e2;
+              if (b1[3] < b[0] || b1[0] > b[3] || b1[4] < b[1] || b1[1] > b[4] || b1[5] < b[2] || b1[2] > b[5])
+                continue;
+            }
+            if (ee_candidate(G, e1, e2, reach, qt, qp)) se[ne++] = e1 * G.ned + e2;
+          }
+        }
       }
     }
-    int cnt = __popc(mask) + ns, total;
+    int cnt = __popc(mask) + ns + ne, total;
     int off = block_exclusive_scan(cnt, &total, sh_scan);
     int pos = base + off;
     for (int o = 0; o < a.K; o++)
@@ -321,6 +405,10 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     }
     for (int k = 0; k < ns; k++) {           // then the self contacts
       if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_SELF_SLOT; ctri[pos] = sf[k]; }
+      pos++;
+    }
+    for (int k = 0; k < ne; k++) {
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_EE_SLOT; ctri[pos] = se[k]; }
       pos++;
     }
     base += total;
@@ -341,14 +429,12 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
     if (a.warm == FLASH_WARM_PREV && pc > 0) {
-      // previous list sorted by (vertex, slot, triangle)
-      const long long key = (long long)(cvert[j] * (FLASH_SELF_SLOT + 1) + cobs[j]) * 0x100000000LL +
-                            (ctri ? ctri[j] + 1 : 0);
+      // previous list sorted by (vertex, slot, feature)
+      const long long key = (long long)(cvert[j] * kSlots + cobs[j]) * 0x100000000LL + (ctri ? ctri[j] + 1 : 0);
       int lo = 0, hi = pc - 1;
       while (lo <= hi) {
         int mid = (lo + hi) >> 1;
-        const long long km = (long long)(pv[mid] * (FLASH_SELF_SLOT + 1) + po[mid]) * 0x100000000LL +
-                             (pt ? pt[mid] + 1 : 0);
+        const long long km = (long long)(pv[mid] * kSlots + po[mid]) * 0x100000000LL + (pt ? pt[mid] + 1 : 0);
         if (km == key) {
           for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
           break;
@@ -454,30 +540,38 @@ __device__ __forceinline__ void lin_at(const ObsShared &O, int o, const StepArgs
   linearize_contact_m(O.type[o], O.dims[o], O.comp[o], O.pm[o], a.tau, mu, a.h, mv, x, xt, g, L);
 }
 
+// A self-contact row moves the contact point as sum_k w_k x_{v_k} over four
+// vertices (v_0 the row's own vertex); its multipliers scale with the
+// effective mass meff = 1 / sum_k w_k^2 / m_{v_k}.
+struct SelfRow {
+  int v[4];
+  float w[4];
+  float meff;
+};
+
 // Self contact of vertex p with triangle f (cloth self-collision, the
 // library's reading): positions x of the iterate ([3][ld]) and xt of the step
 // start ([3][n_pad]).  Frame normal = f's unit normal, oriented towards the
 // side p was on at q_t; gap = distance to the plane - tau; the contact point
 // moves as p minus the barycentric combination w of f's corners (p's
-// projection), effective mass meff = 1 / (1/m_p + sum w^2 / m_i); slip =
-// displacement of p relative to that point over the step.
+// projection): weights (1, -w); slip = displacement of p relative to that
+// point over the step.
 __device__ __noinline__ void lin_self(const GroupView &G, int p, int f, const float *x, int ld, const float *xt,
-                                         float mu, float h, float tau, const float *g, ContactLin &L, float w[3],
-                                         float &meff) {
+                                      float mu, float h, float tau, const float *g, ContactLin &L, SelfRow &S) {
   const int np = G.n_pad;
   const int t[3] = {G.elems[4 * f], G.elems[4 * f + 1], G.elems[4 * f + 2]};
   V3 X[3], Xt[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
-    X[k] = v3(x[t[k]], x[ld + t[k]], x[2 * ld + t[k]]);
-    Xt[k] = v3(xt[t[k]], xt[np + t[k]], xt[2 * np + t[k]]);
+    X[k] = col3(x, ld, t[k]);
+    Xt[k] = col3(xt, np, t[k]);
   }
-  const V3 P = v3(x[p], x[ld + p], x[2 * ld + p]), Pt = v3(xt[p], xt[np + p], xt[2 * np + p]);
+  const V3 P = col3(x, ld, p), Pt = col3(xt, np, p);
   const V3 nf = cross(X[1] - X[0], X[2] - X[0]);
   const float ar = norm(nf);
   V3 nh = v3(0.f, 0.f, 1.f);
   float d = 0.f;
-  w[0] = w[1] = w[2] = 1.f / 3.f;
+  float w[3] = {1.f / 3.f, 1.f / 3.f, 1.f / 3.f};
   if (ar > 0.f) {
     nh = (1.f / ar) * nf;
     d = dot(nh, P - X[0]);
@@ -490,15 +584,70 @@ __device__ __noinline__ void lin_self(const GroupView &G, int p, int f, const fl
   const V3 n = side * nh;
   float inv = 1.f / __ldg(G.mass + p);
   V3 rel = P - Pt;
+  S.v[0] = p;
+  S.w[0] = 1.f;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     inv += w[k] * w[k] / __ldg(G.mass + t[k]);
     rel = rel - w[k] * (X[k] - Xt[k]);
+    S.v[1 + k] = t[k];
+    S.w[1 + k] = -w[k];
   }
-  meff = 1.f / inv;
+  S.meff = 1.f / inv;
   V3 t1, t2;
   tangent_basis(n, t1, t2);
-  contact_law(n, t1, t2, side * d - tau, rel, 0.f, mu, h, meff, g, L);
+  contact_law(n, t1, t2, side * d - tau, rel, 0.f, mu, h, S.meff, g, L);
+}
+
+// Edge-edge contact of e1 = (a, b) with e2 = (c, d) (the library's reading):
+// (s, t) = closest points of the two lines at x (1/2 when parallel), weights
+// (1 - s, s, -(1 - t), -t); frame normal = the unit normal of both edges at
+// x, oriented by the side e1 was on at q_t; gap = n.(point on e1 - point on
+// e2) - tau; slip = that difference's displacement over the step.
+__device__ __noinline__ void lin_ee(const GroupView &G, int e1, int e2, const float *x, int ld, const float *xt,
+                                    float mu, float h, float tau, const float *g, ContactLin &L, SelfRow &S) {
+  const int np = G.n_pad;
+  const int2 E1 = G.edges[e1], E2 = G.edges[e2];
+  const int v[4] = {E1.x, E1.y, E2.x, E2.y};
+  V3 X[4], Dx[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    X[k] = col3(x, ld, v[k]);
+    Dx[k] = X[k] - col3(xt, np, v[k]);
+  }
+  float s = 0.5f, t = 0.5f;
+  line_params(X[0], X[1], X[2], X[3], s, t);
+  const V3 nc = cross(X[1] - X[0], X[3] - X[2]);
+  const float nl = norm(nc);
+  const V3 nr = nl > 0.f ? (1.f / nl) * nc : v3(0.f, 0.f, 1.f);
+  // the side at q_t: n_t.(a - c) (n_t is normal to both edges, so any pair of
+  // points on them gives the same value)
+  const V3 At = col3(xt, np, v[0]), Ct = col3(xt, np, v[2]);
+  const V3 nt = cross(col3(xt, np, v[1]) - At, col3(xt, np, v[3]) - Ct);
+  const float side = dot(nt, At - Ct) < 0.f ? -1.f : 1.f;
+  const float w[4] = {1.f - s, s, -(1.f - t), -t};
+  float inv = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    inv += w[k] * w[k] / __ldg(G.mass + v[k]);
+    S.v[k] = v[k];
+    S.w[k] = w[k];
+  }
+  S.meff = 1.f / inv;
+  const V3 dd = (X[0] - X[2]) + s * (X[1] - X[0]) - t * (X[3] - X[2]);
+  const V3 rel = (Dx[0] - Dx[2]) + s * (Dx[1] - Dx[0]) - t * (Dx[3] - Dx[2]);
+  const V3 n = side * nr;
+  V3 t1, t2;
+  tangent_basis(n, t1, t2);
+  contact_law(n, t1, t2, dot(n, dd) - tau, rel, 0.f, mu, h, S.meff, g, L);
+}
+
+// a self-contact row (slot FLASH_SELF_SLOT or FLASH_EE_SLOT) of vertex vtx
+__device__ __forceinline__ void lin_row(const GroupView &G, int o, int vtx, int feat, const float *x, int ld,
+                                        const float *xt, float mu, float h, float tau, const float *g,
+                                        ContactLin &L, SelfRow &S) {
+  if (o == FLASH_SELF_SLOT) lin_self(G, vtx, feat, x, ld, xt, mu, h, tau, g, L, S);
+  else lin_ee(G, feat / G.ned, feat % G.ned, x, ld, xt, mu, h, tau, g, L, S);
 }
 
 // world force R^T gamma of a contact (gamma = (g_n, g_t world))
@@ -509,15 +658,28 @@ __device__ __forceinline__ V3 contact_force(const ContactLin &L, const float *g)
             L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2);
 }
 
-// -w_k F added to the corners of self-contact triangle f ([3][ld] columns)
-__device__ __forceinline__ void scatter_tri(const GroupView &G, int f, const float w[3], V3 F, float *col, int ld) {
+// w_k F added to the row's four vertices ([3][ld] columns)
+__device__ __forceinline__ void scatter_row(const int v[4], const float w[4], V3 F, float *col, int ld) {
 #pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const int t = G.elems[4 * f + k];
-    atomicAdd(col + t, -w[k] * F.x);
-    atomicAdd(col + ld + t, -w[k] * F.y);
-    atomicAdd(col + 2 * ld + t, -w[k] * F.z);
+  for (int k = 0; k < 4; k++) {
+    atomicAdd(col + v[k], w[k] * F.x);
+    atomicAdd(col + ld + v[k], w[k] * F.y);
+    atomicAdd(col + 2 * ld + v[k], w[k] * F.z);
   }
+}
+
+// full metric: a self row's weights, effective mass and vertices 1..3 (vertex
+// 0 is the row's own) as stored by the setup kernel
+__device__ __forceinline__ void fm_row_store(float *fw, const SelfRow &S) {
+  *reinterpret_cast<float4 *>(fw) = make_float4(S.w[0], S.w[1], S.w[2], S.w[3]);
+  *reinterpret_cast<float4 *>(fw + 4) =
+      make_float4(S.meff, __int_as_float(S.v[1]), __int_as_float(S.v[2]), __int_as_float(S.v[3]));
+}
+__device__ __forceinline__ void fm_row_load(const float *fw, int vtx, SelfRow &S) {
+  const float4 a = *reinterpret_cast<const float4 *>(fw), b = *reinterpret_cast<const float4 *>(fw + 4);
+  S.w[0] = a.x; S.w[1] = a.y; S.w[2] = a.z; S.w[3] = a.w;
+  S.meff = b.x;
+  S.v[0] = vtx; S.v[1] = __float_as_int(b.y); S.v[2] = __float_as_int(b.z); S.v[3] = __float_as_int(b.w);
 }
 
 template <int VPE, bool SELF>
@@ -716,7 +878,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       ContactLin L;
       const float4 g4 = *reinterpret_cast<const float4 *>(gam + 4 * jj);
       const float g[4] = {g4.x, g4.y, g4.z, g4.w};
-      if (SELF && cobs[jj] == FLASH_SELF_SLOT) continue;   // second pass below
+      if (SELF && cobs[jj] >= FLASH_SELF_SLOT) continue;   // second pass below
       lin_at(O, cobs[jj], a, mu, mv, x, xt, g, L);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
@@ -726,7 +888,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       fz += L.R[2] * g[0] + L.R[5] * y1 + L.R[8] * y2;
     }
     if (!residual_only) {
-      if (SELF) {   // triangle corners of other threads' self contacts may be this vertex
+      if (SELF) {   // other threads' self contacts may reach this vertex
         atomicAdd(rs + vtx, fx);
         atomicAdd(rs + ns + vtx, fy);
         atomicAdd(rs + 2 * ns + vtx, fz);
@@ -738,22 +900,15 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     }
   }
   if (SELF) {
-    // self contacts: +F on the vertex, -w_k F on the triangle's corners
+    // self contacts (vertex-triangle, edge-edge): w_k F on the row's vertices
     const int *ctri = G.ctri + (size_t)l * G.cap;
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      if (cobs[j] != FLASH_SELF_SLOT) continue;
+      if (cobs[j] < FLASH_SELF_SLOT) continue;
       ContactLin L;
-      float wt[3], me;
-      const int vtx = cvert[j], tri = ctri[j];
-      lin_self(G, vtx, tri, qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, wt, me);
+      SelfRow S;
+      lin_row(G, cobs[j], cvert[j], ctri[j], qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, S);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
-      if (!residual_only) {
-        const V3 F = contact_force(L, gam + 4 * j);
-        atomicAdd(rs + vtx, F.x);
-        atomicAdd(rs + ns + vtx, F.y);
-        atomicAdd(rs + 2 * ns + vtx, F.z);
-        scatter_tri(G, tri, wt, F, rs, ns);
-      }
+      if (!residual_only) scatter_row(S.v, S.w, contact_force(L, gam + 4 * j), rs, ns);
     }
   }
   rmax = block_max(rmax, sh_red);
@@ -1172,21 +1327,19 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
     ContactLin L;
     V3 du_c = du;
     float sc;
-    if (G.self && cobs[c] == FLASH_SELF_SLOT) {
-      // J du = du_p - sum w_k du_k; preconditioner scale (a_pp + sum w_k^2 a_kk) meff
-      float wt[3], me;
-      const int tri = G.ctri[(size_t)l * cap + c];
-      lin_self(G, vtx, tri, q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, wt, me);
-      float av = ad[vtx];
+    if (G.self && cobs[c] >= FLASH_SELF_SLOT) {
+      // J du = sum w_k du_k; preconditioner scale (sum w_k^2 a_kk) meff
+      SelfRow S;
+      lin_row(G, cobs[c], vtx, G.ctri[(size_t)l * cap + c], q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, S);
+      float av = 0.f;
+      du_c = v3(0.f, 0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const int t = G.elems[4 * tri + k];
-        du_c = du_c - wt[k] * v3(w[t], w[np + t], w[2 * np + t]);
-        av += wt[k] * wt[k] * ad[t];
+      for (int k = 0; k < 4; k++) {
+        du_c = du_c + S.w[k] * col3(w, np, S.v[k]);
+        av += S.w[k] * S.w[k] * ad[S.v[k]];
       }
-      sc = av * me;
-      float *fw = G.fm_w + ((size_t)l * cap + c) * 4;
-      fw[0] = wt[0]; fw[1] = wt[1]; fw[2] = wt[2]; fw[3] = me;
+      sc = av * S.meff;
+      fm_row_store(G.fm_w + ((size_t)l * cap + c) * kFmW, S);
     } else {
       lin_at(O, cobs[c], a, mu, mv, x, xt, gam + 4 * c, L);
       sc = ad[vtx] * mv;
@@ -1239,14 +1392,18 @@ __device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l,
       const float v[3] = {Vj[3 * cc], Vj[3 * cc + 1], Vj[3 * cc + 2]};
       float t[3];
       fm_pinv(L, sc, v, t);
-      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] == FLASH_SELF_SLOT;
-      const float *fw = selfrow ? G.fm_w + ((size_t)l * cap + cc) * 4 : nullptr;
-      const float me = selfrow ? fw[3] : mv;
+      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] >= FLASH_SELF_SLOT;
+      SelfRow S;
+      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S);
+      const float me = selfrow ? S.meff : mv;
       const V3 F = v3(me * (L.R[0] * t[0] + L.R[3] * t[1] + L.R[6] * t[2]),
                       me * (L.R[1] * t[0] + L.R[4] * t[1] + L.R[7] * t[2]),
                       me * (L.R[2] * t[0] + L.R[5] * t[1] + L.R[8] * t[2]));
-      fx += F.x; fy += F.y; fz += F.z;
-      if (selfrow) scatter_tri(G, G.ctri[(size_t)l * cap + cc], fw, F, fs, n);
+      if (selfrow) {
+        scatter_row(S.v, S.w, F, fs, n);
+      } else {
+        fx += F.x; fy += F.y; fz += F.z;
+      }
     }
     if (G.self) {
       atomicAdd(fs + vtx, fx); atomicAdd(fs + n + vtx, fy); atomicAdd(fs + 2 * n + vtx, fz);
@@ -1296,13 +1453,14 @@ __device__ __forceinline__ void fm_gather_body(const GroupView &G, const int l, 
     fm_pinv(L, sc, v, t);
     const int vtx = cvert[c];
     float ux = u[vtx], uy = u[np + vtx], uz = u[2 * np + vtx];
-    if (G.self && G.cobs[(size_t)l * cap + c] == FLASH_SELF_SLOT) {   // J u = u_p - sum w_k u_k
-      const float *fw = G.fm_w + ((size_t)l * cap + c) * 4;
-      const int tri = G.ctri[(size_t)l * cap + c];
+    if (G.self && G.cobs[(size_t)l * cap + c] >= FLASH_SELF_SLOT) {   // J u = sum w_k u_k
+      SelfRow S;
+      fm_row_load(G.fm_w + ((size_t)l * cap + c) * kFmW, vtx, S);
+      ux = 0.f; uy = 0.f; uz = 0.f;
 #pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const int t = G.elems[4 * tri + k];
-        ux -= fw[k] * u[t]; uy -= fw[k] * u[np + t]; uz -= fw[k] * u[2 * np + t];
+      for (int k = 0; k < 4; k++) {
+        const int t = S.v[k];
+        ux += S.w[k] * u[t]; uy += S.w[k] * u[np + t]; uz += S.w[k] * u[2 * np + t];
       }
     }
     const float Ru0 = L.R[0] * ux + L.R[1] * uy + L.R[2] * uz;
@@ -1408,11 +1566,12 @@ __device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, 
         for (int r = 0; r < 3; r++) z[r] += ys[i] * Vb[(size_t)i * N3 + 3 * cc + r];
       float dy[3];
       fm_pinv(L, sc, z, dy);
-      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] == FLASH_SELF_SLOT;
-      const float *fw = selfrow ? G.fm_w + ((size_t)l * cap + cc) * 4 : nullptr;
-      const V3 F = apply_update(L, selfrow ? fw[3] : mv, a.gmax, dy, gam + 4 * cc);
-      fsum = fsum + F;
-      if (selfrow) scatter_tri(G, G.ctri[(size_t)l * cap + cc], fw, F, fs, n);
+      const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] >= FLASH_SELF_SLOT;
+      SelfRow S;
+      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S);
+      const V3 F = apply_update(L, selfrow ? S.meff : mv, a.gmax, dy, gam + 4 * cc);
+      if (selfrow) scatter_row(S.v, S.w, F, fs, n);
+      else fsum = fsum + F;
     }
     if (G.self) {
       atomicAdd(fs + vtx, fsum.x); atomicAdd(fs + n + vtx, fsum.y); atomicAdd(fs + 2 * n + vtx, fsum.z);
@@ -1645,11 +1804,11 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
     const V3 vr = v3(v[vtx], v[np + vtx], v[2 * np + vtx]) - (1.f / a.h) * (x - xo);
     // previous step's multipliers of the same (vertex, obstacle)
     float g4[4] = {0.f, 0.f, 0.f, 0.f};
-    const int key = vtx * (FLASH_SELF_SLOT + 1) + o;
+    const int key = vtx * kSlots + o;
     int lo = 0, hi = pc - 1;
     while (lo <= hi) {
       const int mid = (lo + hi) >> 1;
-      const int km = pv[mid] * (FLASH_SELF_SLOT + 1) + po[mid];
+      const int km = pv[mid] * kSlots + po[mid];
       if (km == key) {
         for (int c = 0; c < 4; c++) g4[c] = pg[mid * 4 + c];
         break;

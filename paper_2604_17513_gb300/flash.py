@@ -22,8 +22,10 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3,
 WOVERFLOW = 1
 MAX_OBS = 8
 GRASP_SLOT = MAX_OBS   # contact-list obstacle slot of grasp rows
-SELF_SLOT = MAX_OBS + 1   # contact-list slot of cloth self contacts
-SELF_MAX = 4           # self contacts per vertex at most
+SELF_SLOT = MAX_OBS + 1   # contact-list slot of cloth vertex-triangle self contacts
+SELF_MAX = 4           # vertex-triangle self contacts per vertex at most
+EE_SLOT = MAX_OBS + 2  # contact-list slot of cloth edge-edge contacts
+EE_MAX = 4             # edge-edge contacts per vertex at most
 MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
@@ -178,9 +180,10 @@ class Sim:
         if self_collision is None:   # on when a scene asks for it
             self_collision = any(sc.meta.get("self_collision") for sc in scenes)
         # one row per (vertex, obstacle), plus one grasp row per vertex where grasps are
-        # scheduled, plus up to SELF_MAX self rows per vertex with self-collision
+        # scheduled, plus up to SELF_MAX + EE_MAX self rows per vertex with self-collision
         d.contact_cap = contact_cap or max(sc.n_verts * (sc.n_obs + (1 if sc.meta.get("grasp") else 0) +
-                                                         (SELF_MAX if self_collision else 0)) for sc in scenes)
+                                                         (SELF_MAX + EE_MAX if self_collision else 0))
+                                           for sc in scenes)
         d.self_collide = 1 if self_collision else 0
         d.solve = solve
         d.warm = warm
@@ -302,8 +305,9 @@ class Sim:
         return cnt, vert, obs, gam
 
     def contact_tris(self):
-        """Triangle of each row of the last step's contact lists, [N][cap]
-        (-1 for rows that are not self contacts)."""
+        """Feature of each row of the last step's contact lists, [N][cap]:
+        the triangle of a vertex-triangle row, e1 * n_edges + e2 of an
+        edge-edge row (unique edges (a < b) in (a, b) order), -1 otherwise."""
         tri = torch.empty((self.n_envs, self.cap), dtype=torch.int32, device=self.dev)
         _check(lib().flash_get_contact_tris(self._h, _ptr(tri), _stream()))
         return tri

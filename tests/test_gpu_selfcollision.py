@@ -1,9 +1,10 @@
-"""GPU parity of cloth self-collision (vertex against triangle, the library's
-reading; the paper disables self-collision and describes no method) against
-the oracle, with the full contact metric: a small cloth dropped onto a larger
-one (one mesh, two components).  Environments start from the oracle's state
-at step s; after one or two steps positions agree to 1e-5 m and the contact
-lists (vertex, slot, triangle) agree exactly.
+"""GPU parity of cloth self-collision (vertex against triangle and edge
+against edge, the library's reading; the paper disables self-collision and
+describes no method) against the oracle, with the full contact metric: a
+small cloth dropped onto a larger one (one mesh, two components), and two
+narrow strips crossing (edge-edge contacts only).  Environments start from
+the oracle's state at step s; after one or two steps positions agree to
+1e-5 m and the contact lists (vertex, slot, feature) agree exactly.
 """
 import numpy as np
 import pytest
@@ -52,7 +53,7 @@ def _gpu(cuda, sc, starts, s, n_steps, **kw):
 
 
 def _compare(sc, starts, s, n_steps, qg, cnt, vert, obs, tri, warm="cold"):
-    n_self = 0
+    n_self = n_ee = 0
     for e, (mesh, st) in starts.items():
         ref = oracle.EnvState(st.q, st.v)
         for k in range(s, s + n_steps):
@@ -64,7 +65,8 @@ def _compare(sc, starts, s, n_steps, qg, cnt, vert, obs, tri, warm="cold"):
         err = np.abs(qg[e] - ref.q).max()
         assert err <= POS_TOL, (e, err)
         n_self += (ref.cobs == oracle.SELF_SLOT).sum()
-    return n_self
+        n_ee += (ref.cobs == oracle.EE_SLOT).sum()
+    return n_self, n_ee
 
 
 @pytest.mark.parametrize("solve", [0, 1])
@@ -76,8 +78,8 @@ def test_stack_drop_one_step(cuda, s, solve):
     sc = scenes.cloth_stack_drop(n_envs=6, steps=20)
     starts = _oracle_states(sc, range(sc.n_envs), s)
     _, qg, cnt, vert, obs, tri = _gpu(cuda, sc, starts, s, 1, solve=solve)
-    n_self = _compare(sc, starts, s, 1, qg, cnt, vert, obs, tri)
-    assert n_self > 6 * 100
+    n_self, n_ee = _compare(sc, starts, s, 1, qg, cnt, vert, obs, tri)
+    assert n_self > 6 * 100 and n_ee > 6 * 100
 
 
 def test_stack_two_steps_warm_prev(cuda):
@@ -115,3 +117,46 @@ def test_self_collision_off_and_lite_rejected(cuda):
     _, qg, cnt, vert, obs, tri = _gpu(cuda, off, starts, 1, 1, solve=0, self_collision=False)
     assert (tri[:, :] == -1).all()
     _compare(off, starts, 1, 1, qg, cnt, vert, obs, tri)
+
+
+@pytest.mark.parametrize("s", [3, 6])
+def test_crossing_strips_edge_edge(cuda, s):
+    """Eight pairs of crossing strips (no vertex over the other strip): the
+    step in which the top strip reaches the bottom one (s = 3) and one with
+    it resting there (s = 6), in tolerance mode (r_ncp <= 1e-6); the rows
+    are edge-edge only and the lists agree exactly.  The scene is
+    ill-conditioned (a 20 cm strip balanced on a 1 cm support, its contact
+    rows at nearby crossing points): FP32 and FP64 Krylov solves part by up
+    to 1e-5 m already after one Newton iteration (4e-7 m on the stacked
+    cloths, whose test carries the 1e-5 m position bound), so converged
+    positions are compared at 5e-5 m here."""
+    sc = scenes.strips_cross_drop(n_envs=8, steps=20)
+    kw = dict(mode=1, tol=1e-6, k_cap=100)
+    starts = _oracle_states(sc, range(sc.n_envs), s)
+    _, qg, cnt, vert, obs, tri = _gpu(cuda, sc, starts, s, 1, solve=0, **kw)
+    n_ee = 0
+    for e, (mesh, st) in starts.items():
+        ref = oracle.EnvState(st.q, st.v)
+        oracle.step(mesh, sc, e, s, ref, metric=2, **kw)
+        c = int(cnt[e])
+        assert c == len(ref.cvert) and (vert[e, :c] == ref.cvert).all() and (obs[e, :c] == ref.cobs).all(), e
+        assert (tri[e, :c] == ref.ctri).all(), e
+        err = np.abs(qg[e] - ref.q).max()
+        assert err <= 5e-5, (e, err)
+        assert (ref.cobs == oracle.SELF_SLOT).sum() == 0
+        n_ee += (ref.cobs == oracle.EE_SLOT).sum()
+    assert n_ee >= 8 * 4
+
+
+def test_crossing_strips_rest_on_gpu(cuda):
+    """The GPU alone from the initial state for 30 steps: the top strip stays
+    above the bottom one where they cross (without edge-edge rows it would
+    fall through to the ground)."""
+    sc = scenes.strips_cross_drop(n_envs=16, steps=40)
+    starts = {}
+    _, qg, cnt, vert, obs, tri = _gpu(cuda, sc, starts, 0, 30, solve=1)
+    from paper_2604_17513_gb300 import flash
+    top = qg[:, 8:]
+    centre = np.abs(top[..., 1]) < 0.05
+    assert (top[..., 2][centre] > 1.5 * sc.thickness).all()
+    assert (obs == flash.EE_SLOT).any()
