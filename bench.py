@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--eager", action="store_true",
+                   help="launch every step kernel by kernel (the host stops the tolerance loop) instead of a graph")
     p.add_argument("--no-warm-compare", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
@@ -513,12 +515,12 @@ def main():
         mode_kw.update(metric=flash.METRIC_FULL, lin_iters=args.lin_iters)
     warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
     try:
-        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, **mode_kw)
+        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, eager=args.eager, **mode_kw)
     except flash.FlashError:
         if args.solve != "auto":
             raise
         solve = flash.SOLVE_F32
-        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, **mode_kw)
+        sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, eager=args.eager, **mode_kw)
     q0, v0 = flash.state_tensors(sc, dev)
     sim.set_state(q0, v0)
     scs = sc if isinstance(sc, list) else [sc]
@@ -706,7 +708,7 @@ def main():
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
-                       "graph": args.mode == "fixed", "tile_widths": sorted(set(sim.tile_widths()))},
+                       "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths()))},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
             "status": status, "warm_start": warm_cmp,
             "step_hbm_frac_of_measured": step_hbm_frac,

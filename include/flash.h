@@ -6,8 +6,9 @@
  * scale) share one constant system matrix A = M + h^2 sum_i w_i G_i^T G_i
  * (Sec. III-B); every step of every environment runs in this library's CUDA
  * kernels.  Calls are stream-ordered: nothing synchronises the host except
- * flash_scene_finalize, the *_host getters and the tolerance mode of
- * flash_step, which reads a device flag once per iteration.
+ * flash_scene_finalize, the *_host getters, flash_launch_count and the
+ * eager tolerance mode of flash_step, which reads a device count every few
+ * iterations (the graphed tolerance mode decides on the device).
  *
  * Conventions
  *   - z is up; positions in metres; obstacle pose = (px,py,pz, qw,qx,qy,qz).
@@ -79,9 +80,13 @@ typedef int32_t flash_status;
  * environment.  solve: FLASH_SOLVE_*.  warm: FLASH_WARM_*.  lanes: number of
  * independent environment partitions stepped concurrently on their own
  * streams (0 = chosen from the batch size; results do not depend on it).
- * eager: 0 = a FLASH_MODE_FIXED step is captured once in a CUDA graph and
- * replayed (not while profiling or with the learned warm start or contact
- * recording on); 1 = every step launches its kernels one by one.
+ * eager: 0 = a step is captured once in a CUDA graph and replayed (not
+ * while profiling or with the learned warm start or contact recording on);
+ * in FLASH_MODE_TOL the graph holds the iteration loop as a while-node that
+ * the device keeps running while an environment is still iterating (at
+ * most k_cap runs), so a step needs no host round trip; 1 = every step
+ * launches its kernels one by one and the host stops the tolerance loop.
+ * Both give the same results.
  * metric: FLASH_METRIC_*.  lin_iters: linear-solver iterations of the full
  * metric, 1..32 (0 = 10, the paper's parameter table): each Newton step runs
  * that many GMRES steps on Z dy = rhs over all contacts of an environment,
@@ -305,7 +310,8 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
  * flash_profile_read synchronises
  * and returns the summed device time (ms) and launch count of one kind since
  * the last enable.  flash_launch_count returns the number of kernels this
- * scene has launched since creation. */
+ * scene has launched since creation; the iterations of a graphed tolerance
+ * loop are counted on the device, so it synchronises the device. */
 #define FLASH_KIND_BEGIN 0
 #define FLASH_KIND_LOCAL 1
 #define FLASH_KIND_SOLVE 2

@@ -6,6 +6,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <utility>
 
@@ -803,6 +804,8 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(dalloc(s, &s->done, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->rncp, (size_t)s->N));
   FLASH_CUDA_TRY(dalloc(s, &s->active, 1));
+  FLASH_CUDA_TRY(dalloc(s, &s->kit, 1));
+  FLASH_CUDA_TRY(dalloc(s, &s->trips, 1));
   FLASH_CUDA_TRY(dalloc(s, &s->gstate, (size_t)s->N));
   FLASH_CUDA_TRY(upload(s, &s->gobs, std::vector<int>(s->N, -1)));
   FLASH_CUDA_TRY(dalloc(s, &s->greq, (size_t)s->N));
@@ -911,9 +914,11 @@ void flash_scene_destroy(flash_scene *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  if (s->body_st) cudaStreamDestroy(s->body_st);
   for (flash::Lane &L : s->lanes) {
     if (L.done) cudaEventDestroy(L.done);
     if (L.st) cudaStreamDestroy(L.st);
+    if (L.body_st) cudaStreamDestroy(L.body_st);
   }
   if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   if (s->h_active) cudaFreeHost(s->h_active);
@@ -1028,6 +1033,9 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
 namespace {
 
 // One time step (Algorithm 1 body) issued on st and the lanes' streams.
+flash_status tol_loop_graphed(flash_scene *s, cudaStream_t st, const std::function<cudaError_t(int, int)> &local,
+                              const std::function<cudaError_t(cudaStream_t)> &solves);
+
 flash_status step_once(flash_scene *s, cudaStream_t st) {
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
   const StepArgs a = step_args(s);
@@ -1121,6 +1129,20 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
       }
       FLASH_CUDA_TRY(local(s->d.k_max + 1, 1));
       FLASH_CUDA_TRY(join(s, st));
+    } else if (s->capturing) {
+      // captured: the loop runs on the device (a graph while-node)
+      FLASH_CUDA_TRY(join(s, st));
+      const flash_status r = tol_loop_graphed(s, st, local, [&](cudaStream_t body) {
+        const cudaStream_t outer = st;
+        st = body;   // the phase lambdas issue on st and the lanes' streams
+        cudaError_t e = fork(s, st);
+        if (e == cudaSuccess) e = solves();
+        if (e == cudaSuccess) e = local(0, 0);
+        if (e == cudaSuccess) e = join(s, st);
+        st = outer;
+        return e;
+      });
+      if (r != FLASH_OK) return r;
     } else {
       // Every environment stops on the device (its local pass sets its done
       // flag; later passes skip it), so the host only needs to learn when all
@@ -1157,9 +1179,76 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
   return FLASH_OK;
 }
 
-// Capture one FLASH_MODE_FIXED step into a graph on an internal stream (the
-// caller's stream may be the legacy default stream, which cannot capture).
+// The tolerance mode's iterations (Algorithm 1's loop, stopped per
+// environment on r_ncp <= tol, Mode B) inside a captured step.  The first
+// iteration's local pass is issued ahead of a graph while-node; each run of
+// the node's body is {global solves, NCP, next local pass, k_tol_next}, and
+// k_tol_next keeps the node running while an environment is still iterating.
+// This is the host loop of the eager path with the host's reads of the
+// active count replaced by the device deciding: the iterations each
+// environment runs, and so the results, are the same.  The body is
+// captured into the node's own graph on separate streams (a stream that has
+// joined one capture cannot join another).
+flash_status tol_loop_graphed(flash_scene *s, cudaStream_t st, const std::function<cudaError_t(int, int)> &local,
+                              const std::function<cudaError_t(cudaStream_t)> &body_phases) {
+  const int last = s->d.k_cap + 1;
+  FLASH_CUDA_TRY(cudaMemsetAsync(s->active, 0, sizeof(int), st));
+  FLASH_CUDA_TRY(fork(s, st));
+  FLASH_CUDA_TRY(local(1, 0));
+  FLASH_CUDA_TRY(join(s, st));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  FLASH_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  FLASH_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+  FLASH_CUDA_TRY(launch_tol_next(h, s->active, s->kit, s->trips, last, 1, st));
+  s->launches++;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  FLASH_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  FLASH_CUDA_TRY(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &p));
+  if (!s->body_st) FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&s->body_st, cudaStreamNonBlocking));
+  if (s->lanes.size() > 1)
+    for (Lane &L : s->lanes)
+      if (!L.body_st) FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&L.body_st, cudaStreamNonBlocking));
+  FLASH_CUDA_TRY(cudaStreamBeginCaptureToGraph(s->body_st, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+  auto swap_lanes = [&] {
+    if (s->lanes.size() > 1)
+      for (Lane &L : s->lanes) std::swap(L.st, L.body_st);
+  };
+  swap_lanes();
+  const int64_t l0 = s->launches;
+  cudaError_t e = body_phases(s->body_st);
+  if (e == cudaSuccess) e = launch_tol_next(h, s->active, s->kit, s->trips, last, 0, s->body_st);
+  s->body_launches = s->launches - l0 + 1;
+  s->launches = l0;
+  swap_lanes();
+  cudaGraph_t body = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(s->body_st, &body);
+  FLASH_CUDA_TRY(e);
+  FLASH_CUDA_TRY(ee);
+  FLASH_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return FLASH_OK;
+}
+
+// Capture one step into a graph on an internal stream (the caller's stream
+// may be the legacy default stream, which cannot capture).
 flash_status capture_step(flash_scene *s) {
+  if (s->body_launches) {
+    // fold the previous graph's loop runs into the host count
+    unsigned long long trips = 0;
+    FLASH_CUDA_TRY(cudaMemcpy(&trips, s->trips, sizeof(trips), cudaMemcpyDeviceToHost));
+    FLASH_CUDA_TRY(cudaMemset(s->trips, 0, sizeof(trips)));
+    s->launches += (int64_t)trips * s->body_launches;
+    s->body_launches = 0;
+  }
   if (s->graph) {
     cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
@@ -1167,7 +1256,9 @@ flash_status capture_step(flash_scene *s) {
   if (!s->cap_st) FLASH_CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
   FLASH_CUDA_TRY(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
   const int64_t l0 = s->launches;
+  s->capturing = true;
   const flash_status r = step_once(s, s->cap_st);
+  s->capturing = false;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
   s->graph_launches = s->launches - l0;
@@ -1192,7 +1283,7 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
   if (learned && !s->mlp_params) return fail(FLASH_ESTATE, "learned warm start needs weights (flash_warmstart_set)");
   cudaStream_t st = (cudaStream_t)stream;
-  const bool graphed = !s->d.eager && s->d.mode == FLASH_MODE_FIXED && !s->profiling && !learned && !s->record;
+  const bool graphed = !s->d.eager && !s->profiling && !learned && !s->record;
   if (graphed) {
     if (!s->graph || s->graph_stale) {
       const flash_status r = capture_step(s);
@@ -1286,7 +1377,14 @@ flash_status flash_profile_read(flash_scene *s, int32_t kind, double *total_ms, 
   return FLASH_OK;
 }
 
-int64_t flash_launch_count(const flash_scene *s) { return s ? s->launches : 0; }
+int64_t flash_launch_count(const flash_scene *s) {
+  if (!s) return 0;
+  if (!s->trips || !s->body_launches) return s->launches;
+  // kernels of the graphed tolerance loop: known on the device only
+  unsigned long long trips = 0;
+  if (cudaMemcpy(&trips, s->trips, sizeof(trips), cudaMemcpyDeviceToHost) != cudaSuccess) return s->launches;
+  return s->launches + (int64_t)trips * s->body_launches;
+}
 
 int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int32_t)s->lanes.size() : 0; }
 

@@ -140,6 +140,7 @@ struct LaneRange {
 struct Lane {
   cudaStream_t st = nullptr;    // null: the caller's stream (single-lane scenes)
   cudaEvent_t done = nullptr;   // join event
+  cudaStream_t body_st = nullptr;   // the lane's stream while the tolerance loop's body is captured
   std::vector<LaneRange> ranges;
   Batch all;                    // begin / NCP / end over the lane's environments
   std::vector<Batch> local;     // local pass, by element type and shared-memory class
@@ -177,6 +178,8 @@ struct flash_scene {
   int *status = nullptr;      // device status word
   int *active = nullptr;      // device counter of environments still iterating
   int *h_active = nullptr;    // pinned host mirror
+  int *kit = nullptr;         // device iteration index of the graphed tolerance loop
+  unsigned long long *trips = nullptr;   // device count of that loop's body runs (launch accounting)
   int64_t *d_voff = nullptr;
   std::vector<void *> allocs;
   // launch accounting
@@ -199,7 +202,10 @@ struct flash_scene {
   // captured FLASH_MODE_FIXED step, replayed by flash_step
   cudaStream_t cap_st = nullptr;
   cudaGraphExec_t graph = nullptr;
-  int64_t graph_launches = 0;   // kernels in one replay
+  int64_t graph_launches = 0;   // kernels in one replay (outside a tolerance loop's body)
+  int64_t body_launches = 0;    // kernels in one run of the tolerance loop's body
+  cudaStream_t body_st = nullptr;   // captures the tolerance loop's body
+  bool capturing = false;       // step_once is being captured
   bool graph_stale = true;      // a setting that changes the step's launches has changed
 };
 
@@ -283,6 +289,8 @@ cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int
 cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
                               cudaStream_t st, int *launched);
 cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);
+cudaError_t launch_tol_next(cudaGraphConditionalHandle h, int *active, int *kit, unsigned long long *trips, int last,
+                            int first, cudaStream_t st);
 cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
 // full contact metric: Newton step with preconditioned GMRES on Z = J A^-1 J^T + E
 cudaError_t launch_fm_setup_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);

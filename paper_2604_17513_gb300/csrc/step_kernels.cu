@@ -58,6 +58,7 @@ struct EnvView {
   const float *mu, *odims, *ocomp, *pose_t, *pose_th;
   const int *otype;
   int *iters, *done, *status, *active;
+  const int *kit;
   float *rncp;
   int *gstate;
   const int *gobs;
@@ -88,6 +89,7 @@ EnvView eview(const flash_scene *s) {
   EnvView e;
   e.mu = s->mu; e.odims = s->odims; e.ocomp = s->ocomp; e.pose_t = s->pose_t; e.pose_th = s->pose_th;
   e.otype = s->otype; e.iters = s->iters; e.done = s->done; e.status = s->status; e.active = s->active;
+  e.kit = s->kit;
   e.rncp = s->rncp;
   e.gstate = s->gstate; e.gobs = s->gobs; e.ganchor = s->ganchor;
   return e;
@@ -1667,7 +1669,24 @@ __global__ void __launch_bounds__(512, 2) k_local_tab(const GroupView *__restric
                                                       EnvView V, StepArgs a, int k, int residual_only, int tc,
                                                       int pending) {
   const int2 b = map[blockIdx.x];
+  if (k == 0) {   // inside the graphed tolerance loop: the iteration index is on the device
+    k = *V.kit;
+    pending = k > 1;
+  }
   local_body<VPE, SELF>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
+}
+// End of one iteration of the graphed tolerance loop (Mode B): the loop runs
+// again while some environment is still iterating and the cap allows; the
+// index only grows, so the loop ends after at most `last` - 1 runs whatever
+// the kernels computed.  first = 1 after the loop's first iteration, which
+// runs ahead of the loop with a literal index.
+__global__ void k_tol_next(cudaGraphConditionalHandle h, int *active, int *kit, unsigned long long *trips, int last,
+                           int first) {
+  const int k = first ? 1 : *kit;
+  cudaGraphSetConditional(h, (*active > 0 && k < last) ? 1u : 0u);
+  *active = 0;
+  *kit = k + 1;
+  if (!first) *trips += 1;
 }
 __global__ void __launch_bounds__(256, 4) k_ncp_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                     EnvView V, StepArgs a, int tc) {
@@ -2100,6 +2119,12 @@ cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArg
     ++*launched;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_tol_next(cudaGraphConditionalHandle h, int *active, int *kit, unsigned long long *trips, int last,
+                            int first, cudaStream_t st) {
+  k_tol_next<<<1, 1, 0, st>>>(h, active, kit, trips, last, first);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st) {

@@ -362,6 +362,43 @@ def test_lanes_do_not_change_results(cuda, solve, mode):
         assert np.array_equal(q, out[0][0]) and np.array_equal(it, out[0][1]) and st == out[0][2]
 
 
+def test_graphed_tolerance_loop_full_metric(cuda):
+    """Tolerance mode replayed from a graph whose iteration loop is a device
+    while-node (the device decides when every environment has stopped) gives
+    bit-identical states, iteration counts and residuals to the eager host
+    loop, on the full contact metric with two lanes.  Launch accounting: the
+    kernels of one graphed step are a fixed part plus a fixed body per loop
+    run, and the loop runs once per iteration after the first of the slowest
+    environment."""
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.tet_squeeze(n_envs=40, steps=12)
+    out, deltas = [], []
+    for eager in (True, False):
+        sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, metric=flash.METRIC_FULL, mode=flash.MODE_TOL, tol=1e-5,
+                        k_cap=60, lanes=2, eager=eager)
+        q0, v0 = flash.state_tensors(sc, cuda)
+        sim.set_state(q0, v0)
+        sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        its = []
+        for s in range(10):
+            sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            l0 = sim.launch_count()
+            sim.step(1)
+            it, r = sim.stats()
+            its.append(it.cpu().numpy())
+            deltas.append((eager, sim.launch_count() - l0, int(it.max().item())))
+        out.append((sim.get_state()[0].cpu().numpy(), np.stack(its), r.cpu().numpy(), sim.status()))
+    (qe, ite, re, se), (qg, itg, rg, sg) = out
+    assert se == 0 and sg == 0
+    assert np.array_equal(qe, qg) and np.array_equal(ite, itg) and np.array_equal(re, rg)
+    pts = sorted({(m, d) for eager, d, m in deltas if not eager})
+    assert len(pts) >= 2, pts
+    (m0, d0), (m1, d1) = pts[0], pts[-1]
+    assert m1 > m0 and (d1 - d0) % (m1 - m0) == 0, pts
+    body = (d1 - d0) // (m1 - m0)
+    assert body > 0 and all(d - d0 == body * (m - m0) for m, d in pts), pts
+
+
 @pytest.mark.parametrize("solve", SOLVES)
 def test_global_apply_eigen_form(cuda, solve):
     """Per-environment stiffness on one tet mesh: the library applies
