@@ -20,12 +20,16 @@ _SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c", "raycast.c")]
 _lib = None
 
 DP_H, DP_GX, DP_GY, DP_GZ, DP_TOL, DP_MAXFORCE, DP_TAU, DP_MARGIN, DP_MU, DP_GRASP_OBS = range(10)
-DP_ANCHOR, DP_SELF, DP_SIZE = 10, 13, 14
+DP_ANCHOR, DP_SELF, DP_OFEAT, DP_SIZE = 10, 13, 14, 15
 GRASP_SLOT = 8   # contact-list slot of grasp constraints (after every obstacle)
 SELF_SLOT = 9    # contact-list slot of cloth vertex-triangle self contacts (after the grasp row)
 SELF_MAX = 4     # vertex-triangle self contacts per vertex at most
 EE_SLOT = 10     # contact-list slot of cloth edge-edge self contacts
 EE_MAX = 4       # edge-edge self contacts per vertex (owning the first edge) at most
+OVT_SLOT = 11    # contact-list slot of box corners against cloth triangles (under the triangle's first vertex)
+OEE_SLOT = 12    # contact-list slot of box edges against cloth edges (under the edge's first vertex)
+OFEAT_MAX = 4    # rows of each box-feature kind per vertex at most
+MAX_OBS = 8      # obstacle slots per environment (box-feature indices count in them)
 IP_KMAX, IP_KMIN, IP_KCAP, IP_MODE, IP_METRIC, IP_LINIT = range(6)
 
 
@@ -191,6 +195,7 @@ def params(sc, env: int = 0, mode=None, metric: int = 0, k_max=None, k_min=None,
     if g:
         dp[DP_ANCHOR:DP_ANCHOR + 3] = g["anchor"]
     dp[DP_SELF] = 1.0 if (sc.meta and sc.meta.get("self_collision")) else 0.0
+    dp[DP_OFEAT] = 1.0 if (sc.meta and sc.meta.get("obstacle_features")) else 0.0
     ip = np.zeros(6, np.int32)
     ip[IP_KMAX] = sc.k_max if k_max is None else k_max
     ip[IP_KMIN] = sc.k_min if k_min is None else k_min
@@ -246,7 +251,7 @@ def detect(mesh: Mesh, sc, env, step, q, v, dp=None, attached=None):
     K = sc.n_obs
     ot, od = _i32(sc.obs_type[env]), _f64(sc.obs_dims[env])
     pth = _f64(sc.poses[env, step + 1])
-    cap = mesh.n * (K + 1 + SELF_MAX + EE_MAX)
+    cap = mesh.n * (K + 1 + SELF_MAX + EE_MAX + 2 * OFEAT_MAX)
     cv, co, ct = np.zeros(cap, np.int32), np.zeros(cap, np.int32), np.zeros(cap, np.int32)
     att = None if attached is None else np.ascontiguousarray(attached, np.uint8)
     cnt = lib().or_detect(mesh._p, _pd(dp), K, _pi(ot), _pd(od), _pd(pth), _pd(_f64(q)), _pd(_f64(v)),

@@ -586,11 +586,61 @@ static int ee_candidate(const OrMesh *m, double reach, int e1, int e2, const dou
   return 1;
 }
 
+/* Box corner k (0..7) in the box's frame: bit i of k set = +dims[i] on axis
+ * i, clear = -dims[i] (dims are half extents). */
+static void box_corner(const double *dims, int k, double *p) {
+  for (int i = 0; i < 3; i++) p[i] = (k >> i & 1) ? dims[i] : -dims[i];
+}
+
+/* Box edge j (0..11) in the box's frame: along axis a = j / 4 from -dims[a]
+ * to +dims[a], on the sides of the other two axes (b < c) given by bits 0
+ * (b) and 1 (c) of j % 4. */
+static void box_edge(const double *dims, int j, double *p0, double *p1) {
+  const int a = j / 4, m = j % 4, b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  p0[a] = -dims[a];
+  p1[a] = dims[a];
+  p0[b] = p1[b] = (m & 1) ? dims[b] : -dims[b];
+  p0[c] = p1[c] = (m & 2) ? dims[c] : -dims[c];
+}
+
+/* Box-corner candidate (a reading, like the vertex-triangle self contact):
+ * the corner C (at the obstacle's pose at t+h) within reach of triangle f's
+ * plane with its projection inside f up to OR_SELF_BARY, at q_t or q~. */
+static int ovt_candidate(const OrMesh *m, double reach, int f, const double *C, const double *x0, const double *x1) {
+  const int *t = m->elems + 3 * f;
+  for (int k = 0; k < 2; k++) {
+    const double *x = k == 0 ? x0 : x1;
+    double nh[3], d, w[3];
+    if (!tri_plane(x + 3 * t[0], x + 3 * t[1], x + 3 * t[2], C, nh, &d, w)) continue;
+    if (fabs(d) < reach && w[0] >= -OR_SELF_BARY && w[1] >= -OR_SELF_BARY && w[2] >= -OR_SELF_BARY) return 1;
+  }
+  return 0;
+}
+
+/* Box-edge candidate (a reading, like the edge-edge self contact): the box
+ * edge (C, D) (at t+h) and the cloth edge e = (a, b), whose lines' closest
+ * points lie inside both and nearer than reach, at q_t or q~. */
+static int oee_candidate(const OrMesh *m, double reach, int e, const double *C, const double *D, const double *x0,
+                         const double *x1) {
+  const int a = m->ed[2 * e], b = m->ed[2 * e + 1];
+  for (int k = 0; k < 2; k++) {
+    const double *x = k == 0 ? x0 : x1;
+    double s, t;
+    if (!line_params(x + 3 * a, x + 3 * b, C, D, &s, &t)) continue;
+    if (!(s > 0 && s < 1 && t > 0 && t < 1)) continue;
+    double dd[3];
+    for (int i = 0; i < 3; i++) dd[i] = (1 - s) * x[3 * a + i] + s * x[3 * b + i] - (1 - t) * C[i] - t * D[i];
+    if (norm3(dd) < reach) return 1;
+  }
+  return 0;
+}
+
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
               int cap, int *cvert, int *cobs, int *ctri) {
   double h = dp[OR_DP_H], tau = dp[OR_DP_TAU], marg = dp[OR_DP_MARGIN];
   const int self = dp[OR_DP_SELF] != 0.0 && m->type == OR_TRI;
+  const int ofeat = dp[OR_DP_OFEAT] != 0.0 && m->type == OR_TRI;
   double *xp = (double *)malloc(sizeof(double) * 3 * (m->n > 0 ? m->n : 1));
   for (int i = 0; i < m->n; i++)
     for (int c = 0; c < 3; c++) xp[3 * i + c] = q[3 * i + c] + h * v[3 * i + c] + h * h * dp[OR_DP_GX + c];
@@ -629,6 +679,43 @@ int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const 
           cnt++;
           ne_i++;
         }
+    }
+    /* box features: corners against the triangles whose first vertex is i,
+     * then box edges against the edges (i, b), each in feature order */
+    int nc_i = 0;
+    for (int f = 0; ofeat && f < m->ne && nc_i < OR_OFEAT_MAX; f++) {
+      if (m->elems[3 * f] != i) continue;
+      for (int o = 0; o < K && nc_i < OR_OFEAT_MAX; o++) {
+        if (otype[o] != OR_BOX) continue;
+        for (int kc = 0; kc < 8 && nc_i < OR_OFEAT_MAX; kc++) {
+          double cb[3], C[3];
+          box_corner(odims + 3 * o, kc, cb);
+          to_world(pose_th + 7 * o, cb, C);
+          if (ovt_candidate(m, tau + marg, f, C, q, xp)) {
+            if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_OVT_SLOT; if (ctri) ctri[cnt] = (f * OR_MAX_OBS + o) * 8 + kc; }
+            cnt++;
+            nc_i++;
+          }
+        }
+      }
+    }
+    int nb_i = 0;
+    for (int e = 0; ofeat && e < m->ned && nb_i < OR_OFEAT_MAX; e++) {
+      if (m->ed[2 * e] != i) continue;
+      for (int o = 0; o < K && nb_i < OR_OFEAT_MAX; o++) {
+        if (otype[o] != OR_BOX) continue;
+        for (int j = 0; j < 12 && nb_i < OR_OFEAT_MAX; j++) {
+          double b0[3], b1[3], C[3], D[3];
+          box_edge(odims + 3 * o, j, b0, b1);
+          to_world(pose_th + 7 * o, b0, C);
+          to_world(pose_th + 7 * o, b1, D);
+          if (oee_candidate(m, tau + marg, e, C, D, q, xp)) {
+            if (cnt < cap) { cvert[cnt] = i; cobs[cnt] = OR_OEE_SLOT; if (ctri) ctri[cnt] = (e * OR_MAX_OBS + o) * 12 + j; }
+            cnt++;
+            nb_i++;
+          }
+        }
+      }
     }
   }
   free(xp);
@@ -826,6 +913,95 @@ static void linearize_ee(const OrMesh *m, double tau, double mu, double h, int e
   contact_law(n, dot3(n, dd) - tau, rel, 0.0, mu, h, L->meff, g, L);
 }
 
+/* Box corner k of obstacle o against triangle f (a reading; feature
+ * (f * OR_MAX_OBS + o) * 8 + k).  The contact point moves as sum_i w_i x_i
+ * over f's corners, w the barycentric weights of the box corner's
+ * projection on f's plane at x; frame normal n = f's unit normal, oriented
+ * towards the side the cloth was on, seen from the box corner, at t; gap =
+ * n.(sum_i w_i x_i - C) - tau with C the box corner at t+h; slip = that
+ * point's displacement relative to the box corner over the step. */
+static void linearize_ovt(const OrMesh *m, const double *odims, const double *pose_t, const double *pose_th,
+                          double tau, double mu, double h, int feat, const double *q, const double *qt,
+                          const double *g, Lin *L) {
+  const int f = feat / (8 * OR_MAX_OBS), o = feat / 8 % OR_MAX_OBS, kc = feat % 8;
+  const int *t = m->elems + 3 * f;
+  double cb[3], C[3], Ct[3];
+  box_corner(odims + 3 * o, kc, cb);
+  to_world(pose_th + 7 * o, cb, C);
+  to_world(pose_t + 7 * o, cb, Ct);
+  double nh[3], d, w[3], nt[3], dt, wt[3];
+  if (!tri_plane(q + 3 * t[0], q + 3 * t[1], q + 3 * t[2], C, nh, &d, w)) {
+    nh[0] = 0; nh[1] = 0; nh[2] = 1; d = 0; w[0] = w[1] = w[2] = 1.0 / 3.0;
+  }
+  /* the cloth lies on the -nt side of the corner when the corner is on its +nt side */
+  double side = 1.0;
+  if (tri_plane(qt + 3 * t[0], qt + 3 * t[1], qt + 3 * t[2], Ct, nt, &dt, wt) && dt > 0) side = -1.0;
+  double n[3] = {side * nh[0], side * nh[1], side * nh[2]};
+  double inv = 0, rel[3];
+  L->nv = 3;
+  for (int i = 0; i < 3; i++) {
+    L->vi[i] = t[i];
+    L->w[i] = w[i];
+    inv += w[i] * w[i] / m->mass[t[i]];
+  }
+  L->meff = 1.0 / inv;
+  for (int c = 0; c < 3; c++) {
+    rel[c] = -(C[c] - Ct[c]);
+    for (int i = 0; i < 3; i++) rel[c] += w[i] * (q[3 * t[i] + c] - qt[3 * t[i] + c]);
+  }
+  /* n.(sum w x - C) = n.(-d nh) */
+  contact_law(n, -side * d - tau, rel, 0.0, mu, h, L->meff, g, L);
+}
+
+/* Box edge j of obstacle o against the cloth edge e = (a, b) (a reading;
+ * feature (e * OR_MAX_OBS + o) * 12 + j).  (s, t) = closest points of the
+ * cloth edge's line and the box edge's line (C, D at t+h) at x (1/2 when
+ * parallel); the contact point moves as (1 - s) x_a + s x_b; frame normal =
+ * the unit normal of both lines at x, oriented by the side the cloth edge
+ * was on at t; gap = n.((1 - s) x_a + s x_b - (1 - t) C - t D) - tau; slip
+ * = that difference's displacement over the step. */
+static void linearize_oee(const OrMesh *m, const double *odims, const double *pose_t, const double *pose_th,
+                          double tau, double mu, double h, int feat, const double *q, const double *qt,
+                          const double *g, Lin *L) {
+  const int e = feat / (12 * OR_MAX_OBS), o = feat / 12 % OR_MAX_OBS, j = feat % 12;
+  const int a = m->ed[2 * e], b = m->ed[2 * e + 1];
+  double b0[3], b1[3], C[3], D[3], Ct[3], Dt[3];
+  box_edge(odims + 3 * o, j, b0, b1);
+  to_world(pose_th + 7 * o, b0, C);
+  to_world(pose_th + 7 * o, b1, D);
+  to_world(pose_t + 7 * o, b0, Ct);
+  to_world(pose_t + 7 * o, b1, Dt);
+  double s = 0.5, t = 0.5;
+  line_params(q + 3 * a, q + 3 * b, C, D, &s, &t);
+  double d1[3], d2[3], nr[3], e1t[3], e2t[3], nt[3], at[3];
+  for (int i = 0; i < 3; i++) {
+    d1[i] = q[3 * b + i] - q[3 * a + i];
+    d2[i] = D[i] - C[i];
+    e1t[i] = qt[3 * b + i] - qt[3 * a + i];
+    e2t[i] = Dt[i] - Ct[i];
+    at[i] = qt[3 * a + i] - Ct[i];
+  }
+  cross3(d1, d2, nr);
+  double nn = norm3(nr);
+  if (nn > 0) for (int i = 0; i < 3; i++) nr[i] /= nn;
+  else { nr[0] = 0; nr[1] = 0; nr[2] = 1; }
+  /* side at the step start: nt is normal to both lines, so nt.(a - C) is
+   * the same for any pair of points on them */
+  cross3(e1t, e2t, nt);
+  const double side = dot3(nt, at) < 0 ? -1.0 : 1.0;
+  double n[3] = {side * nr[0], side * nr[1], side * nr[2]}, dd[3], rel[3];
+  L->nv = 2;
+  L->vi[0] = a; L->vi[1] = b;
+  L->w[0] = 1 - s; L->w[1] = s;
+  L->meff = 1.0 / ((1 - s) * (1 - s) / m->mass[a] + s * s / m->mass[b]);
+  for (int i = 0; i < 3; i++) {
+    dd[i] = (1 - s) * q[3 * a + i] + s * q[3 * b + i] - (1 - t) * C[i] - t * D[i];
+    rel[i] = (1 - s) * (q[3 * a + i] - qt[3 * a + i]) + s * (q[3 * b + i] - qt[3 * b + i]) -
+             (1 - t) * (C[i] - Ct[i]) - t * (D[i] - Dt[i]);
+  }
+  contact_law(n, dot3(n, dd) - tau, rel, 0.0, mu, h, L->meff, g, L);
+}
+
 /* Gaussian elimination with partial pivoting, in place; x = A^-1 b (size k) */
 static void gauss_solve(int k, double *A, double *b) {
   for (int c = 0; c < k; c++) {
@@ -879,6 +1055,11 @@ static void contact_lin_all(const OrMesh *m, const double *dp, const int *otype,
     if (o == OR_EE_SLOT) {
       linearize_ee(m, dp[OR_DP_TAU], dp[OR_DP_MU], dp[OR_DP_H], ctri[i] / m->ned, ctri[i] % m->ned, q, qt,
                    cg + 4 * i, L);
+      continue;
+    }
+    if (o == OR_OVT_SLOT || o == OR_OEE_SLOT) {
+      (o == OR_OVT_SLOT ? linearize_ovt : linearize_oee)(m, odims, pose_t, pose_th, dp[OR_DP_TAU], dp[OR_DP_MU],
+                                                         dp[OR_DP_H], ctri[i], q, qt, cg + 4 * i, L);
       continue;
     }
     if (o == OR_GRASP_SLOT) linearize_grasp(dp, pose_th, q + 3 * v, L);

@@ -51,7 +51,8 @@ typedef struct OrMesh OrMesh;
 #define OR_DP_GRASP_OBS 9 /* obstacle carrying the grasp anchor (as a double), -1: no grasp */
 #define OR_DP_ANCHOR 10   /* 10..12: anchor point in that obstacle's frame */
 #define OR_DP_SELF 13 /* nonzero: cloth self-collision (vertex against triangle) */
-#define OR_DP_SIZE 14
+#define OR_DP_OFEAT 14 /* nonzero: box corners and edges against cloth triangles and edges */
+#define OR_DP_SIZE 15
 
 /* Bilateral grasp (appendix, Bilateral Constraint for Cloth Control): a
  * grasped vertex i carries the equality C = x_i - p_grip = 0 with p_grip the
@@ -69,6 +70,18 @@ typedef struct OrMesh OrMesh;
  * sorted; each unordered pair once): at most OR_EE_MAX per vertex i. */
 #define OR_EE_SLOT 10
 #define OR_EE_MAX 4
+/* Contacts of box obstacle features with a cloth (a reading: the paper
+ * describes none; a vertex row cannot see a box corner or edge that passes
+ * between the cloth's vertices).  Box corner k (0..7) of obstacle o against
+ * triangle f: slot OR_OVT_SLOT, feature (f * OR_MAX_OBS + o) * 8 + k,
+ * listed under f's first vertex.  Box edge j (0..11) of obstacle o against
+ * the cloth edge e = (a, b): slot OR_OEE_SLOT, feature (e * OR_MAX_OBS + o)
+ * * 12 + j, listed under a.  At most OR_OFEAT_MAX of each per vertex, in
+ * feature order. */
+#define OR_OVT_SLOT 11
+#define OR_OEE_SLOT 12
+#define OR_OFEAT_MAX 4
+#define OR_MAX_OBS 8
 #define OR_NDP 9
 /* ip[] (integer parameters) */
 #define OR_IP_KMAX 0
@@ -101,7 +114,8 @@ double or_sdf(int type, const double *dims, const double *pose, const double *x,
 /* attached: [n] grasp flags (or NULL); a flagged vertex gets an OR_GRASP_SLOT
  * entry after its obstacle contacts, then its self contacts (OR_SELF_SLOT,
  * triangle in ctri; OR_EE_SLOT, edge pair in ctri; -1 for the other rows;
- * ctri may be NULL) when dp[OR_DP_SELF] is set */
+ * ctri may be NULL) when dp[OR_DP_SELF] is set, then its box-feature rows
+ * (OR_OVT_SLOT, OR_OEE_SLOT) when dp[OR_DP_OFEAT] is set */
 int or_detect(const OrMesh *m, const double *dp, int K, const int *otype, const double *odims,
               const double *pose_th, const double *q, const double *v, const unsigned char *attached,
               int cap, int *cvert, int *cobs, int *ctri);

@@ -645,3 +645,95 @@ def strips_cross_drop(seed: int = 6, n_envs: int = 4, steps: int = 40, k_max: in
     return Scene("strips_cross_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0), mu, np.ones(n_envs),
                  obs_type, np.zeros((n_envs, K, 3)), np.zeros((n_envs, K)), poses, h=0.01, k_max=k_max,
                  thickness=tau, steps=steps, meta={"self_collision": True})
+
+
+def cloth_bar_drop(seed: int = 7, n_envs: int = 4, n_side: int = 16, side: float = 0.25, steps: int = 40,
+                   k_max: int = 10) -> Scene:
+    """A cloth released flat a few millimetres above a thin horizontal bar
+    and a thin vertical post, both box obstacles narrower than the cloth's
+    cells, over the ground.  The bar (5 x 5 mm section, 40 cm long) runs
+    along x midway between vertex rows n_side/4 and n_side/4 + 1; the post
+    (6 x 6 mm section, 6 cm tall) stands under the incentre of a triangle
+    (the cell at column n_side/2, row 3 n_side/4 - 1), its top inside that
+    triangle.  Both tops are at z = 5 cm.  The cloth meets them between its
+    vertices, through box edges against cloth edges and box corners against
+    cloth triangles (meta["obstacle_features"]); without those rows it falls
+    past both.  Per environment: the bar turned by U[-4, 4] degrees about z
+    (environment 0: not turned), release height U[2, 6] mm above the tops,
+    mu ~ U[0.2, 0.6]; h = 1/100; the areal mass and stiffness of the other
+    cloths."""
+    rest, tris = cloth_grid(n_side, n_side, side)
+    n = len(rest)
+    sp = side / (n_side - 1)
+    mass = np.full(n, 0.1 * side * side / 0.25 / n)
+    tau, z_top = 1e-3, 0.05
+    K = 3
+    obs_type = np.tile(np.array([PLANE, BOX, BOX], np.int32), (n_envs, 1))
+    obs_dims = np.zeros((n_envs, K, 3))
+    obs_dims[:, 1] = (0.2, 0.0025, 0.0025)
+    obs_dims[:, 2] = (0.003, 0.003, 0.03)
+    jb = n_side // 4
+    y_bar = -side / 2 + (jb + 0.5) * sp
+    ip, jp = n_side // 2, 3 * n_side // 4 - 1
+    r_in = sp * (2 - np.sqrt(2)) / 2     # incentre of the right-angled triangle at the cell's corner (ip, jp)
+    post = (-side / 2 + ip * sp + r_in, -side / 2 + jp * sp + r_in, z_top - 0.03)
+    mu = np.zeros(n_envs)
+    q0 = np.zeros((n_envs, n, 3))
+    poses = np.zeros((n_envs, steps + 1, K, 7))
+    for e in range(n_envs):
+        g = env_rng(seed, e)
+        mu[e] = g.uniform(0.2, 0.6)
+        yaw = 0.0 if e == 0 else np.deg2rad(g.uniform(-4.0, 4.0))
+        drop = g.uniform(0.002, 0.006)
+        poses[e, :, 0] = _pose((0, 0, 0))
+        poses[e, :, 1] = _pose((0.0, y_bar, z_top - 0.0025), _quat_axis_angle((0, 0, 1), yaw))
+        poses[e, :, 2] = _pose(post)
+        q0[e] = rest + [0.0, 0.0, z_top + tau + drop]
+    return Scene("cloth_bar_drop", TRI, rest, tris, mass, 1e4, 10.0, q0, np.zeros_like(q0), mu, np.ones(n_envs),
+                 obs_type, obs_dims, np.zeros((n_envs, K)), poses, h=0.01, k_max=k_max, thickness=tau, steps=steps,
+                 meta={"obstacle_features": True})
+
+
+def corner_support(steps: int = 4, mu: float = 0.5) -> Scene:
+    """One equilateral triangle (4 cm sides, 1 g per vertex) lying flat with
+    its centroid one thickness above the top corner of a cube (2 cm side)
+    standing on a vertex: the cube's (1, 1, 1) diagonal is turned onto +z, so
+    corner 7 = (+,+,+) is the top, the three next corners are 1.15 cm lower
+    (out of reach).  No other obstacle; box-feature rows on."""
+    tau, d, zc = 1e-3, 0.01, 0.1
+    L = 0.04
+    rest = np.array([(L / np.sqrt(3) * np.cos(a), L / np.sqrt(3) * np.sin(a), 0.0)
+                     for a in (np.pi / 2, np.pi / 2 + 2 * np.pi / 3, np.pi / 2 + 4 * np.pi / 3)])
+    tris = np.array([(0, 1, 2)], np.int32)
+    u = np.array([1.0, 1.0, 1.0]) / np.sqrt(3)
+    axis = np.cross(u, [0.0, 0.0, 1.0])
+    quat = _quat_axis_angle(axis, np.arccos(u[2]))
+    z_corner = zc + d * np.sqrt(3)
+    q0 = (rest + [0.0, 0.0, z_corner + tau])[None]
+    K = 1
+    poses = np.zeros((1, steps + 1, K, 7))
+    poses[0, :, 0] = _pose((0.0, 0.0, zc), quat)
+    return Scene("corner_support", TRI, rest, tris, np.full(3, 1e-3), 1e4, 10.0, q0, np.zeros_like(q0),
+                 np.array([mu]), np.ones(1), np.full((1, K), BOX, np.int32), np.full((1, K, 3), d),
+                 np.zeros((1, K)), poses, h=0.01, thickness=tau, steps=steps, meta={"obstacle_features": True})
+
+
+def edge_support(steps: int = 4, mu: float = 0.5) -> Scene:
+    """A square of two triangles (4 cm sides, 1 g per vertex, diagonal from
+    vertex 0 to vertex 3) lying flat one thickness above the top edge of a
+    bar (10 x 2 x 2 cm) turned by 45 degrees about its long axis x, so that
+    one of its long edges is the top, under the square's middle line y = 0;
+    the bar's other edges are out of reach.  That edge crosses the square's
+    edges 0-2, 0-3 and 1-3 at their midpoints.  No other obstacle;
+    box-feature rows on."""
+    tau, d, zc = 1e-3, 0.01, 0.1
+    rest, tris = cloth_grid(2, 2, 0.04)
+    z_edge = zc + d * np.sqrt(2)
+    q0 = (rest + [0.0, 0.0, z_edge + tau])[None]
+    K = 1
+    poses = np.zeros((1, steps + 1, K, 7))
+    poses[0, :, 0] = _pose((0.0, 0.0, zc), _quat_axis_angle((1, 0, 0), np.pi / 4))
+    dims = np.array([[[0.05, d, d]]])
+    return Scene("edge_support", TRI, rest, tris, np.full(4, 1e-3), 1e4, 10.0, q0, np.zeros_like(q0),
+                 np.array([mu]), np.ones(1), np.full((1, K), BOX, np.int32), dims, np.zeros((1, K)), poses,
+                 h=0.01, thickness=tau, steps=steps, meta={"obstacle_features": True})

@@ -675,3 +675,192 @@ def test_crossing_strips_meet_edge_to_edge():
             assert centre[:, 2].min() > 1.5 * sc.thickness, centre[:, 2]
         else:
             assert centre[:, 2].max() < 1.2 * sc.thickness
+
+
+# ------------------------------------------------------------ box features against cloth
+def test_corner_support_closed_form():
+    """A triangle whose centroid rests one thickness above the top corner of
+    a cube standing on a vertex is in equilibrium: the corner pushes each
+    vertex up by a third of its weight through the barycentric weights
+    (1/3 each), so one tolerance-mode step leaves it at rest and the corner
+    row's normal impulse is the triangle's weight times h; every other row
+    carries nothing."""
+    sc = scenes.corner_support()
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    for metric in (1, 2):
+        st = oracle.EnvState(sc.q0[0], sc.v0[0])
+        oracle.step(mesh, sc, 0, 0, st, metric=metric, mode=1, tol=1e-11, k_cap=300, lin_iters=32)
+        assert np.abs(st.q - sc.q0[0]).max() < 1e-12
+        top = (st.cobs == oracle.OVT_SLOT) & (st.ctri == 7)   # triangle 0, obstacle 0, corner 7 = (+,+,+)
+        assert top.sum() == 1
+        W = sc.mass.sum() * 9.81
+        assert abs(st.gamma[top, 0][0] / sc.h - W * sc.h) <= 1e-9 * W * sc.h
+        assert np.abs(st.gamma[~top]).max(initial=0.0) <= 1e-15 and np.abs(st.gamma[top, 1:]).max() <= 1e-15
+
+
+def test_edge_support_closed_form():
+    """A square (diagonal 0-3) resting one thickness above a knife edge under
+    its middle line: the edge crosses the square's edges 0-2, 0-3 and 1-3 at
+    their midpoints, so each row's force goes half to each end.  Vertex
+    equilibrium then fixes the rows uniquely: 2 m g on the side edges 0-2
+    and 1-3, none on the diagonal; the square stays at rest."""
+    sc = scenes.edge_support()
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    oracle.step(mesh, sc, 0, 0, st, metric=1, mode=1, tol=1e-11, k_cap=300)
+    assert np.abs(st.q - sc.q0[0]).max() < 1e-10
+    edges = mesh.edges
+    ned = len(edges)
+    assert ned == 5
+    got = {}
+    for v, o, f, g in zip(st.cvert, st.cobs, st.ctri, st.gamma):
+        assert o == oracle.OEE_SLOT
+        e, rest = divmod(int(f), 12 * oracle.MAX_OBS)
+        assert rest == 3          # obstacle 0, box edge 3 = along x at (+y, +z): the top after the turn
+        got[tuple(int(x) for x in edges[e])] = g[0] / sc.h
+    mg = 1e-3 * 9.81
+    assert set(got) == {(0, 2), (0, 3), (1, 3)}
+    # r_ncp <= 1e-11 m bounds the multipliers' error near m x 1e-11 m (impulse ~1e-12 N s)
+    assert abs(got[(0, 2)] - 2 * mg * sc.h) <= 1e-7 * mg * sc.h
+    assert abs(got[(1, 3)] - 2 * mg * sc.h) <= 1e-7 * mg * sc.h
+    assert abs(got[(0, 3)]) <= 1e-7 * mg * sc.h
+
+
+def _box_world(sc, e, o, pts):
+    """Body-frame points of obstacle o of environment e at t+h of step 0, by
+    scipy's rotation (quaternion given scalar-last)."""
+    from scipy.spatial.transform import Rotation
+    p = sc.poses[e, 1, o]
+    return Rotation.from_quat([p[4], p[5], p[6], p[3]]).apply(pts) + p[:3]
+
+
+def _corners(d):
+    return np.array([[d[i] if (k >> i) & 1 else -d[i] for i in range(3)] for k in range(8)])
+
+
+def _box_edges(d):
+    """The 12 edges: j // 4 = the axis they run along, bit 0 / bit 1 of j % 4
+    = the + side of the other two axes in increasing order."""
+    out = []
+    for j in range(12):
+        a, m = divmod(j, 4)
+        b, c = [x for x in range(3) if x != a]
+        p0, p1 = np.zeros(3), np.zeros(3)
+        p0[a], p1[a] = -d[a], d[a]
+        p0[b] = p1[b] = d[b] if m & 1 else -d[b]
+        p0[c] = p1[c] = d[c] if m & 2 else -d[c]
+        out.append((p0, p1))
+    return out
+
+
+def _feature_candidates_numpy(sc, e, q0, q1, reach):
+    """Independent box-feature detection: corners and edges of each box by
+    scipy rotations, each triangle's plane by SVD and barycentric weights by
+    pseudo-inverse, closest points of two lines by least squares, both
+    configurations, the first OFEAT_MAX rows of each kind per owner vertex
+    in feature order."""
+    tris = sc.elems
+    E = np.unique(np.sort(np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]]), axis=1), axis=0)
+    boxes = [o for o in range(sc.n_obs) if sc.obs_type[e, o] == scenes.BOX]
+    corners = {o: _box_world(sc, e, o, _corners(sc.obs_dims[e, o])) for o in boxes}
+    bedges = {o: [_box_world(sc, e, o, np.array(pq)) for pq in _box_edges(sc.obs_dims[e, o])] for o in boxes}
+    ovt, oee = set(), set()
+    for i in range(sc.n_verts):
+        found = []
+        for f in np.nonzero(tris[:, 0] == i)[0]:
+            for o in boxes:
+                for k, C in enumerate(corners[o]):
+                    hit = False
+                    for x in (q0, q1):
+                        P = x[tris[f]]
+                        nrm = np.linalg.svd(P - P.mean(0))[2][2]
+                        d = nrm @ (C - P[0])
+                        w12 = np.linalg.pinv(np.c_[P[1] - P[0], P[2] - P[0]]) @ (C - d * nrm - P[0])
+                        w = np.r_[1 - w12.sum(), w12]
+                        hit = hit or (abs(d) < reach and w.min() >= -0.1)
+                    if hit:
+                        found.append((int(f) * oracle.MAX_OBS + o) * 8 + k)
+        ovt.update((i, f) for f in found[:oracle.OFEAT_MAX])
+        found = []
+        for en in np.nonzero(E[:, 0] == i)[0]:
+            a, b = E[en]
+            for o in boxes:
+                for j, (C, D) in enumerate(bedges[o]):
+                    hit = False
+                    for x in (q0, q1):
+                        M = np.c_[x[b] - x[a], -(D - C)]
+                        if np.linalg.matrix_rank(M, tol=1e-9) < 2:
+                            continue
+                        s, t = np.linalg.lstsq(M, C - x[a], rcond=None)[0]
+                        if 0 < s < 1 and 0 < t < 1:
+                            hit = hit or np.linalg.norm(x[a] + s * (x[b] - x[a]) - C - t * (D - C)) < reach
+                    if hit:
+                        found.append((int(en) * oracle.MAX_OBS + o) * 12 + j)
+        oee.update((i, f) for f in found[:oracle.OFEAT_MAX])
+    return ovt, oee
+
+
+def test_box_feature_detection_matches_brute_force():
+    """Box-corner and box-edge rows of the bar-and-post scene (a turned bar,
+    after the cloth has landed) equal an independent brute force over every
+    triangle, cloth edge, box corner and box edge."""
+    sc = scenes.cloth_bar_drop(n_envs=2, steps=10)
+    e = 1
+    mesh = oracle.Mesh.from_scene(sc, e)
+    st = oracle.EnvState(sc.q0[e], sc.v0[e])
+    for s in range(4):
+        oracle.step(mesh, sc, e, s, st, metric=2)
+    sc.poses[e, 1] = sc.poses[e, 5]    # the obstacles are static: step 4's poses are step 0's
+    dp = oracle.params(sc, e)[0]
+    cv, co, ct = oracle.detect(mesh, sc, e, 4, st.q, st.v, dp)
+    got_vt = {(int(v), int(t)) for v, o, t in zip(cv, co, ct) if o == oracle.OVT_SLOT}
+    got_ee = {(int(v), int(t)) for v, o, t in zip(cv, co, ct) if o == oracle.OEE_SLOT}
+    qp = st.q + sc.h * st.v + sc.h ** 2 * np.asarray(sc.gravity)
+    ref_vt, ref_ee = _feature_candidates_numpy(sc, e, st.q, qp, sc.thickness + sc.margin)
+    assert len(got_vt) >= 4 and len(got_ee) > 30
+    assert got_vt == ref_vt and got_ee == ref_ee
+
+
+def test_bar_and_post_hold_the_cloth_between_its_vertices():
+    """The cloth dropped onto a bar and a post narrower than its cells: with
+    box-feature rows it comes to rest one thickness above their tops (the
+    rows, not the vertices, hold it: no vertex row is active), and every
+    converged box-feature row satisfies gap >= -1e-8 m, lambda_n >= 0,
+    complementarity and the friction cone (gaps recomputed here from the
+    geometry); without them it falls past both to the ground."""
+    for on in (True, False):
+        sc = scenes.cloth_bar_drop(n_envs=1, steps=20)
+        if not on:
+            sc.meta = {}
+        mesh = oracle.Mesh.from_scene(sc, 0)
+        st = oracle.EnvState(sc.q0[0], sc.v0[0])
+        for s in range(12):
+            oracle.step(mesh, sc, 0, s, st, metric=2, mode=1, tol=1e-9, k_cap=400, lin_iters=32)
+        z_top = 0.05
+        if not on:
+            assert st.q[:, 2].max() < 2 * sc.thickness
+            continue
+        assert st.rncp <= 1e-9
+        assert st.q[:, 2].min() > z_top + 0.9 * sc.thickness
+        feat = (st.cobs == oracle.OVT_SLOT) | (st.cobs == oracle.OEE_SLOT)
+        assert (st.gamma[feat, 0] > 1e-9).sum() >= 4
+        assert np.abs(st.gamma[~feat, 0]).max() == 0.0
+        corners = {o: _box_world(sc, 0, o, _corners(sc.obs_dims[0, o])) for o in (1, 2)}
+        bedges = {o: [_box_world(sc, 0, o, np.array(pq)) for pq in _box_edges(sc.obs_dims[0, o])] for o in (1, 2)}
+        E = mesh.edges
+        for i in np.nonzero(feat)[0]:
+            f = int(st.ctri[i])
+            if st.cobs[i] == oracle.OVT_SLOT:
+                tri, o, k = f // (8 * oracle.MAX_OBS), f // 8 % oracle.MAX_OBS, f % 8
+                P = st.q[sc.elems[tri]]
+                nrm = np.linalg.svd(P - P.mean(0))[2][2]
+                gap = abs(nrm @ (corners[o][k] - P[0])) - sc.thickness
+            else:
+                en, o, j = f // (12 * oracle.MAX_OBS), f // 12 % oracle.MAX_OBS, f % 12
+                a, b = E[en]
+                C, D = bedges[o][j]
+                nn = np.cross(st.q[b] - st.q[a], D - C)
+                gap = abs(nn @ (st.q[a] - C)) / np.linalg.norm(nn) - sc.thickness
+            g = st.gamma[i]
+            assert gap >= -1e-8 and g[0] >= -1e-15 and abs(g[0] * gap) <= 1e-14
+            assert np.linalg.norm(g[1:]) <= sc.mu[0] * max(g[0], 0) + 1e-13
