@@ -29,11 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec on 1 GB300 at NCP residual <=1e-5 (batched vs plain); % HBM roofline"
 TOL = 1e-5
-DEFAULT_ENVS = {"cloth_gripper": 1024, "cloth_grasp": 1024, "cloth_stack": 1024, "tet_squeeze": 4096, "mixed": 2048,
-                "towel_render": 128}
+DEFAULT_ENVS = {"cloth_gripper": 1024, "cloth_grasp": 1024, "cloth_stack": 1024, "cloth_bar": 1024,
+                "tet_squeeze": 4096, "mixed": 2048, "towel_render": 128}
 RENDER_METRIC = ("depth frames/s on 1 GB300: batched ray casting of the 32,761-vertex towel, 640x480 depth + "
                  "instance segmentation + point cloud per environment")
-CPU_SAMPLE = {"cloth_gripper": (6, 12), "cloth_grasp": (2, 6), "cloth_stack": (16, 20),
+CPU_SAMPLE = {"cloth_gripper": (6, 12), "cloth_grasp": (2, 6), "cloth_stack": (16, 20), "cloth_bar": (16, 20),
               "tet_squeeze": (24, 40)}   # (envs, steps), 10-30 s
 
 
@@ -44,7 +44,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="cloth_gripper",
-                   choices=["cloth_gripper", "cloth_grasp", "cloth_stack", "tet_squeeze", "mixed", "towel_render"])
+                   choices=["cloth_gripper", "cloth_grasp", "cloth_stack", "cloth_bar", "tet_squeeze", "mixed",
+                            "towel_render"])
     p.add_argument("--envs", type=int, default=None, help="environments per GPU (default: the workload's)")
     p.add_argument("--side", type=int, default=32)
     p.add_argument("--k", type=int, default=10, help="local-global iterations per step (fixed mode)")
@@ -54,8 +55,8 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
     p.add_argument("--metric", default=None, choices=["lite", "full"],
                    help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve "
-                        "(default: full for cloth_grasp and cloth_stack, whose bilateral grasp and stacked "
-                        "layers the lite metric cannot hold, else lite)")
+                        "(default: full for cloth_grasp, cloth_stack and cloth_bar, whose bilateral grasp, "
+                        "stacked layers and box-feature rows the lite metric cannot hold, else lite)")
     p.add_argument("--lin-iters", type=int, default=10, help="linear-solver (GMRES) iterations of the full metric")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
@@ -66,7 +67,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.metric is None:
-        args.metric = "full" if args.workload in ("cloth_grasp", "cloth_stack") else "lite"
+        args.metric = "full" if args.workload in ("cloth_grasp", "cloth_stack", "cloth_bar") else "lite"
     return args
 
 
@@ -219,6 +220,11 @@ def workload_scene(args, n_envs, steps, rank=0):
         sc = scenes.cloth_stack_drop(seed=5 + rank, n_envs=n_envs, steps=steps, k_max=args.k)
         desc = (f"cloth stack: {n_envs} envs x 16x16 cloth + 8x8 piece dropped onto it (one mesh, "
                 f"{len(sc.elems)} tris, {sc.n_verts} verts), cloth self-collision, ground, h=1/100")
+    elif args.workload == "cloth_bar":
+        sc = scenes.cloth_bar_drop(seed=7 + rank, n_envs=n_envs, steps=steps, k_max=args.k)
+        desc = (f"cloth on bar and post: {n_envs} envs x 16x16 cloth ({len(sc.elems)} tris) dropped onto a 5 mm "
+                f"bar and a 6 mm post narrower than its cells (box corners and edges against its triangles and "
+                f"edges), ground, h=1/100")
     elif args.workload == "tet_squeeze":
         sc = scenes.tet_squeeze(seed=1 + rank, n_envs=n_envs, steps=steps, k_max=args.k)
         desc = (f"tet squeeze: {n_envs} envs x 8x8x4-cube tet block (1280 tets, 405 verts), per-env "

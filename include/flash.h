@@ -57,6 +57,9 @@ typedef int32_t flash_status;
 #define FLASH_SELF_MAX 4 /* vertex-triangle self contacts per vertex at most */
 #define FLASH_EE_SLOT (FLASH_MAX_OBS + 2) /* contact-list slot of cloth edge-edge contacts */
 #define FLASH_EE_MAX 4 /* edge-edge contacts per vertex at most */
+#define FLASH_OVT_SLOT (FLASH_MAX_OBS + 3) /* contact-list slot of box corners against cloth triangles */
+#define FLASH_OEE_SLOT (FLASH_MAX_OBS + 4) /* contact-list slot of box edges against cloth edges */
+#define FLASH_OFEAT_MAX 4 /* rows of each box-feature kind per vertex at most */
 
 #define FLASH_MODE_FIXED 0 /* exactly k_max local-global iterations per step */
 #define FLASH_MODE_TOL 1   /* iterate until r_ncp <= tol_ncp (k >= k_min) or k_cap */
@@ -110,9 +113,32 @@ typedef int32_t flash_status;
  * ascending).  Its normal is that of both edges, oriented by the side
  * (a, b) was on at the step start, gap = distance between the lines -
  * thickness, the contact point moving as (1 - s) x_a + s x_b - (1 - t) x_c
- * - t x_d.  Rows of a vertex: obstacles, grasp, vertex-triangle, edge-edge.
+ * - t x_d.  Rows of a vertex: obstacles, grasp, vertex-triangle, edge-edge,
+ * then the box-feature rows below.
  * The paper disables self-collision and describes no method; this is the
- * library's reading. */
+ * library's reading.
+ * obstacle_features: 1 adds contact rows between the corners and edges of
+ * box obstacles and a cloth (triangle meshes; needs FLASH_METRIC_FULL), so
+ * that a box narrower than the cloth's cells cannot pass between its
+ * vertices.  Box corner k (0..7; bit i of k set: +half extent on axis i,
+ * clear: -) of obstacle o against triangle f: a row of f's first vertex
+ * (slot FLASH_OVT_SLOT, feature (f * FLASH_MAX_OBS + o) * 8 + k) when the
+ * corner, at the obstacle's pose at t+h, lies within thickness + margin of
+ * f's plane with its projection inside f up to 0.1 in barycentric terms,
+ * at q_t or q~.  The contact point moves as the barycentric combination of
+ * f's corners; normal = f's, oriented towards the side the cloth was on,
+ * seen from the box corner, at the step start; gap = distance from the box
+ * corner to the plane - thickness.  Box edge j (0..11: along axis j / 4,
+ * on the + side of the other two axes, in increasing order, where bits 0
+ * and 1 of j % 4 are set) of obstacle o against the cloth edge e = (a, b):
+ * a row of a (slot FLASH_OEE_SLOT, feature (e * FLASH_MAX_OBS + o) * 12 +
+ * j) when the closest points of the two lines lie inside both and nearer
+ * than thickness + margin, at q_t or q~; the contact point moves as
+ * (1 - s) x_a + s x_b; normal = that of both lines, oriented by the side the
+ * cloth edge was on at the step start; gap = distance between the lines -
+ * thickness.  The first FLASH_OFEAT_MAX rows of each kind per vertex are
+ * kept, in feature order.  The paper describes none; this is the library's
+ * reading. */
 typedef struct {
   double h;
   double gravity[3];
@@ -129,6 +155,7 @@ typedef struct {
   int32_t metric;
   int32_t lin_iters;
   int32_t self_collide;
+  int32_t obstacle_features;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -280,15 +307,17 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream);
 /* Contacts of the last step: count device int32 [N]; vert, obs device int32
  * [N][cap] (obs = FLASH_GRASP_SLOT for a grasp row); gamma device float32
  * [N][cap][4] (any may be NULL).  A vertex holds at most one row per
- * obstacle plus one grasp row, FLASH_SELF_MAX vertex-triangle and
- * FLASH_EE_MAX edge-edge rows, so cap = n_verts * (n_obs + 1 +
- * FLASH_SELF_MAX + FLASH_EE_MAX) never overflows. */
+ * obstacle plus one grasp row, FLASH_SELF_MAX vertex-triangle,
+ * FLASH_EE_MAX edge-edge and 2 FLASH_OFEAT_MAX box-feature rows, so cap =
+ * n_verts * (n_obs + 1 + FLASH_SELF_MAX + FLASH_EE_MAX + 2 FLASH_OFEAT_MAX)
+ * never overflows. */
 flash_status flash_get_contacts(const flash_scene *s, int32_t *count, int32_t *vert, int32_t *obs,
                                 float *gamma, void *stream);
 int32_t flash_contact_cap(const flash_scene *s);
 /* Feature of each row of the last step's contact lists: device int32
  * [N][cap]; the triangle of a vertex-triangle self contact, e1 * n_edges +
- * e2 for an edge-edge contact, -1 for the other rows. */
+ * e2 for an edge-edge contact, the box-feature index of a FLASH_OVT_SLOT or
+ * FLASH_OEE_SLOT row, -1 for the other rows. */
 flash_status flash_get_contact_tris(const flash_scene *s, int32_t *tri, void *stream);
 
 /* Per-environment statistics of the last step: iterations used and the NCP

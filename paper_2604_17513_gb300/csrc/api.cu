@@ -388,7 +388,9 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.pobs, cc));
   FLASH_CUDA_TRY(dalloc(s, &g.pgam, cc * 4));
   FLASH_CUDA_TRY(dalloc(s, &g.gflag, (size_t)g.N * np));
-  g.self = s->d.self_collide && m.type == FLASH_TRI ? 1 : 0;
+  g.selfc = s->d.self_collide && m.type == FLASH_TRI ? 1 : 0;
+  g.ofeat = s->d.obstacle_features && m.type == FLASH_TRI ? 1 : 0;
+  g.self = g.selfc || g.ofeat ? 1 : 0;
   if (g.self) {
     FLASH_CUDA_TRY(dalloc(s, &g.ctri, cc));
     FLASH_CUDA_TRY(dalloc(s, &g.pctri, cc));
@@ -647,6 +649,10 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
   if (desc->self_collide != 0 && desc->self_collide != 1) return fail(FLASH_EINVAL, "self_collide must be 0 or 1");
   if (desc->self_collide && desc->metric != FLASH_METRIC_FULL)
     return fail(FLASH_EINVAL, "cloth self-collision needs the full metric (FLASH_METRIC_FULL)");
+  if (desc->obstacle_features != 0 && desc->obstacle_features != 1)
+    return fail(FLASH_EINVAL, "obstacle_features must be 0 or 1");
+  if (desc->obstacle_features && desc->metric != FLASH_METRIC_FULL)
+    return fail(FLASH_EINVAL, "box-feature contacts need the full metric (FLASH_METRIC_FULL)");
   flash_scene *s = new flash_scene();
   s->d = *desc;
   if (s->d.lin_iters == 0) s->d.lin_iters = 10;
@@ -777,7 +783,7 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
   if (s->d.self_collide) {
     size_t need = 0;
     for (const Group &g : s->groups)
-      if (g.self) need = std::max(need, sizeof(float) * 6 * ((size_t)g.E + g.ned));
+      if (g.selfc) need = std::max(need, sizeof(float) * 6 * ((size_t)g.E + g.ned));
     s->begin_smem = need <= (size_t)kMaxBeginSmem ? need : 0;
   }
   // env-level arrays

@@ -95,8 +95,9 @@ struct Group {
   float *pgam = nullptr;
   uint8_t *gflag = nullptr;               // [N][n_pad] grasped vertices (S_grip)
   // cloth self-collision (triangle meshes of a scene with self_collide)
-  int self = 0;
-  int *ctri = nullptr, *pctri = nullptr;  // [N][cap] feature of each self-contact row, -1 otherwise
+  int self = 0;                           // multi-vertex rows possible (self contacts or box features)
+  int selfc = 0, ofeat = 0;               // detection of self contacts / of box-feature rows
+  int *ctri = nullptr, *pctri = nullptr;  // [N][cap] feature of each multi-vertex row, -1 otherwise
   float *fm_w = nullptr;                  // [N][cap][8] full metric: weights, effective mass, vertices 1..3
   int ned = 0;                            // unique edges (a < b) in (a, b) order
   int2 *edges = nullptr;                  // [ned]

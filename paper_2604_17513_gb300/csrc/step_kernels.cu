@@ -29,7 +29,8 @@ struct GroupView {
   float *rscale;
   int *ccount, *cvert, *cobs, *pcount, *pvert, *pobs;
   uint8_t *gflag;                // [N][n_pad] grasped vertices
-  int self;                      // cloth self-collision on
+  int self;                      // multi-vertex rows possible (self contacts or box features)
+  int selfc, ofeat;              // detection of cloth self contacts / of box-feature rows
   int *ctri, *pctri;             // [N][cap] feature of self-contact rows (triangle, or e1 * ned + e2)
   float *fm_w;                   // [N][cap][kFmW] full metric: weights, effective mass, vertices 1..3
   int ned;                       // unique edges (a < b), (a, b) order
@@ -73,7 +74,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
   v.ccount = g.ccount; v.cvert = g.cvert; v.cobs = g.cobs; v.pcount = g.pcount; v.pvert = g.pvert;
   v.pobs = g.pobs; v.cgam = g.cgam; v.pgam = g.pgam; v.cscratch = g.cscratch; v.gflag = g.gflag;
-  v.self = g.self; v.ctri = g.ctri; v.pctri = g.pctri; v.fm_w = g.fm_w;
+  v.self = g.self; v.selfc = g.selfc; v.ofeat = g.ofeat; v.ctri = g.ctri; v.pctri = g.pctri; v.fm_w = g.fm_w;
   v.ned = g.ned; v.edges = g.edges; v.eoff = g.eoff;
   v.c_in_smem = g.c_in_smem ? 1 : 0;
   v.coff = g.coff; v.cidx = g.cidx; v.kb = g.kb; v.ev = g.ev; v.deg_b = g.deg_b;
@@ -159,7 +160,7 @@ __device__ void block_max3(float &x0, float &x1, float &x2, float (*sh)[3]) {
 // p), p within `reach` of f's plane with its projection inside f up to
 // kSelfBary (barycentric), at q_t or at q~.
 constexpr float kSelfBary = 0.1f;
-constexpr int kSlots = FLASH_EE_SLOT + 1;   // contact-list slots: obstacles, grasp, self, edge-edge
+constexpr int kSlots = FLASH_OEE_SLOT + 1;   // contact-list slots: obstacles, grasp, self, edge-edge, box features
 
 __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f, float reach, const float *x0,
                                                const float *x1) {
@@ -244,6 +245,63 @@ __device__ __forceinline__ bool ee_candidate(const GroupView &G, int e1, int e2,
   return true;
 }
 
+// Box features (the library's reading; the paper describes none).  Corner
+// k of a box: bit i of k set = +half extent on axis i.  Edge j: along axis
+// j / 4, on the sides of the other two axes (in increasing order) given by
+// bits 0 and 1 of j % 4.
+__device__ __forceinline__ V3 box_corner_body(const float *d, int k) {
+  return v3((k & 1) ? d[0] : -d[0], (k & 2) ? d[1] : -d[1], (k & 4) ? d[2] : -d[2]);
+}
+__device__ __forceinline__ void box_edge_body(const float *d, int j, V3 &p0, V3 &p1) {
+  const int ax = j >> 2, m = j & 3;
+  const float sb = (m & 1) ? 1.f : -1.f, sc = (m & 2) ? 1.f : -1.f;
+  if (ax == 0) { p0 = v3(-d[0], sb * d[1], sc * d[2]); p1 = v3(d[0], sb * d[1], sc * d[2]); }
+  else if (ax == 1) { p0 = v3(sb * d[0], -d[1], sc * d[2]); p1 = v3(sb * d[0], d[1], sc * d[2]); }
+  else { p0 = v3(sb * d[0], sc * d[1], -d[2]); p1 = v3(sb * d[0], sc * d[1], d[2]); }
+}
+__device__ __forceinline__ V3 pose_point(const float *pose, V3 pb) {
+  return qrot(pose + 3, pb, false) + v3(pose[0], pose[1], pose[2]);
+}
+
+// Box-corner candidate: the corner C within `reach` of triangle f's plane,
+// its projection inside f up to kSelfBary (barycentric), at q_t or at q~.
+__device__ __forceinline__ bool ovt_candidate(const GroupView &G, int f, V3 C, float reach, const float *x0,
+                                              const float *x1) {
+  const int np = G.n_pad;
+  const int t0 = G.elems[4 * f], t1 = G.elems[4 * f + 1], t2 = G.elems[4 * f + 2];
+  for (int k = 0; k < 2; k++) {
+    const float *x = k == 0 ? x0 : x1;
+    const V3 A = col3(x, np, t0), B = col3(x, np, t1), Cc = col3(x, np, t2);
+    const V3 nf = cross(B - A, Cc - A);
+    const float ar = norm(nf);
+    if (!(ar > 0.f)) continue;
+    const V3 nh = (1.f / ar) * nf;
+    const float d = dot(nh, C - A);
+    const V3 y = C - d * nh;
+    const float wa = dot(nh, cross(B - y, Cc - y)) / ar, wb = dot(nh, cross(Cc - y, A - y)) / ar;
+    const float wc = 1.f - wa - wb;
+    if (fabsf(d) < reach && wa >= -kSelfBary && wb >= -kSelfBary && wc >= -kSelfBary) return true;
+  }
+  return false;
+}
+
+// Box-edge candidate: the box edge (C, D) and the cloth edge e, whose lines'
+// closest points lie inside both and nearer than `reach`, at q_t or at q~.
+__device__ __forceinline__ bool oee_candidate(const GroupView &G, int e, V3 C, V3 D, float reach, const float *x0,
+                                              const float *x1) {
+  const int np = G.n_pad;
+  const int2 E = G.edges[e];
+  for (int k = 0; k < 2; k++) {
+    const float *x = k == 0 ? x0 : x1;
+    const V3 A = col3(x, np, E.x), B = col3(x, np, E.y);
+    float s, t;
+    if (!line_params(A, B, C, D, s, t)) continue;
+    if (!(s > 0.f && s < 1.f && t > 0.f && t < 1.f)) continue;
+    if (norm((A - C) + s * (B - A) - t * (D - C)) < reach) return true;
+  }
+  return false;
+}
+
 // SELF: the group detects cloth self contacts (a compile-time switch, so the
 // kernels of scenes without self-collision carry none of its code)
 template <bool SELF>
@@ -253,6 +311,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   __shared__ float s_dims[FLASH_MAX_OBS][3], s_pose[FLASH_MAX_OBS][7];
   a.tau = G.tau;
   const bool self = SELF && G.self;   // tetrahedral groups of a self-collision scene have none
+  const bool selfc = self && G.selfc, ofeat = self && G.ofeat;
   const int e = G.genv[l];
   const int n = G.n, np = G.n_pad;
   float *q = G.q + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
@@ -299,7 +358,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   // boxes miss each other cannot come within reach.
   extern __shared__ float sbox[];   // [E][6] then [ned][6] when boxes
   const float reach = a.tau + a.margin;
-  if (self && boxes) {
+  if (selfc && boxes) {
     for (int t = threadIdx.x; t < G.E; t += blockDim.x) {
       float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, el = 0.f;
       int tv[3];
@@ -331,8 +390,8 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     int i = i0 + threadIdx.x;
     unsigned mask = 0;
-    int sf[FLASH_SELF_MAX], se[FLASH_EE_MAX];
-    int ns = 0, ne = 0;
+    int sf[FLASH_SELF_MAX], se[FLASH_EE_MAX], sv[FLASH_OFEAT_MAX], sb[FLASH_OFEAT_MAX];
+    int ns = 0, ne = 0, nv = 0, nb = 0;
     if (i < n) {
       float x0[3], x1[3];
       if (self) {
@@ -356,14 +415,59 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         gflag[i] = 0;
       }
       if (gflag[i]) mask |= 1u << FLASH_GRASP_SLOT;
+      // box features: a box can reach a triangle or edge of i only if it
+      // comes within reach + 1.3 L of i, L the longest edge at i at q_t or
+      // q~ (a projection inside the triangle up to 0.1 lies within 1.3 L of
+      // its first corner)
+      float cull = -INFINITY;
+      if (ofeat) {
+        float L2 = 0.f;
+        for (int sl = G.coff[i]; sl < G.coff[i + 1]; sl++) {
+          const int t = G.cidx[sl] / 3;
+          for (int c = 0; c < 3; c++) {
+            const int u = G.elems[4 * t + c];
+            const V3 d0 = col3(qt, np, u) - v3(x0[0], x0[1], x0[2]), d1 = col3(qp, np, u) - v3(x1[0], x1[1], x1[2]);
+            L2 = fmaxf(L2, fmaxf(dot(d0, d0), dot(d1, d1)));
+          }
+        }
+        cull = a.tau + a.margin + 1.3f * sqrtf(L2) + 1e-4f;
+      }
+      unsigned near = 0;
       for (int o = 0; o < a.K; o++) {
         if (s_type[o] == FLASH_OBS_NONE) continue;
         V3 nn;
         float s0 = obstacle_sdf(s_type[o], s_dims[o], s_pose[o], v3(x0[0], x0[1], x0[2]), nn);
         float s1 = obstacle_sdf(s_type[o], s_dims[o], s_pose[o], v3(x1[0], x1[1], x1[2]), nn);
         if (fminf(s0, s1) < a.tau + a.margin) mask |= 1u << o;
+        if (s_type[o] == FLASH_OBS_BOX && fminf(s0, s1) < cull) near |= 1u << o;
       }
-      if (self) {   // the first FLASH_SELF_MAX candidate triangles in index order
+      if (near) {
+        // corners against the triangles whose first vertex is i (element
+        // slots 3 f + 0 of i, f ascending), then box edges against the
+        // edges (i, b), each in feature order
+        for (int sl = G.coff[i]; sl < G.coff[i + 1] && nv < FLASH_OFEAT_MAX; sl++) {
+          const int cs = G.cidx[sl];
+          if (cs % 3 != 0) continue;
+          const int f = cs / 3;
+          for (int o = 0; o < a.K && nv < FLASH_OFEAT_MAX; o++) {
+            if (!((near >> o) & 1u)) continue;
+            for (int k = 0; k < 8 && nv < FLASH_OFEAT_MAX; k++)
+              if (ovt_candidate(G, f, pose_point(s_pose[o], box_corner_body(s_dims[o], k)), reach, qt, qp))
+                sv[nv++] = (f * FLASH_MAX_OBS + o) * 8 + k;
+          }
+        }
+        for (int e1 = G.eoff[i]; e1 < G.eoff[i + 1] && nb < FLASH_OFEAT_MAX; e1++)
+          for (int o = 0; o < a.K && nb < FLASH_OFEAT_MAX; o++) {
+            if (!((near >> o) & 1u)) continue;
+            for (int j = 0; j < 12 && nb < FLASH_OFEAT_MAX; j++) {
+              V3 p0, p1;
+              box_edge_body(s_dims[o], j, p0, p1);
+              if (oee_candidate(G, e1, pose_point(s_pose[o], p0), pose_point(s_pose[o], p1), reach, qt, qp))
+                sb[nb++] = (e1 * FLASH_MAX_OBS + o) * 12 + j;
+            }
+          }
+      }
+      if (selfc) {   // the first FLASH_SELF_MAX candidate triangles in index order
         const float vlo[3] = {fminf(x0[0], x1[0]), fminf(x0[1], x1[1]), fminf(x0[2], x1[2])};
         const float vhi[3] = {fmaxf(x0[0], x1[0]), fmaxf(x0[1], x1[1]), fmaxf(x0[2], x1[2])};
         for (int t = 0; t < G.E && ns < FLASH_SELF_MAX; t++) {
@@ -393,7 +497,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         }
       }
     }
-    int cnt = __popc(mask) + ns + ne, total;
+    int cnt = __popc(mask) + ns + ne + nv + nb, total;
     int off = block_exclusive_scan(cnt, &total, sh_scan);
     int pos = base + off;
     for (int o = 0; o < a.K; o++)
@@ -411,6 +515,14 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     }
     for (int k = 0; k < ne; k++) {
       if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_EE_SLOT; ctri[pos] = se[k]; }
+      pos++;
+    }
+    for (int k = 0; k < nv; k++) {           // then the box features
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_OVT_SLOT; ctri[pos] = sv[k]; }
+      pos++;
+    }
+    for (int k = 0; k < nb; k++) {
+      if (pos < G.cap) { cvert[pos] = i; cobs[pos] = FLASH_OEE_SLOT; ctri[pos] = sb[k]; }
       pos++;
     }
     base += total;
@@ -644,12 +756,106 @@ __device__ __noinline__ void lin_ee(const GroupView &G, int e1, int e2, const fl
   contact_law(n, t1, t2, dot(n, dd) - tau, rel, 0.f, mu, h, S.meff, g, L);
 }
 
-// a self-contact row (slot FLASH_SELF_SLOT or FLASH_EE_SLOT) of vertex vtx
-__device__ __forceinline__ void lin_row(const GroupView &G, int o, int vtx, int feat, const float *x, int ld,
-                                        const float *xt, float mu, float h, float tau, const float *g,
-                                        ContactLin &L, SelfRow &S) {
+// Box corner k of obstacle o against triangle f (feature (f * FLASH_MAX_OBS
+// + o) * 8 + k; the library's reading): weights w = barycentric weights of
+// the box corner's projection on f's plane at x (row vertices f's corners,
+// the first one the row's own); frame normal = f's unit normal, oriented
+// towards the side the cloth was on, seen from the box corner, at q_t; gap
+// = n.(sum w x - C) - tau, C the box corner at t+h; slip = that point's
+// displacement relative to the box corner over the step.
+__device__ __noinline__ void lin_ovt(const GroupView &G, const ObsShared &O, int feat, const float *x, int ld,
+                                     const float *xt, float mu, float h, float tau, const float *g, ContactLin &L,
+                                     SelfRow &S) {
+  const int np = G.n_pad;
+  const int f = feat / (8 * FLASH_MAX_OBS), o = feat / 8 % FLASH_MAX_OBS, kc = feat % 8;
+  const int t[3] = {G.elems[4 * f], G.elems[4 * f + 1], G.elems[4 * f + 2]};
+  const V3 cb = box_corner_body(O.dims[o], kc);
+  const V3 C = pose_point(O.pose[o], cb), Ct = pose_point(O.poset[o], cb);
+  V3 X[3], Xt[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    X[k] = col3(x, ld, t[k]);
+    Xt[k] = col3(xt, np, t[k]);
+  }
+  const V3 nf = cross(X[1] - X[0], X[2] - X[0]);
+  const float ar = norm(nf);
+  V3 nh = v3(0.f, 0.f, 1.f);
+  float d = 0.f;
+  float w[3] = {1.f / 3.f, 1.f / 3.f, 1.f / 3.f};
+  if (ar > 0.f) {
+    nh = (1.f / ar) * nf;
+    d = dot(nh, C - X[0]);
+    const V3 y = C - d * nh;
+    w[0] = dot(nh, cross(X[1] - y, X[2] - y)) / ar;
+    w[1] = dot(nh, cross(X[2] - y, X[0] - y)) / ar;
+    w[2] = 1.f - w[0] - w[1];
+  }
+  // the cloth lies on the -n_t side of the corner when the corner is on its + side
+  const float side = dot(cross(Xt[1] - Xt[0], Xt[2] - Xt[0]), Ct - Xt[0]) > 0.f ? -1.f : 1.f;
+  const V3 n = side * nh;
+  float inv = 0.f;
+  V3 rel = Ct - C;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    inv += w[k] * w[k] / __ldg(G.mass + t[k]);
+    rel = rel + w[k] * (X[k] - Xt[k]);
+    S.v[k] = t[k];
+    S.w[k] = w[k];
+  }
+  S.v[3] = t[0];
+  S.w[3] = 0.f;
+  S.meff = 1.f / inv;
+  V3 t1, t2;
+  tangent_basis(n, t1, t2);
+  contact_law(n, t1, t2, -side * d - tau, rel, 0.f, mu, h, S.meff, g, L);   // n.(sum w x - C) = -side d
+}
+
+// Box edge j of obstacle o against the cloth edge e = (a, b) (feature (e *
+// FLASH_MAX_OBS + o) * 12 + j; the library's reading): (s, t) = closest
+// points of the cloth edge's line and the box edge's line (C, D at t+h) at
+// x (1/2 when parallel); weights (1 - s, s) on (a, b); frame normal = the
+// unit normal of both lines, oriented by the side the cloth edge was on at
+// q_t; gap = n.((1 - s) x_a + s x_b - (1 - t) C - t D) - tau; slip = that
+// difference's displacement over the step.
+__device__ __noinline__ void lin_oee(const GroupView &G, const ObsShared &O, int feat, const float *x, int ld,
+                                     const float *xt, float mu, float h, float tau, const float *g, ContactLin &L,
+                                     SelfRow &S) {
+  const int np = G.n_pad;
+  const int e = feat / (12 * FLASH_MAX_OBS), o = feat / 12 % FLASH_MAX_OBS, j = feat % 12;
+  const int2 E = G.edges[e];
+  V3 p0, p1;
+  box_edge_body(O.dims[o], j, p0, p1);
+  const V3 C = pose_point(O.pose[o], p0), D = pose_point(O.pose[o], p1);
+  const V3 Ct = pose_point(O.poset[o], p0), Dt = pose_point(O.poset[o], p1);
+  const V3 A = col3(x, ld, E.x), B = col3(x, ld, E.y), At = col3(xt, np, E.x), Bt = col3(xt, np, E.y);
+  float s = 0.5f, t = 0.5f;
+  line_params(A, B, C, D, s, t);
+  const V3 nc = cross(B - A, D - C);
+  const float nl = norm(nc);
+  const V3 nr = nl > 0.f ? (1.f / nl) * nc : v3(0.f, 0.f, 1.f);
+  // n_t is normal to both lines at q_t, so n_t.(a - C) is the side for any pair of points on them
+  const float side = dot(cross(Bt - At, Dt - Ct), At - Ct) < 0.f ? -1.f : 1.f;
+  const float ma = __ldg(G.mass + E.x), mb = __ldg(G.mass + E.y);
+  S.v[0] = E.x; S.v[1] = E.y; S.v[2] = E.x; S.v[3] = E.x;
+  S.w[0] = 1.f - s; S.w[1] = s; S.w[2] = 0.f; S.w[3] = 0.f;
+  S.meff = 1.f / ((1.f - s) * (1.f - s) / ma + s * s / mb);
+  const V3 dd = (A - C) + s * (B - A) - t * (D - C);
+  const V3 rel = (1.f - s) * (A - At) + s * (B - Bt) - (1.f - t) * (C - Ct) - t * (D - Dt);
+  const V3 n = side * nr;
+  V3 t1, t2;
+  tangent_basis(n, t1, t2);
+  contact_law(n, t1, t2, dot(n, dd) - tau, rel, 0.f, mu, h, S.meff, g, L);
+}
+
+// a multi-vertex row (slot FLASH_SELF_SLOT, FLASH_EE_SLOT, FLASH_OVT_SLOT or
+// FLASH_OEE_SLOT) of vertex vtx
+__device__ __forceinline__ void lin_row(const GroupView &G, const ObsShared &O, int o, int vtx, int feat,
+                                        const float *x, int ld, const float *xt, float mu, float h, float tau,
+                                        const float *g, ContactLin &L, SelfRow &S) {
   if (o == FLASH_SELF_SLOT) lin_self(G, vtx, feat, x, ld, xt, mu, h, tau, g, L, S);
-  else lin_ee(G, feat / G.ned, feat % G.ned, x, ld, xt, mu, h, tau, g, L, S);
+  else if (o == FLASH_EE_SLOT) lin_ee(G, feat / G.ned, feat % G.ned, x, ld, xt, mu, h, tau, g, L, S);
+  else if (o == FLASH_OVT_SLOT) lin_ovt(G, O, feat, x, ld, xt, mu, h, tau, g, L, S);
+  else lin_oee(G, O, feat, x, ld, xt, mu, h, tau, g, L, S);
 }
 
 // world force R^T gamma of a contact (gamma = (g_n, g_t world))
@@ -908,7 +1114,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       if (cobs[j] < FLASH_SELF_SLOT) continue;
       ContactLin L;
       SelfRow S;
-      lin_row(G, cobs[j], cvert[j], ctri[j], qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, S);
+      lin_row(G, O, cobs[j], cvert[j], ctri[j], qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, S);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       if (!residual_only) scatter_row(S.v, S.w, contact_force(L, gam + 4 * j), rs, ns);
     }
@@ -1332,7 +1538,7 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
     if (G.self && cobs[c] >= FLASH_SELF_SLOT) {
       // J du = sum w_k du_k; preconditioner scale (sum w_k^2 a_kk) meff
       SelfRow S;
-      lin_row(G, cobs[c], vtx, G.ctri[(size_t)l * cap + c], q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, S);
+      lin_row(G, O, cobs[c], vtx, G.ctri[(size_t)l * cap + c], q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, S);
       float av = 0.f;
       du_c = v3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -2094,7 +2300,7 @@ cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int
 
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st) {
   if (!L.all.blocks) return cudaSuccess;
-  if (s->d.self_collide)
+  if (s->d.self_collide || s->d.obstacle_features)
     k_begin_tab<true><<<L.all.blocks, 256, s->begin_smem, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a,
                                                                s->begin_smem > 0 ? 1 : 0);
   else
@@ -2108,7 +2314,7 @@ cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArg
   const GroupView *tab = (const GroupView *)s->gtab;
   for (const Batch &b : L.local) {
     if (b.vpe == 3)
-      if (s->d.self_collide)
+      if (s->d.self_collide || s->d.obstacle_features)
         k_local_tab<3, true><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
       else
         k_local_tab<3, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);

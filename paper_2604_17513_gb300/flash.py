@@ -26,6 +26,9 @@ SELF_SLOT = MAX_OBS + 1   # contact-list slot of cloth vertex-triangle self cont
 SELF_MAX = 4           # vertex-triangle self contacts per vertex at most
 EE_SLOT = MAX_OBS + 2  # contact-list slot of cloth edge-edge contacts
 EE_MAX = 4             # edge-edge contacts per vertex at most
+OVT_SLOT = MAX_OBS + 3  # contact-list slot of box corners against cloth triangles
+OEE_SLOT = MAX_OBS + 4  # contact-list slot of box edges against cloth edges
+OFEAT_MAX = 4           # rows of each box-feature kind per vertex at most
 MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
@@ -50,7 +53,7 @@ class SceneDesc(C.Structure):
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
-                ("lin_iters", C.c_int32), ("self_collide", C.c_int32)]
+                ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -161,7 +164,7 @@ class Sim:
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
                  warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
-                 self_collision=None):
+                 self_collision=None, obstacle_features=None):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -179,12 +182,17 @@ class Sim:
         d.mode = s0.mode if mode is None else mode
         if self_collision is None:   # on when a scene asks for it
             self_collision = any(sc.meta.get("self_collision") for sc in scenes)
+        if obstacle_features is None:
+            obstacle_features = any(sc.meta.get("obstacle_features") for sc in scenes)
         # one row per (vertex, obstacle), plus one grasp row per vertex where grasps are
         # scheduled, plus up to SELF_MAX + EE_MAX self rows per vertex with self-collision
+        # and 2 OFEAT_MAX box-feature rows with those on
         d.contact_cap = contact_cap or max(sc.n_verts * (sc.n_obs + (1 if sc.meta.get("grasp") else 0) +
-                                                         (SELF_MAX + EE_MAX if self_collision else 0))
+                                                         (SELF_MAX + EE_MAX if self_collision else 0) +
+                                                         (2 * OFEAT_MAX if obstacle_features else 0))
                                            for sc in scenes)
         d.self_collide = 1 if self_collision else 0
+        d.obstacle_features = 1 if obstacle_features else 0
         d.solve = solve
         d.warm = warm
         d.lanes = lanes

@@ -55,6 +55,14 @@ def test_scene_descriptor_validation(lib):
     d.mode = 7
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
     d.mode = 0
+    # box-feature and self contacts are multi-vertex rows: the lite metric refuses them
+    d.obstacle_features = 1
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
+    assert b"full metric" in lib.flash_last_error()
+    d.obstacle_features = 2
+    d.metric = flash.METRIC_FULL
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
+    d.obstacle_features, d.metric = 0, 0
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
     # a mesh with an out-of-range element index is rejected on the host
     rest = np.zeros((3, 3))
