@@ -49,9 +49,11 @@ def parse():
     p.add_argument("--envs", type=int, default=None, help="environments per GPU (default: the workload's)")
     p.add_argument("--side", type=int, default=32)
     p.add_argument("--k", type=int, default=10, help="local-global iterations per step (fixed mode)")
-    p.add_argument("--mode", default="fixed", choices=["fixed", "tol"],
-                   help="fixed: k iterations per step; tol: iterate until r_ncp <= 1e-5 (cap --k-cap)")
-    p.add_argument("--k-cap", type=int, default=200, help="iteration cap of the tolerance mode")
+    p.add_argument("--mode", default="tol", choices=["fixed", "tol"],
+                   help="tol (default, the metric's stopping rule): each environment iterates until its "
+                        "r_ncp <= 1e-5 or --k-cap iterations; fixed: exactly --k iterations per step")
+    p.add_argument("--k-cap", type=int, default=10,
+                   help="iteration cap of the tolerance mode (default 10, the paper's iteration count)")
     p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
     p.add_argument("--metric", default=None, choices=["lite", "full"],
                    help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve "
@@ -575,12 +577,15 @@ def main():
     # (kept out of the timed steps above), continuing the same rollout
     prof_steps = min(args.steps, 10)
     sim.profile(True)
+    prof_it = torch.zeros((), dtype=torch.int64, device=dev)
     for i, s in enumerate(range(args.warmup + args.steps, args.warmup + args.steps + prof_steps)):
         flush_buf.fill_(float(i))
         sim.set_poses(poses[s + 1])
         sim.apply_grasp_schedule(s)
         sim.step(1)
+        prof_it += sim.stats()[0].sum()
     torch.cuda.synchronize()
+    prof_mean_iters = prof_it.item() / (args.envs * prof_steps)
     prof = sim.profile_read()
     sim.profile(False)
     n_steps += prof_steps            # the rollout continues from here
@@ -653,8 +658,9 @@ def main():
     d_ms, d_n = prof[dom]
     avg_s = d_ms / max(d_n, 1) / 1e3
     # passes of each kernel class over every environment per step (Mode A:
-    # k local-global iterations + one residual pass; Mode B: the mean count)
-    it_pp = float(args.k) if args.mode == "fixed" else max(mean_iters, 1e-9)
+    # k local-global iterations + one residual pass; Mode B: the mean count
+    # of the profiled steps, whose launches skip environments that stopped)
+    it_pp = float(args.k) if args.mode == "fixed" else max(prof_mean_iters, 1e-9)
     applies = 2 + (args.lin_iters if args.metric == "full" else 0)   # A^-1 applications per iteration
     passes = {"local": it_pp + 1, "ncp": it_pp, "solve": applies * it_pp, "begin": 1, "end": 1, "warm": 1}[dom]
     # achieved = the kind's algorithmic work over the profiled steps / its
