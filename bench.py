@@ -57,8 +57,9 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="environment lanes stepped concurrently (0: automatic)")
     p.add_argument("--metric", default=None, choices=["lite", "full"],
                    help="contact metric: lite J M^-1 J^T + E, or full J A^-1 J^T + E with a GMRES Newton solve "
-                        "(default: full for cloth_grasp, cloth_stack and cloth_bar, whose bilateral grasp, "
-                        "stacked layers and box-feature rows the lite metric cannot hold, else lite)")
+                        "(default: full for cloth_grasp, cloth_stack, cloth_bar and tet_squeeze, whose bilateral "
+                        "grasp, stacked layers, box-feature rows and stiff pinch the lite metric cannot hold, "
+                        "else lite)")
     p.add_argument("--lin-iters", type=int, default=10, help="linear-solver (GMRES) iterations of the full metric")
     p.add_argument("--solve", default="auto", choices=["auto", "f32", "f16x3"])
     p.add_argument("--warm", default="cold", choices=["cold", "prev"])
@@ -69,7 +70,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.metric is None:
-        args.metric = "full" if args.workload in ("cloth_grasp", "cloth_stack", "cloth_bar") else "lite"
+        args.metric = "full" if args.workload in ("cloth_grasp", "cloth_stack", "cloth_bar", "tet_squeeze") else "lite"
     return args
 
 
