@@ -84,7 +84,8 @@ typedef int32_t flash_status;
  * independent environment partitions stepped concurrently on their own
  * streams (0 = chosen from the batch size; results do not depend on it).
  * eager: 0 = a step is captured once in a CUDA graph and replayed (not
- * while profiling or with the learned warm start or contact recording on);
+ * while profiling; the learned warm start and contact recording are part
+ * of the graph);
  * in FLASH_MODE_TOL the graph holds the iteration loop as a while-node that
  * the device keeps running while an environment is still iterating (at
  * most k_cap runs), so a step needs no host round trip; 1 = every step

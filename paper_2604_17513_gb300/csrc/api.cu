@@ -1289,7 +1289,7 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
   if (learned && !s->mlp_params) return fail(FLASH_ESTATE, "learned warm start needs weights (flash_warmstart_set)");
   cudaStream_t st = (cudaStream_t)stream;
-  const bool graphed = !s->d.eager && !s->profiling && !learned && !s->record;
+  const bool graphed = !s->d.eager && !s->profiling;
   if (graphed) {
     if (!s->graph || s->graph_stale) {
       const flash_status r = capture_step(s);

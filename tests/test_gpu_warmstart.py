@@ -112,3 +112,39 @@ def test_learned_warm_start_gain(cuda):
         it, r = sim.stats()
         conv.append(((r <= 1e-5) | (it >= 60)).all().item())
     assert all(conv) and sim.status() == 0
+
+
+def test_learned_and_recording_steps_replay_from_the_graph(cuda):
+    """With the learned warm start (a fixed random network, default input
+    range) and contact recording on, steps replayed from the captured graph
+    (tolerance mode, loop on the device, two lanes) give bit-identical
+    states, multipliers, iteration counts and recorded rows to steps
+    launched kernel by kernel."""
+    import torch
+    from paper_2604_17513_gb300 import flash, scenes, warmstart
+    sc = scenes.cloth_gripper(n_envs=130, n_side=16, side=0.25, steps=30)
+    p = (warmstart.init_params(3) * 0.01).to(cuda)   # small predictions: the iteration stays well inside its range
+    out = []
+    for eager in (True, False):
+        sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, mode=flash.MODE_TOL, k_cap=20, tol=1e-5, lanes=2, eager=eager)
+        q, v = flash.state_tensors(sc, cuda)
+        sim.set_state(q, v)
+        sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        sim.warmstart(p, flash.WARM_LEARNED)
+        sim.record(True)
+        rec = []
+        for s in range(12):
+            sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            sim.step(1)
+            X, T = sim.recorded()
+            rec.append((X.cpu().numpy(), T.cpu().numpy()))
+        it, r = sim.stats()
+        cnt, vert, obs, gam = sim.contacts()
+        out.append((sim.get_state()[0].cpu().numpy(), gam.cpu().numpy(), it.cpu().numpy(), rec, sim.status()))
+    (qe, ge, ie, re, se), (qg, gg, ig, rg, sg) = out
+    assert se == 0 and sg == 0
+    assert np.array_equal(qe, qg) and np.array_equal(ge, gg) and np.array_equal(ie, ig)
+    # targets of environments that did not converge are NaN rows in both (no target)
+    assert all(np.array_equal(a[0], b[0], equal_nan=True) and np.array_equal(a[1], b[1], equal_nan=True)
+               for a, b in zip(re, rg))
+    assert sum(len(a[0]) for a in re) > 1000
