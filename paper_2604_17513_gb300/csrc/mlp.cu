@@ -11,6 +11,8 @@
 //   k_mlp_adam      Adam update of the FP32 master weights
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "flash_internal.cuh"
 
 namespace flash {
@@ -31,54 +33,81 @@ __device__ void stage_params(const float *p, float *w) {
 }
 
 // ---------------------------------------------------------------- inference
-constexpr int FWD_T = 256;   // samples (= threads) per block
+// One sample per thread.  The layer-1 activations stay in registers; W2 is
+// staged transposed (W2t[j][i]), so the weights of eight consecutive output
+// neurons for input j are two 16-byte broadcast loads.  Blocks stage the
+// weights once and loop over 128-sample tiles.  Every output neuron sums its
+// inputs in ascending order from its bias, as the training kernel does.
+constexpr int FWD_T = 128;    // samples (= threads) per tile
+constexpr int FWD_MIN_BLOCKS = 2;
 
-__global__ void __launch_bounds__(FWD_T) k_mlp_forward(const float *__restrict__ params, const float *__restrict__ X,
-                                                       float *__restrict__ Y, const int64_t *__restrict__ n_rows_dev,
-                                                       int64_t n_rows_host) {
-  extern __shared__ float sm[];
-  float *w = sm;                       // NPARAM
-  float *h1 = sm + NPARAM + (NPARAM & 1);   // [NH][FWD_T]
-  const int64_t n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
-  const int64_t row0 = (int64_t)blockIdx.x * FWD_T;
-  if (row0 >= n_rows) return;
-  stage_params(params, w);
-  __syncthreads();
-  const int t = threadIdx.x;
-  const int64_t row = row0 + t;
-  const bool live = row < n_rows;
-  float x[NI];
-#pragma unroll
-  for (int j = 0; j < NI; j++) x[j] = live ? X[row * NI + j] : 0.f;
-  for (int i = 0; i < NH; i++) {
-    float s = w[OFF_B1 + i];
-#pragma unroll
-    for (int j = 0; j < NI; j++) s = fmaf(w[OFF_W1 + i * NI + j], x[j], s);
-    h1[i * FWD_T + t] = fmaxf(s, 0.f);
-  }
-  // layer 2 fused with layer 3: y += W3[:, i] * relu(W2[i, :] h1 + b2[i])
-  float y[NO];
-#pragma unroll
-  for (int k = 0; k < NO; k++) y[k] = w[OFF_B3 + k];
-  for (int i = 0; i < NH; i += 4) {
-    float s0 = w[OFF_B2 + i], s1 = w[OFF_B2 + i + 1], s2 = w[OFF_B2 + i + 2], s3 = w[OFF_B2 + i + 3];
-#pragma unroll 8
-    for (int j = 0; j < NH; j++) {
-      const float h = h1[j * FWD_T + t];
-      s0 = fmaf(w[OFF_W2 + i * NH + j], h, s0);
-      s1 = fmaf(w[OFF_W2 + (i + 1) * NH + j], h, s1);
-      s2 = fmaf(w[OFF_W2 + (i + 2) * NH + j], h, s2);
-      s3 = fmaf(w[OFF_W2 + (i + 3) * NH + j], h, s3);
+__device__ void stage_params_fwd(const float *p, float *w) {
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
+    const bool bias = (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) || i >= OFF_B3;
+    int d = i;
+    if (i >= OFF_W2 && i < OFF_B2) {   // W2[r][c] -> W2t[c][r]
+      const int r = (i - OFF_W2) / NH, c = (i - OFF_W2) % NH;
+      d = OFF_W2 + c * NH + r;
     }
-    s0 = fmaxf(s0, 0.f); s1 = fmaxf(s1, 0.f); s2 = fmaxf(s2, 0.f); s3 = fmaxf(s3, 0.f);
-#pragma unroll
-    for (int k = 0; k < NO; k++)
-      y[k] += w[OFF_W3 + k * NH + i] * s0 + w[OFF_W3 + k * NH + i + 1] * s1 + w[OFF_W3 + k * NH + i + 2] * s2 +
-              w[OFF_W3 + k * NH + i + 3] * s3;
+    w[d] = bias ? p[i] : bf16r(p[i]);
   }
-  if (live)
+}
+
+__global__ void __launch_bounds__(FWD_T, FWD_MIN_BLOCKS) k_mlp_forward(const float *__restrict__ params,
+                                                                      const float *__restrict__ X,
+                                                                      float *__restrict__ Y,
+                                                                      const int64_t *__restrict__ n_rows_dev,
+                                                                      int64_t n_rows_host) {
+  extern __shared__ __align__(16) float sm[];
+  float *w = sm;   // NPARAM (W2 transposed)
+  const int64_t n_rows = n_rows_dev ? *n_rows_dev : n_rows_host;
+  const int64_t tiles = (n_rows + FWD_T - 1) / FWD_T;
+  if (blockIdx.x >= tiles) return;
+  stage_params_fwd(params, w);
+  __syncthreads();
+  const float4 *w2t = reinterpret_cast<const float4 *>(w + OFF_W2);   // OFF_W2 is a multiple of 4
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * FWD_T + threadIdx.x;
+    const bool live = row < n_rows;
+    float x[NI];
 #pragma unroll
-    for (int k = 0; k < NO; k++) Y[row * NO + k] = y[k];
+    for (int j = 0; j < NI; j++) x[j] = live ? X[row * NI + j] : 0.f;
+    float h1[NH];
+#pragma unroll
+    for (int i = 0; i < NH; i++) {
+      float s = w[OFF_B1 + i];
+#pragma unroll
+      for (int j = 0; j < NI; j++) s = fmaf(w[OFF_W1 + i * NI + j], x[j], s);
+      h1[i] = fmaxf(s, 0.f);
+    }
+    // layer 2 fused with layer 3: y += W3[:, i] * relu(W2[i, :] h1 + b2[i])
+    float y[NO];
+#pragma unroll
+    for (int k = 0; k < NO; k++) y[k] = w[OFF_B3 + k];
+    for (int i = 0; i < NH; i += 8) {
+      float s[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) s[u] = w[OFF_B2 + i + u];
+#pragma unroll
+      for (int j = 0; j < NH; j++) {
+        const float4 a = w2t[(j * NH + i) >> 2], b = w2t[((j * NH + i) >> 2) + 1];
+        const float h = h1[j];
+        s[0] = fmaf(a.x, h, s[0]); s[1] = fmaf(a.y, h, s[1]); s[2] = fmaf(a.z, h, s[2]); s[3] = fmaf(a.w, h, s[3]);
+        s[4] = fmaf(b.x, h, s[4]); s[5] = fmaf(b.y, h, s[5]); s[6] = fmaf(b.z, h, s[6]); s[7] = fmaf(b.w, h, s[7]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) s[u] = fmaxf(s[u], 0.f);
+#pragma unroll
+      for (int g = 0; g < 8; g += 4)
+#pragma unroll
+        for (int k = 0; k < NO; k++)
+          y[k] += w[OFF_W3 + k * NH + i + g] * s[g] + w[OFF_W3 + k * NH + i + g + 1] * s[g + 1] +
+                  w[OFF_W3 + k * NH + i + g + 2] * s[g + 2] + w[OFF_W3 + k * NH + i + g + 3] * s[g + 3];
+    }
+    if (live)
+#pragma unroll
+      for (int k = 0; k < NO; k++) Y[row * NO + k] = y[k];
+  }
 }
 
 // ---------------------------------------------------------------- training
@@ -205,7 +234,7 @@ __global__ void k_sum(const float *x, int n, float *out) {
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-size_t fwd_smem() { return sizeof(float) * (NPARAM + (NPARAM & 1) + NH * FWD_T); }
+size_t fwd_smem() { return sizeof(float) * NPARAM; }
 size_t bwd_smem() { return sizeof(float) * (NPARAM + (NPARAM & 1) + 3 * NH * BWD_T); }
 
 cudaError_t configure_mlp() {
@@ -227,7 +256,15 @@ cudaError_t mlp_forward(const float *params, const float *X, float *Y, const int
   cudaError_t e = configure_mlp();
   if (e != cudaSuccess) return e;
   if (max_rows <= 0) return cudaSuccess;
-  const int64_t blocks = (max_rows + FWD_T - 1) / FWD_T;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  // enough blocks to fill every SM at the resident count; each loops over tiles
+  const int64_t tiles = (max_rows + FWD_T - 1) / FWD_T;
+  const int64_t blocks = std::min<int64_t>(tiles, (int64_t)sms * FWD_MIN_BLOCKS);
   k_mlp_forward<<<(unsigned)blocks, FWD_T, fwd_smem(), st>>>(params, X, Y, n_rows_dev, max_rows);
   return cudaGetLastError();
 }
