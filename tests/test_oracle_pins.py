@@ -864,3 +864,26 @@ def test_bar_and_post_hold_the_cloth_between_its_vertices():
             g = st.gamma[i]
             assert gap >= -1e-8 and g[0] >= -1e-15 and abs(g[0] * gap) <= 1e-14
             assert np.linalg.norm(g[1:]) <= sc.mu[0] * max(g[0], 0) + 1e-13
+
+
+@pytest.mark.parametrize("u", [0.01, 0.2])
+def test_box_feature_friction_closed_form(u):
+    """Coulomb friction through box-edge rows: the knife edge under the
+    square translates along its own axis x at speed u.
+    The body's weight rests on those rows, so friction can change its
+    velocity by at most mu g h per step: for u <= mu g h it sticks and rides
+    along (x_n = u h n); for u > mu g h it slides, x_n = mu g h^2 n (n + 1) / 2
+    until it reaches the support's speed, then rides along.  Heights stay at
+    rest.  This pins the kinematic motion in the rows' slip and the cone."""
+    mu, h, g = 0.5, 0.01, 9.81
+    sc = scenes.edge_support(steps=6, mu=mu)
+    sc.poses[0, :, 0, 0] = u * h * np.arange(sc.poses.shape[1])
+    mesh = oracle.Mesh.from_scene(sc, 0)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    x, v = 0.0, 0.0
+    for n in range(1, 6):
+        oracle.step(mesh, sc, 0, n - 1, st, metric=1, mode=1, tol=1e-12, k_cap=400)
+        v = min(v + mu * g * h, u)          # the velocity friction can reach, capped at the support's
+        x += v * h
+        assert np.abs(st.q[:, 0] - sc.q0[0][:, 0] - x).max() < 1e-9, (n, st.q[:, 0] - sc.q0[0][:, 0], x)
+        assert np.abs(st.q[:, 2] - sc.q0[0][:, 2]).max() < 1e-9
