@@ -1,5 +1,5 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
-times: automatic lanes, graph replay of fixed-iteration steps and autotuned
+times: automatic lanes, graph replay (fixed iterations, or the tolerance loop as a device while-node) and autotuned
 tensor-core tiles.  Every environment steps on the GPU; a sample, including
 the first and last environment of lanes, starts from the oracle's state at
 step s and is checked against one oracle step, one by one (max vertex
@@ -122,3 +122,42 @@ def test_cloth_grasp_full_metric_full_size(cuda):
     sc = scenes.cloth_grasp(seed=1, n_envs=1024, n_side=32, side=0.5, steps=10, grasp_step=2,
                             release_step=1 << 30)
     _check([sc], [(0, 0), (0, 255), (0, 256), (0, 1023)], 6, cuda, lanes=4, metric=1)
+
+
+def test_cloth_gripper_full_size_tolerance_mode(cuda):
+    """The bench's default configuration at full size: 1024 environments of
+    the 32x32 cloth, tolerance mode (r_ncp <= 1e-5, at most 10 iterations)
+    replayed from the graph whose loop is a device while-node, 4 lanes;
+    samples at both ends of lanes against one oracle step with the same
+    stopping rule.  A sample that stops after as many iterations as the
+    oracle ran the same iterates as in fixed mode (bound 1e-5 m); FP32 and
+    FP64 may cross the threshold one iteration apart, and then the states
+    differ by about that iteration's update (bound 1e-4 m)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_gripper(n_envs=1024, steps=20)
+    s = 10
+    kw = dict(mode=1, tol=1e-5, k_min=1, k_cap=10)
+    picks = [0, 255, 256, 1023]
+    q, v = sc.q0.reshape(-1, 3).copy(), sc.v0.reshape(-1, 3).copy()
+    n = sc.n_verts
+    refs = {}
+    for e in picks:
+        mesh, q0, v0, _ = _oracle_state(sc, e, s)
+        q[e * n:(e + 1) * n], v[e * n:(e + 1) * n] = q0, v0
+        ref = oracle.EnvState(q0, v0)
+        oracle.step(mesh, sc, e, s, ref, **kw)
+        refs[e] = ref
+    sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, **kw)
+    assert sim.lane_count() == 4
+    sim.set_state(torch.from_numpy(q.astype(np.float32)).to(cuda), torch.from_numpy(v.astype(np.float32)).to(cuda))
+    sim.set_poses(flash.poses_tensor(sc, s, cuda), which=0)
+    sim.set_poses(flash.poses_tensor(sc, s + 1, cuda), which=1)
+    sim.step(1)
+    assert sim.status() == 0
+    qg = sim.get_state()[0].cpu().numpy()
+    it = sim.stats()[0].cpu().numpy()
+    for e, ref in refs.items():
+        err = np.abs(qg[e * n:(e + 1) * n] - ref.q).max()
+        assert abs(int(it[e]) - ref.iters) <= 1, (e, it[e], ref.iters)
+        assert err <= (POS_TOL if it[e] == ref.iters else 1e-4), (e, it[e], ref.iters, err)
