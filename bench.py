@@ -604,10 +604,11 @@ def main():
     # ---------------- device-resident timed region
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
-    def timed_steps(first):
+    def timed_steps(first, it_log=None):
         """args.steps steps starting at step index ``first``: per-step event
         times (L2 flushed between steps, outside the events), converged count,
-        iteration sum."""
+        iteration sum; each step's per-environment iteration counts are
+        appended to ``it_log`` when given."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         conv = torch.zeros((), dtype=torch.int64, device=dev)
         it_sum = torch.zeros((), dtype=torch.int64, device=dev)
@@ -621,6 +622,8 @@ def main():
             it, r = sim.stats()
             conv += (r <= TOL).sum()
             it_sum += it.sum()
+            if it_log is not None:
+                it_log.append(it)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
         return ms, conv.item(), it_sum.item()
@@ -630,7 +633,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms, n_conv, n_it = timed_steps(args.warmup)
+        it_log = []
+        ms, n_conv, n_it = timed_steps(args.warmup, it_log)
     if world > 1:
         dist.barrier()
     launches = sim.launch_count() - launches0
@@ -652,6 +656,10 @@ def main():
     n_steps += prof_steps            # the rollout continues from here
     frac_conv = n_conv / (args.envs * args.steps)
     mean_iters = n_it / (args.envs * args.steps)
+    try:   # 99th percentile of the per-environment iteration counts of the timed steps
+        p99_iters = float(torch.quantile(torch.cat(it_log).float(), 0.99).item())
+    except Exception:
+        p99_iters = None
     # headline: env-steps that reach r_ncp <= 1e-5, per second (all ranks)
     value, ms_max = aggregate(ms, args.envs * frac_conv, world, dev)
     value_all, _ = aggregate(ms, args.envs, world, dev)
@@ -783,6 +791,7 @@ def main():
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
                        "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths()))},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
+            "p99_iters": p99_iters,
             "status": status, "warm_start": warm_cmp,
             "step_hbm_frac_of_measured": step_hbm_frac,
             "roofline": roof, "kernels": kernels,
