@@ -887,3 +887,117 @@ def test_box_feature_friction_closed_form(u):
         x += v * h
         assert np.abs(st.q[:, 0] - sc.q0[0][:, 0] - x).max() < 1e-9, (n, st.q[:, 0] - sc.q0[0][:, 0], x)
         assert np.abs(st.q[:, 2] - sc.q0[0][:, 2]).max() < 1e-9
+
+
+# ------------------------------------------------------------ sphere, compliance, tet stiffness
+_SPHERE_C = np.array([0.1, -0.2, 0.3])
+_SPHERE_R = 0.15
+
+
+def _sphere_particle(theta, mu, steps, phi=0.7, tau=1e-3, mass=0.01):
+    """A particle released at rest one thickness outside a sphere (off the
+    origin), at polar angle theta from its top and azimuth phi."""
+    d = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+    x0 = _SPHERE_C + (_SPHERE_R + tau) * d
+    poses = np.array([[[*_SPHERE_C, 1, 0, 0, 0]] for _ in range(steps + 1)])
+    sc = _particle_scene([(scenes.SPHERE, (_SPHERE_R, 0, 0))], poses, mu, steps, x0, mass=mass)
+    return sc, d
+
+
+def test_particle_resting_on_top_of_sphere():
+    """Sphere SDF (Sec. III-A contact; obstacle geometry): a particle at the
+    top of a sphere whose centre is not the origin carries its weight through
+    one normal contact, gamma_n = m g h^2, with zero gap, and does not move;
+    the contact frame's normal is the radial direction (+z there)."""
+    sc, _ = _sphere_particle(0.0, 0.3, 6)
+    st = oracle.rollout(sc, 0, 6, mode=1, tol=1e-13, k_cap=100)
+    m, g, h = sc.mass[0], 9.81, sc.h
+    assert len(st.cvert) == 1
+    assert abs(st.gamma[0, 0] - m * g * h * h) < 1e-12
+    assert np.abs(st.q[0] - sc.q0[0, 0]).max() < 1e-12
+    sd, nrm = oracle.sdf(scenes.SPHERE, (_SPHERE_R, 0, 0), sc.poses[0, 0, 0], st.q[0])
+    assert abs(sd - sc.thickness) < 1e-12 and np.abs(nrm - [0, 0, 1]).max() < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.5])
+def test_particle_on_sphere_sticks_iff_tan_theta_le_mu(theta):
+    """On a sphere the supporting tangent plane at polar angle theta is an
+    incline of angle theta: Coulomb friction holds the particle iff
+    tan(theta) <= mu (mu swept in steps of 0.001 around tan theta).  A sliding
+    particle keeps its gap zero (it stays on the sphere, one thickness out)
+    and moves downhill along the sphere's meridian."""
+    t = np.tan(theta)
+    for dmu in (-0.002, -0.001, 0.001, 0.002):
+        mu = t + dmu
+        sc, d = _sphere_particle(theta, mu, 8)
+        st = oracle.rollout(sc, 0, 8, mode=1, tol=1e-13, k_cap=200)
+        disp = st.q[0] - sc.q0[0, 0]
+        if mu >= t:
+            assert np.linalg.norm(disp) < 1e-12, (mu, disp)
+        else:
+            assert np.linalg.norm(disp) > 1e-7, (mu, disp)
+            assert abs(np.linalg.norm(st.q[0] - _SPHERE_C) - (_SPHERE_R + sc.thickness)) < 1e-10
+            # downhill: the polar angle grows, the azimuth is kept
+            r = st.q[0] - _SPHERE_C
+            assert np.arccos(r[2] / np.linalg.norm(r)) > theta
+            assert abs(np.arctan2(r[1], r[0]) - 0.7) < 1e-9
+
+
+@pytest.mark.parametrize("comp", [5e-4, 2e-3])
+def test_compliant_plane_gap_closed_form(comp):
+    """Normal compliance c (m/N) of an obstacle: the normal law is
+    FB(a + alpha y_n, y_n) with y_n = gamma_n / m and alpha = c m / h^2.  A
+    particle resting on the plane carries y_n = g h^2, and FB = 0 with
+    y_n > 0 needs a + alpha y_n = 0: it sinks to the gap -c m g, while the
+    multiplier stays m g h^2.  m = 0.03 kg and h = 1/50 s, so a misplaced mass
+    or h^2 factor changes the gap."""
+    m, h = 0.03, 0.02
+    steps = 30
+    poses = np.array([[[0, 0, 0, 1, 0, 0, 0]] for _ in range(steps + 1)])
+    sc = _particle_scene([(scenes.PLANE, (0, 0, 0))], poses, 0.4, steps, (0, 0, 1e-3), h=h, mass=m)
+    sc.obs_comp[:] = comp
+    st = oracle.rollout(sc, 0, steps, mode=1, tol=1e-13, k_cap=200)
+    g = 9.81
+    gap = st.q[0, 2] - sc.thickness
+    assert abs(gap - (-comp * m * g)) < 1e-9 * max(1.0, comp * m * g / 1e-6)
+    assert abs(st.gamma[0, 0] - m * g * h * h) < 1e-10
+    assert abs(st.v[0, 2]) < 1e-6
+
+
+def test_tet_uniform_stretch_energy_with_stiffness_scale():
+    """Corotational tets (Eq. internal): w_i = w_stretch * k_e * rest volume.
+    Stretching the whole block by (1 + eps) along x gives F = diag(1 + eps,
+    1, 1) in every tet, closest rotation I, so the energy is
+    w_stretch * k_e * V * eps^2 / 2 with V the block's volume."""
+    sc = scenes.tet_squeeze(n_envs=2, steps=1)
+    sc.stiff[1] = 37.0
+    vol = 0.08 * 0.08 * 0.04
+    eps = 0.021
+    for env in (0, 1):
+        m = oracle.Mesh.from_scene(sc, env)
+        q = sc.rest.copy()
+        q[:, 0] *= 1 + eps
+        p = m.project(q)
+        E = m.energy(q, q, p)
+        ref = 0.5 * sc.w_stretch * sc.stiff[env] * vol * eps ** 2
+        assert abs(E - ref) < 1e-9 * ref, (env, E, ref)
+
+
+def test_tet_energy_hessian_equals_system_matrix():
+    """The tet block's PD energy Hessian (central differences, fixed
+    projections) equals A / h^2 with A = M + h^2 sum w_i G_i^T G_i, at a
+    stiffness scale k_e != 1: this pins the scale of A's stiffness block."""
+    sc = scenes.tet_squeeze(n_envs=1, steps=1)
+    sc.stiff[0] = 13.0
+    m = oracle.Mesh.from_scene(sc, 0)
+    A = m.matrix()
+    rng = np.random.default_rng(8)
+    q0 = sc.rest + 1e-3 * rng.normal(size=sc.rest.shape)
+    p0 = m.project(q0)
+    for _ in range(3):
+        d = rng.normal(size=q0.shape)
+        t = 1e-4
+        e_p, e_0, e_m = (m.energy(q0 + t * d, q0, p0), m.energy(q0, q0, p0), m.energy(q0 - t * d, q0, p0))
+        fd = (e_p - 2 * e_0 + e_m) / t ** 2
+        exact = np.sum(d * (A @ d)) / sc.h ** 2
+        assert abs(fd - exact) < 1e-6 * abs(exact)
