@@ -324,7 +324,19 @@ flash_status flash_get_contact_tris(const flash_scene *s, int32_t *tri, void *st
 /* Per-environment statistics of the last step: iterations used and the NCP
  * residual max_j |phi_j| (m) of the final iterate; device int32/float32 [N]. */
 flash_status flash_get_stats(const flash_scene *s, int32_t *iters, float *rncp, void *stream);
-/* Device status word (FLASH_OK or a warning/error code); synchronises. */
+/* Device status word of the steps since the last flash_set_state (which
+ * clears it), as a flash_status; synchronises the stream.  The kernels set
+ * bits and never trap; this call turns them into, by priority:
+ *   FLASH_ETIMEOUT  a bounded mbarrier wait of the tensor-core solve ran out
+ *                   (its results are not valid);
+ *   FLASH_ENUMERIC  a non-finite position or NCP residual (the environment
+ *                   holding it stops iterating; other environments are not
+ *                   affected, they share no data);
+ *   FLASH_WOVERFLOW a contact list exceeded the scene's contact_cap (the
+ *                   rows past it were dropped), or a vertex held more rows
+ *                   than the lite metric's per-vertex block (4; the extra
+ *                   rows were left unsolved).
+ * flash_last_error() names the cause. */
 flash_status flash_status_word(flash_scene *s, void *stream);
 
 /* The global solve alone (Eq. correction's A^-1 apply) on the environments of
@@ -406,12 +418,15 @@ flash_status flash_mlp_adam(float *params, const float *grad, float *m, float *v
  * device memory up front, where an allocation can implicitly synchronise the
  * device and stall the loop or exceed the host's memory budget.  The paper
  * has no counterpart; it is the global solve's FP32 apply as a standalone
- * call.  Ainv: device float32 [n][n] (e.g. the explicit inverse of a mesh's
- * system matrix); rhs, out: device float32 [m][n][3], caller-owned.  Limits:
- * n <= 512 vertices and m <= 256 environments per call; larger sizes return
- * FLASH_EINVAL.  Scratch is a fixed 4 MiB __device__ array that every GPU
- * loading the library holds until exit; the first call on a device looks up
- * its address (make that first call before any stream capture).  Calls share
+ * call.  Ainv: device float32 [n][n], row-major, any square matrix (e.g. the
+ * explicit inverse of a mesh's system matrix; it need not be symmetric):
+ * out[e][i][c] = sum_j Ainv[i][j] rhs[e][j][c].  rhs, out: device float32
+ * [m][n][3], caller-owned.  Limits: n <= 512 vertices and m <= 256
+ * environments per call; larger sizes return FLASH_EINVAL.  Scratch is a
+ * fixed 4 MiB __device__ array that every GPU loading the library holds
+ * until exit; a device's first call looks up its address (make that first
+ * call before any stream capture), and a call looks it up again when the
+ * device's context has changed since (after cudaDeviceReset).  Calls share
  * the array: calls that overlap on the GPU race. */
 flash_status flash_dense_apply_noalloc(const float *Ainv, int32_t n, int32_t m, const float *rhs, float *out,
                                        void *stream);

@@ -958,6 +958,9 @@ int32_t flash_contact_cap(const flash_scene *s) { return s ? s->cap : 0; }
 flash_status flash_set_state(flash_scene *s, const float *q, const float *v, void *stream) {
   if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
   for (auto &g : s->groups) FLASH_CUDA_TRY(launch_state_io(s, g, q, v, nullptr, nullptr, 0, (cudaStream_t)stream));
+  // a new state starts a new history: the status word reports only what the
+  // steps taken from it find
+  FLASH_CUDA_TRY(cudaMemsetAsync(s->status, 0, sizeof(int), (cudaStream_t)stream));
   return FLASH_OK;
 }
 
@@ -1453,8 +1456,16 @@ flash_status flash_status_word(flash_scene *s, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemcpyAsync(&w, s->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  if (w & (1 << 11)) return fail(FLASH_ETIMEOUT, "a bounded wait of the tensor-core solve ran out");
   if (w & (1 << 9)) return fail(FLASH_ENUMERIC, "non-finite state or residual");
-  if (w & ((1 << 8) | (1 << 10))) return FLASH_WOVERFLOW;
+  if (w & (1 << 8)) {
+    set_error("contacts beyond the scene's contact capacity were dropped");
+    return FLASH_WOVERFLOW;
+  }
+  if (w & (1 << 10)) {
+    set_error("a vertex had more contacts than the per-vertex NCP block holds; the extra rows were not solved");
+    return FLASH_WOVERFLOW;
+  }
   return FLASH_OK;
 }
 

@@ -22,31 +22,68 @@ static __device__ __align__(256) float g_noalloc_scratch[kNaA + 2 * kNaCols];
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mu;
 float *g_na_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_na_ctx[kMaxDevices] = {0};   // context the cached address belongs to
 
-// device address of the scratch array for the current device (resolved once
-// per device, with that device current)
+// Unique id of the calling thread's current CUDA context (0 when none is
+// current or the driver cannot say).  A device reset destroys the primary
+// context and a new one loads this library's module at a new address, so the
+// cached symbol address is keyed on this id.  The driver calls are resolved
+// through the runtime, so the library still links no libcuda.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+  });
+  if (!get_cur || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// device address of the scratch array for the current device, looked up with
+// that device current on its first use and again whenever its context has
+// changed since (after a device reset); with no context id available it is
+// looked up on every call
 cudaError_t scratch_for_current_device(float **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_na_mu);
-  if (!g_na_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_na_ptr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_na_ptr[dev] = static_cast<float *>(p);
+    g_na_ctx[dev] = current_context_id();   // the lookup made the primary context current
   }
   *out = g_na_ptr[dev];
   return cudaSuccess;
 }
 
-// copy A^-1 [n][n] into the zero-padded [n_pad][n_pad] block
+// copy the transpose of A^-1 [n][n] (row-major) into the zero-padded
+// [n_pad][n_pad] block: the CUDA-core contraction reads its matrix operand
+// along rows and forms M^T * RHS, so it is given M = (A^-1)^T and returns
+// A^-1 * RHS for any square matrix, symmetric or not
 __global__ void k_na_pad_matrix(const float *A, int n, int n_pad, float *Ap) {
   const size_t total = (size_t)n_pad * n_pad;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / n_pad), j = (int)(t % n_pad);
-    Ap[t] = (i < n && j < n) ? A[(size_t)i * n + j] : 0.f;
+    Ap[t] = (i < n && j < n) ? A[(size_t)j * n + i] : 0.f;
   }
 }
 

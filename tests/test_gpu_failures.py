@@ -1,0 +1,158 @@
+"""Failure paths of the step, injected on the host (no GPU fault, no trap).
+
+The kernels never trap: a device-side problem sets a bit of the scene's
+status word, and flash_status_word turns it into the documented code (with
+flash_last_error naming the cause).  Here the problem is put into the
+inputs by the host: a NaN in one environment's state through
+flash_set_state, a contact capacity smaller than the scene needs, a vertex
+with more contacts than the lite metric's per-vertex block.  The resume test
+checks that flash_get_state / flash_set_state / flash_set_obstacle_poses
+carry everything a cold-started step depends on: a rollout interrupted and
+resumed from its checkpoint is bit-identical to the uninterrupted one.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_17513_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(sim, sc, q, v, s):
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sim.set_state(torch.from_numpy(np.asarray(q, np.float32).reshape(-1, 3)).to(sim.dev),
+                  torch.from_numpy(np.asarray(v, np.float32).reshape(-1, 3)).to(sim.dev))
+    sim.set_poses(flash.poses_tensor(sc, s, sim.dev), which=0)
+
+
+def _steps(sim, sc, s0, n):
+    from paper_2604_17513_gb300 import flash
+    for s in range(s0, s0 + n):
+        sim.set_poses(flash.poses_tensor(sc, s + 1, sim.dev), which=1)
+        sim.step(1)
+
+
+@pytest.mark.parametrize("solve", [0, 1])
+def test_nan_state_reports_enumeric_and_spares_other_envs(cuda, solve):
+    """A NaN position in environment 1 (of 3): the status word reports
+    FLASH_ENUMERIC, and environments 0 and 2 end bit-identical to a run
+    without the NaN (environments share no data)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_drop(n_envs=3, steps=40)
+    s = 26
+    outs = []
+    for poison in (False, True):
+        sim = flash.Sim(sc, solve=solve)
+        q = sc.q0.copy() + np.array([0.0, 0.0, -0.3])
+        if poison:
+            q[1, 17, 2] = np.nan
+        _state(sim, sc, q, sc.v0, s)
+        assert sim.status() == flash.OK
+        _steps(sim, sc, s, 2)
+        qg, _ = sim.get_state()
+        torch.cuda.synchronize()
+        if poison:
+            with pytest.raises(flash.FlashError) as ei:
+                sim.status()
+            assert ei.value.code == flash.ENUMERIC and "non-finite" in str(ei.value)
+            # a clean state clears the word
+            _state(sim, sc, sc.q0, sc.v0, s)
+            assert sim.status() == flash.OK
+        else:
+            assert sim.status() == flash.OK
+        outs.append(qg.cpu().numpy().reshape(3, sc.n_verts, 3))
+    clean, poisoned = outs
+    assert np.isfinite(clean).all() and not np.isfinite(poisoned[1]).all()
+    assert np.array_equal(clean[0], poisoned[0]) and np.array_equal(clean[2], poisoned[2])
+
+
+def test_contact_capacity_overflow_warns(cuda):
+    """A contact capacity of 2 rows for a cloth touching the sphere with 4
+    vertices: the rows past 2 are dropped and the status word reports
+    FLASH_WOVERFLOW (a warning, > 0), naming the capacity; the same scene with
+    the default capacity reports FLASH_OK."""
+    import oracle
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_drop(n_envs=1, steps=60)
+    mesh = oracle.Mesh.from_scene(sc)
+    st = oracle.EnvState(sc.q0[0], sc.v0[0])
+    s = 40
+    for k in range(s):
+        oracle.step(mesh, sc, 0, k, st)
+    assert len(st.cvert) > 2
+    for cap, want in ((2, flash.WOVERFLOW), (None, flash.OK)):
+        sim = flash.Sim(sc, contact_cap=cap)
+        _state(sim, sc, st.q[None], st.v[None], s)
+        _steps(sim, sc, s, 1)
+        assert sim.status() == want, cap
+        cnt = sim.contacts()[0].cpu().numpy()
+        if cap:
+            assert cnt[0] == 2
+            assert b"capacity" in flash.lib().flash_last_error()
+        else:
+            assert cnt[0] == len(st.cvert)
+
+
+def _five_planes_particle(steps=3):
+    """One particle 1 mm above the ground and four more planes through the
+    origin, tilted by 0.1 rad about four horizontal axes: five obstacle rows
+    on one vertex, one more than the lite metric's per-vertex block."""
+    ang = 0.1
+    poses = [scenes._pose((0, 0, 0))]
+    for ax in ((1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0)):
+        c, sn = np.cos(ang / 2), np.sin(ang / 2)
+        poses.append(scenes._pose((0, 0, 0), (c, sn * ax[0], sn * ax[1], sn * ax[2])))
+    P = np.array([[poses for _ in range(steps + 1)]], float)
+    q0 = np.array([[[0.0, 0.0, 1e-3]]])
+    return scenes.Scene("five_planes", scenes.TRI, np.zeros((1, 3)), np.zeros((0, 3), np.int32), np.array([0.01]),
+                        0.0, 0.0, q0, np.zeros_like(q0), np.array([0.5]), np.ones(1),
+                        np.full((1, 5), scenes.PLANE, np.int32), np.zeros((1, 5, 3)), np.zeros((1, 5)), P,
+                        thickness=1e-3, steps=steps)
+
+
+def test_too_many_contacts_on_one_vertex_warns(cuda):
+    """Five rows on one vertex with the lite metric (blocks of at most four):
+    FLASH_WOVERFLOW naming the per-vertex block; the full metric solves all
+    rows jointly and reports FLASH_OK."""
+    from paper_2604_17513_gb300 import flash
+    sc = _five_planes_particle()
+    for metric, want in ((flash.METRIC_LITE, flash.WOVERFLOW), (flash.METRIC_FULL, flash.OK)):
+        sim = flash.Sim(sc, metric=metric)
+        _state(sim, sc, sc.q0, sc.v0, 0)
+        _steps(sim, sc, 0, 1)
+        cnt = sim.contacts()[0].cpu().numpy()
+        assert cnt[0] == 5
+        assert sim.status() == want, metric
+        if want == flash.WOVERFLOW:
+            assert b"per-vertex" in flash.lib().flash_last_error()
+
+
+@pytest.mark.parametrize("mode", ["fixed", "tol"])
+def test_checkpoint_resume_is_bit_exact(cuda, mode):
+    """Checkpoint (flash_get_state) after 3 steps of the gripper scene, 4 more
+    steps; then restore the checkpoint (flash_set_state, obstacle poses of
+    the checkpoint's step) in the same scene and in a new scene, and take the
+    same 4 steps: positions and velocities are bit-identical (cold start: a
+    step depends only on q, v and the obstacle poses)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_gripper(n_envs=8, steps=20)
+    kw = dict(mode=flash.MODE_TOL, k_cap=20) if mode == "tol" else dict(mode=flash.MODE_FIXED)
+    sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, **kw)
+    _state(sim, sc, sc.q0, sc.v0, 0)
+    _steps(sim, sc, 0, 3)
+    q_ck, v_ck = (t.clone() for t in sim.get_state())
+    _steps(sim, sc, 3, 4)
+    q_ref, v_ref = (t.cpu().numpy() for t in sim.get_state())
+    it_ref = sim.stats()[0].cpu().numpy()
+    for target in (sim, flash.Sim(sc, solve=flash.SOLVE_F16X3, **kw)):
+        target.set_state(q_ck, v_ck)
+        target.set_poses(flash.poses_tensor(sc, 3, target.dev), which=0)
+        _steps(target, sc, 3, 4)
+        q, v = (t.cpu().numpy() for t in target.get_state())
+        torch.cuda.synchronize()
+        assert np.array_equal(q, q_ref) and np.array_equal(v, v_ref)
+        assert np.array_equal(target.stats()[0].cpu().numpy(), it_ref)
+        assert target.status() == flash.OK

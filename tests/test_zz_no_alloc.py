@@ -1,10 +1,12 @@
 """The allocation-free dense apply, for callers that must not call cudaMalloc
 (real-time loops and plugin hosts that reserve device memory up front).
 
-It is checked through the C ABI against the scene-based global solve
-(flash_global_apply, FP32 path) on two calls in a row; the second call is
-smaller than the first, so stale scratch contents from the first call would
-show up in its padding.  Collected last on purpose: it holds a fixed
+It is checked through the C ABI on two calls in a row against the scene-based
+global solve (flash_global_apply, FP32 path) and against a float64 product
+on the host, also with a non-symmetric matrix (the call must return
+Ainv * rhs, not its transpose applied).  The second call is smaller than the
+first, so stale scratch contents from the first call would show up in its
+padding.  Collected last on purpose: it holds a fixed
 __device__ scratch array and should run after every other test.
 """
 import ctypes as C
@@ -47,6 +49,37 @@ def test_noalloc_apply_matches_global_apply(cuda):
         torch.cuda.synchronize()
         err = (out - ref).abs().max().item() / ref.abs().max().item()
         assert err < REL_TOL, (m, err)
+        host = np.einsum("ij,ejc->eic", Ainv.cpu().numpy().astype(np.float64),
+                         rhs.cpu().numpy().astype(np.float64).reshape(m, n, 3))
+        err64 = np.abs(out.cpu().numpy().reshape(m, n, 3) - host).max() / np.abs(host).max()
+        assert err64 < REL_TOL, (m, err64)
+
+
+def test_noalloc_apply_non_symmetric_matches_float64(cuda):
+    """out = Ainv * rhs for a random non-symmetric [n][n] matrix, against the
+    float64 host product, on two calls in a row (the second smaller)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    lib = flash.lib()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(12)
+    for n, m in ((300, 40), (130, 3)):
+        M = rng.normal(size=(n, n)) + 4.0 * np.eye(n) + 2.0 * np.triu(rng.normal(size=(n, n)), 1)
+        assert np.abs(M - M.T).max() > 1.0
+        Mf = M.astype(np.float32)
+        rhs = rng.normal(size=(m, n, 3)).astype(np.float32)
+        ref = np.einsum("ij,ejc->eic", Mf.astype(np.float64), rhs.astype(np.float64))
+        out = torch.full((m * n, 3), float("nan"), dtype=torch.float32, device=cuda)
+        code = _noalloc(lib, torch.from_numpy(Mf).to(cuda), n, m, torch.from_numpy(rhs.reshape(-1, 3)).to(cuda),
+                        out, stream)
+        assert code == flash.OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(m, n, 3).astype(np.float64)
+        # FP32 products over n terms: |err| <= n u sum_j |M_ij| |rhs_j|
+        bound = n * 2.0 ** -23 * np.einsum("ij,ejc->eic", np.abs(Mf), np.abs(rhs).astype(np.float64))
+        assert np.all(np.abs(got - ref) <= bound), (n, m, np.abs(got - ref).max())
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < REL_TOL, (n, m, err)
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(cuda):
