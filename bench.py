@@ -661,21 +661,36 @@ def main():
         dist.barrier()
     launches = sim.launch_count() - launches0
     # kernel breakdown: a separate pass with CUDA events around every launch
-    # (kept out of the timed steps above), continuing the same rollout
+    # (kept out of the timed steps above).  It runs the same environments from
+    # the same state in a second scene with one lane, so that no launch
+    # overlaps another and a launch's time is its own; the main rollout does
+    # not advance.
     prof_steps = min(args.steps, 10)
-    sim.profile(True)
+    sim_p = flash.Sim(sc, solve=solve, warm=warm, lanes=1, eager=True, **mode_kw)
+    qs_, vs_ = sim.get_state()
+    sim_p.set_state(qs_, vs_)
+    s0 = args.warmup + args.steps
+    sim_p.set_poses(poses[s0], which=0)
+    first_p = 0
+    for x in scs:   # grasps held at s0 are re-activated
+        g = x.meta.get("grasp")
+        if g and any(k < s0 and r == 1 for k, r in g["schedule"].items()):
+            sim_p.grasp(np.ones(x.n_envs, np.int32), g["obstacle"], g["anchor"], g["radius"], first_p)
+        first_p += x.n_envs
+    sim_p.profile(True)
     prof_it = torch.zeros((), dtype=torch.int64, device=dev)
-    for i, s in enumerate(range(args.warmup + args.steps, args.warmup + args.steps + prof_steps)):
+    for i, s in enumerate(range(s0, s0 + prof_steps)):
         flush_buf.fill_(float(i))
-        sim.set_poses(poses[s + 1])
-        sim.apply_grasp_schedule(s)
-        sim.step(1)
-        prof_it += sim.stats()[0].sum()
+        sim_p.set_poses(poses[s + 1])
+        sim_p.apply_grasp_schedule(s)
+        sim_p.step(1)
+        prof_it += sim_p.stats()[0].sum()
     torch.cuda.synchronize()
     prof_mean_iters = prof_it.item() / (args.envs * prof_steps)
-    prof = sim.profile_read()
-    sim.profile(False)
-    n_steps += prof_steps            # the rollout continues from here
+    prof = sim_p.profile_read()
+    prof_contacts = float(sim_p.contacts()[0].float().mean().item())
+    sim_p.profile(False)
+    del sim_p
     frac_conv = n_conv / (args.envs * args.steps)
     mean_iters = n_it / (args.envs * args.steps)
     # 99th percentile of the per-environment iteration counts of the timed steps
@@ -721,17 +736,37 @@ def main():
         X, T = warmstart.collect(sim, sc, first, 6, dev)
         params, hist, held = warmstart.train(X, T, epochs=2, batch=4096, lr=1e-3)
         first += 6
-        ms_c, conv_c, _ = timed_steps(first)
-        sim.warmstart(params, flash.WARM_LEARNED, bounds=warmstart.input_range(X, T))
-        ms_l, conv_l, _ = timed_steps(first + args.steps)
+        # every arm runs the same steps from the same state (restored between
+        # arms: a step depends only on q, v and the obstacle poses)
+        q_w, v_w = (t.clone() for t in sim.get_state())
+
+        def arm(params_=None, use_dq=False):
+            if params_ is None:
+                sim.warmstart(None, flash.WARM_COLD)
+            else:
+                sim.warmstart(params_, flash.WARM_LEARNED, use_dq=use_dq, bounds=warmstart.input_range(X, T))
+            sim.set_state(q_w, v_w)
+            sim.set_poses(poses[first], which=0)
+            return timed_steps(first)
+
+        ms_c, conv_c, it_c = arm()
+        ms_l, conv_l, it_l = arm(params)
+        # the same network also moving each contact vertex to its predicted
+        # first iterate (the delta q^0 output)
+        ms_d, conv_d, it_d = arm(params, use_dq=True)
         sim.warmstart(None, flash.WARM_COLD)
         v_c, _ = aggregate(ms_c, conv_c / args.steps, world, dev)
         v_l, _ = aggregate(ms_l, conv_l / args.steps, world, dev)
-        warm_cmp = {"plain": {"value": v_c, "ms_per_step": ms_c, "frac_rncp_le_tol": conv_c / (args.envs * args.steps)},
-                    "learned": {"value": v_l, "ms_per_step": ms_l,
-                                "frac_rncp_le_tol": conv_l / (args.envs * args.steps)},
+        v_d, _ = aggregate(ms_d, conv_d / args.steps, world, dev)
+        ne = args.envs * args.steps
+        warm_cmp = {"plain": {"value": v_c, "ms_per_step": ms_c, "frac_rncp_le_tol": conv_c / ne,
+                              "mean_iters": it_c / ne},
+                    "learned": {"value": v_l, "ms_per_step": ms_l, "frac_rncp_le_tol": conv_l / ne,
+                                "mean_iters": it_l / ne},
+                    "learned_dq": {"value": v_d, "ms_per_step": ms_d, "frac_rncp_le_tol": conv_d / ne,
+                                   "mean_iters": it_d / ne},
                     "train": {"samples": int(X.shape[0]), "epochs": 2, "loss": hist, "held_out_loss": held},
-                    "unit": "converged env-steps/s", "note": "consecutive step windows of the same rollout"}
+                    "unit": "converged env-steps/s", "note": "the same steps from the same state for every arm"}
 
     # ---------------- roofline of the dominant kernel
     peaks = load_peaks()
@@ -776,26 +811,40 @@ def main():
                                          N * passes * prof_steps / max(d_n, 1))
     else:
         # data-movement roofline with the algorithmic bytes of each kernel per
-        # environment (n vertices, C contacts): local 72n + 36C, ncp 48n + 40C,
-        # begin 72n + 8C (read q, v; write q_t, q~, q, f; contact list), end 36n + 24C
-        C = float(sim.contacts()[0].float().mean().item())
+        # environment pass (n vertices, C contacts), each term a stream the
+        # kernel must move once:
+        #   local 72n + 36C: read q, w, dq, q~ and write q (5 x 12n), write the
+        #     residual as f16 hi + lo (12n); per contact its vertex and slot
+        #     (8), gamma (16) and q_t at its vertex (12)
+        #   ncp 48n + 40C: read q, w, q_t (36n), write J^T dgamma as f16 hi + lo
+        #     (12n); per contact vertex, slot, gamma read and written (40)
+        #   begin 72n + 8C: read q, v; write q_t, q~, q, f; the contact list
+        #   end 36n + 24C: read q, q_t, write v; the list kept for warm starts
+        C = prof_contacts
         per = {"local": (72, 36), "ncp": (48, 40), "begin": (72, 8), "end": (36, 24), "warm": (0, 64)}[dom]
         b = (per[0] * n_sum + per[1] * C * N) * passes * prof_steps
         peak = peaks.get("hbm_gbs", 6787.2)
         roof = {"bound": "hbm", "achieved": b / (d_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s", "kernel": dom,
+                "bytes_model": f"{per[0]} n + {per[1]} C per environment pass",
+                "env_passes": N * passes * prof_steps,
                 "algorithmic_bytes_per_launch": b / max(d_n, 1), "mean_contacts_per_env": C,
                 "peak_source": "measured HBM copy bandwidth",
                 "traffic": scaled_traffic(traffic_for(dom), N * passes * prof_steps / max(d_n, 1))}
-    roof["lanes"] = sim.lane_count()
-    roof["note_lanes"] = "launch times measured while the other lanes' kernels run" if sim.lane_count() > 1 else None
+    roof["lanes"] = 1
+    roof["note_lanes"] = "profiled in a one-lane copy of the scene: no launch overlaps another"
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_us"] = avg_s * 1e6
     roof["launches"] = d_n
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-12)}
                for k, v in prof.items()}
-    # step-level HBM fraction: minimal state traffic of a step (read q_t, v_t; write q, v)
-    step_bytes = 4 * n_sum * 3 * 4
+    # step-level HBM fraction with the minimal bytes of an environment step:
+    # read q_t, v_t and write q, v (48 n) and each contact's 16 bytes
+    C_step = float(sim.contacts()[0].float().mean().item())
+    step_bytes = 48 * n_sum + 16 * C_step * N
     step_hbm_frac = step_bytes / (ms_max / 1e3) / 1e9 / peaks.get("hbm_gbs", 6787.2)
+    roof["step"] = {"bytes": step_bytes, "bytes_model": "48 n + 16 C per environment step",
+                    "achieved": step_bytes / (ms_max / 1e3) / 1e9, "frac": step_hbm_frac,
+                    "ms_per_step": ms_max}
 
     if rank == 0:
         out = {

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2604_17513_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -49,20 +50,31 @@ def _gpu(cuda, sc, starts, s, n_steps, **kw):
     qg = sim.get_state()[0].cpu().numpy().reshape(sc.n_envs, sc.n_verts, 3)
     cnt, vert, obs, gam = (t.cpu().numpy() for t in sim.contacts())
     tri = sim.contact_tris().cpu().numpy()
+    _LAST["contacts"] = parity.gpu_contacts(sim)
     return sim, qg, cnt, vert, obs, tri, gam
 
 
-def _compare(sc, starts, s, qg, cnt, vert, obs, tri, pos_tol=POS_TOL, **kw):
+_LAST = {}
+
+
+def _compare(sc, starts, s, qg, cnt, vert, obs, tri, measured_bound=False, **kw):
     n_vt = n_ee = 0
     for e, (mesh, st) in starts.items():
-        ref = oracle.EnvState(st.q, st.v)
-        oracle.step(mesh, sc, e, s, ref, metric=2, **kw)
+        def step_fn(q, v, mesh=mesh, e=e):
+            x = oracle.EnvState(q, v)
+            oracle.step(mesh, sc, e, s, x, metric=2, **kw)
+            return x
+        ref = step_fn(st.q, st.v)
         c = int(cnt[e])
         assert c == len(ref.cvert), (e, c, len(ref.cvert))
         assert (vert[e, :c] == ref.cvert).all() and (obs[e, :c] == ref.cobs).all(), e
         assert (tri[e, :c] == ref.ctri).all(), e
         err = np.abs(qg[e] - ref.q).max()
-        assert err <= pos_tol, (e, err)
+        # ill-conditioned steps: 1e-5 m or twice what one FP32 ulp of noise on
+        # the oracle's own input moves the oracle, whichever is larger
+        moved = parity.oracle_spread(step_fn, st.q, st.v, ref)[0] if measured_bound and err > POS_TOL else 0.0
+        assert err <= max(POS_TOL, 2.0 * moved), (e, err, moved)
+        assert parity.impulse_check(_LAST["contacts"], e, ref, sc, e, s, err)[0]   # same lists
         n_vt += (ref.cobs == oracle.OVT_SLOT).sum()
         n_ee += (ref.cobs == oracle.OEE_SLOT).sum()
     return n_vt, n_ee
@@ -88,14 +100,15 @@ def test_bar_drop_landing_step(cuda, solve):
     rows (environment 0): 3e-9 m of noise on the oracle's own input moves
     its output by 4e-7 m (x130, against x3-x10 in the other environments
     and at the resting step), so FP32 and FP64 part by up to 6e-5 m there,
-    converged or not.  Lists agree exactly; positions are compared at
-    1e-4 m."""
+    converged or not.  Lists agree exactly; positions are compared at 1e-5 m
+    or twice what one FP32 ulp of noise on the oracle's own input moves the
+    oracle's result, whichever is larger (measured in the test)."""
     from paper_2604_17513_gb300 import flash
     sc = scenes.cloth_bar_drop(n_envs=4, steps=20)
     starts = _oracle_states(sc, range(sc.n_envs), 3)
     for kw in ({}, dict(mode=flash.MODE_TOL, tol=1e-6, k_cap=200)):
         sim, qg, cnt, vert, obs, tri, _ = _gpu(cuda, sc, starts, 3, 1, solve=solve, **kw)
-        _compare(sc, starts, 3, qg, cnt, vert, obs, tri, pos_tol=1e-4, **kw)
+        _compare(sc, starts, 3, qg, cnt, vert, obs, tri, measured_bound=True, **kw)
         if kw:
             it, r = sim.stats()
             assert r.max().item() <= 1e-6

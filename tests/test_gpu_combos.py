@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2604_17513_gb300 import scenes
 from test_gpu_raycast import _check as raycast_check
 
@@ -86,10 +87,13 @@ def test_grasp_with_self_collision(cuda):
         for k in range(s):
             oracle.step(mesh, sc, e, k, st, metric=2)
         q[e], v[e] = _f32(st.q), _f32(st.v)
-        ref = oracle.EnvState(q[e], v[e])
-        ref.attached = st.attached.copy()
-        oracle.step(mesh, sc, e, s, ref, metric=2)
-        refs[e] = ref
+        def step_fn(qq, vv, mesh=mesh, e=e, att=st.attached.copy()):
+            x = oracle.EnvState(qq, vv)
+            x.attached = att.copy()
+            oracle.step(mesh, sc, e, s, x, metric=2)
+            return x
+        ref = step_fn(q[e], v[e])
+        refs[e] = (ref, None)
     sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, metric=flash.METRIC_FULL)
     sim.set_state(torch.from_numpy(q.reshape(-1, 3).astype(np.float32)).to(cuda),
                   torch.from_numpy(v.reshape(-1, 3).astype(np.float32)).to(cuda))
@@ -102,11 +106,14 @@ def test_grasp_with_self_collision(cuda):
     qg = sim.get_state()[0].cpu().numpy().reshape(sc.n_envs, sc.n_verts, 3)
     cnt, vert, obs, _ = (t.cpu().numpy() for t in sim.contacts())
     tri = sim.contact_tris().cpu().numpy()
-    for e, ref in refs.items():
+    con = parity.gpu_contacts(sim)
+    for e, (ref, spread) in refs.items():
         c = int(cnt[e])
         assert c == len(ref.cvert) and (obs[e, :c] == ref.cobs).all() and (tri[e, :c] == ref.ctri).all()
         assert (ref.cobs == oracle.GRASP_SLOT).sum() == 1
-        assert np.abs(qg[e] - ref.q).max() <= POS_TOL
+        err = np.abs(qg[e] - ref.q).max()
+        assert err <= POS_TOL
+        assert parity.impulse_check(con, e, ref, sc, e, s, err)[0]   # same lists
 
 
 def test_self_collision_with_tet_groups(cuda):
@@ -132,9 +139,12 @@ def test_self_collision_with_tet_groups(cuda):
             oracle.step(mesh, sc, e, k, st, metric=2)
         n = sc.n_verts
         qs[si][:n], vs[si][:n] = _f32(st.q), _f32(st.v)
-        ref = oracle.EnvState(_f32(st.q), _f32(st.v))
-        oracle.step(mesh, sc, e, s, ref, metric=2)
-        refs.append(ref)
+        def step_fn(qq, vv, mesh=mesh, sc=sc):
+            x = oracle.EnvState(qq, vv)
+            oracle.step(mesh, sc, 0, s, x, metric=2)
+            return x
+        ref = step_fn(_f32(st.q), _f32(st.v))
+        refs.append((ref, None))
     sim = flash.Sim(scs, solve=flash.SOLVE_F16X3, metric=flash.METRIC_FULL)
     sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
                   torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
@@ -145,6 +155,9 @@ def test_self_collision_with_tet_groups(cuda):
     q = sim.get_state()[0].cpu().numpy()
     base = np.cumsum([0] + [sc.n_envs for sc in scs])
     off = sim.offsets
-    for (si, sc), ref in zip(picks, refs):
+    con = parity.gpu_contacts(sim)
+    for (si, sc), (ref, spread) in zip(picks, refs):
         g = base[si]
-        assert np.abs(q[off[g]:off[g + 1]] - ref.q).max() <= POS_TOL
+        err = np.abs(q[off[g]:off[g + 1]] - ref.q).max()
+        assert err <= POS_TOL
+        assert parity.impulse_check(con, g, ref, sc, 0, s, err)[0]   # same lists

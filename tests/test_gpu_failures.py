@@ -81,7 +81,9 @@ def test_contact_capacity_overflow_warns(cuda):
     s = 40
     for k in range(s):
         oracle.step(mesh, sc, 0, k, st)
-    assert len(st.cvert) > 2
+    nxt = oracle.EnvState(st.q, st.v)
+    oracle.step(mesh, sc, 0, s, nxt)
+    assert len(nxt.cvert) > 2
     for cap, want in ((2, flash.WOVERFLOW), (None, flash.OK)):
         sim = flash.Sim(sc, contact_cap=cap)
         _state(sim, sc, st.q[None], st.v[None], s)
@@ -92,7 +94,7 @@ def test_contact_capacity_overflow_warns(cuda):
             assert cnt[0] == 2
             assert b"capacity" in flash.lib().flash_last_error()
         else:
-            assert cnt[0] == len(st.cvert)
+            assert cnt[0] == len(nxt.cvert)
 
 
 def _five_planes_particle(steps=3):

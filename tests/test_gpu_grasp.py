@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2604_17513_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +60,7 @@ def _gpu_run(cuda, sc, starts, s, n_steps, activate, **kw):
     assert sim.status() == 0
     qg = sim.get_state()[0].cpu().numpy().reshape(sc.n_envs, sc.n_verts, 3)
     cnt, vert, obs, _ = (t.cpu().numpy() for t in sim.contacts())
+    _LAST["contacts"] = parity.gpu_contacts(sim)
     return sim, qg, cnt, vert, obs
 
 
@@ -67,13 +69,28 @@ def _compare(sc, starts, s, n_steps, metric_gpu, qg, cnt, vert, obs, warm="cold"
     for e, (mesh, st) in starts.items():
         ref = oracle.EnvState(st.q, st.v)
         ref.attached = st.attached.copy()
-        for k in range(s, s + n_steps):
+        for k in range(s, s + n_steps - 1):
             oracle.step(mesh, sc, e, k, ref, metric=om, warm=warm)
+        q1, v1, att, prev = ref.q.copy(), ref.v.copy(), ref.attached.copy(), ref
+        last = s + n_steps - 1
+
+        def step_fn(q, v, mesh=mesh, e=e, att=att, prev=prev):
+            x = oracle.EnvState(q, v)
+            x.attached = att.copy()
+            x.cvert, x.cobs, x.ctri, x.gamma = prev.cvert, prev.cobs, prev.ctri, prev.gamma
+            oracle.step(mesh, sc, e, last, x, metric=om, warm=warm)
+            return x
+        ref = step_fn(q1, v1)
         err = np.abs(qg[e] - ref.q).max()
         assert err <= POS_TOL, (e, err, len(ref.cvert))
         c = int(cnt[e])
         assert c == len(ref.cvert) and (vert[e, :c] == ref.cvert).all() and (obs[e, :c] == ref.cobs).all(), e
+        if not metric_gpu:   # full metric: GMRES iterates, impulses compared at convergence
+            parity.assert_impulses(_LAST["contacts"], e, ref, sc, e, last, err)
     return ref
+
+
+_LAST = {}
 
 
 @pytest.mark.parametrize("metric", [0, 1])

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2604_17513_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -49,21 +50,34 @@ def _gpu(cuda, sc, starts, s, n_steps, **kw):
     qg = sim.get_state()[0].cpu().numpy().reshape(sc.n_envs, sc.n_verts, 3)
     cnt, vert, obs, _ = (t.cpu().numpy() for t in sim.contacts())
     tri = sim.contact_tris().cpu().numpy()
+    _LAST["contacts"] = parity.gpu_contacts(sim)
     return sim, qg, cnt, vert, obs, tri
+
+
+_LAST = {}
 
 
 def _compare(sc, starts, s, n_steps, qg, cnt, vert, obs, tri, warm="cold"):
     n_self = n_ee = 0
     for e, (mesh, st) in starts.items():
         ref = oracle.EnvState(st.q, st.v)
-        for k in range(s, s + n_steps):
+        for k in range(s, s + n_steps - 1):
             oracle.step(mesh, sc, e, k, ref, metric=2, warm=warm)
+        q1, v1, prev, last = ref.q.copy(), ref.v.copy(), ref, s + n_steps - 1
+
+        def step_fn(q, v, mesh=mesh, e=e, prev=prev):
+            x = oracle.EnvState(q, v)
+            x.cvert, x.cobs, x.ctri, x.gamma = prev.cvert, prev.cobs, prev.ctri, prev.gamma
+            oracle.step(mesh, sc, e, last, x, metric=2, warm=warm)
+            return x
+        ref = step_fn(q1, v1)
         c = int(cnt[e])
         assert c == len(ref.cvert), (e, c, len(ref.cvert))
         assert (vert[e, :c] == ref.cvert).all() and (obs[e, :c] == ref.cobs).all(), e
         assert (tri[e, :c] == ref.ctri).all(), e
         err = np.abs(qg[e] - ref.q).max()
         assert err <= POS_TOL, (e, err)
+        assert parity.impulse_check(_LAST["contacts"], e, ref, sc, e, last, err)[0]   # same lists
         n_self += (ref.cobs == oracle.SELF_SLOT).sum()
         n_ee += (ref.cobs == oracle.EE_SLOT).sum()
     return n_self, n_ee
@@ -123,17 +137,22 @@ def test_self_collision_off_and_lite_rejected(cuda):
 def test_crossing_strips_edge_edge(cuda, s):
     """Eight pairs of crossing strips (no vertex over the other strip): the
     step in which the top strip reaches the bottom one (s = 3) and one with
-    it resting there (s = 6), in tolerance mode (r_ncp <= 1e-6); the rows
-    are edge-edge only and the lists agree exactly.  The scene is
-    ill-conditioned (a 20 cm strip balanced on a 1 cm support, its contact
-    rows at nearby crossing points): FP32 and FP64 Krylov solves part by up
-    to 1e-5 m already after one Newton iteration (4e-7 m on the stacked
-    cloths, whose test carries the 1e-5 m position bound), so converged
-    positions are compared at 5e-5 m here."""
+    it resting there (s = 6), in tolerance mode (r_ncp <= 1e-6 m on both
+    sides); the rows are edge-edge only and the lists agree exactly, and
+    the landing step's positions agree to 1e-5 m.  Resting, the 20 cm strip
+    balances on a 1 cm crossing: its rotation about the crossing is a soft
+    mode that a residual of 1e-6 m pins only to some 1e-5 m, and FP32 and
+    FP64 reach that residual on different paths (the GPU in up to 47
+    iterations, the oracle in fewer), so two valid states part by up to
+    1.3e-5 m there.  There each GPU state must itself be a solution by the
+    oracle's definition: the oracle's FP64 residual evaluated at the GPU's
+    positions and multipliers is within the tolerance (plus the FP32
+    resolution of the state), and it stays within 5e-5 m of the oracle's."""
     sc = scenes.strips_cross_drop(n_envs=8, steps=20)
     kw = dict(mode=1, tol=1e-6, k_cap=100)
     starts = _oracle_states(sc, range(sc.n_envs), s)
-    _, qg, cnt, vert, obs, tri = _gpu(cuda, sc, starts, s, 1, solve=0, **kw)
+    sim, qg, cnt, vert, obs, tri = _gpu(cuda, sc, starts, s, 1, solve=0, **kw)
+    con = parity.gpu_contacts(sim)
     n_ee = 0
     for e, (mesh, st) in starts.items():
         ref = oracle.EnvState(st.q, st.v)
@@ -142,7 +161,12 @@ def test_crossing_strips_edge_edge(cuda, s):
         assert c == len(ref.cvert) and (vert[e, :c] == ref.cvert).all() and (obs[e, :c] == ref.cobs).all(), e
         assert (tri[e, :c] == ref.ctri).all(), e
         err = np.abs(qg[e] - ref.q).max()
-        assert err <= 5e-5, (e, err)
+        if s == 3 or err <= POS_TOL:
+            assert err <= POS_TOL, (e, err)
+        else:
+            _, _, _, g = parity.env_rows(con, e)
+            r = oracle.residual(mesh, sc, e, s, st.q, qg[e].astype(np.float64), ref.cvert, ref.cobs, g, ref.ctri)
+            assert r <= 2e-6 and err <= 5e-5, (e, err, r)
         assert (ref.cobs == oracle.SELF_SLOT).sum() == 0
         n_ee += (ref.cobs == oracle.EE_SLOT).sum()
     assert n_ee >= 8 * 4

@@ -2,12 +2,15 @@
 
 Per-step parity from identical states: the oracle and the CUDA path start
 from the same float32-representable state and take one step; max vertex
-position error <= 1e-5 m in FP32 (the tolerance the target states).
+position error <= 1e-5 m in FP32 (the tolerance the target states), the same
+contact lists, and contact impulses within 1e-4 relative (with the FP32
+allowances that ``parity`` states).
 """
 import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2604_17513_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -108,6 +111,7 @@ def test_cloth_drop_one_step(cuda, s, solve):
     oracle.step(mesh, sc, 0, s, ref)
     err = np.abs(qg[0] - ref.q).max()
     assert err <= POS_TOL, (s, err, len(ref.cvert))
+    parity.assert_impulses(parity.gpu_contacts(sim), 0, ref, sc, 0, s, err)
     assert sim.status() == 0
 
 
@@ -128,11 +132,13 @@ def test_cloth_gripper_one_step_sampled(cuda, solve):
         q[e], v[e] = _f32(st.q), _f32(st.v)
     sim = _sim(sc, solve=solve)
     qg, _ = gpu_step_from(sim, sc, s, q, v)
+    con = parity.gpu_contacts(sim)
     for e in sample:
         ref = oracle.EnvState(q[e], v[e])
         oracle.step(meshes[e], sc, e, s, ref)
         err = np.abs(qg[e] - ref.q).max()
         assert err <= POS_TOL, (e, err)
+        parity.assert_impulses(con, e, ref, sc, e, s, err)
 
 
 def test_rest_stays_at_rest(cuda):
@@ -158,11 +164,13 @@ def test_tet_squeeze_one_step(cuda, solve):
         q[e], v[e] = _f32(st.q), _f32(st.v)
     sim = _sim(sc, solve=solve)
     qg, _ = gpu_step_from(sim, sc, s, q, v)
+    con = parity.gpu_contacts(sim)
     for e in range(sc.n_envs):
         ref = oracle.EnvState(q[e], v[e])
         oracle.step(meshes[e], sc, e, s, ref)
         err = np.abs(qg[e] - ref.q).max()
         assert err <= POS_TOL, (e, err, len(ref.cvert))
+        parity.assert_impulses(con, e, ref, sc, e, s, err)
 
 
 @pytest.mark.parametrize("theta", [0.2, 0.35])
@@ -217,7 +225,9 @@ def test_three_contacts_on_one_vertex(cuda):
     assert len(ref.cvert) == 3
     sim = _sim(sc)
     qg, _ = gpu_step_from(sim, sc, 0, sc.q0, sc.v0, n=3)
-    assert np.abs(qg[0] - ref.q).max() <= POS_TOL
+    err = np.abs(qg[0] - ref.q).max()
+    assert err <= POS_TOL
+    parity.assert_impulses(parity.gpu_contacts(sim), 0, ref, sc, 0, 2, err)
     assert np.abs(ref.q[0] - sc.q0[0, 0]).max() < 1e-4
 
 
@@ -231,7 +241,7 @@ def test_mixed_meshes_one_step(cuda, solve):
     from paper_2604_17513_gb300 import flash
     scs = scenes.mixed_batch(n_envs=8, steps=40, side_choices=(16, 20), tet_targets=(250, 500))
     s = 22
-    qs, vs, refs = [], [], []
+    qs, vs, refs, who = [], [], [], []
     for sc in scs:
         for e in range(sc.n_envs):
             mesh, st = oracle_state_at(sc, e, s)
@@ -241,6 +251,7 @@ def test_mixed_meshes_one_step(cuda, solve):
             ref = oracle.EnvState(q0, v0)
             oracle.step(mesh, sc, e, s, ref)
             refs.append(ref)
+            who.append((sc, e))
     assert sum(len(r.cvert) > 0 for r in refs) >= 4      # most environments touch something
     sim = flash.Sim(scs, solve=solve)
     sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
@@ -251,33 +262,35 @@ def test_mixed_meshes_one_step(cuda, solve):
     qg, _ = sim.get_state()
     qg = qg.cpu().numpy()
     off = sim.offsets
+    con = parity.gpu_contacts(sim)
     for i, ref in enumerate(refs):
         err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
         assert err <= POS_TOL, (i, err, len(ref.cvert))
+        parity.assert_impulses(con, i, ref, who[i][0], who[i][1], s, err)
 
 
 @pytest.mark.parametrize("solve", SOLVES)
 def test_mixed_meshes_tolerance_mode(cuda, solve):
     """Mode B on an uneven batch: every environment iterates until its NCP
-    residual is <= 1e-5 (cap 60).  Where the GPU and the oracle stop after the
-    same number of iterations the states agree within the position
-    tolerance; the stop decision itself may differ only where the residual
-    sits at the threshold."""
+    residual is <= 1e-5 (cap 60).  Every environment is compared with the
+    oracle at the GPU's own iteration count: where the oracle's stopping rule
+    stopped at the same count, with that run; where FP32 and FP64 crossed the
+    threshold at different iterations, with the oracle's fixed-count run of
+    as many iterations (the same iterate of the same iteration)."""
     import torch
     from paper_2604_17513_gb300 import flash
     scs = scenes.mixed_batch(n_envs=8, steps=40, side_choices=(16, 20), tet_targets=(250, 500))
     s = 22
-    qs, vs, refs = [], [], []
+    kw = dict(mode=1, tol=1e-5, k_min=1, k_cap=60)
+    qs, vs, starts = [], [], []
     for sc in scs:
         for e in range(sc.n_envs):
             mesh, st = oracle_state_at(sc, e, s)
             q0, v0 = _f32(st.q), _f32(st.v)
             qs.append(q0)
             vs.append(v0)
-            ref = oracle.EnvState(q0, v0)
-            oracle.step(mesh, sc, e, s, ref, mode=1, tol=1e-5, k_min=1, k_cap=60)
-            refs.append(ref)
-    sim = flash.Sim(scs, solve=solve, mode=1, tol=1e-5, k_min=1, k_cap=60)
+            starts.append((sc, e, mesh, q0, v0))
+    sim = flash.Sim(scs, solve=solve, **kw)
     sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
                   torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
     sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
@@ -287,17 +300,23 @@ def test_mixed_meshes_tolerance_mode(cuda, solve):
     it, r = it.cpu().numpy(), r.cpu().numpy()
     qg = sim.get_state()[0].cpu().numpy()
     off = sim.offsets
+    con = parity.gpu_contacts(sim)
     same = 0
-    for i, ref in enumerate(refs):
+    for i, (sc, e, mesh, q0, v0) in enumerate(starts):
         if it[i] < 60:
             assert r[i] <= 1e-5, (i, it[i], r[i])
-        if it[i] == ref.iters:
+        ref = oracle.EnvState(q0, v0)
+        oracle.step(mesh, sc, e, s, ref, **kw)
+        if ref.iters == it[i]:
             same += 1
-            err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
-            assert err <= POS_TOL, (i, err, it[i])
         else:
             assert abs(int(it[i]) - ref.iters) <= 2, (i, it[i], ref.iters)
-    assert same >= 6, (it, [r.iters for r in refs])
+            ref = oracle.EnvState(q0, v0)
+            oracle.step(mesh, sc, e, s, ref, k_max=int(it[i]))
+        err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
+        assert err <= POS_TOL, (i, err, it[i])
+        parity.assert_impulses(con, i, ref, sc, e, s, err)
+    assert same >= 6, (it,)
 
 
 @pytest.mark.parametrize("solve", SOLVES)
@@ -415,3 +434,102 @@ def test_global_apply_eigen_form(cuda, solve):
         ref = oracle.Mesh.from_scene(sc, e).solve(_f32(rhs[e]))
         err = np.abs(out[e] - ref).max() / np.abs(ref).max()
         assert err < (5e-5 if solve == 0 else 2e-4), (e, sc.stiff[e], err)
+
+
+@pytest.mark.parametrize("solve", SOLVES)
+def test_largest_mixed_templates_one_step(cuda, solve):
+    """The largest templates of the mixed batch: a 64x64 cloth (4096
+    vertices) and a 17x17x8-cube tet block (2916 vertices, above the eigen
+    form's limit, so its group has its own dense inverse), one fixed step in
+    contact.  The common start comes from the oracle run with 2 iterations
+    per step for the approach (any common state is a valid start)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    scs = scenes.mixed_batch(n_envs=2, steps=40, side_choices=(64,), tet_targets=(2900, 3000))
+    assert sorted(sc.n_verts for sc in scs) == [2916, 4096]
+    s = 24
+    qs, vs, refs = [], [], []
+    for sc in scs:
+        mesh = oracle.Mesh.from_scene(sc, 0)
+        st = oracle.EnvState(sc.q0[0], sc.v0[0])
+        for k in range(s):
+            oracle.step(mesh, sc, 0, k, st, k_max=2)
+        q0, v0 = _f32(st.q), _f32(st.v)
+        ref = oracle.EnvState(q0, v0)
+        oracle.step(mesh, sc, 0, s, ref)
+        assert len(ref.cvert) > 100
+        qs.append(q0)
+        vs.append(v0)
+        refs.append(ref)
+    sim = flash.Sim(scs, solve=solve)
+    sim.set_state(torch.from_numpy(np.concatenate(qs).astype(np.float32)).to(cuda),
+                  torch.from_numpy(np.concatenate(vs).astype(np.float32)).to(cuda))
+    sim.set_poses(flash.poses_tensor(scs, s, cuda), which=0)
+    sim.set_poses(flash.poses_tensor(scs, s + 1, cuda), which=1)
+    sim.step(1)
+    qg = sim.get_state()[0].cpu().numpy()
+    off = sim.offsets
+    con = parity.gpu_contacts(sim)
+    for i, (sc, ref) in enumerate(zip(scs, refs)):
+        err = np.abs(qg[off[i]:off[i + 1]] - ref.q).max()
+        assert err <= POS_TOL, (sc.name, err)
+        parity.assert_impulses(con, i, ref, sc, 0, s, err, what=sc.name)
+    assert sim.status() == 0
+
+
+def test_cloth_drop_rollout_invariants(cuda):
+    """The 16x16 cloth dropped on the sphere, 200 steps in tolerance mode
+    (r_ncp <= 1e-6, cap 200; the full metric, which reaches that residual in
+    ~8 iterations where the lite metric needs more than the cap on most
+    draped steps) on the GPU: trajectories of a chaotic drape are
+    not compared, the NCP's invariants are.  After every step, every contact
+    of every environment that converged satisfies lambda_n >= 0, gap >=
+    -1e-6 m, |h lambda_n gap| <= 1e-8 (or, for impact forces, h lambda_n
+    times the gap that the residual tolerance and an FP32 position resolve),
+    |lambda_t| <= mu
+    lambda_n (lambda_n and the cone within the residual's resolution
+    m tol / h^2), with gaps
+    evaluated in FP64 at the GPU's positions;
+    at least 95 % of env-steps converge."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_drop(n_envs=4, steps=200)
+    tol = 1e-6
+    sim = flash.Sim(sc, solve=flash.SOLVE_F16X3, mode=flash.MODE_TOL, tol=tol, k_cap=200,
+                    metric=flash.METRIC_FULL)
+    q0, v0 = flash.state_tensors(sc, cuda)
+    sim.set_state(q0, v0)
+    sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+    h, n = sc.h, sc.n_verts
+    conv = checked = 0
+    for s in range(200):
+        sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+        sim.step(1)
+        it, r = (t.cpu().numpy() for t in sim.stats())
+        q = sim.get_state()[0].cpu().numpy().astype(np.float64).reshape(sc.n_envs, n, 3)
+        cnt, vert, obs, _, gam = parity.gpu_contacts(sim)
+        for e in range(sc.n_envs):
+            if r[e] > tol:
+                continue
+            conv += 1
+            for j in range(int(cnt[e])):
+                vtx, o, g = int(vert[e, j]), int(obs[e, j]), gam[e, j].astype(np.float64)
+                sd, _ = oracle.sdf(sc.obs_type[e, o], sc.obs_dims[e, o], sc.poses[e, s + 1, o], q[e, vtx])
+                gap = sd - sc.thickness
+                m = sc.mass[vtx]
+                lam_n, lam_t = g[0] / h ** 2, np.linalg.norm(g[1:]) / h ** 2
+                # the residual bounds min(gap, y_n) by tol, y_n = gamma_n / m in metres
+                assert lam_n >= -m * tol / h ** 2 and gap >= -1e-6, (s, e, j, lam_n, gap)
+                # with lambda_n > 0 the FB residual bounds |gap| by tol, and an
+                # FP32 position and the FP32 distance evaluated from it resolve
+                # a gap to a few ulp(|x|): |h lambda_n gap| <= 1e-8, or
+                # h lambda_n times the larger of tol and 4 ulp(|x|) (impacts)
+                res = max(tol, 4.0 * float(np.spacing(np.float32(np.abs(q[e, vtx]).max()))))
+                assert abs(h * lam_n * gap) <= max(1e-8, h * lam_n * res), (s, e, j, lam_n, gap)
+                # sliding rows sit on the cone: FP32 rounding of the disk
+                # projection and of the frame change between the last
+                # linearisation and the end state, relative 1e-5
+                assert lam_t <= sc.mu[e] * lam_n * (1 + 1e-5) + m * tol / h ** 2, (s, e, j, lam_t, lam_n)
+                checked += 1
+    assert sim.status() == 0
+    assert conv >= 0.95 * 200 * sc.n_envs and checked > 1000, (conv, checked)
