@@ -35,6 +35,7 @@ DEFAULT_ENVS = {"cloth_gripper": 1024, "cloth_grasp": 1024, "cloth_stack": 1024,
                 "tet_squeeze": 4096, "mixed": 2048, "towel_render": 128}
 RENDER_METRIC = ("depth frames/s on 1 GB300: batched ray casting of the 32,761-vertex towel, 640x480 depth + "
                  "instance segmentation + point cloud per environment")
+WARM_SAMPLES = 1_000_000   # contact rows the warm-start network trains on
 CPU_SAMPLE = {"cloth_gripper": (6, 12), "cloth_grasp": (2, 6), "cloth_stack": (16, 20), "cloth_bar": (16, 20),
               "tet_squeeze": (24, 40)}   # (envs, steps), 10-30 s
 
@@ -70,6 +71,8 @@ def parse():
                    help="launch every step kernel by kernel (the host stops the tolerance loop) instead of a graph")
     p.add_argument("--no-warm-compare", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--grouped", default="auto", choices=["auto", "on", "off"],
+                   help="one tensor-core launch for all mesh templates of a lane (auto: the faster, timed at setup)")
     p.add_argument("--clock-log", default=None,
                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     args = p.parse_args()
@@ -598,13 +601,14 @@ def main():
 
     solve = {"auto": flash.SOLVE_F16X3, "f32": flash.SOLVE_F32, "f16x3": flash.SOLVE_F16X3}[args.solve]
     n_steps = args.warmup + args.steps
-    total_steps = n_steps + 3 * args.steps + 8 + 10   # + the profiled pass (at most 10 steps)
+    total_steps = n_steps + 3 * args.steps + 14 + 10   # + warm-start data steps and the profiled pass
     args.envs = args.envs or DEFAULT_ENVS[args.workload]
     sc, workload = workload_scene(args, args.envs, total_steps, rank)
     mode_kw = {"mode": flash.MODE_TOL, "tol": TOL, "k_min": 1, "k_cap": args.k_cap} if args.mode == "tol" else {}
     if args.metric == "full":
         mode_kw.update(metric=flash.METRIC_FULL, lin_iters=args.lin_iters)
     warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
+    mode_kw["grouped"] = {"auto": flash.GROUPED_AUTO, "on": flash.GROUPED_ON, "off": flash.GROUPED_OFF}[args.grouped]
     try:
         sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, eager=args.eager, **mode_kw)
     except flash.FlashError:
@@ -666,7 +670,8 @@ def main():
     # overlaps another and a launch's time is its own; the main rollout does
     # not advance.
     prof_steps = min(args.steps, 10)
-    sim_p = flash.Sim(sc, solve=solve, warm=warm, lanes=1, eager=True, **mode_kw)
+    kw_p = dict(mode_kw, grouped=flash.GROUPED_ON if sim.grouped_solve() else flash.GROUPED_OFF)
+    sim_p = flash.Sim(sc, solve=solve, warm=warm, lanes=1, eager=True, **kw_p)
     qs_, vs_ = sim.get_state()
     sim_p.set_state(qs_, vs_)
     s0 = args.warmup + args.steps
@@ -730,12 +735,21 @@ def main():
 
     # ---------------- plain vs learned warm start (same fixed k, same residual test)
     warm_cmp = None
-    if not args.no_warm_compare and args.workload == "cloth_gripper":
+    if not args.no_warm_compare and args.workload in ("cloth_gripper", "mixed"):
         from paper_2604_17513_gb300 import warmstart
         first = n_steps + args.steps
-        X, T = warmstart.collect(sim, sc, first, 6, dev)
+        # training data: the contact rows of the rollout's own converged steps,
+        # step by step until there are WARM_SAMPLES of them (at most 12 steps)
+        xs, ts, n_rows, n_coll = [], [], 0, 0
+        while n_rows < WARM_SAMPLES and n_coll < 12:
+            X1, T1 = warmstart.collect(sim, sc, first + n_coll, 1, dev)
+            xs.append(X1)
+            ts.append(T1)
+            n_rows += int(warmstart.usable(X1, T1)[0].shape[0])
+            n_coll += 1
+        X, T = torch.cat(xs), torch.cat(ts)
         params, hist, held = warmstart.train(X, T, epochs=2, batch=4096, lr=1e-3)
-        first += 6
+        first += n_coll
         # every arm runs the same steps from the same state (restored between
         # arms: a step depends only on q, v and the obstacle poses)
         q_w, v_w = (t.clone() for t in sim.get_state())
@@ -765,7 +779,8 @@ def main():
                                 "mean_iters": it_l / ne},
                     "learned_dq": {"value": v_d, "ms_per_step": ms_d, "frac_rncp_le_tol": conv_d / ne,
                                    "mean_iters": it_d / ne},
-                    "train": {"samples": int(X.shape[0]), "epochs": 2, "loss": hist, "held_out_loss": held},
+                    "train": {"samples": int(X.shape[0]), "usable_samples": n_rows, "collect_steps": n_coll,
+                              "epochs": 2, "loss": hist, "held_out_loss": held},
                     "unit": "converged env-steps/s", "note": "the same steps from the same state for every arm"}
 
     # ---------------- roofline of the dominant kernel
@@ -858,7 +873,8 @@ def main():
                        "solve": "f16x3 tcgen05" if solve == flash.SOLVE_F16X3 else "f32 simt",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
-                       "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths()))},
+                       "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths())),
+                       "grouped_solve": sim.grouped_solve()},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
             "p99_iters": p99_iters,
             "status": status, "warm_start": warm_cmp,

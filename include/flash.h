@@ -139,7 +139,15 @@ typedef int32_t flash_status;
  * cloth edge was on at the step start; gap = distance between the lines -
  * thickness.  The first FLASH_OFEAT_MAX rows of each kind per vertex are
  * kept, in feature order.  The paper describes none; this is the library's
- * reading. */
+ * reading.
+ * grouped_solve (tensor-core solve, scenes of several mesh templates and
+ * lanes): a lane applies the dense inverses of all its templates in one
+ * launch (FLASH_GROUPED_ON), one launch per template (FLASH_GROUPED_OFF), or
+ * whichever of the two is faster when the scene is finalised
+ * (FLASH_GROUPED_AUTO, 0).  Results do not depend on it. */
+#define FLASH_GROUPED_AUTO 0
+#define FLASH_GROUPED_OFF 1
+#define FLASH_GROUPED_ON 2
 typedef struct {
   double h;
   double gravity[3];
@@ -157,6 +165,7 @@ typedef struct {
   int32_t lin_iters;
   int32_t self_collide;
   int32_t obstacle_features;
+  int32_t grouped_solve;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -372,6 +381,9 @@ int32_t flash_lane_count(const flash_scene *s);
  * into the host array out; returns how many ranges there are (0 on the
  * CUDA-core path or before finalize). */
 int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out);
+/* 1 if the scene's lanes apply their dense inverses in one grouped launch
+ * (flash_scene_desc.grouped_solve), else 0; 0 before finalize. */
+int32_t flash_grouped_solve(const flash_scene *s);
 
 /* Learned warm start (the paper has no learned component; the network
  * predicts the initial multipliers gamma^0 and the first iterate at each

@@ -575,15 +575,83 @@ cudaError_t join(flash_scene *s, cudaStream_t st) {
   return e;
 }
 
-// One lane's global applies of a phase, out_g = A_g^-1 in_g over its ranges.
+// One lane's global applies of a phase, out_g = A_g^-1 in_g over its ranges;
+// kind names the output (0: w, 1: dq, 2: fm_u) for the grouped launch, which
+// covers the lane's dense-inverse ranges when the scene chose it.
 template <typename In, typename Out>
-cudaError_t apply_lane(flash_scene *s, const Lane &L, cudaStream_t st, In in, Out out) {
+cudaError_t apply_lane(flash_scene *s, const Lane &L, cudaStream_t st, In in, Out out, int kind) {
   cudaError_t e = cudaSuccess;
+  const bool grouped = s->grouped && L.ga.n > 0 && use_tc(s);
+  if (grouped)
+    e = timed(s, FLASH_KIND_SOLVE, st, [&] {
+      return gemm_tc_grouped(L.ga.probs, L.ga.n, L.ga.tiles, L.ga.outs[kind], s->done, s->status, st);
+    });
   for (size_t i = 0; i < L.ranges.size() && e == cudaSuccess; i++) {
+    if (grouped && std::find(L.ga.ranges.begin(), L.ga.ranges.end(), (int)i) != L.ga.ranges.end()) continue;
     const LaneRange &r = L.ranges[i];
     Group &g = s->groups[r.group];
     e = apply_inverse(s, g, in(g), out(g), st, r.l0, r.l1, r.tc_bn);
   }
+  return e;
+}
+
+// The grouped apply of every lane with two or more dense-inverse ranges:
+// problem tables (tensor maps encoded once) and per-kind output tables.
+flash_status build_grouped(flash_scene *s) {
+  for (Lane &L : s->lanes) {
+    std::vector<int> idx;
+    for (size_t i = 0; i < L.ranges.size(); i++)
+      if (!s->groups[L.ranges[i].group].eig) idx.push_back((int)i);
+    if (idx.size() < 2) continue;
+    const size_t pb = gemm_problem_bytes();
+    std::vector<unsigned char> host(pb * idx.size());
+    std::vector<float *> outs[3];
+    int tiles = 0;
+    for (size_t k = 0; k < idx.size(); k++) {
+      const LaneRange &r = L.ranges[idx[k]];
+      Group &g = s->groups[r.group];
+      const int t = gemm_problem(host.data() + k * pb, g, g.inv, 3 * r.l0, 3 * r.l1, tiles);
+      if (t < 0) return fail(FLASH_ECUDA, "grouped apply: tensor map encoding failed");
+      tiles += t;
+      outs[0].push_back(g.w);
+      outs[1].push_back(g.dq);
+      outs[2].push_back(g.fm_u);
+    }
+    unsigned char *d = nullptr;
+    FLASH_CUDA_TRY(upload(s, &d, host));
+    L.ga.probs = d;
+    for (int kd = 0; kd < 3; kd++) FLASH_CUDA_TRY(upload(s, &L.ga.outs[kd], outs[kd]));
+    L.ga.n = (int)idx.size();
+    L.ga.tiles = tiles;
+    L.ga.ranges = idx;
+  }
+  return FLASH_OK;
+}
+
+// Device time of one phase of every lane's applies running concurrently
+// (the best of three runs after a warm-up run).
+cudaError_t apply_phase_ms(flash_scene *s, cudaStream_t st, float *best_ms) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  float t = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = fork(s, st);
+    for (const Lane &L : s->lanes)
+      if (e == cudaSuccess)
+        e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; }, 0);
+    if (e == cudaSuccess) e = join(s, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) t = std::min(t, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_ms = t;
   return e;
 }
 
@@ -639,7 +707,8 @@ const char *flash_last_error(void) { return g_error.c_str(); }
 
 flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out) {
   if (!desc || !out) return fail(FLASH_EINVAL, "null argument");
-  if (!(desc->h > 0) || desc->k_max < 0 || desc->k_cap < 0 || desc->k_min < 0 || desc->contact_cap < 0)
+  if (!(desc->h > 0) || desc->k_max < 0 || desc->k_cap < 0 || desc->k_min < 0 || desc->contact_cap < 0 ||
+      desc->grouped_solve < FLASH_GROUPED_AUTO || desc->grouped_solve > FLASH_GROUPED_ON)
     return fail(FLASH_EINVAL, "invalid scene descriptor");
   if (desc->mode != FLASH_MODE_FIXED && desc->mode != FLASH_MODE_TOL) return fail(FLASH_EINVAL, "invalid mode");
   if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3) return fail(FLASH_EINVAL, "invalid solve");
@@ -873,7 +942,7 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
           if (e == cudaSuccess) e = fork(s, st);
           for (const Lane &L : s->lanes)
             if (e == cudaSuccess)
-              e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+              e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; }, 0);
           if (e == cudaSuccess) e = join(s, st);
           if (e == cudaSuccess) e = cudaEventRecord(e1, st);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -905,6 +974,24 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
         for (LaneRange &r : L.ranges) r.tc_bn = chosen[k++];
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      s->launches = launches0;
+    }
+    // lanes of several mesh templates: one grouped launch for all their
+    // dense applies, kept if it beats the per-range launches
+    const flash_status gs = build_grouped(s);
+    if (gs != FLASH_OK) return gs;
+    bool any = false;
+    for (const Lane &L : s->lanes) any = any || L.ga.n > 0;
+    if (any && s->d.grouped_solve == FLASH_GROUPED_ON) {
+      s->grouped = true;
+    } else if (any && s->d.grouped_solve == FLASH_GROUPED_AUTO) {
+      const int64_t launches0 = s->launches;
+      float t_off = 0.f, t_on = 0.f;
+      s->grouped = false;
+      FLASH_CUDA_TRY(apply_phase_ms(s, st, &t_off));
+      s->grouped = true;
+      FLASH_CUDA_TRY(apply_phase_ms(s, st, &t_on));
+      s->grouped = t_on < t_off;
       s->launches = launches0;
     }
   }
@@ -1074,7 +1161,7 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
     // w = A^-1 r ;  NCP ;  dq = A^-1 J^T dgamma  (q^k = q^{k-1} + w + dq, applied by the next local pass)
     cudaError_t e = cudaSuccess;
     for (const Lane &L : s->lanes)
-      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; });
+      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.r; }, [](Group &g) { return g.w; }, 0);
     if (s->d.metric == FLASH_METRIC_FULL) {
       // Newton step on the full metric: GMRES, one A^-1 application per step
       for (const Lane &L : s->lanes)
@@ -1087,7 +1174,7 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
                       [&] { return launch_fm_scatter_lane(s, L, a, j, tc, lane_stream(L, st)); });
         for (const Lane &L : s->lanes)
           if (e == cudaSuccess)
-            e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.fm_u; });
+            e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.fm_u; }, 2);
         for (const Lane &L : s->lanes)
           if (e == cudaSuccess)
             e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_fm_gather_lane(s, L, a, j, lane_stream(L, st)); });
@@ -1101,7 +1188,7 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
         e = timed(s, FLASH_KIND_NCP, lane_stream(L, st), [&] { return launch_ncp_lane(s, L, a, tc, lane_stream(L, st)); });
     }
     for (const Lane &L : s->lanes)
-      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.dq; });
+      if (e == cudaSuccess) e = apply_lane(s, L, lane_stream(L, st), [](Group &g) { return g.f; }, [](Group &g) { return g.dq; }, 1);
     return e;
   };
   auto end = [&]() -> cudaError_t {
@@ -1396,6 +1483,8 @@ int64_t flash_launch_count(const flash_scene *s) {
 }
 
 int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int32_t)s->lanes.size() : 0; }
+
+int32_t flash_grouped_solve(const flash_scene *s) { return s && s->finalized && s->grouped ? 1 : 0; }
 
 int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out) {
   if (!s || !s->finalized || !use_tc(s)) return 0;

@@ -27,6 +27,7 @@ constexpr int kMaxPerVertex = 4; // contacts solved jointly on one vertex
 constexpr int kMaxBeginSmem = 160 * 1024;   // self-contact triangle and edge boxes in the begin kernel
 constexpr int kFmW = 8;          // floats per self-contact row of the full metric's fm_w
 constexpr float kDamp = 1e-6f;   // Newton-step damping of the per-vertex block
+constexpr int kBigMesh = 2048;   // meshes with more vertices get 1024-thread local-pass CTAs
 
 struct MeshTemplate {
   int type = 0, n = 0, E = 0;
@@ -126,6 +127,7 @@ namespace flash {
 // environment map[b].y of group map[b].x (a row of the scene's group table).
 struct Batch {
   int vpe = 0;            // vertices per element of its groups (local pass only)
+  int threads = 512;      // local pass: threads per CTA (1024 for meshes above kBigMesh vertices)
   int blocks = 0;         // CTAs, one per environment
   size_t smem = 0;        // dynamic shared memory per CTA: the largest need of its groups
   int2 *map = nullptr;    // device [blocks]
@@ -138,6 +140,15 @@ struct LaneRange {
 // A lane: a partition of the environments stepped on its own stream, so
 // that the wave tails of one lane's kernels overlap other lanes' work.
 // Results do not depend on the partition.
+// Every dense-inverse apply of a lane in one tensor-core launch (grouped
+// apply): problem table (device) and, per output kind (0: w, 1: dq, 2: the
+// full metric's fm_u), the output buffer of each problem (device).
+struct GroupedApply {
+  void *probs = nullptr;
+  int n = 0, tiles = 0;
+  float **outs[3] = {nullptr, nullptr, nullptr};
+  std::vector<int> ranges;      // the lane's ranges it covers
+};
 struct Lane {
   cudaStream_t st = nullptr;    // null: the caller's stream (single-lane scenes)
   cudaEvent_t done = nullptr;   // join event
@@ -146,6 +157,7 @@ struct Lane {
   Batch all;                    // begin / NCP / end over the lane's environments
   std::vector<Batch> local;     // local pass, by element type and shared-memory class
   size_t ncp_smem_tc = 0;
+  GroupedApply ga;
 };
 }  // namespace flash
 
@@ -208,6 +220,7 @@ struct flash_scene {
   cudaStream_t body_st = nullptr;   // captures the tolerance loop's body
   bool capturing = false;       // step_once is being captured
   bool graph_stale = true;      // a setting that changes the step's launches has changed
+  bool grouped = false;         // lanes apply their dense inverses in one grouped launch (chosen at finalize)
 };
 
 namespace flash {
@@ -315,6 +328,12 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                     const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0);
 bool tc_available();
+// grouped apply (one launch over several groups' dense applies, tile width kGroupedBN)
+constexpr int kGroupedBN = 64;
+size_t gemm_problem_bytes();
+int gemm_problem(void *dst, const Group &g, const SolveMat &M, int c0, int c1, int tile0);
+cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *const *outs, const int *done, int *status,
+                            cudaStream_t st);
 // time the tile widths on columns [c0, c1) of the group; fastest in *bn
 cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn);
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);

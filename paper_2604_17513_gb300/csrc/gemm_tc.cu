@@ -26,6 +26,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "flash_internal.cuh"
 
 namespace flash {
@@ -161,13 +163,15 @@ __device__ __forceinline__ void store_cols(uint32_t taddr, float *o, const float
   }
 }
 
+// One 128 x BN output tile at rows m0.., columns j0.. (tensor maps in
+// parameter or global memory).
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-              float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
-              const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int c_begin,
-              int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
+__device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensorMap *pAl, const CUtensorMap *pBh,
+                                          const CUtensorMap *pBl, float *__restrict__ out,
+                                          const float *__restrict__ W, const float *__restrict__ rscale,
+                                          const int *__restrict__ done, const int *__restrict__ genv, int *status,
+                                          int n_pad, int m0, int j0, int cols, float a_unscale, int mode,
+                                          const float *__restrict__ lam, const float *__restrict__ kenv) {
   using Cfg = TileCfg<BN>;
   constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, TILE_B = Cfg::TILE_B;
   extern __shared__ uint8_t smem_raw[];
@@ -178,8 +182,6 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ float col_k[BN];
   __shared__ int col_live[BN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // columns [c_begin, cols): tile x starts at c_begin + x BN
-  const int m0 = blockIdx.y * BM, j0 = c_begin + blockIdx.x * BN;
   const int KB = n_pad / BK;
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
@@ -218,10 +220,10 @@ __global__ void __launch_bounds__(128, 1)
       uint8_t *st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full_bar[s], STAGE_BYTES);
       const int k0 = kb * BK;
-      tma_load_2d(st, &tmAh, &full_bar[s], k0, m0);
-      tma_load_2d(st + TILE_A, &tmAl, &full_bar[s], k0, m0);
-      tma_load_2d(st + 2 * TILE_A, &tmBh, &full_bar[s], k0, j0);
-      tma_load_2d(st + 2 * TILE_A + TILE_B, &tmBl, &full_bar[s], k0, j0);
+      tma_load_2d(st, pAh, &full_bar[s], k0, m0);
+      tma_load_2d(st + TILE_A, pAl, &full_bar[s], k0, m0);
+      tma_load_2d(st + 2 * TILE_A, pBh, &full_bar[s], k0, j0);
+      tma_load_2d(st + 2 * TILE_A + TILE_B, pBl, &full_bar[s], k0, j0);
     }
     // drain: wait until every stage this thread armed has landed (bounded)
     for (int t = max(0, kb - STAGES); t < kb; t++) mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1);
@@ -282,6 +284,45 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 2) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
   }
+}
+
+// One group's apply: tile (x, y) covers rows 128 y.. and columns
+// c_begin + BN x .. of [c_begin, cols).
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+              float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
+              const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int c_begin,
+              int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
+  gemm_tile<BN>(&tmAh, &tmAl, &tmBh, &tmBl, out, W, rscale, done, genv, status, n_pad, blockIdx.y * BM,
+                c_begin + blockIdx.x * BN, cols, a_unscale, mode, lam, kenv);
+}
+
+// One apply of several groups in one launch (uneven batches: every mesh
+// template of a lane at once).  Problem p owns tiles [tile0_p, tile0_{p+1});
+// its tensor maps live in global memory, encoded once when the scene is
+// finalised.  Plain A^-1 applies only (epilogue mode 0).
+struct GemmProblem {
+  CUtensorMap ah, al, bh, bl;   // 64-byte aligned, 128 bytes each
+  const float *rscale;
+  const int *genv;
+  int n_pad, c_begin, cols, tiles_x, tile0;
+  float a_unscale;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc_grouped(const GemmProblem *__restrict__ P, int nprob, float *const *__restrict__ outs,
+                      const int *__restrict__ done, int *status) {
+  const int t = blockIdx.x;
+  int p = 0;
+  while (p + 1 < nprob && P[p + 1].tile0 <= t) p++;
+  const GemmProblem &pr = P[p];
+  const int local = t - pr.tile0;
+  const int tx = local % pr.tiles_x, ty = local / pr.tiles_x;
+  gemm_tile<BN>(&pr.ah, &pr.al, &pr.bh, &pr.bl, outs[p], nullptr, pr.rscale, done, pr.genv, status, pr.n_pad,
+                ty * BM, pr.c_begin + tx * BN, pr.cols, pr.a_unscale, 0, nullptr, nullptr);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -358,6 +399,46 @@ cudaError_t launch_bn(int bn, const Group &g, const SolveMat &M, float *out, con
 }
 
 }  // namespace
+
+size_t gemm_problem_bytes() { return sizeof(GemmProblem); }
+
+// Fill one grouped-apply problem (host memory of gemm_problem_bytes()) for
+// columns [c0, c1) of group g with matrix M; its tiles start at tile0.
+// Returns the problem's tile count, or -1 if the tensor maps cannot be made.
+int gemm_problem(void *dst, const Group &g, const SolveMat &M, int c0, int c1, int tile0) {
+  if (g.n_pad % BM != 0 || g.n_pad % BK != 0 || c1 <= c0) return -1;
+  GemmProblem pr;
+  std::memset(&pr, 0, sizeof(pr));
+  if (!make_map(&pr.ah, M.hi, g.n_pad, g.n_pad, BM) || !make_map(&pr.al, M.lo, g.n_pad, g.n_pad, BM) ||
+      !make_map(&pr.bh, g.rh, g.n_pad, g.cols_pad, kGroupedBN) || !make_map(&pr.bl, g.rl, g.n_pad, g.cols_pad, kGroupedBN))
+    return -1;
+  pr.rscale = g.rscale;
+  pr.genv = g.genv;
+  pr.n_pad = g.n_pad;
+  pr.c_begin = c0;
+  pr.cols = c1;
+  pr.tiles_x = (c1 - c0 + kGroupedBN - 1) / kGroupedBN;
+  pr.tile0 = tile0;
+  pr.a_unscale = ldexpf(1.f, -M.exp);
+  std::memcpy(dst, &pr, sizeof(pr));
+  return pr.tiles_x * (g.n_pad / BM);
+}
+
+cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *const *outs, const int *done, int *status,
+                            cudaStream_t st) {
+  using Cfg = TileCfg<kGroupedBN>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_grouped<kGroupedBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nprob <= 0 || tiles <= 0) return cudaSuccess;
+  k_gemm_tc_grouped<kGroupedBN><<<tiles, 128, Cfg::SMEM_BYTES, st>>>(static_cast<const GemmProblem *>(probs), nprob,
+                                                                      outs, done, status);
+  return cudaGetLastError();
+}
 
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                     const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn) {

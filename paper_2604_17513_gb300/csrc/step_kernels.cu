@@ -1870,8 +1870,8 @@ __global__ void __launch_bounds__(256) k_begin_tab(const GroupView *__restrict__
   const int2 b = map[blockIdx.x];
   begin_body<SELF>(tab[b.x], b.y, V, a, boxes);
 }
-template <int VPE, bool SELF>
-__global__ void __launch_bounds__(512, 2) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
+template <int VPE, bool SELF, int NT = 512>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_local_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
                                                       EnvView V, StepArgs a, int k, int residual_only, int tc,
                                                       int pending) {
   const int2 b = map[blockIdx.x];
@@ -2129,6 +2129,12 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_local_tab<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<3, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<3, true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<4, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_begin_tab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBeginSmem);
@@ -2272,13 +2278,15 @@ cudaError_t build_lanes(flash_scene *s, int n_lanes) {
     if ((e = upload_owned(s, &L.all.map, all)) != cudaSuccess) return e;
     L.ncp_smem_tc = sizeof(float) * 3 * (size_t)nmax;
     for (int vpe = 3; vpe <= 4; vpe++)
+      for (int big = 1; big >= 0; big--)
       for (int cls = 4; cls >= 1; cls--) {
         Batch b;
         b.vpe = vpe;
+        b.threads = big ? 1024 : 512;
         std::vector<int2> m;
         for (const LaneRange &r : L.ranges) {
           const Group &g = s->groups[r.group];
-          if (g.vpe != vpe || local_class(g.smem_local) != cls) continue;
+          if (g.vpe != vpe || local_class(g.smem_local) != cls || (g.n > kBigMesh) != (big == 1)) continue;
           for (int l = r.l0; l < r.l1; l++) m.push_back(make_int2(r.group, l));
           b.smem = std::max(b.smem, g.smem_local);
         }
@@ -2313,13 +2321,24 @@ cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArg
   const int pending = k > 1;
   const GroupView *tab = (const GroupView *)s->gtab;
   for (const Batch &b : L.local) {
-    if (b.vpe == 3)
-      if (s->d.self_collide || s->d.obstacle_features)
-        k_local_tab<3, true><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    const bool self = s->d.self_collide || s->d.obstacle_features;
+    if (b.threads == 1024) {
+      if (b.vpe == 3 && self)
+        k_local_tab<3, true, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
+                                                                   pending);
+      else if (b.vpe == 3)
+        k_local_tab<3, false, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
+                                                                    pending);
       else
-        k_local_tab<3, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
-    else
+        k_local_tab<4, false, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
+                                                                    pending);
+    } else if (b.vpe == 3 && self) {
+      k_local_tab<3, true><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    } else if (b.vpe == 3) {
+      k_local_tab<3, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    } else {
       k_local_tab<4, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*launched;

@@ -33,6 +33,7 @@ MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3 = 0, 1
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
+GROUPED_AUTO, GROUPED_OFF, GROUPED_ON = 0, 1, 2
 
 
 class FlashError(RuntimeError):
@@ -53,7 +54,8 @@ class SceneDesc(C.Structure):
                 ("thickness", C.c_double), ("margin", C.c_double), ("k_max", C.c_int32), ("k_min", C.c_int32),
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
-                ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32)]
+                ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32),
+                ("grouped_solve", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -117,6 +119,8 @@ def lib():
         L.flash_lane_count.restype = i32
         L.flash_tile_widths.argtypes = [vp, C.POINTER(i32), i32]
         L.flash_tile_widths.restype = i32
+        L.flash_grouped_solve.argtypes = [vp]
+        L.flash_grouped_solve.restype = i32
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
         L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]
@@ -164,7 +168,7 @@ class Sim:
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
                  warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
-                 self_collision=None, obstacle_features=None):
+                 self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -199,6 +203,7 @@ class Sim:
         d.eager = 1 if eager else 0
         d.metric = metric
         d.lin_iters = lin_iters
+        d.grouped_solve = grouped
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))
@@ -349,6 +354,10 @@ class Sim:
 
     def lane_count(self):
         return lib().flash_lane_count(self._h)
+
+    def grouped_solve(self):
+        """True if the lanes apply their dense inverses in one grouped launch."""
+        return bool(lib().flash_grouped_solve(self._h))
 
     def tile_widths(self):
         """Autotuned tensor-core tile width of each lane's column range."""
