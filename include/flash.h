@@ -66,6 +66,8 @@ typedef int32_t flash_status;
 
 #define FLASH_SOLVE_F32 0    /* global solve: FP32 dense apply on the CUDA cores */
 #define FLASH_SOLVE_F16X3 1  /* global solve: tcgen05 f16 hi/lo split, FP32 accumulate */
+#define FLASH_SOLVE_BF16R 2  /* global solve: tcgen05 bf16, FP32 accumulate, refine_steps steps of
+                                iterative refinement with the residual rhs - A w in FP32 (tet meshes) */
 
 #define FLASH_METRIC_LITE 0  /* contact metric Z = J M^-1 J^T + E (Sec. IV-B.1), per-vertex blocks */
 #define FLASH_METRIC_FULL 1  /* Z = J A^-1 J^T + E (Sec. III-C), lin_iters steps of GMRES per Newton step */
@@ -144,7 +146,12 @@ typedef int32_t flash_status;
  * lanes): a lane applies the dense inverses of all its templates in one
  * launch (FLASH_GROUPED_ON), one launch per template (FLASH_GROUPED_OFF), or
  * whichever of the two is faster when the scene is finalised
- * (FLASH_GROUPED_AUTO, 0).  Results do not depend on it. */
+ * (FLASH_GROUPED_AUTO, 0).  Results do not depend on it.
+ * refine_steps (FLASH_SOLVE_BF16R): steps of iterative refinement after the
+ * bf16 apply, 0..4: each computes rhs - A w in FP32 from the element
+ * operators and adds the bf16 apply of it.  BF16R needs a well-conditioned
+ * A: it is refused (FLASH_ENOTIMPL) for triangle meshes, whose systems (cond
+ * ~1e7 for the 32x32 cloth) make each step grow the error. */
 #define FLASH_GROUPED_AUTO 0
 #define FLASH_GROUPED_OFF 1
 #define FLASH_GROUPED_ON 2
@@ -166,6 +173,7 @@ typedef struct {
   int32_t self_collide;
   int32_t obstacle_features;
   int32_t grouped_solve;
+  int32_t refine_steps;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest

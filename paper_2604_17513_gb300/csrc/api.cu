@@ -308,14 +308,15 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
       FLASH_CUDA_TRY(dalloc(s, &Mx->f32, (size_t)np * np));
       FLASH_CUDA_TRY(dalloc(s, &Mx->hi, (size_t)np * np));
       FLASH_CUDA_TRY(dalloc(s, &Mx->lo, (size_t)np * np));
+      if (s->d.solve == FLASH_SOLVE_BF16R) FLASH_CUDA_TRY(dalloc(s, &Mx->bf, (size_t)np * np));
     }
     double *dV = nullptr;
     FLASH_CUDA_TRY(cudaMalloc(&dV, sizeof(double) * Vp.size()));
     FLASH_CUDA_TRY(cudaMemcpy(dV, Vp.data(), sizeof(double) * Vp.size(), cudaMemcpyHostToDevice));
-    FLASH_CUDA_TRY(cast_inverse(dV, np, g.V.f32, g.V.hi, g.V.lo, g.V.exp, st));
+    FLASH_CUDA_TRY(cast_inverse(dV, np, g.V.f32, g.V.hi, g.V.lo, g.V.exp, st, g.V.bf));
     FLASH_CUDA_TRY(cudaStreamSynchronize(st));
     FLASH_CUDA_TRY(cudaMemcpy(dV, Vtp.data(), sizeof(double) * Vtp.size(), cudaMemcpyHostToDevice));
-    FLASH_CUDA_TRY(cast_inverse(dV, np, g.Vt.f32, g.Vt.hi, g.Vt.lo, g.Vt.exp, st));
+    FLASH_CUDA_TRY(cast_inverse(dV, np, g.Vt.f32, g.Vt.hi, g.Vt.lo, g.Vt.exp, st, g.Vt.bf));
     FLASH_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(dV);
     FLASH_CUDA_TRY(upload(s, &g.lam, lamf));
@@ -361,7 +362,8 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
   FLASH_CUDA_TRY(dalloc(s, &g.inv.f32, (size_t)np * np));
   FLASH_CUDA_TRY(dalloc(s, &g.inv.hi, (size_t)np * np));
   FLASH_CUDA_TRY(dalloc(s, &g.inv.lo, (size_t)np * np));
-  FLASH_CUDA_TRY(cast_inverse(dA, np, g.inv.f32, g.inv.hi, g.inv.lo, g.inv.exp, st));
+  if (s->d.solve == FLASH_SOLVE_BF16R) FLASH_CUDA_TRY(dalloc(s, &g.inv.bf, (size_t)np * np));
+  FLASH_CUDA_TRY(cast_inverse(dA, np, g.inv.f32, g.inv.hi, g.inv.lo, g.inv.exp, st, g.inv.bf));
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(dA);
   }
@@ -472,7 +474,7 @@ StepArgs step_args(const flash_scene *s) {
   return a;
 }
 
-bool use_tc(const flash_scene *s) { return s->d.solve == FLASH_SOLVE_F16X3; }
+bool use_tc(const flash_scene *s) { return s->d.solve == FLASH_SOLVE_F16X3 || s->d.solve == FLASH_SOLVE_BF16R; }
 
 // step arguments of one group (contact thickness is a property of the mesh)
 StepArgs group_args(const StepArgs &a, const Group &g) {
@@ -530,6 +532,24 @@ cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, fl
   const bool tc = use_tc(s);
   if (l1 < 0) l1 = g.N;
   const int c0 = 3 * l0, c1 = 3 * l1;
+  if (s->d.solve == FLASH_SOLVE_BF16R) {
+    // one bf16 product per contraction (FP32 accumulation), then
+    // refine_steps corrections: out += A^-1 (rhs - A out), the residual in
+    // FP32 from the element operators (launch_refine)
+    auto bf_apply = [&](int mode) -> cudaError_t {   // mode 0: out = A^-1 rh; 3: out += A^-1 rh
+      if (!g.eig) return gemm_tc(g, g.inv, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true);
+      cudaError_t e = gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn, true);
+      if (e == cudaSuccess) e = launch_split_rhs(g, g.y, st, l0, l1, true);
+      if (e == cudaSuccess) e = gemm_tc(g, g.V, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true);
+      return e;
+    };
+    cudaError_t e = timed(s, FLASH_KIND_SOLVE, st, [&] { return bf_apply(0); });
+    for (int it = 0; it < s->d.refine_steps && e == cudaSuccess; it++) {
+      e = timed(s, FLASH_KIND_SOLVE, st, [&] { return launch_refine(s, g, rhs32, out, l0, l1, st); });
+      if (e == cudaSuccess) e = timed(s, FLASH_KIND_SOLVE, st, [&] { return bf_apply(3); });
+    }
+    return e;
+  }
   if (!g.eig) {
     return timed(s, FLASH_KIND_SOLVE, st, [&] {
       return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn)
@@ -711,7 +731,9 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
       desc->grouped_solve < FLASH_GROUPED_AUTO || desc->grouped_solve > FLASH_GROUPED_ON)
     return fail(FLASH_EINVAL, "invalid scene descriptor");
   if (desc->mode != FLASH_MODE_FIXED && desc->mode != FLASH_MODE_TOL) return fail(FLASH_EINVAL, "invalid mode");
-  if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3) return fail(FLASH_EINVAL, "invalid solve");
+  if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3 && desc->solve != FLASH_SOLVE_BF16R)
+    return fail(FLASH_EINVAL, "invalid solve");
+  if (desc->refine_steps < 0 || desc->refine_steps > 4) return fail(FLASH_EINVAL, "refine_steps must be in 0..4");
   if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
   if (desc->metric != FLASH_METRIC_LITE && desc->metric != FLASH_METRIC_FULL) return fail(FLASH_EINVAL, "invalid metric");
   if (desc->lin_iters < 0 || desc->lin_iters > kMaxLinIters) return fail(FLASH_EINVAL, "lin_iters must be 0..32");
@@ -816,8 +838,13 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
     s->env_local[e] = (int)s->groups[gi].env_ids.size();
     s->groups[gi].env_ids.push_back(e);
   }
-  if (s->d.solve == FLASH_SOLVE_F16X3 && !tc_available())
+  if (use_tc(s) && !tc_available())
     return fail(FLASH_ENOTIMPL, "tensor-core solve needs an sm_103 device and the TMA driver entry point");
+  if (s->d.solve == FLASH_SOLVE_BF16R)
+    for (const auto &m : s->meshes)
+      if (m.type != FLASH_TET)
+        return fail(FLASH_ENOTIMPL, "the bf16 solve with refinement needs a well-conditioned system matrix (tet "
+                                    "meshes); a cloth's (condition ~1e7) makes every refinement step grow the error");
   FLASH_CUDA_TRY(dalloc(s, &s->status, 1));
   s->voff.assign(s->N + 1, 0);
   for (int e = 0; e < s->N; e++) s->voff[e + 1] = s->voff[e] + s->meshes[s->env_mesh[e]].n;
@@ -977,8 +1004,8 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
       s->launches = launches0;
     }
     // lanes of several mesh templates: one grouped launch for all their
-    // dense applies, kept if it beats the per-range launches
-    const flash_status gs = build_grouped(s);
+    // dense applies (f16 hi/lo solve), kept if it beats the per-range launches
+    const flash_status gs = s->d.solve == FLASH_SOLVE_F16X3 ? build_grouped(s) : FLASH_OK;
     if (gs != FLASH_OK) return gs;
     bool any = false;
     for (const Lane &L : s->lanes) any = any || L.ga.n > 0;
@@ -1570,7 +1597,7 @@ flash_status flash_global_apply(flash_scene *s, int32_t first_env, int32_t n, co
   cudaStream_t st = (cudaStream_t)stream;
   FLASH_CUDA_TRY(cudaMemsetAsync(s->done, 0, sizeof(int) * s->N, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, rhs, g.r, 0, st));
-  if (use_tc(s)) FLASH_CUDA_TRY(launch_split_rhs(g, g.r, st));
+  if (use_tc(s)) FLASH_CUDA_TRY(launch_split_rhs(g, g.r, st, 0, -1, s->d.solve == FLASH_SOLVE_BF16R));
   FLASH_CUDA_TRY(apply_inverse(s, g, g.r, g.w, st));
   FLASH_CUDA_TRY(launch_rhs_io(g, s->d_voff, first_env, out, g.w, 1, st));
   return FLASH_OK;

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <string>
@@ -42,6 +43,7 @@ struct MeshTemplate {
 struct SolveMat {
   float *f32 = nullptr;
   __half *hi = nullptr, *lo = nullptr;
+  __nv_bfloat16 *bf = nullptr;   // bf16 copy scaled by 2^exp (FLASH_SOLVE_BF16R)
   int exp = 0;
 };
 
@@ -257,7 +259,13 @@ cudaError_t launch_state_io(const flash_scene *s, const Group &g, const float *q
 cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, const float *user, float *cols,
                           int to_user, cudaStream_t st);
 // f16 hi/lo split of the columns of environments [l0, l1) of src (l1 < 0: all)
-cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0 = 0, int l1 = -1);
+cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0 = 0, int l1 = -1,
+                             bool bf16 = false);
+// bf16 solve with refinement: for environments [l0, l1) of a tet group, the
+// residual rhs32 - A w in FP32 from the element operators, written as the
+// next apply's bf16 right-hand sides (rh) with their column scales
+cudaError_t launch_refine(const flash_scene *s, const Group &g, const float *rhs32, const float *w, int l0, int l1,
+                          cudaStream_t st);
 // lanes and their table launches (build_lanes at finalize)
 cudaError_t build_lanes(flash_scene *s, int n_lanes);
 cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);
@@ -325,8 +333,11 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
                       const int *done, int mode, const float *lam, const float *kenv, cudaStream_t st, int c0 = 0,
                       int c1 = -1);
 // bn: tile width (0: the group's autotuned width)
+// bf: one bf16 product (matrix M.bf, right-hand sides bf16 in rh) instead of the f16 hi/lo split;
+// epilogue mode 3: out += acc (a refinement step's correction)
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0);
+                    const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0,
+                    bool bf = false);
 bool tc_available();
 // grouped apply (one launch over several groups' dense applies, tile width kGroupedBN)
 constexpr int kGroupedBN = 64;
@@ -341,7 +352,7 @@ cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n
 // setup (setup_kernels.cu) ---------------------------------------------------
 cudaError_t invert_spd_f64(double *A, int n, int n_pad, int batch, cudaStream_t st);
 cudaError_t cast_inverse(const double *A64, int n_pad, float *A32, __half *hi, __half *lo, int a_exp,
-                         cudaStream_t st);
+                         cudaStream_t st, __nv_bfloat16 *bf = nullptr);
 // symmetric eigen-decomposition by cyclic Jacobi rotations (host, FP64):
 // B (n x n, destroyed) = W diag(lam) W^T, W row-major with eigenvectors as columns
 void jacobi_eigen(int n, std::vector<double> &B, std::vector<double> &W, std::vector<double> &lam);

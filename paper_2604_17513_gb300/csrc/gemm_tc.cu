@@ -87,9 +87,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// instruction descriptor: kind::f16, A = B = f16, D = f32, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor: kind::f16, A = B = f16 (or both bf16), D = f32,
+// both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16 = false) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -153,6 +155,10 @@ __device__ __forceinline__ void store_cols(uint32_t taddr, float *o, const float
 #pragma unroll
     for (int j = 0; j < X; j++)
       if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
+  } else if (mode == 3) {   // accumulate: a refinement step's correction
+#pragma unroll
+    for (int j = 0; j < X; j++)
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] += __uint_as_float(v[j]) * col_scale[c0 + j];
   } else {
     float prev[X];
 #pragma unroll
@@ -165,7 +171,7 @@ __device__ __forceinline__ void store_cols(uint32_t taddr, float *o, const float
 
 // One 128 x BN output tile at rows m0.., columns j0.. (tensor maps in
 // parameter or global memory).
-template <int BN>
+template <int BN, bool BF = false>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensorMap *pAl, const CUtensorMap *pBh,
                                           const CUtensorMap *pBl, float *__restrict__ out,
                                           const float *__restrict__ W, const float *__restrict__ rscale,
@@ -218,18 +224,24 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
       const int s = kb % STAGES;
       if (!mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1)) { atomicExch(&fail_sh, 1); break; }
       uint8_t *st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
       const int k0 = kb * BK;
-      tma_load_2d(st, pAh, &full_bar[s], k0, m0);
-      tma_load_2d(st + TILE_A, pAl, &full_bar[s], k0, m0);
-      tma_load_2d(st + 2 * TILE_A, pBh, &full_bar[s], k0, j0);
-      tma_load_2d(st + 2 * TILE_A + TILE_B, pBl, &full_bar[s], k0, j0);
+      if constexpr (BF) {   // one bf16 product: the hi slots of the stage only
+        mbar_expect_tx(&full_bar[s], TILE_A + TILE_B);
+        tma_load_2d(st, pAh, &full_bar[s], k0, m0);
+        tma_load_2d(st + 2 * TILE_A, pBh, &full_bar[s], k0, j0);
+      } else {
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        tma_load_2d(st, pAh, &full_bar[s], k0, m0);
+        tma_load_2d(st + TILE_A, pAl, &full_bar[s], k0, m0);
+        tma_load_2d(st + 2 * TILE_A, pBh, &full_bar[s], k0, j0);
+        tma_load_2d(st + 2 * TILE_A + TILE_B, pBl, &full_bar[s], k0, j0);
+      }
     }
     // drain: wait until every stage this thread armed has landed (bounded)
     for (int t = max(0, kb - STAGES); t < kb; t++) mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_f16(BM, BN);
+    constexpr uint32_t idesc = idesc_f16(BM, BN, BF);
     bool ok = true;
     for (int kb = 0; kb < KB; kb++) {
       const int s = kb % STAGES;
@@ -239,10 +251,12 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
       const uint32_t ah = base, al = base + TILE_A, bh = base + 2 * TILE_A, bl = base + 2 * TILE_A + TILE_B;
 #pragma unroll
       for (int ks = 0; ks < BK / 16; ks++) {
-        const uint32_t off = ks * 32;   // 16 f16 along K inside the 128-byte swizzle row
+        const uint32_t off = ks * 32;   // 16 f16 / bf16 along K inside the 128-byte swizzle row
         mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, (kb | ks) ? 1u : 0u);
-        mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-        mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+        if constexpr (!BF) {
+          mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+          mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+        }
       }
       mma_commit(&empty_bar[s]);
     }
@@ -288,15 +302,15 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
 
 // One group's apply: tile (x, y) covers rows 128 y.. and columns
 // c_begin + BN x .. of [c_begin, cols).
-template <int BN>
+template <int BN, bool BF = false>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
               const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int c_begin,
               int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
-  gemm_tile<BN>(&tmAh, &tmAl, &tmBh, &tmBl, out, W, rscale, done, genv, status, n_pad, blockIdx.y * BM,
-                c_begin + blockIdx.x * BN, cols, a_unscale, mode, lam, kenv);
+  gemm_tile<BN, BF>(&tmAh, &tmAl, &tmBh, &tmBl, out, W, rscale, done, genv, status, n_pad, blockIdx.y * BM,
+                    c_begin + blockIdx.x * BN, cols, a_unscale, mode, lam, kenv);
 }
 
 // One apply of several groups in one launch (uneven batches: every mesh
@@ -338,14 +352,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 2D f16 tensor [outer][inner] (inner contiguous), box 64 x rows, 128B swizzle
-bool make_map(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_rows) {
+bool make_map(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_rows,
+              bool bf16 = false) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {BK, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+  CUresult r = enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -363,38 +378,56 @@ bool tc_available() {
 
 namespace {
 
-template <int BN>
+template <int BN, bool BF>
 cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                         const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
   using Cfg = TileCfg<BN>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tc<BN, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   if (g.n_pad % BM != 0 || g.n_pad % BK != 0) return cudaErrorInvalidValue;
   CUtensorMap tmAh, tmAl, tmBh, tmBl;
-  if (!make_map(&tmAh, M.hi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, M.lo, g.n_pad, g.n_pad, BM) ||
-      !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN) || !make_map(&tmBl, g.rl, g.n_pad, g.cols_pad, BN))
+  if (BF) {   // bf16 matrix and right-hand sides (the rh buffer holds bf16 in this mode)
+    if (!M.bf || !make_map(&tmAh, M.bf, g.n_pad, g.n_pad, BM, true) ||
+        !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN, true))
+      return cudaErrorInvalidValue;
+    tmAl = tmAh;
+    tmBl = tmBh;
+  } else if (!make_map(&tmAh, M.hi, g.n_pad, g.n_pad, BM) || !make_map(&tmAl, M.lo, g.n_pad, g.n_pad, BM) ||
+             !make_map(&tmBh, g.rh, g.n_pad, g.cols_pad, BN) || !make_map(&tmBl, g.rl, g.n_pad, g.cols_pad, BN)) {
     return cudaErrorInvalidValue;
+  }
   // column tiles cover the live columns; the last may run past the
   // matrix (TMA fills zeros, the epilogue stores only columns < cols)
   dim3 grid((c1 - c0 + BN - 1) / BN, g.n_pad / BM);
-  k_gemm_tc<BN><<<grid, 128, Cfg::SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv, g.status,
-                                                     g.n_pad, c0, c1, ldexpf(1.f, -M.exp), mode, lam, kenv);
+  k_gemm_tc<BN, BF><<<grid, 128, Cfg::SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv,
+                                                         g.status, g.n_pad, c0, c1, ldexpf(1.f, -M.exp), mode, lam,
+                                                         kenv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bn(int bn, const Group &g, const SolveMat &M, float *out, const float *w, const int *done,
-                      int mode, const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
+                      int mode, const float *lam, const float *kenv, cudaStream_t st, int c0, int c1,
+                      bool bf = false) {
   if (c1 < 0) c1 = g.cols;
   if (c0 < 0 || c1 > g.cols || c0 >= c1) return c0 == c1 ? cudaSuccess : cudaErrorInvalidValue;
+  if (bf) {
+    switch (bn) {
+      case 64: return launch_tile<64, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+      case 176: return launch_tile<176, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+      case 256: return launch_tile<256, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+      default: return launch_tile<128, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    }
+  }
   switch (bn) {
-    case 64: return launch_tile<64>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    case 176: return launch_tile<176>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    case 256: return launch_tile<256>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    default: return launch_tile<128>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 64: return launch_tile<64, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 176: return launch_tile<176, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 256: return launch_tile<256, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    default: return launch_tile<128, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
   }
 }
 
@@ -441,8 +474,8 @@ cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *cons
 }
 
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn) {
-  return launch_bn(bn > 0 ? bn : g.tc_bn, g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+                    const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn, bool bf) {
+  return launch_bn(bn > 0 ? bn : g.tc_bn, g, M, out, w, done, mode, lam, kenv, st, c0, c1, bf);
 }
 
 // Tile autotuner: time each candidate tile width on the group's own matrix

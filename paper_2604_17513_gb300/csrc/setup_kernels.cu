@@ -31,10 +31,12 @@ __global__ void k_gj_update(double *A, int n_pad, int k, const double *rowk, con
   }
 }
 
-__global__ void k_cast(const double *A, size_t count, float *A32, __half *hi, __half *lo, float scale) {
+__global__ void k_cast(const double *A, size_t count, float *A32, __half *hi, __half *lo, __nv_bfloat16 *bf,
+                       float scale) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     double x = A[i];
     A32[i] = (float)x;
+    if (bf) bf[i] = __float2bfloat16_rn((float)(x * scale));
     if (hi) {
       float xs = (float)(x * scale);
       __half h = __float2half_rn(xs);
@@ -66,9 +68,9 @@ cudaError_t invert_spd_f64(double *A, int n, int n_pad, int batch, cudaStream_t 
 }
 
 cudaError_t cast_inverse(const double *A64, int n_pad, float *A32, __half *hi, __half *lo, int a_exp,
-                         cudaStream_t st) {
+                         cudaStream_t st, __nv_bfloat16 *bf) {
   size_t count = (size_t)n_pad * n_pad;
-  k_cast<<<1024, 256, 0, st>>>(A64, count, A32, hi, lo, ldexpf(1.f, a_exp));
+  k_cast<<<1024, 256, 0, st>>>(A64, count, A32, hi, lo, bf, ldexpf(1.f, a_exp));
   return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ struct GroupView {
   const int2 *kb;                // bending operator, off-diagonal entries, slot-major
   int ev, deg_b;
   const float *kenv;   // per-environment stiffness scale (eigen-form groups), else null
+  int bf16;            // right-hand sides as bf16 + an FP32 copy (FLASH_SOLVE_BF16R)
   float *cgam, *pgam, *cscratch;
   int c_in_smem;
   float tau;           // contact thickness of the group's mesh
@@ -82,6 +83,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.fm_beta = g.fm_beta; v.fm_jm = g.fm_jm; v.fm_adiag = g.fm_adiag; v.fm_u = g.fm_u; v.fm_m = g.fm_m;
   v.fm_adiag_stride = g.fm_adiag_stride;
   v.kenv = g.eig ? g.kenv : nullptr;
+  v.bf16 = s->d.solve == FLASH_SOLVE_BF16R ? 1 : 0;
   v.tau = (float)g.tau;
   return v;
 }
@@ -568,7 +570,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
 // thread passes the maxima of |vals| it already knows (or 0); the kernel
 // completes them over the rows this thread owns and reduces once.
 __device__ void write_split_columns(const GroupView &G, int l, const float *vals, int ld, float (*sh3)[3], bool scan,
-                                    float m0 = 0.f, float m1 = 0.f, float m2 = 0.f) {
+                                    float m0 = 0.f, float m1 = 0.f, float m2 = 0.f, float *fp32 = nullptr) {
   const int n = G.n, np = G.n_pad;
   float m[3] = {m0, m1, m2};
   if (scan)
@@ -587,6 +589,17 @@ __device__ void write_split_columns(const GroupView &G, int l, const float *vals
     const float sc = ldexpf(1.f, ex);
     const size_t col = (size_t)(l * 3 + c);
     if (threadIdx.x == 0) G.rscale[col] = ldexpf(1.f, -ex);
+    if (G.bf16) {
+      // one bf16 column with the same power-of-two scale, and the FP32
+      // values the refinement's residual starts from
+      __nv_bfloat162 *hb = reinterpret_cast<__nv_bfloat162 *>(G.rh + col * np);
+      for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
+        const float x0 = 2 * i < n ? vals[c * ld + 2 * i] : 0.f, x1 = 2 * i + 1 < n ? vals[c * ld + 2 * i + 1] : 0.f;
+        hb[i] = __floats2bfloat162_rn(x0 * sc, x1 * sc);
+        if (fp32) *reinterpret_cast<float2 *>(fp32 + col * np + 2 * i) = make_float2(x0, x1);
+      }
+      continue;
+    }
     __half2 *hh = reinterpret_cast<__half2 *>(G.rh + col * np), *hl = reinterpret_cast<__half2 *>(G.rl + col * np);
     for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
       const float x0 = 2 * i < n ? vals[c * ld + 2 * i] * sc : 0.f;
@@ -1138,7 +1151,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
   __syncthreads();
   if (s_done) return;
   if (tc) {
-    write_split_columns(G, l, rs, ns, sh3, true);
+    write_split_columns(G, l, rs, ns, sh3, true, 0.f, 0.f, 0.f, G.r);
   } else {
     float *r = G.r + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -1146,6 +1159,93 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       r[c * np + j] = rs[c * ns + j];
     }
   }
+}
+
+// Iterative refinement of the bf16 solve (tet meshes): the residual
+// rhs - A w of the current solution w in FP32, with A w = M w + sum_e
+// w~_e k_e D_e^T (D_e w) from the element operators (the local pass's
+// operators without the projection), summed per vertex through the same CSR
+// table; the result becomes the next bf16 apply's right-hand side.
+__device__ __forceinline__ void refine_body(const GroupView &G, const int l, const EnvView &V, const float *rhs32,
+                                            const float *wv) {
+  constexpr int vpe = 4, nc = 3;
+  extern __shared__ float smem[];
+  __shared__ float sh3[32][3];
+  const int e = G.genv[l];
+  const int n = G.n, np = G.n_pad, ns = (n + 3) & ~3;
+  if (V.done[e]) return;
+  float *ws = smem, *rs = ws + 3 * ns, *Fs;
+  const uint16_t *coff, *cidx;
+  if (G.c_in_smem) {
+    Fs = rs + 3 * ns;
+    uint32_t *t = reinterpret_cast<uint32_t *>(Fs + 3 * (G.ev + 1));
+    const int w_off = (n + 2) >> 1, w_idx = (G.ev + 1) >> 1;
+    const uint32_t *src_off = reinterpret_cast<const uint32_t *>(G.coff);
+    const uint32_t *src_idx = reinterpret_cast<const uint32_t *>(G.cidx);
+    for (int i = threadIdx.x; i < w_off; i += blockDim.x) t[i] = __ldg(src_off + i);
+    for (int i = threadIdx.x; i < w_idx; i += blockDim.x) t[w_off + i] = __ldg(src_idx + i);
+    coff = reinterpret_cast<const uint16_t *>(t);
+    cidx = coff + 2 * w_off;
+  } else {
+    Fs = G.cscratch + (size_t)l * 3 * (G.ev + 1);
+    coff = G.coff;
+    cidx = G.cidx;
+  }
+  const float *w = wv + (size_t)l * 3 * np, *b = rhs32 + (size_t)l * 3 * np;
+  for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+    const int c = i / ns, j = i - c * ns;
+    const float x = j < n ? w[c * np + j] : 0.f;
+    ws[i] = x;
+    rs[i] = j < n ? b[c * np + j] - __ldg(G.mass + j) * x : 0.f;
+  }
+  __syncthreads();
+  const float ks = G.kenv ? G.kenv[l] : 1.f;
+  for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
+    const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
+    const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
+    const float *D = G.D + 12 * el;
+    float F[9], Dl[12];
+#pragma unroll
+    for (int t = 0; t < 3 * vpe; t++) Dl[t] = __ldg(D + t);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const float x0 = ws[c * ns + vv[0]];
+#pragma unroll
+      for (int j = 0; j < nc; j++) {
+        float sm = 0.f;
+#pragma unroll
+        for (int aa = 1; aa < vpe; aa++) sm += (ws[c * ns + vv[aa]] - x0) * Dl[aa * 3 + j];
+        F[nc * c + j] = sm;
+      }
+    }
+    const float wt = __ldg(G.wt + el) * ks;
+    float *Fe = Fs + (size_t)el * vpe * 3;
+#pragma unroll
+    for (int aa = 0; aa < vpe; aa++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        float sm = 0.f;
+#pragma unroll
+        for (int j = 0; j < nc; j++) sm += Dl[aa * 3 + j] * F[nc * c + j];
+        Fe[aa * 3 + c] = wt * sm;
+      }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float a0 = rs[i], a1 = rs[ns + i], a2 = rs[2 * ns + i];
+    const int t1 = coff[i + 1];
+    for (int t = coff[i]; t < t1; t++) {
+      const float *f = Fs + 3 * (int)cidx[t];
+      a0 -= f[0];
+      a1 -= f[1];
+      a2 -= f[2];
+    }
+    rs[i] = a0;
+    rs[ns + i] = a1;
+    rs[2 * ns + i] = a2;
+  }
+  __syncthreads();
+  write_split_columns(G, l, rs, ns, sh3, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -1422,7 +1522,7 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
   if (tc) {
     __syncthreads();
     // every nonzero row of fs was written by this block with its max tracked
-    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2);
+    write_split_columns(G, l, fs, n, sh3, false, fm0, fm1, fm2, G.f);
   }
 }
 
@@ -1623,7 +1723,7 @@ __device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l,
   __syncthreads();
   if (tc) {
     // with self contacts the column maxima are known only after the sums
-    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2);
+    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2, G.f);
   } else {
     float *f = G.f + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -1790,7 +1890,7 @@ __device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, 
   }
   __syncthreads();
   if (tc) {
-    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2);
+    write_split_columns(G, l, fs, n, sh3, G.self != 0, fm0, fm1, fm2, G.f);
   } else {
     float *f = G.f + (size_t)l * 3 * np;
     for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
@@ -1880,6 +1980,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_local_tab(const GroupView *__
     pending = k > 1;
   }
   local_body<VPE, SELF>(tab[b.x], b.y, V, a, k, residual_only, tc, pending);
+}
+__global__ void __launch_bounds__(512, 2) k_refine(GroupView G, EnvView V, const float *rhs32, const float *w, int l0) {
+  refine_body(G, l0 + blockIdx.x, V, rhs32, w);
 }
 // End of one iteration of the graphed tolerance loop (Mode B): the loop runs
 // again while some environment is still iterating and the cap allows; the
@@ -2135,6 +2238,8 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_local_tab<4, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_begin_tab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBeginSmem);
@@ -2183,12 +2288,21 @@ cudaError_t launch_rhs_io(const Group &g, const int64_t *voff, int first_env, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0, int l1) {
+cudaError_t launch_refine(const flash_scene *s, const Group &g, const float *rhs32, const float *w, int l0, int l1,
+                          cudaStream_t st) {
+  if (g.vpe != 4) return cudaErrorInvalidValue;
+  if (l1 <= l0) return cudaSuccess;
+  k_refine<<<l1 - l0, 512, g.smem_local, st>>>(view(s, g), eview(s), rhs32, w, l0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_rhs(const Group &g, const float *src, cudaStream_t st, int l0, int l1, bool bf16) {
   if (l1 < 0) l1 = g.N;
   if (l0 < 0 || l1 > g.N || l0 >= l1) return l0 == l1 ? cudaSuccess : cudaErrorInvalidValue;
   GroupView v;
   memset(&v, 0, sizeof v);
   v.n = g.n; v.n_pad = g.n_pad; v.rh = g.rh; v.rl = g.rl; v.rscale = g.rscale;
+  v.bf16 = bf16 ? 1 : 0;
   k_split<<<l1 - l0, 256, sizeof(float) * 3 * g.n, st>>>(v, src, l0);
   return cudaGetLastError();
 }

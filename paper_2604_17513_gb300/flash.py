@@ -31,7 +31,7 @@ OEE_SLOT = MAX_OBS + 4  # contact-list slot of box edges against cloth edges
 OFEAT_MAX = 4           # rows of each box-feature kind per vertex at most
 MODE_FIXED, MODE_TOL = 0, 1
 METRIC_LITE, METRIC_FULL = 0, 1
-SOLVE_F32, SOLVE_F16X3 = 0, 1
+SOLVE_F32, SOLVE_F16X3, SOLVE_BF16R = 0, 1, 2
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 GROUPED_AUTO, GROUPED_OFF, GROUPED_ON = 0, 1, 2
 
@@ -55,7 +55,7 @@ class SceneDesc(C.Structure):
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
                 ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32),
-                ("grouped_solve", C.c_int32)]
+                ("grouped_solve", C.c_int32), ("refine_steps", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -168,7 +168,7 @@ class Sim:
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
                  warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
-                 self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO):
+                 self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO, refine_steps=1):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -204,6 +204,7 @@ class Sim:
         d.metric = metric
         d.lin_iters = lin_iters
         d.grouped_solve = grouped
+        d.refine_steps = refine_steps
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))

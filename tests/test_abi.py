@@ -63,6 +63,13 @@ def test_scene_descriptor_validation(lib):
     d.metric = flash.METRIC_FULL
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
     d.obstacle_features, d.metric = 0, 0
+    # the bf16 solve's refinement count and the grouped-solve switch are range checked
+    d.solve, d.refine_steps = flash.SOLVE_BF16R, 5
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
+    assert b"refine_steps" in lib.flash_last_error()
+    d.refine_steps, d.grouped_solve = 1, 3
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
+    d.solve, d.refine_steps, d.grouped_solve = 0, 0, 0
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
     # a mesh with an out-of-range element index is rejected on the host
     rest = np.zeros((3, 3))

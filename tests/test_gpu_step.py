@@ -561,3 +561,63 @@ def test_grouped_solve_equals_per_template_launches(cuda, mode):
     (q_off, it_off, st_off), (q_on, it_on, st_on) = out
     assert st_off == 0 and st_on == 0
     assert np.array_equal(q_on, q_off) and np.array_equal(it_on, it_off)
+
+
+@pytest.mark.parametrize("steps_tol", [(0, 2e-2), (1, 3e-4), (2, 2e-5)])
+@pytest.mark.parametrize("dense", [False, True])
+def test_global_apply_bf16_refinement(cuda, steps_tol, dense):
+    """The bf16 tensor-core solve with FP32 iterative refinement on tet
+    blocks (condition 20-300): one bf16 product of the eigen form (per-
+    environment stiffness) or of the dense inverse (one stiffness), then
+    refine_steps corrections with the residual rhs - A w in FP32.  The
+    error against the oracle's Cholesky solve falls by two orders a step, to
+    the FP32 level after two (bounds from an FP64 emulation of the same
+    arithmetic: 5e-3..1.3e-2, 2.5e-5..6.9e-5, 1e-7..7e-7)."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    steps, tol = steps_tol
+    sc = scenes.tet_squeeze(n_envs=4, steps=2)
+    if dense:
+        sc.stiff[:] = sc.stiff[0]
+    sim = _sim(sc, solve=flash.SOLVE_BF16R, refine_steps=steps)
+    rng = np.random.default_rng(10)
+    rhs = rng.normal(size=(4, sc.n_verts, 3)) * 1e-6
+    out = sim.global_apply(0, 4, torch.from_numpy(rhs.astype(np.float32).reshape(-1, 3)).to(cuda))
+    out = out.cpu().numpy().reshape(4, sc.n_verts, 3)
+    for e in range(4):
+        ref = oracle.Mesh.from_scene(sc, e).solve(_f32(rhs[e]))
+        err = np.abs(out[e] - ref).max() / np.abs(ref).max()
+        assert err < tol, (e, sc.stiff[e], steps, err)
+
+
+def test_tet_squeeze_one_step_bf16_refinement(cuda):
+    """One fixed step of the squeezed tet blocks with the bf16 solve and two
+    refinement steps: positions within 1e-5 m and impulses as the other
+    solves (the correction form keeps the solve's error proportional to the
+    small correction)."""
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.tet_squeeze(n_envs=3, steps=30)
+    s = 18
+    q, v, meshes = sc.q0.copy(), sc.v0.copy(), {}
+    for e in range(sc.n_envs):
+        meshes[e], st = oracle_state_at(sc, e, s)
+        q[e], v[e] = _f32(st.q), _f32(st.v)
+    sim = _sim(sc, solve=flash.SOLVE_BF16R, refine_steps=2)
+    qg, _ = gpu_step_from(sim, sc, s, q, v)
+    con = parity.gpu_contacts(sim)
+    for e in range(sc.n_envs):
+        ref = oracle.EnvState(q[e], v[e])
+        oracle.step(meshes[e], sc, e, s, ref)
+        err = np.abs(qg[e] - ref.q).max()
+        assert err <= POS_TOL, (e, err)
+        parity.assert_impulses(con, e, ref, sc, e, s, err)
+    assert sim.status() == 0
+
+
+def test_bf16_refinement_refused_for_cloth(cuda):
+    """A cloth's system (condition ~1e7) makes each bf16 refinement step grow
+    the error, so the scene refuses the mode."""
+    from paper_2604_17513_gb300 import flash
+    with pytest.raises(flash.FlashError) as ei:
+        _sim(scenes.cloth_drop(n_envs=1, steps=2), solve=flash.SOLVE_BF16R)
+    assert ei.value.code == flash.ENOTIMPL
