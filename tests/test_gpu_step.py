@@ -535,17 +535,18 @@ def test_cloth_drop_rollout_invariants(cuda):
     assert conv >= 0.95 * 200 * sc.n_envs and checked > 1000, (conv, checked)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_grouped_solve_equals_per_template_launches(cuda, mode):
     """Uneven batch in two lanes of several mesh templates each: applying
     every template's dense inverse in one grouped tensor-core launch per lane
     gives bit-identical states and iteration counts to one launch per
-    template (both stopping modes)."""
+    template (both stopping modes, and the full metric, whose Krylov applies
+    write the grouped launch's third output table)."""
     import torch
     from paper_2604_17513_gb300 import flash
     scs = scenes.mixed_batch(n_envs=24, steps=12, side_choices=(16, 20, 24), tet_targets=(250, 600))
     assert len(scs) >= 4
-    kw = dict(mode=1, tol=1e-5, k_cap=40) if mode else {}
+    kw = [{}, dict(mode=1, tol=1e-5, k_cap=40), dict(metric=flash.METRIC_FULL)][mode]
     out = []
     for grouped in (flash.GROUPED_OFF, flash.GROUPED_ON):
         sim = flash.Sim(scs, solve=flash.SOLVE_F16X3, lanes=2, grouped=grouped, **kw)
