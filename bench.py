@@ -74,6 +74,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--grouped", default="auto", choices=["auto", "on", "off"],
                    help="one tensor-core launch for all mesh templates of a lane (auto: the faster, timed at setup)")
+    p.add_argument("--local-threads", type=int, default=0,
+                   help="local pass threads per environment: 256, 512, 1024, 0 (library default) or -1 (timed on "
+                        "the first step)")
+    p.add_argument("--ncp-threads", type=int, default=0,
+                   help="lite NCP pass threads per environment: 128, 256, 512, 0 (library default) or -1 (timed)")
     p.add_argument("--clock-log", default=None,
                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     args = p.parse_args()
@@ -612,6 +617,8 @@ def main():
     warm = flash.WARM_PREV if args.warm == "prev" else flash.WARM_COLD
     mode_kw["grouped"] = {"auto": flash.GROUPED_AUTO, "on": flash.GROUPED_ON, "off": flash.GROUPED_OFF}[args.grouped]
     mode_kw["refine_steps"] = args.refine
+    mode_kw["local_threads"] = args.local_threads
+    mode_kw["ncp_threads"] = args.ncp_threads
     try:
         sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, eager=args.eager, **mode_kw)
     except flash.FlashError:
@@ -884,7 +891,9 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
                        "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths())),
-                       "grouped_solve": sim.grouped_solve()},
+                       "grouped_solve": sim.grouped_solve(),
+                       "threads_per_env": {"local": sorted(set(sim.threads()[0])),
+                                           "ncp": sorted(set(sim.threads()[1]))}},
             "frac_rncp_le_tol": frac_conv, "all_env_steps_per_s": value_all, "mean_iters": mean_iters,
             "p99_iters": p99_iters,
             "status": status, "warm_start": warm_cmp,

@@ -151,7 +151,18 @@ typedef int32_t flash_status;
  * bf16 apply, 0..4: each computes rhs - A w in FP32 from the element
  * operators and adds the bf16 apply of it.  BF16R needs a well-conditioned
  * A: it is refused (FLASH_ENOTIMPL) for triangle meshes, whose systems (cond
- * ~1e7 for the 32x32 cloth) make each step grow the error. */
+ * ~1e7 for the 32x32 cloth) make each step grow the error.
+ * local_threads, ncp_threads: threads per environment (one CTA each) of the
+ * local pass (0, 256, 512 or 1024) and of the lite NCP pass (0, 128, 256 or
+ * 512).  0 takes the library's choice (local: 1024 for meshes above 2048
+ * vertices, else 512; NCP: 256); FLASH_THREADS_TUNE (-1) times the
+ * candidates on the scene's first step and keeps the fastest (see
+ * flash_scene_threads).  Fewer threads per environment put more
+ * environments on each SM; more shorten each environment's dependent chain.
+ * Results do not depend on either (each vertex and contact row is handled
+ * by one thread in a fixed order; the block reductions are maxima), except
+ * with self or box-feature rows, whose forces are summed with atomics. */
+#define FLASH_THREADS_TUNE (-1)
 #define FLASH_GROUPED_AUTO 0
 #define FLASH_GROUPED_OFF 1
 #define FLASH_GROUPED_ON 2
@@ -174,6 +185,8 @@ typedef struct {
   int32_t obstacle_features;
   int32_t grouped_solve;
   int32_t refine_steps;
+  int32_t local_threads;
+  int32_t ncp_threads;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -392,6 +405,14 @@ int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out);
 /* 1 if the scene's lanes apply their dense inverses in one grouped launch
  * (flash_scene_desc.grouped_solve), else 0; 0 before finalize. */
 int32_t flash_grouped_solve(const flash_scene *s);
+/* Threads per environment in use: kind 0, the local pass's launches (one
+ * per batch of environments with the same element type and shared-memory
+ * need, lane by lane); kind 1, the lite NCP pass's (one per lane).  Writes
+ * up to max_out values into the host array out and returns how many there
+ * are (0 before finalize or for another kind).  With FLASH_THREADS_TUNE the
+ * values are the library's choice until the first step has timed the
+ * candidates, and the timed choice after it. */
+int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, int32_t max_out);
 
 /* Learned warm start (the paper has no learned component; the network
  * predicts the initial multipliers gamma^0 and the first iterate at each

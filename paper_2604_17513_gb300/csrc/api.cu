@@ -734,6 +734,12 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
   if (desc->solve != FLASH_SOLVE_F32 && desc->solve != FLASH_SOLVE_F16X3 && desc->solve != FLASH_SOLVE_BF16R)
     return fail(FLASH_EINVAL, "invalid solve");
   if (desc->refine_steps < 0 || desc->refine_steps > 4) return fail(FLASH_EINVAL, "refine_steps must be in 0..4");
+  if (desc->local_threads != 0 && desc->local_threads != FLASH_THREADS_TUNE && desc->local_threads != 256 &&
+      desc->local_threads != 512 && desc->local_threads != 1024)
+    return fail(FLASH_EINVAL, "local_threads must be 0, -1 (tune), 256, 512 or 1024");
+  if (desc->ncp_threads != 0 && desc->ncp_threads != FLASH_THREADS_TUNE && desc->ncp_threads != 128 &&
+      desc->ncp_threads != 256 && desc->ncp_threads != 512)
+    return fail(FLASH_EINVAL, "ncp_threads must be 0, -1 (tune), 128, 256 or 512");
   if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
   if (desc->metric != FLASH_METRIC_LITE && desc->metric != FLASH_METRIC_FULL) return fail(FLASH_EINVAL, "invalid metric");
   if (desc->lin_iters < 0 || desc->lin_iters > kMaxLinIters) return fail(FLASH_EINVAL, "lin_iters must be 0..32");
@@ -1023,6 +1029,8 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
     }
   }
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
+  s->tune_pending = s->d.local_threads == FLASH_THREADS_TUNE ||
+                    (s->d.ncp_threads == FLASH_THREADS_TUNE && s->d.metric == FLASH_METRIC_LITE);
   s->finalized = true;
   return FLASH_OK;
 }
@@ -1155,6 +1163,134 @@ flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *
 
 namespace {
 
+// Threads per environment of the local and lite NCP passes, timed on the
+// scene's first step (FLASH_THREADS_TUNE), between its begin kernels and its
+// first iteration, with the lanes joined on st.  Each candidate runs the
+// first iteration's pass (k = 1: no pending update, outputs overwritten) from
+// the same saved stop flags, iteration counts and residuals, and each NCP
+// candidate from the same saved multipliers; everything is restored after the
+// last candidate, so the step that follows is the one an untuned scene takes.
+// The fastest of three runs of each candidate is compared, per local batch and
+// per lane.
+flash_status tune_threads(flash_scene *s, const StepArgs &a, int tc, cudaStream_t st) {
+  s->tune_pending = false;
+  s->graph_stale = true;
+  const bool profiling = s->profiling;   // the candidates' launches stay out of the kernel profile
+  s->profiling = false;
+  constexpr int kReps = 3;
+  const size_t N = (size_t)s->N;
+  std::vector<void *> tmp;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&] {
+    cudaStreamSynchronize(st);
+    for (void *p : tmp) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  auto run = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // saved per-environment stop state: done, iters, rncp
+    void *sv = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sv, N * (2 * sizeof(int) + sizeof(float)));
+    if (e != cudaSuccess) return e;
+    tmp.push_back(sv);
+    int *sdone = (int *)sv, *siters = sdone + N;
+    float *srncp = (float *)(siters + N);
+    e = cudaMemcpyAsync(sdone, s->done, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(siters, s->iters, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(srncp, s->rncp, N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    auto restore = [&]() -> cudaError_t {
+      cudaError_t r = cudaMemcpyAsync(s->done, sdone, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(s->iters, siters, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(s->rncp, srncp, N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      return r;
+    };
+    auto time_ms = [&](const std::function<cudaError_t()> &f, float *ms) -> cudaError_t {
+      cudaError_t r = cudaEventRecord(e0, st);
+      if (r == cudaSuccess) r = f();
+      if (r == cudaSuccess) r = cudaEventRecord(e1, st);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(ms, e0, e1);
+      s->launches++;
+      return r;
+    };
+    if (s->d.local_threads == FLASH_THREADS_TUNE) {
+      static const int cand[3] = {256, 512, 1024};
+      for (Lane &L : s->lanes)
+        for (Batch &b : L.local) {
+          float best[3] = {1e30f, 1e30f, 1e30f};
+          for (int rep = 0; rep < kReps && e == cudaSuccess; rep++)
+            for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+              float ms = 0.f;
+              e = restore();
+              if (e == cudaSuccess)
+                e = time_ms([&] { return launch_local_batch(s, b, cand[c], a, 1, 0, tc, st); }, &ms);
+              best[c] = std::min(best[c], ms);
+            }
+          int k = 0;
+          for (int c = 1; c < 3; c++)
+            if (best[c] < best[k]) k = c;
+          b.threads = cand[k];
+        }
+    }
+    if (e == cudaSuccess && s->d.ncp_threads == FLASH_THREADS_TUNE && s->d.metric == FLASH_METRIC_LITE) {
+      // the first iteration's residual and w = A^-1 r, then the NCP candidates
+      // from the saved multipliers
+      e = restore();
+      for (Lane &L : s->lanes) {
+        int launched = 0;
+        if (e == cudaSuccess) e = launch_local_lane(s, L, a, 1, 0, tc, st, &launched);
+        s->launches += launched;
+        if (e == cudaSuccess) e = apply_lane(s, L, st, [](Group &g) { return g.r; }, [](Group &g) { return g.w; }, 0);
+      }
+      std::vector<float *> saved(s->groups.size(), nullptr);
+      for (size_t gi = 0; gi < s->groups.size() && e == cudaSuccess; gi++) {
+        const Group &g = s->groups[gi];
+        const size_t bytes = (size_t)g.N * s->cap * 4 * sizeof(float);
+        void *p = nullptr;
+        e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) break;
+        tmp.push_back(p);
+        saved[gi] = (float *)p;
+        e = cudaMemcpyAsync(p, g.cgam, bytes, cudaMemcpyDeviceToDevice, st);
+      }
+      auto restore_gamma = [&]() -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        for (size_t gi = 0; gi < s->groups.size() && r == cudaSuccess; gi++) {
+          const Group &g = s->groups[gi];
+          r = cudaMemcpyAsync(g.cgam, saved[gi], (size_t)g.N * s->cap * 4 * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st);
+        }
+        return r;
+      };
+      static const int cand[3] = {128, 256, 512};
+      for (Lane &L : s->lanes) {
+        float best[3] = {1e30f, 1e30f, 1e30f};
+        for (int rep = 0; rep < kReps && e == cudaSuccess; rep++)
+          for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+            float ms = 0.f;
+            e = restore_gamma();
+            if (e == cudaSuccess) e = time_ms([&] { return launch_ncp_lane(s, L, a, tc, st, cand[c]); }, &ms);
+            best[c] = std::min(best[c], ms);
+          }
+        int k = 0;
+        for (int c = 1; c < 3; c++)
+          if (best[c] < best[k]) k = c;
+        L.ncp_threads = cand[k];
+      }
+      if (e == cudaSuccess) e = restore_gamma();
+    }
+    if (e == cudaSuccess) e = restore();
+    return e;
+  };
+  const cudaError_t e = run();
+  cleanup();
+  s->profiling = profiling;
+  FLASH_CUDA_TRY(e);
+  return FLASH_OK;
+}
+
 // One time step (Algorithm 1 body) issued on st and the lanes' streams.
 flash_status tol_loop_graphed(flash_scene *s, cudaStream_t st, const std::function<cudaError_t(int, int)> &local,
                               const std::function<cudaError_t(cudaStream_t)> &solves);
@@ -1243,6 +1379,12 @@ flash_status step_once(flash_scene *s, cudaStream_t st) {
           }));
         }
       }
+      FLASH_CUDA_TRY(fork(s, st));
+    }
+    if (s->tune_pending && !s->capturing) {
+      FLASH_CUDA_TRY(join(s, st));
+      const flash_status r = tune_threads(s, a, tc, st);
+      if (r != FLASH_OK) return r;
       FLASH_CUDA_TRY(fork(s, st));
     }
     if (s->d.mode == FLASH_MODE_FIXED) {
@@ -1408,6 +1550,12 @@ flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool graphed = !s->d.eager && !s->profiling;
   if (graphed) {
+    if (s->tune_pending && n_steps > 0) {
+      // the first step runs eagerly: it times the thread counts the graph uses
+      const flash_status r = step_once(s, st);
+      if (r != FLASH_OK) return r;
+      n_steps--;
+    }
     if (!s->graph || s->graph_stale) {
       const flash_status r = capture_step(s);
       if (r != FLASH_OK) return r;
@@ -1512,6 +1660,23 @@ int64_t flash_launch_count(const flash_scene *s) {
 int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int32_t)s->lanes.size() : 0; }
 
 int32_t flash_grouped_solve(const flash_scene *s) { return s && s->finalized && s->grouped ? 1 : 0; }
+
+int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, int32_t max_out) {
+  if (!s || !s->finalized || (kind != 0 && kind != 1)) return 0;
+  int32_t k = 0;
+  for (const Lane &L : s->lanes) {
+    if (kind == 1) {
+      if (out && k < max_out) out[k] = L.ncp_threads;
+      k++;
+      continue;
+    }
+    for (const Batch &b : L.local) {
+      if (out && k < max_out) out[k] = b.threads;
+      k++;
+    }
+  }
+  return k;
+}
 
 int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out) {
   if (!s || !s->finalized || !use_tc(s)) return 0;

@@ -129,7 +129,7 @@ namespace flash {
 // environment map[b].y of group map[b].x (a row of the scene's group table).
 struct Batch {
   int vpe = 0;            // vertices per element of its groups (local pass only)
-  int threads = 512;      // local pass: threads per CTA (1024 for meshes above kBigMesh vertices)
+  int threads = 512;      // local pass: threads per CTA, one environment each (256, 512 or 1024)
   int blocks = 0;         // CTAs, one per environment
   size_t smem = 0;        // dynamic shared memory per CTA: the largest need of its groups
   int2 *map = nullptr;    // device [blocks]
@@ -159,6 +159,7 @@ struct Lane {
   Batch all;                    // begin / NCP / end over the lane's environments
   std::vector<Batch> local;     // local pass, by element type and shared-memory class
   size_t ncp_smem_tc = 0;
+  int ncp_threads = 256;        // lite NCP pass: threads per CTA, one environment each (128, 256 or 512)
   GroupedApply ga;
 };
 }  // namespace flash
@@ -221,6 +222,7 @@ struct flash_scene {
   int64_t body_launches = 0;    // kernels in one run of the tolerance loop's body
   cudaStream_t body_st = nullptr;   // captures the tolerance loop's body
   bool capturing = false;       // step_once is being captured
+  bool tune_pending = false;    // threads per environment still to be timed (first step)
   bool graph_stale = true;      // a setting that changes the step's launches has changed
   bool grouped = false;         // lanes apply their dense inverses in one grouped launch (chosen at finalize)
 };
@@ -310,7 +312,10 @@ cudaError_t launch_grasp_set(const flash_scene *s, int first_env, int count, int
                              float az, float radius, cudaStream_t st);
 cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
                               cudaStream_t st, int *launched);
-cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st);
+cudaError_t launch_local_batch(const flash_scene *s, const Batch &b, int threads, const StepArgs &a, int k,
+                               int residual_only, int tc, cudaStream_t st);
+cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st,
+                            int threads = 0);
 cudaError_t launch_tol_next(cudaGraphConditionalHandle h, int *active, int *kit, unsigned long long *trips, int last,
                             int first, cudaStream_t st);
 cudaError_t launch_end_lane(const flash_scene *s, const Lane &L, const StepArgs &a, cudaStream_t st);

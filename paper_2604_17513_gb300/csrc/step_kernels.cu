@@ -1997,8 +1997,9 @@ __global__ void k_tol_next(cudaGraphConditionalHandle h, int *active, int *kit, 
   *kit = k + 1;
   if (!first) *trips += 1;
 }
-__global__ void __launch_bounds__(256, 4) k_ncp_tab(const GroupView *__restrict__ tab, const int2 *__restrict__ map,
-                                                    EnvView V, StepArgs a, int tc) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_ncp_tab(const GroupView *__restrict__ tab,
+                                                          const int2 *__restrict__ map, EnvView V, StepArgs a, int tc) {
   const int2 b = map[blockIdx.x];
   ncp_body(tab[b.x], b.y, V, a, tc);
 }
@@ -2225,22 +2226,30 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
 
 }  // namespace
 
+template <int NT>
+cudaError_t configure_local() {
+  cudaError_t e = cudaFuncSetAttribute(k_local_tab<3, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       220 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_local_tab<3, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_local_tab<4, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_local_tab<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = configure_local<256>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  e = configure_local<512>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<3, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<3, true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_local_tab<4, false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  e = configure_local<1024>();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_ncp_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  e = cudaFuncSetAttribute(k_ncp_tab<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ncp_tab<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ncp_tab<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_begin_tab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBeginSmem);
   if (e != cudaSuccess) return e;
@@ -2320,8 +2329,9 @@ cudaError_t upload_owned(flash_scene *s, T **p, const std::vector<T> &h) {
   return e;
 }
 
-// Resident local-pass CTAs per SM (512 threads, so at most 4) for a CTA with
-// `smem` bytes of dynamic shared memory next to its static shared memory.
+// Shared-memory class of a local-pass CTA (a batching key): how many CTAs with
+// `smem` bytes of dynamic shared memory next to their static shared memory
+// fit on one SM, at most 4.
 int local_class(size_t smem) {
   const size_t per_sm = 228 * 1024, static_smem = sizeof(ObsShared) + 1024;
   const int c = (int)(per_sm / (smem + static_smem + 1024));
@@ -2391,12 +2401,13 @@ cudaError_t build_lanes(flash_scene *s, int n_lanes) {
     L.all.blocks = (int)all.size();
     if ((e = upload_owned(s, &L.all.map, all)) != cudaSuccess) return e;
     L.ncp_smem_tc = sizeof(float) * 3 * (size_t)nmax;
+    L.ncp_threads = s->d.ncp_threads > 0 ? s->d.ncp_threads : 256;
     for (int vpe = 3; vpe <= 4; vpe++)
       for (int big = 1; big >= 0; big--)
       for (int cls = 4; cls >= 1; cls--) {
         Batch b;
         b.vpe = vpe;
-        b.threads = big ? 1024 : 512;
+        b.threads = s->d.local_threads > 0 ? s->d.local_threads : big ? 1024 : 512;
         std::vector<int2> m;
         for (const LaneRange &r : L.ranges) {
           const Group &g = s->groups[r.group];
@@ -2430,30 +2441,39 @@ cudaError_t launch_begin_lane(const flash_scene *s, const Lane &L, const StepArg
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
-                              cudaStream_t st, int *launched) {
+namespace {
+template <int NT>
+void local_launch(const flash_scene *s, const Batch &b, const StepArgs &a, int k, int residual_only, int tc,
+                  cudaStream_t st) {
   const int pending = k > 1;
   const GroupView *tab = (const GroupView *)s->gtab;
+  const bool self = s->d.self_collide || s->d.obstacle_features;
+  if (b.vpe == 3 && self)
+    k_local_tab<3, true, NT><<<b.blocks, NT, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+  else if (b.vpe == 3)
+    k_local_tab<3, false, NT><<<b.blocks, NT, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+  else
+    k_local_tab<4, false, NT><<<b.blocks, NT, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
+}
+}  // namespace
+
+// One local-pass batch with `threads` threads per environment (0: the
+// batch's own choice).
+cudaError_t launch_local_batch(const flash_scene *s, const Batch &b, int threads, const StepArgs &a, int k,
+                               int residual_only, int tc, cudaStream_t st) {
+  switch (threads > 0 ? threads : b.threads) {
+    case 256: local_launch<256>(s, b, a, k, residual_only, tc, st); break;
+    case 512: local_launch<512>(s, b, a, k, residual_only, tc, st); break;
+    case 1024: local_launch<1024>(s, b, a, k, residual_only, tc, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int k, int residual_only, int tc,
+                              cudaStream_t st, int *launched) {
   for (const Batch &b : L.local) {
-    const bool self = s->d.self_collide || s->d.obstacle_features;
-    if (b.threads == 1024) {
-      if (b.vpe == 3 && self)
-        k_local_tab<3, true, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
-                                                                   pending);
-      else if (b.vpe == 3)
-        k_local_tab<3, false, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
-                                                                    pending);
-      else
-        k_local_tab<4, false, 1024><<<b.blocks, 1024, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc,
-                                                                    pending);
-    } else if (b.vpe == 3 && self) {
-      k_local_tab<3, true><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
-    } else if (b.vpe == 3) {
-      k_local_tab<3, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
-    } else {
-      k_local_tab<4, false><<<b.blocks, 512, b.smem, st>>>(tab, b.map, eview(s), a, k, residual_only, tc, pending);
-    }
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_local_batch(s, b, 0, a, k, residual_only, tc, st);
     if (e != cudaSuccess) return e;
     ++*launched;
   }
@@ -2466,10 +2486,17 @@ cudaError_t launch_tol_next(cudaGraphConditionalHandle h, int *active, int *kit,
   return cudaGetLastError();
 }
 
-cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st) {
+cudaError_t launch_ncp_lane(const flash_scene *s, const Lane &L, const StepArgs &a, int tc, cudaStream_t st,
+                            int threads) {
   if (!L.all.blocks) return cudaSuccess;
-  k_ncp_tab<<<L.all.blocks, 256, tc ? L.ncp_smem_tc : 0, st>>>((const GroupView *)s->gtab, L.all.map, eview(s), a,
-                                                              tc);
+  const GroupView *tab = (const GroupView *)s->gtab;
+  const size_t smem = tc ? L.ncp_smem_tc : 0;
+  switch (threads > 0 ? threads : L.ncp_threads) {
+    case 128: k_ncp_tab<128><<<L.all.blocks, 128, smem, st>>>(tab, L.all.map, eview(s), a, tc); break;
+    case 256: k_ncp_tab<256><<<L.all.blocks, 256, smem, st>>>(tab, L.all.map, eview(s), a, tc); break;
+    case 512: k_ncp_tab<512><<<L.all.blocks, 512, smem, st>>>(tab, L.all.map, eview(s), a, tc); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

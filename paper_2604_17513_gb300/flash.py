@@ -34,6 +34,7 @@ METRIC_LITE, METRIC_FULL = 0, 1
 SOLVE_F32, SOLVE_F16X3, SOLVE_BF16R = 0, 1, 2
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 GROUPED_AUTO, GROUPED_OFF, GROUPED_ON = 0, 1, 2
+THREADS_TUNE = -1   # local_threads / ncp_threads: time the candidates on the first step
 
 
 class FlashError(RuntimeError):
@@ -55,7 +56,8 @@ class SceneDesc(C.Structure):
                 ("k_cap", C.c_int32), ("mode", C.c_int32), ("contact_cap", C.c_int32), ("solve", C.c_int32),
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
                 ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32),
-                ("grouped_solve", C.c_int32), ("refine_steps", C.c_int32)]
+                ("grouped_solve", C.c_int32), ("refine_steps", C.c_int32), ("local_threads", C.c_int32),
+                ("ncp_threads", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -121,6 +123,8 @@ def lib():
         L.flash_tile_widths.restype = i32
         L.flash_grouped_solve.argtypes = [vp]
         L.flash_grouped_solve.restype = i32
+        L.flash_scene_threads.argtypes = [vp, i32, C.POINTER(i32), i32]
+        L.flash_scene_threads.restype = i32
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
         L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]
@@ -168,7 +172,8 @@ class Sim:
 
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
                  warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
-                 self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO, refine_steps=1):
+                 self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO, refine_steps=1,
+                 local_threads=0, ncp_threads=0):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -205,6 +210,8 @@ class Sim:
         d.lin_iters = lin_iters
         d.grouped_solve = grouped
         d.refine_steps = refine_steps
+        d.local_threads = local_threads
+        d.ncp_threads = ncp_threads
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))
@@ -359,6 +366,17 @@ class Sim:
     def grouped_solve(self):
         """True if the lanes apply their dense inverses in one grouped launch."""
         return bool(lib().flash_grouped_solve(self._h))
+
+    def threads(self):
+        """Threads per environment in use: (local pass, one per batch lane by
+        lane; lite NCP pass, one per lane)."""
+        out = []
+        for kind in (0, 1):
+            n = lib().flash_scene_threads(self._h, kind, None, 0)
+            buf = (C.c_int32 * max(n, 1))()
+            lib().flash_scene_threads(self._h, kind, buf, n)
+            out.append(list(buf[:n]))
+        return tuple(out)
 
     def tile_widths(self):
         """Autotuned tensor-core tile width of each lane's column range."""

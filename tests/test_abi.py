@@ -70,6 +70,16 @@ def test_scene_descriptor_validation(lib):
     d.refine_steps, d.grouped_solve = 1, 3
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
     d.solve, d.refine_steps, d.grouped_solve = 0, 0, 0
+    # threads per environment: 0, tune (-1) or one of the instantiated counts
+    for field, bad in (("local_threads", 128), ("local_threads", 768), ("ncp_threads", 1024), ("ncp_threads", -2)):
+        setattr(d, field, bad)
+        assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL, (field, bad)
+        assert field.encode() in lib.flash_last_error()
+        setattr(d, field, 0)
+    d.local_threads, d.ncp_threads = flash.THREADS_TUNE, 512
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
+    lib.flash_scene_destroy(h)
+    d.local_threads, d.ncp_threads = 0, 0
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
     # a mesh with an out-of-range element index is rejected on the host
     rest = np.zeros((3, 3))

@@ -564,6 +564,44 @@ def test_grouped_solve_equals_per_template_launches(cuda, mode):
     assert np.array_equal(q_on, q_off) and np.array_equal(it_on, it_off)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_threads_per_environment_do_not_change_results(cuda, mode):
+    """Cloth and tet templates in two lanes: the local pass with 256, 512 or
+    1024 threads per environment, the NCP pass with 128, 256 or 512, and
+    both timed on the first step (FLASH_THREADS_TUNE; graphed, and eager)
+    give bit-identical states, iteration counts and residuals (one thread
+    owns each vertex and each contact run, in a fixed order, and the block
+    reductions are maxima), in both stopping modes.  The timed choice is
+    one of the candidates for every local batch and every lane."""
+    from paper_2604_17513_gb300 import flash
+    scs = scenes.mixed_batch(n_envs=24, steps=12, side_choices=(16, 20, 24), tet_targets=(250, 600))
+    kw = dict(mode=1, tol=1e-5, k_cap=40) if mode else {}
+    runs = [(0, 0, False), (256, 128, False), (1024, 512, False), (512, 256, True),
+            (flash.THREADS_TUNE, flash.THREADS_TUNE, False), (flash.THREADS_TUNE, flash.THREADS_TUNE, True)]
+    out = []
+    for lt, nt, eager in runs:
+        sim = flash.Sim(scs, solve=flash.SOLVE_F16X3, lanes=2, eager=eager, local_threads=lt, ncp_threads=nt, **kw)
+        q0, v0 = flash.state_tensors(scs, cuda)
+        sim.set_state(q0, v0)
+        sim.set_poses(flash.poses_tensor(scs, 0, cuda), which=0)
+        for s in range(8):
+            sim.set_poses(flash.poses_tensor(scs, s + 1, cuda))
+            sim.step(1)
+        it, r = sim.stats()
+        out.append((sim.get_state()[0].cpu().numpy(), it.cpu().numpy(), r.cpu().numpy(), sim.status()))
+        loc, ncp = sim.threads()
+        assert len(ncp) == 2 and len(loc) >= 2
+        if lt > 0:
+            assert set(loc) == {lt} and set(ncp) == {nt}
+        elif lt == flash.THREADS_TUNE:
+            assert set(loc) <= {256, 512, 1024} and set(ncp) <= {128, 256, 512}
+    q_ref, it_ref, r_ref, st_ref = out[0]
+    assert st_ref == 0
+    for (lt, nt, eager), (q, it, r, st) in zip(runs[1:], out[1:]):
+        assert st == st_ref and np.array_equal(q, q_ref) and np.array_equal(it, it_ref) and np.array_equal(r, r_ref), \
+            (lt, nt, eager)
+
+
 @pytest.mark.parametrize("steps_tol", [(0, 2e-2), (1, 3e-4), (2, 2e-5)])
 @pytest.mark.parametrize("dense", [False, True])
 def test_global_apply_bf16_refinement(cuda, steps_tol, dense):
