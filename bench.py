@@ -79,6 +79,8 @@ def parse():
                         "the first step)")
     p.add_argument("--ncp-threads", type=int, default=0,
                    help="lite NCP pass threads per environment: 128, 256, 512, 0 (library default) or -1 (timed)")
+    p.add_argument("--split-k", default="auto", choices=["auto", "on", "off"],
+                   help="tensor-core applies: each tile's two K halves on two CTAs (on), one CTA (off) or timed")
     p.add_argument("--clock-log", default=None,
                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     args = p.parse_args()
@@ -619,6 +621,7 @@ def main():
     mode_kw["refine_steps"] = args.refine
     mode_kw["local_threads"] = args.local_threads
     mode_kw["ncp_threads"] = args.ncp_threads
+    mode_kw["split_k"] = {"auto": flash.SPLITK_AUTO, "on": flash.SPLITK_ON, "off": flash.SPLITK_OFF}[args.split_k]
     try:
         sim = flash.Sim(sc, solve=solve, warm=warm, lanes=args.lanes, eager=args.eager, **mode_kw)
     except flash.FlashError:
@@ -891,6 +894,7 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}", "lanes": sim.lane_count(),
                        "graph": not args.eager, "tile_widths": sorted(set(sim.tile_widths())),
+                       "tile_splits": sorted(set(sim.tile_splits())),
                        "grouped_solve": sim.grouped_solve(),
                        "threads_per_env": {"local": sorted(set(sim.threads()[0])),
                                            "ncp": sorted(set(sim.threads()[1]))}},

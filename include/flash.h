@@ -161,7 +161,15 @@ typedef int32_t flash_status;
  * environments on each SM; more shorten each environment's dependent chain.
  * Results do not depend on either (each vertex and contact row is handled
  * by one thread in a fixed order; the block reductions are maxima), except
- * with self or box-feature rows, whose forces are summed with atomics. */
+ * with self or box-feature rows, whose forces are summed with atomics.
+ * split_k (tensor-core solve): each output tile of a lane's apply sums its
+ * two K halves on one CTA (FLASH_SPLITK_OFF) or on two CTAs that meet
+ * through a scratch tile (FLASH_SPLITK_ON), or whichever the autotuner
+ * times faster for each column range (FLASH_SPLITK_AUTO, 0); results do not
+ * depend on it (see flash_tile_splits). */
+#define FLASH_SPLITK_AUTO 0
+#define FLASH_SPLITK_OFF 1
+#define FLASH_SPLITK_ON 2
 #define FLASH_THREADS_TUNE (-1)
 #define FLASH_GROUPED_AUTO 0
 #define FLASH_GROUPED_OFF 1
@@ -187,6 +195,7 @@ typedef struct {
   int32_t refine_steps;
   int32_t local_threads;
   int32_t ncp_threads;
+  int32_t split_k;
 } flash_scene_desc;
 
 /* A mesh template (asset).  type: FLASH_TRI (TRI_ARAP stretch + flat-rest
@@ -402,6 +411,11 @@ int32_t flash_lane_count(const flash_scene *s);
  * into the host array out; returns how many ranges there are (0 on the
  * CUDA-core path or before finalize). */
 int32_t flash_tile_widths(const flash_scene *s, int32_t *out, int32_t max_out);
+/* For the same ranges, in the same order: 2 where the autotuner runs each
+ * output tile's two K halves on two CTAs (split-K), else 1.  Every apply
+ * sums the two K halves separately and adds them last, so results do not
+ * depend on this choice. */
+int32_t flash_tile_splits(const flash_scene *s, int32_t *out, int32_t max_out);
 /* 1 if the scene's lanes apply their dense inverses in one grouped launch
  * (flash_scene_desc.grouped_solve), else 0; 0 before finalize. */
 int32_t flash_grouped_solve(const flash_scene *s);

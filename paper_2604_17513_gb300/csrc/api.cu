@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <tuple>
 #include <utility>
 
 #include "flash_internal.cuh"
@@ -528,7 +529,7 @@ cudaError_t flush_profile(flash_scene *s) {
 // [l0, l1) (l1 < 0: all): r in FP32 (CUDA-core path) or its f16 split
 // (tensor-core path); bn is the tile width for that column range
 cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, float *out, cudaStream_t st, int l0 = 0,
-                          int l1 = -1, int bn = 0) {
+                          int l1 = -1, int bn = 0, const SplitK &sk = SplitK()) {
   const bool tc = use_tc(s);
   if (l1 < 0) l1 = g.N;
   const int c0 = 3 * l0, c1 = 3 * l1;
@@ -537,10 +538,10 @@ cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, fl
     // refine_steps corrections: out += A^-1 (rhs - A out), the residual in
     // FP32 from the element operators (launch_refine)
     auto bf_apply = [&](int mode) -> cudaError_t {   // mode 0: out = A^-1 rh; 3: out += A^-1 rh
-      if (!g.eig) return gemm_tc(g, g.inv, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true);
-      cudaError_t e = gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn, true);
+      if (!g.eig) return gemm_tc(g, g.inv, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true, sk);
+      cudaError_t e = gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn, true, sk);
       if (e == cudaSuccess) e = launch_split_rhs(g, g.y, st, l0, l1, true);
-      if (e == cudaSuccess) e = gemm_tc(g, g.V, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true);
+      if (e == cudaSuccess) e = gemm_tc(g, g.V, out, nullptr, s->done, mode, nullptr, nullptr, st, c0, c1, bn, true, sk);
       return e;
     };
     cudaError_t e = timed(s, FLASH_KIND_SOLVE, st, [&] { return bf_apply(0); });
@@ -552,14 +553,14 @@ cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, fl
   }
   if (!g.eig) {
     return timed(s, FLASH_KIND_SOLVE, st, [&] {
-      return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn)
+      return tc ? gemm_tc(g, g.inv, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn, false, sk)
                 : gemm_simt(g, g.inv, rhs32, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1);
     });
   }
   // eigen form: y = diag(1/(1 + k_e lam)) V^T rhs, out = V y
   // (the CUDA-core kernel reads its matrix transposed, so it is given V for V^T and V^T for V)
   cudaError_t e = timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn)
+    return tc ? gemm_tc(g, g.Vt, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1, bn, false, sk)
               : gemm_simt(g, g.V, rhs32, g.y, nullptr, s->done, 2, g.lam, g.kenv, st, c0, c1);
   });
   if (e != cudaSuccess) return e;
@@ -568,7 +569,7 @@ cudaError_t apply_inverse(flash_scene *s, const Group &g, const float *rhs32, fl
     if (e != cudaSuccess) return e;
   }
   return timed(s, FLASH_KIND_SOLVE, st, [&] {
-    return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn)
+    return tc ? gemm_tc(g, g.V, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1, bn, false, sk)
               : gemm_simt(g, g.Vt, g.y, out, nullptr, s->done, 0, nullptr, nullptr, st, c0, c1);
   });
 }
@@ -610,7 +611,9 @@ cudaError_t apply_lane(flash_scene *s, const Lane &L, cudaStream_t st, In in, Ou
     if (grouped && std::find(L.ga.ranges.begin(), L.ga.ranges.end(), (int)i) != L.ga.ranges.end()) continue;
     const LaneRange &r = L.ranges[i];
     Group &g = s->groups[r.group];
-    e = apply_inverse(s, g, in(g), out(g), st, r.l0, r.l1, r.tc_bn);
+    SplitK sk = L.sk;
+    sk.split = r.tc_split;
+    e = apply_inverse(s, g, in(g), out(g), st, r.l0, r.l1, r.tc_bn, sk);
   }
   return e;
 }
@@ -740,6 +743,8 @@ flash_status flash_scene_create(const flash_scene_desc *desc, flash_scene **out)
   if (desc->ncp_threads != 0 && desc->ncp_threads != FLASH_THREADS_TUNE && desc->ncp_threads != 128 &&
       desc->ncp_threads != 256 && desc->ncp_threads != 512)
     return fail(FLASH_EINVAL, "ncp_threads must be 0, -1 (tune), 128, 256 or 512");
+  if (desc->split_k < FLASH_SPLITK_AUTO || desc->split_k > FLASH_SPLITK_ON)
+    return fail(FLASH_EINVAL, "split_k must be 0 (auto), 1 (off) or 2 (on)");
   if (desc->warm < FLASH_WARM_COLD || desc->warm > FLASH_WARM_LEARNED) return fail(FLASH_EINVAL, "invalid warm start");
   if (desc->metric != FLASH_METRIC_LITE && desc->metric != FLASH_METRIC_FULL) return fail(FLASH_EINVAL, "invalid metric");
   if (desc->lin_iters < 0 || desc->lin_iters > kMaxLinIters) return fail(FLASH_EINVAL, "lin_iters must be 0..32");
@@ -936,28 +941,50 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
     }
   }
   if (use_tc(s)) {
-    // tile autotuner: each group's full column range (global applies) and
-    // each lane's range (the step), timed once per distinct column count
-    std::map<std::pair<int, int>, int> tuned;
-    auto tune = [&](int gi, int l0, int l1) -> int {
-      const auto key = std::make_pair(gi, l1 - l0);
+    // split-K scratch per lane, for the largest of its column ranges
+    for (Lane &L : s->lanes) {
+      if (s->d.split_k == FLASH_SPLITK_OFF) break;
+      size_t tiles = 0, part = 0;
+      for (const LaneRange &r : L.ranges) {
+        size_t t = 0, p = 0;
+        splitk_need(s->groups[r.group], 3 * r.l0, 3 * r.l1, &t, &p);
+        tiles = std::max(tiles, t);
+        part = std::max(part, p);
+      }
+      if (!tiles) continue;
+      FLASH_CUDA_TRY(dalloc(s, &L.sk.part, part));
+      FLASH_CUDA_TRY(dalloc(s, &L.sk.sem, tiles));
+      FLASH_CUDA_TRY(cudaMemset(L.sk.sem, 0, tiles * sizeof(int)));
+      L.sk.tiles = tiles;
+      L.sk.part_floats = part;
+    }
+    // tile autotuner: each group's full column range (global applies, one
+    // CTA per tile) and each lane's range (the step, split-K as well), timed
+    // once per distinct column count
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+    auto tune = [&](int gi, int l0, int l1, const SplitK &sk) -> std::pair<int, int> {
+      const auto key = std::make_tuple(gi, l1 - l0, sk.part ? sk.split : -1);
       auto it = tuned.find(key);
       if (it != tuned.end()) return it->second;
-      int bn = 128;
-      if (tune_gemm_tc(s->groups[gi], s->done, st, 3 * l0, 3 * l1, &bn) != cudaSuccess) bn = -1;
-      tuned[key] = bn;
-      return bn;
+      int bn = 128, split = 1;
+      if (tune_gemm_tc(s->groups[gi], s->done, st, 3 * l0, 3 * l1, &bn, &split, sk) != cudaSuccess) bn = -1;
+      tuned[key] = std::make_pair(bn, split);
+      return tuned[key];
     };
     for (size_t gi = 0; gi < s->groups.size(); gi++) {
-      const int bn = tune((int)gi, 0, s->groups[gi].N);
+      const int bn = tune((int)gi, 0, s->groups[gi].N, SplitK()).first;
       if (bn < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
       s->groups[gi].tc_bn = bn;
     }
     for (Lane &L : s->lanes)
       for (LaneRange &r : L.ranges) {
-        const int bn = tune(r.group, r.l0, r.l1);
-        if (bn < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
-        r.tc_bn = bn;
+        // FLASH_SPLITK_ON times the widths as split-K only
+        SplitK sk = L.sk;
+        sk.split = s->d.split_k == FLASH_SPLITK_ON ? 2 : 0;
+        const auto c = tune(r.group, r.l0, r.l1, sk);
+        if (c.first < 0) return fail(FLASH_ECUDA, "tile autotuner failed");
+        r.tc_bn = c.first;
+        r.tc_split = c.second;
       }
     if (s->lanes.size() > 1) {
       // lanes run their contractions at the same time, which the per-range
@@ -987,24 +1014,32 @@ flash_status flash_scene_finalize(flash_scene *s, void *stream) {
         *best_ms = t;
         return cudaSuccess;
       };
-      std::vector<int> chosen;
+      std::vector<std::pair<int, int>> chosen;
       for (const Lane &L : s->lanes)
-        for (const LaneRange &r : L.ranges) chosen.push_back(r.tc_bn);
+        for (const LaneRange &r : L.ranges) chosen.push_back(std::make_pair(r.tc_bn, r.tc_split));
       float best = 0.f;
       FLASH_CUDA_TRY(phase_ms(&best));
-      for (int bn : {64, 128, 176, 256}) {
-        for (Lane &L : s->lanes)
-          for (LaneRange &r : L.ranges) r.tc_bn = bn;
-        float t = 0.f;
-        FLASH_CUDA_TRY(phase_ms(&t));
-        if (t < best) {
-          best = t;
-          chosen.assign(chosen.size(), bn);
+      const int split0 = s->d.split_k == FLASH_SPLITK_ON ? 2 : 1, split1 = s->d.split_k == FLASH_SPLITK_AUTO ? 2 : split0;
+      for (int split = split0; split <= split1; split++)
+        for (int bn : {64, 128, 176, 256}) {
+          for (Lane &L : s->lanes)
+            for (LaneRange &r : L.ranges) {
+              r.tc_bn = bn;
+              r.tc_split = split;
+            }
+          float t = 0.f;
+          FLASH_CUDA_TRY(phase_ms(&t));
+          if (t < best) {
+            best = t;
+            chosen.assign(chosen.size(), std::make_pair(bn, split));
+          }
         }
-      }
       size_t k = 0;
       for (Lane &L : s->lanes)
-        for (LaneRange &r : L.ranges) r.tc_bn = chosen[k++];
+        for (LaneRange &r : L.ranges) {
+          r.tc_bn = chosen[k].first;
+          r.tc_split = chosen[k++].second;
+        }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       s->launches = launches0;
@@ -1675,6 +1710,17 @@ int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, in
       k++;
     }
   }
+  return k;
+}
+
+int32_t flash_tile_splits(const flash_scene *s, int32_t *out, int32_t max_out) {
+  if (!s || !s->finalized || !use_tc(s)) return 0;
+  int32_t k = 0;
+  for (const Lane &L : s->lanes)
+    for (const LaneRange &r : L.ranges) {
+      if (out && k < max_out) out[k] = r.tc_split;
+      k++;
+    }
   return k;
 }
 

@@ -125,6 +125,15 @@ struct Group {
 }  // namespace flash
 
 namespace flash {
+// Split-K launch of a tensor-core apply: split 2 runs the two K halves of
+// each tile on two CTAs, which meet through the scratch partial tiles and
+// per-tile arrival counters (zero between launches); split 1 needs none.
+struct SplitK {
+  int split = 1;
+  float *part = nullptr;   // [tiles][2][BN][128]
+  int *sem = nullptr;      // [tiles]
+  size_t tiles = 0, part_floats = 0;
+};
 // One table launch over the environments of several groups: CTA b works on
 // environment map[b].y of group map[b].x (a row of the scene's group table).
 struct Batch {
@@ -138,6 +147,7 @@ struct Batch {
 struct LaneRange {
   int group = 0, l0 = 0, l1 = 0;
   int tc_bn = 128;        // tensor-core tile width for this column range (autotuned)
+  int tc_split = 1;       // 2: each tile's K halves on two CTAs (autotuned)
 };
 // A lane: a partition of the environments stepped on its own stream, so
 // that the wave tails of one lane's kernels overlap other lanes' work.
@@ -160,6 +170,7 @@ struct Lane {
   std::vector<Batch> local;     // local pass, by element type and shared-memory class
   size_t ncp_smem_tc = 0;
   int ncp_threads = 256;        // lite NCP pass: threads per CTA, one environment each (128, 256 or 512)
+  SplitK sk;                    // split-K scratch of the lane's applies (they run in stream order)
   GroupedApply ga;
 };
 }  // namespace flash
@@ -342,7 +353,9 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
 // epilogue mode 3: out += acc (a refinement step's correction)
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                     const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0,
-                    bool bf = false);
+                    bool bf = false, const SplitK &sk = SplitK());
+// scratch a split-K apply of columns [c0, c1) of g needs at any tile width
+void splitk_need(const Group &g, int c0, int c1, size_t *tiles, size_t *part_floats);
 bool tc_available();
 // grouped apply (one launch over several groups' dense applies, tile width kGroupedBN)
 constexpr int kGroupedBN = 64;
@@ -350,8 +363,10 @@ size_t gemm_problem_bytes();
 int gemm_problem(void *dst, const Group &g, const SolveMat &M, int c0, int c1, int tile0);
 cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *const *outs, const int *done, int *status,
                             cudaStream_t st);
-// time the tile widths on columns [c0, c1) of the group; fastest in *bn
-cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn);
+// time the tile widths (and, given scratch, split-K) on columns [c0, c1) of
+// the group; fastest in *bn and *split
+cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn, int *split,
+                         const SplitK &sk = SplitK());
 cudaError_t gemm_simt_raw(const float *Ainv, const float *rhs, float *out, int n_pad, int cols, cudaStream_t st);
 
 // setup (setup_kernels.cu) ---------------------------------------------------

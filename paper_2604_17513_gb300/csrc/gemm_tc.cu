@@ -10,9 +10,18 @@
 // correction form q^k = q^{k-1} + A^-1 r, whose error against the FP64
 // oracle must stay below 1e-5 m.
 //
-// Structure (one 128 x BN output tile per CTA, 128 threads; BN = 64, 128,
-// 176 or 256 columns, chosen per group by timing the candidates on the
-// group's own matrix when the scene is finalised):
+// K halves: every apply sums k < n/2 and k >= n/2 into two separate FP32
+// accumulators and adds the two in the epilogue.  A tile runs either on one
+// CTA (both accumulators in its TMEM) or on two CTAs, one half each
+// (split-K): each writes its accumulator to a global scratch tile and counts
+// itself in the tile's arrival counter, and the second to arrive adds the
+// first's partial to its own.  FP32 addition of two values is commutative,
+// so both forms give bit-identical results and the choice can be timed.
+//
+// Structure (one 128 x BN output tile per CTA or CTA pair, 128 threads;
+// BN = 64, 128, 176 or 256 columns and the split, chosen per column range
+// by timing the candidates on the group's own matrix when the scene is
+// finalised):
 //   warp 0 lane 0  TMA producer: 4 tiles (A hi/lo 128 x 64, B hi/lo BN x 64
 //                  f16) per k-block into a 2..4-stage ring, 128B swizzle; the
 //                  last column tile may run past the matrix (zero fill)
@@ -112,7 +121,8 @@ template <int BN> struct TileCfg {
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
   static constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES > 4 ? 4 : (227 * 1024 - 2048) / STAGE_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-  static constexpr int TMEM_COLS = BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr int TMEM_COLS = BN <= 64 ? 64 : BN <= 128 ? 128 : 256;          // one accumulator
+  static constexpr int TMEM_COLS2 = 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;  // both K halves
   static_assert(BN % 16 == 0 && BN >= 64 && BN <= 256, "tcgen05 M128 needs N in [16, 256], multiple of 16");
   static_assert(TILE_B % 1024 == 0, "128B-swizzled tiles start on 1 KiB boundaries");
   static_assert(STAGES >= 2, "ring needs two stages");
@@ -139,56 +149,89 @@ template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t
       : "r"(taddr));
 }
 
-// epilogue of X columns starting at tile column c0: rescale and store the live ones
+// epilogue of X accumulated columns starting at tile column c0: rescale and
+// store the live ones
 template <int X>
-__device__ __forceinline__ void store_cols(uint32_t taddr, float *o, const float *wv, int n_pad, int mode, float lr,
+__device__ __forceinline__ void store_cols(const float *v, float *o, const float *wv, int n_pad, int mode, float lr,
                                            const float *col_scale, const float *col_k, const int *col_live, int c0) {
-  uint32_t v[X];
-  tmem_ld<X>(taddr, v);
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
   if (mode == 2) {
 #pragma unroll
     for (int j = 0; j < X; j++)
-      if (col_live[c0 + j])
-        o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j] / (1.f + col_k[c0 + j] * lr);
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] = v[j] * col_scale[c0 + j] / (1.f + col_k[c0 + j] * lr);
   } else if (mode == 0) {
 #pragma unroll
     for (int j = 0; j < X; j++)
-      if (col_live[c0 + j]) o[(size_t)j * n_pad] = __uint_as_float(v[j]) * col_scale[c0 + j];
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] = v[j] * col_scale[c0 + j];
   } else if (mode == 3) {   // accumulate: a refinement step's correction
 #pragma unroll
     for (int j = 0; j < X; j++)
-      if (col_live[c0 + j]) o[(size_t)j * n_pad] += __uint_as_float(v[j]) * col_scale[c0 + j];
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] += v[j] * col_scale[c0 + j];
   } else {
     float prev[X];
 #pragma unroll
     for (int j = 0; j < X; j++) prev[j] = col_live[c0 + j] ? o[(size_t)j * n_pad] + wv[(size_t)j * n_pad] : 0.f;
 #pragma unroll
     for (int j = 0; j < X; j++)
-      if (col_live[c0 + j]) o[(size_t)j * n_pad] = prev[j] + __uint_as_float(v[j]) * col_scale[c0 + j];
+      if (col_live[c0 + j]) o[(size_t)j * n_pad] = prev[j] + v[j] * col_scale[c0 + j];
   }
 }
 
+// The tile's sum of both K halves for X columns at tile column c0 of this
+// thread's row: both TMEM accumulators (one CTA), or this CTA's accumulator
+// plus the other CTA's partial from the scratch tile (split-K, last arrival).
+template <int X>
+__device__ __forceinline__ void tile_sum(uint32_t tbase, int two_acc, int bn, const float *other, float *v) {
+  uint32_t a[X];
+  tmem_ld<X>(tbase, a);
+  if (two_acc) {
+    uint32_t b[X];
+    tmem_ld<X>(tbase + (uint32_t)bn, b);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < X; j++) v[j] = __uint_as_float(a[j]) + __uint_as_float(b[j]);
+  } else {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < X; j++) v[j] = __uint_as_float(a[j]) + __ldcg(other + (size_t)j * BM);
+  }
+}
+
+// this CTA's accumulator for X columns at tile column c0 into the scratch tile
+template <int X>
+__device__ __forceinline__ void tile_spill(uint32_t tbase, float *mine) {
+  uint32_t a[X];
+  tmem_ld<X>(tbase, a);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < X; j++) mine[(size_t)j * BM] = __uint_as_float(a[j]);
+}
+
 // One 128 x BN output tile at rows m0.., columns j0.. (tensor maps in
-// parameter or global memory).
+// parameter or global memory).  nsplit = 1: both K halves on this CTA;
+// nsplit = 2: half ksplit only, with the scratch tiles part (two per tile,
+// [2][BN][128] floats) and the arrival counter sem of tile tile_id.
 template <int BN, bool BF = false>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensorMap *pAl, const CUtensorMap *pBh,
                                           const CUtensorMap *pBl, float *__restrict__ out,
                                           const float *__restrict__ W, const float *__restrict__ rscale,
                                           const int *__restrict__ done, const int *__restrict__ genv, int *status,
                                           int n_pad, int m0, int j0, int cols, float a_unscale, int mode,
-                                          const float *__restrict__ lam, const float *__restrict__ kenv) {
+                                          const float *__restrict__ lam, const float *__restrict__ kenv,
+                                          int nsplit = 1, int ksplit = 0, float *part = nullptr, int *sem = nullptr,
+                                          int tile_id = 0) {
   using Cfg = TileCfg<BN>;
   constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, TILE_B = Cfg::TILE_B;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int fail_sh;
+  __shared__ int fail_sh, last_sh;
   __shared__ float col_scale[BN];
   __shared__ float col_k[BN];
   __shared__ int col_live[BN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int KB = n_pad / BK;
+  const int KB = n_pad / BK, KH = KB / 2;   // n_pad is a multiple of 128: KB is even
+  const int kb0 = nsplit == 2 ? ksplit * KH : 0, kb1 = nsplit == 2 ? kb0 + KH : KB;
+  const uint32_t tmem_cols = nsplit == 2 ? Cfg::TMEM_COLS : Cfg::TMEM_COLS2;
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
   // skip tiles whose environments have all converged (their columns are
@@ -209,7 +252,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(Cfg::TMEM_COLS));
+                 "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -219,12 +262,12 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int kb = 0;
-    for (; kb < KB; kb++) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1)) { atomicExch(&fail_sh, 1); break; }
+    int i = 0;   // k-blocks issued
+    for (; kb0 + i < kb1; i++) {
+      const int s = i % STAGES;
+      if (!mbar_wait(&empty_bar[s], ((i / STAGES) & 1) ^ 1)) { atomicExch(&fail_sh, 1); break; }
       uint8_t *st = smem + s * STAGE_BYTES;
-      const int k0 = kb * BK;
+      const int k0 = (kb0 + i) * BK;
       if constexpr (BF) {   // one bf16 product: the hi slots of the stage only
         mbar_expect_tx(&full_bar[s], TILE_A + TILE_B);
         tma_load_2d(st, pAh, &full_bar[s], k0, m0);
@@ -238,24 +281,28 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
       }
     }
     // drain: wait until every stage this thread armed has landed (bounded)
-    for (int t = max(0, kb - STAGES); t < kb; t++) mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1);
+    for (int t = max(0, i - STAGES); t < i; t++) mbar_wait(&full_bar[t % STAGES], (t / STAGES) & 1);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: k-blocks below KH into the first
+    // accumulator, the others into the second (one CTA), or this CTA's half
+    // into its only accumulator (split-K)
     constexpr uint32_t idesc = idesc_f16(BM, BN, BF);
     bool ok = true;
-    for (int kb = 0; kb < KB; kb++) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1)) { atomicExch(&fail_sh, 1); ok = false; break; }
+    for (int i = 0; kb0 + i < kb1; i++) {
+      const int s = i % STAGES, kb = kb0 + i;
+      if (!mbar_wait(&full_bar[s], (i / STAGES) & 1)) { atomicExch(&fail_sh, 1); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
       const uint32_t ah = base, al = base + TILE_A, bh = base + 2 * TILE_A, bl = base + 2 * TILE_A + TILE_B;
+      const uint32_t acc = tmem + ((nsplit == 1 && kb >= KH) ? (uint32_t)BN : 0u);
+      const bool first = kb == kb0 || (nsplit == 1 && kb == KH);
 #pragma unroll
       for (int ks = 0; ks < BK / 16; ks++) {
         const uint32_t off = ks * 32;   // 16 f16 / bf16 along K inside the 128-byte swizzle row
-        mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, (kb | ks) ? 1u : 0u);
+        mma_f16(acc, smem_desc(ah + off), smem_desc(bh + off), idesc, (first && ks == 0) ? 0u : 1u);
         if constexpr (!BF) {
-          mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-          mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+          mma_f16(acc, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+          mma_f16(acc, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
         }
       }
       mma_commit(&empty_bar[s]);
@@ -276,41 +323,74 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *pAh, const CUtensor
   bool ok = mbar_wait(&done_bar, 0);
   if (!ok) atomicExch(&fail_sh, 1);
   __syncthreads();
+  const int rl = warp * 32 + lane;   // this thread's row of the tile (its TMEM lane)
+  const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+  const float *other = nullptr;
+  bool write_out = true;
+  if (nsplit == 2) {
+    // split-K: spill this half, count the arrival; the second CTA to arrive
+    // owns the output.  A CTA that failed still counts itself, so the
+    // counter is back at zero for the next launch.
+    float *mine = part + ((size_t)(2 * tile_id + ksplit) * BN) * BM + rl;
+    if (!fail_sh) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+      for (int c0 = 0; c0 + 32 <= BN; c0 += 32) tile_spill<32>(tbase + (uint32_t)c0, mine + (size_t)c0 * BM);
+      if constexpr (BN % 32 == 16) tile_spill<16>(tbase + (uint32_t)(BN - 16), mine + (size_t)(BN - 16) * BM);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int old = atomicAdd(sem + tile_id, 1);
+      last_sh = old == 1;
+      if (old == 1) sem[tile_id] = 0;
+    }
+    __syncthreads();
+    write_out = last_sh != 0;
+    if (write_out) __threadfence();
+    other = part + ((size_t)(2 * tile_id + 1 - ksplit) * BN) * BM + rl;
+  }
   if (fail_sh) {
     if (threadIdx.x == 0) atomicOr(status, 1 << 11);
-  } else {
+  } else if (write_out) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int row = m0 + warp * 32 + lane;
+    const int row = m0 + rl;
     const float lr = mode == 2 ? lam[row] : 0.f;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    const int two = nsplit == 1;
+    float v[32];
 #pragma unroll 1
-    for (int c0 = 0; c0 + 32 <= BN; c0 += 32)
-      store_cols<32>(tbase + (uint32_t)c0, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
+    for (int c0 = 0; c0 + 32 <= BN; c0 += 32) {
+      tile_sum<32>(tbase + (uint32_t)c0, two, BN, other ? other + (size_t)c0 * BM : nullptr, v);
+      store_cols<32>(v, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
                      n_pad, mode, lr, col_scale, col_k, col_live, c0);
+    }
     if constexpr (BN % 32 == 16) {
       constexpr int c0 = BN - 16;
-      store_cols<16>(tbase + (uint32_t)c0, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
+      tile_sum<16>(tbase + (uint32_t)c0, two, BN, other ? other + (size_t)c0 * BM : nullptr, v);
+      store_cols<16>(v, out + (size_t)(j0 + c0) * n_pad + row, W ? W + (size_t)(j0 + c0) * n_pad + row : nullptr,
                      n_pad, mode, lr, col_scale, col_k, col_live, c0);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
   }
 }
 
 // One group's apply: tile (x, y) covers rows 128 y.. and columns
-// c_begin + BN x .. of [c_begin, cols).
+// c_begin + BN x .. of [c_begin, cols); z is the K half with gridDim.z = 2.
 template <int BN, bool BF = false>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float *__restrict__ out, const float *__restrict__ W, const float *__restrict__ rscale,
               const int *__restrict__ done, const int *__restrict__ genv, int *status, int n_pad, int c_begin,
-              int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv) {
+              int cols, float a_unscale, int mode, const float *__restrict__ lam, const float *__restrict__ kenv,
+              float *part, int *sem) {
   gemm_tile<BN, BF>(&tmAh, &tmAl, &tmBh, &tmBl, out, W, rscale, done, genv, status, n_pad, blockIdx.y * BM,
-                    c_begin + blockIdx.x * BN, cols, a_unscale, mode, lam, kenv);
+                    c_begin + blockIdx.x * BN, cols, a_unscale, mode, lam, kenv, (int)gridDim.z, (int)blockIdx.z, part,
+                    sem, (int)(blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 // One apply of several groups in one launch (uneven batches: every mesh
@@ -380,7 +460,7 @@ namespace {
 
 template <int BN, bool BF>
 cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                        const float *lam, const float *kenv, cudaStream_t st, int c0, int c1) {
+                        const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, const SplitK &sk) {
   using Cfg = TileCfg<BN>;
   static bool configured = false;
   if (!configured) {
@@ -403,31 +483,35 @@ cudaError_t launch_tile(const Group &g, const SolveMat &M, float *out, const flo
   }
   // column tiles cover the live columns; the last may run past the
   // matrix (TMA fills zeros, the epilogue stores only columns < cols)
-  dim3 grid((c1 - c0 + BN - 1) / BN, g.n_pad / BM);
+  const int split = sk.split == 2 ? 2 : 1;
+  dim3 grid((c1 - c0 + BN - 1) / BN, g.n_pad / BM, split);
+  if (split == 2 && (!sk.part || !sk.sem || (size_t)grid.x * grid.y > sk.tiles ||
+                     (size_t)grid.x * grid.y * 2 * BN * BM > sk.part_floats))
+    return cudaErrorInvalidValue;
   k_gemm_tc<BN, BF><<<grid, 128, Cfg::SMEM_BYTES, st>>>(tmAh, tmAl, tmBh, tmBl, out, w, g.rscale, done, g.genv,
                                                          g.status, g.n_pad, c0, c1, ldexpf(1.f, -M.exp), mode, lam,
-                                                         kenv);
+                                                         kenv, sk.part, sk.sem);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bn(int bn, const Group &g, const SolveMat &M, float *out, const float *w, const int *done,
                       int mode, const float *lam, const float *kenv, cudaStream_t st, int c0, int c1,
-                      bool bf = false) {
+                      bool bf = false, const SplitK &sk = SplitK()) {
   if (c1 < 0) c1 = g.cols;
   if (c0 < 0 || c1 > g.cols || c0 >= c1) return c0 == c1 ? cudaSuccess : cudaErrorInvalidValue;
   if (bf) {
     switch (bn) {
-      case 64: return launch_tile<64, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-      case 176: return launch_tile<176, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-      case 256: return launch_tile<256, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-      default: return launch_tile<128, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+      case 64: return launch_tile<64, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+      case 176: return launch_tile<176, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+      case 256: return launch_tile<256, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+      default: return launch_tile<128, true>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
     }
   }
   switch (bn) {
-    case 64: return launch_tile<64, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    case 176: return launch_tile<176, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    case 256: return launch_tile<256, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
-    default: return launch_tile<128, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1);
+    case 64: return launch_tile<64, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+    case 176: return launch_tile<176, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+    case 256: return launch_tile<256, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
+    default: return launch_tile<128, false>(g, M, out, w, done, mode, lam, kenv, st, c0, c1, sk);
   }
 }
 
@@ -474,15 +558,26 @@ cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *cons
 }
 
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
-                    const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn, bool bf) {
-  return launch_bn(bn > 0 ? bn : g.tc_bn, g, M, out, w, done, mode, lam, kenv, st, c0, c1, bf);
+                    const float *lam, const float *kenv, cudaStream_t st, int c0, int c1, int bn, bool bf,
+                    const SplitK &sk) {
+  return launch_bn(bn > 0 ? bn : g.tc_bn, g, M, out, w, done, mode, lam, kenv, st, c0, c1, bf, sk);
 }
 
-// Tile autotuner: time each candidate tile width on the group's own matrix
-// and column count (the right-hand side is whatever the group holds, zeros
-// at setup) and keep the fastest.  Which width wins depends on how the
-// 128 x BN tiles of the group fill the SMs.
-cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn_out) {
+// Scratch of a split-K apply of columns [c0, c1) of group g, any tile width:
+// two [BN][128] partial tiles and one arrival counter per tile.
+void splitk_need(const Group &g, int c0, int c1, size_t *tiles, size_t *part_floats) {
+  const size_t ty = (size_t)g.n_pad / BM, cols = (size_t)(c1 - c0);
+  *tiles = ((cols + 63) / 64) * ty;
+  *part_floats = 2 * (cols + 255) * ty * BM;
+}
+
+// Tile autotuner: time each candidate tile width (and, with split-K scratch,
+// each width run as two K halves on two CTAs) on the group's own matrix and
+// column count (the right-hand side is whatever the group holds, zeros at
+// setup) and keep the fastest.  Which wins depends on how the tiles of the
+// group fill the SMs.
+cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c0, int c1, int *bn_out,
+                         int *split_out, const SplitK &sk) {
   const SolveMat &M = g.eig ? g.Vt : g.inv;
   const int cand[] = {64, 128, 176, 256};
   cudaEvent_t e0, e1;
@@ -490,26 +585,34 @@ cudaError_t tune_gemm_tc(const Group &g, const int *done, cudaStream_t st, int c
   if (e != cudaSuccess) return e;
   if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
   float best = 1e30f;
-  int best_bn = 128;
-  for (int bn : cand) {
-    if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1)) != cudaSuccess) break;
-    float t_min = 1e30f;
-    for (int r = 0; r < 5 && e == cudaSuccess; r++) {
-      // one launch per measurement; the minimum is the least disturbed
-      cudaEventRecord(e0, st);
-      e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1);
-      cudaEventRecord(e1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-      t_min = fminf(t_min, ms);
+  int best_bn = 128, best_split = 1;
+  // sk.split: 0 times both forms, 2 split-K only; no scratch: one CTA per tile
+  const int min_split = sk.part && sk.sem && sk.split == 2 ? 2 : 1;
+  const int max_split = sk.part && sk.sem ? 2 : 1;
+  for (int split = min_split; split <= max_split && e == cudaSuccess; split++)
+    for (int bn : cand) {
+      SplitK k = sk;
+      k.split = split;
+      if ((e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1, false, k)) != cudaSuccess)
+        break;
+      float t_min = 1e30f;
+      for (int r = 0; r < 5 && e == cudaSuccess; r++) {
+        // one launch per measurement; the minimum is the least disturbed
+        cudaEventRecord(e0, st);
+        e = launch_bn(bn, g, M, g.w, nullptr, done, 0, nullptr, nullptr, st, c0, c1, false, k);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        t_min = fminf(t_min, ms);
+      }
+      if (e != cudaSuccess) break;
+      if (t_min < best) { best = t_min; best_bn = bn; best_split = split; }
     }
-    if (e != cudaSuccess) break;
-    if (t_min < best) { best = t_min; best_bn = bn; }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *bn_out = best_bn;
+  if (split_out) *split_out = best_split;
   return e;
 }
 

@@ -35,6 +35,7 @@ SOLVE_F32, SOLVE_F16X3, SOLVE_BF16R = 0, 1, 2
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 GROUPED_AUTO, GROUPED_OFF, GROUPED_ON = 0, 1, 2
 THREADS_TUNE = -1   # local_threads / ncp_threads: time the candidates on the first step
+SPLITK_AUTO, SPLITK_OFF, SPLITK_ON = 0, 1, 2
 
 
 class FlashError(RuntimeError):
@@ -57,7 +58,7 @@ class SceneDesc(C.Structure):
                 ("warm", C.c_int32), ("lanes", C.c_int32), ("eager", C.c_int32), ("metric", C.c_int32),
                 ("lin_iters", C.c_int32), ("self_collide", C.c_int32), ("obstacle_features", C.c_int32),
                 ("grouped_solve", C.c_int32), ("refine_steps", C.c_int32), ("local_threads", C.c_int32),
-                ("ncp_threads", C.c_int32)]
+                ("ncp_threads", C.c_int32), ("split_k", C.c_int32)]
 
 
 class MeshDesc(C.Structure):
@@ -121,6 +122,8 @@ def lib():
         L.flash_lane_count.restype = i32
         L.flash_tile_widths.argtypes = [vp, C.POINTER(i32), i32]
         L.flash_tile_widths.restype = i32
+        L.flash_tile_splits.argtypes = [vp, C.POINTER(i32), i32]
+        L.flash_tile_splits.restype = i32
         L.flash_grouped_solve.argtypes = [vp]
         L.flash_grouped_solve.restype = i32
         L.flash_scene_threads.argtypes = [vp, i32, C.POINTER(i32), i32]
@@ -173,7 +176,7 @@ class Sim:
     def __init__(self, scenes, solve=SOLVE_F32, mode=None, k_max=None, k_min=None, k_cap=None, tol=None,
                  warm=WARM_COLD, contact_cap=None, lanes=0, eager=False, metric=0, lin_iters=10,
                  self_collision=None, obstacle_features=None, grouped=GROUPED_AUTO, refine_steps=1,
-                 local_threads=0, ncp_threads=0):
+                 local_threads=0, ncp_threads=0, split_k=SPLITK_AUTO):
         if isinstance(scenes, _sc.Scene):
             scenes = [scenes]
         self.scenes = scenes
@@ -212,6 +215,7 @@ class Sim:
         d.refine_steps = refine_steps
         d.local_threads = local_threads
         d.ncp_threads = ncp_threads
+        d.split_k = split_k
         self.desc = d
         self._h = C.c_void_p()
         _check(lib().flash_scene_create(C.byref(d), C.byref(self._h)))
@@ -383,6 +387,13 @@ class Sim:
         n = lib().flash_tile_widths(self._h, None, 0)
         out = (C.c_int32 * max(n, 1))()
         lib().flash_tile_widths(self._h, out, n)
+        return list(out[:n])
+
+    def tile_splits(self):
+        """Per lane column range: 2 where each tile's K halves run on two CTAs."""
+        n = lib().flash_tile_splits(self._h, None, 0)
+        out = (C.c_int32 * max(n, 1))()
+        lib().flash_tile_splits(self._h, out, n)
         return list(out[:n])
 
     def warmstart(self, params=None, mode=WARM_LEARNED, use_dq=False, normal_only=False, bounds=None):

@@ -80,6 +80,13 @@ def test_scene_descriptor_validation(lib):
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
     lib.flash_scene_destroy(h)
     d.local_threads, d.ncp_threads = 0, 0
+    d.split_k = 3
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.EINVAL
+    assert b"split_k" in lib.flash_last_error()
+    d.split_k = flash.SPLITK_ON
+    assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
+    lib.flash_scene_destroy(h)
+    d.split_k = 0
     assert lib.flash_scene_create(C.byref(d), C.byref(h)) == flash.OK
     # a mesh with an out-of-range element index is rejected on the host
     rest = np.zeros((3, 3))

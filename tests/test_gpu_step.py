@@ -602,6 +602,42 @@ def test_threads_per_environment_do_not_change_results(cuda, mode):
             (lt, nt, eager)
 
 
+@pytest.mark.parametrize("case", ["cloth_tol", "tet_eigen", "tet_bf16r"])
+def test_split_k_does_not_change_results(cuda, case):
+    """Every tensor-core apply sums the two K halves of each output tile
+    separately and adds them last, on one CTA or, split-K, on two CTAs that
+    meet through a scratch tile: both forms, and the autotuner's mix of them
+    over lanes, give bit-identical states and iteration counts (dense
+    inverse in tolerance mode, the eigen form's two contractions, the bf16
+    solve with refinement)."""
+    from paper_2604_17513_gb300 import flash
+    if case == "cloth_tol":
+        sc = scenes.cloth_gripper(n_envs=200, n_side=16, side=0.25, steps=12)
+        kw = dict(solve=flash.SOLVE_F16X3, mode=flash.MODE_TOL, tol=1e-5, k_cap=20)
+    else:
+        sc = scenes.tet_squeeze(n_envs=96, steps=12)
+        kw = dict(solve=flash.SOLVE_BF16R if case == "tet_bf16r" else flash.SOLVE_F16X3)
+    out = []
+    for split, lanes in ((flash.SPLITK_OFF, 1), (flash.SPLITK_ON, 1), (flash.SPLITK_ON, 3), (flash.SPLITK_AUTO, 2)):
+        sim = flash.Sim(sc, lanes=lanes, split_k=split, **kw)
+        if split != flash.SPLITK_AUTO:
+            assert set(sim.tile_splits()) == {2 if split == flash.SPLITK_ON else 1}
+        else:
+            assert set(sim.tile_splits()) <= {1, 2}
+        q0, v0 = flash.state_tensors(sc, cuda)
+        sim.set_state(q0, v0)
+        sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        for s in range(8):
+            sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            sim.step(1)
+        it, r = sim.stats()
+        out.append((sim.get_state()[0].cpu().numpy(), it.cpu().numpy(), sim.status()))
+    q0_, it0, st0 = out[0]
+    assert st0 == 0 and np.isfinite(q0_).all()
+    for q, it, st in out[1:]:
+        assert st == st0 and np.array_equal(q, q0_) and np.array_equal(it, it0)
+
+
 @pytest.mark.parametrize("steps_tol", [(0, 2e-2), (1, 3e-4), (2, 2e-5)])
 @pytest.mark.parametrize("dense", [False, True])
 def test_global_apply_bf16_refinement(cuda, steps_tol, dense):
