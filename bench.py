@@ -180,13 +180,24 @@ def load_peaks():
         return {}
 
 
-def traffic_for(kernel):
+def traffic_key(args):
+    """Workload key of the committed DRAM captures (profiles/traffic.json):
+    the workload's name at its default mesh size, else none."""
+    if args.workload == "cloth_gripper" and args.side != 32:
+        return None
+    return args.workload
+
+
+def traffic_for(kernel, workload):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
-    None if the kernel source changed since the counters were taken."""
+    None if it was captured on another workload or the kernel source changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))[kernel]
     except Exception:
+        return None
+    if d.get("workload_key") != workload:
         return None
     src = os.path.join(ROOT, d["source"])
     try:
@@ -559,7 +570,7 @@ def run_render(args, rank, world, local):
             "kernel": {"resolve": "k_rc_resolve", "tri": "k_rc_tri"}[dom], "algorithmic_bytes_per_launch": per,
             "avg_launch_us": d_ms / max(d_n, 1) * 1e3, "launches": d_n,
             "peak_source": "measured HBM copy bandwidth",
-            "traffic": scaled_traffic(traffic_for("rc_" + dom), n_envs)}
+            "traffic": scaled_traffic(traffic_for("rc_" + dom, traffic_key(args)), n_envs)}
     tot = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(tot, 1e-12)} for k, v in prof.items()}
     if rank == 0:
@@ -841,8 +852,8 @@ def main():
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
         roof["kernel"] = "global solve (dense A^-1 apply)"
         roof["algorithmic_flops_per_launch"] = flops / max(d_n, 1)
-        roof["traffic"] = scaled_traffic(traffic_for("solve_f16x3" if solve == flash.SOLVE_F16X3 else "solve_f32"),
-                                         N * passes * prof_steps / max(d_n, 1))
+        roof["traffic"] = scaled_traffic(traffic_for("solve_f16x3" if solve == flash.SOLVE_F16X3 else "solve_f32",
+                                                     traffic_key(args)), N * passes * prof_steps / max(d_n, 1))
     else:
         # data-movement roofline with the algorithmic bytes of each kernel per
         # environment pass (n vertices, C contacts), each term a stream the
@@ -863,7 +874,7 @@ def main():
                 "env_passes": N * passes * prof_steps,
                 "algorithmic_bytes_per_launch": b / max(d_n, 1), "mean_contacts_per_env": C,
                 "peak_source": "measured HBM copy bandwidth",
-                "traffic": scaled_traffic(traffic_for(dom), N * passes * prof_steps / max(d_n, 1))}
+                "traffic": scaled_traffic(traffic_for(dom, traffic_key(args)), N * passes * prof_steps / max(d_n, 1))}
     roof["lanes"] = 1
     roof["note_lanes"] = "profiled in a one-lane copy of the scene: no launch overlaps another"
     roof["frac"] = roof["achieved"] / roof["peak"]
