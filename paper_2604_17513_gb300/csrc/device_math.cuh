@@ -203,9 +203,12 @@ __device__ __forceinline__ void closest_rot33_jacobi(const float *F, float *R);
 // the closest rotation is the orthogonal polar factor, reached by the
 // scaled Newton iteration X <- (z X + X^-T / z) / 2 from X = F (Higham's
 // polar iteration: quadratic convergence, (1,F)-norm scaling
-// z = sqrt(|X^-1|_F / |X|_F) in the first two steps); six steps take a
-// strain of tens of percent to FP32 precision with about a third of the
-// operations of the Jacobi eigen-decomposition.  Nearly singular or
+// z = sqrt(|X^-1|_F / |X|_F) in the first two steps); at most six steps
+// take a strain of tens of percent to FP32 precision with about a third of
+// the operations of the Jacobi eigen-decomposition.  From the third step on
+// the iteration stops once no entry moved by more than 5e-7 (four ulps of
+// a rotation's entries): the iterate is then at the rounding level, where a
+// further step only moves it within that noise.  Nearly singular or
 // inverted F (det F <= 1e-2 (|F|_F / sqrt 3)^3) take the Jacobi path,
 // which handles rank deficiency and reflections.
 __device__ __forceinline__ void closest_rot33(const float *F, float *R) {
@@ -249,8 +252,14 @@ __device__ __forceinline__ void closest_rot33(const float *F, float *R) {
       a = 0.5f * z;
       b = 0.5f / z;
     }
+    float dmax = 0.f;
 #pragma unroll
-    for (int t = 0; t < 9; t++) X[t] = a * X[t] + b * Y[t];
+    for (int t = 0; t < 9; t++) {
+      const float xn = a * X[t] + b * Y[t];
+      dmax = fmaxf(dmax, fabsf(xn - X[t]));
+      X[t] = xn;
+    }
+    if (it >= 2 && dmax <= 5e-7f) break;
   }
 #pragma unroll
   for (int t = 0; t < 9; t++) R[t] = X[t];
