@@ -764,8 +764,19 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         v_e2e, _ = aggregate(e0.elapsed_time(e1) / args.steps, conv_e.item() / args.steps, world, dev)
+        # the read-back alone: device-to-host copy rate into pinned memory
+        qd, _ = sim.get_state()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record()
+        for i in range(5):
+            q_h[i % 2].copy_(qd, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        d2h_gbs = 5 * qd.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
         e2e = {"value": v_e2e, "unit": "converged env-steps/s",
                "h2d_bytes_per_step": int(poses_h[0].numel() * 4), "d2h_bytes_per_step": int(q_h[0].numel() * 4),
+               "ms_per_step": e0.elapsed_time(e1) / args.steps, "d2h_gbs_alone": d2h_gbs,
                "note": "each step's positions are read back on a copy stream, overlapping the next step"}
 
     # ---------------- plain vs learned warm start (same fixed k, same residual test)
