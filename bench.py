@@ -662,6 +662,7 @@ def main():
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         conv = torch.zeros((), dtype=torch.int64, device=dev)
         it_sum = torch.zeros((), dtype=torch.int64, device=dev)
+        t_host = time.perf_counter()
         for i, s in enumerate(range(first, first + args.steps)):
             flush_buf.fill_(float(i))
             ev[i][0].record()
@@ -674,9 +675,23 @@ def main():
             it_sum += it.sum()
             if it_log is not None:
                 it_log.append(it)
+        t_host = time.perf_counter() - t_host
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        # the whole loop on the device (L2 flushes and any gap between steps
+        # included) and the host's time to issue it, per step
+        timing["span_ms_per_step"] = ev[0][0].elapsed_time(ev[-1][1]) / args.steps
+        timing["host_issue_ms_per_step"] = t_host * 1e3 / args.steps
         return ms, conv.item(), it_sum.item()
+
+    timing = {}
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for i in range(5):
+        flush_buf.fill_(float(i))
+    f1.record()
+    torch.cuda.synchronize()
+    timing["l2_flush_ms"] = f0.elapsed_time(f1) / 5
 
     launches0 = sim.launch_count()
     if world > 1:
@@ -685,6 +700,7 @@ def main():
     with ClockSampler(local, args.clock_log) as clk:
         it_log = []
         ms, n_conv, n_it = timed_steps(args.warmup, it_log)
+    timing_main = dict(timing)
     if world > 1:
         dist.barrier()
     launches = sim.launch_count() - launches0
@@ -749,6 +765,7 @@ def main():
             dist.barrier()
         conv_e = torch.zeros((), dtype=torch.int64, device=dev)
         e0.record()
+        t_host = time.perf_counter()
         for i, s in enumerate(range(n_steps, n_steps + args.steps)):
             dpose.copy_(poses_h[s + 1], non_blocking=True)
             sim.set_poses(dpose)
@@ -762,6 +779,7 @@ def main():
             conv_e += (sim.stats()[1] <= TOL).sum()
         main_st.wait_stream(copy_st)
         e1.record()
+        t_host = time.perf_counter() - t_host
         torch.cuda.synchronize()
         v_e2e, _ = aggregate(e0.elapsed_time(e1) / args.steps, conv_e.item() / args.steps, world, dev)
         # the read-back alone: device-to-host copy rate into pinned memory
@@ -777,6 +795,7 @@ def main():
         e2e = {"value": v_e2e, "unit": "converged env-steps/s",
                "h2d_bytes_per_step": int(poses_h[0].numel() * 4), "d2h_bytes_per_step": int(q_h[0].numel() * 4),
                "ms_per_step": e0.elapsed_time(e1) / args.steps, "d2h_gbs_alone": d2h_gbs,
+               "host_issue_ms_per_step": t_host * 1e3 / args.steps,
                "note": "each step's positions are read back on a copy stream, overlapping the next step"}
 
     # ---------------- plain vs learned warm start (same fixed k, same residual test)
@@ -937,6 +956,9 @@ def main():
             "step_hbm_frac_of_measured": step_hbm_frac,
             "roofline": roof, "kernels": kernels,
             "gpu_launches": int(launches),
+            "timing": dict(timing_main, note="ms_per_step sums each step's events; span_ms_per_step is the first "
+                                             "step's start to the last step's end (the L2 flushes between steps "
+                                             "included)"),
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
