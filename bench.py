@@ -645,14 +645,20 @@ def main():
     scs = sc if isinstance(sc, list) else [sc]
     poses = torch.stack([flash.poses_tensor(sc, s, dev) for s in range(total_steps + 1)])  # [S+1][N][8][7]
     sim.set_poses(poses[0], which=0)
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    # warm-up steps run the timed loop's per-step work too, so that the
+    # one-time loading of those kernels stays out of the timed region
+    warm_conv = torch.zeros((), dtype=torch.int64, device=dev)
     for s in range(args.warmup):
+        flush_buf.fill_(float(s))
         sim.set_poses(poses[s + 1])
         sim.apply_grasp_schedule(s)
         sim.step(1)
+        it, r = sim.stats()
+        warm_conv += (r <= TOL).sum() + it.sum()
     torch.cuda.synchronize()
 
     # ---------------- device-resident timed region
-    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def timed_steps(first, it_log=None):
         """args.steps steps starting at step index ``first``: per-step event
@@ -759,6 +765,14 @@ def main():
         q_h = [torch.empty((sim.n_verts, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
         dpose = torch.empty_like(poses[0])
         main_st, copy_st = torch.cuda.current_stream(), torch.cuda.Stream()
+        # one untimed pass of the copies (first use of the copy stream and buffers)
+        qw, _ = sim.get_state()
+        copy_st.wait_stream(main_st)
+        with torch.cuda.stream(copy_st):
+            for b in q_h:
+                b.copy_(qw, non_blocking=True)
+            dpose.copy_(poses_h[0], non_blocking=True)
+        main_st.wait_stream(copy_st)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
