@@ -42,6 +42,7 @@ typedef int32_t flash_status;
 #define FLASH_ENOTIMPL (-5) /* feature not available in this build */
 #define FLASH_ESTATE (-6)   /* call out of order (e.g. step before finalize) */
 #define FLASH_ENUMERIC (-7) /* setup matrix not positive definite, NaN state */
+#define FLASH_EINDEX (-8)   /* checked build: a kernel read an index out of its range */
 #define FLASH_WOVERFLOW 1   /* warning: contacts beyond capacity were dropped */
 
 #define FLASH_TRI 0
@@ -368,6 +369,10 @@ flash_status flash_get_stats(const flash_scene *s, int32_t *iters, float *rncp, 
  * bits and never trap; this call turns them into, by priority:
  *   FLASH_ETIMEOUT  a bounded mbarrier wait of the tensor-core solve ran out
  *                   (its results are not valid);
+ *   FLASH_EINDEX    (checked build only, see flash_checked_build) a step
+ *                   kernel read a vertex, element-slot or contact index
+ *                   outside its range; it used index 0 instead, so the
+ *                   step's results are not valid;
  *   FLASH_ENUMERIC  a non-finite position or NCP residual (the environment
  *                   holding it stops iterating; other environments are not
  *                   affected, they share no data);
@@ -427,6 +432,23 @@ int32_t flash_grouped_solve(const flash_scene *s);
  * values are the library's choice until the first step has timed the
  * candidates, and the timed choice after it. */
 int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, int32_t max_out);
+
+/* 1 in the checked build (libflash_check.so, compiled with FLASH_CHECK):
+ * the step kernels range-check every vertex, element-slot and contact index
+ * they read, replace an index out of range by 0 and report FLASH_EINDEX
+ * through flash_status_word, instead of reading or writing out of bounds.
+ * 0 in the regular build. */
+int32_t flash_checked_build(void);
+/* Fault injection for the checked build (the paper describes no failure
+ * handling; this is the library's own test hook): sets corner `corner` of
+ * element `element` of the mesh that environment `env` uses to vertex index
+ * `value` in the device element table the step kernels read (shared by the
+ * environments of that mesh group), and returns the previous index in *old.
+ * Returns FLASH_ENOTIMPL in the regular build, FLASH_EINVAL for an env,
+ * element or corner out of range; `value` itself is not checked (that is
+ * its purpose).  Synchronous. */
+flash_status flash_check_poke_element(flash_scene *s, int32_t env, int32_t element, int32_t corner, int32_t value,
+                                      int32_t *old);
 
 /* Learned warm start (the paper has no learned component; the network
  * predicts the initial multipliers gamma^0 and the first iterate at each

@@ -1696,6 +1696,37 @@ int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int
 
 int32_t flash_grouped_solve(const flash_scene *s) { return s && s->finalized && s->grouped ? 1 : 0; }
 
+int32_t flash_checked_build(void) {
+#ifdef FLASH_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+flash_status flash_check_poke_element(flash_scene *s, int32_t env, int32_t element, int32_t corner, int32_t value,
+                                      int32_t *old) {
+#ifndef FLASH_CHECK
+  (void)s; (void)env; (void)element; (void)corner; (void)value; (void)old;
+  return fail(FLASH_ENOTIMPL, "element poking exists in the checked build only");
+#else
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (env < 0 || env >= s->N) return fail(FLASH_EINVAL, "environment out of range");
+  Group &g = s->groups[s->env_group[env]];
+  if (element < 0 || element >= g.E || corner < 0 || corner >= g.vpe)
+    return fail(FLASH_EINVAL, "element or corner out of range");
+  int prev = 0;
+  FLASH_CUDA_TRY(cudaDeviceSynchronize());
+  FLASH_CUDA_TRY(cudaMemcpy(&prev, g.elems + (size_t)4 * element + corner, sizeof(int), cudaMemcpyDeviceToHost));
+  FLASH_CUDA_TRY(cudaMemcpy(g.elems + (size_t)4 * element + corner, &value, sizeof(int), cudaMemcpyHostToDevice));
+  if (g.erec)   // the triangle records carry the same vertex ids as float bits
+    FLASH_CUDA_TRY(cudaMemcpy(reinterpret_cast<float *>(g.erec) + (size_t)8 * element + corner, &value, sizeof(int),
+                              cudaMemcpyHostToDevice));
+  if (old) *old = prev;
+  return FLASH_OK;
+#endif
+}
+
 int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, int32_t max_out) {
   if (!s || !s->finalized || (kind != 0 && kind != 1)) return 0;
   int32_t k = 0;
@@ -1784,6 +1815,7 @@ flash_status flash_status_word(flash_scene *s, void *stream) {
   FLASH_CUDA_TRY(cudaMemcpyAsync(&w, s->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   FLASH_CUDA_TRY(cudaStreamSynchronize(st));
   if (w & (1 << 11)) return fail(FLASH_ETIMEOUT, "a bounded wait of the tensor-core solve ran out");
+  if (w & (1 << 12)) return fail(FLASH_EINDEX, "a step kernel read an index out of its range (checked build)");
   if (w & (1 << 9)) return fail(FLASH_ENUMERIC, "non-finite state or residual");
   if (w & (1 << 8)) {
     set_error("contacts beyond the scene's contact capacity were dropped");

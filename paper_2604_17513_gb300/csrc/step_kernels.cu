@@ -54,6 +54,7 @@ struct GroupView {
   const float *fm_adiag;   // [N or 1][n_pad] diagonal of A^-1 (fm_adiag_stride 0: shared)
   float *fm_u;         // [cols_pad][n_pad] A^-1 applied to the Krylov forces
   int fm_m, fm_adiag_stride;
+  int *status;         // the scene's status word (checked build: index range errors)
 };
 
 struct EnvView {
@@ -85,6 +86,7 @@ GroupView view(const flash_scene *s, const Group &g) {
   v.kenv = g.eig ? g.kenv : nullptr;
   v.bf16 = s->d.solve == FLASH_SOLVE_BF16R ? 1 : 0;
   v.tau = (float)g.tau;
+  v.status = s->status;
   return v;
 }
 
@@ -96,6 +98,33 @@ EnvView eview(const flash_scene *s) {
   e.rncp = s->rncp;
   e.gstate = s->gstate; e.gobs = s->gobs; e.ganchor = s->ganchor;
   return e;
+}
+
+// Index range check of the checked build (FLASH_CHECK): an index outside
+// [0, n) sets bit 12 of the status word and reads as 0, so no access leaves
+// its array.  The regular build passes every index through unchanged.
+__device__ __forceinline__ int chk(int i, int n, int *status) {
+#ifdef FLASH_CHECK
+  if ((unsigned)i >= (unsigned)n) {
+    atomicOr(status, 1 << 12);
+    return 0;
+  }
+#else
+  (void)n;
+  (void)status;
+#endif
+  return i;
+}
+// corner k of element f, a vertex of the group's mesh
+__device__ __forceinline__ int elem_v(const GroupView &G, int f, int k) {
+  return chk(G.elems[4 * f + k], G.n, G.status);
+}
+// the CSR tables: slot offsets of vertex p, and the element slot at sl
+__device__ __forceinline__ int csr_off(const GroupView &G, int p) { return chk(G.coff[p], G.ev + 1, G.status); }
+__device__ __forceinline__ int csr_slot(const GroupView &G, int sl) { return chk(G.cidx[sl], G.ev, G.status); }
+__device__ __forceinline__ int2 edge_v(const GroupView &G, int e) {
+  const int2 E = G.edges[e];
+  return make_int2(chk(E.x, G.n, G.status), chk(E.y, G.n, G.status));
 }
 
 // block-wide exclusive scan of one int per thread (blockDim <= 1024)
@@ -167,7 +196,7 @@ constexpr int kSlots = FLASH_OEE_SLOT + 1;   // contact-list slots: obstacles, g
 __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f, float reach, const float *x0,
                                                const float *x1) {
   const int np = G.n_pad;
-  const int t0 = G.elems[4 * f], t1 = G.elems[4 * f + 1], t2 = G.elems[4 * f + 2];
+  const int t0 = elem_v(G, f, 0), t1 = elem_v(G, f, 1), t2 = elem_v(G, f, 2);
   if (t0 == p || t1 == p || t2 == p) return false;
   bool hit = false;
   for (int k = 0; k < 2 && !hit; k++) {
@@ -186,10 +215,10 @@ __device__ __forceinline__ bool self_candidate(const GroupView &G, int p, int f,
   }
   if (!hit) return false;
   // f must not touch a triangle of p (topological neighbours never collide)
-  for (int sl = G.coff[p]; sl < G.coff[p + 1]; sl++) {
-    const int g = G.cidx[sl] / 3;
+  for (int sl = csr_off(G, p); sl < csr_off(G, p + 1); sl++) {
+    const int g = csr_slot(G, sl) / 3;
     for (int c = 0; c < 3; c++) {
-      const int u = G.elems[4 * g + c];
+      const int u = elem_v(G, g, c);
       if (u == t0 || u == t1 || u == t2) return false;
     }
   }
@@ -220,7 +249,7 @@ __device__ __forceinline__ V3 col3(const float *x, int ld, int i) { return v3(x[
 __device__ __forceinline__ bool ee_candidate(const GroupView &G, int e1, int e2, float reach, const float *x0,
                                              const float *x1) {
   const int np = G.n_pad;
-  const int2 E1 = G.edges[e1], E2 = G.edges[e2];
+  const int2 E1 = edge_v(G, e1), E2 = edge_v(G, e2);
   const int a = E1.x, b = E1.y, c = E2.x, d = E2.y;
   if (a == c || a == d || b == c || b == d) return false;
   bool hit = false;
@@ -236,10 +265,10 @@ __device__ __forceinline__ bool ee_candidate(const GroupView &G, int e1, int e2,
   if (!hit) return false;
   for (int k = 0; k < 2; k++) {
     const int p = k == 0 ? a : b;
-    for (int sl = G.coff[p]; sl < G.coff[p + 1]; sl++) {
-      const int g = G.cidx[sl] / 3;
+    for (int sl = csr_off(G, p); sl < csr_off(G, p + 1); sl++) {
+      const int g = csr_slot(G, sl) / 3;
       for (int j = 0; j < 3; j++) {
-        const int u = G.elems[4 * g + j];
+        const int u = elem_v(G, g, j);
         if (u == c || u == d) return false;
       }
     }
@@ -270,7 +299,7 @@ __device__ __forceinline__ V3 pose_point(const float *pose, V3 pb) {
 __device__ __forceinline__ bool ovt_candidate(const GroupView &G, int f, V3 C, float reach, const float *x0,
                                               const float *x1) {
   const int np = G.n_pad;
-  const int t0 = G.elems[4 * f], t1 = G.elems[4 * f + 1], t2 = G.elems[4 * f + 2];
+  const int t0 = elem_v(G, f, 0), t1 = elem_v(G, f, 1), t2 = elem_v(G, f, 2);
   for (int k = 0; k < 2; k++) {
     const float *x = k == 0 ? x0 : x1;
     const V3 A = col3(x, np, t0), B = col3(x, np, t1), Cc = col3(x, np, t2);
@@ -292,7 +321,7 @@ __device__ __forceinline__ bool ovt_candidate(const GroupView &G, int f, V3 C, f
 __device__ __forceinline__ bool oee_candidate(const GroupView &G, int e, V3 C, V3 D, float reach, const float *x0,
                                               const float *x1) {
   const int np = G.n_pad;
-  const int2 E = G.edges[e];
+  const int2 E = edge_v(G, e);
   for (int k = 0; k < 2; k++) {
     const float *x = k == 0 ? x0 : x1;
     const V3 A = col3(x, np, E.x), B = col3(x, np, E.y);
@@ -364,7 +393,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     for (int t = threadIdx.x; t < G.E; t += blockDim.x) {
       float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, el = 0.f;
       int tv[3];
-      for (int k = 0; k < 3; k++) tv[k] = G.elems[4 * t + k];
+      for (int k = 0; k < 3; k++) tv[k] = elem_v(G, t, k);
       for (int k = 0; k < 3; k++)
         for (int c = 0; c < 3; c++) {
           const float x0 = qt[c * np + tv[k]], x1 = qp[c * np + tv[k]];
@@ -377,7 +406,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
     }
     float *ebox = sbox + 6 * G.E;
     for (int k = threadIdx.x; k < G.ned; k += blockDim.x) {
-      const int2 ev = G.edges[k];
+      const int2 ev = edge_v(G, k);
       for (int c = 0; c < 3; c++) {
         const float a0 = qt[c * np + ev.x], a1 = qp[c * np + ev.x], b0 = qt[c * np + ev.y], b1 = qp[c * np + ev.y];
         ebox[6 * k + c] = fminf(fminf(a0, a1), fminf(b0, b1)) - reach;
@@ -424,10 +453,10 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
       float cull = -INFINITY;
       if (ofeat) {
         float L2 = 0.f;
-        for (int sl = G.coff[i]; sl < G.coff[i + 1]; sl++) {
-          const int t = G.cidx[sl] / 3;
+        for (int sl = csr_off(G, i); sl < csr_off(G, i + 1); sl++) {
+          const int t = csr_slot(G, sl) / 3;
           for (int c = 0; c < 3; c++) {
-            const int u = G.elems[4 * t + c];
+            const int u = elem_v(G, t, c);
             const V3 d0 = col3(qt, np, u) - v3(x0[0], x0[1], x0[2]), d1 = col3(qp, np, u) - v3(x1[0], x1[1], x1[2]);
             L2 = fmaxf(L2, fmaxf(dot(d0, d0), dot(d1, d1)));
           }
@@ -447,8 +476,8 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         // corners against the triangles whose first vertex is i (element
         // slots 3 f + 0 of i, f ascending), then box edges against the
         // edges (i, b), each in feature order
-        for (int sl = G.coff[i]; sl < G.coff[i + 1] && nv < FLASH_OFEAT_MAX; sl++) {
-          const int cs = G.cidx[sl];
+        for (int sl = csr_off(G, i); sl < csr_off(G, i + 1) && nv < FLASH_OFEAT_MAX; sl++) {
+          const int cs = csr_slot(G, sl);
           if (cs % 3 != 0) continue;
           const int f = cs / 3;
           for (int o = 0; o < a.K && nv < FLASH_OFEAT_MAX; o++) {
@@ -458,7 +487,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
                 sv[nv++] = (f * FLASH_MAX_OBS + o) * 8 + k;
           }
         }
-        for (int e1 = G.eoff[i]; e1 < G.eoff[i + 1] && nb < FLASH_OFEAT_MAX; e1++)
+        for (int e1 = chk(G.eoff[i], G.ned + 1, G.status); e1 < chk(G.eoff[i + 1], G.ned + 1, G.status) && nb < FLASH_OFEAT_MAX; e1++)
           for (int o = 0; o < a.K && nb < FLASH_OFEAT_MAX; o++) {
             if (!((near >> o) & 1u)) continue;
             for (int j = 0; j < 12 && nb < FLASH_OFEAT_MAX; j++) {
@@ -484,7 +513,7 @@ __device__ __forceinline__ void begin_body(const GroupView &G, const int l, cons
         // i owns (e1, then e2 ascending); the pair (e2, e1) would repeat the
         // same constraint
         const float *ebox = sbox + 6 * G.E;
-        for (int e1 = G.eoff[i]; e1 < G.eoff[i + 1] && ne < FLASH_EE_MAX; e1++) {
+        for (int e1 = chk(G.eoff[i], G.ned + 1, G.status); e1 < chk(G.eoff[i + 1], G.ned + 1, G.status) && ne < FLASH_EE_MAX; e1++) {
           float b1[6];
           if (boxes)
             for (int c = 0; c < 6; c++) b1[c] = ebox[6 * e1 + c];
@@ -686,7 +715,7 @@ struct SelfRow {
 __device__ __noinline__ void lin_self(const GroupView &G, int p, int f, const float *x, int ld, const float *xt,
                                       float mu, float h, float tau, const float *g, ContactLin &L, SelfRow &S) {
   const int np = G.n_pad;
-  const int t[3] = {G.elems[4 * f], G.elems[4 * f + 1], G.elems[4 * f + 2]};
+  const int t[3] = {elem_v(G, f, 0), elem_v(G, f, 1), elem_v(G, f, 2)};
   V3 X[3], Xt[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
@@ -734,7 +763,7 @@ __device__ __noinline__ void lin_self(const GroupView &G, int p, int f, const fl
 __device__ __noinline__ void lin_ee(const GroupView &G, int e1, int e2, const float *x, int ld, const float *xt,
                                     float mu, float h, float tau, const float *g, ContactLin &L, SelfRow &S) {
   const int np = G.n_pad;
-  const int2 E1 = G.edges[e1], E2 = G.edges[e2];
+  const int2 E1 = edge_v(G, e1), E2 = edge_v(G, e2);
   const int v[4] = {E1.x, E1.y, E2.x, E2.y};
   V3 X[4], Dx[4];
 #pragma unroll
@@ -781,7 +810,7 @@ __device__ __noinline__ void lin_ovt(const GroupView &G, const ObsShared &O, int
                                      SelfRow &S) {
   const int np = G.n_pad;
   const int f = feat / (8 * FLASH_MAX_OBS), o = feat / 8 % FLASH_MAX_OBS, kc = feat % 8;
-  const int t[3] = {G.elems[4 * f], G.elems[4 * f + 1], G.elems[4 * f + 2]};
+  const int t[3] = {elem_v(G, f, 0), elem_v(G, f, 1), elem_v(G, f, 2)};
   const V3 cb = box_corner_body(O.dims[o], kc);
   const V3 C = pose_point(O.pose[o], cb), Ct = pose_point(O.poset[o], cb);
   V3 X[3], Xt[3];
@@ -835,7 +864,7 @@ __device__ __noinline__ void lin_oee(const GroupView &G, const ObsShared &O, int
                                      SelfRow &S) {
   const int np = G.n_pad;
   const int e = feat / (12 * FLASH_MAX_OBS), o = feat / 12 % FLASH_MAX_OBS, j = feat % 12;
-  const int2 E = G.edges[e];
+  const int2 E = edge_v(G, e);
   V3 p0, p1;
   box_edge_body(O.dims[o], j, p0, p1);
   const V3 C = pose_point(O.pose[o], p0), D = pose_point(O.pose[o], p1);
@@ -896,11 +925,14 @@ __device__ __forceinline__ void fm_row_store(float *fw, const SelfRow &S) {
   *reinterpret_cast<float4 *>(fw + 4) =
       make_float4(S.meff, __int_as_float(S.v[1]), __int_as_float(S.v[2]), __int_as_float(S.v[3]));
 }
-__device__ __forceinline__ void fm_row_load(const float *fw, int vtx, SelfRow &S) {
+__device__ __forceinline__ void fm_row_load(const float *fw, int vtx, SelfRow &S, int n, int *status) {
   const float4 a = *reinterpret_cast<const float4 *>(fw), b = *reinterpret_cast<const float4 *>(fw + 4);
   S.w[0] = a.x; S.w[1] = a.y; S.w[2] = a.z; S.w[3] = a.w;
   S.meff = b.x;
-  S.v[0] = vtx; S.v[1] = __float_as_int(b.y); S.v[2] = __float_as_int(b.z); S.v[3] = __float_as_int(b.w);
+  S.v[0] = vtx;
+  S.v[1] = chk(__float_as_int(b.y), n, status);
+  S.v[2] = chk(__float_as_int(b.z), n, status);
+  S.v[3] = chk(__float_as_int(b.w), n, status);
 }
 
 template <int VPE, bool SELF>
@@ -973,7 +1005,8 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       // forces sum to zero as the operator's rows do
       for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
         const float4 r0 = __ldg(G.erec + 2 * el), r1 = __ldg(G.erec + 2 * el + 1);
-        const int v0 = __float_as_int(r0.x), v1 = __float_as_int(r0.y), v2 = __float_as_int(r0.z);
+        const int v0 = chk(__float_as_int(r0.x), n, G.status), v1 = chk(__float_as_int(r0.y), n, G.status),
+                  v2 = chk(__float_as_int(r0.z), n, G.status);
         float F[6], R[6], P[6];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -999,7 +1032,8 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     } else
     for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
-      const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
+      const int vv[4] = {chk(vi.x, n, G.status), chk(vi.y, n, G.status), chk(vi.z, n, G.status),
+                          chk(vi.w, n, G.status)};
       const float *D = G.D + 12 * el;
       float F[9], R[9], P[9], Dl[12];
 #pragma unroll
@@ -1048,10 +1082,11 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
 #pragma unroll 4
       for (int t = 0; t < G.deg_b; t++) {
         const int2 kj = __ldg(G.kb + (size_t)t * np + i);
+        const int kjx = chk(kj.x, n, G.status);
         const float kk = __int_as_float(kj.y);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-          const float d = __fsub_rn(qs[c * ns + kj.x], x[c]);
+          const float d = __fsub_rn(qs[c * ns + kjx], x[c]);
           const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
           const float s1 = __fadd_rn(sum[c], pr), bp = __fsub_rn(s1, sum[c]);
           const float se = __fadd_rn(__fsub_rn(sum[c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
@@ -1067,9 +1102,9 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     // ---- residual r = M (q~ - q) + sum_e D_a^T w~ (p_e - F_e) - bending
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       float acc0 = rs[i], acc1 = rs[ns + i], acc2 = rs[2 * ns + i];
-      const int t1 = coff[i + 1];
-      for (int t = coff[i]; t < t1; t++) {
-        const float *f = Fs + 3 * (int)cidx[t];
+      const int t1 = chk(coff[i + 1], G.ev + 1, G.status);
+      for (int t = chk(coff[i], G.ev + 1, G.status); t < t1; t++) {
+        const float *f = Fs + 3 * chk(cidx[t], G.ev, G.status);
         acc0 += f[0];
         acc1 += f[1];
         acc2 += f[2];
@@ -1089,7 +1124,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
   const float mu = V.mu[e];
   float rmax = 0.f;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int vtx = cvert[j];
+    const int vtx = chk(cvert[j], G.n, G.status);
     if (j > 0 && cvert[j - 1] == vtx) continue;
     const V3 x = v3(qs[vtx], qs[ns + vtx], qs[2 * ns + vtx]);
     const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
@@ -1100,7 +1135,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       const float4 g4 = *reinterpret_cast<const float4 *>(gam + 4 * jj);
       const float g[4] = {g4.x, g4.y, g4.z, g4.w};
       if (SELF && cobs[jj] >= FLASH_SELF_SLOT) continue;   // second pass below
-      lin_at(O, cobs[jj], a, mu, mv, x, xt, g, L);
+      lin_at(O, chk(cobs[jj], kSlots, G.status), a, mu, mv, x, xt, g, L);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       const float y1 = L.R[3] * g[1] + L.R[4] * g[2] + L.R[5] * g[3];
       const float y2 = L.R[6] * g[1] + L.R[7] * g[2] + L.R[8] * g[3];
@@ -1127,7 +1162,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       if (cobs[j] < FLASH_SELF_SLOT) continue;
       ContactLin L;
       SelfRow S;
-      lin_row(G, O, cobs[j], cvert[j], ctri[j], qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, S);
+      lin_row(G, O, chk(cobs[j], kSlots, G.status), chk(cvert[j], G.n, G.status), ctri[j], qs, ns, qt, mu, a.h, a.tau, gam + 4 * j, L, S);
       rmax = fmaxf(rmax, fmaxf(fabsf(L.phi[0]), fmaxf(fabsf(L.phi[1]), fabsf(L.phi[2]))));
       if (!residual_only) scatter_row(S.v, S.w, contact_force(L, gam + 4 * j), rs, ns);
     }
@@ -1202,7 +1237,8 @@ __device__ __forceinline__ void refine_body(const GroupView &G, const int l, con
   const float ks = G.kenv ? G.kenv[l] : 1.f;
   for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
     const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
-    const int vv[4] = {vi.x, vi.y, vi.z, vi.w};
+    const int vv[4] = {chk(vi.x, n, G.status), chk(vi.y, n, G.status), chk(vi.z, n, G.status),
+                          chk(vi.w, n, G.status)};
     const float *D = G.D + 12 * el;
     float F[9], Dl[12];
 #pragma unroll
@@ -1233,9 +1269,9 @@ __device__ __forceinline__ void refine_body(const GroupView &G, const int l, con
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     float a0 = rs[i], a1 = rs[ns + i], a2 = rs[2 * ns + i];
-    const int t1 = coff[i + 1];
-    for (int t = coff[i]; t < t1; t++) {
-      const float *f = Fs + 3 * (int)cidx[t];
+    const int t1 = chk(coff[i + 1], G.ev + 1, G.status);
+    for (int t = chk(coff[i], G.ev + 1, G.status); t < t1; t++) {
+      const float *f = Fs + 3 * chk(cidx[t], G.ev, G.status);
       a0 -= f[0];
       a1 -= f[1];
       a2 -= f[2];
@@ -1451,7 +1487,7 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
   __syncthreads();
   float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int vtx = cvert[j];
+    const int vtx = chk(cvert[j], G.n, G.status);
     if (j > 0 && cvert[j - 1] == vtx) continue;
     int c = 1;
     while (j + c < cnt && cvert[j + c] == vtx) c++;
@@ -1469,7 +1505,7 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
       // triangular (normal row first, then the 2x2 tangential block)
       ContactLin L;
       float *g = gam + 4 * j;
-      lin_at(O, cobs[j], a, mu, mv, x, xt, g, L);
+      lin_at(O, chk(cobs[j], kSlots, G.status), a, mu, mv, x, xt, g, L);
       if (!separated_free(L, g)) {
         const float Rdu0 = L.R[0] * du.x + L.R[1] * du.y + L.R[2] * du.z;
         const float Rdu1 = L.R[3] * du.x + L.R[4] * du.y + L.R[5] * du.z;
@@ -1492,7 +1528,7 @@ __device__ __forceinline__ void ncp_body(const GroupView &G, const int l, const 
       int idx[kMaxPerVertex];
       int na = 0;
       for (int aa = 0; aa < c; aa++) {
-        lin_at(O, cobs[j + aa], a, mu, mv, x, xt, gam + 4 * (j + aa), Ls[na]);
+        lin_at(O, chk(cobs[j + aa], kSlots, G.status), a, mu, mv, x, xt, gam + 4 * (j + aa), Ls[na]);
         if (!separated_free(Ls[na], gam + 4 * (j + aa))) idx[na++] = j + aa;
       }
       if (na == 1) {
@@ -1627,7 +1663,7 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
   __syncthreads();
   float ss = 0.f;
   for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
-    const int vtx = cvert[c];
+    const int vtx = chk(cvert[c], G.n, G.status);
     const float mv = __ldg(G.mass + vtx);
     const V3 x = v3(q[vtx], q[np + vtx], q[2 * np + vtx]);
     const V3 xt = v3(qt[vtx], qt[np + vtx], qt[2 * np + vtx]);
@@ -1638,7 +1674,7 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
     if (G.self && cobs[c] >= FLASH_SELF_SLOT) {
       // J du = sum w_k du_k; preconditioner scale (sum w_k^2 a_kk) meff
       SelfRow S;
-      lin_row(G, O, cobs[c], vtx, G.ctri[(size_t)l * cap + c], q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, S);
+      lin_row(G, O, chk(cobs[c], kSlots, G.status), vtx, G.ctri[(size_t)l * cap + c], q, np, qt, mu, a.h, a.tau, gam + 4 * c, L, S);
       float av = 0.f;
       du_c = v3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -1649,7 +1685,7 @@ __device__ __forceinline__ void fm_setup_body(const GroupView &G, const int l, c
       sc = av * S.meff;
       fm_row_store(G.fm_w + ((size_t)l * cap + c) * kFmW, S);
     } else {
-      lin_at(O, cobs[c], a, mu, mv, x, xt, gam + 4 * c, L);
+      lin_at(O, chk(cobs[c], kSlots, G.status), a, mu, mv, x, xt, gam + 4 * c, L);
       sc = ad[vtx] * mv;
     }
     const float Rdu0 = L.R[0] * du_c.x + L.R[1] * du_c.y + L.R[2] * du_c.z;
@@ -1690,7 +1726,7 @@ __device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l,
   __syncthreads();
   float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
   for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
-    const int vtx = cvert[c];
+    const int vtx = chk(cvert[c], G.n, G.status);
     if (c > 0 && cvert[c - 1] == vtx) continue;
     const float mv = __ldg(G.mass + vtx);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -1702,7 +1738,7 @@ __device__ __forceinline__ void fm_scatter_body(const GroupView &G, const int l,
       fm_pinv(L, sc, v, t);
       const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] >= FLASH_SELF_SLOT;
       SelfRow S;
-      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S);
+      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S, G.n, G.status);
       const float me = selfrow ? S.meff : mv;
       const V3 F = v3(me * (L.R[0] * t[0] + L.R[3] * t[1] + L.R[6] * t[2]),
                       me * (L.R[1] * t[0] + L.R[4] * t[1] + L.R[7] * t[2]),
@@ -1759,11 +1795,11 @@ __device__ __forceinline__ void fm_gather_body(const GroupView &G, const int l, 
     const float v[3] = {Vj[3 * c], Vj[3 * c + 1], Vj[3 * c + 2]};
     float t[3];
     fm_pinv(L, sc, v, t);
-    const int vtx = cvert[c];
+    const int vtx = chk(cvert[c], G.n, G.status);
     float ux = u[vtx], uy = u[np + vtx], uz = u[2 * np + vtx];
     if (G.self && G.cobs[(size_t)l * cap + c] >= FLASH_SELF_SLOT) {   // J u = sum w_k u_k
       SelfRow S;
-      fm_row_load(G.fm_w + ((size_t)l * cap + c) * kFmW, vtx, S);
+      fm_row_load(G.fm_w + ((size_t)l * cap + c) * kFmW, vtx, S, G.n, G.status);
       ux = 0.f; uy = 0.f; uz = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; k++) {
@@ -1862,7 +1898,7 @@ __device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, 
   float *gam = G.cgam + (size_t)l * cap * 4;
   float fm0 = 0.f, fm1 = 0.f, fm2 = 0.f;
   for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
-    const int vtx = cvert[c];
+    const int vtx = chk(cvert[c], G.n, G.status);
     if (c > 0 && cvert[c - 1] == vtx) continue;
     const float mv = __ldg(G.mass + vtx);
     V3 fsum = v3(0.f, 0.f, 0.f);
@@ -1876,7 +1912,7 @@ __device__ __forceinline__ void fm_finish_body(const GroupView &G, const int l, 
       fm_pinv(L, sc, z, dy);
       const bool selfrow = G.self && G.cobs[(size_t)l * cap + cc] >= FLASH_SELF_SLOT;
       SelfRow S;
-      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S);
+      if (selfrow) fm_row_load(G.fm_w + ((size_t)l * cap + cc) * kFmW, vtx, S, G.n, G.status);
       const V3 F = apply_update(L, selfrow ? S.meff : mv, a.gmax, dy, gam + 4 * cc);
       if (selfrow) scatter_row(S.v, S.w, F, fs, n);
       else fsum = fsum + F;
@@ -2117,7 +2153,7 @@ __global__ void __launch_bounds__(256) k_features(GroupView G, EnvView V, StepAr
   const int *pv = G.pvert + (size_t)l * G.cap, *po = G.pobs + (size_t)l * G.cap;
   const float *pg = G.pgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int vtx = cvert[j], o = cobs[j];
+    const int vtx = chk(cvert[j], G.n, G.status), o = chk(cobs[j], kSlots, G.status);
     if (o >= FLASH_GRASP_SLOT) {   // grasp and self rows are not predicted: NaN features keep them cold
       for (int c = 0; c < 10; c++) X[(off[l] + j) * 10 + c] = __int_as_float(0x7fc00000);
       continue;
@@ -2168,7 +2204,7 @@ __global__ void __launch_bounds__(256) k_apply_learned(GroupView G, EnvView V, S
   float *qp = G.qp + (size_t)l * 3 * np, *q = G.q + (size_t)l * 3 * np;
   float *gam = G.cgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int vtx = cvert[j], o = cobs[j];
+    const int vtx = chk(cvert[j], G.n, G.status), o = chk(cobs[j], kSlots, G.status);
     if (o >= FLASH_GRASP_SLOT) continue;
     const V3 x = v3(qp[vtx], qp[np + vtx], qp[2 * np + vtx]);
     V3 n, t1, t2;
@@ -2206,7 +2242,7 @@ __global__ void __launch_bounds__(256) k_targets(GroupView G, EnvView V, StepArg
   const float *qp = G.qp + (size_t)l * 3 * np, *q = G.q + (size_t)l * 3 * np;
   const float *gam = G.cgam + (size_t)l * G.cap * 4;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int vtx = cvert[j], o = cobs[j];
+    const int vtx = chk(cvert[j], G.n, G.status), o = chk(cobs[j], kSlots, G.status);
     float *t = T + (off[l] + j) * 6;
     if (o >= FLASH_GRASP_SLOT || !(V.rncp[e] <= a.tol)) {   // grasp / self row or not converged: no target
       for (int c = 0; c < 6; c++) t[c] = __int_as_float(0x7fc00000);

@@ -16,9 +16,11 @@ import torch
 from . import scenes as _sc
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libflash.so")
+# FLASH_CHECKED_BUILD=1 loads the checked variant (every index a step kernel
+# reads is range-checked; an out-of-range one is reported as FLASH_EINDEX)
+LIB_PATH = os.path.join(_HERE, "libflash_check.so" if os.environ.get("FLASH_CHECKED_BUILD") == "1" else "libflash.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, ESTATE, ENUMERIC, EINDEX = 0, -1, -2, -3, -4, -5, -6, -7, -8
 WOVERFLOW = 1
 MAX_OBS = 8
 GRASP_SLOT = MAX_OBS   # contact-list obstacle slot of grasp rows
@@ -128,6 +130,9 @@ def lib():
         L.flash_grouped_solve.restype = i32
         L.flash_scene_threads.argtypes = [vp, i32, C.POINTER(i32), i32]
         L.flash_scene_threads.restype = i32
+        L.flash_checked_build.argtypes = []
+        L.flash_checked_build.restype = i32
+        L.flash_check_poke_element.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32)]
         L.flash_warmstart_set.argtypes = [vp, vp, i32, i32]
         L.flash_warmstart_bounds.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.flash_record_contacts.argtypes = [vp, i32]

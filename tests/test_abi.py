@@ -37,6 +37,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_regular_build_has_no_poke_hook(lib):
+    """flash_check_poke_element corrupts device tables only in the checked
+    build; the regular library reports itself unchecked and refuses it
+    before touching any scene."""
+    import ctypes as C
+    from paper_2604_17513_gb300 import flash
+    assert lib.flash_checked_build() == 0
+    old = C.c_int32(0)
+    assert lib.flash_check_poke_element(None, 0, 0, 0, 0, C.byref(old)) == flash.ENOTIMPL
+
+
 def test_header_has_no_torch_types():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()

@@ -8,14 +8,24 @@ flash_set_state, a contact capacity smaller than the scene needs, a vertex
 with more contacts than the lite metric's per-vertex block.  The resume test
 checks that flash_get_state / flash_set_state / flash_set_obstacle_poses
 carry everything a cold-started step depends on: a rollout interrupted and
-resumed from its checkpoint is bit-identical to the uninterrupted one.
+resumed from its checkpoint is bit-identical to the uninterrupted one.  The
+checked build (libflash_check.so, every index a step kernel reads
+range-checked) is loaded in a child process: it steps like the regular
+build, and an element index corrupted on the host through its test hook is
+reported as FLASH_EINDEX instead of being dereferenced.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
 from paper_2604_17513_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _state(sim, sc, q, v, s):
@@ -158,3 +168,81 @@ def test_checkpoint_resume_is_bit_exact(cuda, mode):
         assert np.array_equal(q, q_ref) and np.array_equal(v, v_ref)
         assert np.array_equal(target.stats()[0].cpu().numpy(), it_ref)
         assert target.status() == flash.OK
+
+
+_CHECKED_CHILD = r"""
+import ctypes as C, json, sys
+import numpy as np, torch
+sys.path.insert(0, ROOT)
+from paper_2604_17513_gb300 import flash, scenes
+L = flash.lib()
+assert L.flash_checked_build() == 1
+dev = torch.device("cuda", 0)
+out = {}
+for name in ("tri", "tet"):
+    sc = scenes.cloth_drop(n_envs=3, steps=12) if name == "tri" else scenes.tet_squeeze(n_envs=4, steps=12)
+    sim = flash.Sim(sc, solve=flash.SOLVE_F16X3)
+    q0, v0 = flash.state_tensors(sc, dev)
+    sim.set_state(q0, v0)
+    sim.set_poses(flash.poses_tensor(sc, 0, dev), which=0)
+    for s in range(6):
+        sim.set_poses(flash.poses_tensor(sc, s + 1, dev))
+        sim.step(1)
+    clean = L.flash_status_word(sim._h, None)
+    q, v = (t.clone() for t in sim.get_state())
+    old = C.c_int32(-1)
+    poke = L.flash_check_poke_element(sim._h, 0, 5, 1, sc.n_verts + 7, C.byref(old))
+    sim.set_poses(flash.poses_tensor(sc, 7, dev))
+    sim.step(1)
+    bad = L.flash_status_word(sim._h, None)
+    msg = L.flash_last_error().decode()
+    finite = bool(torch.isfinite(sim.get_state()[0]).all().item())
+    back = L.flash_check_poke_element(sim._h, 0, 5, 1, old.value, None)
+    sim.set_state(q, v)
+    sim.set_poses(flash.poses_tensor(sc, 6, dev), which=0)
+    sim.set_poses(flash.poses_tensor(sc, 7, dev))
+    sim.step(1)
+    again = L.flash_status_word(sim._h, None)
+    out[name] = dict(clean=clean, poke=poke, old=old.value, bad=bad, msg=msg, finite=finite, back=back,
+                     again=again, q=q.cpu().numpy().ravel().tolist())
+print("RESULT" + json.dumps(out))
+"""
+
+
+def test_checked_build_steps_alike_and_reports_corrupted_index(cuda):
+    """The checked build (child process, FLASH_CHECKED_BUILD=1): 6 steps of
+    a cloth and of a tet scene report FLASH_OK and end within 1e-6 m of the
+    regular build's; an element corner set to an index past the mesh
+    through flash_check_poke_element makes the next step report
+    FLASH_EINDEX (named in flash_last_error) with finite positions, and
+    after the index is restored and the state reset the step is clean
+    again.  The regular build refuses the hook (FLASH_ENOTIMPL)."""
+    import ctypes as C
+    import torch
+    from paper_2604_17513_gb300 import flash
+    lib = flash.lib()
+    assert lib.flash_checked_build() == 0
+    env = dict(os.environ, FLASH_CHECKED_BUILD="1")
+    res = subprocess.run([sys.executable, "-c", _CHECKED_CHILD.replace("ROOT", repr(ROOT))], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-3000:]
+    line = [x for x in res.stdout.splitlines() if x.startswith("RESULT")][-1]
+    out = json.loads(line[len("RESULT"):])
+    for name in ("tri", "tet"):
+        r = out[name]
+        assert r["clean"] == flash.OK and r["poke"] == flash.OK and r["back"] == flash.OK, r
+        assert 0 <= r["old"] and r["bad"] == flash.EINDEX and "index" in r["msg"] and r["finite"], r
+        assert r["again"] == flash.OK, r
+        sc = scenes.cloth_drop(n_envs=3, steps=12) if name == "tri" else scenes.tet_squeeze(n_envs=4, steps=12)
+        sim = flash.Sim(sc, solve=flash.SOLVE_F16X3)
+        q0, v0 = flash.state_tensors(sc, cuda)
+        sim.set_state(q0, v0)
+        sim.set_poses(flash.poses_tensor(sc, 0, cuda), which=0)
+        for s in range(6):
+            sim.set_poses(flash.poses_tensor(sc, s + 1, cuda))
+            sim.step(1)
+        q = sim.get_state()[0].cpu().numpy().ravel()
+        assert np.abs(q - np.asarray(r["q"])).max() <= 1e-6, name
+        old = C.c_int32(0)
+        assert lib.flash_check_poke_element(sim._h, 0, 5, 1, 0, C.byref(old)) == flash.ENOTIMPL
+        torch.cuda.synchronize()
