@@ -433,6 +433,14 @@ int32_t flash_grouped_solve(const flash_scene *s);
  * candidates, and the timed choice after it. */
 int32_t flash_scene_threads(const flash_scene *s, int32_t kind, int32_t *out, int32_t max_out);
 
+/* The bounded-wait failure path, run on purpose (a test hook, both builds):
+ * one GPU thread waits, with the tensor-core solve's wait routine and a
+ * limit of limit_cycles SM cycles (1..4e9; the solve itself uses 4e9,
+ * about 2 s), on an mbarrier that nothing arrives at.  The wait runs out,
+ * the status word's timeout bit is set and the thread returns, so the next
+ * flash_status_word reports FLASH_ETIMEOUT and flash_set_state clears it;
+ * the context stays usable.  Asynchronous on stream. */
+flash_status flash_test_bounded_wait(flash_scene *s, int64_t limit_cycles, void *stream);
 /* 1 in the checked build (libflash_check.so, compiled with FLASH_CHECK):
  * the step kernels range-check every vertex, element-slot and contact index
  * they read, replace an index out of range by 0 and report FLASH_EINDEX

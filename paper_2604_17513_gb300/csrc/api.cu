@@ -1696,6 +1696,15 @@ int32_t flash_lane_count(const flash_scene *s) { return s && s->finalized ? (int
 
 int32_t flash_grouped_solve(const flash_scene *s) { return s && s->finalized && s->grouped ? 1 : 0; }
 
+flash_status flash_test_bounded_wait(flash_scene *s, int64_t limit_cycles, void *stream) {
+  if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
+  if (limit_cycles <= 0 || limit_cycles > 4000000000LL)
+    return fail(FLASH_EINVAL, "limit_cycles must be in 1..4e9");
+  FLASH_CUDA_TRY(launch_wait_probe(s->status, (long long)limit_cycles, (cudaStream_t)stream));
+  s->launches++;
+  return FLASH_OK;
+}
+
 int32_t flash_checked_build(void) {
 #ifdef FLASH_CHECK
   return 1;

@@ -354,6 +354,9 @@ cudaError_t gemm_simt(const Group &g, const SolveMat &M, const float *rhs, float
 cudaError_t gemm_tc(const Group &g, const SolveMat &M, float *out, const float *w, const int *done, int mode,
                     const float *lam, const float *kenv, cudaStream_t st, int c0 = 0, int c1 = -1, int bn = 0,
                     bool bf = false, const SplitK &sk = SplitK());
+// one bounded mbarrier wait that nothing completes (limit in SM cycles, at
+// most the solve's own limit): sets the status word's timeout bit
+cudaError_t launch_wait_probe(int *status, long long limit, cudaStream_t st);
 // scratch a split-K apply of columns [c0, c1) of g needs at any tile width
 void splitk_need(const Group &g, int c0, int c1, size_t *tiles, size_t *part_floats);
 bool tc_available();

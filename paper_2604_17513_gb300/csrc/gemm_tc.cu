@@ -60,7 +60,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 
 // bounded wait on the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = WAIT_CYCLES) {
   uint32_t addr = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
@@ -73,7 +73,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -539,6 +539,27 @@ int gemm_problem(void *dst, const Group &g, const SolveMat &M, int c0, int c1, i
   pr.a_unscale = ldexpf(1.f, -M.exp);
   std::memcpy(dst, &pr, sizeof(pr));
   return pr.tiles_x * (g.n_pad / BM);
+}
+
+namespace {
+// The failure path of the bounded waits, run on purpose: one thread waits,
+// with the solve's own wait routine and a given cycle limit, on an mbarrier
+// that nothing arrives at; the wait runs out and the timeout bit is set, as
+// a tensor-core tile does when its wait runs out.
+__global__ void k_wait_probe(int *status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, limit)) atomicOr(status, 1 << 11);
+  }
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(int *status, long long limit, cudaStream_t st) {
+  if (limit <= 0 || limit > WAIT_CYCLES) return cudaErrorInvalidValue;
+  k_wait_probe<<<1, 32, 0, st>>>(status, limit);
+  return cudaGetLastError();
 }
 
 cudaError_t gemm_tc_grouped(const void *probs, int nprob, int tiles, float *const *outs, const int *done, int *status,

@@ -130,6 +130,7 @@ def lib():
         L.flash_grouped_solve.restype = i32
         L.flash_scene_threads.argtypes = [vp, i32, C.POINTER(i32), i32]
         L.flash_scene_threads.restype = i32
+        L.flash_test_bounded_wait.argtypes = [vp, i64, vp]
         L.flash_checked_build.argtypes = []
         L.flash_checked_build.restype = i32
         L.flash_check_poke_element.argtypes = [vp, i32, i32, i32, i32, C.POINTER(i32)]

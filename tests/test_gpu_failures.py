@@ -246,3 +246,31 @@ def test_checked_build_steps_alike_and_reports_corrupted_index(cuda):
         old = C.c_int32(0)
         assert lib.flash_check_poke_element(sim._h, 0, 5, 1, 0, C.byref(old)) == flash.ENOTIMPL
         torch.cuda.synchronize()
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(cuda):
+    """A bounded mbarrier wait that nothing completes (the solve's own wait
+    routine, a 2e6-cycle limit, about 1 ms): the waiting thread gives up and
+    sets the timeout bit, flash_status_word reports FLASH_ETIMEOUT naming
+    the wait, flash_set_state clears it, and the context stays usable: the
+    next steps are clean and equal a scene that never timed out."""
+    import torch
+    from paper_2604_17513_gb300 import flash
+    sc = scenes.cloth_drop(n_envs=2, steps=12)
+    qs = []
+    for probe in (True, False):
+        sim = flash.Sim(sc, solve=flash.SOLVE_F16X3)
+        _state(sim, sc, sc.q0, sc.v0, 0)
+        if probe:
+            assert flash.lib().flash_test_bounded_wait(sim._h, 2_000_000, None) == flash.OK
+            with pytest.raises(flash.FlashError) as ei:
+                sim.status()
+            assert ei.value.code == flash.ETIMEOUT and "bounded wait" in str(ei.value)
+            assert flash.lib().flash_test_bounded_wait(sim._h, 0, None) == flash.EINVAL
+            _state(sim, sc, sc.q0, sc.v0, 0)
+            assert sim.status() == flash.OK
+        _steps(sim, sc, 0, 3)
+        assert sim.status() == flash.OK
+        qs.append(sim.get_state()[0].cpu().numpy())
+        torch.cuda.synchronize()
+    assert np.array_equal(qs[0], qs[1])
