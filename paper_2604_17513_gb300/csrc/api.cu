@@ -11,9 +11,21 @@
 #include <tuple>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "flash_internal.cuh"
 
 namespace flash {
+
+// NVTX range over a host call (finalize, step, render, ...): profilers can
+// select or leave out its launches (e.g. the autotuner's timing launches
+// inside "flash.finalize"); a no-op unless a tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 static thread_local std::string g_error;
 void set_error(const std::string &msg) { g_error = msg; }
@@ -806,6 +818,7 @@ flash_status flash_envs_add(flash_scene *s, int32_t mesh_id, int32_t n, const fl
 }
 
 flash_status flash_scene_finalize(flash_scene *s, void *stream) {
+  NvtxRange range("flash.finalize");
   if (!s) return fail(FLASH_EINVAL, "null scene");
   if (s->finalized) return fail(FLASH_ESTATE, "scene already finalized");
   if (s->envs.empty()) return fail(FLASH_EINVAL, "no environments");
@@ -1162,6 +1175,7 @@ flash_status flash_grasp(flash_scene *s, int32_t first_env, int32_t count, const
 
 flash_status flash_render(flash_scene *s, const flash_camera *cam, const float *cam_poses, float *depth,
                           uint8_t *seg, float *points, void *stream) {
+  NvtxRange range("flash.render");
   if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
   if (!cam_poses || !depth) return fail(FLASH_EINVAL, "cam_poses and depth are required");
   if (s->N > 65535) return fail(FLASH_EINVAL, "ray casting takes at most 65535 environments");
@@ -1208,6 +1222,7 @@ namespace {
 // The fastest of three runs of each candidate is compared, per local batch and
 // per lane.
 flash_status tune_threads(flash_scene *s, const StepArgs &a, int tc, cudaStream_t st) {
+  NvtxRange range("flash.tune_threads");
   s->tune_pending = false;
   s->graph_stale = true;
   const bool profiling = s->profiling;   // the candidates' launches stay out of the kernel profile
@@ -1331,6 +1346,7 @@ flash_status tol_loop_graphed(flash_scene *s, cudaStream_t st, const std::functi
                               const std::function<cudaError_t(cudaStream_t)> &solves);
 
 flash_status step_once(flash_scene *s, cudaStream_t st) {
+  NvtxRange range(s->capturing ? "flash.capture_step" : "flash.step_once");
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
   const StepArgs a = step_args(s);
   const int tc = use_tc(s) ? 1 : 0;
@@ -1578,6 +1594,7 @@ flash_status capture_step(flash_scene *s) {
 }  // namespace
 
 flash_status flash_step(flash_scene *s, int32_t n_steps, void *stream) {
+  NvtxRange range("flash.step");
   if (!s || !s->finalized) return fail(FLASH_ESTATE, "scene not finalized");
   if (n_steps < 0) return fail(FLASH_EINVAL, "negative step count");
   const bool learned = s->d.warm == FLASH_WARM_LEARNED;
