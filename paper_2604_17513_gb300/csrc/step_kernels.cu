@@ -1034,10 +1034,14 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
       const int vv[4] = {chk(vi.x, n, G.status), chk(vi.y, n, G.status), chk(vi.z, n, G.status),
                           chk(vi.w, n, G.status)};
-      const float *D = G.D + 12 * el;
+      // the element's 4 x 3 operator rows: three 16-byte loads (48 B a record)
+      const float4 *D4 = reinterpret_cast<const float4 *>(G.D + 12 * el);
       float F[9], R[9], P[9], Dl[12];
 #pragma unroll
-      for (int t = 0; t < 3 * vpe; t++) Dl[t] = __ldg(D + t);
+      for (int t = 0; t < 3; t++) {
+        const float4 d = __ldg(D4 + t);
+        Dl[4 * t] = d.x; Dl[4 * t + 1] = d.y; Dl[4 * t + 2] = d.z; Dl[4 * t + 3] = d.w;
+      }
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         const float x0 = qs[c * ns + vv[0]];
@@ -1239,10 +1243,13 @@ __device__ __forceinline__ void refine_body(const GroupView &G, const int l, con
     const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
     const int vv[4] = {chk(vi.x, n, G.status), chk(vi.y, n, G.status), chk(vi.z, n, G.status),
                           chk(vi.w, n, G.status)};
-    const float *D = G.D + 12 * el;
+    const float4 *D4 = reinterpret_cast<const float4 *>(G.D + 12 * el);
     float F[9], Dl[12];
 #pragma unroll
-    for (int t = 0; t < 3 * vpe; t++) Dl[t] = __ldg(D + t);
+    for (int t = 0; t < 3; t++) {
+      const float4 d = __ldg(D4 + t);
+      Dl[4 * t] = d.x; Dl[4 * t + 1] = d.y; Dl[4 * t + 2] = d.z; Dl[4 * t + 3] = d.w;
+    }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const float x0 = ws[c * ns + vv[0]];
