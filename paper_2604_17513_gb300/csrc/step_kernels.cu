@@ -1029,7 +1029,8 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
           Fe[c] = -(f1 + f2);
         }
       }
-    } else
+    } else {
+    const bool fs16 = (reinterpret_cast<uintptr_t>(Fs) & 15) == 0;   // shared memory; the global scratch may not be
     for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
       const int4 vi = *reinterpret_cast<const int4 *>(G.elems + 4 * el);
       const int vv[4] = {chk(vi.x, n, G.status), chk(vi.y, n, G.status), chk(vi.z, n, G.status),
@@ -1062,6 +1063,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
 #pragma unroll
       for (int t = 0; t < 3 * nc; t++) P[t] = wt * (R[t] - F[t]);
       float *Fe = Fs + (size_t)el * vpe * 3;
+      float fe[3 * vpe];
 #pragma unroll
       for (int aa = 0; aa < vpe; aa++)
 #pragma unroll
@@ -1069,8 +1071,17 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
           float s = 0.f;
 #pragma unroll
           for (int j = 0; j < nc; j++) s += Dl[aa * 3 + j] * P[nc * c + j];
-          Fe[aa * 3 + c] = s;
+          fe[aa * 3 + c] = s;
         }
+      if (fs16) {   // 48-byte records: three 16-byte stores
+#pragma unroll
+        for (int t = 0; t < 3; t++)
+          reinterpret_cast<float4 *>(Fe)[t] = make_float4(fe[4 * t], fe[4 * t + 1], fe[4 * t + 2], fe[4 * t + 3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 3 * vpe; t++) Fe[t] = fe[t];
+      }
+    }
     }
     // ---- per vertex: inertia M (q~ - q) and bending - sum_j K_ij (q_j - q_i).
     //      The operator's rows sum to zero; the terms are large and cancel.
@@ -1971,19 +1982,27 @@ __device__ __forceinline__ void end_body(const GroupView &G, const int l, const 
   const float inv_h = 1.f / a.h;
   float *q = G.q + (size_t)l * 3 * np, *v = G.v + (size_t)l * 3 * np;
   const float *qt = G.qt + (size_t)l * 3 * np;
-  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-    int c = i / n, j = i - c * n;
-    float qq = q[c * np + j];
-    v[c * np + j] = (qq - qt[c * np + j]) * inv_h;
-    if (!isfinite(qq)) atomicOr(V.status, 1 << 9);
+  // 16-byte columns (n_pad is a multiple of 128); q and q_t are zero in the
+  // padding, so the velocity there is zero too
+  const int n4 = (n + 3) >> 2;
+  for (int i = threadIdx.x; i < 3 * n4; i += blockDim.x) {
+    const int c = i / n4, j = (i - c * n4) * 4;
+    const float4 qq = *reinterpret_cast<const float4 *>(q + c * np + j);
+    const float4 tt = *reinterpret_cast<const float4 *>(qt + c * np + j);
+    const float4 vv = make_float4((qq.x - tt.x) * inv_h, (qq.y - tt.y) * inv_h, (qq.z - tt.z) * inv_h,
+                                  (qq.w - tt.w) * inv_h);
+    *reinterpret_cast<float4 *>(v + c * np + j) = vv;
+    if (!(isfinite(qq.x) && isfinite(qq.y) && isfinite(qq.z) && isfinite(qq.w))) atomicOr(V.status, 1 << 9);
   }
   const int cnt = G.ccount[l];
   if (threadIdx.x == 0) G.pcount[l] = cnt;
+  const float4 *cg = reinterpret_cast<const float4 *>(G.cgam + (size_t)l * G.cap * 4);
+  float4 *pg = reinterpret_cast<float4 *>(G.pgam + (size_t)l * G.cap * 4);
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     G.pvert[(size_t)l * G.cap + j] = G.cvert[(size_t)l * G.cap + j];
     G.pobs[(size_t)l * G.cap + j] = G.cobs[(size_t)l * G.cap + j];
     if (G.self) G.pctri[(size_t)l * G.cap + j] = G.ctri[(size_t)l * G.cap + j];
-    for (int c = 0; c < 4; c++) G.pgam[((size_t)l * G.cap + j) * 4 + c] = G.cgam[((size_t)l * G.cap + j) * 4 + c];
+    pg[j] = cg[j];
   }
 }
 
