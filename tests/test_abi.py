@@ -48,6 +48,25 @@ def test_regular_build_has_no_poke_hook(lib):
     assert lib.flash_check_poke_element(None, 0, 0, 0, 0, C.byref(old)) == flash.ENOTIMPL
 
 
+def test_header_compiles_as_c(tmp_path):
+    """include/flash.h is a plain C header: a C99 translation unit that
+    includes it and names its types and entry points compiles without
+    warnings (gcc -std=c99 -Wall -Wextra -Werror, syntax only)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "uses_header.c"
+    src.write_text('#include "flash.h"\n'
+                   "int main(void) {\n"
+                   "  flash_scene_desc d;\n  flash_scene *s = 0;\n  (void)d;\n"
+                   "  return (int)flash_checked_build() + (int)flash_lane_count(s);\n}\n")
+    res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                          "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+
+
 def test_header_has_no_torch_types():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
