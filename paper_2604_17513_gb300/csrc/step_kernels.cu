@@ -1090,28 +1090,46 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
     //      products and sums use error-free transforms (the row is rounded
     //      once); the operations are explicitly rounded, out of FMA contraction.
     const float *qp = G.qp + (size_t)l * 3 * np;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float m = __ldg(G.mass + i);
-      const float x[3] = {qs[i], qs[ns + i], qs[2 * ns + i]};
-      float sum[3] = {0.f, 0.f, 0.f}, err[3] = {0.f, 0.f, 0.f};
-#pragma unroll 4
-      for (int t = 0; t < G.deg_b; t++) {
-        const int2 kj = __ldg(G.kb + (size_t)t * np + i);
-        const int kjx = chk(kj.x, n, G.status);
-        const float kk = __int_as_float(kj.y);
+    // two vertices per pass of a thread (i and i + blockDim), their sums
+    // interleaved entry by entry: six independent chains and two operator
+    // loads in flight; each vertex's own sum keeps its order
+    for (int i = threadIdx.x; i < n; i += 2 * blockDim.x) {
+      const int i2 = i + blockDim.x;
+      const bool two = i2 < n;
+      const int j2 = two ? i2 : i;
+      float x[2][3], sum[2][3], err[2][3];
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-          const float d = __fsub_rn(qs[c * ns + kjx], x[c]);
-          const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
-          const float s1 = __fadd_rn(sum[c], pr), bp = __fsub_rn(s1, sum[c]);
-          const float se = __fadd_rn(__fsub_rn(sum[c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
-          sum[c] = s1;
-          err[c] = __fadd_rn(err[c], __fadd_rn(se, pe));
-        }
+      for (int c = 0; c < 3; c++) {
+        x[0][c] = qs[c * ns + i];
+        x[1][c] = qs[c * ns + j2];
+        sum[0][c] = sum[1][c] = err[0][c] = err[1][c] = 0.f;
       }
-      rs[i] = m * (qp[i] - x[0]) - (sum[0] + err[0]);
-      rs[ns + i] = m * (qp[np + i] - x[1]) - (sum[1] + err[1]);
-      rs[2 * ns + i] = m * (qp[2 * np + i] - x[2]) - (sum[2] + err[2]);
+#pragma unroll 2
+      for (int t = 0; t < G.deg_b; t++) {
+        const int2 kja = __ldg(G.kb + (size_t)t * np + i), kjb = __ldg(G.kb + (size_t)t * np + j2);
+        const int ka[2] = {chk(kja.x, n, G.status), chk(kjb.x, n, G.status)};
+        const float kv[2] = {__int_as_float(kja.y), __int_as_float(kjb.y)};
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const float kk = kv[u];
+            const float d = __fsub_rn(qs[c * ns + ka[u]], x[u][c]);
+            const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
+            const float s1 = __fadd_rn(sum[u][c], pr), bp = __fsub_rn(s1, sum[u][c]);
+            const float se = __fadd_rn(__fsub_rn(sum[u][c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
+            sum[u][c] = s1;
+            err[u][c] = __fadd_rn(err[u][c], __fadd_rn(se, pe));
+          }
+      }
+      const float m0 = __ldg(G.mass + i);
+#pragma unroll
+      for (int c = 0; c < 3; c++) rs[c * ns + i] = m0 * (qp[c * np + i] - x[0][c]) - (sum[0][c] + err[0][c]);
+      if (two) {
+        const float m1 = __ldg(G.mass + i2);
+#pragma unroll
+        for (int c = 0; c < 3; c++) rs[c * ns + i2] = m1 * (qp[c * np + i2] - x[1][c]) - (sum[1][c] + err[1][c]);
+      }
     }
     __syncthreads();
     // ---- residual r = M (q~ - q) + sum_e D_a^T w~ (p_e - F_e) - bending
