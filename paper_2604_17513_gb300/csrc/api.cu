@@ -273,13 +273,21 @@ flash_status build_group(flash_scene *s, Group &g, cudaStream_t st) {
     }
     g.deg_b = 0;
     for (int i = 0; i < n; i++) g.deg_b = std::max(g.deg_b, (int)rows[i].size());
-    std::vector<int2> kb((size_t)std::max(g.deg_b, 1) * np);
+    // entries in pairs (2p, 2p + 1) per 16-byte record, pair-major
+    // [pairs][n_pad]; unused entries are (i, 0)
+    const int pairs = (std::max(g.deg_b, 1) + 1) / 2;
+    std::vector<int4> kb((size_t)pairs * np);
     auto bits = [](float f) { int b; std::memcpy(&b, &f, 4); return b; };
     for (int i = 0; i < np; i++)
-      for (int t = 0; t < std::max(g.deg_b, 1); t++) kb[(size_t)t * np + i] = int2{i < n ? i : 0, 0};
+      for (int p = 0; p < pairs; p++) kb[(size_t)p * np + i] = int4{i < n ? i : 0, 0, i < n ? i : 0, 0};
     for (int i = 0; i < n; i++) {
       int t = 0;
-      for (auto &kv : rows[i]) kb[(size_t)(t++) * np + i] = int2{kv.first, bits((float)kv.second)};
+      for (auto &kv : rows[i]) {
+        int4 &r = kb[(size_t)(t / 2) * np + i];
+        if (t % 2 == 0) { r.x = kv.first; r.y = bits((float)kv.second); }
+        else { r.z = kv.first; r.w = bits((float)kv.second); }
+        t++;
+      }
     }
     FLASH_CUDA_TRY(upload(s, &g.kb, kb));
   }

@@ -71,9 +71,9 @@ struct Group {
   uint16_t *cidx = nullptr;   // [E * vpe, padded to even] slots
   int ev = 0;                 // E * vpe
   // bending as a constant operator K_b (rows sum to zero), off-diagonal
-  // entries slot-major: entry t of vertex i at [t * n_pad + i] = {j, K_ij bits};
-  // empty entries are {i, 0}
-  int2 *kb = nullptr;
+  // entries in pairs, pair-major: entries 2p and 2p + 1 of vertex i at
+  // [p * n_pad + i] = {j, K_ij bits, j', K_ij' bits}; empty entries are {i, 0}
+  int4 *kb = nullptr;
   int deg_b = 0;
   float *mass = nullptr;      // [n]
   // explicit inverse (groups with one stiffness) ...

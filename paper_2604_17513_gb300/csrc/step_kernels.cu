@@ -37,7 +37,7 @@ struct GroupView {
   const int2 *edges;             // [ned]
   const int *eoff;               // [n + 1] edges owned by vertex a
   const uint16_t *coff, *cidx;   // CSR vertex -> element slots e * vpe + a
-  const int2 *kb;                // bending operator, off-diagonal entries, slot-major
+  const int4 *kb;                // bending operator, off-diagonal entries in pairs, pair-major
   int ev, deg_b;
   const float *kenv;   // per-environment stiffness scale (eigen-form groups), else null
   int bf16;            // right-hand sides as bf16 + an FP32 copy (FLASH_SOLVE_BF16R)
@@ -1104,23 +1104,28 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
         x[1][c] = qs[c * ns + j2];
         sum[0][c] = sum[1][c] = err[0][c] = err[1][c] = 0.f;
       }
-#pragma unroll 2
-      for (int t = 0; t < G.deg_b; t++) {
-        const int2 kja = __ldg(G.kb + (size_t)t * np + i), kjb = __ldg(G.kb + (size_t)t * np + j2);
-        const int ka[2] = {chk(kja.x, n, G.status), chk(kjb.x, n, G.status)};
-        const float kv[2] = {__int_as_float(kja.y), __int_as_float(kjb.y)};
+      // entries in pairs: one 16-byte load holds two (index, weight) entries
+      const int pairs = (G.deg_b + 1) >> 1;
+      for (int p = 0; p < pairs; p++) {
+        const int4 ra = __ldg(G.kb + (size_t)p * np + i), rb = __ldg(G.kb + (size_t)p * np + j2);
 #pragma unroll
-        for (int u = 0; u < 2; u++)
+        for (int h = 0; h < 2; h++) {
+          if (h == 1 && 2 * p + 1 >= G.deg_b) break;   // the filler of an odd count
+          const int ka[2] = {chk(h ? ra.z : ra.x, n, G.status), chk(h ? rb.z : rb.x, n, G.status)};
+          const float kv[2] = {__int_as_float(h ? ra.w : ra.y), __int_as_float(h ? rb.w : rb.y)};
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            const float kk = kv[u];
-            const float d = __fsub_rn(qs[c * ns + ka[u]], x[u][c]);
-            const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
-            const float s1 = __fadd_rn(sum[u][c], pr), bp = __fsub_rn(s1, sum[u][c]);
-            const float se = __fadd_rn(__fsub_rn(sum[u][c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
-            sum[u][c] = s1;
-            err[u][c] = __fadd_rn(err[u][c], __fadd_rn(se, pe));
-          }
+          for (int u = 0; u < 2; u++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              const float kk = kv[u];
+              const float d = __fsub_rn(qs[c * ns + ka[u]], x[u][c]);
+              const float pr = __fmul_rn(kk, d), pe = __fmaf_rn(kk, d, -pr);   // kk d = pr + pe exactly
+              const float s1 = __fadd_rn(sum[u][c], pr), bp = __fsub_rn(s1, sum[u][c]);
+              const float se = __fadd_rn(__fsub_rn(sum[u][c], __fsub_rn(s1, bp)), __fsub_rn(pr, bp));   // sum + pr = s1 + se
+              sum[u][c] = s1;
+              err[u][c] = __fadd_rn(err[u][c], __fadd_rn(se, pe));
+            }
+        }
       }
       const float m0 = __ldg(G.mass + i);
 #pragma unroll
