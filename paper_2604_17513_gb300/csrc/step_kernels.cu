@@ -1003,6 +1003,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       // triangles: one packed record per element (two 16-byte loads); the
       // force on the first vertex is minus the other two, so every element's
       // forces sum to zero as the operator's rows do
+#pragma unroll 2
       for (int el = threadIdx.x; el < G.E; el += blockDim.x) {
         const float4 r0 = __ldg(G.erec + 2 * el), r1 = __ldg(G.erec + 2 * el + 1);
         const int v0 = chk(__float_as_int(r0.x), n, G.status), v1 = chk(__float_as_int(r0.y), n, G.status),
@@ -1137,7 +1138,45 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       }
     }
     __syncthreads();
-    // ---- residual r = M (q~ - q) + sum_e D_a^T w~ (p_e - F_e) - bending
+    // ---- residual r = M (q~ - q) + sum_e D_a^T w~ (p_e - F_e) - bending.
+    //      Triangle meshes (about six slots a vertex): a thread's two
+    //      vertices gathered in one loop, each in its own slot order (six
+    //      independent chains); tet meshes (about twenty, more uneven) one
+    //      vertex at a time, which measured faster for them.
+    if constexpr (VPE == 3) {
+    for (int i = threadIdx.x; i < n; i += 2 * blockDim.x) {
+      const int i2 = i + blockDim.x;
+      const bool two = i2 < n;
+      float acc[2][3];
+      int t[2], t1[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int iv = u == 0 ? i : (two ? i2 : i);
+        acc[u][0] = rs[iv]; acc[u][1] = rs[ns + iv]; acc[u][2] = rs[2 * ns + iv];
+        t[u] = chk(coff[iv], G.ev + 1, G.status);
+        t1[u] = u == 1 && !two ? t[u] : chk(coff[iv + 1], G.ev + 1, G.status);
+      }
+      while (t[0] < t1[0] || t[1] < t1[1]) {
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+          if (t[u] < t1[u]) {
+            const float *f = Fs + 3 * chk(cidx[t[u]], G.ev, G.status);
+            acc[u][0] += f[0];
+            acc[u][1] += f[1];
+            acc[u][2] += f[2];
+            t[u]++;
+          }
+      }
+      rs[i] = acc[0][0];
+      rs[ns + i] = acc[0][1];
+      rs[2 * ns + i] = acc[0][2];
+      if (two) {
+        rs[i2] = acc[1][0];
+        rs[ns + i2] = acc[1][1];
+        rs[2 * ns + i2] = acc[1][2];
+      }
+    }
+    } else {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       float acc0 = rs[i], acc1 = rs[ns + i], acc2 = rs[2 * ns + i];
       const int t1 = chk(coff[i + 1], G.ev + 1, G.status);
@@ -1150,6 +1189,7 @@ __device__ __forceinline__ void local_body(const GroupView &G, const int l, cons
       rs[i] = acc0;
       rs[ns + i] = acc1;
       rs[2 * ns + i] = acc2;
+    }
     }
   }
   __syncthreads();
